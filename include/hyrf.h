@@ -1,0 +1,380 @@
+/*
+ * libhyrf: the HyRF render-and-train hot path (arXiv 2509.17083) as
+ * hand-written sm_103a CUDA kernels behind a C ABI.
+ *
+ * One view is rendered and differentiated by five stages, each a forward call
+ * and a backward call:
+ *
+ *   hyrf_query_fields          pre-cull + field query + aggregation  (Sec. 3.2-3.3, Eqs. 2-9)
+ *   hyrf_project               EWA projection to screen space         (Sec. 3.2: "3DGS rasterizer")
+ *   hyrf_bin_sort              tile binning + depth sort              (Sec. 3.1: Gaussians "ordered by depth")
+ *   hyrf_rasterize             front-to-back alpha compositing        (Sec. 3.1, Eq. 1)
+ *   hyrf_composite_background  neural background blend               (Sec. 3.3, Eqs. 10-11, App. A.2)
+ *
+ * plus the training loss of Sec. 3.4 (Eq. 12), hyrf_loss.
+ *
+ * Conventions shared by every call
+ *   - Every pointer argument is a DEVICE pointer unless its comment says
+ *     "host". The caller owns all memory; the library never allocates,
+ *     frees or synchronises (except hyrf_read_status, which synchronises
+ *     the given stream). Temporary storage is the caller's `workspace`
+ *     (device, 256-byte aligned), at least hyrf_X_workspace_size(args)
+ *     bytes; workspace contents need not be preserved between calls.
+ *   - Arrays are contiguous and row-major. float32 unless stated.
+ *   - All launches go to `stream` (a cudaStream_t, passed as void*), in
+ *     order; no call reads device memory on the host, so every call may be
+ *     captured in a CUDA graph.
+ *   - Return value: HYRF_OK, or HYRF_ERR_INVALID_ARG / HYRF_ERR_UNSUPPORTED
+ *     for arguments rejected on the host (nothing is launched), or
+ *     HYRF_ERR_CUDA if a launch failed. Errors found on the device
+ *     (capacity overflow, out-of-range input) are OR-ed into the optional
+ *     `status` word (device int32, caller-zeroed) as HYRF_ERR_* bit flags
+ *     and read back with hyrf_read_status. No call traps or prints.
+ *   - Outputs marked "accumulate" are added to (caller zeroes them);
+ *     all other outputs are overwritten.
+ *   - Index spaces: N = number of Gaussians (full arrays), V = the visible
+ *     subset produced by hyrf_query_fields (compacted arrays of capacity N,
+ *     valid entries [0, *n_vis)), K = tile instances (capacity `capacity`).
+ */
+#ifndef HYRF_H
+#define HYRF_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYRF_OK = 0,
+  HYRF_ERR_INVALID_ARG = 1,
+  HYRF_ERR_UNSUPPORTED = 2,
+  HYRF_ERR_CUDA = 4,
+  HYRF_ERR_OVERFLOW = 8,  /* device: more tile instances than `capacity` */
+  HYRF_ERR_BOUNDS = 16,   /* device: an index read from memory was out of range */
+} hyrf_status;
+
+typedef enum { HYRF_F32 = 0, HYRF_BF16 = 1 } hyrf_dtype;
+
+/* Pinhole camera, world to camera x_c = R x_w + t (Eq. 8). Pixel (i, j)
+ * samples the image plane at (i + 0.5, j + 0.5); u = fx x_c/z_c + cx.
+ * z_near: Gaussians with z_c <= z_near are culled ("too close", Sec. 3.3).
+ * cull_tol: the tolerance band "tol" of Eq. 9, applied to normalised device
+ * coordinates 2u/W - 1 and 2v/H - 1. Passed by value (host struct). */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float z_near, cull_tol;
+} hyrf_camera;
+
+/* Multi-resolution hash grid (Eq. 3): table [n_levels][2^log2_T][n_feat] of
+ * `dtype` (HYRF_F32 or HYRF_BF16). Level l has resolution
+ * floor(base_res * growth^l) and is stored densely when its (res+1)^3
+ * vertices fit in 2^log2_T entries, else spatially hashed. n_feat must be 2. */
+typedef struct {
+  const void* table;
+  int32_t n_levels, log2_T, n_feat, base_res;
+  float growth;
+  int32_t dtype;
+} hyrf_grid;
+
+/* Decoder MLP (Eqs. 4, 6; Sec. 4.1): n_hidden ReLU layers of `width`, then a
+ * linear output layer. W[0] [width][n_in], W[1] [width][width] (if
+ * n_hidden = 2), W[n_hidden] [n_out][width], all of `dtype`; biases b[l]
+ * float32. Supported: (n_hidden, width) in {(1, 32), (2, 64)}. */
+typedef struct {
+  const void* W[3];
+  const float* b[3];
+  int32_t n_in, width, n_hidden, n_out;
+  int32_t dtype;
+} hyrf_mlp;
+
+/* The two decoupled fields of Sec. 3.2 with their decoders. box: the scene
+ * box B0 mapped onto [-1,1]^3 before the contraction (App. A.1). The colour
+ * decoder's input is [f_rad (n_levels*2), PE(dir) (3 + 6 pe_freq), zero
+ * padding up to pe_pad]. geo_mlp.n_out = 8: (alpha_n, s_n[3], r_n[4]);
+ * col_mlp.n_out = 3. */
+typedef struct {
+  float box_lo[3], box_hi[3];
+  hyrf_grid geo, rad;
+  hyrf_mlp geo_mlp, col_mlp;
+  int32_t pe_freq, pe_pad;
+} hyrf_fields;
+
+/* float32 gradient buffers matching hyrf_fields (accumulate). Any pointer
+ * may be NULL to skip that gradient. Tables [n_levels][2^log2_T][2]. */
+typedef struct {
+  float* geo_table;
+  float* rad_table;
+  float* geo_W[3];
+  float* geo_b[3];
+  float* col_W[3];
+  float* col_b[3];
+} hyrf_field_grads;
+
+/* ------------------------------------------------------------------------
+ * hyrf_query_fields: visibility pre-culling (Eqs. 8-9) of all N Gaussians,
+ * ascending compaction of the kept ones, then for each kept Gaussian the
+ * contraction (Eq. 2), both hash encodings (Eq. 3), both decoders
+ * (Eqs. 4-6) and the aggregation with the explicit parameters (Eq. 7).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;                 /* N */
+  const float* pos;          /* [N][3] p_e */
+  const float* alpha_e;      /* [N] explicit opacity logit */
+  const float* scale_e;      /* [N] explicit isotropic scale logit */
+  const float* color_e;      /* [N][3] explicit colour logits */
+  hyrf_camera cam;
+  hyrf_fields fields;
+  int32_t* vis_ids;          /* out [N]: ids of visible Gaussians, ascending, first *n_vis valid */
+  int32_t* n_vis;            /* out [1] */
+  float* alpha;              /* out [V] sigma(alpha_n + alpha_e) */
+  float* scale;              /* out [V][3] sigma(s_n + s_e) */
+  float* quat;               /* out [V][4] r_n / |r_n|, (w, x, y, z) */
+  float* color;              /* out [V][3] sigma(c_n + c_e) */
+  int32_t* status;           /* optional device status word */
+} hyrf_query_fields_args;
+
+size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a);
+hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* workspace, size_t ws_bytes,
+                              void* stream);
+
+/* Reverse of hyrf_query_fields. Takes dL/d(alpha, scale, quat, color) of
+ * the visible set and adds dL/d(pos, alpha_e, scale_e, color_e) at the
+ * Gaussians' full indices and the field gradients (tables, weights,
+ * biases). Decoder activations are recomputed, not stored. loss_scale
+ * multiplies the upstream gradient inside the BF16 decoders and is divided
+ * out again before anything is written (use 1 for the FP32 path). */
+typedef struct {
+  int32_t n;
+  const float* pos;
+  const float* alpha_e;
+  const float* scale_e;
+  const float* color_e;
+  hyrf_camera cam;
+  hyrf_fields fields;
+  const int32_t* vis_ids;    /* [N] from the forward */
+  const int32_t* n_vis;      /* [1] */
+  const float* d_alpha;      /* [V] */
+  const float* d_scale;      /* [V][3] */
+  const float* d_quat;       /* [V][4] */
+  const float* d_color;      /* [V][3] */
+  float* d_pos;              /* accumulate [N][3] */
+  float* d_alpha_e;          /* accumulate [N] */
+  float* d_scale_e;          /* accumulate [N] */
+  float* d_color_e;          /* accumulate [N][3] */
+  hyrf_field_grads grads;    /* accumulate */
+  float loss_scale;
+  int32_t* status;
+} hyrf_query_fields_backward_args;
+
+size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a);
+hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a, void* workspace,
+                                       size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * hyrf_project: EWA splatting of the visible Gaussians (the 3DGS rasterizer
+ * the paper builds on): Sigma = R_q diag(s)^2 R_q^T, J the perspective
+ * Jacobian with the tangent clamped at 1.3 x the half field of view,
+ * Sigma' = J R Sigma R^T J^T + 0.3 I, conic = Sigma'^-1, radius
+ * ceil(3 sqrt(lambda_max)), and the half-open tile rectangle
+ * [floor((u - r)/tile), floor((u + r)/tile) + 1) clamped to the grid.
+ * Integer outputs follow a fixed FP32 operation order (no contraction), so
+ * they are reproducible bit for bit; when |det Sigma'| < 1e-2 a c the conic
+ * is recomputed in FP64 (fp64_flag = 1).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;                 /* N (capacity of the V arrays) */
+  const float* pos;          /* [N][3] */
+  const int32_t* vis_ids;    /* [N] */
+  const int32_t* n_vis;      /* [1] */
+  const float* scale;        /* [V][3] */
+  const float* quat;         /* [V][4] */
+  hyrf_camera cam;
+  int32_t tile;              /* tile edge in pixels; must be 16 */
+  float* mean2d;             /* out [V][2] */
+  float* conic;              /* out [V][3] (a, b, c) of Sigma'^-1 */
+  float* depth;              /* out [V] camera-space z */
+  int32_t* rect;             /* out [V][4] (x0, y0, x1, y1) in tiles, half-open */
+  int32_t* ntiles;           /* out [V] (x1-x0)(y1-y0), 0 if empty */
+  uint8_t* fp64_flag;        /* out [V], may be NULL */
+  int32_t* status;
+} hyrf_project_args;
+
+size_t hyrf_project_workspace_size(const hyrf_project_args* a);
+hyrf_status hyrf_project(const hyrf_project_args* a, void* workspace, size_t ws_bytes,
+                         void* stream);
+
+/* Reverse of hyrf_project: dL/d(mean2d, conic) -> dL/dpos (accumulate at
+ * full index), dL/dscale and dL/dquat (overwrite, [V]). */
+typedef struct {
+  int32_t n;
+  const float* pos;
+  const int32_t* vis_ids;
+  const int32_t* n_vis;
+  const float* scale;
+  const float* quat;
+  hyrf_camera cam;
+  const float* d_mean2d;     /* [V][2] */
+  const float* d_conic;      /* [V][3] */
+  float* d_pos;              /* accumulate [N][3] */
+  float* d_scale;            /* out [V][3] */
+  float* d_quat;             /* out [V][4] */
+  int32_t* status;
+} hyrf_project_backward_args;
+
+size_t hyrf_project_backward_workspace_size(const hyrf_project_backward_args* a);
+hyrf_status hyrf_project_backward(const hyrf_project_backward_args* a, void* workspace,
+                                  size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * hyrf_bin_sort: tile instances of every visible Gaussian (one per tile of
+ * its rectangle, emitted in (Gaussian, tile row-major) order), ordered by
+ * the 64-bit key (tile << 32) | float_bits(depth) with a stable LSD radix
+ * sort, and the per-tile [start, end) ranges. The 32 depth bits are sorted
+ * on the V Gaussians before the instances are emitted (identical result to
+ * sorting the instances on them: a Gaussian's instances share its depth and
+ * are contiguous), the tile bits on the K instances.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;                 /* N (capacity of the V arrays) */
+  const int32_t* n_vis;      /* [1] */
+  const int32_t* rect;       /* [V][4] */
+  const int32_t* ntiles;     /* [V] */
+  const float* depth;        /* [V] (> 0) */
+  int32_t tiles_x, tiles_y;
+  int64_t capacity;          /* capacity of keys / vals */
+  uint64_t* keys;            /* out [capacity] sort keys, may be NULL */
+  int32_t* vals;             /* out [capacity] visible index per instance */
+  int32_t* ranges;           /* out [tiles_y*tiles_x][2] */
+  int32_t* n_instances;      /* out [1] K (clamped to capacity; HYRF_ERR_OVERFLOW if above) */
+  int32_t* status;
+} hyrf_bin_sort_args;
+
+size_t hyrf_bin_sort_workspace_size(const hyrf_bin_sort_args* a);
+hyrf_status hyrf_bin_sort(const hyrf_bin_sort_args* a, void* workspace, size_t ws_bytes,
+                          void* stream);
+/* Binning is discrete: its reverse only validates the arguments. */
+hyrf_status hyrf_bin_sort_backward(const hyrf_bin_sort_args* a, void* workspace, size_t ws_bytes,
+                                   void* stream);
+
+/* ------------------------------------------------------------------------
+ * hyrf_rasterize: per 16x16 tile, front-to-back compositing of Eq. 1:
+ * alpha_i = min(0.99, o_i exp(-1/2 d^T conic d)), skipped if < 1/255;
+ * a pixel stops before T (1 - alpha) < 1e-4.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;                 /* N (capacity of the V arrays) */
+  const int32_t* n_vis;
+  const int32_t* ranges;     /* [tiles][2] */
+  const int32_t* vals;       /* [K] */
+  const float* mean2d;       /* [V][2] */
+  const float* conic;        /* [V][3] */
+  const float* alpha;        /* [V] opacity */
+  const float* color;        /* [V][3] */
+  int32_t width, height, tile;
+  float* C_fg;               /* out [H][W][3] */
+  float* T_final;            /* out [H][W] */
+  int32_t* n_contrib;        /* out [H][W] list position of the last contributor + 1 */
+  int32_t* status;
+} hyrf_rasterize_args;
+
+size_t hyrf_rasterize_workspace_size(const hyrf_rasterize_args* a);
+hyrf_status hyrf_rasterize(const hyrf_rasterize_args* a, void* workspace, size_t ws_bytes,
+                           void* stream);
+
+/* Reverse of hyrf_rasterize, back to front, recovering T from T_final:
+ * dL/d(C_fg, T_final) -> dL/d(mean2d, conic, alpha, color) (accumulate). */
+typedef struct {
+  hyrf_rasterize_args fwd;   /* the forward's arguments; its outputs are inputs here */
+  const float* d_C_fg;       /* [H][W][3] */
+  const float* d_T_final;    /* [H][W] */
+  float* d_mean2d;           /* accumulate [V][2] */
+  float* d_conic;            /* accumulate [V][3] */
+  float* d_alpha;            /* accumulate [V] */
+  float* d_color;            /* accumulate [V][3] */
+} hyrf_rasterize_backward_args;
+
+size_t hyrf_rasterize_backward_workspace_size(const hyrf_rasterize_backward_args* a);
+hyrf_status hyrf_rasterize_backward(const hyrf_rasterize_backward_args* a, void* workspace,
+                                    size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * hyrf_composite_background: for each pixel, the ray o + t d hits the
+ * sphere |x| = radius (centred at the origin of the normalised box space,
+ * App. A.2; positive root); the colour c_s = sigma(dec(enc(contract(p_s);
+ * Theta_rad) (+) PE(d); Phi_c)) and C = C_fg + T_final c_s (Eqs. 10-11).
+ * mode 0 queries the field per pixel; mode 1 evaluates it on a map_h x
+ * map_w equirectangular map of directions and samples it bilinearly.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t mode, map_h, map_w;
+  float radius;
+} hyrf_background;
+
+typedef struct {
+  hyrf_camera cam;
+  hyrf_fields fields;        /* rad grid and col_mlp are used */
+  hyrf_background bg;
+  const float* C_fg;         /* [H][W][3] */
+  const float* T_final;      /* [H][W] */
+  float* C;                  /* out [H][W][3] */
+  int32_t* status;
+} hyrf_composite_background_args;
+
+size_t hyrf_composite_background_workspace_size(const hyrf_composite_background_args* a);
+hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, void* workspace,
+                                      size_t ws_bytes, void* stream);
+
+/* Reverse: dL/dC -> dL/dT_final (out), dL/dC_fg (out, = dL/dC; may be NULL
+ * when the caller passes dL/dC on as dL/dC_fg) and the radiance-field and
+ * colour-decoder gradients (accumulate, into grads.rad_table / col_*). */
+typedef struct {
+  hyrf_composite_background_args fwd;
+  const float* d_C;          /* [H][W][3] */
+  float* d_C_fg;             /* out [H][W][3], may be NULL */
+  float* d_T_final;          /* out [H][W] */
+  hyrf_field_grads grads;    /* accumulate */
+  float loss_scale;
+} hyrf_composite_background_backward_args;
+
+size_t hyrf_composite_background_backward_workspace_size(
+    const hyrf_composite_background_backward_args* a);
+hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_backward_args* a,
+                                               void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * hyrf_loss: Eq. 12, L = (1 - lambda) mean|C - target| + lambda (1 - SSIM)
+ * with an 11x11 Gaussian window (sigma 1.5, zero padding), means over all
+ * pixels and channels. Writes L to *loss and, if d_C is not NULL,
+ * grad_scale * dL/dC to d_C.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t width, height;
+  const float* C;            /* [H][W][3] */
+  const float* target;       /* [H][W][3] */
+  float lambda;
+  float grad_scale;
+  float* loss;               /* out [1] */
+  float* d_C;                /* out [H][W][3], may be NULL */
+} hyrf_loss_args;
+
+size_t hyrf_loss_workspace_size(const hyrf_loss_args* a);
+hyrf_status hyrf_loss(const hyrf_loss_args* a, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Synchronises `stream`, copies the device status word to *host_out (host
+ * pointer) and returns it as hyrf_status bits (HYRF_ERR_CUDA if the copy
+ * failed). */
+hyrf_status hyrf_read_status(const int32_t* status, void* stream, int32_t* host_out);
+const char* hyrf_error_string(int32_t status);
+/* Number of kernel launches issued by this library since load (host
+ * counter; for launch accounting in benchmarks). */
+uint64_t hyrf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

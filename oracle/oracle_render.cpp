@@ -396,7 +396,7 @@ int32_t orc_project_f32(int32_t n, const float* pos, const float* scale, const f
     rect[4 * i + 3] = iy1;
     ntiles[i] = (ix1 > ix0 && iy1 > iy0) ? (ix1 - ix0) * (iy1 - iy0) : 0;
     depth[i] = z;
-    flag[i] = std::fabs(det) < 1e-3f * a * cc ? 1 : 0;
+    flag[i] = std::fabs(det) < 1e-2f * a * cc ? 1 : 0;
   }
   return 0;
 }

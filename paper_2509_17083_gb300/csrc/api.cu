@@ -1,0 +1,287 @@
+// extern "C" entry points of libhyrf (declared in include/hyrf.h): argument
+// checks on the host, workspace sizing and kernel dispatch.
+#include <atomic>
+
+#include "common.cuh"
+
+namespace hyrf {
+
+// launchers (one per translation unit)
+size_t precull_workspace(int n);
+hyrf_status launch_precull(const CamDev& cam, const float* pos, int n, int32_t* vis_ids,
+                           int32_t* n_vis, void* ws, cudaStream_t s);
+hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int32_t* vis_ids,
+                           const int32_t* n_vis, const float* scale, const float* quat, float* mean2d,
+                           float* conic, float* depth, int32_t* rect, int32_t* ntiles, uint8_t* flag,
+                           int32_t* status, cudaStream_t s);
+hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t s);
+hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
+hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
+                             cudaStream_t s);
+size_t slab_bytes(const FieldsDev& F, bool geo);
+size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward);
+hyrf_status launch_bg_fwd(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
+                          cudaStream_t s);
+hyrf_status launch_bg_bwd(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
+                          void* ws, cudaStream_t s);
+size_t bin_sort_workspace(int n, int64_t cap);
+hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t s);
+size_t raster_workspace(int n);
+hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream_t s);
+hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, cudaStream_t s);
+size_t loss_workspace(const hyrf_loss_args& a);
+hyrf_status launch_loss(const hyrf_loss_args& a, void* ws, cudaStream_t s);
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 148;
+  }
+  return sms;
+}
+
+static bool cam_ok(const hyrf_camera& c) {
+  return c.width > 0 && c.height > 0 && c.width <= 16384 && c.height <= 16384 && c.fx > 0.0f &&
+         c.fy > 0.0f && c.z_near >= 0.0f && c.cull_tol >= 0.0f;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static bool ws_ok(void* ws, size_t have, size_t need) {
+  return have >= need && (need == 0 || (ws != nullptr && aligned(ws, 256)));
+}
+
+}  // namespace hyrf
+
+using namespace hyrf;
+
+#define S(x) static_cast<cudaStream_t>(x)
+
+extern "C" {
+
+// ------------------------------------------------------------------ query fields
+
+size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a) {
+  return a ? precull_workspace(a->n) : 0;
+}
+
+hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (!a || a->n < 0 || !cam_ok(a->cam)) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->pos || !a->alpha_e || !a->scale_e || !a->color_e || !a->vis_ids || !a->alpha ||
+                   !a->scale || !a->quat || !a->color))
+    return HYRF_ERR_INVALID_ARG;
+  if (!a->n_vis || !ws_ok(ws, ws_bytes, hyrf_query_fields_workspace_size(a)))
+    return HYRF_ERR_INVALID_ARG;
+  FieldsDev F;
+  if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
+  if (F.gm.bf16 || F.cm.bf16) return HYRF_ERR_UNSUPPORTED;
+  hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
+  if (st != HYRF_OK) return st;
+  return launch_query_fwd(*a, F, S(stream));
+}
+
+size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a) {
+  if (!a) return 0;
+  FieldsDev F;
+  if (!make_fields(a->fields, F, true)) return 0;
+  return align_up(slab_bytes(F, true));
+}
+
+hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  if (!a || a->n < 0 || !cam_ok(a->cam) || !(a->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->pos || !a->alpha_e || !a->scale_e || !a->color_e || !a->vis_ids || !a->n_vis ||
+                   !a->d_alpha || !a->d_scale || !a->d_quat || !a->d_color || !a->d_pos ||
+                   !a->d_alpha_e || !a->d_scale_e || !a->d_color_e))
+    return HYRF_ERR_INVALID_ARG;
+  FieldsDev F;
+  if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
+  if (F.gm.bf16 || F.cm.bf16) return HYRF_ERR_UNSUPPORTED;
+  if (!ws_ok(ws, ws_bytes, hyrf_query_fields_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_query_bwd(*a, F, ws, S(stream));
+}
+
+// ------------------------------------------------------------------ project
+
+size_t hyrf_project_workspace_size(const hyrf_project_args*) { return 0; }
+
+hyrf_status hyrf_project(const hyrf_project_args* a, void* ws, size_t ws_bytes, void* stream) {
+  (void)ws;
+  (void)ws_bytes;
+  if (!a || a->n < 0 || !cam_ok(a->cam) || a->tile != kTile) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->pos || !a->vis_ids || !a->n_vis || !a->scale || !a->quat || !a->mean2d ||
+                   !a->conic || !a->depth || !a->rect || !a->ntiles))
+    return HYRF_ERR_INVALID_ARG;
+  return launch_project(to_dev(a->cam), a->n, a->pos, a->vis_ids, a->n_vis, a->scale, a->quat,
+                        a->mean2d, a->conic, a->depth, a->rect, a->ntiles, a->fp64_flag, a->status,
+                        S(stream));
+}
+
+size_t hyrf_project_backward_workspace_size(const hyrf_project_backward_args*) { return 0; }
+
+hyrf_status hyrf_project_backward(const hyrf_project_backward_args* a, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  (void)ws;
+  (void)ws_bytes;
+  if (!a || a->n < 0 || !cam_ok(a->cam)) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->pos || !a->vis_ids || !a->n_vis || !a->scale || !a->quat || !a->d_mean2d ||
+                   !a->d_conic || !a->d_pos || !a->d_scale || !a->d_quat))
+    return HYRF_ERR_INVALID_ARG;
+  return launch_project_bwd(*a, S(stream));
+}
+
+// ------------------------------------------------------------------ bin + sort
+
+size_t hyrf_bin_sort_workspace_size(const hyrf_bin_sort_args* a) {
+  return a && a->n >= 0 && a->capacity >= 0 ? bin_sort_workspace(a->n, a->capacity) : 0;
+}
+
+static hyrf_status bin_sort_check(const hyrf_bin_sort_args* a) {
+  if (!a || a->n < 0 || a->tiles_x <= 0 || a->tiles_y <= 0 || a->capacity < 0 ||
+      a->capacity > 0x7fffffffLL || (int64_t)a->tiles_x * a->tiles_y > (1 << 24))
+    return HYRF_ERR_INVALID_ARG;
+  if (!a->n_vis || !a->ranges || !a->n_instances) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->rect || !a->ntiles || !a->depth)) return HYRF_ERR_INVALID_ARG;
+  if (a->capacity > 0 && !a->vals) return HYRF_ERR_INVALID_ARG;
+  return HYRF_OK;
+}
+
+hyrf_status hyrf_bin_sort(const hyrf_bin_sort_args* a, void* ws, size_t ws_bytes, void* stream) {
+  hyrf_status st = bin_sort_check(a);
+  if (st != HYRF_OK) return st;
+  if (!ws_ok(ws, ws_bytes, hyrf_bin_sort_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_bin_sort(*a, ws, S(stream));
+}
+
+hyrf_status hyrf_bin_sort_backward(const hyrf_bin_sort_args* a, void* ws, size_t ws_bytes,
+                                   void* stream) {
+  (void)ws;
+  (void)ws_bytes;
+  (void)stream;
+  return bin_sort_check(a);
+}
+
+// ------------------------------------------------------------------ rasterize
+
+static hyrf_status raster_check(const hyrf_rasterize_args* a) {
+  if (!a || a->n < 0 || a->width <= 0 || a->height <= 0 || a->tile != kTile) return HYRF_ERR_INVALID_ARG;
+  if (!a->n_vis || !a->ranges || !a->C_fg || !a->T_final || !a->n_contrib) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->vals || !a->mean2d || !a->conic || !a->alpha || !a->color))
+    return HYRF_ERR_INVALID_ARG;
+  return HYRF_OK;
+}
+
+size_t hyrf_rasterize_workspace_size(const hyrf_rasterize_args* a) {
+  return a ? raster_workspace(a->n) : 0;
+}
+
+hyrf_status hyrf_rasterize(const hyrf_rasterize_args* a, void* ws, size_t ws_bytes, void* stream) {
+  hyrf_status st = raster_check(a);
+  if (st != HYRF_OK) return st;
+  if (!ws_ok(ws, ws_bytes, hyrf_rasterize_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_raster_fwd(*a, ws, S(stream));
+}
+
+size_t hyrf_rasterize_backward_workspace_size(const hyrf_rasterize_backward_args* a) {
+  return a ? raster_workspace(a->fwd.n) : 0;
+}
+
+hyrf_status hyrf_rasterize_backward(const hyrf_rasterize_backward_args* a, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  if (!a) return HYRF_ERR_INVALID_ARG;
+  hyrf_status st = raster_check(&a->fwd);
+  if (st != HYRF_OK) return st;
+  if (!a->d_C_fg || !a->d_T_final) return HYRF_ERR_INVALID_ARG;
+  if (a->fwd.n > 0 && (!a->d_mean2d || !a->d_conic || !a->d_alpha || !a->d_color))
+    return HYRF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, hyrf_rasterize_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_raster_bwd(*a, ws, S(stream));
+}
+
+// ------------------------------------------------------------------ background
+
+static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& F) {
+  if (!a || !cam_ok(a->cam) || !a->C_fg || !a->T_final) return HYRF_ERR_INVALID_ARG;
+  if (!(a->bg.radius > 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (a->bg.mode == 1 && (a->bg.map_h <= 0 || a->bg.map_w <= 0 || a->bg.map_h > 4096 || a->bg.map_w > 4096))
+    return HYRF_ERR_INVALID_ARG;
+  if (a->bg.mode != 0 && a->bg.mode != 1) return HYRF_ERR_INVALID_ARG;
+  if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
+  if (F.cm.bf16) return HYRF_ERR_UNSUPPORTED;
+  return HYRF_OK;
+}
+
+size_t hyrf_composite_background_workspace_size(const hyrf_composite_background_args* a) {
+  FieldsDev F;
+  if (!a || !make_fields(a->fields, F, false)) return 0;
+  return bg_workspace(*a, F, false);
+}
+
+hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  FieldsDev F;
+  hyrf_status st = bg_check(a, F);
+  if (st != HYRF_OK) return st;
+  if (!a->C || !ws_ok(ws, ws_bytes, bg_workspace(*a, F, false))) return HYRF_ERR_INVALID_ARG;
+  return launch_bg_fwd(*a, F, ws, S(stream));
+}
+
+size_t hyrf_composite_background_backward_workspace_size(
+    const hyrf_composite_background_backward_args* b) {
+  FieldsDev F;
+  if (!b || !make_fields(b->fwd.fields, F, false)) return 0;
+  return bg_workspace(b->fwd, F, true);
+}
+
+hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_backward_args* b,
+                                               void* ws, size_t ws_bytes, void* stream) {
+  if (!b) return HYRF_ERR_INVALID_ARG;
+  FieldsDev F;
+  hyrf_status st = bg_check(&b->fwd, F);
+  if (st != HYRF_OK) return st;
+  if (!b->d_C || !b->d_T_final || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, bg_workspace(b->fwd, F, true))) return HYRF_ERR_INVALID_ARG;
+  return launch_bg_bwd(*b, F, ws, S(stream));
+}
+
+// ------------------------------------------------------------------ loss
+
+size_t hyrf_loss_workspace_size(const hyrf_loss_args* a) { return a ? loss_workspace(*a) : 0; }
+
+hyrf_status hyrf_loss(const hyrf_loss_args* a, void* ws, size_t ws_bytes, void* stream) {
+  if (!a || a->width <= 0 || a->height <= 0 || !a->C || !a->target || !a->loss) return HYRF_ERR_INVALID_ARG;
+  if (!(a->lambda >= 0.0f && a->lambda <= 1.0f)) return HYRF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, loss_workspace(*a))) return HYRF_ERR_INVALID_ARG;
+  return launch_loss(*a, ws, S(stream));
+}
+
+// ------------------------------------------------------------------ misc
+
+hyrf_status hyrf_read_status(const int32_t* status, void* stream, int32_t* host_out) {
+  if (!status || !host_out) return HYRF_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(host_out, status, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess)
+    return HYRF_ERR_CUDA;
+  if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return HYRF_ERR_CUDA;
+  return static_cast<hyrf_status>(*host_out);
+}
+
+const char* hyrf_error_string(int32_t st) {
+  if (st == HYRF_OK) return "ok";
+  if (st & HYRF_ERR_CUDA) return "CUDA launch or copy failed";
+  if (st & HYRF_ERR_INVALID_ARG) return "invalid argument";
+  if (st & HYRF_ERR_UNSUPPORTED) return "unsupported configuration";
+  if (st & HYRF_ERR_OVERFLOW) return "tile instances exceeded the capacity";
+  if (st & HYRF_ERR_BOUNDS) return "an index read from memory was out of range";
+  return "unknown status";
+}
+
+uint64_t hyrf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

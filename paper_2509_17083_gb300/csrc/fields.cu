@@ -1,0 +1,817 @@
+// Field query (Sec. 3.2, Eqs. 2-7) and neural background (Sec. 3.3,
+// Eqs. 10-11, App. A.2): FP32 CUDA-core kernels, forward and backward.
+// Backward kernels recompute the decoder activations, keep them in shared
+// memory as [feature][point] tiles, and reduce the weight gradients per CTA
+// into a private float32 slab (no atomics); one reduction kernel adds the
+// slabs into the caller's gradient buffers.
+#include <cmath>
+
+#include "field_ops.cuh"
+
+namespace hyrf {
+
+struct QueryFwdIO {
+  int n;
+  const float* pos;
+  const float* alpha_e;
+  const float* scale_e;
+  const float* color_e;
+  const int32_t* vis_ids;
+  const int32_t* n_vis;
+  float* alpha;
+  float* scale;
+  float* quat;
+  float* color;
+  int32_t* status;
+};
+
+struct QueryBwdIO {
+  int n;
+  const float* pos;
+  const float* alpha_e;
+  const float* scale_e;
+  const float* color_e;
+  const int32_t* vis_ids;
+  const int32_t* n_vis;
+  const float* d_alpha;
+  const float* d_scale;
+  const float* d_quat;
+  const float* d_color;
+  float* d_pos;
+  float* d_alpha_e;
+  float* d_scale_e;
+  float* d_color_e;
+  float* g_geo_table;
+  float* g_rad_table;
+  float loss_scale;
+  int32_t* status;
+};
+
+__device__ __forceinline__ void cam_center(const CamDev& c, float pc[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
+}
+
+template <int NL, int WID, int NH>
+__global__ void __launch_bounds__(128) k_query_fwd(FieldsDev F, CamDev cam, QueryFwdIO io) {
+  constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
+  const int nv = min(*io.n_vis, io.n);
+  float pc[3];
+  cam_center(cam, pc);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    const int g = io.vis_ids[i];
+    if (g < 0 || g >= io.n) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      continue;
+    }
+    const float p[3] = {io.pos[3 * (int64_t)g], io.pos[3 * (int64_t)g + 1], io.pos[3 * (int64_t)g + 2]};
+    float y[3];
+    contract_p(F, p, y, nullptr);
+    float go[8];
+    {
+      float fg[NG];
+      encode<NL>(F.geo, y, fg);
+      mlp_fwd<NG, WID, NH, 8>(F.gm, fg, go);
+    }
+    float co[3];
+    {
+      float fc[NC];
+      encode<NL>(F.rad, y, fc);
+      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+      const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+      pos_enc(dir, fc + NG);
+      mlp_fwd<NC, WID, NH, 3>(F.cm, fc, co);
+    }
+    // Eq. 7 aggregation with the explicit parameters.
+    io.alpha[i] = sigmoidf_(go[0] + io.alpha_e[g]);
+    const float se = io.scale_e[g];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(go[1 + k] + se);
+    const float rn = sqrtf(go[4] * go[4] + go[5] * go[5] + go[6] * go[6] + go[7] * go[7]);
+    const float den = fmaxf(rn, 1e-12f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = go[4 + k] / den;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) io.color[3 * i + k] = sigmoidf_(co[k] + io.color_e[3 * (int64_t)g + k]);
+  }
+}
+
+// Reverse of a decoder whose activations are in smem (act: input rows
+// [0, IN), hidden rows after it) and whose output gradient dz_out is given;
+// updates the CTA slab and returns dL/dinput in dx. All threads of the CTA
+// must call it (it synchronises).
+template <int IN, int WID, int NH, int OUT>
+__device__ __forceinline__ void decoder_bwd(const MlpDev& m, const float* act, float* dzb,
+                                            const float* dz_out, float* slab, const SlabLayout& SL,
+                                            int dec, float* dx) {
+  const int t = threadIdx.x;
+  const float* hl = act + (IN + (NH - 1) * WID) * kActPitch;
+#pragma unroll
+  for (int r = 0; r < OUT; ++r) dzb[r * kActPitch + t] = dz_out[r];
+  __syncthreads();
+  cta_dw<OUT, WID>(dzb, hl, slab + SL.off_W[dec][NH], slab + SL.off_b[dec][NH]);
+  float dh[WID], dz[WID];
+  dense_dx<WID, OUT>(static_cast<const float*>(m.W[NH]), dz_out, dh);
+#pragma unroll
+  for (int r = 0; r < WID; ++r) dz[r] = hl[r * kActPitch + t] > 0.0f ? dh[r] : 0.0f;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < WID; ++r) dzb[r * kActPitch + t] = dz[r];
+  __syncthreads();
+  if constexpr (NH == 2) {
+    const float* h1 = act + IN * kActPitch;
+    cta_dw<WID, WID>(dzb, h1, slab + SL.off_W[dec][1], slab + SL.off_b[dec][1]);
+    dense_dx<WID, WID>(static_cast<const float*>(m.W[1]), dz, dh);
+#pragma unroll
+    for (int r = 0; r < WID; ++r) dz[r] = h1[r * kActPitch + t] > 0.0f ? dh[r] : 0.0f;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < WID; ++r) dzb[r * kActPitch + t] = dz[r];
+    __syncthreads();
+  }
+  cta_dw<WID, IN>(dzb, act, slab + SL.off_W[dec][0], slab + SL.off_b[dec][0]);
+  dense_dx<IN, WID>(static_cast<const float*>(m.W[0]), dz, dx);
+  __syncthreads();
+}
+
+// Forward of a decoder storing its input and hidden activations in smem.
+template <int IN, int WID, int NH, int OUT>
+__device__ __forceinline__ void decoder_fwd_store(const MlpDev& m, const float* x, float* act,
+                                                  float* out) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < IN; ++r) act[r * kActPitch + t] = x[r];
+  float h1[WID];
+  dense_fwd<IN, WID, true>(static_cast<const float*>(m.W[0]), m.b[0], x, h1);
+#pragma unroll
+  for (int r = 0; r < WID; ++r) act[(IN + r) * kActPitch + t] = h1[r];
+  if constexpr (NH == 2) {
+    float h2[WID];
+    dense_fwd<WID, WID, true>(static_cast<const float*>(m.W[1]), m.b[1], h1, h2);
+#pragma unroll
+    for (int r = 0; r < WID; ++r) act[(IN + WID + r) * kActPitch + t] = h2[r];
+    dense_fwd<WID, OUT, false>(static_cast<const float*>(m.W[2]), m.b[2], h2, out);
+  } else {
+    dense_fwd<WID, OUT, false>(static_cast<const float*>(m.W[1]), m.b[1], h1, out);
+  }
+}
+
+template <int NL, int WID, int NH>
+constexpr int query_bwd_smem_floats() {
+  return (2 * NL + kPEPad + NH * WID) * kActPitch + WID * kActPitch;
+}
+
+template <int NL, int WID, int NH>
+__global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev cam, QueryBwdIO io,
+                                                           SlabLayout SL, float* slabs) {
+  extern __shared__ float sm[];
+  constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
+  float* act = sm;
+  float* dzb = sm + (NC + NH * WID) * kActPitch;
+  float* slab = slabs + (size_t)blockIdx.x * SL.total;
+  const int t = threadIdx.x;
+  const int nv = min(*io.n_vis, io.n);
+  const float ls = io.loss_scale, inv_ls = 1.0f / io.loss_scale;
+  float pc[3];
+  cam_center(cam, pc);
+  for (int base = blockIdx.x * kBwdThreads; base < nv; base += gridDim.x * kBwdThreads) {
+    const int i = base + t;
+    bool ok = i < nv;
+    int g = ok ? io.vis_ids[i] : 0;
+    if (ok && (g < 0 || g >= io.n)) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      ok = false;
+    }
+    float p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];  // box centre when idle
+    float y[3], J[9];
+    contract_p(F, p, y, J);
+    float da = 0.0f, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dcol[3] = {0, 0, 0};
+    float ae = 0.0f, se = 0.0f, ce[3] = {0, 0, 0};
+    if (ok) {
+      da = io.d_alpha[i] * ls;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ds[k] = io.d_scale[3 * i + k] * ls;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dq[k] = io.d_quat[4 * i + k] * ls;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dcol[k] = io.d_color[3 * i + k] * ls;
+      ae = io.alpha_e[g];
+      se = io.scale_e[g];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ce[k] = io.color_e[3 * (int64_t)g + k];
+    }
+    float dy[3] = {0.0f, 0.0f, 0.0f};
+    // ---------------- geometry decoder (Eq. 4) and the reverse of Eq. 7
+    {
+      float x0[NG], out[8], dz8[8];
+      encode<NL>(F.geo, y, x0);
+      decoder_fwd_store<NG, WID, NH, 8>(F.gm, x0, act, out);
+      const float a = sigmoidf_(out[0] + ae);
+      dz8[0] = da * a * (1.0f - a);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float s = sigmoidf_(out[1 + k] + se);
+        dz8[1 + k] = ds[k] * s * (1.0f - s);
+      }
+      const float rn = sqrtf(out[4] * out[4] + out[5] * out[5] + out[6] * out[6] + out[7] * out[7]);
+      if (rn > 1e-12f) {
+        float qd = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qd += out[4 + k] / rn * dq[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dz8[4 + k] = (dq[k] - out[4 + k] / rn * qd) / rn;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dz8[4 + k] = dq[k] / 1e-12f;
+      }
+      if (!ok) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dz8[k] = 0.0f;
+      }
+      if (ok) {
+        io.d_alpha_e[g] += dz8[0] * inv_ls;
+        io.d_scale_e[g] += (dz8[1] + dz8[2] + dz8[3]) * inv_ls;
+      }
+      float dx[NG];
+      decoder_bwd<NG, WID, NH, 8>(F.gm, act, dzb, dz8, slab, SL, 0, dx);
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
+        encode_bwd<NL>(F.geo, y, dx, io.g_geo_table, dy);
+      }
+    }
+    // ---------------- colour decoder (Eqs. 5-6) and the reverse of Eq. 7
+    float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+    const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+    float dp[3] = {0.0f, 0.0f, 0.0f};
+    {
+      float x0[NC], out[3], dz3[3];
+      encode<NL>(F.rad, y, x0);
+      pos_enc(dir, x0 + NG);
+      decoder_fwd_store<NC, WID, NH, 3>(F.cm, x0, act, out);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float c = sigmoidf_(out[k] + ce[k]);
+        dz3[k] = ok ? dcol[k] * c * (1.0f - c) : 0.0f;
+      }
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) io.d_color_e[3 * (int64_t)g + k] += dz3[k] * inv_ls;
+      }
+      float dx[NC];
+      decoder_bwd<NC, WID, NH, 3>(F.cm, act, dzb, dz3, slab, SL, 1, dx);
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) dx[k] *= inv_ls;
+        encode_bwd<NL>(F.rad, y, dx, io.g_rad_table, dy);
+        float ddir[3];
+        pos_enc_bwd(dir, dx + NG, ddir);
+        const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dp[k] = (ddir[k] - dir[k] * dd) / vn;
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        io.d_pos[3 * (int64_t)g + j] += dp[j] + J[j] * dy[0] + J[3 + j] * dy[1] + J[6 + j] * dy[2];
+    }
+  }
+}
+
+// Adds sum over CTAs of the slabs (times `scale`) into the gradient buffers.
+struct SlabTargets {
+  float* W[2][3];
+  float* b[2][3];
+};
+
+__global__ void k_slab_reduce(const float* __restrict__ slabs, int nslabs, SlabLayout SL,
+                              SlabTargets T, float scale) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < SL.total; e += gridDim.x * blockDim.x) {
+    float* dst = nullptr;
+    for (int d = 0; d < 2; ++d)
+      for (int l = 0; l < 3; ++l) {
+        if (e >= SL.off_W[d][l] && e < SL.off_W[d][l] + SL.n_W[d][l] && T.W[d][l])
+          dst = T.W[d][l] + (e - SL.off_W[d][l]);
+        if (e >= SL.off_b[d][l] && e < SL.off_b[d][l] + SL.n_b[d][l] && T.b[d][l])
+          dst = T.b[d][l] + (e - SL.off_b[d][l]);
+      }
+    if (!dst) continue;
+    float s = 0.0f;
+    for (int c = 0; c < nslabs; ++c) s += slabs[(size_t)c * SL.total + e];
+    *dst += s * scale;
+  }
+}
+
+// ---------------------------------------------------------------- background (Eqs. 10-11)
+
+// Pixel (i, j): hit point p_s of the ray with the sphere |x| = r in the
+// normalised box space (App. A.2, positive root) and the unit world-space
+// ray direction.
+__device__ __forceinline__ void bg_ray(const CamDev& c, const FieldsDev& F, float radius, int i, int j,
+                                       float ps[3], float dirw[3]) {
+  float oc[3];
+  cam_center(c, oc);
+  const float dc[3] = {((float)i + 0.5f - c.cx) / c.fx, ((float)j + 0.5f - c.cy) / c.fy, 1.0f};
+  float on[3], dn[3], dw[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dw[k] = c.R[k] * dc[0] + c.R[3 + k] * dc[1] + c.R[6 + k] * dc[2];
+    on[k] = (oc[k] - F.lo[k]) * F.sx[k] - 1.0f;
+    dn[k] = dw[k] * F.sx[k];
+  }
+  const float A = dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2];
+  const float B = 2.0f * (on[0] * dn[0] + on[1] * dn[1] + on[2] * dn[2]);
+  const float C = on[0] * on[0] + on[1] * on[1] + on[2] * on[2] - radius * radius;
+  const float t = (-B + sqrtf(B * B - 4.0f * A * C)) / (2.0f * A);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ps[k] = on[k] + t * dn[k];
+  const float nd = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dirw[k] = dw[k] / nd;
+}
+
+// Equirectangular texel (a, b): unit direction and contracted point r * dir.
+__device__ __forceinline__ void texel_point(int a, int b, int Hb, int Wb, float radius, float y[3],
+                                            float dir[3]) {
+  const float phi = ((float)b + 0.5f) / (float)Wb * 6.28318530717959f - 3.14159265358979f;
+  const float th = ((float)a + 0.5f) / (float)Hb * 3.14159265358979f - 1.57079632679490f;
+  float sp, cp, st, ct;
+  sincosf(phi, &sp, &cp);
+  sincosf(th, &st, &ct);
+  dir[0] = ct * sp;
+  dir[1] = st;
+  dir[2] = ct * cp;
+  const float x[3] = {radius * dir[0], radius * dir[1], radius * dir[2]};
+  contract_n(x, y);
+}
+
+// Bilinear footprint of the direction of p_s in the map (wrap in longitude,
+// clamp in latitude).
+struct MapTap {
+  int a[2], b[2];
+  float wa[2], wb[2];
+};
+
+__device__ __forceinline__ MapTap map_tap(const float ps[3], int Hb, int Wb) {
+  const float n = sqrtf(ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2]);
+  const float w1 = fminf(1.0f, fmaxf(-1.0f, ps[1] / n));
+  const float th = asinf(w1);
+  const float phi = atan2f(ps[0] / n, ps[2] / n);
+  const float bf = (phi + 3.14159265358979f) / 6.28318530717959f * (float)Wb - 0.5f;
+  const float af = (th + 1.57079632679490f) / 3.14159265358979f * (float)Hb - 0.5f;
+  const float b0 = floorf(bf), a0 = floorf(af);
+  MapTap m;
+  m.wb[1] = bf - b0;
+  m.wb[0] = 1.0f - m.wb[1];
+  m.wa[1] = af - a0;
+  m.wa[0] = 1.0f - m.wa[1];
+  const int ib = (int)b0, ia = (int)a0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    m.b[k] = ((ib + k) % Wb + Wb) % Wb;
+    m.a[k] = min(Hb - 1, max(0, ia + k));
+  }
+  return m;
+}
+
+// Background colour at contracted point y with view direction dir.
+template <int NL, int WID, int NH>
+__device__ __forceinline__ void bg_color(const FieldsDev& F, const float y[3], const float dir[3],
+                                         float cs[3]) {
+  constexpr int NG = 2 * NL, NC = NG + kPEPad;
+  float x0[NC], out[3];
+  encode<NL>(F.rad, y, x0);
+  pos_enc(dir, x0 + NG);
+  mlp_fwd<NC, WID, NH, 3>(F.cm, x0, out);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cs[k] = sigmoidf_(out[k]);
+}
+
+template <int NL, int WID, int NH>
+__global__ void __launch_bounds__(128) k_bg_exact_fwd(FieldsDev F, CamDev cam, float radius,
+                                                      const float* __restrict__ C_fg,
+                                                      const float* __restrict__ T_final,
+                                                      float* __restrict__ C) {
+  const int P = cam.W * cam.H;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const int i = p % cam.W, j = p / cam.W;
+    float ps[3], dir[3], y[3], cs[3];
+    bg_ray(cam, F, radius, i, j, ps, dir);
+    contract_n(ps, y);
+    bg_color<NL, WID, NH>(F, y, dir, cs);
+    const float T = T_final[p];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * cs[k];
+  }
+}
+
+template <int NL, int WID, int NH>
+__global__ void __launch_bounds__(128) k_bg_map_texels(FieldsDev F, int Hb, int Wb, float radius,
+                                                       float* __restrict__ map) {
+  const int n = Hb * Wb;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    float y[3], dir[3], cs[3];
+    texel_point(e / Wb, e % Wb, Hb, Wb, radius, y, dir);
+    bg_color<NL, WID, NH>(F, y, dir, cs);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) map[3 * e + k] = cs[k];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bg_map_fwd(FieldsDev F, CamDev cam, float radius, int Hb,
+                                                    int Wb, const float* __restrict__ map,
+                                                    const float* __restrict__ C_fg,
+                                                    const float* __restrict__ T_final,
+                                                    float* __restrict__ C) {
+  const int P = cam.W * cam.H;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float ps[3], dir[3];
+    bg_ray(cam, F, radius, p % cam.W, p / cam.W, ps, dir);
+    const MapTap m = map_tap(ps, Hb, Wb);
+    float cs[3] = {0, 0, 0};
+#pragma unroll
+    for (int ka = 0; ka < 2; ++ka)
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        const float w = m.wa[ka] * m.wb[kb];
+        const float* t = map + 3 * (m.a[ka] * Wb + m.b[kb]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cs[k] += w * t[k];
+      }
+    const float T = T_final[p];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * cs[k];
+  }
+}
+
+// Map mode, reverse, per pixel: dL/dT_final, dL/dC_fg and the map gradient.
+__global__ void __launch_bounds__(256) k_bg_map_bwd_pix(FieldsDev F, CamDev cam, float radius, int Hb,
+                                                        int Wb, const float* __restrict__ map,
+                                                        const float* __restrict__ T_final,
+                                                        const float* __restrict__ dC,
+                                                        float* __restrict__ dC_fg,
+                                                        float* __restrict__ dT,
+                                                        float* __restrict__ dmap) {
+  const int P = cam.W * cam.H;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float ps[3], dir[3];
+    bg_ray(cam, F, radius, p % cam.W, p / cam.W, ps, dir);
+    const MapTap m = map_tap(ps, Hb, Wb);
+    float cs[3] = {0, 0, 0};
+#pragma unroll
+    for (int ka = 0; ka < 2; ++ka)
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        const float w = m.wa[ka] * m.wb[kb];
+        const float* t = map + 3 * (m.a[ka] * Wb + m.b[kb]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cs[k] += w * t[k];
+      }
+    const float T = T_final[p];
+    float g[3], dt = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      g[k] = dC[3 * (int64_t)p + k];
+      dt += g[k] * cs[k];
+      if (dC_fg) dC_fg[3 * (int64_t)p + k] = g[k];
+    }
+    dT[p] = dt;
+#pragma unroll
+    for (int ka = 0; ka < 2; ++ka)
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        const float w = m.wa[ka] * m.wb[kb] * T;
+        float* t = dmap + 3 * (m.a[ka] * Wb + m.b[kb]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(t + k, w * g[k]);
+      }
+  }
+}
+
+// Reverse of the colour field at background points: MODE 0 = one point per
+// pixel (exact mode, also writes dL/dT_final and dL/dC_fg), MODE 1 = one
+// point per map texel with the texel gradient given in dmap.
+template <int NL, int WID, int NH, int MODE>
+__global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
+    FieldsDev F, CamDev cam, float radius, int Hb, int Wb, const float* __restrict__ T_final,
+    const float* __restrict__ dC, float* __restrict__ dC_fg, float* __restrict__ dT,
+    const float* __restrict__ dmap, float* __restrict__ g_rad_table, float loss_scale,
+    SlabLayout SL, float* slabs) {
+  extern __shared__ float sm[];
+  constexpr int NG = 2 * NL, NC = NG + kPEPad;
+  float* act = sm;
+  float* dzb = sm + (NC + NH * WID) * kActPitch;
+  float* slab = slabs + (size_t)blockIdx.x * SL.total;
+  const int t = threadIdx.x;
+  const int P = MODE == 0 ? cam.W * cam.H : Hb * Wb;
+  const float inv_ls = 1.0f / loss_scale;
+  for (int base = blockIdx.x * kBwdThreads; base < P; base += gridDim.x * kBwdThreads) {
+    const int e = base + t;
+    const bool ok = e < P;
+    const int ee = ok ? e : 0;
+    float y[3], dir[3], dcs[3];
+    if (MODE == 0) {
+      float ps[3];
+      bg_ray(cam, F, radius, ee % cam.W, ee / cam.W, ps, dir);
+      contract_n(ps, y);
+    } else {
+      texel_point(ee / Wb, ee % Wb, Hb, Wb, radius, y, dir);
+    }
+    float x0[NC], out[3], dz3[3];
+    encode<NL>(F.rad, y, x0);
+    pos_enc(dir, x0 + NG);
+    decoder_fwd_store<NC, WID, NH, 3>(F.cm, x0, act, out);
+    float cs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cs[k] = sigmoidf_(out[k]);
+    if (MODE == 0) {
+      const float T = ok ? T_final[ee] : 0.0f;
+      float dt = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float g = ok ? dC[3 * (int64_t)ee + k] : 0.0f;
+        dt += g * cs[k];
+        dcs[k] = g * T;
+        if (ok && dC_fg) dC_fg[3 * (int64_t)ee + k] = g;
+      }
+      if (ok) dT[ee] = dt;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dcs[k] = ok ? dmap[3 * ee + k] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dz3[k] = dcs[k] * loss_scale * cs[k] * (1.0f - cs[k]);
+    float dx[NC];
+    decoder_bwd<NC, WID, NH, 3>(F.cm, act, dzb, dz3, slab, SL, 1, dx);
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
+      encode_bwd<NL>(F.rad, y, dx, g_rad_table, nullptr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
+  const hyrf_grid* gs[2] = {&f.geo, &f.rad};
+  GridDev* gd[2] = {&d.geo, &d.rad};
+  for (int k = 0; k < 2; ++k) {
+    const hyrf_grid& g = *gs[k];
+    if (k == 0 && !need_geo) {
+      *gd[0] = GridDev{};
+      continue;
+    }
+    if (!g.table || g.n_levels < 1 || g.n_levels > kMaxLevels || g.n_feat != 2 || g.log2_T < 4 ||
+        g.log2_T > 26 || g.base_res < 1 || !(g.growth >= 1.0f) ||
+        (g.dtype != HYRF_F32 && g.dtype != HYRF_BF16))
+      return false;
+    GridDev& o = *gd[k];
+    o.table = g.table;
+    o.L = g.n_levels;
+    o.T = 1u << g.log2_T;
+    o.mask = o.T - 1u;
+    o.bf16 = g.dtype == HYRF_BF16;
+    o.dense = 0;
+    for (int l = 0; l < g.n_levels; ++l) {
+      const double r = std::floor((double)g.base_res * std::pow((double)g.growth, (double)l));
+      if (r > 1.0e6) return false;
+      o.res[l] = (int)r;
+      const uint64_t n1 = (uint64_t)o.res[l] + 1;
+      if (n1 * n1 * n1 <= (uint64_t)o.T) o.dense |= 1u << l;
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    d.lo[k] = f.box_lo[k];
+    const float ext = f.box_hi[k] - f.box_lo[k];
+    if (!(ext > 0.0f)) return false;
+    d.sx[k] = 2.0f / ext;
+  }
+  const hyrf_mlp* ms[2] = {&f.geo_mlp, &f.col_mlp};
+  MlpDev* md[2] = {&d.gm, &d.cm};
+  for (int k = 0; k < 2; ++k) {
+    const hyrf_mlp& m = *ms[k];
+    if (k == 0 && !need_geo) {
+      *md[0] = MlpDev{};
+      continue;
+    }
+    if (!((m.n_hidden == 1 && m.width == 32) || (m.n_hidden == 2 && m.width == 64))) return false;
+    for (int l = 0; l <= m.n_hidden; ++l)
+      if (!m.W[l] || !m.b[l]) return false;
+    if (m.dtype != HYRF_F32 && m.dtype != HYRF_BF16) return false;
+    MlpDev& o = *md[k];
+    for (int l = 0; l < 3; ++l) {
+      o.W[l] = l <= m.n_hidden ? m.W[l] : nullptr;
+      o.b[l] = l <= m.n_hidden ? m.b[l] : nullptr;
+    }
+    o.n_in = m.n_in;
+    o.width = m.width;
+    o.n_hidden = m.n_hidden;
+    o.n_out = m.n_out;
+    o.bf16 = m.dtype == HYRF_BF16;
+  }
+  if (f.pe_freq != kPEFreq || f.pe_pad != kPEPad) return false;
+  const int L = f.rad.n_levels;
+  if (need_geo) {
+    if (f.geo.n_levels != L) return false;
+    if (f.geo_mlp.n_in != 2 * L || f.geo_mlp.n_out != 8) return false;
+    if (f.geo_mlp.n_hidden != f.col_mlp.n_hidden || f.geo_mlp.width != f.col_mlp.width) return false;
+  }
+  if (f.col_mlp.n_in != 2 * L + kPEPad || f.col_mlp.n_out != 3) return false;
+  d.pe_freq = f.pe_freq;
+  d.pe_pad = f.pe_pad;
+  return true;
+}
+
+// Shape dispatch: (levels, width, hidden layers) in {(8, 32, 1), (16, 64, 2)}.
+enum class Shape { S8_32_1, S16_64_2, NONE };
+
+static Shape shape_of(const hyrf_fields& f) {
+  const int L = f.rad.n_levels;
+  if (L == 8 && f.col_mlp.width == 32 && f.col_mlp.n_hidden == 1) return Shape::S8_32_1;
+  if (L == 16 && f.col_mlp.width == 64 && f.col_mlp.n_hidden == 2) return Shape::S16_64_2;
+  return Shape::NONE;
+}
+
+static int fwd_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+int bwd_ctas() { return num_sms() * 3; }
+
+template <int NL, int WID, int NH>
+static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const QueryFwdIO& io,
+                                  cudaStream_t s) {
+  k_query_fwd<NL, WID, NH><<<fwd_blocks(io.n, 128), 128, 0, s>>>(F, cam, io);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s) {
+  QueryFwdIO io{a.n,      a.pos,   a.alpha_e, a.scale_e, a.color_e, a.vis_ids,
+                a.n_vis,  a.alpha, a.scale,   a.quat,    a.color,   a.status};
+  const CamDev cam = to_dev(a.cam);
+  if (a.n == 0) return HYRF_OK;
+  switch (shape_of(a.fields)) {
+    case Shape::S8_32_1: return query_fwd_impl<8, 32, 1>(F, cam, io, s);
+    case Shape::S16_64_2: return query_fwd_impl<16, 64, 2>(F, cam, io, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+size_t slab_bytes(const FieldsDev& F, bool geo) {
+  SlabLayout SL = make_slab_layout(geo ? &F.gm : nullptr, &F.cm);
+  return (size_t)bwd_ctas() * SL.total * sizeof(float);
+}
+
+static SlabTargets targets(const hyrf_field_grads& g, bool geo) {
+  SlabTargets T{};
+  for (int l = 0; l < 3; ++l) {
+    T.W[0][l] = geo ? g.geo_W[l] : nullptr;
+    T.b[0][l] = geo ? g.geo_b[l] : nullptr;
+    T.W[1][l] = g.col_W[l];
+    T.b[1][l] = g.col_b[l];
+  }
+  return T;
+}
+
+template <class K>
+static void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int NL, int WID, int NH>
+static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const QueryBwdIO& io,
+                                  const hyrf_field_grads& grads, float* slabs, cudaStream_t s) {
+  const SlabLayout SL = make_slab_layout(&F.gm, &F.cm);
+  const int ctas = bwd_ctas();
+  cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
+  const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
+  set_smem(k_query_bwd<NL, WID, NH>, smem);
+  k_query_bwd<NL, WID, NH><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs);
+  HYRF_LAUNCH_CHECK();
+  k_slab_reduce<<<64, 256, 0, s>>>(slabs, ctas, SL, targets(grads, true), 1.0f / io.loss_scale);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F,
+                             void* ws, cudaStream_t s) {
+  QueryBwdIO io{a.n,        a.pos,       a.alpha_e,   a.scale_e,   a.color_e,
+                a.vis_ids,  a.n_vis,     a.d_alpha,   a.d_scale,   a.d_quat,
+                a.d_color,  a.d_pos,     a.d_alpha_e, a.d_scale_e, a.d_color_e,
+                a.grads.geo_table, a.grads.rad_table, a.loss_scale, a.status};
+  const CamDev cam = to_dev(a.cam);
+  if (a.n == 0) return HYRF_OK;
+  float* slabs = static_cast<float*>(ws);
+  switch (shape_of(a.fields)) {
+    case Shape::S8_32_1: return query_bwd_impl<8, 32, 1>(F, cam, io, a.grads, slabs, s);
+    case Shape::S16_64_2: return query_bwd_impl<16, 64, 2>(F, cam, io, a.grads, slabs, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward) {
+  Carver c(nullptr);
+  if (a.bg.mode == 1) {
+    c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);  // map
+    if (backward) c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);  // dmap
+  }
+  if (backward) c.take<char>(slab_bytes(F, false));
+  return c.size();
+}
+
+template <int NL, int WID, int NH>
+static hyrf_status bg_fwd_impl(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
+                               cudaStream_t s) {
+  const CamDev cam = to_dev(a.cam);
+  const int P = cam.W * cam.H;
+  if (a.bg.mode == 0) {
+    k_bg_exact_fwd<NL, WID, NH><<<fwd_blocks(P, 128), 128, 0, s>>>(F, cam, a.bg.radius, a.C_fg,
+                                                                  a.T_final, a.C);
+    HYRF_LAUNCH_CHECK();
+  } else {
+    Carver c(ws);
+    float* map = c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);
+    const int nt = a.bg.map_h * a.bg.map_w;
+    k_bg_map_texels<NL, WID, NH><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, a.bg.map_h, a.bg.map_w,
+                                                                      a.bg.radius, map);
+    HYRF_LAUNCH_CHECK();
+    k_bg_map_fwd<<<fwd_blocks(P, 256), 256, 0, s>>>(F, cam, a.bg.radius, a.bg.map_h, a.bg.map_w, map,
+                                                      a.C_fg, a.T_final, a.C);
+    HYRF_LAUNCH_CHECK();
+  }
+  return HYRF_OK;
+}
+
+hyrf_status launch_bg_fwd(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
+                          cudaStream_t s) {
+  switch (shape_of(a.fields)) {
+    case Shape::S8_32_1: return bg_fwd_impl<8, 32, 1>(a, F, ws, s);
+    case Shape::S16_64_2: return bg_fwd_impl<16, 64, 2>(a, F, ws, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+template <int NL, int WID, int NH>
+static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
+                               void* ws, cudaStream_t s) {
+  const hyrf_composite_background_args& a = b.fwd;
+  const CamDev cam = to_dev(a.cam);
+  const int P = cam.W * cam.H;
+  const SlabLayout SL = make_slab_layout(nullptr, &F.cm);
+  const int ctas = bwd_ctas();
+  Carver c(ws);
+  float* map = nullptr;
+  float* dmap = nullptr;
+  const int Hb = a.bg.map_h, Wb = a.bg.map_w;
+  if (a.bg.mode == 1) {
+    map = c.take<float>((size_t)Hb * Wb * 3);
+    dmap = c.take<float>((size_t)Hb * Wb * 3);
+  }
+  float* slabs = c.take<float>((size_t)ctas * SL.total);
+  cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
+  const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
+  if (a.bg.mode == 0) {
+    set_smem(k_bg_field_bwd<NL, WID, NH, 0>, smem);
+    k_bg_field_bwd<NL, WID, NH, 0><<<ctas, kBwdThreads, smem, s>>>(
+        F, cam, a.bg.radius, 0, 0, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, nullptr,
+        b.grads.rad_table, b.loss_scale, SL, slabs);
+    HYRF_LAUNCH_CHECK();
+  } else {
+    const int nt = Hb * Wb;
+    k_bg_map_texels<NL, WID, NH><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, Hb, Wb, a.bg.radius, map);
+    HYRF_LAUNCH_CHECK();
+    cudaMemsetAsync(dmap, 0, (size_t)nt * 3 * sizeof(float), s);
+    k_bg_map_bwd_pix<<<fwd_blocks(P, 256), 256, 0, s>>>(F, cam, a.bg.radius, Hb, Wb, map, a.T_final,
+                                                          b.d_C, b.d_C_fg, b.d_T_final, dmap);
+    HYRF_LAUNCH_CHECK();
+    set_smem(k_bg_field_bwd<NL, WID, NH, 1>, smem);
+    k_bg_field_bwd<NL, WID, NH, 1><<<ctas, kBwdThreads, smem, s>>>(
+        F, cam, a.bg.radius, Hb, Wb, nullptr, nullptr, nullptr, nullptr, dmap, b.grads.rad_table,
+        b.loss_scale, SL, slabs);
+    HYRF_LAUNCH_CHECK();
+  }
+  k_slab_reduce<<<64, 256, 0, s>>>(slabs, ctas, SL, targets(b.grads, false), 1.0f / b.loss_scale);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_bg_bwd(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
+                          void* ws, cudaStream_t s) {
+  switch (shape_of(b.fwd.fields)) {
+    case Shape::S8_32_1: return bg_bwd_impl<8, 32, 1>(b, F, ws, s);
+    case Shape::S16_64_2: return bg_bwd_impl<16, 64, 2>(b, F, ws, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace hyrf

@@ -1,0 +1,268 @@
+// Front-to-back alpha compositing of Eq. 1 per 16x16 tile, and its reverse.
+// One CTA of 256 threads per tile, one pixel per thread. The visible
+// Gaussians' screen-space records are first packed into 48-byte rows
+// (three float4: {u, v, conic a, conic b}, {conic c, opacity, r, g}, {b})
+// so that a tile stages a batch of 256 of them into shared memory with
+// three vector loads per thread. The forward ends a tile early once every
+// pixel has stopped (CTA-wide vote). The reverse walks each pixel's list
+// back to front, recovering T from the stored T_final by division, reduces
+// the per-Gaussian gradients across each warp and adds them with atomics.
+#include "common.cuh"
+
+namespace hyrf {
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+__global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis, int n,
+                                              const float* __restrict__ mean2d,
+                                              const float* __restrict__ conic,
+                                              const float* __restrict__ alpha,
+                                              const float* __restrict__ color,
+                                              float4* __restrict__ rec) {
+  const int nv = min(*n_vis, n);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    rec[3 * i] = make_float4(mean2d[2 * i], mean2d[2 * i + 1], conic[3 * i], conic[3 * i + 1]);
+    rec[3 * i + 1] = make_float4(conic[3 * i + 2], alpha[i], color[3 * i], color[3 * i + 1]);
+    rec[3 * i + 2] = make_float4(color[3 * i + 2], 0.0f, 0.0f, 0.0f);
+  }
+}
+
+// Exponent of the 2D Gaussian at offset (dx, dy) = mean - pixel centre, with
+// a fixed multiply-add order shared by the forward and the reverse pass.
+__device__ __forceinline__ float splat_power(float ca, float cb, float cc, float dx, float dy) {
+  const float q = fmaf(cc * dy, dy, ca * dx * dx);
+  return fmaf(-0.5f, q, -(cb * dx * dy));
+}
+
+__global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ ranges,
+                                                    const int32_t* __restrict__ vals, int n,
+                                                    const float4* __restrict__ rec, int W, int H,
+                                                    int TX, float* __restrict__ C_fg,
+                                                    float* __restrict__ T_final,
+                                                    int32_t* __restrict__ n_contrib,
+                                                    int32_t* status) {
+  __shared__ float4 s0[256], s1[256], s2[256];
+  const int tile = blockIdx.x;
+  const int t = threadIdx.x;
+  const int px = (tile % TX) * kTile + (t % kTile);
+  const int py = (tile / TX) * kTile + (t / kTile);
+  const bool inside = px < W && py < H;
+  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+  int last = 0;
+  bool done = !inside;
+  for (int b0 = start; b0 < end; b0 += 256) {
+    if (__syncthreads_count(done) == 256) break;
+    const int k = b0 + t;
+    if (k < end) {
+      int g = vals[k];
+      if (g < 0 || g >= n) {
+        set_status(status, HYRF_ERR_BOUNDS);
+        s0[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s1[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // opacity 0: never contributes
+      } else {
+        s0[t] = rec[3 * g];
+        s1[t] = rec[3 * g + 1];
+        s2[t] = rec[3 * g + 2];
+      }
+    }
+    __syncthreads();
+    const int cnt = min(256, end - b0);
+    for (int j = 0; j < cnt && !done; ++j) {
+      const float4 r0 = s0[j], r1 = s1[j];
+      const float dx = r0.x - fx, dy = r0.y - fy;
+      const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
+      if (power > 0.0f) continue;
+      const float alpha = fminf(kAlphaMax, r1.y * expf(power));
+      if (alpha < kAlphaMin) continue;
+      const float test_T = T * (1.0f - alpha);
+      if (test_T < kTMin) {
+        done = true;
+        break;
+      }
+      const float w = alpha * T;
+      c0 = fmaf(r1.z, w, c0);
+      c1 = fmaf(r1.w, w, c1);
+      c2 = fmaf(s2[j].x, w, c2);
+      T = test_T;
+      last = b0 - start + j + 1;
+    }
+  }
+  if (inside) {
+    const int p = py * W + px;
+    C_fg[3 * p] = c0;
+    C_fg[3 * p + 1] = c1;
+    C_fg[3 * p + 2] = c2;
+    T_final[p] = T;
+    n_contrib[p] = last;
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_raster_bwd(
+    const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
+    const float4* __restrict__ rec, int W, int H, int TX, const float* __restrict__ T_final,
+    const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
+    const float* __restrict__ dT, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
+    float* __restrict__ d_alpha, float* __restrict__ d_color) {
+  __shared__ float4 s0[256], s1[256], s2[256];
+  __shared__ int sg[256];
+  __shared__ int max_last;
+  const int tile = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31;
+  const int px = (tile % TX) * kTile + (t % kTile);
+  const int py = (tile / TX) * kTile + (t / kTile);
+  const bool inside = px < W && py < H;
+  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  const int p = inside ? py * W + px : 0;
+  const float Tf = inside ? T_final[p] : 1.0f;
+  const int last = inside ? n_contrib[p] : 0;
+  const float g0 = inside ? dC[3 * p] : 0.0f, g1 = inside ? dC[3 * p + 1] : 0.0f,
+              g2 = inside ? dC[3 * p + 2] : 0.0f;
+  const float gT = inside ? dT[p] : 0.0f;
+  if (t == 0) max_last = 0;
+  __syncthreads();
+  atomicMax(&max_last, last);
+  __syncthreads();
+  const int stop = start + max_last;  // no pixel of the tile used list positions >= stop
+  float T = Tf;
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;  // colour behind, normalised by T after the current one
+  float la = 0.0f, lc0 = 0.0f, lc1 = 0.0f, lc2 = 0.0f;
+  for (int b1 = stop; b1 > start; b1 -= 256) {
+    const int b0 = max(start, b1 - 256);
+    __syncthreads();
+    const int k = b0 + t;
+    if (k < b1) {
+      int g = vals[k];
+      if (g < 0 || g >= n) {
+        g = -1;
+        s1[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      } else {
+        s0[t] = rec[3 * g];
+        s1[t] = rec[3 * g + 1];
+        s2[t] = rec[3 * g + 2];
+      }
+      sg[t] = g;
+    }
+    __syncthreads();
+    for (int j = b1 - b0 - 1; j >= 0; --j) {
+      const int pos = b0 - start + j;  // list position
+      float gu = 0.0f, gv = 0.0f, ga = 0.0f, gb = 0.0f, gc = 0.0f, go = 0.0f, gr = 0.0f,
+            gg = 0.0f, gbl = 0.0f;
+      bool contrib = false;
+      if (pos < last) {
+        const float4 r0 = s0[j], r1 = s1[j];
+        const float dx = r0.x - fx, dy = r0.y - fy;
+        const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
+        if (power <= 0.0f) {
+          const float G = expf(power);
+          const float oG = r1.y * G;
+          const float alpha = fminf(kAlphaMax, oG);
+          if (alpha >= kAlphaMin) {
+            contrib = true;
+            T = T / (1.0f - alpha);  // T before this Gaussian
+            const float cb = s2[j].x;
+            a0 = la * lc0 + (1.0f - la) * a0;
+            a1 = la * lc1 + (1.0f - la) * a1;
+            a2 = la * lc2 + (1.0f - la) * a2;
+            la = alpha;
+            lc0 = r1.z;
+            lc1 = r1.w;
+            lc2 = cb;
+            const float w = alpha * T;
+            gr = w * g0;
+            gg = w * g1;
+            gbl = w * g2;
+            float dal = ((r1.z - a0) * g0 + (r1.w - a1) * g1 + (cb - a2) * g2) * T;
+            dal -= gT * Tf / (1.0f - alpha);
+            if (oG <= kAlphaMax) {
+              go = dal * G;
+              const float dp = dal * alpha;
+              gu = dp * (-(r0.z * dx) - r0.w * dy);
+              gv = dp * (-(r1.x * dy) - r0.w * dx);
+              ga = dp * (-0.5f * dx * dx);
+              gb = dp * (-(dx * dy));
+              gc = dp * (-0.5f * dy * dy);
+            }
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+        gu = warp_sum(gu);
+        gv = warp_sum(gv);
+        ga = warp_sum(ga);
+        gb = warp_sum(gb);
+        gc = warp_sum(gc);
+        go = warp_sum(go);
+        gr = warp_sum(gr);
+        gg = warp_sum(gg);
+        gbl = warp_sum(gbl);
+        const int g = sg[j];
+        if (lane == 0 && g >= 0) {
+          atomicAdd(reinterpret_cast<float2*>(d_mean2d) + g, make_float2(gu, gv));
+          atomicAdd(d_conic + 3 * g, ga);
+          atomicAdd(d_conic + 3 * g + 1, gb);
+          atomicAdd(d_conic + 3 * g + 2, gc);
+          atomicAdd(d_alpha + g, go);
+          atomicAdd(d_color + 3 * g, gr);
+          atomicAdd(d_color + 3 * g + 1, gg);
+          atomicAdd(d_color + 3 * g + 2, gbl);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+size_t raster_workspace(int n) {
+  Carver c(nullptr);
+  c.take<float4>((size_t)3 * (n > 0 ? n : 1));
+  return c.size();
+}
+
+static hyrf_status pack(const hyrf_rasterize_args& a, float4* rec, cudaStream_t s) {
+  int blocks = (a.n + 255) / 256;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  if (blocks < 1) blocks = 1;
+  k_pack<<<blocks, 256, 0, s>>>(a.n_vis, a.n, a.mean2d, a.conic, a.alpha, a.color, rec);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream_t s) {
+  const int TX = (a.width + kTile - 1) / kTile, TY = (a.height + kTile - 1) / kTile;
+  Carver c(ws);
+  float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
+  hyrf_status st = pack(a, rec, s);
+  if (st != HYRF_OK) return st;
+  k_raster_fwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.C_fg,
+                                       a.T_final, a.n_contrib, a.status);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, cudaStream_t s) {
+  const hyrf_rasterize_args& a = b.fwd;
+  const int TX = (a.width + kTile - 1) / kTile, TY = (a.height + kTile - 1) / kTile;
+  Carver c(ws);
+  float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
+  hyrf_status st = pack(a, rec, s);
+  if (st != HYRF_OK) return st;
+  k_raster_bwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
+                                       a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
+                                       b.d_alpha, b.d_color);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+}  // namespace hyrf

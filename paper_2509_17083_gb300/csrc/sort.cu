@@ -1,0 +1,435 @@
+// Tile binning and depth ordering (Sec. 3.1: Gaussians are ordered by depth
+// and composited per pixel). Instances carry the 64-bit key
+// (tile << 32) | float_bits(depth); their stable order is produced by LSD
+// radix passes: four 8-bit passes over the 32 depth bits of the visible
+// Gaussians, emission of each Gaussian's tiles in that order, then the tile
+// bits over the instances. Every pass is reduce-then-scan (histogram,
+// per-digit column scan, stable scatter), so no kernel waits on another CTA.
+#include "common.cuh"
+
+namespace hyrf {
+
+constexpr int kRT = 256;         // radix threads per CTA
+constexpr int kSub = 1024;       // elements per scatter sub-tile (8 warps x 4 rounds x 32)
+constexpr int kMaxRadixCTAs = 2048;
+
+__device__ __forceinline__ int dev_chunk(int n, int G) {
+  int c = (n + G - 1) / G;
+  return (c + kSub - 1) / kSub * kSub;
+}
+
+__device__ __forceinline__ int clamp_n(const int32_t* n_ptr, int cap) {
+  int n = *n_ptr;
+  return n < 0 ? 0 : (n > cap ? cap : n);
+}
+
+__global__ void __launch_bounds__(kRT) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                    const int32_t* __restrict__ n_ptr, int cap,
+                                                    int shift, uint32_t mask,
+                                                    uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  const int G = gridDim.x, b = blockIdx.x;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int n = clamp_n(n_ptr, cap);
+  const int chunk = dev_chunk(n, G);
+  const int64_t start = (int64_t)b * chunk;
+  const int64_t end = (start + chunk < (int64_t)n) ? start + chunk : (int64_t)n;
+  for (int64_t i = start + threadIdx.x; i < end; i += kRT) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+  __syncthreads();
+  hist[threadIdx.x * G + b] = h[threadIdx.x];
+}
+
+// One CTA per digit: exclusive scan of the digit's column over the G CTAs;
+// digit totals to totals[d].
+__global__ void __launch_bounds__(kRT) k_radix_colscan(uint32_t* __restrict__ hist, int G,
+                                                       uint32_t* __restrict__ totals) {
+  __shared__ uint32_t wsum[kRT / 32];
+  uint32_t* col = hist + (size_t)blockIdx.x * G;
+  const int per = (G + kRT - 1) / kRT;
+  const int s0 = threadIdx.x * per;
+  uint32_t v[kMaxRadixCTAs / kRT];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxRadixCTAs / kRT; ++k) {
+    v[k] = (k < per && s0 + k < G) ? col[s0 + k] : 0u;
+    sum += v[k];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+  for (int j = 0; j < kRT / 32; ++j) {
+    before += j < w ? wsum[j] : 0u;
+    total += wsum[j];
+  }
+  uint32_t run = before + x - sum;
+#pragma unroll
+  for (int k = 0; k < kMaxRadixCTAs / kRT; ++k) {
+    if (k < per && s0 + k < G) col[s0 + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restrict__ keys_in,
+                                                       const int32_t* __restrict__ vals_in,
+                                                       uint32_t* __restrict__ keys_out,
+                                                       int32_t* __restrict__ vals_out,
+                                                       const int32_t* __restrict__ n_ptr, int cap,
+                                                       int shift, uint32_t mask,
+                                                       const uint32_t* __restrict__ hist,
+                                                       const uint32_t* __restrict__ totals) {
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t sub_total[256];
+  __shared__ uint32_t whist[8][256];
+  __shared__ uint32_t wsum[8];
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int lane = t & 31, w = t >> 5;
+  // digit base = exclusive scan of the digit totals + this CTA's column prefix
+  {
+    const uint32_t tot = totals[t];
+    uint32_t x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int j = 0; j < w; ++j) before += wsum[j];
+    base[t] = before + x - tot + hist[t * G + b];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) whist[j][t] = 0;
+  }
+  __syncthreads();
+  const int n = clamp_n(n_ptr, cap);
+  const int chunk = dev_chunk(n, G);
+  const int64_t start = (int64_t)b * chunk;
+  const int64_t end = (start + chunk < (int64_t)n) ? start + chunk : (int64_t)n;
+  for (int64_t sub = start; sub < end; sub += kSub) {
+    uint32_t key[4], rank[4];
+    int32_t val[4];
+    uint32_t dig[4];
+    bool valid[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t idx = sub + w * 128 + r * 32 + lane;
+      valid[r] = idx < end;
+      key[r] = valid[r] ? keys_in[idx] : 0u;
+      val[r] = valid[r] ? vals_in[idx] : 0;
+      dig[r] = (key[r] >> shift) & mask;
+      const uint32_t m_valid = __ballot_sync(0xffffffffu, valid[r]);
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid[r] ? dig[r] : 0x10000u + lane) & m_valid;
+      uint32_t prev = 0;
+      if (valid[r]) prev = whist[w][dig[r]];
+      __syncwarp();
+      rank[r] = prev + __popc(peers & ((1u << lane) - 1u));
+      if (valid[r] && lane == __ffs(peers) - 1) whist[w][dig[r]] = prev + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {
+      uint32_t run = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t c = whist[j][t];
+        whist[j][t] = run;
+        run += c;
+      }
+      sub_total[t] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (!valid[r]) continue;
+      const uint32_t pos = base[dig[r]] + whist[w][dig[r]] + rank[r];
+      keys_out[pos] = key[r];
+      vals_out[pos] = val[r];
+    }
+    __syncthreads();
+    base[t] += sub_total[t];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) whist[j][t] = 0;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- scan of tile counts
+
+constexpr int kScanChunk = 2048;  // elements per scan CTA (256 threads x 8)
+
+__device__ __forceinline__ int tiles_of_sorted(const int32_t* ntiles, const int32_t* order, int j,
+                                               int n) {
+  const int g = order[j];
+  return (g >= 0 && g < n) ? ntiles[g] : 0;
+}
+
+__global__ void __launch_bounds__(256) k_count_sums(const int32_t* __restrict__ ntiles,
+                                                    const int32_t* __restrict__ order,
+                                                    const int32_t* __restrict__ n_ptr, int cap,
+                                                    int64_t* __restrict__ sums) {
+  const int n = clamp_n(n_ptr, cap);
+  const int64_t start = (int64_t)blockIdx.x * kScanChunk;
+  int64_t s = 0;
+  for (int k = 0; k < kScanChunk / 256; ++k) {
+    const int64_t j = start + k * 256 + threadIdx.x;
+    if (j < n) s += tiles_of_sorted(ntiles, order, (int)j, cap);
+  }
+  __shared__ int64_t red[8];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the CTA sums; writes K = min(total, capacity) and the
+// overflow flag.
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t* __restrict__ sums, int m,
+                                                    int64_t capacity, int32_t* __restrict__ n_inst,
+                                                    int32_t* status) {
+  __shared__ int64_t wsums[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < m; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int64_t v = i < m ? sums[i] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int64_t s = wsums[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      wsums[lane] = s;
+    }
+    __syncthreads();
+    const int64_t incl = x + (w > 0 ? wsums[w - 1] : 0) + carry;
+    if (i < m) sums[i] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (carry > capacity) set_status(status, HYRF_ERR_OVERFLOW);
+    *n_inst = (int32_t)(carry < capacity ? carry : capacity);
+  }
+}
+
+// Per sorted Gaussian j: instance offset, then its tiles in row-major order
+// (instances beyond the capacity are dropped).
+__global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ ntiles,
+                                              const int32_t* __restrict__ rect,
+                                              const int32_t* __restrict__ order,
+                                              const int32_t* __restrict__ n_ptr, int cap_n,
+                                              const int64_t* __restrict__ sums, int TX,
+                                              int64_t capacity, uint32_t* __restrict__ tile_keys,
+                                              int32_t* __restrict__ tile_vals) {
+  __shared__ int64_t wsum[8];
+  const int n = clamp_n(n_ptr, cap_n);
+  const int64_t start = (int64_t)blockIdx.x * kScanChunk;
+  int64_t run = sums[blockIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < kScanChunk / 256; ++k) {
+    const int64_t j = start + k * 256 + threadIdx.x;
+    const int c = j < n ? tiles_of_sorted(ntiles, order, (int)j, cap_n) : 0;
+    int64_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int64_t before = 0, tot = 0;
+    for (int q = 0; q < 8; ++q) {
+      before += q < w ? wsum[q] : 0;
+      tot += wsum[q];
+    }
+    int64_t off = run + before + x - c;
+    if (c > 0) {
+      const int g = order[j];
+      const int x0 = rect[4 * g], y0 = rect[4 * g + 1], x1 = rect[4 * g + 2], y1 = rect[4 * g + 3];
+      for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx, ++off) {
+          if (off >= capacity) break;
+          tile_keys[off] = (uint32_t)(ty * TX + tx);
+          tile_vals[off] = g;
+        }
+    }
+    run += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ tile_keys,
+                                                const int32_t* __restrict__ n_ptr, int cap,
+                                                int n_tiles, int32_t* __restrict__ ranges) {
+  const int K = clamp_n(n_ptr, cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    const uint32_t t = tile_keys[k];
+    if (t >= (uint32_t)n_tiles) continue;
+    if (k == 0 || tile_keys[k - 1] != t) ranges[2 * t] = k;
+    if (k == K - 1 || tile_keys[k + 1] != t) ranges[2 * t + 1] = k + 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_keys64(const uint32_t* __restrict__ tile_keys,
+                                                const int32_t* __restrict__ vals,
+                                                const float* __restrict__ depth,
+                                                const int32_t* __restrict__ n_ptr, int cap,
+                                                uint64_t* __restrict__ keys) {
+  const int K = clamp_n(n_ptr, cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+    keys[k] = ((uint64_t)tile_keys[k] << 32) | (uint64_t)__float_as_uint(depth[vals[k]]);
+}
+
+__global__ void __launch_bounds__(256) k_depth_keys(const float* __restrict__ depth,
+                                                    const int32_t* __restrict__ n_ptr, int cap,
+                                                    uint32_t* __restrict__ keys,
+                                                    int32_t* __restrict__ vals) {
+  const int n = clamp_n(n_ptr, cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    keys[i] = __float_as_uint(depth[i]);
+    vals[i] = i;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+static int radix_ctas(int64_t cap) {
+  int64_t g = (cap + 4095) / 4096;
+  return (int)(g < 1 ? 1 : (g > kMaxRadixCTAs ? kMaxRadixCTAs : g));
+}
+
+static int bits_for(int64_t n_values) {
+  int b = 0;
+  while ((1ll << b) < n_values) ++b;
+  return b < 1 ? 1 : b;
+}
+
+struct SortWs {
+  uint32_t *dk_a, *dk_b, *tk_a, *tk_b;
+  int32_t *dv_a, *dv_b, *tv_b;
+  uint32_t *hist, *totals;
+  int64_t* sums;
+};
+
+static SortWs carve_sort(Carver& c, int n, int64_t cap) {
+  SortWs w;
+  const int Gd = radix_ctas(n), Gt = radix_ctas(cap);
+  const int G = Gd > Gt ? Gd : Gt;
+  w.dk_a = c.take<uint32_t>(n);
+  w.dk_b = c.take<uint32_t>(n);
+  w.dv_a = c.take<int32_t>(n);
+  w.dv_b = c.take<int32_t>(n);
+  w.tk_a = c.take<uint32_t>(cap);
+  w.tk_b = c.take<uint32_t>(cap);
+  w.tv_b = c.take<int32_t>(cap);
+  w.hist = c.take<uint32_t>((size_t)256 * G);
+  w.totals = c.take<uint32_t>(256);
+  w.sums = c.take<int64_t>((n + kScanChunk - 1) / kScanChunk + 1);
+  return w;
+}
+
+size_t bin_sort_workspace(int n, int64_t cap) {
+  Carver c(nullptr);
+  carve_sort(c, n, cap);
+  return c.size();
+}
+
+// Stable LSD radix sort of (keys, vals) on bits [0, nbits); the result ends in
+// (ka, va); (kb, vb) is scratch. The input must be in (ka, va) when the pass
+// count is even and in (kb, vb) when it is odd.
+static hyrf_status radix_sort(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* vb,
+                              const int32_t* n_ptr, int cap, int nbits, uint32_t* hist,
+                              uint32_t* totals, cudaStream_t s) {
+  const int G = radix_ctas(cap);
+  const int passes = (nbits + 7) / 8;
+  uint32_t* src_k = (passes & 1) ? kb : ka;
+  int32_t* src_v = (passes & 1) ? vb : va;
+  uint32_t* dst_k = (passes & 1) ? ka : kb;
+  int32_t* dst_v = (passes & 1) ? va : vb;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    const int bits = nbits - shift < 8 ? nbits - shift : 8;
+    const uint32_t mask = (1u << bits) - 1u;
+    k_radix_hist<<<G, kRT, 0, s>>>(src_k, n_ptr, cap, shift, mask, hist);
+    HYRF_LAUNCH_CHECK();
+    k_radix_colscan<<<256, kRT, 0, s>>>(hist, G, totals);
+    HYRF_LAUNCH_CHECK();
+    k_radix_scatter<<<G, kRT, 0, s>>>(src_k, src_v, dst_k, dst_v, n_ptr, cap, shift, mask, hist,
+                                      totals);
+    HYRF_LAUNCH_CHECK();
+    uint32_t* tk = src_k;
+    src_k = dst_k;
+    dst_k = tk;
+    int32_t* tv = src_v;
+    src_v = dst_v;
+    dst_v = tv;
+  }
+  return HYRF_OK;
+}
+
+hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t s) {
+  const int n = a.n;
+  const int64_t cap = a.capacity;
+  const int n_tiles = a.tiles_x * a.tiles_y;
+  Carver c(ws);
+  SortWs w = carve_sort(c, n, cap);
+  cudaMemsetAsync(a.ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), s);
+  if (n == 0 || cap == 0) {
+    cudaMemsetAsync(a.n_instances, 0, sizeof(int32_t), s);
+    return cudaPeekAtLastError() == cudaSuccess ? HYRF_OK : HYRF_ERR_CUDA;
+  }
+  // 1. depth keys of the visible Gaussians, sorted (4 x 8 bits)
+  const int eb = (n + 255) / 256 < num_sms() * 8 ? (n + 255) / 256 : num_sms() * 8;
+  k_depth_keys<<<eb, 256, 0, s>>>(a.depth, a.n_vis, n, w.dk_a, w.dv_a);
+  HYRF_LAUNCH_CHECK();
+  hyrf_status st = radix_sort(w.dk_a, w.dv_a, w.dk_b, w.dv_b, a.n_vis, n, 32, w.hist, w.totals, s);
+  if (st != HYRF_OK) return st;
+  // 2. instance offsets in depth order, K, and emission
+  const int sc = (n + kScanChunk - 1) / kScanChunk;
+  k_count_sums<<<sc, 256, 0, s>>>(a.ntiles, w.dv_a, a.n_vis, n, w.sums);
+  HYRF_LAUNCH_CHECK();
+  k_scan_sums<<<1, 1024, 0, s>>>(w.sums, sc, cap, a.n_instances, a.status);
+  HYRF_LAUNCH_CHECK();
+  const int tbits = bits_for(n_tiles);
+  const int tpasses = (tbits + 7) / 8;
+  uint32_t* emit_k = (tpasses & 1) ? w.tk_b : w.tk_a;
+  int32_t* emit_v = (tpasses & 1) ? w.tv_b : a.vals;
+  k_emit<<<sc, 256, 0, s>>>(a.ntiles, a.rect, w.dv_a, a.n_vis, n, w.sums, a.tiles_x, cap, emit_k,
+                            emit_v);
+  HYRF_LAUNCH_CHECK();
+  // 3. stable sort of the instances on their tile bits
+  const int capi = (int)(cap < 0x7fffffff ? cap : 0x7fffffff);
+  st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s);
+  if (st != HYRF_OK) return st;
+  // 4. per-tile ranges and (optionally) the composed 64-bit keys
+  const int kb = (int)((cap + 255) / 256 < num_sms() * 8 ? (cap + 255) / 256 : num_sms() * 8);
+  k_ranges<<<kb, 256, 0, s>>>(w.tk_a, a.n_instances, capi, n_tiles, a.ranges);
+  HYRF_LAUNCH_CHECK();
+  if (a.keys) {
+    k_keys64<<<kb, 256, 0, s>>>(w.tk_a, a.vals, a.depth, a.n_instances, capi, a.keys);
+    HYRF_LAUNCH_CHECK();
+  }
+  return HYRF_OK;
+}
+
+}  // namespace hyrf

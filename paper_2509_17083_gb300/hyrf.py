@@ -1,0 +1,341 @@
+"""ctypes binding of libhyrf (include/hyrf.h): same call names, argument
+marshalling only. Tensors are torch CUDA tensors; every call is enqueued on
+the current torch stream (or `stream`). The library is loaded from this
+package directory; importing this module on a machine without it, or
+without CUDA, raises.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhyrf.so")
+
+HYRF_OK = 0
+HYRF_ERR_INVALID_ARG = 1
+HYRF_ERR_UNSUPPORTED = 2
+HYRF_ERR_CUDA = 4
+HYRF_ERR_OVERFLOW = 8
+HYRF_ERR_BOUNDS = 16
+HYRF_F32 = 0
+HYRF_BF16 = 1
+TILE = 16
+
+_vp = C.c_void_p
+
+
+class hyrf_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("z_near", C.c_float), ("cull_tol", C.c_float)]
+
+
+class hyrf_grid(C.Structure):
+    _fields_ = [("table", _vp), ("n_levels", C.c_int32), ("log2_T", C.c_int32),
+                ("n_feat", C.c_int32), ("base_res", C.c_int32), ("growth", C.c_float),
+                ("dtype", C.c_int32)]
+
+
+class hyrf_mlp(C.Structure):
+    _fields_ = [("W", _vp * 3), ("b", _vp * 3), ("n_in", C.c_int32), ("width", C.c_int32),
+                ("n_hidden", C.c_int32), ("n_out", C.c_int32), ("dtype", C.c_int32)]
+
+
+class hyrf_fields(C.Structure):
+    _fields_ = [("box_lo", C.c_float * 3), ("box_hi", C.c_float * 3), ("geo", hyrf_grid),
+                ("rad", hyrf_grid), ("geo_mlp", hyrf_mlp), ("col_mlp", hyrf_mlp),
+                ("pe_freq", C.c_int32), ("pe_pad", C.c_int32)]
+
+
+class hyrf_field_grads(C.Structure):
+    _fields_ = [("geo_table", _vp), ("rad_table", _vp), ("geo_W", _vp * 3), ("geo_b", _vp * 3),
+                ("col_W", _vp * 3), ("col_b", _vp * 3)]
+
+
+class hyrf_query_fields_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("alpha_e", _vp), ("scale_e", _vp),
+                ("color_e", _vp), ("cam", hyrf_camera), ("fields", hyrf_fields),
+                ("vis_ids", _vp), ("n_vis", _vp), ("alpha", _vp), ("scale", _vp), ("quat", _vp),
+                ("color", _vp), ("status", _vp)]
+
+
+class hyrf_query_fields_backward_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("alpha_e", _vp), ("scale_e", _vp),
+                ("color_e", _vp), ("cam", hyrf_camera), ("fields", hyrf_fields),
+                ("vis_ids", _vp), ("n_vis", _vp), ("d_alpha", _vp), ("d_scale", _vp),
+                ("d_quat", _vp), ("d_color", _vp), ("d_pos", _vp), ("d_alpha_e", _vp),
+                ("d_scale_e", _vp), ("d_color_e", _vp), ("grads", hyrf_field_grads),
+                ("loss_scale", C.c_float), ("status", _vp)]
+
+
+class hyrf_project_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("vis_ids", _vp), ("n_vis", _vp), ("scale", _vp),
+                ("quat", _vp), ("cam", hyrf_camera), ("tile", C.c_int32), ("mean2d", _vp),
+                ("conic", _vp), ("depth", _vp), ("rect", _vp), ("ntiles", _vp),
+                ("fp64_flag", _vp), ("status", _vp)]
+
+
+class hyrf_project_backward_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("vis_ids", _vp), ("n_vis", _vp), ("scale", _vp),
+                ("quat", _vp), ("cam", hyrf_camera), ("d_mean2d", _vp), ("d_conic", _vp),
+                ("d_pos", _vp), ("d_scale", _vp), ("d_quat", _vp), ("status", _vp)]
+
+
+class hyrf_bin_sort_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_vis", _vp), ("rect", _vp), ("ntiles", _vp), ("depth", _vp),
+                ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("capacity", C.c_int64),
+                ("keys", _vp), ("vals", _vp), ("ranges", _vp), ("n_instances", _vp),
+                ("status", _vp)]
+
+
+class hyrf_rasterize_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_vis", _vp), ("ranges", _vp), ("vals", _vp), ("mean2d", _vp),
+                ("conic", _vp), ("alpha", _vp), ("color", _vp), ("width", C.c_int32),
+                ("height", C.c_int32), ("tile", C.c_int32), ("C_fg", _vp), ("T_final", _vp),
+                ("n_contrib", _vp), ("status", _vp)]
+
+
+class hyrf_rasterize_backward_args(C.Structure):
+    _fields_ = [("fwd", hyrf_rasterize_args), ("d_C_fg", _vp), ("d_T_final", _vp),
+                ("d_mean2d", _vp), ("d_conic", _vp), ("d_alpha", _vp), ("d_color", _vp)]
+
+
+class hyrf_background(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("map_h", C.c_int32), ("map_w", C.c_int32),
+                ("radius", C.c_float)]
+
+
+class hyrf_composite_background_args(C.Structure):
+    _fields_ = [("cam", hyrf_camera), ("fields", hyrf_fields), ("bg", hyrf_background),
+                ("C_fg", _vp), ("T_final", _vp), ("C", _vp), ("status", _vp)]
+
+
+class hyrf_composite_background_backward_args(C.Structure):
+    _fields_ = [("fwd", hyrf_composite_background_args), ("d_C", _vp), ("d_C_fg", _vp),
+                ("d_T_final", _vp), ("grads", hyrf_field_grads), ("loss_scale", C.c_float)]
+
+
+class hyrf_loss_args(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("C", _vp), ("target", _vp),
+                ("lambda_", C.c_float), ("grad_scale", C.c_float), ("loss", _vp), ("d_C", _vp)]
+
+
+_ARGS = {
+    "hyrf_query_fields": hyrf_query_fields_args,
+    "hyrf_query_fields_backward": hyrf_query_fields_backward_args,
+    "hyrf_project": hyrf_project_args,
+    "hyrf_project_backward": hyrf_project_backward_args,
+    "hyrf_bin_sort": hyrf_bin_sort_args,
+    "hyrf_bin_sort_backward": hyrf_bin_sort_args,
+    "hyrf_rasterize": hyrf_rasterize_args,
+    "hyrf_rasterize_backward": hyrf_rasterize_backward_args,
+    "hyrf_composite_background": hyrf_composite_background_args,
+    "hyrf_composite_background_backward": hyrf_composite_background_backward_args,
+    "hyrf_loss": hyrf_loss_args,
+}
+_WS = {k: (k + "_workspace_size") for k in _ARGS if k != "hyrf_bin_sort_backward"}
+_WS["hyrf_bin_sort_backward"] = None
+
+_lib = None
+
+
+class HyrfError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libhyrf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise HyrfError(f"{LIB_PATH} is missing: build it with paper_2509_17083_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, st in _ARGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = [C.POINTER(st), _vp, C.c_size_t, _vp]
+            fn.restype = C.c_int32
+            ws = _WS.get(name)
+            if ws:
+                f = getattr(L, ws)
+                f.argtypes = [C.POINTER(st)]
+                f.restype = C.c_size_t
+        L.hyrf_read_status.argtypes = [_vp, _vp, C.POINTER(C.c_int32)]
+        L.hyrf_read_status.restype = C.c_int32
+        L.hyrf_error_string.argtypes = [C.c_int32]
+        L.hyrf_error_string.restype = C.c_char_p
+        L.hyrf_launch_count.argtypes = []
+        L.hyrf_launch_count.restype = C.c_uint64
+        _lib = L
+    return _lib
+
+
+EXPORTED = list(_ARGS) + [k + "_workspace_size" for k in _ARGS if k != "hyrf_bin_sort_backward"] + [
+    "hyrf_read_status", "hyrf_error_string", "hyrf_launch_count"]
+
+
+def ptr(t):
+    """Device address of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise HyrfError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Workspace:
+    """Grow-only device scratch buffer handed to the library as `workspace`."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes):
+        if nbytes == 0:
+            return None, 0
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        return self.buf.data_ptr(), self.buf.numel()
+
+
+def call(name, args, ws: Workspace = None, stream=None):
+    """Invoke hyrf_<name>(&args, workspace, bytes, stream); raise on a host-side error."""
+    L = lib()
+    size_fn = _WS.get(name)
+    need = getattr(L, size_fn)(C.byref(args)) if size_fn else 0
+    if need and ws is None:
+        ws = Workspace()
+    wp, wb = ws.get(need) if need else (None, 0)
+    st = getattr(L, name)(C.byref(args), wp, wb, stream_handle(stream))
+    if st != HYRF_OK:
+        raise HyrfError(f"{name}: {L.hyrf_error_string(st).decode()} ({st})")
+    return st
+
+
+def read_status(status, stream=None):
+    out = C.c_int32(0)
+    lib().hyrf_read_status(ptr(status), stream_handle(stream), C.byref(out))
+    return out.value
+
+
+def error_string(st):
+    return lib().hyrf_error_string(st).decode()
+
+
+def launch_count():
+    return int(lib().hyrf_launch_count())
+
+
+# ---------------------------------------------------------------- struct builders
+
+def camera(cam):
+    c = hyrf_camera()
+    R = [float(x) for x in torch.as_tensor(cam.R, dtype=torch.float32).reshape(9)]
+    t = [float(x) for x in torch.as_tensor(cam.t, dtype=torch.float32).reshape(3)]
+    c.R[:] = R
+    c.t[:] = t
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height = cam.width, cam.height
+    c.z_near, c.cull_tol = cam.z_near, cam.cull_tol
+    return c
+
+
+def grid(table, g, dtype):
+    s = hyrf_grid()
+    s.table = ptr(table)
+    s.n_levels, s.log2_T, s.n_feat, s.base_res = g.n_levels, g.log2_T, g.n_feat, g.base_res
+    s.growth = g.growth
+    s.dtype = dtype
+    return s
+
+
+def mlp(Ws, bs, m, dtype):
+    s = hyrf_mlp()
+    for l in range(m.n_hidden + 1):
+        s.W[l] = ptr(Ws[l])
+        s.b[l] = ptr(bs[l])
+    s.n_in, s.width, s.n_hidden, s.n_out = m.n_in, m.width, m.n_hidden, m.n_out
+    s.dtype = dtype
+    return s
+
+
+def field_grads(geo_table=None, rad_table=None, geo_W=(), geo_b=(), col_W=(), col_b=()):
+    s = hyrf_field_grads()
+    s.geo_table, s.rad_table = ptr(geo_table), ptr(rad_table)
+    for l, t in enumerate(geo_W):
+        s.geo_W[l] = ptr(t)
+    for l, t in enumerate(geo_b):
+        s.geo_b[l] = ptr(t)
+    for l, t in enumerate(col_W):
+        s.col_W[l] = ptr(t)
+    for l, t in enumerate(col_b):
+        s.col_b[l] = ptr(t)
+    return s
+
+
+def _fill(st, kw):
+    for k, v in kw.items():
+        if isinstance(v, torch.Tensor):
+            v = ptr(v)
+        setattr(st, k, v)
+    return st
+
+
+# ---------------------------------------------------------------- the calls
+
+def hyrf_query_fields(ws=None, stream=None, **kw):
+    return call("hyrf_query_fields", _fill(hyrf_query_fields_args(), kw), ws, stream)
+
+
+def hyrf_query_fields_backward(ws=None, stream=None, **kw):
+    return call("hyrf_query_fields_backward", _fill(hyrf_query_fields_backward_args(), kw), ws,
+                stream)
+
+
+def hyrf_project(ws=None, stream=None, **kw):
+    return call("hyrf_project", _fill(hyrf_project_args(), kw), ws, stream)
+
+
+def hyrf_project_backward(ws=None, stream=None, **kw):
+    return call("hyrf_project_backward", _fill(hyrf_project_backward_args(), kw), ws, stream)
+
+
+def hyrf_bin_sort(ws=None, stream=None, **kw):
+    return call("hyrf_bin_sort", _fill(hyrf_bin_sort_args(), kw), ws, stream)
+
+
+def hyrf_bin_sort_backward(ws=None, stream=None, **kw):
+    return call("hyrf_bin_sort_backward", _fill(hyrf_bin_sort_args(), kw), ws, stream)
+
+
+def hyrf_rasterize(ws=None, stream=None, **kw):
+    return call("hyrf_rasterize", _fill(hyrf_rasterize_args(), kw), ws, stream)
+
+
+def hyrf_rasterize_backward(fwd, ws=None, stream=None, **kw):
+    a = _fill(hyrf_rasterize_backward_args(), kw)
+    a.fwd = fwd
+    return call("hyrf_rasterize_backward", a, ws, stream)
+
+
+def hyrf_composite_background(ws=None, stream=None, **kw):
+    return call("hyrf_composite_background", _fill(hyrf_composite_background_args(), kw), ws,
+                stream)
+
+
+def hyrf_composite_background_backward(fwd, ws=None, stream=None, **kw):
+    a = _fill(hyrf_composite_background_backward_args(), kw)
+    a.fwd = fwd
+    return call("hyrf_composite_background_backward", a, ws, stream)
+
+
+def hyrf_loss(ws=None, stream=None, **kw):
+    lam = kw.pop("lambda_", kw.pop("lam", 0.0))
+    a = _fill(hyrf_loss_args(), kw)
+    a.lambda_ = lam
+    return call("hyrf_loss", a, ws, stream)

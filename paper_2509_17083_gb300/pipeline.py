@@ -1,0 +1,229 @@
+"""One HyRF view, forward and backward, through the libhyrf C ABI.
+
+DeviceModel holds the trainable state on the GPU (explicit Gaussians, the
+two hash grids and decoders) and its float32 gradient buffers. ViewRenderer
+holds every per-view buffer (sized once) and runs the path of Fig. 3:
+
+  hyrf_query_fields -> hyrf_project -> hyrf_bin_sort -> hyrf_rasterize
+  -> hyrf_composite_background -> hyrf_loss, then the reverse calls.
+
+All arithmetic happens in the library's kernels; this module only allocates
+tensors and fills the argument structs.
+"""
+import math
+
+import torch
+
+from . import hyrf as H
+
+
+def _t(a, device, dtype=torch.float32):
+    return torch.as_tensor(a).to(device=device, dtype=dtype).contiguous()
+
+
+class DeviceModel:
+    def __init__(self, workload, device="cuda"):
+        self.device = device
+        self.workload = workload
+        g = workload.gaussians
+        fl = workload.fields
+        self.n = g.n
+        self.pos = _t(g.pos, device)
+        self.alpha_e = _t(g.alpha_e, device)
+        self.scale_e = _t(g.scale_e, device)
+        self.color_e = _t(g.color_e, device)
+        self.fl = fl
+        self.bf16 = workload.precision == "bf16"
+        tdt = torch.bfloat16 if self.bf16 else torch.float32
+        self.geo_table = _t(fl.geo.table, device, tdt)
+        self.rad_table = _t(fl.rad.table, device, tdt)
+        wdt = torch.bfloat16 if self.bf16 else torch.float32
+        self.geo_W = [_t(w, device, wdt) for w in fl.geo_mlp.W]
+        self.geo_b = [_t(b, device) for b in fl.geo_mlp.b]
+        self.col_W = [_t(w, device, wdt) for w in fl.col_mlp.W]
+        self.col_b = [_t(b, device) for b in fl.col_mlp.b]
+        self.dtype_code = H.HYRF_BF16 if self.bf16 else H.HYRF_F32
+        self.grad = {}
+        self.zero_grad()
+
+    def zero_grad(self):
+        d = self.device
+        if not self.grad:
+            self.grad = dict(
+                pos=torch.zeros_like(self.pos), alpha_e=torch.zeros_like(self.alpha_e),
+                scale_e=torch.zeros_like(self.scale_e), color_e=torch.zeros_like(self.color_e),
+                geo_table=torch.zeros(self.geo_table.shape, device=d),
+                rad_table=torch.zeros(self.rad_table.shape, device=d),
+                geo_W=[torch.zeros(w.shape, device=d) for w in self.geo_W],
+                geo_b=[torch.zeros_like(b) for b in self.geo_b],
+                col_W=[torch.zeros(w.shape, device=d) for w in self.col_W],
+                col_b=[torch.zeros_like(b) for b in self.col_b])
+        else:
+            for v in self.grad.values():
+                if isinstance(v, list):
+                    for x in v:
+                        x.zero_()
+                else:
+                    v.zero_()
+
+    def fields_struct(self):
+        fl = self.fl
+        s = H.hyrf_fields()
+        s.box_lo[:] = [float(x) for x in fl.box_lo]
+        s.box_hi[:] = [float(x) for x in fl.box_hi]
+        s.geo = H.grid(self.geo_table, fl.geo, self.dtype_code)
+        s.rad = H.grid(self.rad_table, fl.rad, self.dtype_code)
+        s.geo_mlp = H.mlp(self.geo_W, self.geo_b, fl.geo_mlp, self.dtype_code)
+        s.col_mlp = H.mlp(self.col_W, self.col_b, fl.col_mlp, self.dtype_code)
+        s.pe_freq, s.pe_pad = fl.pe_freq, fl.pe_pad
+        return s
+
+    def grads_struct(self):
+        g = self.grad
+        return H.field_grads(g["geo_table"], g["rad_table"], g["geo_W"], g["geo_b"], g["col_W"],
+                             g["col_b"])
+
+
+class ViewRenderer:
+    """Buffers and calls for one camera of fixed size."""
+
+    def __init__(self, model: DeviceModel, cam, bg, lam=0.0, loss_scale=1.0, capacity=None):
+        self.m = model
+        self.cam = cam
+        self.bg = bg
+        self.lam = float(lam)
+        self.loss_scale = float(loss_scale)
+        d = model.device
+        n = model.n
+        W, Hh = cam.width, cam.height
+        self.W, self.H = W, Hh
+        self.TX, self.TY = (W + H.TILE - 1) // H.TILE, (Hh + H.TILE - 1) // H.TILE
+        i32, f32 = torch.int32, torch.float32
+        z = lambda *s, dt=f32: torch.zeros(*s, dtype=dt, device=d)
+        self.status = z(1, dt=i32)
+        self.vis_ids, self.n_vis = z(max(n, 1), dt=i32), z(1, dt=i32)
+        self.alpha, self.scale, self.quat, self.color = z(n), z(n, 3), z(n, 4), z(n, 3)
+        self.mean2d, self.conic, self.depth = z(n, 2), z(n, 3), z(n)
+        self.rect, self.ntiles = z(n, 4, dt=i32), z(n, dt=i32)
+        self.flag = z(max(n, 1), dt=torch.uint8)
+        self.ranges = z(self.TX * self.TY, 2, dt=i32)
+        self.n_inst = z(1, dt=i32)
+        self.C_fg, self.T_final = z(Hh, W, 3), z(Hh, W)
+        self.n_contrib = z(Hh, W, dt=i32)
+        self.C = z(Hh, W, 3)
+        self.loss = z(1)
+        self.dC, self.dT = z(Hh, W, 3), z(Hh, W)
+        self.d_mean2d, self.d_conic, self.d_alpha, self.d_color = z(n, 2), z(n, 3), z(n), z(n, 3)
+        self.d_scale, self.d_quat = z(n, 3), z(n, 4)
+        self.ws = {k: H.Workspace(d) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l")}
+        self.set_capacity(capacity if capacity is not None else max(4 * n, 1 << 16))
+        self.ccam = H.camera(cam)
+        self.cbg = H.hyrf_background(int(bg.mode), int(bg.map_h), int(bg.map_w), float(bg.radius))
+
+    def set_capacity(self, cap):
+        self.capacity = int(cap)
+        d = self.m.device
+        self.keys = torch.zeros(self.capacity, dtype=torch.int64, device=d)
+        self.vals = torch.zeros(self.capacity, dtype=torch.int32, device=d)
+
+    # ------------------------------------------------------------- forward
+    def _raster_args(self):
+        a = H.hyrf_rasterize_args()
+        H._fill(a, dict(n=self.m.n, n_vis=self.n_vis, ranges=self.ranges, vals=self.vals,
+                        mean2d=self.mean2d, conic=self.conic, alpha=self.alpha, color=self.color,
+                        width=self.W, height=self.H, tile=H.TILE, C_fg=self.C_fg,
+                        T_final=self.T_final, n_contrib=self.n_contrib, status=self.status))
+        return a
+
+    def _bg_args(self):
+        a = H.hyrf_composite_background_args()
+        a.cam = self.ccam
+        a.fields = self.m.fields_struct()
+        a.bg = self.cbg
+        H._fill(a, dict(C_fg=self.C_fg, T_final=self.T_final, C=self.C, status=self.status))
+        return a
+
+    def forward(self, target=None, want_keys=True):
+        m = self.m
+        fs = m.fields_struct()
+        H.hyrf_query_fields(ws=self.ws["q"], n=m.n, pos=m.pos, alpha_e=m.alpha_e, scale_e=m.scale_e,
+                            color_e=m.color_e, cam=self.ccam, fields=fs, vis_ids=self.vis_ids,
+                            n_vis=self.n_vis, alpha=self.alpha, scale=self.scale, quat=self.quat,
+                            color=self.color, status=self.status)
+        self.project()
+        self.bin_sort(want_keys)
+        H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
+        H.call("hyrf_composite_background", self._bg_args(), self.ws["b"])
+        if target is not None:
+            self.loss_fn(target)
+        return self.C
+
+    def project(self):
+        m = self.m
+        H.hyrf_project(ws=self.ws["p"], n=m.n, pos=m.pos, vis_ids=self.vis_ids, n_vis=self.n_vis,
+                       scale=self.scale, quat=self.quat, cam=self.ccam, tile=H.TILE,
+                       mean2d=self.mean2d, conic=self.conic, depth=self.depth, rect=self.rect,
+                       ntiles=self.ntiles, fp64_flag=self.flag, status=self.status)
+
+    def bin_sort(self, want_keys=True):
+        H.hyrf_bin_sort(ws=self.ws["s"], n=self.m.n, n_vis=self.n_vis, rect=self.rect,
+                        ntiles=self.ntiles, depth=self.depth, tiles_x=self.TX, tiles_y=self.TY,
+                        capacity=self.capacity, keys=self.keys if want_keys else None,
+                        vals=self.vals, ranges=self.ranges, n_instances=self.n_inst,
+                        status=self.status)
+
+    def loss_fn(self, target, grad=True):
+        H.hyrf_loss(ws=self.ws["l"], width=self.W, height=self.H, C=self.C, target=target,
+                    lam=self.lam, grad_scale=1.0, loss=self.loss, d_C=self.dC if grad else None)
+
+    # ------------------------------------------------------------- backward
+    def backward(self):
+        """Reverse of every stage; dL/dC must be in self.dC. Adds into model.grad."""
+        m = self.m
+        for t in (self.d_mean2d, self.d_conic, self.d_alpha, self.d_color):
+            t.zero_()
+        g = m.grads_struct()
+        H.hyrf_composite_background_backward(self._bg_args(), ws=self.ws["bb"], d_C=self.dC,
+                                             d_C_fg=None, d_T_final=self.dT, grads=g,
+                                             loss_scale=self.loss_scale)
+        H.hyrf_rasterize_backward(self._raster_args(), ws=self.ws["rb"], d_C_fg=self.dC,
+                                  d_T_final=self.dT, d_mean2d=self.d_mean2d, d_conic=self.d_conic,
+                                  d_alpha=self.d_alpha, d_color=self.d_color)
+        H.hyrf_project_backward(ws=self.ws["p"], n=m.n, pos=m.pos, vis_ids=self.vis_ids,
+                                n_vis=self.n_vis, scale=self.scale, quat=self.quat, cam=self.ccam,
+                                d_mean2d=self.d_mean2d, d_conic=self.d_conic, d_pos=m.grad["pos"],
+                                d_scale=self.d_scale, d_quat=self.d_quat, status=self.status)
+        H.hyrf_query_fields_backward(ws=self.ws["qb"], n=m.n, pos=m.pos, alpha_e=m.alpha_e,
+                                     scale_e=m.scale_e, color_e=m.color_e, cam=self.ccam,
+                                     fields=m.fields_struct(), vis_ids=self.vis_ids,
+                                     n_vis=self.n_vis, d_alpha=self.d_alpha, d_scale=self.d_scale,
+                                     d_quat=self.d_quat, d_color=self.d_color, d_pos=m.grad["pos"],
+                                     d_alpha_e=m.grad["alpha_e"], d_scale_e=m.grad["scale_e"],
+                                     d_color_e=m.grad["color_e"], grads=g,
+                                     loss_scale=self.loss_scale, status=self.status)
+
+    def step(self, target):
+        """One training iteration of the view: forward, loss, backward."""
+        self.forward(target)
+        self.backward()
+        return self.loss
+
+    def check_status(self):
+        st = H.read_status(self.status)
+        return st
+
+    def fit_capacity(self, target=None, headroom=1.25):
+        """Run the forward once and grow the instance capacity until it fits."""
+        for _ in range(8):
+            self.status.zero_()
+            self.forward(target)
+            st = H.read_status(self.status)
+            if not st & H.HYRF_ERR_OVERFLOW:
+                k = int(self.n_inst.item())
+                if self.capacity > 3 * int(k * headroom) + (1 << 16):
+                    self.set_capacity(int(k * headroom) + (1 << 16))
+                    self.status.zero_()
+                    self.forward(target)
+                return st
+            self.set_capacity(self.capacity * 2)
+        raise H.HyrfError("instance capacity could not be fitted")

@@ -1,0 +1,93 @@
+"""End-to-end GPU parity: one training iteration of a view (all five stages
+forward, Eq. 12 loss, all reverse passes) against the composed FP64 oracle,
+at sizes the oracle finishes in seconds (several tiles, ragged image edges).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_17083_gb300 import hyrf as H
+from paper_2509_17083_gb300 import synth
+from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer
+from tests.gpu_util import (TOL_GRAD_F32, TOL_IMG_F32, TOL_IMG_F32_TRAINED, cuda_f32, np_,
+                            rect_flip_tiles, rel_l2, tile_mask)
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # full-size config 1 (4,096 Gaussians, 128x128, 16x16 map, L1), its U(+-1e-4) init
+    "config1": lambda: synth.config1(),
+    # config 1 with trained-like grids (U(+-0.5))
+    "config1_trained": lambda: synth.config1(table_init=0.5),
+    # config 2 generator at reduced size (map background, L1 + 0.2 D-SSIM)
+    "config2_small": lambda: synth.config2(n=20000, width=203, height=157, log2_T=14,
+                                           n_clusters=16),
+    "config2_small_trained": lambda: synth.config2(n=20000, width=203, height=157, log2_T=14,
+                                                   n_clusters=16, table_init=0.5),
+    # config 3 generator at reduced size, FP32 variant (exact background)
+    "config3_small_f32": lambda: synth.config3(n=30000, width=301, height=203, log2_T=15,
+                                               n_clusters=32, precision="f32"),
+    "config3_small_f32_trained": lambda: synth.config3(n=30000, width=301, height=203, log2_T=15,
+                                                       n_clusters=32, precision="f32",
+                                                       table_init=0.5),
+}
+
+
+def _run(w):
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+    tgt = cuda_f32(w.targets[0])
+    r.fit_capacity(tgt)
+    m.zero_grad()
+    r.status.zero_()
+    r.step(tgt)
+    torch.cuda.synchronize()
+    return m, r
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_view_iteration_matches_oracle(case):
+    w = CASES[case]()
+    m, r = _run(w)
+    assert H.read_status(r.status) == 0
+    L, fw, grads, inter = oracle.loss_and_grads(w.gaussians, w.fields, w.cams[0], w.bg,
+                                                w.targets[0], w.ssim_lambda)
+    # integer path: visibility exact
+    nv = int(r.n_vis.item())
+    assert nv == len(fw["ids"]) and np.array_equal(np_(r.vis_ids)[:nv], fw["ids"])
+    # image: within tolerance wherever no threshold test sits within 1e-4 of
+    # its threshold and no tile-rectangle decision differs between the two
+    # sides (the FP32 field outputs feed the FP32 rectangle)
+    W, Hh = w.cams[0].width, w.cams[0].height
+    flips, n_flip = rect_flip_tiles(np_(r.rect)[:nv], fw["rect"], (W + 15) // 16)
+    assert n_flip <= max(3, nv // 2000), n_flip
+    safe = (fw["margin"] > 1e-4) & ~tile_mask(flips, W, Hh)
+    assert safe.mean() > 0.95, safe.mean()
+    tol = TOL_IMG_F32_TRAINED if case.endswith("_trained") else TOL_IMG_F32
+    err = np.abs(np_(r.C) - fw["C"]).max(-1)
+    assert err[safe].max() < tol, err[safe].max()
+    assert np.quantile(err, 0.999) < 1e-3
+    assert abs(float(r.loss.item()) - L) < 1e-5
+    # gradients of every parameter class
+    g = m.grad
+    for key in ("pos", "alpha_e", "scale_e", "color_e", "geo_table", "rad_table"):
+        e = rel_l2(np_(g[key]), grads[key])
+        assert e < TOL_GRAD_F32, (key, e)
+    for key in ("geo_W", "geo_b", "col_W", "col_b"):
+        for l in range(len(g[key])):
+            e = rel_l2(np_(g[key][l]), grads[key][l])
+            assert e < TOL_GRAD_F32, (key, l, e)
+
+
+def test_two_iterations_are_identical_in_integers():
+    w = CASES["config2_small_trained"]()
+    m, r = _run(w)
+    k1, v1, rg1 = np_(r.keys).copy(), np_(r.vals).copy(), np_(r.ranges).copy()
+    n1 = int(r.n_inst.item())
+    r.step(cuda_f32(w.targets[0]))
+    torch.cuda.synchronize()
+    assert int(r.n_inst.item()) == n1
+    assert np.array_equal(np_(r.keys)[:n1], k1[:n1])
+    assert np.array_equal(np_(r.vals)[:n1], v1[:n1])
+    assert np.array_equal(np_(r.ranges), rg1)
