@@ -52,6 +52,7 @@ typedef enum {
   HYRF_ERR_CUDA = 4,
   HYRF_ERR_OVERFLOW = 8,  /* device: more tile instances than `capacity` */
   HYRF_ERR_BOUNDS = 16,   /* device: an index read from memory was out of range */
+  HYRF_ERR_TIMEOUT = 32,  /* device: a bounded wait on a tensor-core completion gave up */
 } hyrf_status;
 
 typedef enum { HYRF_F32 = 0, HYRF_BF16 = 1 } hyrf_dtype;

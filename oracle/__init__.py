@@ -450,11 +450,14 @@ def render(g, fields, cam, bg, tile=TILE):
                 T_final=T_final, n_contrib=n_contrib, margin=margin, C=C_img, c_s=c_s)
 
 
-def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE):
+def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE, dC_mask=None):
     """Forward, Eq. 12 loss and the analytic reverse pass of every stage.
-    Returns (loss, forward dict, gradient dict over all parameters)."""
+    Returns (loss, forward dict, gradient dict over all parameters).
+    dC_mask (optional [H,W]) multiplies dL/dC before the reverse pass."""
     fw = render(g, fields, cam, bg, tile)
     L, dC = loss(fw["C"], target, lam)
+    if dC_mask is not None:
+        dC = dC * np.asarray(dC_mask, np.float64)[..., None]
     gb = background_backward(cam, fields, bg, fw["T_final"], dC)
     d_mean2d, d_conic, d_op, d_col = rasterize_backward(
         cam.width, cam.height, fw["ranges"], fw["vals"], fw["mean2d"], fw["conic"], fw["alpha"],
@@ -482,6 +485,34 @@ def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE):
                  d_scale=d_scale, d_quat=d_quat, dC=dC, d_T_final=gb["T_final"],
                  d_C_fg=gb["C_fg"])
     return L, fw, grads, inter
+
+
+def decision_safe_mask(fw, cam, tile=TILE, comp_margin=1e-4, rect_margin_px=1e-2):
+    """Pixels of a rendered view (the dict `render` returns) whose value is a
+    smooth function of the inputs near this point: no compositing threshold
+    test within `comp_margin` (relative) of its threshold, and not in a tile
+    that a Gaussian's rectangle could gain or lose because 3 sqrt(lambda_max)
+    or a rectangle edge lies within `rect_margin_px` of an integer boundary."""
+    safe = fw["margin"] > comp_margin
+    con = np.asarray(fw["conic"])
+    det = con[:, 0] * con[:, 2] - con[:, 1] ** 2
+    sa, sb, sc = con[:, 2] / det, -con[:, 1] / det, con[:, 0] / det
+    mid = 0.5 * (sa + sc)
+    lam = mid + np.sqrt(np.maximum(mid * mid - (sa * sc - sb * sb), 0.0))
+    r3 = 3.0 * np.sqrt(lam)
+    rad = np.ceil(r3)
+    m = np.asarray(fw["mean2d"])
+    dist = np.abs(r3 - np.round(r3))
+    for e in ((m[:, 0] - rad) / tile, (m[:, 0] + rad) / tile, (m[:, 1] - rad) / tile,
+              (m[:, 1] + rad) / tile):
+        dist = np.minimum(dist, np.abs(e - np.round(e)) * tile)
+    TX, TY = tiles_of(cam.width, cam.height, tile)
+    bad = np.zeros((TY, TX), bool)
+    for i in np.nonzero(dist < rect_margin_px)[0]:
+        x0, y0, x1, y1 = fw["rect"][i]
+        bad[max(0, y0 - 1):min(TY, y1 + 1), max(0, x0 - 1):min(TX, x1 + 1)] = True
+    tile_bad = np.kron(bad, np.ones((tile, tile), bool))[:cam.height, :cam.width]
+    return safe & ~tile_bad
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]

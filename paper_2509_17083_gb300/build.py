@@ -16,14 +16,19 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libhyrf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# object name -> (source, extra nvcc flags)
 UNITS = {
-    "api.cu": [],
-    "geom.cu": ["-fmad=false"],
-    "fields.cu": [],
-    "proj_bwd.cu": [],
-    "sort.cu": [],
-    "raster.cu": [],
-    "loss.cu": [],
+    "api": ("api.cu", []),
+    "geom": ("geom.cu", ["-fmad=false"]),
+    "fields0": ("fields.cu", ["-DHYRF_FIELDS_PART=0"]),
+    "fields1": ("fields.cu", ["-DHYRF_FIELDS_PART=1"]),
+    "fields2": ("fields.cu", ["-DHYRF_FIELDS_PART=2"]),
+    "fields3": ("fields.cu", ["-DHYRF_FIELDS_PART=3"]),
+    "fields_tc": ("fields_tc.cu", []),
+    "proj_bwd": ("proj_bwd.cu", []),
+    "sort": ("sort.cu", []),
+    "raster": ("raster.cu", []),
+    "loss": ("loss.cu", []),
 }
 
 
@@ -47,9 +52,10 @@ def _stale(obj, src):
     return any(os.path.getmtime(f) > t for f in _deps() + [__file__])
 
 
-def _compile(unit, extra, verbose):
+def _compile(name, spec, verbose):
+    unit, extra = spec
     src = os.path.join(CSRC, unit)
-    obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+    obj = os.path.join(BUILD, name + ".o")
     if not _stale(obj, src):
         return obj
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -58,7 +64,7 @@ def _compile(unit, extra, verbose):
         cmd.append("-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {unit}:\n{r.stderr}")
+        raise RuntimeError(f"nvcc failed for {name} ({unit}):\n{r.stderr}")
     if verbose and r.stderr:
         sys.stderr.write(r.stderr)
     os.replace(obj + ".tmp", obj)

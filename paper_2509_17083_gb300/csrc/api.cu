@@ -16,6 +16,9 @@ hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int
                            int32_t* status, cudaStream_t s);
 hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t s);
 hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
+hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
+hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F,
+                                   cudaStream_t s);
 hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
                              cudaStream_t s);
 size_t slab_bytes(const FieldsDev& F, bool geo);
@@ -53,6 +56,14 @@ static bool cam_ok(const hyrf_camera& c) {
 
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// bf16 decoder weights are staged with 16-byte vector loads
+static bool bf16_weights_ok(const hyrf_mlp& m) {
+  if (m.dtype != HYRF_BF16) return true;
+  for (int l = 0; l <= m.n_hidden && l < 3; ++l)
+    if (!aligned(m.W[l], 16)) return false;
+  return true;
+}
+
 static bool ws_ok(void* ws, size_t have, size_t need) {
   return have >= need && (need == 0 || (ws != nullptr && aligned(ws, 256)));
 }
@@ -81,10 +92,13 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
     return HYRF_ERR_INVALID_ARG;
   FieldsDev F;
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
-  if (F.gm.bf16 || F.cm.bf16) return HYRF_ERR_UNSUPPORTED;
+  if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
+    return HYRF_ERR_UNSUPPORTED;
+  if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
   if (st != HYRF_OK) return st;
-  return launch_query_fwd(*a, F, S(stream));
+  // BF16 decoders run on the tensor cores, FP32 decoders on the CUDA cores
+  return F.cm.bf16 ? launch_query_fwd_tc(*a, F, S(stream)) : launch_query_fwd(*a, F, S(stream));
 }
 
 size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a) {
@@ -103,7 +117,8 @@ hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a,
     return HYRF_ERR_INVALID_ARG;
   FieldsDev F;
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
-  if (F.gm.bf16 || F.cm.bf16) return HYRF_ERR_UNSUPPORTED;
+  if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
+    return HYRF_ERR_UNSUPPORTED;
   if (!ws_ok(ws, ws_bytes, hyrf_query_fields_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
   return launch_query_bwd(*a, F, ws, S(stream));
 }
@@ -214,7 +229,7 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
     return HYRF_ERR_INVALID_ARG;
   if (a->bg.mode != 0 && a->bg.mode != 1) return HYRF_ERR_INVALID_ARG;
   if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
-  if (F.cm.bf16) return HYRF_ERR_UNSUPPORTED;
+  if (F.cm.bf16 && a->fields.rad.n_levels != 16) return HYRF_ERR_UNSUPPORTED;
   return HYRF_OK;
 }
 
@@ -230,6 +245,8 @@ hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, v
   hyrf_status st = bg_check(a, F);
   if (st != HYRF_OK) return st;
   if (!a->C || !ws_ok(ws, ws_bytes, bg_workspace(*a, F, false))) return HYRF_ERR_INVALID_ARG;
+  if (!bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
+  if (a->bg.mode == 0 && F.cm.bf16) return launch_bg_exact_fwd_tc(*a, F, S(stream));
   return launch_bg_fwd(*a, F, ws, S(stream));
 }
 
@@ -279,6 +296,7 @@ const char* hyrf_error_string(int32_t st) {
   if (st & HYRF_ERR_UNSUPPORTED) return "unsupported configuration";
   if (st & HYRF_ERR_OVERFLOW) return "tile instances exceeded the capacity";
   if (st & HYRF_ERR_BOUNDS) return "an index read from memory was out of range";
+  if (st & HYRF_ERR_TIMEOUT) return "a bounded wait on a tensor-core completion gave up";
   return "unknown status";
 }
 

@@ -182,42 +182,72 @@ __device__ __forceinline__ void pos_enc_bwd(const float d[3], const float* dout,
   }
 }
 
-// ---------------------------------------------------------------- decoder layers (FP32)
+// ---------------------------------------------------------------- decoder layers (CUDA cores)
 
-// y = W x + b (ReLU if requested). W [OUT][IN] float32 read through the
-// read-only path: every lane of a warp reads the same weight, one broadcast.
-template <int IN, int OUT, bool RELU>
-__device__ __forceinline__ void dense_fwd(const float* __restrict__ W, const float* __restrict__ b,
-                                          const float* x, float* y) {
-  static_assert(IN % 4 == 0, "IN must be a multiple of 4");
-#pragma unroll
-  for (int o = 0; o < OUT; ++o) {
-    float acc = __ldg(b + o);
-    const float4* w4 = reinterpret_cast<const float4*>(W + o * IN);
-#pragma unroll
-    for (int i = 0; i < IN / 4; ++i) {
-      const float4 w = __ldg(w4 + i);
-      acc = fmaf(w.x, x[4 * i], acc);
-      acc = fmaf(w.y, x[4 * i + 1], acc);
-      acc = fmaf(w.z, x[4 * i + 2], acc);
-      acc = fmaf(w.w, x[4 * i + 3], acc);
-    }
-    y[o] = RELU ? fmaxf(acc, 0.0f) : acc;
-  }
+// Four consecutive weights as float (float32 or bfloat16 storage). Every
+// lane of a warp reads the same weights: one broadcast through the
+// read-only path.
+__device__ __forceinline__ float4 w4(const float* __restrict__ W, int idx) {
+  return __ldg(reinterpret_cast<const float4*>(W + idx));
+}
+__device__ __forceinline__ float4 w4(const __nv_bfloat16* __restrict__ W, int idx) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(W + idx));
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// dx = W^T dz.
-template <int IN, int OUT>
-__device__ __forceinline__ void dense_dx(const float* __restrict__ W, const float* dz, float* dx) {
+// Dot product of weight row o (IN weights) with x (registers).
+template <int IN, class WT>
+__device__ __forceinline__ float dot_row(const WT* __restrict__ W, int o, const float* x) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < IN / 4; ++i) {
+    const float4 w = w4(W, o * IN + 4 * i);
+    acc = fmaf(w.x, x[4 * i], acc);
+    acc = fmaf(w.y, x[4 * i + 1], acc);
+    acc = fmaf(w.z, x[4 * i + 2], acc);
+    acc = fmaf(w.w, x[4 * i + 3], acc);
+  }
+  return acc;
+}
+
+// Hidden layer: col[o * pitch] = ReLU(W[o] . x + b[o]) for o < OUT. x is in
+// registers; the output goes to this thread's shared-memory column.
+template <int IN, int OUT, class WT>
+__device__ __forceinline__ void dense_col(const WT* __restrict__ W, const float* __restrict__ b,
+                                          const float* x, float* col, int pitch) {
+  static_assert(IN % 4 == 0, "IN must be a multiple of 4");
+#pragma unroll 2
+  for (int o = 0; o < OUT; ++o) col[o * pitch] = fmaxf(dot_row<IN>(W, o, x) + __ldg(b + o), 0.0f);
+}
+
+// Output layer (small OUT, registers): y = W x + b.
+template <int IN, int OUT, class WT>
+__device__ __forceinline__ void dense_out(const WT* __restrict__ W, const float* __restrict__ b,
+                                          const float* x, float* y) {
+#pragma unroll
+  for (int o = 0; o < OUT; ++o) y[o] = dot_row<IN>(W, o, x) + __ldg(b + o);
+}
+
+template <int N>
+__device__ __forceinline__ void load_col(const float* col, int pitch, float* x) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = col[i * pitch];
+}
+
+// dx = W^T dz with dz in this thread's shared-memory column (rows < OUT).
+template <int IN, int OUT, class WT>
+__device__ __forceinline__ void dense_dx_col(const WT* __restrict__ W, const float* dzcol, int pitch,
+                                             float* dx) {
 #pragma unroll
   for (int i = 0; i < IN; ++i) dx[i] = 0.0f;
-#pragma unroll
+#pragma unroll 2
   for (int o = 0; o < OUT; ++o) {
-    const float d = dz[o];
-    const float4* w4 = reinterpret_cast<const float4*>(W + o * IN);
+    const float d = dzcol[o * pitch];
 #pragma unroll
     for (int i = 0; i < IN / 4; ++i) {
-      const float4 w = __ldg(w4 + i);
+      const float4 w = w4(W, o * IN + 4 * i);
       dx[4 * i] = fmaf(w.x, d, dx[4 * i]);
       dx[4 * i + 1] = fmaf(w.y, d, dx[4 * i + 1]);
       dx[4 * i + 2] = fmaf(w.z, d, dx[4 * i + 2]);
@@ -226,18 +256,25 @@ __device__ __forceinline__ void dense_dx(const float* __restrict__ W, const floa
   }
 }
 
-// Whole decoder forward: IN -> WID (ReLU) [-> WID (ReLU)] -> OUT.
-template <int IN, int WID, int NH, int OUT>
-__device__ __forceinline__ void mlp_fwd(const MlpDev& m, const float* x, float* out) {
-  float h1[WID];
-  dense_fwd<IN, WID, true>(static_cast<const float*>(m.W[0]), m.b[0], x, h1);
+template <class WT>
+__device__ __forceinline__ const WT* wptr(const MlpDev& m, int l) {
+  return static_cast<const WT*>(m.W[l]);
+}
+
+// Whole decoder: IN -> WID (ReLU) [-> WID (ReLU)] -> OUT. `col` is this
+// thread's shared-memory column (WID rows, stride `pitch`) for the hidden
+// activations.
+template <int IN, int WID, int NH, int OUT, class WT>
+__device__ __forceinline__ void mlp_fwd(const MlpDev& m, const float* x, float* col, int pitch,
+                                        float* out) {
+  dense_col<IN, WID>(wptr<WT>(m, 0), m.b[0], x, col, pitch);
+  float h[WID];
+  load_col<WID>(col, pitch, h);
   if constexpr (NH == 2) {
-    float h2[WID];
-    dense_fwd<WID, WID, true>(static_cast<const float*>(m.W[1]), m.b[1], h1, h2);
-    dense_fwd<WID, OUT, false>(static_cast<const float*>(m.W[2]), m.b[2], h2, out);
-  } else {
-    dense_fwd<WID, OUT, false>(static_cast<const float*>(m.W[1]), m.b[1], h1, out);
+    dense_col<WID, WID>(wptr<WT>(m, 1), m.b[1], h, col, pitch);
+    load_col<WID>(col, pitch, h);
   }
+  dense_out<WID, OUT>(wptr<WT>(m, NH), m.b[NH], h, out);
 }
 
 // ---------------------------------------------------------------- CTA-level weight gradient

@@ -5,8 +5,17 @@
 // into a private float32 slab (no atomics); one reduction kernel adds the
 // slabs into the caller's gradient buffers.
 #include <cmath>
+#include <type_traits>
 
 #include "field_ops.cuh"
+
+// This file is compiled several times: part 0 holds the host-side dispatch,
+// the shape-independent kernels and their launch wrappers; parts 1-3 each
+// instantiate the templated kernels for one (levels, width, hidden layers,
+// weight type) combination, so the instantiations compile in parallel.
+#ifndef HYRF_FIELDS_PART
+#define HYRF_FIELDS_PART 0
+#endif
 
 namespace hyrf {
 
@@ -52,9 +61,14 @@ __device__ __forceinline__ void cam_center(const CamDev& c, float pc[3]) {
   for (int i = 0; i < 3; ++i) pc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
 }
 
-template <int NL, int WID, int NH>
-__global__ void __launch_bounds__(128) k_query_fwd(FieldsDev F, CamDev cam, QueryFwdIO io) {
+constexpr int kFwdThreads = 128;
+constexpr int kFwdPitch = kFwdThreads + 1;
+
+template <int NL, int WID, int NH, class WT>
+__global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev cam, QueryFwdIO io) {
   constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
+  __shared__ float hid[WID * kFwdPitch];
+  float* col = hid + threadIdx.x;
   const int nv = min(*io.n_vis, io.n);
   float pc[3];
   cam_center(cam, pc);
@@ -71,7 +85,7 @@ __global__ void __launch_bounds__(128) k_query_fwd(FieldsDev F, CamDev cam, Quer
     {
       float fg[NG];
       encode<NL>(F.geo, y, fg);
-      mlp_fwd<NG, WID, NH, 8>(F.gm, fg, go);
+      mlp_fwd<NG, WID, NH, 8, WT>(F.gm, fg, col, kFwdPitch, go);
     }
     float co[3];
     {
@@ -81,7 +95,7 @@ __global__ void __launch_bounds__(128) k_query_fwd(FieldsDev F, CamDev cam, Quer
       const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
       pos_enc(dir, fc + NG);
-      mlp_fwd<NC, WID, NH, 3>(F.cm, fc, co);
+      mlp_fwd<NC, WID, NH, 3, WT>(F.cm, fc, col, kFwdPitch, co);
     }
     // Eq. 7 aggregation with the explicit parameters.
     io.alpha[i] = sigmoidf_(go[0] + io.alpha_e[g]);
@@ -101,7 +115,7 @@ __global__ void __launch_bounds__(128) k_query_fwd(FieldsDev F, CamDev cam, Quer
 // [0, IN), hidden rows after it) and whose output gradient dz_out is given;
 // updates the CTA slab and returns dL/dinput in dx. All threads of the CTA
 // must call it (it synchronises).
-template <int IN, int WID, int NH, int OUT>
+template <int IN, int WID, int NH, int OUT, class WT>
 __device__ __forceinline__ void decoder_bwd(const MlpDev& m, const float* act, float* dzb,
                                             const float* dz_out, float* slab, const SlabLayout& SL,
                                             int dec, float* dx) {
@@ -111,50 +125,43 @@ __device__ __forceinline__ void decoder_bwd(const MlpDev& m, const float* act, f
   for (int r = 0; r < OUT; ++r) dzb[r * kActPitch + t] = dz_out[r];
   __syncthreads();
   cta_dw<OUT, WID>(dzb, hl, slab + SL.off_W[dec][NH], slab + SL.off_b[dec][NH]);
-  float dh[WID], dz[WID];
-  dense_dx<WID, OUT>(static_cast<const float*>(m.W[NH]), dz_out, dh);
-#pragma unroll
-  for (int r = 0; r < WID; ++r) dz[r] = hl[r * kActPitch + t] > 0.0f ? dh[r] : 0.0f;
+  float dh[WID];
+  dense_dx_col<WID, OUT>(wptr<WT>(m, NH), dzb + t, kActPitch, dh);
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < WID; ++r) dzb[r * kActPitch + t] = dz[r];
+  for (int r = 0; r < WID; ++r) dzb[r * kActPitch + t] = hl[r * kActPitch + t] > 0.0f ? dh[r] : 0.0f;
   __syncthreads();
   if constexpr (NH == 2) {
     const float* h1 = act + IN * kActPitch;
     cta_dw<WID, WID>(dzb, h1, slab + SL.off_W[dec][1], slab + SL.off_b[dec][1]);
-    dense_dx<WID, WID>(static_cast<const float*>(m.W[1]), dz, dh);
-#pragma unroll
-    for (int r = 0; r < WID; ++r) dz[r] = h1[r * kActPitch + t] > 0.0f ? dh[r] : 0.0f;
+    dense_dx_col<WID, WID>(wptr<WT>(m, 1), dzb + t, kActPitch, dh);
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < WID; ++r) dzb[r * kActPitch + t] = dz[r];
+    for (int r = 0; r < WID; ++r) dzb[r * kActPitch + t] = h1[r * kActPitch + t] > 0.0f ? dh[r] : 0.0f;
     __syncthreads();
   }
   cta_dw<WID, IN>(dzb, act, slab + SL.off_W[dec][0], slab + SL.off_b[dec][0]);
-  dense_dx<IN, WID>(static_cast<const float*>(m.W[0]), dz, dx);
+  dense_dx_col<IN, WID>(wptr<WT>(m, 0), dzb + t, kActPitch, dx);
   __syncthreads();
 }
 
 // Forward of a decoder storing its input and hidden activations in smem.
-template <int IN, int WID, int NH, int OUT>
+template <int IN, int WID, int NH, int OUT, class WT>
 __device__ __forceinline__ void decoder_fwd_store(const MlpDev& m, const float* x, float* act,
                                                   float* out) {
   const int t = threadIdx.x;
 #pragma unroll
   for (int r = 0; r < IN; ++r) act[r * kActPitch + t] = x[r];
-  float h1[WID];
-  dense_fwd<IN, WID, true>(static_cast<const float*>(m.W[0]), m.b[0], x, h1);
-#pragma unroll
-  for (int r = 0; r < WID; ++r) act[(IN + r) * kActPitch + t] = h1[r];
+  float* h1 = act + IN * kActPitch + t;
+  dense_col<IN, WID>(wptr<WT>(m, 0), m.b[0], x, h1, kActPitch);
+  float h[WID];
+  load_col<WID>(h1, kActPitch, h);
   if constexpr (NH == 2) {
-    float h2[WID];
-    dense_fwd<WID, WID, true>(static_cast<const float*>(m.W[1]), m.b[1], h1, h2);
-#pragma unroll
-    for (int r = 0; r < WID; ++r) act[(IN + WID + r) * kActPitch + t] = h2[r];
-    dense_fwd<WID, OUT, false>(static_cast<const float*>(m.W[2]), m.b[2], h2, out);
-  } else {
-    dense_fwd<WID, OUT, false>(static_cast<const float*>(m.W[1]), m.b[1], h1, out);
+    float* h2 = act + (IN + WID) * kActPitch + t;
+    dense_col<WID, WID>(wptr<WT>(m, 1), m.b[1], h, h2, kActPitch);
+    load_col<WID>(h2, kActPitch, h);
   }
+  dense_out<WID, OUT>(wptr<WT>(m, NH), m.b[NH], h, out);
 }
 
 template <int NL, int WID, int NH>
@@ -162,7 +169,7 @@ constexpr int query_bwd_smem_floats() {
   return (2 * NL + kPEPad + NH * WID) * kActPitch + WID * kActPitch;
 }
 
-template <int NL, int WID, int NH>
+template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev cam, QueryBwdIO io,
                                                            SlabLayout SL, float* slabs) {
   extern __shared__ float sm[];
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     {
       float x0[NG], out[8], dz8[8];
       encode<NL>(F.geo, y, x0);
-      decoder_fwd_store<NG, WID, NH, 8>(F.gm, x0, act, out);
+      decoder_fwd_store<NG, WID, NH, 8, WT>(F.gm, x0, act, out);
       const float a = sigmoidf_(out[0] + ae);
       dz8[0] = da * a * (1.0f - a);
 #pragma unroll
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
         io.d_scale_e[g] += (dz8[1] + dz8[2] + dz8[3]) * inv_ls;
       }
       float dx[NG];
-      decoder_bwd<NG, WID, NH, 8>(F.gm, act, dzb, dz8, slab, SL, 0, dx);
+      decoder_bwd<NG, WID, NH, 8, WT>(F.gm, act, dzb, dz8, slab, SL, 0, dx);
       if (ok) {
 #pragma unroll
         for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       float x0[NC], out[3], dz3[3];
       encode<NL>(F.rad, y, x0);
       pos_enc(dir, x0 + NG);
-      decoder_fwd_store<NC, WID, NH, 3>(F.cm, x0, act, out);
+      decoder_fwd_store<NC, WID, NH, 3, WT>(F.cm, x0, act, out);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const float c = sigmoidf_(out[k] + ce[k]);
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
         for (int k = 0; k < 3; ++k) io.d_color_e[3 * (int64_t)g + k] += dz3[k] * inv_ls;
       }
       float dx[NC];
-      decoder_bwd<NC, WID, NH, 3>(F.cm, act, dzb, dz3, slab, SL, 1, dx);
+      decoder_bwd<NC, WID, NH, 3, WT>(F.cm, act, dzb, dz3, slab, SL, 1, dx);
       if (ok) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) dx[k] *= inv_ls;
@@ -381,44 +388,48 @@ __device__ __forceinline__ MapTap map_tap(const float ps[3], int Hb, int Wb) {
 }
 
 // Background colour at contracted point y with view direction dir.
-template <int NL, int WID, int NH>
+template <int NL, int WID, int NH, class WT>
 __device__ __forceinline__ void bg_color(const FieldsDev& F, const float y[3], const float dir[3],
-                                         float cs[3]) {
+                                         float* col, float cs[3]) {
   constexpr int NG = 2 * NL, NC = NG + kPEPad;
   float x0[NC], out[3];
   encode<NL>(F.rad, y, x0);
   pos_enc(dir, x0 + NG);
-  mlp_fwd<NC, WID, NH, 3>(F.cm, x0, out);
+  mlp_fwd<NC, WID, NH, 3, WT>(F.cm, x0, col, kFwdPitch, out);
 #pragma unroll
   for (int k = 0; k < 3; ++k) cs[k] = sigmoidf_(out[k]);
 }
 
-template <int NL, int WID, int NH>
-__global__ void __launch_bounds__(128) k_bg_exact_fwd(FieldsDev F, CamDev cam, float radius,
-                                                      const float* __restrict__ C_fg,
-                                                      const float* __restrict__ T_final,
-                                                      float* __restrict__ C) {
+template <int NL, int WID, int NH, class WT>
+__global__ void __launch_bounds__(kFwdThreads) k_bg_exact_fwd(FieldsDev F, CamDev cam, float radius,
+                                                              const float* __restrict__ C_fg,
+                                                              const float* __restrict__ T_final,
+                                                              float* __restrict__ C) {
+  __shared__ float hid[WID * kFwdPitch];
+  float* col = hid + threadIdx.x;
   const int P = cam.W * cam.H;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const int i = p % cam.W, j = p / cam.W;
     float ps[3], dir[3], y[3], cs[3];
     bg_ray(cam, F, radius, i, j, ps, dir);
     contract_n(ps, y);
-    bg_color<NL, WID, NH>(F, y, dir, cs);
+    bg_color<NL, WID, NH, WT>(F, y, dir, col, cs);
     const float T = T_final[p];
 #pragma unroll
     for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * cs[k];
   }
 }
 
-template <int NL, int WID, int NH>
-__global__ void __launch_bounds__(128) k_bg_map_texels(FieldsDev F, int Hb, int Wb, float radius,
-                                                       float* __restrict__ map) {
+template <int NL, int WID, int NH, class WT>
+__global__ void __launch_bounds__(kFwdThreads) k_bg_map_texels(FieldsDev F, int Hb, int Wb, float radius,
+                                                               float* __restrict__ map) {
+  __shared__ float hid[WID * kFwdPitch];
+  float* col = hid + threadIdx.x;
   const int n = Hb * Wb;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     float y[3], dir[3], cs[3];
     texel_point(e / Wb, e % Wb, Hb, Wb, radius, y, dir);
-    bg_color<NL, WID, NH>(F, y, dir, cs);
+    bg_color<NL, WID, NH, WT>(F, y, dir, col, cs);
 #pragma unroll
     for (int k = 0; k < 3; ++k) map[3 * e + k] = cs[k];
   }
@@ -497,7 +508,7 @@ __global__ void __launch_bounds__(256) k_bg_map_bwd_pix(FieldsDev F, CamDev cam,
 // Reverse of the colour field at background points: MODE 0 = one point per
 // pixel (exact mode, also writes dL/dT_final and dL/dC_fg), MODE 1 = one
 // point per map texel with the texel gradient given in dmap.
-template <int NL, int WID, int NH, int MODE>
+template <int NL, int WID, int NH, int MODE, class WT>
 __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     FieldsDev F, CamDev cam, float radius, int Hb, int Wb, const float* __restrict__ T_final,
     const float* __restrict__ dC, float* __restrict__ dC_fg, float* __restrict__ dT,
@@ -526,7 +537,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     float x0[NC], out[3], dz3[3];
     encode<NL>(F.rad, y, x0);
     pos_enc(dir, x0 + NG);
-    decoder_fwd_store<NC, WID, NH, 3>(F.cm, x0, act, out);
+    decoder_fwd_store<NC, WID, NH, 3, WT>(F.cm, x0, act, out);
     float cs[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cs[k] = sigmoidf_(out[k]);
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
 #pragma unroll
     for (int k = 0; k < 3; ++k) dz3[k] = dcs[k] * loss_scale * cs[k] * (1.0f - cs[k]);
     float dx[NC];
-    decoder_bwd<NC, WID, NH, 3>(F.cm, act, dzb, dz3, slab, SL, 1, dx);
+    decoder_bwd<NC, WID, NH, 3, WT>(F.cm, act, dzb, dz3, slab, SL, 1, dx);
     if (ok) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
@@ -558,6 +569,30 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
 }
 
 // ---------------------------------------------------------------- host side
+
+static int fwd_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+int bwd_ctas();
+hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout& SL,
+                               const SlabTargets& T, float scale, cudaStream_t s);
+hyrf_status launch_bg_map_fwd(const FieldsDev& F, const CamDev& cam, float radius, int Hb, int Wb,
+                              const float* map, const float* C_fg, const float* T_final, float* C,
+                              cudaStream_t s);
+hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float radius, int Hb, int Wb,
+                                  const float* map, const float* T_final, const float* dC,
+                                  float* dC_fg, float* dT, float* dmap, cudaStream_t s);
+SlabTargets slab_targets(const hyrf_field_grads& g, bool geo);
+
+template <class K>
+static void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#if HYRF_FIELDS_PART == 0
 
 bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
   const hyrf_grid* gs[2] = {&f.geo, &f.rad};
@@ -629,50 +664,14 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
   return true;
 }
 
-// Shape dispatch: (levels, width, hidden layers) in {(8, 32, 1), (16, 64, 2)}.
-enum class Shape { S8_32_1, S16_64_2, NONE };
-
-static Shape shape_of(const hyrf_fields& f) {
-  const int L = f.rad.n_levels;
-  if (L == 8 && f.col_mlp.width == 32 && f.col_mlp.n_hidden == 1) return Shape::S8_32_1;
-  if (L == 16 && f.col_mlp.width == 64 && f.col_mlp.n_hidden == 2) return Shape::S16_64_2;
-  return Shape::NONE;
-}
-
-static int fwd_blocks(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  const int64_t cap = (int64_t)num_sms() * 16;
-  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
-
 int bwd_ctas() { return num_sms() * 3; }
-
-template <int NL, int WID, int NH>
-static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const QueryFwdIO& io,
-                                  cudaStream_t s) {
-  k_query_fwd<NL, WID, NH><<<fwd_blocks(io.n, 128), 128, 0, s>>>(F, cam, io);
-  HYRF_LAUNCH_CHECK();
-  return HYRF_OK;
-}
-
-hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s) {
-  QueryFwdIO io{a.n,      a.pos,   a.alpha_e, a.scale_e, a.color_e, a.vis_ids,
-                a.n_vis,  a.alpha, a.scale,   a.quat,    a.color,   a.status};
-  const CamDev cam = to_dev(a.cam);
-  if (a.n == 0) return HYRF_OK;
-  switch (shape_of(a.fields)) {
-    case Shape::S8_32_1: return query_fwd_impl<8, 32, 1>(F, cam, io, s);
-    case Shape::S16_64_2: return query_fwd_impl<16, 64, 2>(F, cam, io, s);
-    default: return HYRF_ERR_UNSUPPORTED;
-  }
-}
 
 size_t slab_bytes(const FieldsDev& F, bool geo) {
   SlabLayout SL = make_slab_layout(geo ? &F.gm : nullptr, &F.cm);
   return (size_t)bwd_ctas() * SL.total * sizeof(float);
 }
 
-static SlabTargets targets(const hyrf_field_grads& g, bool geo) {
+SlabTargets slab_targets(const hyrf_field_grads& g, bool geo) {
   SlabTargets T{};
   for (int l = 0; l < 3; ++l) {
     T.W[0][l] = geo ? g.geo_W[l] : nullptr;
@@ -683,40 +682,29 @@ static SlabTargets targets(const hyrf_field_grads& g, bool geo) {
   return T;
 }
 
-template <class K>
-static void set_smem(K kernel, size_t bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int NL, int WID, int NH>
-static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const QueryBwdIO& io,
-                                  const hyrf_field_grads& grads, float* slabs, cudaStream_t s) {
-  const SlabLayout SL = make_slab_layout(&F.gm, &F.cm);
-  const int ctas = bwd_ctas();
-  cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
-  const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
-  set_smem(k_query_bwd<NL, WID, NH>, smem);
-  k_query_bwd<NL, WID, NH><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs);
-  HYRF_LAUNCH_CHECK();
-  k_slab_reduce<<<64, 256, 0, s>>>(slabs, ctas, SL, targets(grads, true), 1.0f / io.loss_scale);
+hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout& SL,
+                               const SlabTargets& T, float scale, cudaStream_t s) {
+  k_slab_reduce<<<64, 256, 0, s>>>(slabs, nslabs, SL, T, scale);
   HYRF_LAUNCH_CHECK();
   return HYRF_OK;
 }
 
-hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F,
-                             void* ws, cudaStream_t s) {
-  QueryBwdIO io{a.n,        a.pos,       a.alpha_e,   a.scale_e,   a.color_e,
-                a.vis_ids,  a.n_vis,     a.d_alpha,   a.d_scale,   a.d_quat,
-                a.d_color,  a.d_pos,     a.d_alpha_e, a.d_scale_e, a.d_color_e,
-                a.grads.geo_table, a.grads.rad_table, a.loss_scale, a.status};
-  const CamDev cam = to_dev(a.cam);
-  if (a.n == 0) return HYRF_OK;
-  float* slabs = static_cast<float*>(ws);
-  switch (shape_of(a.fields)) {
-    case Shape::S8_32_1: return query_bwd_impl<8, 32, 1>(F, cam, io, a.grads, slabs, s);
-    case Shape::S16_64_2: return query_bwd_impl<16, 64, 2>(F, cam, io, a.grads, slabs, s);
-    default: return HYRF_ERR_UNSUPPORTED;
-  }
+hyrf_status launch_bg_map_fwd(const FieldsDev& F, const CamDev& cam, float radius, int Hb, int Wb,
+                              const float* map, const float* C_fg, const float* T_final, float* C,
+                              cudaStream_t s) {
+  k_bg_map_fwd<<<fwd_blocks((int64_t)cam.W * cam.H, 256), 256, 0, s>>>(F, cam, radius, Hb, Wb, map,
+                                                                      C_fg, T_final, C);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float radius, int Hb, int Wb,
+                                  const float* map, const float* T_final, const float* dC,
+                                  float* dC_fg, float* dT, float* dmap, cudaStream_t s) {
+  k_bg_map_bwd_pix<<<fwd_blocks((int64_t)cam.W * cam.H, 256), 256, 0, s>>>(F, cam, radius, Hb, Wb, map,
+                                                                          T_final, dC, dC_fg, dT, dmap);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
 }
 
 size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward) {
@@ -729,44 +717,141 @@ size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F,
   return c.size();
 }
 
-template <int NL, int WID, int NH>
+#define HYRF_DECLARE_PART(P)                                                                      \
+  hyrf_status query_fwd_p##P(const FieldsDev&, const CamDev&, const QueryFwdIO&, cudaStream_t);   \
+  hyrf_status query_bwd_p##P(const FieldsDev&, const CamDev&, const QueryBwdIO&,                  \
+                             const hyrf_field_grads&, float*, cudaStream_t);                      \
+  hyrf_status bg_fwd_p##P(const hyrf_composite_background_args&, const FieldsDev&, void*,          \
+                          cudaStream_t);                                                          \
+  hyrf_status bg_bwd_p##P(const hyrf_composite_background_backward_args&, const FieldsDev&, void*, \
+                          cudaStream_t);
+HYRF_DECLARE_PART(1)
+HYRF_DECLARE_PART(2)
+HYRF_DECLARE_PART(3)
+
+// Shape dispatch: (levels, width, hidden layers, weights) in
+// {(8, 32, 1, f32) = part 1, (16, 64, 2, f32) = part 2, (16, 64, 2, bf16) = part 3}.
+static int part_of(const hyrf_fields& f, const FieldsDev& F) {
+  const int L = f.rad.n_levels;
+  if (L == 8 && f.col_mlp.width == 32 && f.col_mlp.n_hidden == 1 && !F.cm.bf16) return 1;
+  if (L == 16 && f.col_mlp.width == 64 && f.col_mlp.n_hidden == 2) return F.cm.bf16 ? 3 : 2;
+  return 0;
+}
+
+hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s) {
+  QueryFwdIO io{a.n,      a.pos,   a.alpha_e, a.scale_e, a.color_e, a.vis_ids,
+                a.n_vis,  a.alpha, a.scale,   a.quat,    a.color,   a.status};
+  const CamDev cam = to_dev(a.cam);
+  if (a.n == 0) return HYRF_OK;
+  switch (part_of(a.fields, F)) {
+    case 1: return query_fwd_p1(F, cam, io, s);
+    case 2: return query_fwd_p2(F, cam, io, s);
+    case 3: return query_fwd_p3(F, cam, io, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F,
+                             void* ws, cudaStream_t s) {
+  QueryBwdIO io{a.n,        a.pos,       a.alpha_e,   a.scale_e,   a.color_e,
+                a.vis_ids,  a.n_vis,     a.d_alpha,   a.d_scale,   a.d_quat,
+                a.d_color,  a.d_pos,     a.d_alpha_e, a.d_scale_e, a.d_color_e,
+                a.grads.geo_table, a.grads.rad_table, a.loss_scale, a.status};
+  const CamDev cam = to_dev(a.cam);
+  if (a.n == 0) return HYRF_OK;
+  float* slabs = static_cast<float*>(ws);
+  switch (part_of(a.fields, F)) {
+    case 1: return query_bwd_p1(F, cam, io, a.grads, slabs, s);
+    case 2: return query_bwd_p2(F, cam, io, a.grads, slabs, s);
+    case 3: return query_bwd_p3(F, cam, io, a.grads, slabs, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+hyrf_status launch_bg_fwd(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
+                          cudaStream_t s) {
+  switch (part_of(a.fields, F)) {
+    case 1: return bg_fwd_p1(a, F, ws, s);
+    case 2: return bg_fwd_p2(a, F, ws, s);
+    case 3: return bg_fwd_p3(a, F, ws, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+hyrf_status launch_bg_bwd(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
+                          void* ws, cudaStream_t s) {
+  switch (part_of(b.fwd.fields, F)) {
+    case 1: return bg_bwd_p1(b, F, ws, s);
+    case 2: return bg_bwd_p2(b, F, ws, s);
+    case 3: return bg_bwd_p3(b, F, ws, s);
+    default: return HYRF_ERR_UNSUPPORTED;
+  }
+}
+
+#else  // parts 1-3: one shape each
+
+#if HYRF_FIELDS_PART == 1
+#define HYRF_SHAPE 8, 32, 1, float
+#elif HYRF_FIELDS_PART == 2
+#define HYRF_SHAPE 16, 64, 2, float
+#else
+#define HYRF_SHAPE 16, 64, 2, __nv_bfloat16
+#endif
+
+template <int NL, int WID, int NH, class WT>
+static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const QueryFwdIO& io,
+                                  cudaStream_t s) {
+  if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+    return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
+  } else {
+    k_query_fwd<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(F, cam, io);
+    HYRF_LAUNCH_CHECK();
+    return HYRF_OK;
+  }
+}
+
+template <int NL, int WID, int NH, class WT>
+static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const QueryBwdIO& io,
+                                  const hyrf_field_grads& grads, float* slabs, cudaStream_t s) {
+  const SlabLayout SL = make_slab_layout(&F.gm, &F.cm);
+  const int ctas = bwd_ctas();
+  cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
+  const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
+  set_smem(k_query_bwd<NL, WID, NH, WT>, smem);
+  k_query_bwd<NL, WID, NH, WT><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs);
+  HYRF_LAUNCH_CHECK();
+  return launch_slab_reduce(slabs, ctas, SL, slab_targets(grads, true), 1.0f / io.loss_scale, s);
+}
+
+template <int NL, int WID, int NH, class WT>
 static hyrf_status bg_fwd_impl(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
                                cudaStream_t s) {
   const CamDev cam = to_dev(a.cam);
   const int P = cam.W * cam.H;
   if (a.bg.mode == 0) {
-    k_bg_exact_fwd<NL, WID, NH><<<fwd_blocks(P, 128), 128, 0, s>>>(F, cam, a.bg.radius, a.C_fg,
-                                                                  a.T_final, a.C);
-    HYRF_LAUNCH_CHECK();
-  } else {
-    Carver c(ws);
-    float* map = c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);
-    const int nt = a.bg.map_h * a.bg.map_w;
-    k_bg_map_texels<NL, WID, NH><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, a.bg.map_h, a.bg.map_w,
-                                                                      a.bg.radius, map);
-    HYRF_LAUNCH_CHECK();
-    k_bg_map_fwd<<<fwd_blocks(P, 256), 256, 0, s>>>(F, cam, a.bg.radius, a.bg.map_h, a.bg.map_w, map,
-                                                      a.C_fg, a.T_final, a.C);
-    HYRF_LAUNCH_CHECK();
+    if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+      return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
+    } else {
+      k_bg_exact_fwd<NL, WID, NH, WT><<<fwd_blocks(P, kFwdThreads), kFwdThreads, 0, s>>>(
+          F, cam, a.bg.radius, a.C_fg, a.T_final, a.C);
+      HYRF_LAUNCH_CHECK();
+      return HYRF_OK;
+    }
   }
-  return HYRF_OK;
+  Carver c(ws);
+  float* map = c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);
+  const int nt = a.bg.map_h * a.bg.map_w;
+  k_bg_map_texels<NL, WID, NH, WT><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, a.bg.map_h, a.bg.map_w,
+                                                                        a.bg.radius, map);
+  HYRF_LAUNCH_CHECK();
+  return launch_bg_map_fwd(F, cam, a.bg.radius, a.bg.map_h, a.bg.map_w, map, a.C_fg, a.T_final, a.C, s);
 }
 
-hyrf_status launch_bg_fwd(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
-                          cudaStream_t s) {
-  switch (shape_of(a.fields)) {
-    case Shape::S8_32_1: return bg_fwd_impl<8, 32, 1>(a, F, ws, s);
-    case Shape::S16_64_2: return bg_fwd_impl<16, 64, 2>(a, F, ws, s);
-    default: return HYRF_ERR_UNSUPPORTED;
-  }
-}
-
-template <int NL, int WID, int NH>
+template <int NL, int WID, int NH, class WT>
 static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
                                void* ws, cudaStream_t s) {
   const hyrf_composite_background_args& a = b.fwd;
   const CamDev cam = to_dev(a.cam);
-  const int P = cam.W * cam.H;
   const SlabLayout SL = make_slab_layout(nullptr, &F.cm);
   const int ctas = bwd_ctas();
   Carver c(ws);
@@ -781,37 +866,50 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
   cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
   const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
   if (a.bg.mode == 0) {
-    set_smem(k_bg_field_bwd<NL, WID, NH, 0>, smem);
-    k_bg_field_bwd<NL, WID, NH, 0><<<ctas, kBwdThreads, smem, s>>>(
+    set_smem(k_bg_field_bwd<NL, WID, NH, 0, WT>, smem);
+    k_bg_field_bwd<NL, WID, NH, 0, WT><<<ctas, kBwdThreads, smem, s>>>(
         F, cam, a.bg.radius, 0, 0, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, nullptr,
         b.grads.rad_table, b.loss_scale, SL, slabs);
     HYRF_LAUNCH_CHECK();
   } else {
     const int nt = Hb * Wb;
-    k_bg_map_texels<NL, WID, NH><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, Hb, Wb, a.bg.radius, map);
+    k_bg_map_texels<NL, WID, NH, WT><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, Hb, Wb, a.bg.radius, map);
     HYRF_LAUNCH_CHECK();
     cudaMemsetAsync(dmap, 0, (size_t)nt * 3 * sizeof(float), s);
-    k_bg_map_bwd_pix<<<fwd_blocks(P, 256), 256, 0, s>>>(F, cam, a.bg.radius, Hb, Wb, map, a.T_final,
-                                                          b.d_C, b.d_C_fg, b.d_T_final, dmap);
-    HYRF_LAUNCH_CHECK();
-    set_smem(k_bg_field_bwd<NL, WID, NH, 1>, smem);
-    k_bg_field_bwd<NL, WID, NH, 1><<<ctas, kBwdThreads, smem, s>>>(
+    hyrf_status st = launch_bg_map_bwd_pix(F, cam, a.bg.radius, Hb, Wb, map, a.T_final, b.d_C,
+                                           b.d_C_fg, b.d_T_final, dmap, s);
+    if (st != HYRF_OK) return st;
+    set_smem(k_bg_field_bwd<NL, WID, NH, 1, WT>, smem);
+    k_bg_field_bwd<NL, WID, NH, 1, WT><<<ctas, kBwdThreads, smem, s>>>(
         F, cam, a.bg.radius, Hb, Wb, nullptr, nullptr, nullptr, nullptr, dmap, b.grads.rad_table,
         b.loss_scale, SL, slabs);
     HYRF_LAUNCH_CHECK();
   }
-  k_slab_reduce<<<64, 256, 0, s>>>(slabs, ctas, SL, targets(b.grads, false), 1.0f / b.loss_scale);
-  HYRF_LAUNCH_CHECK();
-  return HYRF_OK;
+  return launch_slab_reduce(slabs, ctas, SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
 }
 
-hyrf_status launch_bg_bwd(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
-                          void* ws, cudaStream_t s) {
-  switch (shape_of(b.fwd.fields)) {
-    case Shape::S8_32_1: return bg_bwd_impl<8, 32, 1>(b, F, ws, s);
-    case Shape::S16_64_2: return bg_bwd_impl<16, 64, 2>(b, F, ws, s);
-    default: return HYRF_ERR_UNSUPPORTED;
-  }
+#define HYRF_PASTE2(a, b) a##b
+#define HYRF_PASTE(a, b) HYRF_PASTE2(a, b)
+
+hyrf_status HYRF_PASTE(query_fwd_p, HYRF_FIELDS_PART)(const FieldsDev& F, const CamDev& cam,
+                                                      const QueryFwdIO& io, cudaStream_t s) {
+  return query_fwd_impl<HYRF_SHAPE>(F, cam, io, s);
 }
+hyrf_status HYRF_PASTE(query_bwd_p, HYRF_FIELDS_PART)(const FieldsDev& F, const CamDev& cam,
+                                                      const QueryBwdIO& io,
+                                                      const hyrf_field_grads& g, float* slabs,
+                                                      cudaStream_t s) {
+  return query_bwd_impl<HYRF_SHAPE>(F, cam, io, g, slabs, s);
+}
+hyrf_status HYRF_PASTE(bg_fwd_p, HYRF_FIELDS_PART)(const hyrf_composite_background_args& a,
+                                                   const FieldsDev& F, void* ws, cudaStream_t s) {
+  return bg_fwd_impl<HYRF_SHAPE>(a, F, ws, s);
+}
+hyrf_status HYRF_PASTE(bg_bwd_p, HYRF_FIELDS_PART)(const hyrf_composite_background_backward_args& b,
+                                                   const FieldsDev& F, void* ws, cudaStream_t s) {
+  return bg_bwd_impl<HYRF_SHAPE>(b, F, ws, s);
+}
+
+#endif  // HYRF_FIELDS_PART
 
 }  // namespace hyrf

@@ -1,0 +1,498 @@
+// BF16 field query and background forward with the decoders (Eqs. 4, 6) on
+// the 5th-generation tensor cores. A CTA owns a tile of 128 points (the MMA
+// M dimension): every thread gathers one point's hash features (Eq. 3),
+// converts them to bf16 and writes its row of the A operand into shared
+// memory; one thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32) per
+// layer with the weights staged once per CTA as the B operand; the f32
+// accumulators live in tensor memory and come back with tcgen05.ld for the
+// bias + ReLU epilogue, which writes the next layer's bf16 A operand.
+//
+// Shared-memory operands use the no-swizzle K-major core-matrix layout: an
+// 8-row x 16-byte core matrix is 128 contiguous bytes; core matrices
+// adjacent along K are 128 bytes apart (leading byte offset) and 8-row
+// groups are K/8 * 128 bytes apart (stride byte offset).
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records
+// HYRF_ERR_TIMEOUT in the status word, waits (bounded) for its MMAs, frees
+// its tensor memory and returns.
+#include "field_ops.cuh"
+
+namespace hyrf {
+namespace tc {
+
+constexpr uint32_t kSpin = 1u << 24;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__host__ __device__ constexpr uint32_t kmaj(int r, int k, int K) {
+  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128.
+template <int N>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+  static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar)));
+}
+
+__device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(phase));
+  return ok != 0;
+}
+
+// Bounded wait on the given phase; returns false (on every thread) if any
+// thread of the CTA gave up.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase) {
+  bool ok = false;
+  for (uint32_t it = 0; it < kSpin && !ok; ++it) ok = try_wait(bar, phase);
+  return !__syncthreads_or(!ok);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_smem_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive f32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// D[128 x N] (+)= A[128 x K] B[N x K]^T with both operands K-major in smem.
+template <int N, int K>
+__device__ __forceinline__ void gemm(uint32_t d, const uint8_t* A, const uint8_t* B) {
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint64_t da = sdesc(saddr(A) + ks * 256, 128, (K / 8) * 128);
+    const uint64_t db = sdesc(saddr(B) + ks * 256, 128, (K / 8) * 128);
+    mma(d, da, db, idesc<N>(), ks > 0 ? 1u : 0u);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Row r of a K-major bf16 tile from 8*n floats.
+template <int K>
+__device__ __forceinline__ void store_row(uint8_t* tile, int r, const float* v) {
+#pragma unroll
+  for (int kc = 0; kc < K / 8; ++kc) {
+    uint4 u;
+    u.x = pack2(v[8 * kc], v[8 * kc + 1]);
+    u.y = pack2(v[8 * kc + 2], v[8 * kc + 3]);
+    u.z = pack2(v[8 * kc + 4], v[8 * kc + 5]);
+    u.w = pack2(v[8 * kc + 6], v[8 * kc + 7]);
+    *reinterpret_cast<uint4*>(tile + kmaj(r, 8 * kc, K)) = u;
+  }
+}
+
+// Weights W [rows][K] bf16 (row-major, rows_real valid rows) into a K-major
+// tile of N rows (rows >= rows_real zero).
+template <int N, int K>
+__device__ __forceinline__ void stage_w(uint8_t* tile, const void* W, int rows_real) {
+  const uint4* src = static_cast<const uint4*>(W);
+  for (int e = threadIdx.x; e < N * (K / 8); e += blockDim.x) {
+    const int r = e / (K / 8), kc = e % (K / 8);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (r < rows_real) v = __ldg(src + r * (K / 8) + kc);
+    *reinterpret_cast<uint4*>(tile + kmaj(r, 8 * kc, K)) = v;
+  }
+}
+
+// ReLU(D + b) of this thread's 64 accumulator columns -> its row of H.
+__device__ __forceinline__ void epilogue_relu64(uint32_t taddr, const float* b, uint8_t* H, int r) {
+#pragma unroll
+  for (int c0 = 0; c0 < 64; c0 += 16) {
+    float v[16];
+    ld16(taddr + c0, v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b[c0 + j], 0.0f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint4 u;
+      u.x = pack2(v[8 * h], v[8 * h + 1]);
+      u.y = pack2(v[8 * h + 2], v[8 * h + 3]);
+      u.z = pack2(v[8 * h + 4], v[8 * h + 5]);
+      u.w = pack2(v[8 * h + 6], v[8 * h + 7]);
+      *reinterpret_cast<uint4*>(H + kmaj(r, c0 + 8 * h, 64)) = u;
+    }
+  }
+}
+
+__device__ __forceinline__ void cam_center(const CamDev& c, float pc[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
+}
+
+// ---------------------------------------------------------------- field query
+
+struct QueryIO {
+  int n;
+  const float* pos;
+  const float* alpha_e;
+  const float* scale_e;
+  const float* color_e;
+  const int32_t* vis_ids;
+  const int32_t* n_vis;
+  float* alpha;
+  float* scale;
+  float* quat;
+  float* color;
+  int32_t* status;
+};
+
+// smem byte offsets
+constexpr int oW0g = 0, oW1g = oW0g + 64 * 32 * 2, oW2g = oW1g + 64 * 64 * 2, oW0c = oW2g + 16 * 64 * 2,
+              oW1c = oW0c + 64 * 64 * 2, oW2c = oW1c + 64 * 64 * 2, oAg = oW2c + 16 * 64 * 2,
+              oAc = oAg + 128 * 32 * 2, oHg = oAc + 128 * 64 * 2, oHc = oHg + 128 * 64 * 2,
+              oBias = oHc + 128 * 64 * 2, kQuerySmem = oBias + 288 * 4;
+constexpr uint32_t kQueryTmemCols = 256;
+
+__global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam, QueryIO io) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x, w = t >> 5, r = t & 127;
+  const bool geo = t < 128;
+  float* bias = reinterpret_cast<float*>(sm + oBias);
+  float *b0g = bias, *b1g = bias + 64, *b2g = bias + 128, *b0c = bias + 144, *b1c = bias + 208,
+        *b2c = bias + 272;
+  stage_w<64, 32>(sm + oW0g, F.gm.W[0], 64);
+  stage_w<64, 64>(sm + oW1g, F.gm.W[1], 64);
+  stage_w<16, 64>(sm + oW2g, F.gm.W[2], 8);
+  stage_w<64, 64>(sm + oW0c, F.cm.W[0], 64);
+  stage_w<64, 64>(sm + oW1c, F.cm.W[1], 64);
+  stage_w<16, 64>(sm + oW2c, F.cm.W[2], 3);
+  if (t < 64) {
+    b0g[t] = F.gm.b[0][t];
+    b1g[t] = F.gm.b[1][t];
+    b0c[t] = F.cm.b[0][t];
+    b1c[t] = F.cm.b[1][t];
+  }
+  if (t < 16) {
+    b2g[t] = t < 8 ? F.gm.b[2][t] : 0.0f;
+    b2c[t] = t < 3 ? F.cm.b[2][t] : 0.0f;
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(kQueryTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_smem_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tm = tmem_base;
+  const uint32_t lane = ((uint32_t)((w & 3) * 32)) << 16;
+  const uint32_t colD = geo ? 0u : 64u, colO = geo ? 128u : 144u;
+  uint8_t* Hs = sm + (geo ? oHg : oHc);
+  const float* b0 = geo ? b0g : b0c;
+  const float* b1 = geo ? b1g : b1c;
+  const float* b2 = geo ? b2g : b2c;
+  float pc[3];
+  cam_center(cam, pc);
+  const int nv = min(*io.n_vis, io.n);
+  const int ntile = (nv + 127) / 128;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const int i = tile * 128 + r;
+    bool ok = i < nv;
+    int g = ok ? io.vis_ids[i] : 0;
+    if (ok && (g < 0 || g >= io.n)) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      ok = false;
+    }
+    float p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];
+    float y[3];
+    contract_p(F, p, y, nullptr);
+    {
+      float f[64];
+      if (geo) {
+        encode<16>(F.geo, y, f);
+        store_row<32>(sm + oAg, r, f);
+      } else {
+        encode<16>(F.rad, y, f);
+        float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+        const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+        pos_enc(dir, f + 32);
+        store_row<64>(sm + oAc, r, f);
+      }
+    }
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      gemm<64, 32>(tm + 0, sm + oAg, sm + oW0g);
+      gemm<64, 64>(tm + 64, sm + oAc, sm + oW0c);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    epilogue_relu64(tm + lane + colD, b0, Hs, r);
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      gemm<64, 64>(tm + 0, sm + oHg, sm + oW1g);
+      gemm<64, 64>(tm + 64, sm + oHc, sm + oW1c);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    epilogue_relu64(tm + lane + colD, b1, Hs, r);
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      gemm<16, 64>(tm + 128, sm + oHg, sm + oW2g);
+      gemm<16, 64>(tm + 144, sm + oHc, sm + oW2c);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    float o[16];
+    ld16(tm + lane + colO, o);
+    if (ok) {
+      if (geo) {
+        // Eq. 7: alpha, scale from the geometry decoder, rotation normalised
+        io.alpha[i] = sigmoidf_(o[0] + b2[0] + io.alpha_e[g]);
+        const float se = io.scale_e[g];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(o[1 + k] + b2[1 + k] + se);
+        float q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = o[4 + k] + b2[4 + k];
+        const float rn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float den = fmaxf(rn, 1e-12f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = q[k] / den;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          io.color[3 * i + k] = sigmoidf_(o[k] + b2[k] + io.color_e[3 * (int64_t)g + k]);
+      }
+    }
+    fence_before();
+  }
+  if (failed) {
+    set_status(io.status, HYRF_ERR_TIMEOUT);
+    for (uint32_t it = 0; it < kSpin; ++it)
+      if (try_wait(&bar, phase)) break;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kQueryTmemCols));
+}
+
+// ---------------------------------------------------------------- background, exact mode
+
+constexpr int bW0c = 0, bW1c = bW0c + 64 * 64 * 2, bW2c = bW1c + 64 * 64 * 2, bAc = bW2c + 16 * 64 * 2,
+              bHc = bAc + 128 * 64 * 2, bBias = bHc + 128 * 64 * 2, kBgSmem = bBias + 144 * 4;
+constexpr uint32_t kBgTmemCols = 128;
+
+__device__ __forceinline__ void bg_ray(const CamDev& c, const FieldsDev& F, float radius, int i, int j,
+                                       float ps[3], float dirw[3]) {
+  float oc[3];
+  cam_center(c, oc);
+  const float dc[3] = {((float)i + 0.5f - c.cx) / c.fx, ((float)j + 0.5f - c.cy) / c.fy, 1.0f};
+  float on[3], dn[3], dw[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dw[k] = c.R[k] * dc[0] + c.R[3 + k] * dc[1] + c.R[6 + k] * dc[2];
+    on[k] = (oc[k] - F.lo[k]) * F.sx[k] - 1.0f;
+    dn[k] = dw[k] * F.sx[k];
+  }
+  const float A = dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2];
+  const float B = 2.0f * (on[0] * dn[0] + on[1] * dn[1] + on[2] * dn[2]);
+  const float C = on[0] * on[0] + on[1] * on[1] + on[2] * on[2] - radius * radius;
+  const float tt = (-B + sqrtf(B * B - 4.0f * A * C)) / (2.0f * A);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ps[k] = on[k] + tt * dn[k];
+  const float nd = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dirw[k] = dw[k] / nd;
+}
+
+__global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
+                                                           const float* __restrict__ C_fg,
+                                                           const float* __restrict__ T_final,
+                                                           float* __restrict__ C, int32_t* status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x, w = t >> 5;
+  float* bias = reinterpret_cast<float*>(sm + bBias);
+  float *b0 = bias, *b1 = bias + 64, *b2 = bias + 128;
+  stage_w<64, 64>(sm + bW0c, F.cm.W[0], 64);
+  stage_w<64, 64>(sm + bW1c, F.cm.W[1], 64);
+  stage_w<16, 64>(sm + bW2c, F.cm.W[2], 3);
+  if (t < 64) {
+    b0[t] = F.cm.b[0][t];
+    b1[t] = F.cm.b[1][t];
+  }
+  if (t < 16) b2[t] = t < 3 ? F.cm.b[2][t] : 0.0f;
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(kBgTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_smem_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tm = tmem_base;
+  const uint32_t lane = ((uint32_t)(w * 32)) << 16;
+  const int P = cam.W * cam.H;
+  const int ntile = (P + 127) / 128;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const int p = tile * 128 + t;
+    const bool ok = p < P;
+    const int pp = ok ? p : 0;
+    {
+      float ps[3], dir[3], y[3], f[64];
+      bg_ray(cam, F, radius, pp % cam.W, pp / cam.W, ps, dir);
+      contract_n(ps, y);
+      encode<16>(F.rad, y, f);
+      pos_enc(dir, f + 32);
+      store_row<64>(sm + bAc, t, f);
+    }
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      gemm<64, 64>(tm, sm + bAc, sm + bW0c);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    epilogue_relu64(tm + lane, b0, sm + bHc, t);
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      gemm<64, 64>(tm, sm + bHc, sm + bW1c);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    epilogue_relu64(tm + lane, b1, sm + bHc, t);
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      gemm<16, 64>(tm + 64, sm + bHc, sm + bW2c);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    float o[16];
+    ld16(tm + lane + 64, o);
+    if (ok) {
+      const float T = T_final[p];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * sigmoidf_(o[k] + b2[k]);
+    }
+    fence_before();
+  }
+  if (failed) {
+    set_status(status, HYRF_ERR_TIMEOUT);
+    for (uint32_t it = 0; it < kSpin; ++it)
+      if (try_wait(&bar, phase)) break;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kBgTmemCols));
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- launchers
+
+hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s) {
+  tc::QueryIO io{a.n,     a.pos,   a.alpha_e, a.scale_e, a.color_e, a.vis_ids,
+                 a.n_vis, a.alpha, a.scale,   a.quat,    a.color,   a.status};
+  if (a.n == 0) return HYRF_OK;
+  cudaFuncSetAttribute(tc::k_query_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kQuerySmem);
+  int tiles = (a.n + 127) / 128;
+  int grid = num_sms() * 2;
+  if (tiles < grid) grid = tiles;
+  tc::k_query_fwd_tc<<<grid, 256, tc::kQuerySmem, s>>>(F, to_dev(a.cam), io);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F,
+                                   cudaStream_t s) {
+  const CamDev cam = to_dev(a.cam);
+  cudaFuncSetAttribute(tc::k_bg_exact_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kBgSmem);
+  const int P = cam.W * cam.H;
+  int tiles = (P + 127) / 128;
+  int grid = num_sms() * 4;
+  if (tiles < grid) grid = tiles;
+  tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, a.C_fg, a.T_final, a.C,
+                                                       a.status);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+}  // namespace hyrf

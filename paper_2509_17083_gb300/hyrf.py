@@ -18,6 +18,7 @@ HYRF_ERR_UNSUPPORTED = 2
 HYRF_ERR_CUDA = 4
 HYRF_ERR_OVERFLOW = 8
 HYRF_ERR_BOUNDS = 16
+HYRF_ERR_TIMEOUT = 32
 HYRF_F32 = 0
 HYRF_BF16 = 1
 TILE = 16

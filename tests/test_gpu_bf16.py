@@ -1,0 +1,91 @@
+"""BF16-field path (bf16 hash tables and decoder weights, tcgen05 decoders in
+the forward, FP32 accumulation and compositing, loss scale 1024) against the
+FP64 oracle evaluated on the same bf16 parameter values.
+
+Tolerances: image 2e-3 absolute, gradients 2e-2 relative L2, and the PSNR
+against the target within 0.05 dB of the FP32 path's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_17083_gb300 import hyrf as H
+from paper_2509_17083_gb300 import synth
+from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer
+from tests.gpu_util import TOL_GRAD_BF16, TOL_IMG_BF16, cuda_f32, np_, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _workload(prec, init=1e-4, n=30000, W=301, H_=203):
+    return synth.config3(n=n, width=W, height=H_, log2_T=15, n_clusters=32, precision=prec,
+                         table_init=init)
+
+
+def _render(w, mask=None, backward=True):
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+    tgt = cuda_f32(w.targets[0])
+    r.fit_capacity(tgt)
+    m.zero_grad()
+    r.status.zero_()
+    r.forward(tgt)
+    if backward:
+        if mask is not None:
+            r.dC.mul_(cuda_f32(mask)[..., None])
+        r.backward()
+    torch.cuda.synchronize()
+    return m, r
+
+
+def test_query_fields_tensor_cores_match_oracle():
+    w = _workload("bf16", init=0.3)
+    m, r = _render(w, backward=False)
+    assert H.read_status(r.status) == 0
+    g = w.gaussians
+    ids = np.nonzero(oracle.precull_f32(g.pos, w.cams[0]))[0]
+    a, s, q, c = oracle.query_fields(g.pos[ids].astype(np.float64), g.alpha_e[ids], g.scale_e[ids],
+                                     g.color_e[ids], w.cams[0], w.fields)
+    nv = len(ids)
+    assert int(r.n_vis.item()) == nv
+    # bf16 operands: hidden activations rounded to 8 significant bits per layer
+    for gpu, ref, tol in [(r.alpha, a, 5e-3), (r.scale, s, 5e-3), (r.quat, q, 2e-2), (r.color, c, 5e-3)]:
+        err = np.abs(np_(gpu)[:nv] - ref)
+        assert err.max() < tol, err.max()
+        assert err.mean() < tol / 10, err.mean()
+
+
+@pytest.mark.parametrize("init", [1e-4, 0.3])
+def test_bf16_iteration_matches_oracle(init):
+    w = _workload("bf16", init=init)
+    fw = oracle.render(w.gaussians, w.fields, w.cams[0], w.bg)
+    mask = oracle.decision_safe_mask(fw, w.cams[0])
+    m, r = _render(w, mask.astype(np.float32))
+    assert H.read_status(r.status) == 0
+    L, fw, grads, _ = oracle.loss_and_grads(w.gaussians, w.fields, w.cams[0], w.bg, w.targets[0],
+                                            w.ssim_lambda, dC_mask=mask)
+    err = np.abs(np_(r.C) - fw["C"]).max(-1)
+    assert err[mask].max() < TOL_IMG_BF16, err[mask].max()
+    g = m.grad
+    for key in ("pos", "alpha_e", "scale_e", "color_e", "geo_table", "rad_table"):
+        e = rel_l2(np_(g[key]), grads[key])
+        assert e < TOL_GRAD_BF16, (key, e)
+    for key in ("geo_W", "col_W", "geo_b", "col_b"):
+        for l in range(3):
+            e = rel_l2(np_(g[key][l]), grads[key][l])
+            assert e < TOL_GRAD_BF16, (key, l, e)
+
+
+def test_bf16_psnr_within_005_db_of_fp32():
+    def psnr(img, tgt):
+        mse = float(np.mean((np.clip(img, 0, 1) - tgt) ** 2))
+        return -10.0 * np.log10(mse)
+    wb = _workload("bf16", init=0.3)
+    wf = _workload("f32", init=0.3)
+    _, rb = _render(wb, backward=False)
+    _, rf = _render(wf, backward=False)
+    # the same scene: the bf16 workload is the f32 one with tables/weights rounded
+    pb = psnr(np_(rb.C), wb.targets[0])
+    pf = psnr(np_(rf.C), wf.targets[0])
+    assert abs(pb - pf) <= 0.05, (pb, pf)
