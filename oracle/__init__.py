@@ -259,6 +259,41 @@ def query_fields_backward(pos, alpha_e, scale_e, color_e, cam, fields, d_alpha, 
     return g
 
 
+def decoder_margins(pos, cam, fields):
+    """Smallest relative ReLU margin of each point's geometry and colour
+    decoders: (margin_geo [n], margin_col [n])."""
+    n = len(pos)
+    keep = _Keep()
+    fl = fields_struct(fields, keep)
+    c = camera(cam)
+    mg, mc = np.zeros(n), np.zeros(n)
+    rc = lib().orc_decoder_margins(n, keep.d(pos), C.byref(c), C.byref(fl), _ptr(mg, _f64p),
+                                   _ptr(mc, _f64p))
+    assert rc == 0
+    return mg, mc
+
+
+def bg_margins(cam, fields, bg):
+    """Per pixel, the smallest relative ReLU margin of the background's
+    colour-decoder evaluations."""
+    keep = _Keep()
+    fl = fields_struct(fields, keep)
+    c = camera(cam)
+    b = _bg(bg)
+    out = np.zeros((cam.height, cam.width))
+    rc = lib().orc_bg_margins(C.byref(c), C.byref(fl), C.byref(b), _ptr(out, _f64p))
+    assert rc == 0
+    return out
+
+
+def relu_safe_mask(g, fields, cam, vis_ids, geo_margin, col_margin):
+    """Per visible Gaussian: 1 if no ReLU pre-activation of its decoders lies
+    within the given relative margins of the kink, else 0."""
+    pos = np.asarray(g.pos, np.float64)[vis_ids]
+    mg, mc = decoder_margins(pos, cam, fields)
+    return ((mg > geo_margin) & (mc > col_margin)).astype(np.float64)
+
+
 def project(pos, scale, quat, cam):
     """EWA projection (3DGS conventions): mean2d [n,2], conic [n,3], depth [n] (FP64)."""
     n = len(pos)
@@ -450,10 +485,12 @@ def render(g, fields, cam, bg, tile=TILE):
                 T_final=T_final, n_contrib=n_contrib, margin=margin, C=C_img, c_s=c_s)
 
 
-def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE, dC_mask=None):
+def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE, dC_mask=None, query_mask=None):
     """Forward, Eq. 12 loss and the analytic reverse pass of every stage.
     Returns (loss, forward dict, gradient dict over all parameters).
-    dC_mask (optional [H,W]) multiplies dL/dC before the reverse pass."""
+    dC_mask (optional [H,W]) multiplies dL/dC before the reverse pass;
+    query_mask (optional, one entry per visible Gaussian) multiplies the
+    gradients entering the field-query reverse pass."""
     fw = render(g, fields, cam, bg, tile)
     L, dC = loss(fw["C"], target, lam)
     if dC_mask is not None:
@@ -466,6 +503,10 @@ def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE, dC_mask=None):
     pos = np.asarray(g.pos, dtype=np.float64)[ids]
     d_pos_p, d_scale, d_quat = project_backward(pos, fw["scale"], fw["quat"], cam, d_mean2d,
                                                 d_conic)
+    if query_mask is not None:
+        qm = np.asarray(query_mask, np.float64)
+        d_op, d_col = d_op * qm, d_col * qm[:, None]
+        d_scale, d_quat = d_scale * qm[:, None], d_quat * qm[:, None]
     gq = query_fields_backward(pos, np.asarray(g.alpha_e)[ids], np.asarray(g.scale_e)[ids],
                                np.asarray(g.color_e)[ids], cam, fields, d_op, d_scale, d_quat,
                                d_col)
@@ -487,30 +528,45 @@ def loss_and_grads(g, fields, cam, bg, target, lam, tile=TILE, dC_mask=None):
     return L, fw, grads, inter
 
 
-def decision_safe_mask(fw, cam, tile=TILE, comp_margin=1e-4, rect_margin_px=1e-2):
+def decision_safe_mask(fw, cam, tile=TILE, comp_margin=1e-4, rel_radius=1e-5, center_px=1e-4,
+                       fields=None, bg=None, bg_relu_margin=0.0):
     """Pixels of a rendered view (the dict `render` returns) whose value is a
     smooth function of the inputs near this point: no compositing threshold
     test within `comp_margin` (relative) of its threshold, and not in a tile
-    that a Gaussian's rectangle could gain or lose because 3 sqrt(lambda_max)
-    or a rectangle edge lies within `rect_margin_px` of an integer boundary."""
+    whose membership in a Gaussian's rectangle changes when 3 sqrt(lambda_max)
+    moves by `rel_radius` (relative) or the centre by `center_px` pixels;
+    with `bg_relu_margin` > 0, also not a pixel whose background decoder has a
+    hidden pre-activation within that relative margin of the ReLU kink."""
     safe = fw["margin"] > comp_margin
+    if bg_relu_margin > 0.0:
+        safe &= bg_margins(cam, fields, bg) > bg_relu_margin
     con = np.asarray(fw["conic"])
     det = con[:, 0] * con[:, 2] - con[:, 1] ** 2
     sa, sb, sc = con[:, 2] / det, -con[:, 1] / det, con[:, 0] / det
     mid = 0.5 * (sa + sc)
     lam = mid + np.sqrt(np.maximum(mid * mid - (sa * sc - sb * sb), 0.0))
     r3 = 3.0 * np.sqrt(lam)
-    rad = np.ceil(r3)
     m = np.asarray(fw["mean2d"])
-    dist = np.abs(r3 - np.round(r3))
-    for e in ((m[:, 0] - rad) / tile, (m[:, 0] + rad) / tile, (m[:, 1] - rad) / tile,
-              (m[:, 1] + rad) / tile):
-        dist = np.minimum(dist, np.abs(e - np.round(e)) * tile)
     TX, TY = tiles_of(cam.width, cam.height, tile)
+    lo, hi = None, None
+    for dr in (-rel_radius, rel_radius):
+        rad = np.ceil(r3 * (1.0 + dr))
+        for du in (-center_px, center_px):
+            x0 = np.clip(np.floor((m[:, 0] + du - rad) / tile), 0, TX)
+            x1 = np.clip(np.floor((m[:, 0] + du + rad) / tile) + 1, 0, TX)
+            y0 = np.clip(np.floor((m[:, 1] + du - rad) / tile), 0, TY)
+            y1 = np.clip(np.floor((m[:, 1] + du + rad) / tile) + 1, 0, TY)
+            r = np.stack([x0, y0, x1, y1], 1)
+            lo = r if lo is None else np.minimum(lo, r)
+            hi = r if hi is None else np.maximum(hi, r)
     bad = np.zeros((TY, TX), bool)
-    for i in np.nonzero(dist < rect_margin_px)[0]:
-        x0, y0, x1, y1 = fw["rect"][i]
-        bad[max(0, y0 - 1):min(TY, y1 + 1), max(0, x0 - 1):min(TX, x1 + 1)] = True
+    for i in np.nonzero((lo != hi).any(1))[0]:
+        ox0, oy0, ox1, oy1 = int(lo[i, 0]), int(lo[i, 1]), int(hi[i, 2]), int(hi[i, 3])
+        ix0, iy0, ix1, iy1 = int(hi[i, 0]), int(hi[i, 1]), int(lo[i, 2]), int(lo[i, 3])
+        outer = np.zeros((TY, TX), bool)
+        outer[oy0:oy1, ox0:ox1] = True
+        outer[iy0:max(iy0, iy1), ix0:max(ix0, ix1)] = False
+        bad |= outer
     tile_bad = np.kron(bad, np.ones((tile, tile), bool))[:cam.height, :cam.width]
     return safe & ~tile_bad
 

@@ -133,6 +133,13 @@ int32_t orc_query_fields_backward(int32_t n, const double* pos, const double* al
                                   double* d_color_e, double* d_geo_table, double* d_rad_table,
                                   const orc_mlp_grad* d_geo_mlp, const orc_mlp_grad* d_col_mlp);
 
+/* Smallest relative ReLU margin of each point's decoders: over every hidden
+ * unit, min |z| / (sum_i |W_i x_i| + |b|), where z is the pre-activation (a
+ * diagnostic used to find points whose ReLU decisions a lower-precision
+ * evaluation could flip). margin_geo[n], margin_col[n]. */
+int32_t orc_decoder_margins(int32_t n, const double* pos, const orc_camera* cam,
+                            const orc_fields* fl, double* margin_geo, double* margin_col);
+
 /* ---------------- stage 3: projection (EWA, 3DGS conventions) ----------- */
 /* FP64: mean2d[n][2], conic[n][3] (a, b, c of the inverse 2D covariance),
  * depth[n]. */
@@ -201,6 +208,12 @@ int32_t orc_background_backward(const orc_camera* cam, const orc_fields* fl,
                                 const orc_bg* bg, const double* T_final, const double* d_C,
                                 double* d_C_fg, double* d_T_final, double* d_rad_table,
                                 const orc_mlp_grad* d_col_mlp);
+
+/* Smallest relative ReLU margin of the colour decoder evaluated for each
+ * pixel's background (exact mode: at its sphere hit; map mode: the four
+ * texels it samples). margin[H][W]. Diagnostic, like orc_decoder_margins. */
+int32_t orc_bg_margins(const orc_camera* cam, const orc_fields* fl, const orc_bg* bg,
+                       double* margin);
 
 /* ---------------- stage 7: loss (Eq. 12) -------------------------------- */
 /* L = (1 - lambda) * mean|C - target| + lambda * (1 - SSIM(C, target)).

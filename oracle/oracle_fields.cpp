@@ -134,6 +134,28 @@ static void layer_dims(const orc_mlp& m, int l, int& n_out, int& n_in) {
   n_out = (l == m.n_hidden) ? m.n_out : m.width;
 }
 
+// Smallest relative margin of the hidden pre-activations of one decoder.
+static double mlp_margin(const orc_mlp& m, const double* x) {
+  std::vector<double> a(x, x + m.n_in), next;
+  double mg = 1e300;
+  for (int l = 0; l < m.n_hidden; ++l) {
+    int no, ni;
+    layer_dims(m, l, no, ni);
+    next.assign(no, 0.0);
+    for (int o = 0; o < no; ++o) {
+      double z = m.b[l][o], mag = std::fabs(m.b[l][o]);
+      for (int i = 0; i < ni; ++i) {
+        z += m.W[l][(size_t)o * ni + i] * a[i];
+        mag += std::fabs(m.W[l][(size_t)o * ni + i] * a[i]);
+      }
+      if (mag > 0.0) mg = std::min(mg, std::fabs(z) / mag);
+      next[o] = z > 0.0 ? z : 0.0;
+    }
+    a.swap(next);
+  }
+  return mg;
+}
+
 // Forward keeping every layer input (acts[l]) and pre-activation (pre[l]).
 void mlp_forward_acts(const orc_mlp& m, const double* x, std::vector<std::vector<double>>& acts,
                       std::vector<std::vector<double>>& pre, double* y) {
@@ -244,6 +266,13 @@ void bg_color(const orc_fields& fl, const double y[3], const double dir[3], doub
   for (int k = 0; k < 3; ++k) c[k] = sigmoid(cn[k]);
 }
 
+double bg_margin(const orc_fields& fl, const double y[3], const double dir[3]) {
+  std::vector<double> f(fl.rad.n_levels * fl.rad.n_feat), in;
+  hash_encode(fl.rad, y, f.data());
+  color_input(fl, f.data(), dir, in);
+  return mlp_margin(fl.col_mlp, in.data());
+}
+
 void bg_color_backward(const orc_fields& fl, const double y[3], const double dir[3],
                        const double dc[3], double* d_rad_table, const orc_mlp_grad* d_col) {
   std::vector<double> f(fl.rad.n_levels * fl.rad.n_feat), in;
@@ -290,6 +319,28 @@ static bool fields_ok(const orc_fields* fl) {
   if (fl->pe_pad < 3 + 6 * fl->pe_freq) return false;
   if (fl->col_mlp.n_in != nr + fl->pe_pad || fl->col_mlp.n_out != 3) return false;
   return true;
+}
+
+int32_t orc_decoder_margins(int32_t n, const double* pos, const orc_camera* cam,
+                            const orc_fields* fl, double* margin_geo, double* margin_col) {
+  if (!fields_ok(fl) || n < 0) return -1;
+  double pc[3];
+  camera_center(*cam, pc);
+  std::vector<double> fg(fl->geo.n_levels * fl->geo.n_feat), fr(fl->rad.n_levels * fl->rad.n_feat), in;
+  for (int i = 0; i < n; ++i) {
+    const double* p = pos + 3 * i;
+    double y[3];
+    contract_point(fl->box, p, y, nullptr);
+    hash_encode(fl->geo, y, fg.data());
+    hash_encode(fl->rad, y, fr.data());
+    double v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+    double nv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double dir[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
+    color_input(*fl, fr.data(), dir, in);
+    margin_geo[i] = mlp_margin(fl->geo_mlp, fg.data());
+    margin_col[i] = mlp_margin(fl->col_mlp, in.data());
+  }
+  return 0;
 }
 
 // Eqs. 3-7 for n visible Gaussians.

@@ -19,6 +19,7 @@ void mlp_backward(const orc_mlp& m, const double* x, const double* dy, const orc
 void pos_enc(const double d[3], int n_freq, double* out);
 void camera_center(const orc_camera& cam, double c[3]);
 void bg_color(const orc_fields& fl, const double y[3], const double dir[3], double c[3]);
+double bg_margin(const orc_fields& fl, const double y[3], const double dir[3]);
 void bg_color_backward(const orc_fields& fl, const double y[3], const double dir[3],
                        const double dc[3], double* d_rad_table, const orc_mlp_grad* d_col);
 }  // namespace orc

@@ -724,6 +724,36 @@ int32_t orc_background_backward(const orc_camera* cam, const orc_fields* fl, con
   return 0;
 }
 
+int32_t orc_bg_margins(const orc_camera* cam, const orc_fields* fl, const orc_bg* bg,
+                       double* margin) {
+  if (!bg_ok(cam, fl, bg)) return -1;
+  const int W = cam->width, H = cam->height;
+  std::vector<double> tm;
+  if (bg->mode == 1) {
+    tm.resize((size_t)bg->map_h * bg->map_w);
+    for (int a = 0; a < bg->map_h; ++a)
+      for (int b = 0; b < bg->map_w; ++b) {
+        double y[3], dir[3];
+        map_texel_point(*bg, a, b, y, dir);
+        tm[(size_t)a * bg->map_w + b] = bg_margin(*fl, y, dir);
+      }
+  }
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      BgSample s;
+      bg_sample(*cam, fl->box, *bg, i, j, s);
+      double m = 1e300;
+      if (bg->mode == 0) {
+        m = bg_margin(*fl, s.y, s.dir);
+      } else {
+        for (int ka = 0; ka < 2; ++ka)
+          for (int kb = 0; kb < 2; ++kb) m = std::min(m, tm[(size_t)s.a[ka] * bg->map_w + s.b[kb]]);
+      }
+      margin[(size_t)j * W + i] = m;
+    }
+  return 0;
+}
+
 double orc_ssim(int32_t width, int32_t height, const double* x, const double* y) {
   double t = 0;
   for (int ch = 0; ch < 3; ++ch) t += ssim_channel(width, height, x, y, ch, 0.0, nullptr);

@@ -25,6 +25,7 @@ UNITS = {
     "fields2": ("fields.cu", ["-DHYRF_FIELDS_PART=2"]),
     "fields3": ("fields.cu", ["-DHYRF_FIELDS_PART=3"]),
     "fields_tc": ("fields_tc.cu", []),
+    "fields_tc_bwd": ("fields_tc_bwd.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
     "raster": ("raster.cu", []),

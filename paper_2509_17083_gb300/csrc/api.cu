@@ -21,6 +21,10 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
                                    cudaStream_t s);
 hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
                              cudaStream_t s);
+hyrf_status launch_query_bwd_tc(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
+                                cudaStream_t s);
+hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
+                             void* ws, cudaStream_t s);
 size_t slab_bytes(const FieldsDev& F, bool geo);
 size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward);
 hyrf_status launch_bg_fwd(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
@@ -120,7 +124,8 @@ hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a,
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
     return HYRF_ERR_UNSUPPORTED;
   if (!ws_ok(ws, ws_bytes, hyrf_query_fields_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
-  return launch_query_bwd(*a, F, ws, S(stream));
+  if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
+  return F.cm.bf16 ? launch_query_bwd_tc(*a, F, ws, S(stream)) : launch_query_bwd(*a, F, ws, S(stream));
 }
 
 // ------------------------------------------------------------------ project
@@ -265,6 +270,8 @@ hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_b
   if (st != HYRF_OK) return st;
   if (!b->d_C || !b->d_T_final || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (!ws_ok(ws, ws_bytes, bg_workspace(b->fwd, F, true))) return HYRF_ERR_INVALID_ARG;
+  if (!bf16_weights_ok(b->fwd.fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
+  if (b->fwd.bg.mode == 0 && F.cm.bf16) return launch_bg_bwd_tc(*b, F, ws, S(stream));
   return launch_bg_bwd(*b, F, ws, S(stream));
 }
 

@@ -330,6 +330,12 @@ struct SlabLayout {
   int total;
 };
 
+// Gradient buffers the slab sums are added to (NULL entries are skipped).
+struct SlabTargets {
+  float* W[2][3];
+  float* b[2][3];
+};
+
 inline SlabLayout make_slab_layout(const MlpDev* m0, const MlpDev* m1) {
   SlabLayout s{};
   int off = 0;

@@ -291,12 +291,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
   }
 }
 
-// Adds sum over CTAs of the slabs (times `scale`) into the gradient buffers.
-struct SlabTargets {
-  float* W[2][3];
-  float* b[2][3];
-};
 
+#if HYRF_FIELDS_PART == 0
 __global__ void k_slab_reduce(const float* __restrict__ slabs, int nslabs, SlabLayout SL,
                               SlabTargets T, float scale) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < SL.total; e += gridDim.x * blockDim.x) {
@@ -314,6 +310,7 @@ __global__ void k_slab_reduce(const float* __restrict__ slabs, int nslabs, SlabL
     *dst += s * scale;
   }
 }
+#endif
 
 // ---------------------------------------------------------------- background (Eqs. 10-11)
 
@@ -435,6 +432,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_bg_map_texels(FieldsDev F, int 
   }
 }
 
+#if HYRF_FIELDS_PART == 0
 __global__ void __launch_bounds__(256) k_bg_map_fwd(FieldsDev F, CamDev cam, float radius, int Hb,
                                                     int Wb, const float* __restrict__ map,
                                                     const float* __restrict__ C_fg,
@@ -504,6 +502,7 @@ __global__ void __launch_bounds__(256) k_bg_map_bwd_pix(FieldsDev F, CamDev cam,
       }
   }
 }
+#endif
 
 // Reverse of the colour field at background points: MODE 0 = one point per
 // pixel (exact mode, also writes dL/dT_final and dL/dC_fg), MODE 1 = one

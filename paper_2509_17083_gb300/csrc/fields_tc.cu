@@ -15,145 +15,10 @@
 // Every wait on an mbarrier is bounded; on expiry the kernel records
 // HYRF_ERR_TIMEOUT in the status word, waits (bounded) for its MMAs, frees
 // its tensor memory and returns.
-#include "field_ops.cuh"
+#include "tc_ops.cuh"
 
 namespace hyrf {
 namespace tc {
-
-constexpr uint32_t kSpin = 1u << 24;
-
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__host__ __device__ constexpr uint32_t kmaj(int r, int k, int K) {
-  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128.
-template <int N>
-__device__ __forceinline__ constexpr uint32_t idesc() {
-  static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-
-__device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar)));
-}
-
-__device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(saddr(bar)), "r"(phase));
-  return ok != 0;
-}
-
-// Bounded wait on the given phase; returns false (on every thread) if any
-// thread of the CTA gave up.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase) {
-  bool ok = false;
-  for (uint32_t it = 0; it < kSpin && !ok; ++it) ok = try_wait(bar, phase);
-  return !__syncthreads_or(!ok);
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_smem_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 16 consecutive f32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// D[128 x N] (+)= A[128 x K] B[N x K]^T with both operands K-major in smem.
-template <int N, int K>
-__device__ __forceinline__ void gemm(uint32_t d, const uint8_t* A, const uint8_t* B) {
-#pragma unroll
-  for (int ks = 0; ks < K / 16; ++ks) {
-    const uint64_t da = sdesc(saddr(A) + ks * 256, 128, (K / 8) * 128);
-    const uint64_t db = sdesc(saddr(B) + ks * 256, 128, (K / 8) * 128);
-    mma(d, da, db, idesc<N>(), ks > 0 ? 1u : 0u);
-  }
-}
-
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// Row r of a K-major bf16 tile from 8*n floats.
-template <int K>
-__device__ __forceinline__ void store_row(uint8_t* tile, int r, const float* v) {
-#pragma unroll
-  for (int kc = 0; kc < K / 8; ++kc) {
-    uint4 u;
-    u.x = pack2(v[8 * kc], v[8 * kc + 1]);
-    u.y = pack2(v[8 * kc + 2], v[8 * kc + 3]);
-    u.z = pack2(v[8 * kc + 4], v[8 * kc + 5]);
-    u.w = pack2(v[8 * kc + 6], v[8 * kc + 7]);
-    *reinterpret_cast<uint4*>(tile + kmaj(r, 8 * kc, K)) = u;
-  }
-}
-
-// Weights W [rows][K] bf16 (row-major, rows_real valid rows) into a K-major
-// tile of N rows (rows >= rows_real zero).
-template <int N, int K>
-__device__ __forceinline__ void stage_w(uint8_t* tile, const void* W, int rows_real) {
-  const uint4* src = static_cast<const uint4*>(W);
-  for (int e = threadIdx.x; e < N * (K / 8); e += blockDim.x) {
-    const int r = e / (K / 8), kc = e % (K / 8);
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (r < rows_real) v = __ldg(src + r * (K / 8) + kc);
-    *reinterpret_cast<uint4*>(tile + kmaj(r, 8 * kc, K)) = v;
-  }
-}
-
-// ReLU(D + b) of this thread's 64 accumulator columns -> its row of H.
-__device__ __forceinline__ void epilogue_relu64(uint32_t taddr, const float* b, uint8_t* H, int r) {
-#pragma unroll
-  for (int c0 = 0; c0 < 64; c0 += 16) {
-    float v[16];
-    ld16(taddr + c0, v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b[c0 + j], 0.0f);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint4 u;
-      u.x = pack2(v[8 * h], v[8 * h + 1]);
-      u.y = pack2(v[8 * h + 2], v[8 * h + 3]);
-      u.z = pack2(v[8 * h + 4], v[8 * h + 5]);
-      u.w = pack2(v[8 * h + 6], v[8 * h + 7]);
-      *reinterpret_cast<uint4*>(H + kmaj(r, c0 + 8 * h, 64)) = u;
-    }
-  }
-}
-
-__device__ __forceinline__ void cam_center(const CamDev& c, float pc[3]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) pc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
-}
 
 // ---------------------------------------------------------------- field query
 
@@ -335,29 +200,6 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
 constexpr int bW0c = 0, bW1c = bW0c + 64 * 64 * 2, bW2c = bW1c + 64 * 64 * 2, bAc = bW2c + 16 * 64 * 2,
               bHc = bAc + 128 * 64 * 2, bBias = bHc + 128 * 64 * 2, kBgSmem = bBias + 144 * 4;
 constexpr uint32_t kBgTmemCols = 128;
-
-__device__ __forceinline__ void bg_ray(const CamDev& c, const FieldsDev& F, float radius, int i, int j,
-                                       float ps[3], float dirw[3]) {
-  float oc[3];
-  cam_center(c, oc);
-  const float dc[3] = {((float)i + 0.5f - c.cx) / c.fx, ((float)j + 0.5f - c.cy) / c.fy, 1.0f};
-  float on[3], dn[3], dw[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    dw[k] = c.R[k] * dc[0] + c.R[3 + k] * dc[1] + c.R[6 + k] * dc[2];
-    on[k] = (oc[k] - F.lo[k]) * F.sx[k] - 1.0f;
-    dn[k] = dw[k] * F.sx[k];
-  }
-  const float A = dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2];
-  const float B = 2.0f * (on[0] * dn[0] + on[1] * dn[1] + on[2] * dn[2]);
-  const float C = on[0] * on[0] + on[1] * on[1] + on[2] * on[2] - radius * radius;
-  const float tt = (-B + sqrtf(B * B - 4.0f * A * C)) / (2.0f * A);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) ps[k] = on[k] + tt * dn[k];
-  const float nd = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) dirw[k] = dw[k] / nd;
-}
 
 __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
                                                            const float* __restrict__ C_fg,

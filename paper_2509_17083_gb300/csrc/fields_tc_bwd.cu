@@ -1,0 +1,545 @@
+// Reverse of the BF16 decoders (Eqs. 4, 6) and of the aggregation (Eq. 7)
+// on the tensor cores. One CTA of 128 threads owns a tile of 128 points (one
+// per thread, the MMA M dimension) and one decoder:
+//
+//   forward recompute  X -> H1 -> H2 -> O          (K-major A, K-major B)
+//   dZ2 = reverse of Eq. 7 (or of Eq. 10 for background pixels), x loss scale
+//   dH2 = dZ2 W2,  dW2 += dZ2^T H2                  (B MN-major; A and B MN-major)
+//   dZ1 = dH2 * [H2 > 0] -> dH1 = dZ1 W1, dW1 += dZ1^T H1
+//   dZ0 = dH1 * [H1 > 0] -> dX  = dZ0 W0, dW0 += dZ0^T X
+//   dX -> hash-table gradient (float2 atomics) and dL/dposition
+//
+// dX products read the forward weight tile as an MN-major B operand, so no
+// transposed copy exists; dW products read the point-row tiles as MN-major
+// operands with M = 128 output rows, of which only the decoder's real
+// outputs are used. Each dW comes out of tensor memory after its product
+// and is added (plain read-modify-write) into this CTA's f32 slab; one
+// reduction kernel sums the slabs. Bias gradients are column sums of dZ.
+// Activations are never stored in global memory: they are recomputed.
+#include "tc_ops.cuh"
+
+namespace hyrf {
+namespace tc {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void unpack8(uint4 u, float* v) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
+    v[2 * k] = f.x;
+    v[2 * k + 1] = f.y;
+  }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  uint4 u;
+  u.x = pack2(v[0], v[1]);
+  u.y = pack2(v[2], v[3]);
+  u.z = pack2(v[4], v[5]);
+  u.w = pack2(v[6], v[7]);
+  return u;
+}
+
+// ---------------------------------------------------------------- point sources
+
+struct GaussP {
+  int n;
+  const float* pos;
+  const float* alpha_e;
+  const float* scale_e;
+  const float* color_e;
+  const int32_t* vis_ids;
+  const int32_t* n_vis;
+  const float* d_alpha;
+  const float* d_scale;
+  const float* d_quat;
+  const float* d_color;
+  float* d_pos;
+  float* d_alpha_e;
+  float* d_scale_e;
+  float* d_color_e;
+  float* g_geo_table;
+  float* g_rad_table;
+  int32_t* status;
+};
+
+// Geometry decoder at visible Gaussians: inputs enc(y; Theta_geo), outputs
+// (alpha_n, s_n[3], r_n[4]).
+struct GeoGauss {
+  static constexpr int IN = 32, OUT = 8, DEC = 0;
+  using Params = GaussP;
+  struct Row {
+    int i, g;
+    bool ok;
+    float y[3], J[9];
+    float da, ds[3], dq[4], ae, se;
+  };
+  __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
+  __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.gm; }
+  __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev&, int idx, bool ok,
+                               Row& R, float* x) {
+    R.i = idx;
+    R.ok = ok;
+    R.g = ok ? P.vis_ids[idx] : 0;
+    if (ok && (R.g < 0 || R.g >= P.n)) {
+      set_status(P.status, HYRF_ERR_BOUNDS);
+      R.ok = false;
+      R.g = 0;
+    }
+    float p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = R.ok ? P.pos[3 * (int64_t)R.g + k] : F.lo[k] + 1.0f / F.sx[k];
+    contract_p(F, p, R.y, R.J);
+    encode<16>(F.geo, R.y, x);
+    R.da = R.ok ? P.d_alpha[idx] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) R.ds[k] = R.ok ? P.d_scale[3 * idx + k] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) R.dq[k] = R.ok ? P.d_quat[4 * idx + k] : 0.0f;
+    R.ae = R.ok ? P.alpha_e[R.g] : 0.0f;
+    R.se = R.ok ? P.scale_e[R.g] : 0.0f;
+  }
+  // Reverse of Eq. 7 for alpha, scale and rotation; o = raw decoder outputs.
+  __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
+    const float a = sigmoidf_(o[0] + R.ae);
+    dz[0] = R.da * a * (1.0f - a);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float s = sigmoidf_(o[1 + k] + R.se);
+      dz[1 + k] = R.ds[k] * s * (1.0f - s);
+    }
+    const float rn = sqrtf(o[4] * o[4] + o[5] * o[5] + o[6] * o[6] + o[7] * o[7]);
+    if (rn > 1e-12f) {
+      float qd = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) qd += o[4 + k] / rn * R.dq[k];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dz[4 + k] = (R.dq[k] - o[4 + k] / rn * qd) / rn;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dz[4 + k] = R.dq[k] / 1e-12f;
+    }
+    if (!R.ok) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dz[k] = 0.0f;
+      return;
+    }
+    P.d_alpha_e[R.g] += dz[0];
+    P.d_scale_e[R.g] += dz[1] + dz[2] + dz[3];
+  }
+  __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
+                                const float* dx) {
+    if (!R.ok) return;
+    float dy[3] = {0.0f, 0.0f, 0.0f};
+    encode_bwd<16>(F.geo, R.y, dx, P.g_geo_table, dy);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      P.d_pos[3 * (int64_t)R.g + j] += R.J[j] * dy[0] + R.J[3 + j] * dy[1] + R.J[6 + j] * dy[2];
+  }
+};
+
+// Colour decoder at visible Gaussians: inputs enc(y; Theta_rad) (+) PE(dir).
+struct ColGauss {
+  static constexpr int IN = 64, OUT = 3, DEC = 1;
+  using Params = GaussP;
+  struct Row {
+    int g;
+    bool ok;
+    float y[3], J[9], dir[3], vn, dc[3], ce[3];
+  };
+  __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
+  __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
+  __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
+                               Row& R, float* x) {
+    R.ok = ok;
+    R.g = ok ? P.vis_ids[idx] : 0;
+    if (ok && (R.g < 0 || R.g >= P.n)) {
+      set_status(P.status, HYRF_ERR_BOUNDS);
+      R.ok = false;
+      R.g = 0;
+    }
+    float p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = R.ok ? P.pos[3 * (int64_t)R.g + k] : F.lo[k] + 1.0f / F.sx[k];
+    contract_p(F, p, R.y, R.J);
+    encode<16>(F.rad, R.y, x);
+    float pc[3];
+    cam_center(cam, pc);
+    const float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+    R.vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) R.dir[k] = v[k] / R.vn;
+    pos_enc(R.dir, x + 32);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      R.dc[k] = R.ok ? P.d_color[3 * idx + k] : 0.0f;
+      R.ce[k] = R.ok ? P.color_e[3 * (int64_t)R.g + k] : 0.0f;
+    }
+  }
+  __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float c = sigmoidf_(o[k] + R.ce[k]);
+      dz[k] = R.ok ? R.dc[k] * c * (1.0f - c) : 0.0f;
+    }
+    if (R.ok) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) P.d_color_e[3 * (int64_t)R.g + k] += dz[k];
+    }
+  }
+  __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
+                                const float* dx) {
+    if (!R.ok) return;
+    float dy[3] = {0.0f, 0.0f, 0.0f};
+    encode_bwd<16>(F.rad, R.y, dx, P.g_rad_table, dy);
+    float ddir[3];
+    pos_enc_bwd(R.dir, dx + 32, ddir);
+    const float dd = R.dir[0] * ddir[0] + R.dir[1] * ddir[1] + R.dir[2] * ddir[2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      P.d_pos[3 * (int64_t)R.g + j] += (ddir[j] - R.dir[j] * dd) / R.vn + R.J[j] * dy[0] +
+                                       R.J[3 + j] * dy[1] + R.J[6 + j] * dy[2];
+  }
+};
+
+struct PixelP {
+  float radius;
+  const float* T_final;
+  const float* dC;
+  float* dC_fg;
+  float* dT;
+  float* g_rad_table;
+};
+
+// Colour decoder at the background-sphere hit of every pixel (exact mode):
+// reverse of C = C_fg + T_final sigma(c_n).
+struct BgPixel {
+  static constexpr int IN = 64, OUT = 3, DEC = 1;
+  using Params = PixelP;
+  struct Row {
+    int p;
+    bool ok;
+    float y[3], T, g[3];
+  };
+  __device__ static int count_px(const CamDev& cam) { return cam.W * cam.H; }
+  __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
+  __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
+                               Row& R, float* x) {
+    R.ok = ok;
+    R.p = ok ? idx : 0;
+    float ps[3], dir[3];
+    bg_ray(cam, F, P.radius, R.p % cam.W, R.p / cam.W, ps, dir);
+    contract_n(ps, R.y);
+    encode<16>(F.rad, R.y, x);
+    pos_enc(dir, x + 32);
+    R.T = ok ? P.T_final[R.p] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) R.g[k] = ok ? P.dC[3 * (int64_t)R.p + k] : 0.0f;
+  }
+  __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
+    float dt = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float cs = sigmoidf_(o[k]);
+      dt += R.g[k] * cs;
+      dz[k] = R.g[k] * R.T * cs * (1.0f - cs);
+    }
+    if (R.ok) {
+      P.dT[R.p] = dt;
+      if (P.dC_fg) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P.dC_fg[3 * (int64_t)R.p + k] = R.g[k];
+      }
+    }
+  }
+  __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
+                                const float* dx) {
+    if (!R.ok) return;
+    encode_bwd<16>(F.rad, R.y, dx, P.g_rad_table, nullptr);
+  }
+};
+
+template <class S>
+__device__ __forceinline__ int point_count(const typename S::Params& P, const CamDev& cam) {
+  if constexpr (std::is_same<S, BgPixel>::value) {
+    return BgPixel::count_px(cam);
+  } else {
+    return S::count(P);
+  }
+}
+
+// ---------------------------------------------------------------- the kernel
+
+// Shared-memory map. The dW products read their dZ operand with 128 output
+// rows; rows beyond the real outputs come from the following bytes (always
+// inside this map: each dZ tile is followed by another tile or the guard).
+template <int IN>
+struct BwdSmem {
+  static constexpr int W0 = 0, W1 = W0 + 64 * IN * 2, W2 = W1 + 64 * 64 * 2, X = W2 + 16 * 64 * 2,
+                       H1 = X + 128 * IN * 2, H2 = H1 + 128 * 64 * 2, Z2 = H2 + 128 * 64 * 2,
+                       GUARD = Z2 + 128 * 16 * 2, BIAS = GUARD + 2048, DB = BIAS + 144 * 4,
+                       SIZE = DB + 144 * 4;
+};
+constexpr uint32_t kBwdTmemCols = 128;  // [0, 64): products, [64, 128): dW
+
+// ReLU mask from the bf16 activations of this row, applied to 64 columns of
+// D read from tensor memory; the masked gradient replaces the activations in
+// place (bf16) and its column sums go to db.
+__device__ __forceinline__ void relu_back64(uint32_t taddr, uint8_t* Hbuf, int r, bool ok, float* db) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c0 = 0; c0 < 64; c0 += 16) {
+    float v[16], h[16];
+    ld16(taddr + c0, v);
+    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0, 64)), h);
+    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + 8, 64)), h + 8);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = (ok && h[j] > 0.0f) ? v[j] : 0.0f;
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0, 64)) = pack8(v);
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + 8, 64)) = pack8(v + 8);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float s = warp_sum(v[j]);
+      if (lane == 0) atomicAdd(db + c0 + j, s);
+    }
+  }
+}
+
+// dW rows < rows_used (TMEM lanes) x N columns, added to the CTA slab.
+template <int N>
+__device__ __forceinline__ void flush_dw(uint32_t tm_w, int rows_used, float* slab_W) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w * 32 >= rows_used) return;  // warp-uniform
+  const int o = w * 32 + lane;
+#pragma unroll
+  for (int c0 = 0; c0 < N; c0 += 16) {
+    float v[16];
+    ld16(tm_w + ((uint32_t)(w * 32) << 16) + c0, v);
+    if (o < rows_used) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) slab_W[o * N + c0 + j] += v[j];
+    }
+  }
+}
+
+__device__ __forceinline__ void sync_for_mma() {
+  fence_smem_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+}
+
+template <class S>
+__global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P, FieldsDev F, CamDev cam,
+                                                           float loss_scale, SlabLayout SL, float* slabs,
+                                                           int32_t* status) {
+  constexpr int IN = S::IN, OUT = S::OUT;
+  using L = BwdSmem<IN>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x, w = t >> 5, r = t;
+  const MlpDev& M = S::mlp(F);
+  float* bias = reinterpret_cast<float*>(sm + L::BIAS);
+  float* db = reinterpret_cast<float*>(sm + L::DB);  // db0 [0,64), db1 [64,128), db2 [128,144)
+  stage_w<64, IN>(sm + L::W0, M.W[0], 64);
+  stage_w<64, 64>(sm + L::W1, M.W[1], 64);
+  stage_w<16, 64>(sm + L::W2, M.W[2], OUT);
+  if (t < 64) {
+    bias[t] = M.b[0][t];
+    bias[64 + t] = M.b[1][t];
+    db[t] = 0.0f;
+    db[64 + t] = 0.0f;
+  }
+  if (t < 16) {
+    bias[128 + t] = t < OUT ? M.b[2][t] : 0.0f;
+    db[128 + t] = 0.0f;
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(kBwdTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  sync_for_mma();
+  const uint32_t tm = tmem_base, tmW = tmem_base + 64;
+  const uint32_t lane_off = ((uint32_t)(w * 32)) << 16;
+  float* slab = slabs + (size_t)blockIdx.x * SL.total;
+  const float inv_ls = 1.0f / loss_scale;
+  const int n = point_count<S>(P, cam);
+  const int ntile = (n + 127) / 128;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const int idx = tile * 128 + r;
+    const bool ok = idx < n;
+    typename S::Row R;
+    {
+      float x[IN];
+      S::begin(P, F, cam, idx, ok, R, x);
+      store_row<IN>(sm + L::X, r, x);
+    }
+    // ---- forward recompute
+    sync_for_mma();
+    if (t == 0) {
+      gemm<64, IN>(tm, sm + L::X, sm + L::W0);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    epilogue_relu64(tm + lane_off, bias, sm + L::H1, r);
+    sync_for_mma();
+    if (t == 0) {
+      gemm<64, 64>(tm, sm + L::H1, sm + L::W1);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    epilogue_relu64(tm + lane_off, bias + 64, sm + L::H2, r);
+    sync_for_mma();
+    if (t == 0) {
+      gemm<16, 64>(tm, sm + L::H2, sm + L::W2);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    {
+      float o[16], dz[16];
+      ld16(tm + lane_off, o);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o[k] += bias[128 + k];
+      S::dz_out(P, R, o, dz);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) dz[k] = k < OUT ? dz[k] * loss_scale : 0.0f;
+      *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 0, 16)) = pack8(dz);
+      *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 8, 16)) = pack8(dz + 8);
+#pragma unroll
+      for (int k = 0; k < OUT; ++k) {
+        const float s = warp_sum(dz[k]);
+        if ((t & 31) == 0) atomicAdd(db + 128 + k, s);
+      }
+    }
+    // ---- layer 2: dH2 = dZ2 W2, dW2 += dZ2^T H2
+    sync_for_mma();
+    if (t == 0) {
+      gemm_dx<64, 16>(tm, sm + L::Z2, sm + L::W2, false);
+      gemm_dw<64, 16>(tmW, sm + L::Z2, sm + L::H2, false);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    relu_back64(tm + lane_off, sm + L::H2, r, ok, db + 64);  // dZ1 replaces H2
+    flush_dw<64>(tmW, OUT, slab + SL.off_W[S::DEC][2]);
+    // ---- layer 1: dH1 = dZ1 W1, dW1 += dZ1^T H1
+    sync_for_mma();
+    if (t == 0) {
+      gemm_dx<64, 64>(tm, sm + L::H2, sm + L::W1, false);
+      gemm_dw<64, 64>(tmW, sm + L::H2, sm + L::H1, false);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    relu_back64(tm + lane_off, sm + L::H1, r, ok, db);  // dZ0 replaces H1
+    flush_dw<64>(tmW, 64, slab + SL.off_W[S::DEC][1]);
+    // ---- layer 0: dX = dZ0 W0, dW0 += dZ0^T X
+    sync_for_mma();
+    if (t == 0) {
+      gemm_dx<IN, 64>(tm, sm + L::H1, sm + L::W0, false);
+      gemm_dw<IN, 64>(tmW, sm + L::H1, sm + L::X, false);
+      commit(&bar);
+    }
+    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    phase ^= 1u;
+    fence_after();
+    {
+      float dx[IN];
+#pragma unroll
+      for (int c0 = 0; c0 < IN; c0 += 16) ld16(tm + lane_off + c0, dx + c0);
+#pragma unroll
+      for (int k = 0; k < IN; ++k) dx[k] *= inv_ls;
+      S::finish(P, F, cam, R, dx);
+    }
+    flush_dw<IN>(tmW, 64, slab + SL.off_W[S::DEC][0]);
+    fence_before();
+  }
+  if (failed) {
+    set_status(status, HYRF_ERR_TIMEOUT);
+    for (uint32_t it = 0; it < kSpin; ++it)
+      if (try_wait(&bar, phase)) break;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (t < 64) {
+    slab[SL.off_b[S::DEC][0] + t] += db[t];
+    slab[SL.off_b[S::DEC][1] + t] += db[64 + t];
+  }
+  if (t < OUT) slab[SL.off_b[S::DEC][2] + t] += db[128 + t];
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kBwdTmemCols));
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- launchers
+
+int bwd_ctas();
+hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout& SL,
+                               const SlabTargets& T, float scale, cudaStream_t s);
+SlabTargets slab_targets(const hyrf_field_grads& g, bool geo);
+
+template <class S>
+static hyrf_status launch_dec_bwd(const typename S::Params& P, const FieldsDev& F, const CamDev& cam,
+                                  float ls, const SlabLayout& SL, float* slabs, int32_t* status,
+                                  cudaStream_t s) {
+  constexpr int smem = tc::BwdSmem<S::IN>::SIZE;
+  cudaFuncSetAttribute(tc::k_decoder_bwd_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 128, smem, s>>>(P, F, cam, ls, SL, slabs, status);
+  HYRF_LAUNCH_CHECK();
+  return HYRF_OK;
+}
+
+hyrf_status launch_query_bwd_tc(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
+                                cudaStream_t s) {
+  if (a.n == 0) return HYRF_OK;
+  const CamDev cam = to_dev(a.cam);
+  const SlabLayout SL = make_slab_layout(&F.gm, &F.cm);
+  float* slabs = static_cast<float*>(ws);
+  cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
+  tc::GaussP P{a.n,       a.pos,       a.alpha_e,   a.scale_e,   a.color_e,         a.vis_ids,
+               a.n_vis,   a.d_alpha,   a.d_scale,   a.d_quat,    a.d_color,         a.d_pos,
+               a.d_alpha_e, a.d_scale_e, a.d_color_e, a.grads.geo_table, a.grads.rad_table, a.status};
+  hyrf_status st = launch_dec_bwd<tc::GeoGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
+  if (st != HYRF_OK) return st;
+  st = launch_dec_bwd<tc::ColGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
+  if (st != HYRF_OK) return st;
+  return launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(a.grads, true), 1.0f / a.loss_scale, s);
+}
+
+hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
+                             void* ws, cudaStream_t s) {
+  const hyrf_composite_background_args& a = b.fwd;
+  const CamDev cam = to_dev(a.cam);
+  const SlabLayout SL = make_slab_layout(nullptr, &F.cm);
+  float* slabs = static_cast<float*>(ws);
+  cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
+  tc::PixelP P{a.bg.radius, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, b.grads.rad_table};
+  hyrf_status st = launch_dec_bwd<tc::BgPixel>(P, F, cam, b.loss_scale, SL, slabs, a.status, s);
+  if (st != HYRF_OK) return st;
+  return launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
+}
+
+}  // namespace hyrf

@@ -179,6 +179,13 @@ class ViewRenderer:
     # ------------------------------------------------------------- backward
     def backward(self):
         """Reverse of every stage; dL/dC must be in self.dC. Adds into model.grad."""
+        self.backward_render()
+        self.backward_fields()
+
+    def backward_render(self):
+        """Reverse of background, compositing and projection: fills the
+        visible Gaussians' dL/d(alpha, scale, quat, color) and adds the
+        projection's dL/dpos."""
         m = self.m
         for t in (self.d_mean2d, self.d_conic, self.d_alpha, self.d_color):
             t.zero_()
@@ -193,6 +200,11 @@ class ViewRenderer:
                                 n_vis=self.n_vis, scale=self.scale, quat=self.quat, cam=self.ccam,
                                 d_mean2d=self.d_mean2d, d_conic=self.d_conic, d_pos=m.grad["pos"],
                                 d_scale=self.d_scale, d_quat=self.d_quat, status=self.status)
+
+    def backward_fields(self):
+        """Reverse of the field query (decoders, hash encodings, aggregation)."""
+        m = self.m
+        g = m.grads_struct()
         H.hyrf_query_fields_backward(ws=self.ws["qb"], n=m.n, pos=m.pos, alpha_e=m.alpha_e,
                                      scale_e=m.scale_e, color_e=m.color_e, cam=self.ccam,
                                      fields=m.fields_struct(), vis_ids=self.vis_ids,

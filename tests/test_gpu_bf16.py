@@ -23,7 +23,7 @@ def _workload(prec, init=1e-4, n=30000, W=301, H_=203):
                          table_init=init)
 
 
-def _render(w, mask=None, backward=True):
+def _render(w, mask=None, backward=True, qmask=None):
     m = DeviceModel(w)
     r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
     tgt = cuda_f32(w.targets[0])
@@ -34,9 +34,28 @@ def _render(w, mask=None, backward=True):
     if backward:
         if mask is not None:
             r.dC.mul_(cuda_f32(mask)[..., None])
-        r.backward()
+        r.backward_render()
+        if qmask is not None:
+            q = cuda_f32(qmask)
+            nv = len(qmask)
+            r.d_alpha[:nv].mul_(q)
+            for t in (r.d_scale, r.d_quat, r.d_color):
+                t[:nv].mul_(q[:, None])
+        r.backward_fields()
     torch.cuda.synchronize()
     return m, r
+
+
+# bf16 activations carry ~2^-9 relative rounding per value: Gaussians with a
+# hidden pre-activation within 3e-3 (relative) of the ReLU kink are left out
+# of the decoder-backward comparison on both sides.
+RELU_MARGIN_BF16 = (3e-3, 3e-3)
+# Trained-like tables add the FP32 hash-coordinate error (up to ~2e-3 of
+# image, see gpu_util) to the bf16 budget; the position gradient's hash term
+# is the level resolution (up to 7006) times the corner-value spread (~0.3
+# here) times the bf16-rounded feature gradient, which bounds it near 3e-2.
+TOL_IMG_BF16_TRAINED = 4e-3
+TOL_POS_BF16_TRAINED = 3e-2
 
 
 def test_query_fields_tensor_cores_match_oracle():
@@ -60,17 +79,23 @@ def test_query_fields_tensor_cores_match_oracle():
 def test_bf16_iteration_matches_oracle(init):
     w = _workload("bf16", init=init)
     fw = oracle.render(w.gaussians, w.fields, w.cams[0], w.bg)
-    mask = oracle.decision_safe_mask(fw, w.cams[0])
-    m, r = _render(w, mask.astype(np.float32))
+    mask = oracle.decision_safe_mask(fw, w.cams[0], fields=w.fields, bg=w.bg,
+                                     bg_relu_margin=RELU_MARGIN_BF16[1])
+    assert mask.mean() > 0.05, mask.mean()
+    qmask = oracle.relu_safe_mask(w.gaussians, w.fields, w.cams[0], fw["ids"], *RELU_MARGIN_BF16)
+    assert qmask.sum() > 1000, qmask.sum()
+    m, r = _render(w, mask.astype(np.float32), qmask=qmask)
     assert H.read_status(r.status) == 0
     L, fw, grads, _ = oracle.loss_and_grads(w.gaussians, w.fields, w.cams[0], w.bg, w.targets[0],
-                                            w.ssim_lambda, dC_mask=mask)
+                                            w.ssim_lambda, dC_mask=mask, query_mask=qmask)
     err = np.abs(np_(r.C) - fw["C"]).max(-1)
-    assert err[mask].max() < TOL_IMG_BF16, err[mask].max()
+    tol = TOL_IMG_BF16 if init <= 1e-3 else TOL_IMG_BF16_TRAINED
+    assert err[mask].max() < tol, err[mask].max()
     g = m.grad
     for key in ("pos", "alpha_e", "scale_e", "color_e", "geo_table", "rad_table"):
         e = rel_l2(np_(g[key]), grads[key])
-        assert e < TOL_GRAD_BF16, (key, e)
+        tol = TOL_POS_BF16_TRAINED if (key == "pos" and init > 1e-3) else TOL_GRAD_BF16
+        assert e < tol, (key, e)
     for key in ("geo_W", "col_W", "geo_b", "col_b"):
         for l in range(3):
             e = rel_l2(np_(g[key][l]), grads[key][l])
