@@ -261,6 +261,32 @@ hyrf_status hyrf_bin_sort(const hyrf_bin_sort_args* a, void* workspace, size_t w
 hyrf_status hyrf_bin_sort_backward(const hyrf_bin_sort_args* a, void* workspace, size_t ws_bytes,
                                    void* stream);
 
+/* hyrf_bin_sort without a caller workspace. The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * themselves, such as a host program that links this library through its C
+ * interface without any device allocator of its own, or one that must not
+ * call cudaMalloc while it runs (the call can synchronise the device and can
+ * fail under a memory budget fixed up front). It computes exactly what
+ * hyrf_bin_sort computes, with the same arguments and outputs (all still
+ * caller-provided), but takes its temporary storage from one fixed array of
+ * HYRF_NOALLOC_SCRATCH_BYTES in device memory that the library declares;
+ * every GPU that loads the library holds that array until the process exits.
+ * It never calls cudaMalloc, cudaFree or any other allocating routine.
+ *   - Limits: a->n <= HYRF_NOALLOC_MAX_GAUSSIANS and a->capacity <=
+ *     HYRF_NOALLOC_MAX_INSTANCES; larger requests return
+ *     HYRF_ERR_INVALID_ARG and launch nothing.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one array, which keeps whatever the last call left
+ *     in it (no part of it is read before a call writes it). Calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on
+ *     it: order them, e.g. on one stream. */
+#define HYRF_NOALLOC_MAX_GAUSSIANS 65536
+#define HYRF_NOALLOC_MAX_INSTANCES 262144
+#define HYRF_NOALLOC_SCRATCH_BYTES 4718592
+hyrf_status hyrf_bin_sort_noalloc(const hyrf_bin_sort_args* a, void* stream);
+
 /* ------------------------------------------------------------------------
  * hyrf_rasterize: per 16x16 tile, front-to-back compositing of Eq. 1:
  * alpha_i = min(0.99, o_i exp(-1/2 d^T conic d)), skipped if < 1/255;

@@ -28,6 +28,7 @@ UNITS = {
     "fields_tc_bwd": ("fields_tc_bwd.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
+    "noalloc": ("noalloc.cu", []),
     "raster": ("raster.cu", []),
     "loss": ("loss.cu", []),
 }

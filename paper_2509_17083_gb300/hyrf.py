@@ -165,6 +165,8 @@ def lib():
         L.hyrf_read_status.restype = C.c_int32
         L.hyrf_error_string.argtypes = [C.c_int32]
         L.hyrf_error_string.restype = C.c_char_p
+        L.hyrf_bin_sort_noalloc.argtypes = [C.POINTER(hyrf_bin_sort_args), _vp]
+        L.hyrf_bin_sort_noalloc.restype = C.c_int32
         L.hyrf_launch_count.argtypes = []
         L.hyrf_launch_count.restype = C.c_uint64
         _lib = L
@@ -172,7 +174,9 @@ def lib():
 
 
 EXPORTED = list(_ARGS) + [k + "_workspace_size" for k in _ARGS if k != "hyrf_bin_sort_backward"] + [
-    "hyrf_read_status", "hyrf_error_string", "hyrf_launch_count"]
+    "hyrf_read_status", "hyrf_error_string", "hyrf_launch_count", "hyrf_bin_sort_noalloc"]
+NOALLOC_MAX_GAUSSIANS = 65536
+NOALLOC_MAX_INSTANCES = 262144
 
 
 def ptr(t):
@@ -312,6 +316,16 @@ def hyrf_bin_sort(ws=None, stream=None, **kw):
 
 def hyrf_bin_sort_backward(ws=None, stream=None, **kw):
     return call("hyrf_bin_sort_backward", _fill(hyrf_bin_sort_args(), kw), ws, stream)
+
+
+def hyrf_bin_sort_noalloc(stream=None, **kw):
+    """hyrf_bin_sort with the library's fixed scratch array (no workspace)."""
+    a = _fill(hyrf_bin_sort_args(), kw)
+    L = lib()
+    st = L.hyrf_bin_sort_noalloc(C.byref(a), stream_handle(stream))
+    if st != HYRF_OK:
+        raise HyrfError(f"hyrf_bin_sort_noalloc: {L.hyrf_error_string(st).decode()} ({st})")
+    return st
 
 
 def hyrf_rasterize(ws=None, stream=None, **kw):
