@@ -51,11 +51,12 @@ def _render(w, mask=None, backward=True, qmask=None):
 # of the decoder-backward comparison on both sides.
 RELU_MARGIN_BF16 = (3e-3, 3e-3)
 # Trained-like tables add the FP32 hash-coordinate error (up to ~2e-3 of
-# image, see gpu_util) to the bf16 budget; the position gradient's hash term
-# is the level resolution (up to 7006) times the corner-value spread (~0.3
-# here) times the bf16-rounded feature gradient, which bounds it near 3e-2.
+# image, see gpu_util) to the bf16 budget; with corner values spread ~0.3
+# the bf16-rounded features and hidden activations move the decoder outputs
+# by ~1e-2 of their own size, and the position gradient's hash term scales
+# with the level resolution (up to 7006): gradients are bounded near 3e-2.
 TOL_IMG_BF16_TRAINED = 4e-3
-TOL_POS_BF16_TRAINED = 3e-2
+TOL_GRAD_BF16_TRAINED = 3e-2
 
 
 def test_query_fields_tensor_cores_match_oracle():
@@ -94,12 +95,12 @@ def test_bf16_iteration_matches_oracle(init):
     g = m.grad
     for key in ("pos", "alpha_e", "scale_e", "color_e", "geo_table", "rad_table"):
         e = rel_l2(np_(g[key]), grads[key])
-        tol = TOL_POS_BF16_TRAINED if (key == "pos" and init > 1e-3) else TOL_GRAD_BF16
+        tol = TOL_GRAD_BF16_TRAINED if init > 1e-3 else TOL_GRAD_BF16
         assert e < tol, (key, e)
     for key in ("geo_W", "col_W", "geo_b", "col_b"):
         for l in range(3):
             e = rel_l2(np_(g[key][l]), grads[key][l])
-            assert e < TOL_GRAD_BF16, (key, l, e)
+            assert e < (TOL_GRAD_BF16_TRAINED if init > 1e-3 else TOL_GRAD_BF16), (key, l, e)
 
 
 def test_bf16_psnr_within_005_db_of_fp32():
