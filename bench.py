@@ -29,8 +29,8 @@ WORKLOAD = "config3: 1M Gaussians (256 clusters + 10% far), 1237x822, 2x16-level
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "bf16", "f32"])
     p.add_argument("--n", type=int, default=1_000_000)
@@ -63,8 +63,11 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -99,18 +102,32 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- algorithmic work per stage
 
-def stage_work(r, m, nv, K, P, bf16):
-    """Algorithmic bytes (HBM-bound stages) or flops per launch, from the
-    per-unit figures documented with the kernels."""
-    L = m.fl.geo.n_levels
-    ent = 4 if bf16 else 8                     # bytes per (2-feature) table entry
-    gather = 2 * L * 8 * ent                   # both fields, 8 corners per level
-    # query backward: gather + scatter (8-byte float2 atomic per corner) per field
+def kernel_work(nv, K, P, tiles, bf16):
+    """Algorithmic HBM bytes per launch of the main kernels: every input read
+    once, every output written once, each table-gradient atomic counted as its
+    8-byte float2 payload. Per-unit figures: visible Gaussian (nv), tile
+    instance (K), pixel (P)."""
+    L = 16
+    ent = 4 if bf16 else 8                     # bytes per 2-feature table entry
+    gather = L * 8 * ent                       # one field, 8 corners per level
+    scatter = L * 8 * 8                        # one field, float2 atomic per corner
     return {
-        "query_fwd": nv * (gather + 12 + 32 + 44),
-        "query_bwd": nv * (gather + 2 * L * 8 * 8 + 12 + 32 + 44 + 44 + 32),
-        "raster_fwd": K * 48 + P * 20,
-        "raster_bwd": K * 48 + P * 36 + nv * 36,
+        # vis id, position, both fields, explicit params (20 B), outputs (44 B)
+        "k_query_fwd_tc": nv * (4 + 12 + 2 * gather + 20 + 44),
+        "k_query_fwd": nv * (4 + 12 + 2 * gather + 20 + 44),
+        # vis id, position, geo gathers, dalpha/dscale/dquat, alpha_e/scale_e,
+        # d_alpha_e/d_scale_e and d_pos read-modify-write, scatter
+        "k_decoder_bwd_tc<GeoGauss>": nv * (4 + 12 + gather + 32 + 8 + 16 + 24 + scatter),
+        # vis id, position, rad gathers, dcolor, color_e, d_color_e and d_pos RMW, scatter
+        "k_decoder_bwd_tc<ColGauss>": nv * (4 + 12 + gather + 12 + 12 + 24 + 24 + scatter),
+        # rad gathers, T_final, dC, dT written, scatter
+        "k_decoder_bwd_tc<BgPixel>": P * (gather + 4 + 12 + 4 + scatter),
+        # rad gathers, C_fg and T_final read, C written
+        "k_bg_exact_fwd_tc": P * (gather + 12 + 4 + 12),
+        # 48-B record + 4-B id per instance, ranges, C_fg/T_final/n_contrib out
+        "k_raster_fwd": K * 52 + tiles * 8 + P * 20,
+        # as forward, plus dC/dT/T_final/n_contrib per pixel, 36-B grads RMW per Gaussian
+        "k_raster_bwd": K * 52 + tiles * 8 + P * 24 + nv * 72,
     }
 
 
@@ -220,6 +237,8 @@ def run_ours(args):
         step_ms = []
         if prec == precisions[0]:
             sampler.start()
+        H.hyrf_timer_read()
+        H.hyrf_timer_enable(True)
         t_wall = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1)
@@ -234,6 +253,8 @@ def run_ours(args):
                 ev[k].append(a.elapsed_time(b))
         t_wall = time.perf_counter() - t_wall
         launches = H.launch_count() - l0
+        H.hyrf_timer_enable(False)
+        ktimes = H.hyrf_timer_read()
         clocks = sampler.stop() if prec == precisions[0] else None
         st = H.read_status(r.status)
         nv = int(r.n_vis.item())
@@ -272,21 +293,29 @@ def run_ours(args):
             torch.cuda.synchronize()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
         stage_ms = {k: float(np.mean(v)) for k, v in ev.items() if v}
+        C = r.C.float()
+        psnr = float(-10.0 * torch.log10(((C - tgt) ** 2).mean()).item())
+        evals = int(r.n_contrib.sum().item())
         results[prec] = dict(ms=ms, fwd_ms=float(np.mean(fwd_ms)), e2e_ms=float(np.mean(e2e_ms)),
                              stage_ms=stage_ms, launches_per_step=launches / args.steps,
                              n_vis=nv, instances=K, status=st, clocks=clocks, wall_s=t_wall,
                              loss=float(r.loss.item()),
-                             h2d=int(pinned.numel() * 4), d2h=4,
-                             work=stage_work(r, m, nv, K, w.cams[0].width * w.cams[0].height,
-                                             prec == "bf16"))
+                             h2d=int(pinned.numel() * 4), d2h=4, psnr=psnr, evals=evals,
+                             kernels={k: (n / args.steps, t / n) for k, (n, t) in ktimes.items()},
+                             work=kernel_work(nv, K, w.cams[0].width * w.cams[0].height,
+                                              int(r.ranges.shape[0]), prec == "bf16"))
         del r, m
         torch.cuda.empty_cache()
     head = "bf16" if "bf16" in results and "ms" in results["bf16"] else "f32"
     R = results[head]
     value = ws * 1000.0 / R["ms"]
-    # dominant stage for the roofline
-    dom = max(R["stage_ms"], key=R["stage_ms"].get)
-    roof = roofline(dom, R, peaks, head)
+    roof = roofline(R, peaks, head)
+    per_step = {k: n * t for k, (n, t) in R["kernels"].items()}
+    tot = sum(per_step.values()) or 1.0
+    top = sorted(per_step, key=per_step.get, reverse=True)[:12]
+    kern = {k: {"ms_per_step": round(per_step[k], 4), "share": round(per_step[k] / tot, 4),
+                "launches_per_step": round(R["kernels"][k][0], 2)} for k in top}
+    rf = R["kernels"].get("k_raster_fwd")
     out = {"metric": METRIC, "value": round(value, 3), "unit": "iters/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(R["ms"], 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -297,6 +326,9 @@ def run_ours(args):
                       "parallelism": f"replicas x{ws}"},
            "render_fps": round(ws * 1000.0 / R["fwd_ms"], 2),
            "stage_ms": {k: round(v, 4) for k, v in R["stage_ms"].items()},
+           "kernels": kern,
+           "psnr_db": round(R["psnr"], 4),
+           "gaussian_pixel_evals_per_s": (round(R["evals"] / (rf[1] * 1e-3), 1) if rf else None),
            "e2e": {"value": round(ws * 1000.0 / R["e2e_ms"], 3), "unit": "iters/s",
                    "h2d_bytes_per_step": R["h2d"], "d2h_bytes_per_step": R["d2h"]},
            "gpu_launches": int(round(R["launches_per_step"] * args.steps)),
@@ -305,8 +337,11 @@ def run_ours(args):
         if p != head:
             out[f"{p}_path"] = ({"iters_per_s": round(1000.0 / v["ms"], 3),
                                  "render_fps": round(1000.0 / v["fwd_ms"], 2),
+                                 "psnr_db": round(v["psnr"], 4),
                                  "stage_ms": {k: round(x, 4) for k, x in v["stage_ms"].items()}}
                                 if "ms" in v else v)
+            if "psnr" in v:
+                out["delta_psnr_db"] = round(R["psnr"] - v["psnr"], 5)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_sample_s)
     if ws > 1:
@@ -316,21 +351,31 @@ def run_ours(args):
         print(json.dumps(out))
 
 
-def roofline(stage, R, peaks, prec):
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the named kernel on this workload; an entry is removed when
+# the kernel changes after its capture.
+NCU_TRAFFIC = {}
+
+
+def roofline(R, peaks, prec):
+    """Roofline of the kernel with the largest time per step, from the
+    library's own CUDA-event kernel timer over the timed region."""
     hbm = peaks.get("hbm_gbs")
-    peak_src = "of measured" if hbm else "of fallback"
+    src = "of measured" if hbm else "of fallback"
     hbm = hbm or 6800.0
-    work = R["work"]
-    kernel_of = {"query_bwd": "k_query_bwd", "query_fwd": "k_query_fwd", "raster_fwd": "k_raster_fwd",
-                 "raster_bwd": "k_raster_bwd"}
-    if stage in work:
-        gbs = work[stage] / (R["stage_ms"][stage] * 1e-3) / 1e9
-        return {"kernel": kernel_of.get(stage, stage), "bound": "hbm", "achieved": round(gbs, 1),
-                "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": None,
-                "peak_source": peak_src,
-                "note": "stage time (CUDA events around the C-ABI call) incl. its helper launches"}
-    return {"kernel": stage, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
-            "frac": None, "traffic": None}
+    per_step = {k: n * t for k, (n, t) in R["kernels"].items()}
+    if not per_step:
+        return {"kernel": None, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None}
+    k = max(per_step, key=per_step.get)
+    n, avg_ms = R["kernels"][k]
+    work = R["work"].get(k)
+    gbs = work / (avg_ms * 1e-3) / 1e9 if work else None
+    tr = NCU_TRAFFIC.get((k, prec))
+    return {"kernel": k, "bound": "hbm", "achieved": round(gbs, 1) if gbs else None, "peak": hbm,
+            "unit": "GB/s", "frac": round(gbs / hbm, 4) if gbs else None,
+            "traffic": tr, "algorithmic_bytes": work, "avg_launch_ms": round(avg_ms, 4),
+            "peak_source": src}
 
 
 # ---------------------------------------------------------------- oracle arm

@@ -401,6 +401,25 @@ const char* hyrf_error_string(int32_t status);
  * counter; for launch accounting in benchmarks). */
 uint64_t hyrf_launch_count(void);
 
+/* Kernel timer (measurement support; the paper has no counterpart). While
+ * enabled, every kernel launch of this library records a pair of CUDA events
+ * on its own launching stream around the launch; launches issued while that
+ * stream is being captured into a CUDA graph are not timed. The events are
+ * library-owned and reused. hyrf_timer_read waits for every recorded pair,
+ * writes at most `max_entries` per-kernel totals to `out` (host array owned
+ * by the caller; `name` points to a static string of the library), clears
+ * the totals and returns the number of distinct kernels seen (which may
+ * exceed max_entries). Timing adds two event records per launch. Not
+ * thread-safe against concurrent launches from other host threads while
+ * enabled or read. */
+typedef struct {
+  const char* name;
+  uint64_t launches;
+  double total_ms;
+} hyrf_kernel_time;
+void hyrf_timer_enable(int on);
+int hyrf_timer_read(hyrf_kernel_time* out, int max_entries);
+
 #ifdef __cplusplus
 }
 #endif

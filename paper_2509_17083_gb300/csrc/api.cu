@@ -1,6 +1,9 @@
 // extern "C" entry points of libhyrf (declared in include/hyrf.h): argument
 // checks on the host, workspace sizing and kernel dispatch.
 #include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -41,6 +44,68 @@ hyrf_status launch_loss(const hyrf_loss_args& a, void* ws, cudaStream_t s);
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- kernel timer
+namespace {
+struct TimedLaunch {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct KernelTotal {
+  const char* name;
+  uint64_t launches;
+  double ms;
+};
+std::atomic<bool> g_timer_on{false};
+std::mutex g_timer_mu;
+std::vector<TimedLaunch> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+std::vector<KernelTotal> g_totals;
+
+cudaEvent_t take_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+KernelTimer::KernelTimer(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  if (!g_timer_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  a_ = take_event();
+  b_ = take_event();
+  if (!a_ || !b_ || cudaEventRecord(a_, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (a_) g_free_events.push_back(a_);
+    if (b_) g_free_events.push_back(b_);
+    a_ = b_ = nullptr;
+  }
+}
+
+KernelTimer::~KernelTimer() {
+  if (!a_) return;
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  if (cudaEventRecord(b_, s_) != cudaSuccess) {
+    cudaGetLastError();
+    g_free_events.push_back(a_);
+    g_free_events.push_back(b_);
+    return;
+  }
+  g_pending.push_back({name_, a_, b_});
+}
 
 int num_sms() {
   static int sms = 0;
@@ -308,5 +373,36 @@ const char* hyrf_error_string(int32_t st) {
 }
 
 uint64_t hyrf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void hyrf_timer_enable(int on) { hyrf::g_timer_on.store(on != 0, std::memory_order_relaxed); }
+
+int hyrf_timer_read(hyrf_kernel_time* out, int max_entries) {
+  using namespace hyrf;
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  for (const TimedLaunch& t : g_pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.0f;
+    }
+    KernelTotal* k = nullptr;
+    for (KernelTotal& x : g_totals)
+      if (std::strcmp(x.name, t.name) == 0) k = &x;
+    if (!k) {
+      g_totals.push_back({t.name, 0, 0.0});
+      k = &g_totals.back();
+    }
+    k->launches += 1;
+    k->ms += ms;
+    g_free_events.push_back(t.a);
+    g_free_events.push_back(t.b);
+  }
+  g_pending.clear();
+  const int n = (int)g_totals.size();
+  for (int i = 0; out && i < n && i < max_entries; ++i)
+    out[i] = {g_totals[i].name, g_totals[i].launches, g_totals[i].ms};
+  g_totals.clear();
+  return n;
+}
 
 }  // extern "C"

@@ -95,6 +95,21 @@ struct Carver {
 
 int num_sms();
 
+// Records a CUDA event pair on `s` around the launches in its scope while the
+// kernel timer is enabled (hyrf_timer_enable); otherwise does nothing.
+class KernelTimer {
+ public:
+  KernelTimer(const char* name, cudaStream_t s);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 }  // namespace hyrf
 
 #define HYRF_LAUNCH_CHECK()                                 \
@@ -104,4 +119,15 @@ int num_sms();
       cudaGetLastError();                                   \
       return HYRF_ERR_CUDA;                                 \
     }                                                       \
+  } while (0)
+
+// One kernel launch (the variadic tail, so the launch may hold commas):
+// optionally timed under `name`, counted and checked.
+#define HYRF_LAUNCH(name, stream, ...)                      \
+  do {                                                      \
+    {                                                       \
+      ::hyrf::KernelTimer hyrf_kt_(name, stream);           \
+      __VA_ARGS__;                                          \
+    }                                                       \
+    HYRF_LAUNCH_CHECK();                                    \
   } while (0)

@@ -113,10 +113,15 @@ __device__ __forceinline__ void encode(const GridDev& G, const float y[3], float
 
 // Reverse of encode: scatter w_c * df into the float32 table gradient and,
 // if dy is given, accumulate dL/dy through the trilinear weights.
-template <int L>
+// COHERENT: the lanes of a warp hold neighbouring points (e.g. background
+// pixels of one image row), so at coarse levels they often share a corner;
+// when the whole warp targets one entry its contributions are summed with
+// shuffles and added by one atomic instead of 32 serialised ones.
+template <int L, bool COHERENT = false>
 __device__ __forceinline__ void encode_bwd(const GridDev& G, const float y[3], const float* df,
                                            float* __restrict__ gtab, float* dy) {
-#pragma unroll 1
+  const unsigned am = COHERENT ? __activemask() : 0u;
+#pragma unroll 2
   for (int l = 0; l < L; ++l) {
     uint32_t idx[8];
     float f[3];
@@ -127,8 +132,25 @@ __device__ __forceinline__ void encode_bwd(const GridDev& G, const float y[3], c
     for (int c = 0; c < 8; ++c) {
       const size_t e = (size_t)l * G.T + idx[c];
       const float w = corner_w(f, c);
-      if (gtab && (d0 != 0.0f || d1 != 0.0f))
-        atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(w * d0, w * d1));
+      if (gtab) {
+        float g0 = w * d0, g1 = w * d1;
+        bool done = false;
+        if (COHERENT && am == 0xffffffffu) {
+          const uint32_t e0 = __shfl_sync(am, idx[c], 0);
+          if (__all_sync(am, idx[c] == e0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              g0 += __shfl_xor_sync(am, g0, o);
+              g1 += __shfl_xor_sync(am, g1, o);
+            }
+            if ((threadIdx.x & 31) == 0 && (g0 != 0.0f || g1 != 0.0f))
+              atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+            done = true;
+          }
+        }
+        if (!done && (g0 != 0.0f || g1 != 0.0f))
+          atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+      }
       if (dy) {
         const float2 v = load_entry(G, e);
         const float dot = v.x * d0 + v.y * d1;

@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     if (ok) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
-      encode_bwd<NL>(F.rad, y, dx, g_rad_table, nullptr);
+      encode_bwd<NL, true>(F.rad, y, dx, g_rad_table, nullptr);
     }
   }
 }
@@ -683,26 +683,26 @@ SlabTargets slab_targets(const hyrf_field_grads& g, bool geo) {
 
 hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout& SL,
                                const SlabTargets& T, float scale, cudaStream_t s) {
-  k_slab_reduce<<<64, 256, 0, s>>>(slabs, nslabs, SL, T, scale);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_slab_reduce", s,
+              k_slab_reduce<<<64, 256, 0, s>>>(slabs, nslabs, SL, T, scale));
   return HYRF_OK;
 }
 
 hyrf_status launch_bg_map_fwd(const FieldsDev& F, const CamDev& cam, float radius, int Hb, int Wb,
                               const float* map, const float* C_fg, const float* T_final, float* C,
                               cudaStream_t s) {
-  k_bg_map_fwd<<<fwd_blocks((int64_t)cam.W * cam.H, 256), 256, 0, s>>>(F, cam, radius, Hb, Wb, map,
-                                                                      C_fg, T_final, C);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_bg_map_fwd", s,
+              k_bg_map_fwd<<<fwd_blocks((int64_t)cam.W * cam.H, 256), 256, 0, s>>>(F, cam, radius, Hb, Wb, map,
+                                                                      C_fg, T_final, C));
   return HYRF_OK;
 }
 
 hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float radius, int Hb, int Wb,
                                   const float* map, const float* T_final, const float* dC,
                                   float* dC_fg, float* dT, float* dmap, cudaStream_t s) {
-  k_bg_map_bwd_pix<<<fwd_blocks((int64_t)cam.W * cam.H, 256), 256, 0, s>>>(F, cam, radius, Hb, Wb, map,
-                                                                          T_final, dC, dC_fg, dT, dmap);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_bg_map_bwd_pix", s,
+              k_bg_map_bwd_pix<<<fwd_blocks((int64_t)cam.W * cam.H, 256), 256, 0, s>>>(F, cam, radius, Hb, Wb, map,
+                                                                          T_final, dC, dC_fg, dT, dmap));
   return HYRF_OK;
 }
 
@@ -803,8 +803,8 @@ static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const Q
   if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
     return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
   } else {
-    k_query_fwd<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(F, cam, io);
-    HYRF_LAUNCH_CHECK();
+    HYRF_LAUNCH("k_query_fwd", s,
+                k_query_fwd<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(F, cam, io));
     return HYRF_OK;
   }
 }
@@ -817,8 +817,8 @@ static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const Q
   cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
   const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
   set_smem(k_query_bwd<NL, WID, NH, WT>, smem);
-  k_query_bwd<NL, WID, NH, WT><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_query_bwd", s,
+              k_query_bwd<NL, WID, NH, WT><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs));
   return launch_slab_reduce(slabs, ctas, SL, slab_targets(grads, true), 1.0f / io.loss_scale, s);
 }
 
@@ -831,18 +831,18 @@ static hyrf_status bg_fwd_impl(const hyrf_composite_background_args& a, const Fi
     if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
       return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
     } else {
-      k_bg_exact_fwd<NL, WID, NH, WT><<<fwd_blocks(P, kFwdThreads), kFwdThreads, 0, s>>>(
-          F, cam, a.bg.radius, a.C_fg, a.T_final, a.C);
-      HYRF_LAUNCH_CHECK();
+      HYRF_LAUNCH("k_bg_exact_fwd", s,
+                  k_bg_exact_fwd<NL, WID, NH, WT><<<fwd_blocks(P, kFwdThreads), kFwdThreads, 0, s>>>(
+          F, cam, a.bg.radius, a.C_fg, a.T_final, a.C));
       return HYRF_OK;
     }
   }
   Carver c(ws);
   float* map = c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);
   const int nt = a.bg.map_h * a.bg.map_w;
-  k_bg_map_texels<NL, WID, NH, WT><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, a.bg.map_h, a.bg.map_w,
-                                                                        a.bg.radius, map);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_bg_map_texels", s,
+              k_bg_map_texels<NL, WID, NH, WT><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, a.bg.map_h, a.bg.map_w,
+                                                                        a.bg.radius, map));
   return launch_bg_map_fwd(F, cam, a.bg.radius, a.bg.map_h, a.bg.map_w, map, a.C_fg, a.T_final, a.C, s);
 }
 
@@ -866,23 +866,23 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
   const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
   if (a.bg.mode == 0) {
     set_smem(k_bg_field_bwd<NL, WID, NH, 0, WT>, smem);
-    k_bg_field_bwd<NL, WID, NH, 0, WT><<<ctas, kBwdThreads, smem, s>>>(
+    HYRF_LAUNCH("k_bg_field_bwd", s,
+                k_bg_field_bwd<NL, WID, NH, 0, WT><<<ctas, kBwdThreads, smem, s>>>(
         F, cam, a.bg.radius, 0, 0, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, nullptr,
-        b.grads.rad_table, b.loss_scale, SL, slabs);
-    HYRF_LAUNCH_CHECK();
+        b.grads.rad_table, b.loss_scale, SL, slabs));
   } else {
     const int nt = Hb * Wb;
-    k_bg_map_texels<NL, WID, NH, WT><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, Hb, Wb, a.bg.radius, map);
-    HYRF_LAUNCH_CHECK();
+    HYRF_LAUNCH("k_bg_map_texels", s,
+                k_bg_map_texels<NL, WID, NH, WT><<<fwd_blocks(nt, 128), 128, 0, s>>>(F, Hb, Wb, a.bg.radius, map));
     cudaMemsetAsync(dmap, 0, (size_t)nt * 3 * sizeof(float), s);
     hyrf_status st = launch_bg_map_bwd_pix(F, cam, a.bg.radius, Hb, Wb, map, a.T_final, b.d_C,
                                            b.d_C_fg, b.d_T_final, dmap, s);
     if (st != HYRF_OK) return st;
     set_smem(k_bg_field_bwd<NL, WID, NH, 1, WT>, smem);
-    k_bg_field_bwd<NL, WID, NH, 1, WT><<<ctas, kBwdThreads, smem, s>>>(
+    HYRF_LAUNCH("k_bg_field_bwd", s,
+                k_bg_field_bwd<NL, WID, NH, 1, WT><<<ctas, kBwdThreads, smem, s>>>(
         F, cam, a.bg.radius, Hb, Wb, nullptr, nullptr, nullptr, nullptr, dmap, b.grads.rad_table,
-        b.loss_scale, SL, slabs);
-    HYRF_LAUNCH_CHECK();
+        b.loss_scale, SL, slabs));
   }
   return launch_slab_reduce(slabs, ctas, SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
 }

@@ -318,8 +318,8 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
   int tiles = (a.n + 127) / 128;
   int grid = num_sms() * 2;
   if (tiles < grid) grid = tiles;
-  tc::k_query_fwd_tc<<<grid, 256, tc::kQuerySmem, s>>>(F, to_dev(a.cam), io);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_query_fwd_tc", s,
+              tc::k_query_fwd_tc<<<grid, 256, tc::kQuerySmem, s>>>(F, to_dev(a.cam), io));
   return HYRF_OK;
 }
 
@@ -331,9 +331,9 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
   int tiles = (P + 127) / 128;
   int grid = num_sms() * 4;
   if (tiles < grid) grid = tiles;
-  tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, a.C_fg, a.T_final, a.C,
-                                                       a.status);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_bg_exact_fwd_tc", s,
+              tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, a.C_fg, a.T_final, a.C,
+                                                       a.status));
   return HYRF_OK;
 }
 

@@ -73,6 +73,7 @@ struct GaussP {
 // (alpha_n, s_n[3], r_n[4]).
 struct GeoGauss {
   static constexpr int IN = 32, OUT = 8, DEC = 0;
+  static constexpr const char* kName = "k_decoder_bwd_tc<GeoGauss>";
   using Params = GaussP;
   struct Row {
     int i, g;
@@ -148,6 +149,7 @@ struct GeoGauss {
 struct ColGauss {
   static constexpr int IN = 64, OUT = 3, DEC = 1;
   using Params = GaussP;
+  static constexpr const char* kName = "k_decoder_bwd_tc<ColGauss>";
   struct Row {
     int g;
     bool ok;
@@ -222,6 +224,7 @@ struct PixelP {
 struct BgPixel {
   static constexpr int IN = 64, OUT = 3, DEC = 1;
   using Params = PixelP;
+  static constexpr const char* kName = "k_decoder_bwd_tc<BgPixel>";
   struct Row {
     int p;
     bool ok;
@@ -261,7 +264,7 @@ struct BgPixel {
   __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
                                 const float* dx) {
     if (!R.ok) return;
-    encode_bwd<16>(F.rad, R.y, dx, P.g_rad_table, nullptr);
+    encode_bwd<16, true>(F.rad, R.y, dx, P.g_rad_table, nullptr);
   }
 };
 
@@ -507,8 +510,8 @@ static hyrf_status launch_dec_bwd(const typename S::Params& P, const FieldsDev& 
                                   cudaStream_t s) {
   constexpr int smem = tc::BwdSmem<S::IN>::SIZE;
   cudaFuncSetAttribute(tc::k_decoder_bwd_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 128, smem, s>>>(P, F, cam, ls, SL, slabs, status);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH(S::kName, s,
+              tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 128, smem, s>>>(P, F, cam, ls, SL, slabs, status));
   return HYRF_OK;
 }
 

@@ -276,12 +276,12 @@ hyrf_status launch_precull(const CamDev& cam, const float* pos, int n, int32_t* 
     cudaMemsetAsync(n_vis, 0, sizeof(int32_t), s);
     return cudaPeekAtLastError() == cudaSuccess ? HYRF_OK : HYRF_ERR_CUDA;
   }
-  k_precull_count<<<chunks, 256, 0, s>>>(cam, pos, n, counts);
-  HYRF_LAUNCH_CHECK();
-  k_scan_small<<<1, 1024, 0, s>>>(counts, chunks, n_vis);
-  HYRF_LAUNCH_CHECK();
-  k_precull_scatter<<<chunks, 256, 0, s>>>(cam, pos, n, counts, vis_ids);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_precull_count", s,
+              k_precull_count<<<chunks, 256, 0, s>>>(cam, pos, n, counts));
+  HYRF_LAUNCH("k_scan_small", s,
+              k_scan_small<<<1, 1024, 0, s>>>(counts, chunks, n_vis));
+  HYRF_LAUNCH("k_precull_scatter", s,
+              k_precull_scatter<<<chunks, 256, 0, s>>>(cam, pos, n, counts, vis_ids));
   return HYRF_OK;
 }
 
@@ -294,8 +294,8 @@ hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int
   ProjOut o{mean2d, conic, depth, rect, ntiles, flag};
   int blocks = (n + 255) / 256;
   blocks = blocks < num_sms() * 8 ? blocks : num_sms() * 8;
-  k_project<<<blocks, 256, 0, s>>>(cam, n, pos, vis_ids, n_vis, scale, quat, TX, TY, o, status);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_project", s,
+              k_project<<<blocks, 256, 0, s>>>(cam, n, pos, vis_ids, n_vis, scale, quat, TX, TY, o, status));
   return HYRF_OK;
 }
 

@@ -131,20 +131,20 @@ hyrf_status launch_loss(const hyrf_loss_args& a, void* ws, cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   if (blocks < 1) blocks = 1;
-  k_l1<<<blocks, 256, 0, s>>>(a.C, a.target, n, 1.0f - a.lambda, a.grad_scale, a.loss, a.d_C);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_l1", s,
+              k_l1<<<blocks, 256, 0, s>>>(a.C, a.target, n, 1.0f - a.lambda, a.grad_scale, a.loss, a.d_C));
   if (a.lambda != 0.0f) {
     Carver c(ws);
     float* dmu = c.take<float>(n);
     float* dsxx = c.take<float>(n);
     float* dsxy = c.take<float>(n);
-    k_ssim_maps<<<blocks, 256, 0, s>>>(a.C, a.target, a.width, a.height, a.lambda, a.loss, dmu, dsxx,
-                                       dsxy);
-    HYRF_LAUNCH_CHECK();
+    HYRF_LAUNCH("k_ssim_maps", s,
+                k_ssim_maps<<<blocks, 256, 0, s>>>(a.C, a.target, a.width, a.height, a.lambda, a.loss, dmu, dsxx,
+                                       dsxy));
     if (a.d_C) {
-      k_ssim_grad<<<blocks, 256, 0, s>>>(a.C, a.target, a.width, a.height,
-                                         -a.lambda * a.grad_scale / (float)n, dmu, dsxx, dsxy, a.d_C);
-      HYRF_LAUNCH_CHECK();
+      HYRF_LAUNCH("k_ssim_grad", s,
+                  k_ssim_grad<<<blocks, 256, 0, s>>>(a.C, a.target, a.width, a.height,
+                                         -a.lambda * a.grad_scale / (float)n, dmu, dsxx, dsxy, a.d_C));
     }
   }
   return HYRF_OK;

@@ -152,10 +152,10 @@ hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t
   if (a.n == 0) return HYRF_OK;
   int blocks = (a.n + 255) / 256;
   if (blocks > num_sms() * 8) blocks = num_sms() * 8;
-  k_project_bwd<<<blocks, 256, 0, s>>>(to_dev(a.cam), a.n, a.pos, a.vis_ids, a.n_vis, a.scale,
+  HYRF_LAUNCH("k_project_bwd", s,
+              k_project_bwd<<<blocks, 256, 0, s>>>(to_dev(a.cam), a.n, a.pos, a.vis_ids, a.n_vis, a.scale,
                                        a.quat, a.d_mean2d, a.d_conic, a.d_pos, a.d_scale,
-                                       a.d_quat, a.status);
-  HYRF_LAUNCH_CHECK();
+                                       a.d_quat, a.status));
   return HYRF_OK;
 }
 

@@ -234,8 +234,8 @@ static hyrf_status pack(const hyrf_rasterize_args& a, float4* rec, cudaStream_t 
   int blocks = (a.n + 255) / 256;
   if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   if (blocks < 1) blocks = 1;
-  k_pack<<<blocks, 256, 0, s>>>(a.n_vis, a.n, a.mean2d, a.conic, a.alpha, a.color, rec);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_pack", s,
+              k_pack<<<blocks, 256, 0, s>>>(a.n_vis, a.n, a.mean2d, a.conic, a.alpha, a.color, rec));
   return HYRF_OK;
 }
 
@@ -245,9 +245,9 @@ hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream
   float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
-  k_raster_fwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.C_fg,
-                                       a.T_final, a.n_contrib, a.status);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_raster_fwd", s,
+              k_raster_fwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.C_fg,
+                                       a.T_final, a.n_contrib, a.status));
   return HYRF_OK;
 }
 
@@ -258,10 +258,10 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
-  k_raster_bwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
+  HYRF_LAUNCH("k_raster_bwd", s,
+              k_raster_bwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
                                        a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
-                                       b.d_alpha, b.d_color);
-  HYRF_LAUNCH_CHECK();
+                                       b.d_alpha, b.d_color));
   return HYRF_OK;
 }
 

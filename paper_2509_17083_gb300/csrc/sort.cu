@@ -370,13 +370,13 @@ static hyrf_status radix_sort(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* 
     const int shift = 8 * p;
     const int bits = nbits - shift < 8 ? nbits - shift : 8;
     const uint32_t mask = (1u << bits) - 1u;
-    k_radix_hist<<<G, kRT, 0, s>>>(src_k, n_ptr, cap, shift, mask, hist);
-    HYRF_LAUNCH_CHECK();
-    k_radix_colscan<<<256, kRT, 0, s>>>(hist, G, totals);
-    HYRF_LAUNCH_CHECK();
-    k_radix_scatter<<<G, kRT, 0, s>>>(src_k, src_v, dst_k, dst_v, n_ptr, cap, shift, mask, hist,
-                                      totals);
-    HYRF_LAUNCH_CHECK();
+    HYRF_LAUNCH("k_radix_hist", s,
+                k_radix_hist<<<G, kRT, 0, s>>>(src_k, n_ptr, cap, shift, mask, hist));
+    HYRF_LAUNCH("k_radix_colscan", s,
+                k_radix_colscan<<<256, kRT, 0, s>>>(hist, G, totals));
+    HYRF_LAUNCH("k_radix_scatter", s,
+                k_radix_scatter<<<G, kRT, 0, s>>>(src_k, src_v, dst_k, dst_v, n_ptr, cap, shift, mask, hist,
+                                      totals));
     uint32_t* tk = src_k;
     src_k = dst_k;
     dst_k = tk;
@@ -400,34 +400,34 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   }
   // 1. depth keys of the visible Gaussians, sorted (4 x 8 bits)
   const int eb = (n + 255) / 256 < num_sms() * 8 ? (n + 255) / 256 : num_sms() * 8;
-  k_depth_keys<<<eb, 256, 0, s>>>(a.depth, a.n_vis, n, w.dk_a, w.dv_a);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_depth_keys", s,
+              k_depth_keys<<<eb, 256, 0, s>>>(a.depth, a.n_vis, n, w.dk_a, w.dv_a));
   hyrf_status st = radix_sort(w.dk_a, w.dv_a, w.dk_b, w.dv_b, a.n_vis, n, 32, w.hist, w.totals, s);
   if (st != HYRF_OK) return st;
   // 2. instance offsets in depth order, K, and emission
   const int sc = (n + kScanChunk - 1) / kScanChunk;
-  k_count_sums<<<sc, 256, 0, s>>>(a.ntiles, w.dv_a, a.n_vis, n, w.sums);
-  HYRF_LAUNCH_CHECK();
-  k_scan_sums<<<1, 1024, 0, s>>>(w.sums, sc, cap, a.n_instances, a.status);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_count_sums", s,
+              k_count_sums<<<sc, 256, 0, s>>>(a.ntiles, w.dv_a, a.n_vis, n, w.sums));
+  HYRF_LAUNCH("k_scan_sums", s,
+              k_scan_sums<<<1, 1024, 0, s>>>(w.sums, sc, cap, a.n_instances, a.status));
   const int tbits = bits_for(n_tiles);
   const int tpasses = (tbits + 7) / 8;
   uint32_t* emit_k = (tpasses & 1) ? w.tk_b : w.tk_a;
   int32_t* emit_v = (tpasses & 1) ? w.tv_b : a.vals;
-  k_emit<<<sc, 256, 0, s>>>(a.ntiles, a.rect, w.dv_a, a.n_vis, n, w.sums, a.tiles_x, cap, emit_k,
-                            emit_v);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_emit", s,
+              k_emit<<<sc, 256, 0, s>>>(a.ntiles, a.rect, w.dv_a, a.n_vis, n, w.sums, a.tiles_x, cap, emit_k,
+                            emit_v));
   // 3. stable sort of the instances on their tile bits
   const int capi = (int)(cap < 0x7fffffff ? cap : 0x7fffffff);
   st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s);
   if (st != HYRF_OK) return st;
   // 4. per-tile ranges and (optionally) the composed 64-bit keys
   const int kb = (int)((cap + 255) / 256 < num_sms() * 8 ? (cap + 255) / 256 : num_sms() * 8);
-  k_ranges<<<kb, 256, 0, s>>>(w.tk_a, a.n_instances, capi, n_tiles, a.ranges);
-  HYRF_LAUNCH_CHECK();
+  HYRF_LAUNCH("k_ranges", s,
+              k_ranges<<<kb, 256, 0, s>>>(w.tk_a, a.n_instances, capi, n_tiles, a.ranges));
   if (a.keys) {
-    k_keys64<<<kb, 256, 0, s>>>(w.tk_a, a.vals, a.depth, a.n_instances, capi, a.keys);
-    HYRF_LAUNCH_CHECK();
+    HYRF_LAUNCH("k_keys64", s,
+                k_keys64<<<kb, 256, 0, s>>>(w.tk_a, a.vals, a.depth, a.n_instances, capi, a.keys));
   }
   return HYRF_OK;
 }

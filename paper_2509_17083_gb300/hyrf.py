@@ -169,6 +169,10 @@ def lib():
         L.hyrf_bin_sort_noalloc.restype = C.c_int32
         L.hyrf_launch_count.argtypes = []
         L.hyrf_launch_count.restype = C.c_uint64
+        L.hyrf_timer_enable.argtypes = [C.c_int]
+        L.hyrf_timer_enable.restype = None
+        L.hyrf_timer_read.argtypes = [C.POINTER(hyrf_kernel_time), C.c_int]
+        L.hyrf_timer_read.restype = C.c_int
         _lib = L
     return _lib
 
@@ -234,6 +238,24 @@ def error_string(st):
 
 def launch_count():
     return int(lib().hyrf_launch_count())
+
+
+class hyrf_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+def hyrf_timer_enable(on=True):
+    """Time every kernel launch of the library with CUDA events on its stream."""
+    lib().hyrf_timer_enable(1 if on else 0)
+
+
+def hyrf_timer_read(max_entries=256):
+    """Per-kernel totals since the last read: {name: (launches, total_ms)}; waits
+    for the recorded events and clears the totals."""
+    buf = (hyrf_kernel_time * max_entries)()
+    n = lib().hyrf_timer_read(buf, max_entries)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(min(n, max_entries))}
 
 
 # ---------------------------------------------------------------- struct builders

@@ -321,3 +321,29 @@ def test_loss_matches_oracle(lib, lam):
     L, g = oracle.loss(x, y, lam)
     assert abs(float(loss.item()) - L) < 1e-5 * max(1, abs(L))
     assert rel_l2(np_(dC), g) < TOL_GRAD_F32
+
+
+# ------------------------------------------------------------------ kernel timer
+
+def test_kernel_timer_counts_each_launch(lib):
+    w = _cfg("c1")
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg)
+    r.forward()
+    torch.cuda.synchronize()
+    H.hyrf_timer_read()                      # clear
+    H.hyrf_timer_enable(True)
+    l0 = H.launch_count()
+    try:
+        r.forward()
+    finally:
+        H.hyrf_timer_enable(False)
+    launched = H.launch_count() - l0
+    t = H.hyrf_timer_read()
+    assert sum(n for n, _ in t.values()) == launched
+    assert t["k_raster_fwd"][0] == 1 and t["k_project"][0] == 1
+    assert all(ms >= 0.0 for _, ms in t.values())
+    assert H.hyrf_timer_read() == {}         # totals were cleared
+    r.forward()                              # disabled: nothing recorded
+    torch.cuda.synchronize()
+    assert H.hyrf_timer_read() == {}
