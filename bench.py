@@ -111,19 +111,30 @@ def kernel_work(nv, K, P, tiles, bf16):
     ent = 4 if bf16 else 8                     # bytes per 2-feature table entry
     gather = L * 8 * ent                       # one field, 8 corners per level
     scatter = L * 8 * 8                        # one field, float2 atomic per corner
+    feat, dfeat = 64, 128                      # bf16 features / f32 gradients per row and field
     return {
-        # vis id, position, both fields, explicit params (20 B), outputs (44 B)
-        "k_query_fwd_tc": nv * (4 + 12 + 2 * gather + 20 + 44),
+        # FP32 fused field kernels: vis id, position, both fields, explicit
+        # params (20 B), outputs (44 B)
         "k_query_fwd": nv * (4 + 12 + 2 * gather + 20 + 44),
-        # vis id, position, geo gathers, dalpha/dscale/dquat, alpha_e/scale_e,
-        # d_alpha_e/d_scale_e and d_pos read-modify-write, scatter
-        "k_decoder_bwd_tc<GeoGauss>": nv * (4 + 12 + gather + 32 + 8 + 16 + 24 + scatter),
-        # vis id, position, rad gathers, dcolor, color_e, d_color_e and d_pos RMW, scatter
-        "k_decoder_bwd_tc<ColGauss>": nv * (4 + 12 + gather + 12 + 12 + 24 + 24 + scatter),
-        # rad gathers, T_final, dC, dT written, scatter
-        "k_decoder_bwd_tc<BgPixel>": P * (gather + 4 + 12 + 4 + scatter),
-        # rad gathers, C_fg and T_final read, C written
-        "k_bg_exact_fwd_tc": P * (gather + 12 + 4 + 12),
+        # BF16 split path. gather: vis id, position, 8 corners x 16 levels per
+        # field, features written
+        "k_gather<gaussians>": nv * (4 + 12 + 2 * (gather + feat)),
+        "k_gather<pixels>": P * (gather + feat),
+        # decoders on the tensor cores: features in, outputs / gradients out
+        "k_query_fwd_tc": nv * (4 + 12 + 2 * feat + 20 + 44),
+        "k_bg_exact_fwd_tc": P * (feat + 12 + 4 + 12),
+        # vis id, features, dalpha/dscale/dquat, alpha_e/scale_e, their
+        # gradients read-modify-write, feature gradients out
+        "k_decoder_bwd_tc<GeoGauss>": nv * (4 + feat + 32 + 8 + 16 + dfeat),
+        # vis id, features, position, dcolor, color_e, d_color_e and d_pos RMW,
+        # feature gradients out
+        "k_decoder_bwd_tc<ColGauss>": nv * (4 + feat + 12 + 12 + 12 + 24 + 24 + dfeat),
+        # features, T_final, dC, dT out, feature gradients out
+        "k_decoder_bwd_tc<BgPixel>": P * (feat + 4 + 12 + 4 + dfeat),
+        # scatter: feature gradients in, float2 atomics, corner values re-read
+        # for dL/dp (Gaussians), d_pos RMW
+        "k_scatter<gaussians>": nv * (4 + 12 + 2 * (dfeat + scatter + gather) + 24),
+        "k_scatter<pixels>": P * (dfeat + scatter),
         # 48-B record + 4-B id per instance, ranges, C_fg/T_final/n_contrib out
         "k_raster_fwd": K * 52 + tiles * 8 + P * 20,
         # as forward, plus dC/dT/T_final/n_contrib per pixel, 36-B grads RMW per Gaussian
@@ -191,7 +202,7 @@ def run_ours(args):
             H.hyrf_query_fields(ws=r.ws["q"], n=m.n, pos=m.pos, alpha_e=m.alpha_e,
                                 scale_e=m.scale_e, color_e=m.color_e, cam=r.ccam, fields=fs,
                                 vis_ids=r.vis_ids, n_vis=r.n_vis, alpha=r.alpha, scale=r.scale,
-                                quat=r.quat, color=r.color, status=r.status)
+                                quat=r.quat, color=r.color, status=r.status, features=r.feat_q)
             mark("query_fwd"); mark("project_fwd")
             r.project()
             mark("project_fwd"); mark("bin_sort")
@@ -224,7 +235,8 @@ def run_ours(args):
                                          d_color=r.d_color, d_pos=m.grad["pos"],
                                          d_alpha_e=m.grad["alpha_e"], d_scale_e=m.grad["scale_e"],
                                          d_color_e=m.grad["color_e"], grads=g,
-                                         loss_scale=r.loss_scale, status=r.status)
+                                         loss_scale=r.loss_scale, status=r.status,
+                                         features=r.feat_q)
             mark("query_bwd")
             return evs
 
@@ -237,8 +249,6 @@ def run_ours(args):
         step_ms = []
         if prec == precisions[0]:
             sampler.start()
-        H.hyrf_timer_read()
-        H.hyrf_timer_enable(True)
         t_wall = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1)
@@ -253,6 +263,14 @@ def run_ours(args):
                 ev[k].append(a.elapsed_time(b))
         t_wall = time.perf_counter() - t_wall
         launches = H.launch_count() - l0
+        # the same steps again with the library's kernel timer on (CUDA events
+        # around every launch, on its stream): per-kernel durations
+        H.hyrf_timer_read()
+        H.hyrf_timer_enable(True)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            timed_step(False)
+        torch.cuda.synchronize()
         H.hyrf_timer_enable(False)
         ktimes = H.hyrf_timer_read()
         clocks = sampler.stop() if prec == precisions[0] else None

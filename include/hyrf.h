@@ -136,6 +136,12 @@ typedef struct {
   float* quat;               /* out [V][4] r_n / |r_n|, (w, x, y, z) */
   float* color;              /* out [V][3] sigma(c_n + c_e) */
   int32_t* status;           /* optional device status word */
+  /* Optional out, BF16 fields only (must be NULL for float32 fields):
+   * [2][N][32] bf16, 16-byte aligned, caller-owned. Row i of block 0 / 1
+   * receives the geometry / radiance hash features (Eq. 3) of visible
+   * Gaussian i. Passing the buffer on to hyrf_query_fields_backward saves
+   * that call the gather (memory for time; NULL: the backward gathers). */
+  void* features;
 } hyrf_query_fields_args;
 
 size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a);
@@ -169,6 +175,10 @@ typedef struct {
   hyrf_field_grads grads;    /* accumulate */
   float loss_scale;
   int32_t* status;
+  /* Optional, BF16 fields only: the `features` buffer filled by the forward
+   * call of the same view, with the tables unchanged since; NULL: the hash
+   * features are gathered again. */
+  const void* features;
 } hyrf_query_fields_backward_args;
 
 size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a);
@@ -349,6 +359,12 @@ typedef struct {
   const float* T_final;      /* [H][W] */
   float* C;                  /* out [H][W][3] */
   int32_t* status;
+  /* Optional, mode 0 with BF16 fields only (NULL otherwise): [H*W][32]
+   * bf16, 16-byte aligned, caller-owned. The forward writes the radiance
+   * hash features of every pixel's sphere hit; the backward, which gets
+   * these arguments as `fwd`, reads them instead of gathering again (the
+   * buffer must still hold the forward's values). */
+  void* features;
 } hyrf_composite_background_args;
 
 size_t hyrf_composite_background_workspace_size(const hyrf_composite_background_args* a);

@@ -26,6 +26,7 @@ UNITS = {
     "fields3": ("fields.cu", ["-DHYRF_FIELDS_PART=3"]),
     "fields_tc": ("fields_tc.cu", []),
     "fields_tc_bwd": ("fields_tc_bwd.cu", []),
+    "gather": ("gather.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
     "noalloc": ("noalloc.cu", []),

@@ -19,8 +19,10 @@ hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int
                            int32_t* status, cudaStream_t s);
 hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t s);
 hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
-hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
-hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F,
+hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s);
+size_t tc_fwd_feature_bytes(int64_t rows, int fields);
+size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features);
+hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
                                    cudaStream_t s);
 hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
                              cudaStream_t s);
@@ -148,7 +150,10 @@ extern "C" {
 // ------------------------------------------------------------------ query fields
 
 size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a) {
-  return a ? precull_workspace(a->n) : 0;
+  if (!a || a->n < 0) return 0;
+  FieldsDev F;
+  const bool tc = make_fields(a->fields, F, true) && F.cm.bf16;
+  return align_up(precull_workspace(a->n)) + (tc && !a->features ? tc_fwd_feature_bytes(a->n, 2) : 0);
 }
 
 hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t ws_bytes,
@@ -164,17 +169,18 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
     return HYRF_ERR_UNSUPPORTED;
   if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
+  if (a->features && (!F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
   if (st != HYRF_OK) return st;
   // BF16 decoders run on the tensor cores, FP32 decoders on the CUDA cores
-  return F.cm.bf16 ? launch_query_fwd_tc(*a, F, S(stream)) : launch_query_fwd(*a, F, S(stream));
+  return F.cm.bf16 ? launch_query_fwd_tc(*a, F, ws, S(stream)) : launch_query_fwd(*a, F, S(stream));
 }
 
 size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a) {
   if (!a) return 0;
   FieldsDev F;
-  if (!make_fields(a->fields, F, true)) return 0;
-  return align_up(slab_bytes(F, true));
+  if (!make_fields(a->fields, F, true) || a->n < 0) return 0;
+  return F.cm.bf16 ? tc_bwd_workspace(F, true, a->n, a->features != nullptr) : align_up(slab_bytes(F, true));
 }
 
 hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a, void* ws,
@@ -190,6 +196,7 @@ hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a,
     return HYRF_ERR_UNSUPPORTED;
   if (!ws_ok(ws, ws_bytes, hyrf_query_fields_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
   if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
+  if (a->features && (!F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   return F.cm.bf16 ? launch_query_bwd_tc(*a, F, ws, S(stream)) : launch_query_bwd(*a, F, ws, S(stream));
 }
 
@@ -300,6 +307,7 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
   if (a->bg.mode != 0 && a->bg.mode != 1) return HYRF_ERR_INVALID_ARG;
   if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
   if (F.cm.bf16 && a->fields.rad.n_levels != 16) return HYRF_ERR_UNSUPPORTED;
+  if (a->features && (a->bg.mode != 0 || !F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   return HYRF_OK;
 }
 
@@ -316,7 +324,7 @@ hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, v
   if (st != HYRF_OK) return st;
   if (!a->C || !ws_ok(ws, ws_bytes, bg_workspace(*a, F, false))) return HYRF_ERR_INVALID_ARG;
   if (!bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
-  if (a->bg.mode == 0 && F.cm.bf16) return launch_bg_exact_fwd_tc(*a, F, S(stream));
+  if (a->bg.mode == 0 && F.cm.bf16) return launch_bg_exact_fwd_tc(*a, F, ws, S(stream));
   return launch_bg_fwd(*a, F, ws, S(stream));
 }
 

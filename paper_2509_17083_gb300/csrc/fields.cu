@@ -706,7 +706,15 @@ hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float r
   return HYRF_OK;
 }
 
+size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features);
+size_t tc_fwd_feature_bytes(int64_t rows, int fields);
+
 size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward) {
+  if (a.bg.mode == 0 && F.cm.bf16) {  // tensor-core path: gathered features (+ gradients)
+    const int64_t P = (int64_t)a.cam.width * a.cam.height;
+    const bool have = a.features != nullptr;
+    return backward ? tc_bwd_workspace(F, false, P, have) : (have ? 0 : tc_fwd_feature_bytes(P, 1));
+  }
   Carver c(nullptr);
   if (a.bg.mode == 1) {
     c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);  // map

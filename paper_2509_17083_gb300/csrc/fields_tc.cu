@@ -1,8 +1,9 @@
 // BF16 field query and background forward with the decoders (Eqs. 4, 6) on
 // the 5th-generation tensor cores. A CTA owns a tile of 128 points (the MMA
-// M dimension): every thread gathers one point's hash features (Eq. 3),
-// converts them to bf16 and writes its row of the A operand into shared
-// memory; one thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32) per
+// M dimension): every thread copies one point's bf16 hash features (Eq. 3,
+// gathered by k_gather in gather.cu) and, for the colour decoder, its
+// positional encoding into its row of the A operand in shared memory; one
+// thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32) per
 // layer with the weights staged once per CTA as the B operand; the f32
 // accumulators live in tensor memory and come back with tcgen05.ld for the
 // bias + ReLU epilogue, which writes the next layer's bf16 A operand.
@@ -30,6 +31,8 @@ struct QueryIO {
   const float* color_e;
   const int32_t* vis_ids;
   const int32_t* n_vis;
+  const uint32_t* Xg;   // [n_vis][32] bf16 geometry features (k_gather)
+  const uint32_t* Xr;   // [n_vis][32] bf16 radiance features
   float* alpha;
   float* scale;
   float* quat;
@@ -103,24 +106,19 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
       set_status(io.status, HYRF_ERR_BOUNDS);
       ok = false;
     }
-    float p[3];
+    if (geo) {
+      load_row32<32>(sm + oAg, r, io.Xg + (size_t)i * 16, ok);
+    } else {
+      load_row32<64>(sm + oAc, r, io.Xr + (size_t)i * 16, ok);
+      float p[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];
-    float y[3];
-    contract_p(F, p, y, nullptr);
-    {
-      float f[64];
-      if (geo) {
-        encode<16>(F.geo, y, f);
-        store_row<32>(sm + oAg, r, f);
-      } else {
-        encode<16>(F.rad, y, f);
-        float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
-        const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
-        pos_enc(dir, f + 32);
-        store_row<64>(sm + oAc, r, f);
-      }
+      for (int k = 0; k < 3; ++k) p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];
+      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+      const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+      float pe[32];
+      pos_enc(dir, pe);
+      store_cols<64, 32, 32>(sm + oAc, r, pe);
     }
     fence_smem_async();
     fence_before();
@@ -202,6 +200,7 @@ constexpr int bW0c = 0, bW1c = bW0c + 64 * 64 * 2, bW2c = bW1c + 64 * 64 * 2, bA
 constexpr uint32_t kBgTmemCols = 128;
 
 __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
+                                                           const uint32_t* __restrict__ Xb,
                                                            const float* __restrict__ C_fg,
                                                            const float* __restrict__ T_final,
                                                            float* __restrict__ C, int32_t* status) {
@@ -243,12 +242,11 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
     const bool ok = p < P;
     const int pp = ok ? p : 0;
     {
-      float ps[3], dir[3], y[3], f[64];
+      load_row32<64>(sm + bAc, t, Xb + (size_t)pp * 16, ok);
+      float ps[3], dir[3], pe[32];
       bg_ray(cam, F, radius, pp % cam.W, pp / cam.W, ps, dir);
-      contract_n(ps, y);
-      encode<16>(F.rad, y, f);
-      pos_enc(dir, f + 32);
-      store_row<64>(sm + bAc, t, f);
+      pos_enc(dir, pe);
+      store_cols<64, 32, 32>(sm + bAc, t, pe);
     }
     fence_smem_async();
     fence_before();
@@ -310,30 +308,47 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
 
 // ---------------------------------------------------------------- launchers
 
-hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s) {
-  tc::QueryIO io{a.n,     a.pos,   a.alpha_e, a.scale_e, a.color_e, a.vis_ids,
-                 a.n_vis, a.alpha, a.scale,   a.quat,    a.color,   a.status};
+size_t precull_workspace(int n);
+
+// Workspace of the BF16 forward calls beyond their own: bf16 features of
+// `rows` rows for `fields` fields.
+size_t tc_fwd_feature_bytes(int64_t rows, int fields) { return align_up((size_t)fields * rows * 64); }
+
+hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s) {
   if (a.n == 0) return HYRF_OK;
+  Carver c(ws);
+  c.take<char>(precull_workspace(a.n));
+  uint32_t* X = a.features ? static_cast<uint32_t*>(a.features) : c.take<uint32_t>((size_t)2 * a.n * 16);
+  uint32_t *Xg = X, *Xr = X + (size_t)a.n * 16;
+  const CamDev cam = to_dev(a.cam);
+  const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status};
+  hyrf_status st = launch_gather(F, cam, RS, a.n, Xg, Xr, s);
+  if (st != HYRF_OK) return st;
+  tc::QueryIO io{a.n,     a.pos, a.alpha_e, a.scale_e, a.color_e, a.vis_ids, a.n_vis,
+                 Xg,      Xr,    a.alpha,   a.scale,   a.quat,    a.color,   a.status};
   cudaFuncSetAttribute(tc::k_query_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kQuerySmem);
   int tiles = (a.n + 127) / 128;
   int grid = num_sms() * 2;
   if (tiles < grid) grid = tiles;
-  HYRF_LAUNCH("k_query_fwd_tc", s,
-              tc::k_query_fwd_tc<<<grid, 256, tc::kQuerySmem, s>>>(F, to_dev(a.cam), io));
+  HYRF_LAUNCH("k_query_fwd_tc", s, tc::k_query_fwd_tc<<<grid, 256, tc::kQuerySmem, s>>>(F, cam, io));
   return HYRF_OK;
 }
 
-hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F,
+hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
                                    cudaStream_t s) {
   const CamDev cam = to_dev(a.cam);
-  cudaFuncSetAttribute(tc::k_bg_exact_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kBgSmem);
   const int P = cam.W * cam.H;
+  uint32_t* Xb = static_cast<uint32_t*>(a.features ? a.features : ws);
+  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status};
+  hyrf_status st = launch_gather(F, cam, RS, P, nullptr, Xb, s);
+  if (st != HYRF_OK) return st;
+  cudaFuncSetAttribute(tc::k_bg_exact_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kBgSmem);
   int tiles = (P + 127) / 128;
   int grid = num_sms() * 4;
   if (tiles < grid) grid = tiles;
   HYRF_LAUNCH("k_bg_exact_fwd_tc", s,
-              tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, a.C_fg, a.T_final, a.C,
-                                                       a.status));
+              tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, a.C_fg, a.T_final,
+                                                                  a.C, a.status));
   return HYRF_OK;
 }
 

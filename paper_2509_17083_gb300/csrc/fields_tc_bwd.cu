@@ -1,30 +1,52 @@
 // Reverse of the BF16 decoders (Eqs. 4, 6) and of the aggregation (Eq. 7)
-// on the tensor cores. One CTA of 128 threads owns a tile of 128 points (one
+// on the tensor cores. One CTA of 128 threads owns a tile of 128 rows (one
 // per thread, the MMA M dimension) and one decoder:
 //
+//   X = bf16 hash features of the rows (written by k_gather, gather.cu)
 //   forward recompute  X -> H1 -> H2 -> O          (K-major A, K-major B)
 //   dZ2 = reverse of Eq. 7 (or of Eq. 10 for background pixels), x loss scale
 //   dH2 = dZ2 W2,  dW2 += dZ2^T H2                  (B MN-major; A and B MN-major)
 //   dZ1 = dH2 * [H2 > 0] -> dH1 = dZ1 W1, dW1 += dZ1^T H1
 //   dZ0 = dH1 * [H1 > 0] -> dX  = dZ0 W0, dW0 += dZ0^T X
-//   dX -> hash-table gradient (float2 atomics) and dL/dposition
+//   dX: the feature part goes to global memory (f32) for k_scatter, the
+//   positional-encoding part of the colour decoder to dL/dposition here
 //
 // dX products read the forward weight tile as an MN-major B operand, so no
-// transposed copy exists; dW products read the point-row tiles as MN-major
+// transposed copy exists; dW products read the row tiles as MN-major
 // operands with M = 128 output rows, of which only the decoder's real
 // outputs are used. Each dW comes out of tensor memory after its product
 // and is added (plain read-modify-write) into this CTA's f32 slab; one
 // reduction kernel sums the slabs. Bias gradients are column sums of dZ.
-// Activations are never stored in global memory: they are recomputed.
+// Hidden activations are recomputed, never stored in global memory.
 #include "tc_ops.cuh"
 
 namespace hyrf {
 namespace tc {
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums of 16 columns over the 32 lanes of a warp by recursive halving: at
+// each step a lane keeps half of its partial sums and adds its partner's
+// copy of that half (16 shuffles instead of 16 x 5). On return lane l holds
+// the sum of column col_of_lane(l); lanes l and l ^ 1 hold the same column.
+__device__ __forceinline__ float col_sum16(const float* in) {
+  const int lane = threadIdx.x & 31;
+  float v[16];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int j = 0; j < 16; ++j) v[j] = in[j];
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = up ? v[j] : v[j + h];
+      const float keep = up ? v[j + h] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int col_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
 __device__ __forceinline__ void unpack8(uint4 u, float* v) {
@@ -60,31 +82,38 @@ struct GaussP {
   const float* d_scale;
   const float* d_quat;
   const float* d_color;
+  const uint32_t* Xg;   // [n_vis][32] bf16 features of the geometry field
+  const uint32_t* Xr;   // [n_vis][32] bf16 features of the radiance field
+  float* dXg;           // [n_vis][32] f32 out
+  float* dXr;           // [n_vis][32] f32 out
   float* d_pos;
   float* d_alpha_e;
   float* d_scale_e;
   float* d_color_e;
-  float* g_geo_table;
-  float* g_rad_table;
   int32_t* status;
 };
+
+__device__ __forceinline__ void store_dx32(float* dst, const float* dx) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d4[k] = make_float4(dx[4 * k], dx[4 * k + 1], dx[4 * k + 2], dx[4 * k + 3]);
+}
 
 // Geometry decoder at visible Gaussians: inputs enc(y; Theta_geo), outputs
 // (alpha_n, s_n[3], r_n[4]).
 struct GeoGauss {
-  static constexpr int IN = 32, OUT = 8, DEC = 0;
+  static constexpr int IN = 32, OUT = 8, DEC = 0, DXC = 32;
   static constexpr const char* kName = "k_decoder_bwd_tc<GeoGauss>";
   using Params = GaussP;
   struct Row {
     int i, g;
     bool ok;
-    float y[3], J[9];
     float da, ds[3], dq[4], ae, se;
   };
   __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.gm; }
-  __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev&, int idx, bool ok,
-                               Row& R, float* x) {
+  __device__ static void begin(const Params& P, const FieldsDev&, const CamDev&, int idx, bool ok, Row& R,
+                               uint8_t* X, int r) {
     R.i = idx;
     R.ok = ok;
     R.g = ok ? P.vis_ids[idx] : 0;
@@ -93,11 +122,7 @@ struct GeoGauss {
       R.ok = false;
       R.g = 0;
     }
-    float p[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = R.ok ? P.pos[3 * (int64_t)R.g + k] : F.lo[k] + 1.0f / F.sx[k];
-    contract_p(F, p, R.y, R.J);
-    encode<16>(F.geo, R.y, x);
+    load_row32<IN>(X, r, P.Xg + (size_t)idx * 16, R.ok);
     R.da = R.ok ? P.d_alpha[idx] : 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) R.ds[k] = R.ok ? P.d_scale[3 * idx + k] : 0.0f;
@@ -134,31 +159,28 @@ struct GeoGauss {
     P.d_alpha_e[R.g] += dz[0];
     P.d_scale_e[R.g] += dz[1] + dz[2] + dz[3];
   }
-  __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
-                                const float* dx) {
-    if (!R.ok) return;
-    float dy[3] = {0.0f, 0.0f, 0.0f};
-    encode_bwd<16>(F.geo, R.y, dx, P.g_geo_table, dy);
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      P.d_pos[3 * (int64_t)R.g + j] += R.J[j] * dy[0] + R.J[3 + j] * dy[1] + R.J[6 + j] * dy[2];
+  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx) {
+    if (R.ok) store_dx32(P.dXg + (size_t)R.i * 32, dx);
   }
 };
 
 // Colour decoder at visible Gaussians: inputs enc(y; Theta_rad) (+) PE(dir).
+// The PE part of dX goes to dL/dp here; the feature part goes out for the
+// scatter.
 struct ColGauss {
-  static constexpr int IN = 64, OUT = 3, DEC = 1;
+  static constexpr int IN = 64, OUT = 3, DEC = 1, DXC = 64;
   using Params = GaussP;
   static constexpr const char* kName = "k_decoder_bwd_tc<ColGauss>";
   struct Row {
-    int g;
+    int i, g;
     bool ok;
-    float y[3], J[9], dir[3], vn, dc[3], ce[3];
+    float dir[3], vn, dc[3], ce[3];
   };
   __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
   __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
-                               Row& R, float* x) {
+                               Row& R, uint8_t* X, int r) {
+    R.i = idx;
     R.ok = ok;
     R.g = ok ? P.vis_ids[idx] : 0;
     if (ok && (R.g < 0 || R.g >= P.n)) {
@@ -166,18 +188,19 @@ struct ColGauss {
       R.ok = false;
       R.g = 0;
     }
+    load_row32<IN>(X, r, P.Xr + (size_t)idx * 16, R.ok);
     float p[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[k] = R.ok ? P.pos[3 * (int64_t)R.g + k] : F.lo[k] + 1.0f / F.sx[k];
-    contract_p(F, p, R.y, R.J);
-    encode<16>(F.rad, R.y, x);
     float pc[3];
     cam_center(cam, pc);
     const float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
     R.vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) R.dir[k] = v[k] / R.vn;
-    pos_enc(R.dir, x + 32);
+    float pe[32];
+    pos_enc(R.dir, pe);
+    store_cols<IN, 32, 32>(X, r, pe);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       R.dc[k] = R.ok ? P.d_color[3 * idx + k] : 0.0f;
@@ -195,18 +218,14 @@ struct ColGauss {
       for (int k = 0; k < 3; ++k) P.d_color_e[3 * (int64_t)R.g + k] += dz[k];
     }
   }
-  __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
-                                const float* dx) {
+  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx) {
     if (!R.ok) return;
-    float dy[3] = {0.0f, 0.0f, 0.0f};
-    encode_bwd<16>(F.rad, R.y, dx, P.g_rad_table, dy);
+    store_dx32(P.dXr + (size_t)R.i * 32, dx);
     float ddir[3];
     pos_enc_bwd(R.dir, dx + 32, ddir);
     const float dd = R.dir[0] * ddir[0] + R.dir[1] * ddir[1] + R.dir[2] * ddir[2];
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-      P.d_pos[3 * (int64_t)R.g + j] += (ddir[j] - R.dir[j] * dd) / R.vn + R.J[j] * dy[0] +
-                                       R.J[3 + j] * dy[1] + R.J[6 + j] * dy[2];
+    for (int j = 0; j < 3; ++j) P.d_pos[3 * (int64_t)R.g + j] += (ddir[j] - R.dir[j] * dd) / R.vn;
   }
 };
 
@@ -214,33 +233,34 @@ struct PixelP {
   float radius;
   const float* T_final;
   const float* dC;
+  const uint32_t* Xb;   // [W*H][32] bf16 radiance features at the sphere hits
+  float* dXb;           // [W*H][32] f32 out
   float* dC_fg;
   float* dT;
-  float* g_rad_table;
 };
 
 // Colour decoder at the background-sphere hit of every pixel (exact mode):
 // reverse of C = C_fg + T_final sigma(c_n).
 struct BgPixel {
-  static constexpr int IN = 64, OUT = 3, DEC = 1;
+  static constexpr int IN = 64, OUT = 3, DEC = 1, DXC = 32;
   using Params = PixelP;
   static constexpr const char* kName = "k_decoder_bwd_tc<BgPixel>";
   struct Row {
     int p;
     bool ok;
-    float y[3], T, g[3];
+    float T, g[3];
   };
   __device__ static int count_px(const CamDev& cam) { return cam.W * cam.H; }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
   __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
-                               Row& R, float* x) {
+                               Row& R, uint8_t* X, int r) {
     R.ok = ok;
     R.p = ok ? idx : 0;
-    float ps[3], dir[3];
+    load_row32<IN>(X, r, P.Xb + (size_t)R.p * 16, ok);
+    float ps[3], dir[3], pe[32];
     bg_ray(cam, F, P.radius, R.p % cam.W, R.p / cam.W, ps, dir);
-    contract_n(ps, R.y);
-    encode<16>(F.rad, R.y, x);
-    pos_enc(dir, x + 32);
+    pos_enc(dir, pe);
+    store_cols<IN, 32, 32>(X, r, pe);
     R.T = ok ? P.T_final[R.p] : 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) R.g[k] = ok ? P.dC[3 * (int64_t)R.p + k] : 0.0f;
@@ -261,10 +281,8 @@ struct BgPixel {
       }
     }
   }
-  __device__ static void finish(const Params& P, const FieldsDev& F, const CamDev&, Row& R,
-                                const float* dx) {
-    if (!R.ok) return;
-    encode_bwd<16, true>(F.rad, R.y, dx, P.g_rad_table, nullptr);
+  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx) {
+    if (R.ok) store_dx32(P.dXb + (size_t)R.p * 32, dx);
   }
 };
 
@@ -306,11 +324,8 @@ __device__ __forceinline__ void relu_back64(uint32_t taddr, uint8_t* Hbuf, int r
     for (int j = 0; j < 16; ++j) v[j] = (ok && h[j] > 0.0f) ? v[j] : 0.0f;
     *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0, 64)) = pack8(v);
     *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + 8, 64)) = pack8(v + 8);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float s = warp_sum(v[j]);
-      if (lane == 0) atomicAdd(db + c0 + j, s);
-    }
+    const float s = col_sum16(v);
+    if ((lane & 1) == 0) atomicAdd(db + c0 + col_of_lane(lane), s);
   }
 }
 
@@ -386,11 +401,7 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     const int idx = tile * 128 + r;
     const bool ok = idx < n;
     typename S::Row R;
-    {
-      float x[IN];
-      S::begin(P, F, cam, idx, ok, R, x);
-      store_row<IN>(sm + L::X, r, x);
-    }
+    S::begin(P, F, cam, idx, ok, R, sm + L::X, r);
     // ---- forward recompute
     sync_for_mma();
     if (t == 0) {
@@ -428,10 +439,10 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
       for (int k = 0; k < 16; ++k) dz[k] = k < OUT ? dz[k] * loss_scale : 0.0f;
       *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 0, 16)) = pack8(dz);
       *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 8, 16)) = pack8(dz + 8);
-#pragma unroll
-      for (int k = 0; k < OUT; ++k) {
-        const float s = warp_sum(dz[k]);
-        if ((t & 31) == 0) atomicAdd(db + 128 + k, s);
+      {
+        const float s = col_sum16(dz);
+        const int c = col_of_lane(t & 31);
+        if ((t & 1) == 0 && c < OUT) atomicAdd(db + 128 + c, s);
       }
     }
     // ---- layer 2: dH2 = dZ2 W2, dW2 += dZ2^T H2
@@ -469,11 +480,11 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     phase ^= 1u;
     fence_after();
     {
-      float dx[IN];
+      float dx[S::DXC];
 #pragma unroll
-      for (int c0 = 0; c0 < IN; c0 += 16) ld16(tm + lane_off + c0, dx + c0);
+      for (int c0 = 0; c0 < S::DXC; c0 += 16) ld16(tm + lane_off + c0, dx + c0);
 #pragma unroll
-      for (int k = 0; k < IN; ++k) dx[k] *= inv_ls;
+      for (int k = 0; k < S::DXC; ++k) dx[k] *= inv_ls;
       S::finish(P, F, cam, R, dx);
     }
     flush_dw<IN>(tmW, 64, slab + SL.off_W[S::DEC][0]);
@@ -500,6 +511,7 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
 // ---------------------------------------------------------------- launchers
 
 int bwd_ctas();
+size_t slab_bytes(const FieldsDev& F, bool geo);
 hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout& SL,
                                const SlabTargets& T, float scale, cudaStream_t s);
 SlabTargets slab_targets(const hyrf_field_grads& g, bool geo);
@@ -515,19 +527,43 @@ static hyrf_status launch_dec_bwd(const typename S::Params& P, const FieldsDev& 
   return HYRF_OK;
 }
 
+// Workspace of the BF16 backward calls: CTA slabs, bf16 features (unless
+// the caller saved them in the forward) and f32 feature gradients of `rows`
+// rows for one or both fields.
+size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features) {
+  Carver c(nullptr);
+  c.take<char>(slab_bytes(F, geo));
+  const int fields = geo ? 2 : 1;
+  if (!have_features) c.take<uint32_t>((size_t)fields * rows * 16);
+  c.take<float>((size_t)fields * rows * 32);
+  return c.size();
+}
+
 hyrf_status launch_query_bwd_tc(const hyrf_query_fields_backward_args& a, const FieldsDev& F, void* ws,
                                 cudaStream_t s) {
   if (a.n == 0) return HYRF_OK;
   const CamDev cam = to_dev(a.cam);
   const SlabLayout SL = make_slab_layout(&F.gm, &F.cm);
-  float* slabs = static_cast<float*>(ws);
+  Carver c(ws);
+  float* slabs = reinterpret_cast<float*>(c.take<char>(slab_bytes(F, true)));
+  const bool saved = a.features != nullptr;
+  uint32_t* X = saved ? const_cast<uint32_t*>(static_cast<const uint32_t*>(a.features))
+                      : c.take<uint32_t>((size_t)2 * a.n * 16);
+  float* dX = c.take<float>((size_t)2 * a.n * 32);
+  uint32_t *Xg = X, *Xr = X + (size_t)a.n * 16;
+  float *dXg = dX, *dXr = dX + (size_t)a.n * 32;
   cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
-  tc::GaussP P{a.n,       a.pos,       a.alpha_e,   a.scale_e,   a.color_e,         a.vis_ids,
-               a.n_vis,   a.d_alpha,   a.d_scale,   a.d_quat,    a.d_color,         a.d_pos,
-               a.d_alpha_e, a.d_scale_e, a.d_color_e, a.grads.geo_table, a.grads.rad_table, a.status};
-  hyrf_status st = launch_dec_bwd<tc::GeoGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
+  const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status};
+  hyrf_status st = saved ? HYRF_OK : launch_gather(F, cam, RS, a.n, Xg, Xr, s);
+  if (st != HYRF_OK) return st;
+  tc::GaussP P{a.n,       a.pos,     a.alpha_e, a.scale_e, a.color_e, a.vis_ids,   a.n_vis,
+               a.d_alpha, a.d_scale, a.d_quat,  a.d_color, Xg,        Xr,          dXg,
+               dXr,       a.d_pos,   a.d_alpha_e, a.d_scale_e, a.d_color_e, a.status};
+  st = launch_dec_bwd<tc::GeoGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
   if (st != HYRF_OK) return st;
   st = launch_dec_bwd<tc::ColGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
+  if (st != HYRF_OK) return st;
+  st = launch_scatter(F, cam, RS, a.n, dXg, dXr, a.grads.geo_table, a.grads.rad_table, a.d_pos, s);
   if (st != HYRF_OK) return st;
   return launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(a.grads, true), 1.0f / a.loss_scale, s);
 }
@@ -536,11 +572,21 @@ hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, c
                              void* ws, cudaStream_t s) {
   const hyrf_composite_background_args& a = b.fwd;
   const CamDev cam = to_dev(a.cam);
+  const int P_ = cam.W * cam.H;
   const SlabLayout SL = make_slab_layout(nullptr, &F.cm);
-  float* slabs = static_cast<float*>(ws);
+  Carver c(ws);
+  float* slabs = reinterpret_cast<float*>(c.take<char>(slab_bytes(F, false)));
+  const bool saved = a.features != nullptr;
+  uint32_t* Xb = saved ? static_cast<uint32_t*>(a.features) : c.take<uint32_t>((size_t)P_ * 16);
+  float* dXb = c.take<float>((size_t)P_ * 32);
   cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
-  tc::PixelP P{a.bg.radius, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, b.grads.rad_table};
-  hyrf_status st = launch_dec_bwd<tc::BgPixel>(P, F, cam, b.loss_scale, SL, slabs, a.status, s);
+  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status};
+  hyrf_status st = saved ? HYRF_OK : launch_gather(F, cam, RS, P_, nullptr, Xb, s);
+  if (st != HYRF_OK) return st;
+  tc::PixelP P{a.bg.radius, a.T_final, b.d_C, Xb, dXb, b.d_C_fg, b.d_T_final};
+  st = launch_dec_bwd<tc::BgPixel>(P, F, cam, b.loss_scale, SL, slabs, a.status, s);
+  if (st != HYRF_OK) return st;
+  st = launch_scatter(F, cam, RS, P_, nullptr, dXb, nullptr, b.grads.rad_table, nullptr, s);
   if (st != HYRF_OK) return st;
   return launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
 }

@@ -1,0 +1,295 @@
+// Hash-grid gather (Eq. 3) and its reverse for the BF16 tensor-core path.
+//
+// The decoders run on the tensor cores over tiles of 128 rows, a shape that
+// needs most of an SM's shared memory and therefore runs only a few warps per
+// SM. The hash gathers and the gradient scatter are latency-bound memory work
+// that wants the opposite: as many independent loads and atomics in flight as
+// possible. So they run here, in their own kernels, with one thread per
+// (row, level) pair: a CTA holds 32 rows (the lanes) x 16 levels (the warps),
+// 512 threads, 3-4 CTAs per SM.
+//
+//   k_gather   rows -> bf16 features X [rows][32] per field (row-major; the
+//              decoder kernels stage them into their operand tiles)
+//   k_scatter  f32 feature gradients dX [rows][32] per field -> float2
+//              atomics into the f32 table gradients, and, for Gaussians,
+//              dL/dp through the trilinear weights and the contraction
+//              Jacobian (App. A.1, Eq. 2)
+//
+// A row is a visible Gaussian (position via vis_ids) or a pixel (the hit of
+// its ray with the background sphere, App. A.2). A lane works on one row at a
+// fixed level, so for pixels, whose neighbours are adjacent lanes, runs of
+// lanes hit the same corner at all but the finest levels; the scatter sums
+// each run with shuffles and issues one atomic per run.
+#include "tc_ops.cuh"
+
+namespace hyrf {
+
+namespace {
+
+constexpr int kRows = 32;    // rows per CTA (lanes)
+constexpr int kLevels = 16;  // levels (warps)
+constexpr int kThreads = kRows * kLevels;
+
+__device__ __forceinline__ int row_count(const RowSource& S, const CamDev& cam) {
+  return S.pixels ? cam.W * cam.H : min(*S.n_vis, S.n);
+}
+
+// Contracted position (and, for Gaussians, the Gaussian index and the
+// contraction Jacobian) of row `row`; rows past the end, or with an
+// out-of-range id, get a harmless in-box point and ok = false.
+__device__ __forceinline__ void row_point(const RowSource& S, const FieldsDev& F, const CamDev& cam,
+                                          int row, int nrows, float y[3], float* J, int& g, bool& ok) {
+  ok = row < nrows;
+  g = 0;
+  if (S.pixels) {
+    const int p = ok ? row : 0;
+    float ps[3], dir[3];
+    tc::bg_ray(cam, F, S.radius, p % cam.W, p / cam.W, ps, dir);
+    contract_n(ps, y);
+    return;
+  }
+  if (ok) {
+    g = S.vis_ids[row];
+    if (g < 0 || g >= S.n) {
+      set_status(S.status, HYRF_ERR_BOUNDS);
+      ok = false;
+      g = 0;
+    }
+  }
+  float p[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p[k] = ok ? S.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];
+  contract_p(F, p, y, J);
+}
+
+// Eq. 3 at one level: the two interpolated features, summed over the corners
+// in the same order as the fused field kernels.
+__device__ __forceinline__ float2 level_feature(const GridDev& G, int l, const float y[3]) {
+  uint32_t idx[8];
+  float f[3];
+  level_cell(G, l, y, idx, f);
+  float2 e[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) e[c] = load_entry(G, (size_t)l * G.T + idx[c]);
+  float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = corner_w(f, c);
+    a0 = fmaf(w, e[c].x, a0);
+    a1 = fmaf(w, e[c].y, a1);
+  }
+  return make_float2(a0, a1);
+}
+
+// One float2 atomic per run of consecutive lanes that target the same table
+// entry e: lanes hold neighbouring pixels of an image row, so lanes sharing
+// a cell form runs. Each run's contributions are summed by a segmented
+// shuffle scan and its last lane issues the atomic. A key that appears in
+// two separate runs is simply added twice. Warp-uniform fast paths: no run
+// longer than one lane, or one run over the whole warp.
+__device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, uint32_t key, float g0, float g1) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint32_t prev = __shfl_up_sync(full, key, 1);
+  const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
+  if (heads == full) {
+    if (g0 != 0.0f || g1 != 0.0f) atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+    return;
+  }
+  if (heads == 1u) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      g0 += __shfl_xor_sync(full, g0, o);
+      g1 += __shfl_xor_sync(full, g1, o);
+    }
+    if (lane == 0 && (g0 != 0.0f || g1 != 0.0f))
+      atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+    return;
+  }
+  const int start = 31 - __clz(heads & (full >> (31 - lane)));  // first lane of this run
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float a0 = __shfl_up_sync(full, g0, o), a1 = __shfl_up_sync(full, g1, o);
+    if (lane - o >= start) {
+      g0 += a0;
+      g1 += a1;
+    }
+  }
+  const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  if (tail && (g0 != 0.0f || g1 != 0.0f)) atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+}
+
+// Reverse of level_feature: (d0, d1) = dL/d features of level l. Adds
+// w_c (d0, d1) to the table gradient of every corner and returns the level's
+// dL/dy if WANT_DY. COHERENT: lanes hold neighbouring points (run_atomic).
+template <bool COHERENT, bool WANT_DY>
+__device__ __forceinline__ void level_scatter(const GridDev& G, int l, const float y[3], float d0, float d1,
+                                              float* __restrict__ gtab, float dy[3]) {
+  uint32_t idx[8];
+  float f[3];
+  level_cell(G, l, y, idx, f);
+  float g[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const size_t e = (size_t)l * G.T + idx[c];
+    const float w = corner_w(f, c);
+    const float g0 = w * d0, g1 = w * d1;
+    if (COHERENT)
+      run_atomic(gtab, e, idx[c], g0, g1);
+    else if (g0 != 0.0f || g1 != 0.0f)
+      atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+    if (WANT_DY) {
+      const float2 v = load_entry(G, e);
+      const float dot = v.x * d0 + v.y * d1;
+      const float wx = (c & 1) ? f[0] : 1.0f - f[0];
+      const float wy = (c & 2) ? f[1] : 1.0f - f[1];
+      const float wz = (c & 4) ? f[2] : 1.0f - f[2];
+      g[0] += dot * ((c & 1) ? 1.0f : -1.0f) * wy * wz;
+      g[1] += dot * ((c & 2) ? 1.0f : -1.0f) * wx * wz;
+      g[2] += dot * ((c & 4) ? 1.0f : -1.0f) * wx * wy;
+    }
+  }
+  if (WANT_DY) {
+    const float N = (float)G.res[l];
+    dy[0] = g[0] * N;
+    dy[1] = g[1] * N;
+    dy[2] = g[2] * N;
+  }
+}
+
+// Features of both fields (Gaussians) or of the radiance field only (pixels).
+// X*: [rows][16] uint32 = [rows][32] bf16, level-major (2l, 2l+1).
+template <bool BOTH>
+__global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
+    k_gather(FieldsDev F, CamDev cam, RowSource S, uint32_t* __restrict__ Xg, uint32_t* __restrict__ Xr) {
+  __shared__ float ys[kRows][3];
+  __shared__ uint32_t xs[2][kRows][kLevels + 1];
+  const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
+  const int nrows = row_count(S, cam);
+  const int row0 = blockIdx.x * kRows;
+  if (row0 >= nrows) return;  // CTA-uniform
+  if (l == 0) {
+    float y[3];
+    int g;
+    bool ok;
+    row_point(S, F, cam, row0 + lane, nrows, y, nullptr, g, ok);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ys[lane][k] = y[k];
+  }
+  __syncthreads();
+  const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
+  if (BOTH) {
+    const float2 a = level_feature(F.geo, l, y);
+    xs[0][lane][l] = tc::pack2(a.x, a.y);
+  }
+  const float2 b = level_feature(F.rad, l, y);
+  xs[1][lane][l] = tc::pack2(b.x, b.y);
+  __syncthreads();
+  // coalesced write-out: thread t -> row t/16, word t%16
+  const int r = threadIdx.x >> 4, wd = threadIdx.x & 15;
+  if (row0 + r < nrows) {
+    const size_t o = (size_t)(row0 + r) * 16 + wd;
+    if (BOTH) Xg[o] = xs[0][r][wd];
+    Xr[o] = xs[1][r][wd];
+  }
+}
+
+// Reverse of k_gather. dXg/dXr: [rows][32] f32 feature gradients (already
+// unscaled). Gaussians: d_pos[g] += J^T sum_l dL/dy_l over both fields.
+template <bool BOTH>
+__global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
+    k_scatter(FieldsDev F, CamDev cam, RowSource S, const float* __restrict__ dXg,
+              const float* __restrict__ dXr, float* __restrict__ g_geo, float* __restrict__ g_rad,
+              float* __restrict__ d_pos) {
+  __shared__ float ys[kRows][3];
+  __shared__ float Js[kRows][9];
+  __shared__ int gs[kRows];
+  __shared__ float dys[kLevels][kRows][3];
+  const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
+  const int nrows = row_count(S, cam);
+  const int row0 = blockIdx.x * kRows;
+  if (row0 >= nrows) return;  // CTA-uniform
+  const bool gauss = !S.pixels;
+  if (l == 0) {
+    float y[3], J[9];
+    int g;
+    bool ok;
+    row_point(S, F, cam, row0 + lane, nrows, y, gauss ? J : nullptr, g, ok);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ys[lane][k] = y[k];
+    if (gauss) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Js[lane][k] = J[k];
+    }
+    gs[lane] = ok ? g : -1;
+  }
+  __syncthreads();
+  const int row = row0 + lane;
+  const bool ok = gs[lane] >= 0;
+  const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
+  float dy[3] = {0.0f, 0.0f, 0.0f};
+  if (gauss) {
+    float2 dr = ok ? *reinterpret_cast<const float2*>(dXr + (size_t)row * 32 + 2 * l) : make_float2(0.0f, 0.0f);
+    level_scatter<false, true>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
+    if (BOTH) {
+      const float2 dg =
+          ok ? *reinterpret_cast<const float2*>(dXg + (size_t)row * 32 + 2 * l) : make_float2(0.0f, 0.0f);
+      float dy2[3];
+      level_scatter<false, true>(F.geo, l, y, dg.x, dg.y, g_geo, dy2);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dy[k] += dy2[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dys[l][lane][k] = dy[k];
+    __syncthreads();
+    if (l == 0 && ok) {
+      float s[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int m = 0; m < kLevels; ++m) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s[k] += dys[m][lane][k];
+      }
+      const float* J = Js[lane];
+      const int g = gs[lane];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) d_pos[3 * (int64_t)g + j] += J[j] * s[0] + J[3 + j] * s[1] + J[6 + j] * s[2];
+    }
+  } else {
+    float2 dr = ok ? *reinterpret_cast<const float2*>(dXr + (size_t)row * 32 + 2 * l) : make_float2(0.0f, 0.0f);
+    level_scatter<true, false>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
+  }
+}
+
+int grid_for(int rows) { return rows > 0 ? (rows + kRows - 1) / kRows : 0; }
+
+}  // namespace
+
+// rows: an upper bound of the device row count (n for Gaussians, W*H for
+// pixels). Gaussians gather and scatter both fields, pixels the radiance
+// field only.
+hyrf_status launch_gather(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows, uint32_t* Xg,
+                          uint32_t* Xr, cudaStream_t s) {
+  const int grid = grid_for(rows);
+  if (grid == 0) return HYRF_OK;
+  if (!S.pixels)
+    HYRF_LAUNCH("k_gather<gaussians>", s, k_gather<true><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
+  else
+    HYRF_LAUNCH("k_gather<pixels>", s, k_gather<false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
+  return HYRF_OK;
+}
+
+hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows,
+                           const float* dXg, const float* dXr, float* g_geo, float* g_rad, float* d_pos,
+                           cudaStream_t s) {
+  const int grid = grid_for(rows);
+  if (grid == 0) return HYRF_OK;
+  if (!S.pixels)
+    HYRF_LAUNCH("k_scatter<gaussians>", s,
+                k_scatter<true><<<grid, kThreads, 0, s>>>(F, cam, S, dXg, dXr, g_geo, g_rad, d_pos));
+  else
+    HYRF_LAUNCH("k_scatter<pixels>", s,
+                k_scatter<false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, dXr, nullptr, g_rad, nullptr));
+  return HYRF_OK;
+}
+
+}  // namespace hyrf

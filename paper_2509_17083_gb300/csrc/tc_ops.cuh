@@ -16,6 +16,27 @@
 #include "field_ops.cuh"
 
 namespace hyrf {
+
+// Rows of the BF16 field kernels: visible Gaussians or camera pixels.
+struct RowSource {
+  int pixels;               // 0: visible Gaussians, 1: pixels of the camera
+  int n;                    // Gaussians (capacity of vis_ids)
+  const int32_t* vis_ids;   // [n]
+  const int32_t* n_vis;     // device count
+  const float* pos;         // [n][3]
+  float radius;             // background sphere radius (pixels)
+  int32_t* status;
+};
+
+// gather.cu: bf16 features X [rows][32] per field, and the reverse scatter
+// of f32 feature gradients dX [rows][32]. Gaussians use both fields, pixels
+// the radiance field only; `rows` bounds the device row count.
+hyrf_status launch_gather(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows, uint32_t* Xg,
+                          uint32_t* Xr, cudaStream_t s);
+hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows,
+                           const float* dXg, const float* dXr, float* g_geo, float* g_rad, float* d_pos,
+                           cudaStream_t s);
+
 namespace tc {
 
 constexpr uint32_t kSpin = 1u << 24;
@@ -114,6 +135,32 @@ __device__ __forceinline__ void store_row(uint8_t* tile, int r, const float* v) 
     u.z = pack2(v[8 * kc + 4], v[8 * kc + 5]);
     u.w = pack2(v[8 * kc + 6], v[8 * kc + 7]);
     *reinterpret_cast<uint4*>(tile + kmaj(r, 8 * kc, K)) = u;
+  }
+}
+
+// Columns [C0, C0 + NC) of row r of a K-major bf16 tile from NC floats.
+template <int K, int C0, int NC>
+__device__ __forceinline__ void store_cols(uint8_t* tile, int r, const float* v) {
+#pragma unroll
+  for (int kc = 0; kc < NC / 8; ++kc) {
+    uint4 u;
+    u.x = pack2(v[8 * kc], v[8 * kc + 1]);
+    u.y = pack2(v[8 * kc + 2], v[8 * kc + 3]);
+    u.z = pack2(v[8 * kc + 4], v[8 * kc + 5]);
+    u.w = pack2(v[8 * kc + 6], v[8 * kc + 7]);
+    *reinterpret_cast<uint4*>(tile + kmaj(r, C0 + 8 * kc, K)) = u;
+  }
+}
+
+// Columns [0, 32) of row r of a K-major bf16 tile from 32 bf16 values in
+// global memory (16-byte aligned); zeros if !ok.
+template <int K>
+__device__ __forceinline__ void load_row32(uint8_t* tile, int r, const uint32_t* src, bool ok) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+    const uint4 v = ok ? __ldg(s4 + kc) : make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(tile + kmaj(r, 8 * kc, K)) = v;
   }
 }
 

@@ -85,9 +85,15 @@ class DeviceModel:
 
 
 class ViewRenderer:
-    """Buffers and calls for one camera of fixed size."""
+    """Buffers and calls for one camera of fixed size.
 
-    def __init__(self, model: DeviceModel, cam, bg, lam=0.0, loss_scale=1.0, capacity=None):
+    save_features (BF16 fields only; default on for them): keep the hash
+    features gathered by the forward (2 x 64 B per Gaussian, 64 B per pixel)
+    for the backward, which then skips its gather; off = gather again
+    (recompute)."""
+
+    def __init__(self, model: DeviceModel, cam, bg, lam=0.0, loss_scale=1.0, capacity=None,
+                 save_features=None):
         self.m = model
         self.cam = cam
         self.bg = bg
@@ -116,6 +122,16 @@ class ViewRenderer:
         self.d_mean2d, self.d_conic, self.d_alpha, self.d_color = z(n, 2), z(n, 3), z(n), z(n, 3)
         self.d_scale, self.d_quat = z(n, 3), z(n, 4)
         self.ws = {k: H.Workspace(d) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l")}
+        if save_features is None:
+            save_features = model.bf16
+        if save_features and not model.bf16:
+            raise ValueError("save_features needs BF16 fields")
+        self.save_features = bool(save_features)
+        self.feat_q = self.feat_b = None
+        if self.save_features:
+            self.feat_q = torch.empty(2 * max(n, 1) * 32, dtype=torch.bfloat16, device=d)
+            if int(bg.mode) == 0:
+                self.feat_b = torch.empty(W * Hh * 32, dtype=torch.bfloat16, device=d)
         self.set_capacity(capacity if capacity is not None else max(4 * n, 1 << 16))
         self.ccam = H.camera(cam)
         self.cbg = H.hyrf_background(int(bg.mode), int(bg.map_h), int(bg.map_w), float(bg.radius))
@@ -140,7 +156,8 @@ class ViewRenderer:
         a.cam = self.ccam
         a.fields = self.m.fields_struct()
         a.bg = self.cbg
-        H._fill(a, dict(C_fg=self.C_fg, T_final=self.T_final, C=self.C, status=self.status))
+        H._fill(a, dict(C_fg=self.C_fg, T_final=self.T_final, C=self.C, status=self.status,
+                        features=self.feat_b))
         return a
 
     def forward(self, target=None, want_keys=True):
@@ -149,7 +166,7 @@ class ViewRenderer:
         H.hyrf_query_fields(ws=self.ws["q"], n=m.n, pos=m.pos, alpha_e=m.alpha_e, scale_e=m.scale_e,
                             color_e=m.color_e, cam=self.ccam, fields=fs, vis_ids=self.vis_ids,
                             n_vis=self.n_vis, alpha=self.alpha, scale=self.scale, quat=self.quat,
-                            color=self.color, status=self.status)
+                            color=self.color, status=self.status, features=self.feat_q)
         self.project()
         self.bin_sort(want_keys)
         H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
@@ -212,7 +229,8 @@ class ViewRenderer:
                                      d_quat=self.d_quat, d_color=self.d_color, d_pos=m.grad["pos"],
                                      d_alpha_e=m.grad["alpha_e"], d_scale_e=m.grad["scale_e"],
                                      d_color_e=m.grad["color_e"], grads=g,
-                                     loss_scale=self.loss_scale, status=self.status)
+                                     loss_scale=self.loss_scale, status=self.status,
+                                     features=self.feat_q)
 
     def step(self, target):
         """One training iteration of the view: forward, loss, backward."""

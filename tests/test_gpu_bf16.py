@@ -115,3 +115,30 @@ def test_bf16_psnr_within_005_db_of_fp32():
     pb = psnr(np_(rb.C), wb.targets[0])
     pf = psnr(np_(rf.C), wf.targets[0])
     assert abs(pb - pf) <= 0.05, (pb, pf)
+
+
+def test_saved_features_match_regathered():
+    """The backward fed with the forward's saved hash features equals the
+    backward that gathers them again (same bf16 features; only the order of
+    float atomics differs)."""
+    w = _workload("bf16", n=20000, W=257, H_=171)
+    out = []
+    for save in (True, False):
+        m = DeviceModel(w)
+        r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale,
+                         save_features=save)
+        tgt = cuda_f32(w.targets[0])
+        r.fit_capacity(tgt)
+        m.zero_grad()
+        r.status.zero_()
+        r.step(tgt)
+        torch.cuda.synchronize()
+        assert H.read_status(r.status) == 0
+        flat = {}
+        for k, v in m.grad.items():
+            for j, t in enumerate(v if isinstance(v, list) else [v]):
+                flat[f"{k}{j}"] = np_(t)
+        out.append((np_(r.C), flat))
+    assert np.array_equal(out[0][0], out[1][0])
+    for k, g in out[0][1].items():
+        assert rel_l2(g, out[1][1][k]) < 1e-5, k
