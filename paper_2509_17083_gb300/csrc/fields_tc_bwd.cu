@@ -340,8 +340,16 @@ __device__ __forceinline__ void flush_dw(uint32_t tm_w, int rows_used, float* sl
     float v[16];
     ld16(tm_w + ((uint32_t)(w * 32) << 16) + c0, v);
     if (o < rows_used) {
+      float4* d = reinterpret_cast<float4*>(slab_W + o * N + c0);  // slab rows are 16-byte aligned
 #pragma unroll
-      for (int j = 0; j < 16; ++j) slab_W[o * N + c0 + j] += v[j];
+      for (int q = 0; q < 4; ++q) {
+        float4 x = d[q];
+        x.x += v[4 * q];
+        x.y += v[4 * q + 1];
+        x.z += v[4 * q + 2];
+        x.w += v[4 * q + 3];
+        d[q] = x;
+      }
     }
   }
 }

@@ -107,6 +107,32 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sums of 8 values over the 32 lanes by recursive halving (9 shuffles
+// instead of 8 x 5): each step a lane keeps half of its partial sums and
+// adds its partner's copy of that half. On return the lanes with
+// (lane & 3) == 0 hold the sum of value col8(lane), one value each.
+__device__ __forceinline__ float reduce8(float* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = up ? v[j] : v[j + h];
+      const float keep = up ? v[j + h] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  float s = v[0];
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+
+__device__ __forceinline__ int col8(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
 __global__ void __launch_bounds__(256) k_raster_bwd(
     const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
     const float4* __restrict__ rec, int W, int H, int TX, const float* __restrict__ T_final,
@@ -197,25 +223,21 @@ __global__ void __launch_bounds__(256) k_raster_bwd(
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-        gu = warp_sum(gu);
-        gv = warp_sum(gv);
-        ga = warp_sum(ga);
-        gb = warp_sum(gb);
-        gc = warp_sum(gc);
-        go = warp_sum(go);
-        gr = warp_sum(gr);
-        gg = warp_sum(gg);
+        // mean2d (2), conic (3), opacity, colour r, g: one sum per lane group
+        float v8[8] = {gu, gv, ga, gb, gc, go, gr, gg};
+        const float s8 = reduce8(v8);
         gbl = warp_sum(gbl);
         const int g = sg[j];
-        if (lane == 0 && g >= 0) {
-          atomicAdd(reinterpret_cast<float2*>(d_mean2d) + g, make_float2(gu, gv));
-          atomicAdd(d_conic + 3 * g, ga);
-          atomicAdd(d_conic + 3 * g + 1, gb);
-          atomicAdd(d_conic + 3 * g + 2, gc);
-          atomicAdd(d_alpha + g, go);
-          atomicAdd(d_color + 3 * g, gr);
-          atomicAdd(d_color + 3 * g + 1, gg);
-          atomicAdd(d_color + 3 * g + 2, gbl);
+        if (g >= 0) {
+          if ((lane & 3) == 0) {
+            const int c = col8(lane);
+            float* dst = c < 2 ? d_mean2d + 2 * g + c
+                         : c < 5 ? d_conic + 3 * g + (c - 2)
+                         : c == 5 ? d_alpha + g
+                                  : d_color + 3 * g + (c - 6);
+            atomicAdd(dst, s8);
+          }
+          if (lane == 1) atomicAdd(d_color + 3 * g + 2, gbl);
         }
       }
     }
