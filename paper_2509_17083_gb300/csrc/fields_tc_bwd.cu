@@ -1,6 +1,7 @@
 // Reverse of the BF16 decoders (Eqs. 4, 6) and of the aggregation (Eq. 7)
-// on the tensor cores. One CTA of 128 threads owns a tile of 128 rows (one
-// per thread, the MMA M dimension) and one decoder:
+// on the tensor cores. One CTA of 256 threads owns a tile of 128 rows (the
+// MMA M dimension; two threads per row, each taking half of every row's
+// columns) and one decoder:
 //
 //   X = bf16 hash features of the rows (written by k_gather, gather.cu)
 //   forward recompute  X -> H1 -> H2 -> O          (K-major A, K-major B)
@@ -93,10 +94,24 @@ struct GaussP {
   int32_t* status;
 };
 
-__device__ __forceinline__ void store_dx32(float* dst, const float* dx) {
+__device__ __forceinline__ void store_dx16(float* dst, const float* dx) {
   float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) d4[k] = make_float4(dx[4 * k], dx[4 * k + 1], dx[4 * k + 2], dx[4 * k + 3]);
+  for (int k = 0; k < 4; ++k) __stcs(d4 + k, make_float4(dx[4 * k], dx[4 * k + 1], dx[4 * k + 2], dx[4 * k + 3]));
+}
+
+// Two threads serve each row: half h = 0 (warps 0-3) and h = 1 (warps 4-7).
+// begin() fills the row's operand columns and the state its half needs;
+// dz_out() runs on half 0 only; finish() gets the half's share of dX.
+
+__device__ __forceinline__ bool gauss_row(const GaussP& P, int idx, bool ok, int& g) {
+  g = ok ? P.vis_ids[idx] : 0;
+  if (ok && (g < 0 || g >= P.n)) {
+    set_status(P.status, HYRF_ERR_BOUNDS);
+    g = 0;
+    return false;
+  }
+  return ok;
 }
 
 // Geometry decoder at visible Gaussians: inputs enc(y; Theta_geo), outputs
@@ -113,16 +128,17 @@ struct GeoGauss {
   __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.gm; }
   __device__ static void begin(const Params& P, const FieldsDev&, const CamDev&, int idx, bool ok, Row& R,
-                               uint8_t* X, int r) {
+                               uint8_t* X, int r, int h) {
     R.i = idx;
-    R.ok = ok;
-    R.g = ok ? P.vis_ids[idx] : 0;
-    if (ok && (R.g < 0 || R.g >= P.n)) {
-      set_status(P.status, HYRF_ERR_BOUNDS);
-      R.ok = false;
-      R.g = 0;
+    R.ok = gauss_row(P, idx, ok, R.g);
+    // half h copies feature columns [16h, 16h + 16)
+    const uint4* src = reinterpret_cast<const uint4*>(P.Xg + (size_t)idx * 16) + 2 * h;
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      const uint4 v = R.ok ? __ldcs(src + kc) : make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(X + kmaj(r, 16 * h + 8 * kc, IN)) = v;
     }
-    load_row32<IN>(X, r, P.Xg + (size_t)idx * 16, R.ok);
+    if (h != 0) return;
     R.da = R.ok ? P.d_alpha[idx] : 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) R.ds[k] = R.ok ? P.d_scale[3 * idx + k] : 0.0f;
@@ -159,14 +175,16 @@ struct GeoGauss {
     P.d_alpha_e[R.g] += dz[0];
     P.d_scale_e[R.g] += dz[1] + dz[2] + dz[3];
   }
-  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx) {
-    if (R.ok) store_dx32(P.dXg + (size_t)R.i * 32, dx);
+  // dx = dX columns [16h, 16h + 16)
+  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx,
+                                int h) {
+    if (R.ok) store_dx16(P.dXg + (size_t)R.i * 32 + 16 * h, dx);
   }
 };
 
 // Colour decoder at visible Gaussians: inputs enc(y; Theta_rad) (+) PE(dir).
-// The PE part of dX goes to dL/dp here; the feature part goes out for the
-// scatter.
+// The PE part of dX goes to dL/dp here (half 1); the feature part goes out
+// for the scatter (half 0).
 struct ColGauss {
   static constexpr int IN = 64, OUT = 3, DEC = 1, DXC = 64;
   using Params = GaussP;
@@ -179,16 +197,18 @@ struct ColGauss {
   __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
   __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
-                               Row& R, uint8_t* X, int r) {
+                               Row& R, uint8_t* X, int r, int h) {
     R.i = idx;
-    R.ok = ok;
-    R.g = ok ? P.vis_ids[idx] : 0;
-    if (ok && (R.g < 0 || R.g >= P.n)) {
-      set_status(P.status, HYRF_ERR_BOUNDS);
-      R.ok = false;
-      R.g = 0;
+    R.ok = gauss_row(P, idx, ok, R.g);
+    if (h == 0) {
+      load_row32<IN>(X, r, P.Xr + (size_t)idx * 16, R.ok);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        R.dc[k] = R.ok ? P.d_color[3 * idx + k] : 0.0f;
+        R.ce[k] = R.ok ? P.color_e[3 * (int64_t)R.g + k] : 0.0f;
+      }
+      return;
     }
-    load_row32<IN>(X, r, P.Xr + (size_t)idx * 16, R.ok);
     float p[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[k] = R.ok ? P.pos[3 * (int64_t)R.g + k] : F.lo[k] + 1.0f / F.sx[k];
@@ -201,11 +221,6 @@ struct ColGauss {
     float pe[32];
     pos_enc(R.dir, pe);
     store_cols<IN, 32, 32>(X, r, pe);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      R.dc[k] = R.ok ? P.d_color[3 * idx + k] : 0.0f;
-      R.ce[k] = R.ok ? P.color_e[3 * (int64_t)R.g + k] : 0.0f;
-    }
   }
   __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
 #pragma unroll
@@ -218,11 +233,17 @@ struct ColGauss {
       for (int k = 0; k < 3; ++k) P.d_color_e[3 * (int64_t)R.g + k] += dz[k];
     }
   }
-  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx) {
+  // dx = dX columns [32h, 32h + 32)
+  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx,
+                                int h) {
     if (!R.ok) return;
-    store_dx32(P.dXr + (size_t)R.i * 32, dx);
+    if (h == 0) {
+      store_dx16(P.dXr + (size_t)R.i * 32, dx);
+      store_dx16(P.dXr + (size_t)R.i * 32 + 16, dx + 16);
+      return;
+    }
     float ddir[3];
-    pos_enc_bwd(R.dir, dx + 32, ddir);
+    pos_enc_bwd(R.dir, dx, ddir);
     const float dd = R.dir[0] * ddir[0] + R.dir[1] * ddir[1] + R.dir[2] * ddir[2];
 #pragma unroll
     for (int j = 0; j < 3; ++j) P.d_pos[3 * (int64_t)R.g + j] += (ddir[j] - R.dir[j] * dd) / R.vn;
@@ -253,17 +274,20 @@ struct BgPixel {
   __device__ static int count_px(const CamDev& cam) { return cam.W * cam.H; }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
   __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
-                               Row& R, uint8_t* X, int r) {
+                               Row& R, uint8_t* X, int r, int h) {
     R.ok = ok;
     R.p = ok ? idx : 0;
-    load_row32<IN>(X, r, P.Xb + (size_t)R.p * 16, ok);
+    if (h == 0) {
+      load_row32<IN>(X, r, P.Xb + (size_t)R.p * 16, ok);
+      R.T = ok ? P.T_final[R.p] : 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) R.g[k] = ok ? P.dC[3 * (int64_t)R.p + k] : 0.0f;
+      return;
+    }
     float ps[3], dir[3], pe[32];
     bg_ray(cam, F, P.radius, R.p % cam.W, R.p / cam.W, ps, dir);
     pos_enc(dir, pe);
     store_cols<IN, 32, 32>(X, r, pe);
-    R.T = ok ? P.T_final[R.p] : 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) R.g[k] = ok ? P.dC[3 * (int64_t)R.p + k] : 0.0f;
   }
   __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
     float dt = 0.0f;
@@ -281,8 +305,10 @@ struct BgPixel {
       }
     }
   }
-  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx) {
-    if (R.ok) store_dx32(P.dXb + (size_t)R.p * 32, dx);
+  // dx = dX columns [16h, 16h + 16)
+  __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx,
+                                int h) {
+    if (R.ok) store_dx16(P.dXb + (size_t)R.p * 32 + 16 * h, dx);
   }
 };
 
@@ -309,46 +335,65 @@ struct BwdSmem {
 };
 constexpr uint32_t kBwdTmemCols = 128;  // [0, 64): products, [64, 128): dW
 
-// ReLU mask from the bf16 activations of this row, applied to 64 columns of
-// D read from tensor memory; the masked gradient replaces the activations in
-// place (bf16) and its column sums go to db.
-__device__ __forceinline__ void relu_back64(uint32_t taddr, uint8_t* Hbuf, int r, bool ok, float* db) {
-  const int lane = threadIdx.x & 31;
+// ReLU(D + b) of NC accumulator columns [c0, c0 + NC) of this thread's lane
+// -> the same columns of its row of the 64-column tile H. taddr points at
+// column c0.
+template <int NC>
+__device__ __forceinline__ void epilogue_relu(uint32_t taddr, const float* b, uint8_t* H, int r, int c0) {
 #pragma unroll
-  for (int c0 = 0; c0 < 64; c0 += 16) {
-    float v[16], h[16];
-    ld16(taddr + c0, v);
-    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0, 64)), h);
-    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + 8, 64)), h + 8);
+  for (int c = 0; c < NC; c += 16) {
+    float v[16];
+    ld16(taddr + c, v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = (ok && h[j] > 0.0f) ? v[j] : 0.0f;
-    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0, 64)) = pack8(v);
-    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + 8, 64)) = pack8(v + 8);
-    const float s = col_sum16(v);
-    if ((lane & 1) == 0) atomicAdd(db + c0 + col_of_lane(lane), s);
+    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b[c0 + c + j], 0.0f);
+    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, 64)) = pack8(v);
+    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c + 8, 64)) = pack8(v + 8);
   }
 }
 
-// dW rows < rows_used (TMEM lanes) x N columns, added to the CTA slab.
-template <int N>
-__device__ __forceinline__ void flush_dw(uint32_t tm_w, int rows_used, float* slab_W) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w * 32 >= rows_used) return;  // warp-uniform
-  const int o = w * 32 + lane;
+// ReLU mask from the bf16 activations of this row, applied to NC columns
+// [c0, c0 + NC) of D read from tensor memory (taddr at column c0); the
+// masked gradient replaces the activations in place (bf16) and its column
+// sums go to db[c0 + ...].
+template <int NC>
+__device__ __forceinline__ void relu_back(uint32_t taddr, uint8_t* Hbuf, int r, bool ok, float* db, int c0) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c0 = 0; c0 < N; c0 += 16) {
+  for (int c = 0; c < NC; c += 16) {
+    float v[16], hv[16];
+    ld16(taddr + c, v);
+    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c, 64)), hv);
+    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)), hv + 8);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = (ok && hv[j] > 0.0f) ? v[j] : 0.0f;
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c, 64)) = pack8(v);
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)) = pack8(v + 8);
+    const float sum = col_sum16(v);
+    if ((lane & 1) == 0) atomicAdd(db + c0 + c + col_of_lane(lane), sum);
+  }
+}
+
+// Columns [c0, c0 + NC) of the dW rows < rows_used (TMEM lanes) x N columns,
+// added to the CTA slab (row stride N). Warps of both halves share lanes.
+template <int N, int NC>
+__device__ __forceinline__ void flush_dw(uint32_t tm_w, int rows_used, float* slab_W, int c0) {
+  const int q = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+  if (q * 32 >= rows_used) return;  // warp-uniform
+  const int o = q * 32 + lane;
+#pragma unroll
+  for (int c = 0; c < NC; c += 16) {
     float v[16];
-    ld16(tm_w + ((uint32_t)(w * 32) << 16) + c0, v);
+    ld16(tm_w + ((uint32_t)(q * 32) << 16) + c0 + c, v);
     if (o < rows_used) {
-      float4* d = reinterpret_cast<float4*>(slab_W + o * N + c0);  // slab rows are 16-byte aligned
+      float4* d = reinterpret_cast<float4*>(slab_W + o * N + c0 + c);  // slab rows are 16-byte aligned
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float4 x = d[q];
-        x.x += v[4 * q];
-        x.y += v[4 * q + 1];
-        x.z += v[4 * q + 2];
-        x.w += v[4 * q + 3];
-        d[q] = x;
+      for (int k = 0; k < 4; ++k) {
+        float4 x = d[k];
+        x.x += v[4 * k];
+        x.y += v[4 * k + 1];
+        x.z += v[4 * k + 2];
+        x.w += v[4 * k + 3];
+        d[k] = x;
       }
     }
   }
@@ -361,8 +406,10 @@ __device__ __forceinline__ void sync_for_mma() {
   fence_after();
 }
 
+// 256 threads: row r = t % 128 of the tile, half h = t / 128. Warps w and
+// w + 4 read the same TMEM lanes (32 (w % 4) ...) and split the columns.
 template <class S>
-__global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P, FieldsDev F, CamDev cam,
+__global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P, FieldsDev F, CamDev cam,
                                                            float loss_scale, SlabLayout SL, float* slabs,
                                                            int32_t* status) {
   constexpr int IN = S::IN, OUT = S::OUT;
@@ -370,7 +417,7 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
-  const int t = threadIdx.x, w = t >> 5, r = t;
+  const int t = threadIdx.x, w = t >> 5, h = t >> 7, r = t & 127;
   const MlpDev& M = S::mlp(F);
   float* bias = reinterpret_cast<float*>(sm + L::BIAS);
   float* db = reinterpret_cast<float*>(sm + L::DB);  // db0 [0,64), db1 [64,128), db2 [128,144)
@@ -398,18 +445,19 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
   }
   sync_for_mma();
   const uint32_t tm = tmem_base, tmW = tmem_base + 64;
-  const uint32_t lane_off = ((uint32_t)(w * 32)) << 16;
+  const uint32_t lane_off = ((uint32_t)((w & 3) * 32)) << 16;
   float* slab = slabs + (size_t)blockIdx.x * SL.total;
   const float inv_ls = 1.0f / loss_scale;
   const int n = point_count<S>(P, cam);
   const int ntile = (n + 127) / 128;
+  const int hc = 32 * h;  // this half's first column of 64
   uint32_t phase = 0;
   bool failed = false;
   for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
     const int idx = tile * 128 + r;
     const bool ok = idx < n;
     typename S::Row R;
-    S::begin(P, F, cam, idx, ok, R, sm + L::X, r);
+    S::begin(P, F, cam, idx, ok, R, sm + L::X, r, h);
     // ---- forward recompute
     sync_for_mma();
     if (t == 0) {
@@ -419,7 +467,7 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu64(tm + lane_off, bias, sm + L::H1, r);
+    epilogue_relu<32>(tm + lane_off + hc, bias, sm + L::H1, r, hc);
     sync_for_mma();
     if (t == 0) {
       gemm<64, 64>(tm, sm + L::H1, sm + L::W1);
@@ -428,7 +476,7 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu64(tm + lane_off, bias + 64, sm + L::H2, r);
+    epilogue_relu<32>(tm + lane_off + hc, bias + 64, sm + L::H2, r, hc);
     sync_for_mma();
     if (t == 0) {
       gemm<16, 64>(tm, sm + L::H2, sm + L::W2);
@@ -437,7 +485,7 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    {
+    if (h == 0) {  // warp-uniform
       float o[16], dz[16];
       ld16(tm + lane_off, o);
 #pragma unroll
@@ -447,11 +495,9 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
       for (int k = 0; k < 16; ++k) dz[k] = k < OUT ? dz[k] * loss_scale : 0.0f;
       *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 0, 16)) = pack8(dz);
       *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 8, 16)) = pack8(dz + 8);
-      {
-        const float s = col_sum16(dz);
-        const int c = col_of_lane(t & 31);
-        if ((t & 1) == 0 && c < OUT) atomicAdd(db + 128 + c, s);
-      }
+      const float sum = col_sum16(dz);
+      const int c = col_of_lane(t & 31);
+      if ((t & 1) == 0 && c < OUT) atomicAdd(db + 128 + c, sum);
     }
     // ---- layer 2: dH2 = dZ2 W2, dW2 += dZ2^T H2
     sync_for_mma();
@@ -463,8 +509,8 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    relu_back64(tm + lane_off, sm + L::H2, r, ok, db + 64);  // dZ1 replaces H2
-    flush_dw<64>(tmW, OUT, slab + SL.off_W[S::DEC][2]);
+    relu_back<32>(tm + lane_off + hc, sm + L::H2, r, ok, db + 64, hc);  // dZ1 replaces H2
+    flush_dw<64, 32>(tmW, OUT, slab + SL.off_W[S::DEC][2], hc);
     // ---- layer 1: dH1 = dZ1 W1, dW1 += dZ1^T H1
     sync_for_mma();
     if (t == 0) {
@@ -475,8 +521,8 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    relu_back64(tm + lane_off, sm + L::H1, r, ok, db);  // dZ0 replaces H1
-    flush_dw<64>(tmW, 64, slab + SL.off_W[S::DEC][1]);
+    relu_back<32>(tm + lane_off + hc, sm + L::H1, r, ok, db, hc);  // dZ0 replaces H1
+    flush_dw<64, 32>(tmW, 64, slab + SL.off_W[S::DEC][1], hc);
     // ---- layer 0: dX = dZ0 W0, dW0 += dZ0^T X
     sync_for_mma();
     if (t == 0) {
@@ -488,14 +534,15 @@ __global__ void __launch_bounds__(128, 3) k_decoder_bwd_tc(typename S::Params P,
     phase ^= 1u;
     fence_after();
     {
-      float dx[S::DXC];
+      constexpr int HALF = S::DXC / 2;
+      float dx[HALF];
 #pragma unroll
-      for (int c0 = 0; c0 < S::DXC; c0 += 16) ld16(tm + lane_off + c0, dx + c0);
+      for (int c0 = 0; c0 < HALF; c0 += 16) ld16(tm + lane_off + h * HALF + c0, dx + c0);
 #pragma unroll
-      for (int k = 0; k < S::DXC; ++k) dx[k] *= inv_ls;
-      S::finish(P, F, cam, R, dx);
+      for (int k = 0; k < HALF; ++k) dx[k] *= inv_ls;
+      S::finish(P, F, cam, R, dx, h);
     }
-    flush_dw<IN>(tmW, 64, slab + SL.off_W[S::DEC][0]);
+    flush_dw<IN, IN / 2>(tmW, 64, slab + SL.off_W[S::DEC][0], h * (IN / 2));
     fence_before();
   }
   if (failed) {
@@ -531,7 +578,7 @@ static hyrf_status launch_dec_bwd(const typename S::Params& P, const FieldsDev& 
   constexpr int smem = tc::BwdSmem<S::IN>::SIZE;
   cudaFuncSetAttribute(tc::k_decoder_bwd_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   HYRF_LAUNCH(S::kName, s,
-              tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 128, smem, s>>>(P, F, cam, ls, SL, slabs, status));
+              tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 256, smem, s>>>(P, F, cam, ls, SL, slabs, status));
   return HYRF_OK;
 }
 

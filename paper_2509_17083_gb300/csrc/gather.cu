@@ -125,6 +125,11 @@ __device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, u
 template <bool COHERENT, bool WANT_DY>
 __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const float y[3], float d0, float d1,
                                               float* __restrict__ gtab, float dy[3]) {
+  if (WANT_DY) dy[0] = dy[1] = dy[2] = 0.0f;
+  // A zero feature gradient adds nothing to the table and nothing to dL/dy
+  // (every term carries d0 or d1): skip the level. Not in COHERENT mode,
+  // whose lanes must all reach the shuffles.
+  if (!COHERENT && d0 == 0.0f && d1 == 0.0f) return;
   uint32_t idx[8];
   float f[3];
   level_cell(G, l, y, idx, f);
@@ -189,15 +194,16 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
   const int r = threadIdx.x >> 4, wd = threadIdx.x & 15;
   if (row0 + r < nrows) {
     const size_t o = (size_t)(row0 + r) * 16 + wd;
-    if (BOTH) Xg[o] = xs[0][r][wd];
-    Xr[o] = xs[1][r][wd];
+    if (BOTH) __stcs(Xg + o, xs[0][r][wd]);
+    __stcs(Xr + o, xs[1][r][wd]);
   }
 }
 
 // Reverse of k_gather. dXg/dXr: [rows][32] f32 feature gradients (already
-// unscaled). Gaussians: d_pos[g] += J^T sum_l dL/dy_l over both fields.
-template <bool BOTH>
-__global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
+// unscaled; streamed with evict-first loads). Gaussians: both fields, and
+// d_pos[g] += J^T sum_l dL/dy_l; pixels: the radiance field.
+template <bool GAUSS>
+__global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
     k_scatter(FieldsDev F, CamDev cam, RowSource S, const float* __restrict__ dXg,
               const float* __restrict__ dXr, float* __restrict__ g_geo, float* __restrict__ g_rad,
               float* __restrict__ d_pos) {
@@ -209,15 +215,14 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
   const int nrows = row_count(S, cam);
   const int row0 = blockIdx.x * kRows;
   if (row0 >= nrows) return;  // CTA-uniform
-  const bool gauss = !S.pixels;
   if (l == 0) {
     float y[3], J[9];
     int g;
     bool ok;
-    row_point(S, F, cam, row0 + lane, nrows, y, gauss ? J : nullptr, g, ok);
+    row_point(S, F, cam, row0 + lane, nrows, y, GAUSS ? J : nullptr, g, ok);
 #pragma unroll
     for (int k = 0; k < 3; ++k) ys[lane][k] = y[k];
-    if (gauss) {
+    if (GAUSS) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) Js[lane][k] = J[k];
     }
@@ -227,20 +232,16 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
   const int row = row0 + lane;
   const bool ok = gs[lane] >= 0;
   const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
-  float dy[3] = {0.0f, 0.0f, 0.0f};
-  if (gauss) {
-    float2 dr = ok ? *reinterpret_cast<const float2*>(dXr + (size_t)row * 32 + 2 * l) : make_float2(0.0f, 0.0f);
-    level_scatter<false, true>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
-    if (BOTH) {
-      const float2 dg =
-          ok ? *reinterpret_cast<const float2*>(dXg + (size_t)row * 32 + 2 * l) : make_float2(0.0f, 0.0f);
-      float dy2[3];
-      level_scatter<false, true>(F.geo, l, y, dg.x, dg.y, g_geo, dy2);
+  const size_t o = (size_t)row * 32 + 2 * l;
+  const float2 zero = make_float2(0.0f, 0.0f);
+  if (GAUSS) {
+    const float2 dg = ok ? __ldcs(reinterpret_cast<const float2*>(dXg + o)) : zero;
+    const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
+    float dy[3], dy2[3];
+    level_scatter<false, true>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
+    level_scatter<false, true>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dy[k] += dy2[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dys[l][lane][k] = dy[k];
+    for (int k = 0; k < 3; ++k) dys[l][lane][k] = dy[k] + dy2[k];
     __syncthreads();
     if (l == 0 && ok) {
       float s[3] = {0.0f, 0.0f, 0.0f};
@@ -255,7 +256,8 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
       for (int j = 0; j < 3; ++j) d_pos[3 * (int64_t)g + j] += J[j] * s[0] + J[3 + j] * s[1] + J[6 + j] * s[2];
     }
   } else {
-    float2 dr = ok ? *reinterpret_cast<const float2*>(dXr + (size_t)row * 32 + 2 * l) : make_float2(0.0f, 0.0f);
+    const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
+    float dy[3];
     level_scatter<true, false>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
   }
 }

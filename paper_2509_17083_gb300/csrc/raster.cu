@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(
   atomicMax(&max_last, last);
   __syncthreads();
   const int stop = start + max_last;  // no pixel of the tile used list positions >= stop
+  // nor did any pixel of this warp use positions >= wstop (warp-uniform bound)
+  const int wstop = start + __reduce_max_sync(0xffffffffu, last);
   float T = Tf;
   float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;  // colour behind, normalised by T after the current one
   float la = 0.0f, lc0 = 0.0f, lc1 = 0.0f, lc2 = 0.0f;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(
       sg[t] = g;
     }
     __syncthreads();
-    for (int j = b1 - b0 - 1; j >= 0; --j) {
+    for (int j = min(b1, wstop) - b0 - 1; j >= 0; --j) {
       const int pos = b0 - start + j;  // list position
       float gu = 0.0f, gv = 0.0f, ga = 0.0f, gb = 0.0f, gc = 0.0f, go = 0.0f, gr = 0.0f,
             gg = 0.0f, gbl = 0.0f;

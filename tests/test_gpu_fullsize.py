@@ -143,9 +143,9 @@ def test_fullsize_rasterize_forward_and_reverse(scene):
         assert e < TOL_GRAD_F32, (key, e)
 
 
-def _sample(ids, seed):
+def _sample(ids, seed, k=N_SAMPLE):
     rng = np.random.default_rng(seed)
-    return np.sort(rng.choice(len(ids), N_SAMPLE, replace=False))
+    return np.sort(rng.choice(len(ids), k, replace=False))
 
 
 def test_fullsize_field_query_sampled(scene):
@@ -174,11 +174,13 @@ def test_fullsize_field_query_reverse_sampled(scene):
     g = w.gaussians
     cam = w.cams[0]
     nv = len(ids)
-    rows = _sample(ids, 24)
+    # trained-like tables put ~9 of 10 rows within the bf16 ReLU margin of a
+    # kink somewhere in their 128 hidden units: sample widely, keep the safe
+    rows = _sample(ids, 24, 16 * N_SAMPLE)
     sel = ids[rows]
     ok = oracle.relu_safe_mask(g, w.fields, cam, sel, *RELU_MARGIN_BF16)
     rows, sel = rows[ok > 0], sel[ok > 0]
-    assert len(rows) > N_SAMPLE // 2
+    assert len(rows) > N_SAMPLE // 2, len(rows)
     rng = np.random.default_rng(25)
     up = [(rng.standard_normal((len(rows),) + sh) * 1e-3).astype(np.float32)
           for sh in [(), (3,), (4,), (3,)]]
