@@ -29,6 +29,12 @@ __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis,
   }
 }
 
+// exp of the (non-positive) splat exponent with the hardware exponential
+// (relative error ~1e-6 here, far inside the compositing tolerances); the
+// forward and the reverse pass evaluate it identically, so their
+// threshold decisions agree bit for bit.
+__device__ __forceinline__ float splat_exp(float power) { return __expf(power); }
+
 // Exponent of the 2D Gaussian at offset (dx, dy) = mean - pixel centre, with
 // a fixed multiply-add order shared by the forward and the reverse pass.
 __device__ __forceinline__ float splat_power(float ca, float cb, float cc, float dx, float dy) {
@@ -76,7 +82,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
       const float dx = r0.x - fx, dy = r0.y - fy;
       const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
       if (power > 0.0f) continue;
-      const float alpha = fminf(kAlphaMax, r1.y * expf(power));
+      const float alpha = fminf(kAlphaMax, r1.y * splat_exp(power));
       if (alpha < kAlphaMin) continue;
       const float test_T = T * (1.0f - alpha);
       if (test_T < kTMin) {
@@ -133,102 +139,129 @@ __device__ __forceinline__ int col8(int lane) {
   return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-__global__ void __launch_bounds__(256) k_raster_bwd(
+// State of one pixel's back-to-front walk: T before the current Gaussian
+// (recovered from T_final), the colour composited behind it (normalised by T
+// after it), the previous contributor, and the pixel's upstream gradients.
+struct PixBack {
+  float fx, fy, Tf, T, g0, g1, g2, gT, a0, a1, a2, la, lc0, lc1, lc2;
+  int last;
+};
+
+__device__ __forceinline__ void pix_init(PixBack& q, int px, int py, int W, int H,
+                                         const float* __restrict__ T_final,
+                                         const int32_t* __restrict__ n_contrib,
+                                         const float* __restrict__ dC, const float* __restrict__ dT) {
+  const bool inside = px < W && py < H;
+  const int p = inside ? py * W + px : 0;
+  q.fx = (float)px + 0.5f;
+  q.fy = (float)py + 0.5f;
+  q.Tf = inside ? T_final[p] : 1.0f;
+  q.T = q.Tf;
+  q.last = inside ? n_contrib[p] : 0;
+  q.g0 = inside ? dC[3 * p] : 0.0f;
+  q.g1 = inside ? dC[3 * p + 1] : 0.0f;
+  q.g2 = inside ? dC[3 * p + 2] : 0.0f;
+  q.gT = inside ? dT[p] : 0.0f;
+  q.a0 = q.a1 = q.a2 = q.la = q.lc0 = q.lc1 = q.lc2 = 0.0f;
+}
+
+// Reverse of one (pixel, Gaussian) compositing step at list position pos:
+// adds dL/d(mean2d u, v, conic a, b, c, opacity, colour r, g, b) of this
+// pixel to acc; false if the Gaussian did not contribute to the pixel.
+__device__ __forceinline__ bool pix_step(PixBack& q, int pos, const float4& r0, const float4& r1, float cb,
+                                         float* acc) {
+  if (pos >= q.last) return false;
+  const float dx = r0.x - q.fx, dy = r0.y - q.fy;
+  const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
+  if (power > 0.0f) return false;
+  const float G = splat_exp(power);
+  const float oG = r1.y * G;
+  const float alpha = fminf(kAlphaMax, oG);
+  if (alpha < kAlphaMin) return false;
+  const float inv = __fdividef(1.0f, 1.0f - alpha);  // 1 - alpha >= 0.01
+  q.T = q.T * inv;                                   // T before this Gaussian
+  q.a0 = q.la * q.lc0 + (1.0f - q.la) * q.a0;
+  q.a1 = q.la * q.lc1 + (1.0f - q.la) * q.a1;
+  q.a2 = q.la * q.lc2 + (1.0f - q.la) * q.a2;
+  q.la = alpha;
+  q.lc0 = r1.z;
+  q.lc1 = r1.w;
+  q.lc2 = cb;
+  const float w = alpha * q.T;
+  acc[6] += w * q.g0;
+  acc[7] += w * q.g1;
+  acc[8] += w * q.g2;
+  float dal = ((r1.z - q.a0) * q.g0 + (r1.w - q.a1) * q.g1 + (cb - q.a2) * q.g2) * q.T;
+  dal -= q.gT * q.Tf * inv;
+  if (oG <= kAlphaMax) {
+    acc[5] += dal * G;
+    const float dp = dal * alpha;
+    acc[0] += dp * (-(r0.z * dx) - r0.w * dy);
+    acc[1] += dp * (-(r1.x * dy) - r0.w * dx);
+    acc[2] += dp * (-0.5f * dx * dx);
+    acc[3] += dp * (-(dx * dy));
+    acc[4] += dp * (-0.5f * dy * dy);
+  }
+  return true;
+}
+
+// Two pixels per thread, (x, y) and (x, y + 2): a warp covers four rows of the
+// tile, so each warp-level reduction of a Gaussian's gradient sums 64 pixels.
+constexpr int kBwdRasterThreads = 128;
+
+__global__ void __launch_bounds__(kBwdRasterThreads) k_raster_bwd(
     const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
     const float4* __restrict__ rec, int W, int H, int TX, const float* __restrict__ T_final,
     const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
     const float* __restrict__ dT, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
     float* __restrict__ d_alpha, float* __restrict__ d_color) {
-  __shared__ float4 s0[256], s1[256], s2[256];
-  __shared__ int sg[256];
+  constexpr int B = 256;  // Gaussians staged per batch
+  __shared__ float4 s0[B], s1[B], s2[B];
+  __shared__ int sg[B];
   __shared__ int max_last;
   const int tile = blockIdx.x;
-  const int t = threadIdx.x, lane = t & 31;
-  const int px = (tile % TX) * kTile + (t % kTile);
-  const int py = (tile / TX) * kTile + (t / kTile);
-  const bool inside = px < W && py < H;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  const int px = (tile % TX) * kTile + (lane & 15);
+  const int py = (tile / TX) * kTile + 4 * wp + (lane >> 4);
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
-  const int p = inside ? py * W + px : 0;
-  const float Tf = inside ? T_final[p] : 1.0f;
-  const int last = inside ? n_contrib[p] : 0;
-  const float g0 = inside ? dC[3 * p] : 0.0f, g1 = inside ? dC[3 * p + 1] : 0.0f,
-              g2 = inside ? dC[3 * p + 2] : 0.0f;
-  const float gT = inside ? dT[p] : 0.0f;
+  PixBack A, Bq;
+  pix_init(A, px, py, W, H, T_final, n_contrib, dC, dT);
+  pix_init(Bq, px, py + 2, W, H, T_final, n_contrib, dC, dT);
+  const int mylast = max(A.last, Bq.last);
   if (t == 0) max_last = 0;
   __syncthreads();
-  atomicMax(&max_last, last);
+  atomicMax(&max_last, mylast);
   __syncthreads();
-  const int stop = start + max_last;  // no pixel of the tile used list positions >= stop
+  const int stop = min(end, start + max_last);  // no pixel of the tile used positions >= stop
   // nor did any pixel of this warp use positions >= wstop (warp-uniform bound)
-  const int wstop = start + __reduce_max_sync(0xffffffffu, last);
-  float T = Tf;
-  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;  // colour behind, normalised by T after the current one
-  float la = 0.0f, lc0 = 0.0f, lc1 = 0.0f, lc2 = 0.0f;
-  for (int b1 = stop; b1 > start; b1 -= 256) {
-    const int b0 = max(start, b1 - 256);
+  const int wstop = start + __reduce_max_sync(0xffffffffu, mylast);
+  for (int b1 = stop; b1 > start; b1 -= B) {
+    const int b0 = max(start, b1 - B);
     __syncthreads();
-    const int k = b0 + t;
-    if (k < b1) {
-      int g = vals[k];
+    for (int e = t; e < b1 - b0; e += kBwdRasterThreads) {
+      int g = vals[b0 + e];
       if (g < 0 || g >= n) {
         g = -1;
-        s1[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s1[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // opacity 0: never contributes
       } else {
-        s0[t] = rec[3 * g];
-        s1[t] = rec[3 * g + 1];
-        s2[t] = rec[3 * g + 2];
+        s0[e] = rec[3 * g];
+        s1[e] = rec[3 * g + 1];
+        s2[e] = rec[3 * g + 2];
       }
-      sg[t] = g;
+      sg[e] = g;
     }
     __syncthreads();
     for (int j = min(b1, wstop) - b0 - 1; j >= 0; --j) {
       const int pos = b0 - start + j;  // list position
-      float gu = 0.0f, gv = 0.0f, ga = 0.0f, gb = 0.0f, gc = 0.0f, go = 0.0f, gr = 0.0f,
-            gg = 0.0f, gbl = 0.0f;
-      bool contrib = false;
-      if (pos < last) {
-        const float4 r0 = s0[j], r1 = s1[j];
-        const float dx = r0.x - fx, dy = r0.y - fy;
-        const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
-        if (power <= 0.0f) {
-          const float G = expf(power);
-          const float oG = r1.y * G;
-          const float alpha = fminf(kAlphaMax, oG);
-          if (alpha >= kAlphaMin) {
-            contrib = true;
-            T = T / (1.0f - alpha);  // T before this Gaussian
-            const float cb = s2[j].x;
-            a0 = la * lc0 + (1.0f - la) * a0;
-            a1 = la * lc1 + (1.0f - la) * a1;
-            a2 = la * lc2 + (1.0f - la) * a2;
-            la = alpha;
-            lc0 = r1.z;
-            lc1 = r1.w;
-            lc2 = cb;
-            const float w = alpha * T;
-            gr = w * g0;
-            gg = w * g1;
-            gbl = w * g2;
-            float dal = ((r1.z - a0) * g0 + (r1.w - a1) * g1 + (cb - a2) * g2) * T;
-            dal -= gT * Tf / (1.0f - alpha);
-            if (oG <= kAlphaMax) {
-              go = dal * G;
-              const float dp = dal * alpha;
-              gu = dp * (-(r0.z * dx) - r0.w * dy);
-              gv = dp * (-(r1.x * dy) - r0.w * dx);
-              ga = dp * (-0.5f * dx * dx);
-              gb = dp * (-(dx * dy));
-              gc = dp * (-0.5f * dy * dy);
-            }
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
+      const float4 r0 = s0[j], r1 = s1[j];
+      const float cb = s2[j].x;
+      float acc[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      const bool ca = pix_step(A, pos, r0, r1, cb, acc);
+      const bool cbq = pix_step(Bq, pos, r0, r1, cb, acc);
+      if (__any_sync(0xffffffffu, ca || cbq)) {
         // mean2d (2), conic (3), opacity, colour r, g: one sum per lane group
-        float v8[8] = {gu, gv, ga, gb, gc, go, gr, gg};
-        const float s8 = reduce8(v8);
-        gbl = warp_sum(gbl);
+        const float s8 = reduce8(acc);
+        const float sb = warp_sum(acc[8]);
         const int g = sg[j];
         if (g >= 0) {
           if ((lane & 3) == 0) {
@@ -239,7 +272,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(
                                   : d_color + 3 * g + (c - 6);
             atomicAdd(dst, s8);
           }
-          if (lane == 1) atomicAdd(d_color + 3 * g + 2, gbl);
+          if (lane == 1) atomicAdd(d_color + 3 * g + 2, sb);
         }
       }
     }
@@ -283,7 +316,7 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
   HYRF_LAUNCH("k_raster_bwd", s,
-              k_raster_bwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
+              k_raster_bwd<<<TX * TY, kBwdRasterThreads, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
                                        a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
                                        b.d_alpha, b.d_color));
   return HYRF_OK;

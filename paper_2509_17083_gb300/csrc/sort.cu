@@ -234,7 +234,11 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int64_t* __restrict__ sums, 
 }
 
 // Per sorted Gaussian j: instance offset, then its tiles in row-major order
-// (instances beyond the capacity are dropped).
+// (instances beyond the capacity are dropped). A CTA owns a chunk of
+// kScanChunk Gaussians: it scans their tile counts into shared memory, then
+// its threads walk the chunk's instances with unit stride (coalesced
+// stores, no per-Gaussian loop), each finding its Gaussian by binary search
+// of the offsets.
 __global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ ntiles,
                                               const int32_t* __restrict__ rect,
                                               const int32_t* __restrict__ order,
@@ -242,39 +246,59 @@ __global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ ntiles
                                               const int64_t* __restrict__ sums, int TX,
                                               int64_t capacity, uint32_t* __restrict__ tile_keys,
                                               int32_t* __restrict__ tile_vals) {
-  __shared__ int64_t wsum[8];
+  __shared__ int32_t soff[kScanChunk + 1];  // exclusive offsets within the chunk
+  __shared__ int32_t sid[kScanChunk];       // Gaussian ids
+  __shared__ int32_t wsum[8];
+  __shared__ int32_t carry;
   const int n = clamp_n(n_ptr, cap_n);
   const int64_t start = (int64_t)blockIdx.x * kScanChunk;
-  int64_t run = sums[blockIdx.x];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = sums[blockIdx.x];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) carry = 0;
+  __syncthreads();
   for (int k = 0; k < kScanChunk / 256; ++k) {
-    const int64_t j = start + k * 256 + threadIdx.x;
+    const int64_t j = start + k * 256 + t;
     const int c = j < n ? tiles_of_sorted(ntiles, order, (int)j, cap_n) : 0;
-    int64_t x = c;
+    sid[k * 256 + t] = j < n ? order[j] : -1;
+    int x = c;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
-    int64_t before = 0, tot = 0;
+    int before = 0, tot = 0;
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
       before += q < w ? wsum[q] : 0;
       tot += wsum[q];
     }
-    int64_t off = run + before + x - c;
-    if (c > 0) {
-      const int g = order[j];
-      const int x0 = rect[4 * g], y0 = rect[4 * g + 1], x1 = rect[4 * g + 2], y1 = rect[4 * g + 3];
-      for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx, ++off) {
-          if (off >= capacity) break;
-          tile_keys[off] = (uint32_t)(ty * TX + tx);
-          tile_vals[off] = g;
-        }
-    }
-    run += tot;
+    soff[k * 256 + t] = carry + before + x - c;
     __syncthreads();
+    if (t == 0) carry += tot;
+    __syncthreads();
+  }
+  if (t == 0) soff[kScanChunk] = carry;
+  __syncthreads();
+  const int total = soff[kScanChunk];
+  for (int e = t; e < total; e += 256) {
+    const int64_t off = base + e;
+    if (off >= capacity) break;
+    int lo = 0, hi = kScanChunk;  // soff[lo] <= e < soff[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (soff[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    const int g = sid[lo];
+    const int r = e - soff[lo];
+    const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2);
+    const int wdt = x1 - x0;
+    if (wdt <= 0) continue;  // rect inconsistent with ntiles: nothing sensible to emit
+    const int ty = y0 + r / wdt, tx = x0 + r % wdt;
+    tile_keys[off] = (uint32_t)(ty * TX + tx);
+    tile_vals[off] = g;
   }
 }
 
