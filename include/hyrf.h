@@ -407,6 +407,40 @@ typedef struct {
 size_t hyrf_loss_workspace_size(const hyrf_loss_args* a);
 hyrf_status hyrf_loss(const hyrf_loss_args* a, void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * hyrf_adam_step: one Adam update (Kingma & Ba) of a list of float32
+ * parameter tensors, the optimiser the paper inherits from 3DGS for the
+ * explicit parameters and from Instant-NGP for the fields (Sec. 4.1: "other
+ * hyperparameters as 3DGS"). Per element, with g = grad_scale * grad:
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   p -= lr * lr_scale * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps),
+ * then, if `shadow` is set, shadow = bf16(p) (round to nearest even): the
+ * working copy of a BF16 table or weight matrix whose float32 master is p.
+ * All tensors are updated by one launch (at most HYRF_ADAM_MAX_TENSORS per
+ * call). Pointers are device pointers to n contiguous elements, 16-byte
+ * aligned; m and v are caller-owned state (zero before the first step).
+ * Errors: HYRF_ERR_INVALID_ARG for a bad count, hyper-parameter or pointer.
+ * ---------------------------------------------------------------------- */
+#define HYRF_ADAM_MAX_TENSORS 32
+typedef struct {
+  float* param;              /* [n] float32 master values, updated in place */
+  const float* grad;         /* [n] float32 */
+  float* m;                  /* [n] float32 first moment */
+  float* v;                  /* [n] float32 second moment */
+  void* shadow;              /* optional [n] bf16 working copy, or NULL */
+  int64_t n;
+  float lr_scale;            /* multiplies lr for this tensor */
+} hyrf_adam_tensor;
+
+typedef struct {
+  float lr, beta1, beta2, eps;
+  int32_t step;              /* t >= 1, for the bias corrections */
+  float grad_scale;
+} hyrf_adam_hparams;
+
+hyrf_status hyrf_adam_step(const hyrf_adam_tensor* tensors, int32_t count,
+                           const hyrf_adam_hparams* hp, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Synchronises `stream`, copies the device status word to *host_out (host
  * pointer) and returns it as hyrf_status bits (HYRF_ERR_CUDA if the copy

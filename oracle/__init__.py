@@ -454,6 +454,18 @@ def loss(C_img, target, lam):
     return L, dC
 
 
+def adam_step(p, grad, m, v, lr, b1, b2, eps, t, grad_scale=1.0):
+    """One Adam step (Kingma & Ba, Algorithm 1) on float64 copies; returns
+    the updated (p, m, v)."""
+    p, m, v = [np.array(x, dtype=np.float64).ravel() for x in (p, m, v)]
+    g = np.ascontiguousarray(grad, dtype=np.float64).ravel()
+    rc = lib().orc_adam_step(C.c_int64(len(p)), _ptr(p, _f64p), _ptr(g, _f64p), _ptr(m, _f64p),
+                             _ptr(v, _f64p), C.c_double(lr), C.c_double(b1), C.c_double(b2),
+                             C.c_double(eps), C.c_int32(t), C.c_double(grad_scale))
+    assert rc == 0
+    return p, m, v
+
+
 def ssim(x, y):
     keep = _Keep()
     H, W = x.shape[:2]

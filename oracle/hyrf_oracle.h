@@ -37,6 +37,8 @@
  *                    form, FD gradient
  *   whole path       reduction to isotropic 3DGS (Tab. 5 "w/o Neural"); FD of
  *                    the loss w.r.t. every parameter class
+ *   Adam             first-step closed form p - lr g / (|g| + eps); constant
+ *                    gradient over t steps; zero gradient decays the moments
  */
 #ifndef HYRF_ORACLE_H
 #define HYRF_ORACLE_H
@@ -224,6 +226,14 @@ double orc_loss(int32_t width, int32_t height, const double* C, const double* ta
 /* SSIM alone (11x11 Gaussian window, sigma 1.5, zero padding), mean over
  * pixels and channels. */
 double orc_ssim(int32_t width, int32_t height, const double* x, const double* y);
+
+/* ---------------- training: Adam (Kingma & Ba, Algorithm 1) ------------- */
+/* One Adam step of n parameters in place (3DGS and Instant-NGP train with
+ * it; the paper keeps 3DGS's other hyper-parameters, Sec. 4.1). With
+ * g = grad_scale * grad: m <- b1 m + (1 - b1) g; v <- b2 v + (1 - b2) g^2;
+ * p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+int32_t orc_adam_step(int64_t n, double* p, const double* grad, double* m, double* v, double lr,
+                      double b1, double b2, double eps, int32_t t, double grad_scale);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,7 @@ UNITS = {
     "fields_tc": ("fields_tc.cu", []),
     "fields_tc_bwd": ("fields_tc_bwd.cu", []),
     "gather": ("gather.cu", []),
+    "optim": ("optim.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
     "noalloc": ("noalloc.cu", []),

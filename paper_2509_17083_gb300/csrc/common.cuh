@@ -1,5 +1,6 @@
 // Internal definitions shared by the libhyrf translation units.
 #pragma once
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -94,6 +95,20 @@ struct Carver {
 };
 
 int num_sms();
+
+// Raise a kernel's dynamic shared-memory limit once per device: the
+// attribute persists, so later calls (for instance during CUDA graph
+// capture) make no API call.
+template <auto Kern>
+inline void set_smem_limit(int bytes) {
+  static std::atomic<uint64_t> done{0};  // bit d: set on device d
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done.fetch_or(bit, std::memory_order_release);
+}
 
 // Records a CUDA event pair on `s` around the launches in its scope while the
 // kernel timer is enabled (hyrf_timer_enable); otherwise does nothing.

@@ -586,10 +586,6 @@ hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float r
                                   float* dC_fg, float* dT, float* dmap, cudaStream_t s);
 SlabTargets slab_targets(const hyrf_field_grads& g, bool geo);
 
-template <class K>
-static void set_smem(K kernel, size_t bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 #if HYRF_FIELDS_PART == 0
 
@@ -824,7 +820,7 @@ static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const Q
   const int ctas = bwd_ctas();
   cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
   const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
-  set_smem(k_query_bwd<NL, WID, NH, WT>, smem);
+  set_smem_limit<k_query_bwd<NL, WID, NH, WT>>((int)smem);
   HYRF_LAUNCH("k_query_bwd", s,
               k_query_bwd<NL, WID, NH, WT><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs));
   return launch_slab_reduce(slabs, ctas, SL, slab_targets(grads, true), 1.0f / io.loss_scale, s);
@@ -873,7 +869,7 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
   cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
   const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
   if (a.bg.mode == 0) {
-    set_smem(k_bg_field_bwd<NL, WID, NH, 0, WT>, smem);
+    set_smem_limit<k_bg_field_bwd<NL, WID, NH, 0, WT>>((int)smem);
     HYRF_LAUNCH("k_bg_field_bwd", s,
                 k_bg_field_bwd<NL, WID, NH, 0, WT><<<ctas, kBwdThreads, smem, s>>>(
         F, cam, a.bg.radius, 0, 0, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, nullptr,
@@ -886,7 +882,7 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
     hyrf_status st = launch_bg_map_bwd_pix(F, cam, a.bg.radius, Hb, Wb, map, a.T_final, b.d_C,
                                            b.d_C_fg, b.d_T_final, dmap, s);
     if (st != HYRF_OK) return st;
-    set_smem(k_bg_field_bwd<NL, WID, NH, 1, WT>, smem);
+    set_smem_limit<k_bg_field_bwd<NL, WID, NH, 1, WT>>((int)smem);
     HYRF_LAUNCH("k_bg_field_bwd", s,
                 k_bg_field_bwd<NL, WID, NH, 1, WT><<<ctas, kBwdThreads, smem, s>>>(
         F, cam, a.bg.radius, Hb, Wb, nullptr, nullptr, nullptr, nullptr, dmap, b.grads.rad_table,

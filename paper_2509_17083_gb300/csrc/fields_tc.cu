@@ -326,7 +326,7 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
   if (st != HYRF_OK) return st;
   tc::QueryIO io{a.n,     a.pos, a.alpha_e, a.scale_e, a.color_e, a.vis_ids, a.n_vis,
                  Xg,      Xr,    a.alpha,   a.scale,   a.quat,    a.color,   a.status};
-  cudaFuncSetAttribute(tc::k_query_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kQuerySmem);
+  set_smem_limit<tc::k_query_fwd_tc>(tc::kQuerySmem);
   int tiles = (a.n + 127) / 128;
   int grid = num_sms() * 2;
   if (tiles < grid) grid = tiles;
@@ -342,7 +342,7 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
   const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status};
   hyrf_status st = launch_gather(F, cam, RS, P, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
-  cudaFuncSetAttribute(tc::k_bg_exact_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kBgSmem);
+  set_smem_limit<tc::k_bg_exact_fwd_tc>(tc::kBgSmem);
   int tiles = (P + 127) / 128;
   int grid = num_sms() * 4;
   if (tiles < grid) grid = tiles;

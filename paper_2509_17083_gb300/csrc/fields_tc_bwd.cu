@@ -576,7 +576,7 @@ static hyrf_status launch_dec_bwd(const typename S::Params& P, const FieldsDev& 
                                   float ls, const SlabLayout& SL, float* slabs, int32_t* status,
                                   cudaStream_t s) {
   constexpr int smem = tc::BwdSmem<S::IN>::SIZE;
-  cudaFuncSetAttribute(tc::k_decoder_bwd_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  set_smem_limit<tc::k_decoder_bwd_tc<S>>(smem);
   HYRF_LAUNCH(S::kName, s,
               tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 256, smem, s>>>(P, F, cam, ls, SL, slabs, status));
   return HYRF_OK;

@@ -233,72 +233,114 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int64_t* __restrict__ sums, 
   }
 }
 
-// Per sorted Gaussian j: instance offset, then its tiles in row-major order
-// (instances beyond the capacity are dropped). A CTA owns a chunk of
-// kScanChunk Gaussians: it scans their tile counts into shared memory, then
-// its threads walk the chunk's instances with unit stride (coalesced
-// stores, no per-Gaussian loop), each finding its Gaussian by binary search
-// of the offsets.
-__global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ ntiles,
-                                              const int32_t* __restrict__ rect,
-                                              const int32_t* __restrict__ order,
-                                              const int32_t* __restrict__ n_ptr, int cap_n,
-                                              const int64_t* __restrict__ sums, int TX,
-                                              int64_t capacity, uint32_t* __restrict__ tile_keys,
-                                              int32_t* __restrict__ tile_vals) {
-  __shared__ int32_t soff[kScanChunk + 1];  // exclusive offsets within the chunk
-  __shared__ int32_t sid[kScanChunk];       // Gaussian ids
-  __shared__ int32_t wsum[8];
-  __shared__ int32_t carry;
+// Instance offset of every sorted Gaussian: the chunk's base (k_scan_sums)
+// plus the exclusive scan of the tile counts inside the chunk. off[n] = K
+// (unclamped total, saturated to 32 bits).
+__global__ void __launch_bounds__(256) k_offsets(const int32_t* __restrict__ ntiles,
+                                                 const int32_t* __restrict__ order,
+                                                 const int32_t* __restrict__ n_ptr, int cap_n,
+                                                 const int64_t* __restrict__ sums, int nchunks,
+                                                 uint32_t* __restrict__ off) {
+  __shared__ int64_t wsum[8];
   const int n = clamp_n(n_ptr, cap_n);
   const int64_t start = (int64_t)blockIdx.x * kScanChunk;
-  const int64_t base = sums[blockIdx.x];
+  int64_t run = sums[blockIdx.x];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  if (t == 0) carry = 0;
-  __syncthreads();
   for (int k = 0; k < kScanChunk / 256; ++k) {
     const int64_t j = start + k * 256 + t;
     const int c = j < n ? tiles_of_sorted(ntiles, order, (int)j, cap_n) : 0;
-    sid[k * 256 + t] = j < n ? order[j] : -1;
-    int x = c;
+    int64_t x = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
-    int before = 0, tot = 0;
+    int64_t before = 0, tot = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       before += q < w ? wsum[q] : 0;
       tot += wsum[q];
     }
-    soff[k * 256 + t] = carry + before + x - c;
-    __syncthreads();
-    if (t == 0) carry += tot;
+    const int64_t o = run + before + x - c;
+    if (j < n) off[j] = (uint32_t)(o < 0xffffffffll ? o : 0xffffffffll);
+    run += tot;
     __syncthreads();
   }
-  if (t == 0) soff[kScanChunk] = carry;
+  if (blockIdx.x == nchunks - 1 && t == 0) off[n] = (uint32_t)(run < 0xffffffffll ? run : 0xffffffffll);
+}
+
+// Largest index i in [lo, hi] with a[i] <= e (a non-decreasing, a[lo] <= e).
+template <class A>
+__device__ __forceinline__ int last_le(const A& a, int lo, int hi, uint32_t e) {
+  ++hi;  // a[hi] > e or hi one past the range
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kExpandItems = 2048;  // instances per CTA
+constexpr int kExpandSlice = 2048;  // sorted Gaussians cached per CTA
+
+// Each CTA writes a fixed range of instances (balanced however unequal the
+// Gaussians' footprints are): it finds the sorted Gaussians that own its
+// range, caches their offsets, and its threads write consecutive instances
+// (coalesced), each finding its owner by binary search. Instance r of a
+// Gaussian with rectangle [x0, x1) x [y0, y1) is tile (y0 + r / w, x0 + r % w):
+// row-major order.
+__global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect,
+                                                const int32_t* __restrict__ order,
+                                                const int32_t* __restrict__ n_ptr, int cap_n,
+                                                const uint32_t* __restrict__ off,
+                                                const int32_t* __restrict__ k_ptr, int cap_k, int TX,
+                                                uint32_t* __restrict__ tile_keys,
+                                                int32_t* __restrict__ tile_vals) {
+  __shared__ uint32_t soff[kExpandSlice + 1];
+  __shared__ int32_t sid[kExpandSlice];
+  __shared__ int range[2];
+  const int n = clamp_n(n_ptr, cap_n);
+  const int K = clamp_n(k_ptr, cap_k);
+  const int64_t e0 = (int64_t)blockIdx.x * kExpandItems;
+  if (e0 >= K || n == 0) return;  // CTA-uniform
+  const int e1 = (int)(e0 + kExpandItems < K ? e0 + kExpandItems : K);
+  const int t = threadIdx.x;
+  if (t == 0) {
+    range[0] = last_le(off, 0, n - 1, (uint32_t)e0);
+    range[1] = last_le(off, range[0], n - 1, (uint32_t)(e1 - 1));
+  }
   __syncthreads();
-  const int total = soff[kScanChunk];
-  for (int e = t; e < total; e += 256) {
-    const int64_t off = base + e;
-    if (off >= capacity) break;
-    int lo = 0, hi = kScanChunk;  // soff[lo] <= e < soff[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (soff[mid] <= e) lo = mid;
-      else hi = mid;
+  const int jlo = range[0], jhi = range[1];
+  const int L = jhi - jlo + 1;
+  const bool cached = L <= kExpandSlice;
+  if (cached) {
+    for (int i = t; i < L; i += 256) {
+      soff[i] = off[jlo + i];
+      sid[i] = order[jlo + i];
     }
-    const int g = sid[lo];
-    const int r = e - soff[lo];
+    if (t == 0) soff[L] = off[jhi + 1];
+  }
+  __syncthreads();
+  for (int e = (int)e0 + t; e < e1; e += 256) {
+    int g, r;
+    if (cached) {
+      const int i = last_le(soff, 0, L - 1, (uint32_t)e);
+      g = sid[i];
+      r = e - (int)soff[i];
+    } else {
+      const int j = last_le(off, jlo, jhi, (uint32_t)e);
+      g = order[j];
+      r = e - (int)off[j];
+    }
+    if (g < 0 || g >= cap_n) continue;
     const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2);
     const int wdt = x1 - x0;
     if (wdt <= 0) continue;  // rect inconsistent with ntiles: nothing sensible to emit
-    const int ty = y0 + r / wdt, tx = x0 + r % wdt;
-    tile_keys[off] = (uint32_t)(ty * TX + tx);
-    tile_vals[off] = g;
+    tile_keys[e] = (uint32_t)((y0 + r / wdt) * TX + x0 + r % wdt);
+    tile_vals[e] = g;
   }
 }
 
@@ -353,6 +395,7 @@ struct SortWs {
   int32_t *dv_a, *dv_b, *tv_b;
   uint32_t *hist, *totals;
   int64_t* sums;
+  uint32_t* off;
 };
 
 static SortWs carve_sort(Carver& c, int n, int64_t cap) {
@@ -369,6 +412,7 @@ static SortWs carve_sort(Carver& c, int n, int64_t cap) {
   w.hist = c.take<uint32_t>((size_t)256 * G);
   w.totals = c.take<uint32_t>(256);
   w.sums = c.take<int64_t>((n + kScanChunk - 1) / kScanChunk + 1);
+  w.off = c.take<uint32_t>((size_t)n + 1);
   return w;
 }
 
@@ -438,11 +482,14 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   const int tpasses = (tbits + 7) / 8;
   uint32_t* emit_k = (tpasses & 1) ? w.tk_b : w.tk_a;
   int32_t* emit_v = (tpasses & 1) ? w.tv_b : a.vals;
-  HYRF_LAUNCH("k_emit", s,
-              k_emit<<<sc, 256, 0, s>>>(a.ntiles, a.rect, w.dv_a, a.n_vis, n, w.sums, a.tiles_x, cap, emit_k,
-                            emit_v));
-  // 3. stable sort of the instances on their tile bits
+  HYRF_LAUNCH("k_offsets", s,
+              k_offsets<<<sc, 256, 0, s>>>(a.ntiles, w.dv_a, a.n_vis, n, w.sums, sc, w.off));
   const int capi = (int)(cap < 0x7fffffff ? cap : 0x7fffffff);
+  const int64_t xb = (cap + kExpandItems - 1) / kExpandItems;
+  HYRF_LAUNCH("k_expand", s,
+              k_expand<<<(int)(xb < 0x7fffffff ? xb : 0x7fffffff), 256, 0, s>>>(
+                  a.rect, w.dv_a, a.n_vis, n, w.off, a.n_instances, capi, a.tiles_x, emit_k, emit_v));
+  // 3. stable sort of the instances on their tile bits
   st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s);
   if (st != HYRF_OK) return st;
   // 4. per-tile ranges and (optionally) the composed 64-bit keys

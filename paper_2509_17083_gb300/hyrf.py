@@ -169,6 +169,8 @@ def lib():
         L.hyrf_bin_sort_noalloc.restype = C.c_int32
         L.hyrf_launch_count.argtypes = []
         L.hyrf_launch_count.restype = C.c_uint64
+        L.hyrf_adam_step.argtypes = [C.POINTER(hyrf_adam_tensor), C.c_int32, C.POINTER(hyrf_adam_hparams), _vp]
+        L.hyrf_adam_step.restype = C.c_int32
         L.hyrf_timer_enable.argtypes = [C.c_int]
         L.hyrf_timer_enable.restype = None
         L.hyrf_timer_read.argtypes = [C.POINTER(hyrf_kernel_time), C.c_int]
@@ -238,6 +240,37 @@ def error_string(st):
 
 def launch_count():
     return int(lib().hyrf_launch_count())
+
+
+class hyrf_adam_tensor(C.Structure):
+    _fields_ = [("param", _vp), ("grad", _vp), ("m", _vp), ("v", _vp), ("shadow", _vp),
+                ("n", C.c_int64), ("lr_scale", C.c_float)]
+
+
+class hyrf_adam_hparams(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("grad_scale", C.c_float)]
+
+
+ADAM_MAX_TENSORS = 32
+
+
+def hyrf_adam_step(tensors, lr, beta1, beta2, eps, step, grad_scale=1.0, stream=None):
+    """One fused Adam step. tensors: list of dicts with param, grad, m, v
+    (float32 tensors of equal size), optional shadow (bfloat16) and lr_scale."""
+    L = lib()
+    for c0 in range(0, len(tensors), ADAM_MAX_TENSORS):
+        chunk = tensors[c0:c0 + ADAM_MAX_TENSORS]
+        arr = (hyrf_adam_tensor * len(chunk))()
+        for d, t in zip(arr, chunk):
+            d.param, d.grad, d.m, d.v = ptr(t["param"]), ptr(t["grad"]), ptr(t["m"]), ptr(t["v"])
+            d.shadow = ptr(t["shadow"]) if t.get("shadow") is not None else None
+            d.n = int(t["param"].numel())
+            d.lr_scale = float(t.get("lr_scale", 1.0))
+        hp = hyrf_adam_hparams(float(lr), float(beta1), float(beta2), float(eps), int(step), float(grad_scale))
+        st = L.hyrf_adam_step(arr, len(chunk), C.byref(hp), stream_handle(stream))
+        if st != HYRF_OK:
+            raise HyrfError(f"hyrf_adam_step: {L.hyrf_error_string(st).decode()} ({st})")
 
 
 class hyrf_kernel_time(C.Structure):

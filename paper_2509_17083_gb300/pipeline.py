@@ -84,16 +84,25 @@ class DeviceModel:
                              g["col_b"])
 
 
+def shared_workspaces(device="cuda"):
+    """Scratch buffers of the library calls of one view. Pass the same dict to
+    several ViewRenderers that run one after the other on one stream to share
+    it (with save_features off, the gathered hash features then live only in
+    this scratch: memory for time)."""
+    return {k: H.Workspace(device) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l")}
+
+
 class ViewRenderer:
     """Buffers and calls for one camera of fixed size.
 
     save_features (BF16 fields only; default on for them): keep the hash
     features gathered by the forward (2 x 64 B per Gaussian, 64 B per pixel)
     for the backward, which then skips its gather; off = gather again
-    (recompute)."""
+    (recompute). workspaces: a scratch dict shared with other views
+    (shared_workspaces())."""
 
     def __init__(self, model: DeviceModel, cam, bg, lam=0.0, loss_scale=1.0, capacity=None,
-                 save_features=None):
+                 save_features=None, workspaces=None):
         self.m = model
         self.cam = cam
         self.bg = bg
@@ -121,7 +130,9 @@ class ViewRenderer:
         self.dC, self.dT = z(Hh, W, 3), z(Hh, W)
         self.d_mean2d, self.d_conic, self.d_alpha, self.d_color = z(n, 2), z(n, 3), z(n), z(n, 3)
         self.d_scale, self.d_quat = z(n, 3), z(n, 4)
-        self.ws = {k: H.Workspace(d) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l")}
+        # scratch of the library calls; views that run one after the other on
+        # one stream may share one dict (see shared_workspaces)
+        self.ws = workspaces if workspaces is not None else shared_workspaces(d)
         if save_features is None:
             save_features = model.bf16
         if save_features and not model.bf16:
@@ -257,3 +268,60 @@ class ViewRenderer:
                 return st
             self.set_capacity(self.capacity * 2)
         raise H.HyrfError("instance capacity could not be fitted")
+
+
+class Trainer:
+    """Training iterations of several views with the fused Adam update
+    (hyrf_adam_step). The gradients of all views are accumulated, averaged
+    and applied in one launch over every trainable tensor.
+
+    BF16 fields train float32 master copies of the tables and decoder
+    weights; the Adam kernel refreshes the bf16 working copies the render
+    kernels read. Learning rates (the paper keeps 3DGS's hyper-parameters,
+    Sec. 4.1): explicit position 1.6e-4 x the scene extent, opacity 0.05,
+    scale 5e-3, colour 2.5e-3 (3DGS); hash tables 1e-2 and decoders 1e-3
+    (Instant-NGP); Adam betas (0.9, 0.999), eps 1e-15 for all.
+    """
+
+    LR = dict(pos=1.6e-4, alpha_e=0.05, scale_e=5e-3, color_e=2.5e-3, table=1e-2, mlp=1e-3)
+
+    def __init__(self, model: DeviceModel, views, lr=None, betas=(0.9, 0.999), eps=1e-15):
+        self.m = model
+        self.views = list(views)
+        self.betas, self.eps = betas, eps
+        self.t = 0
+        lr = dict(self.LR, **(lr or {}))
+        fl = model.fl
+        extent = float(max(fl.box_hi[k] - fl.box_lo[k] for k in range(3)))
+        g = model.grad
+        z = torch.zeros_like
+        self.groups = []
+
+        def add(param, grad, lr_v, shadow=None):
+            master = param.float().clone() if shadow is not None else param
+            self.groups.append(dict(param=master, grad=grad, m=z(master), v=z(master), shadow=shadow,
+                                    lr_scale=lr_v))
+
+        add(model.pos, g["pos"], lr["pos"] * extent)
+        add(model.alpha_e, g["alpha_e"], lr["alpha_e"])
+        add(model.scale_e, g["scale_e"], lr["scale_e"])
+        add(model.color_e, g["color_e"], lr["color_e"])
+        for name in ("geo_table", "rad_table"):
+            t = getattr(model, name)
+            add(t, g[name], lr["table"], shadow=t if model.bf16 else None)
+        for W, gW, b, gb in zip(model.geo_W + model.col_W, g["geo_W"] + g["col_W"],
+                                model.geo_b + model.col_b, g["geo_b"] + g["col_b"]):
+            add(W, gW, lr["mlp"], shadow=W if model.bf16 else None)
+            add(b, gb, lr["mlp"])
+
+    def step(self, targets):
+        """One iteration over all views; returns the per-view loss tensors."""
+        self.m.zero_grad()
+        losses = []
+        for r, tgt in zip(self.views, targets):
+            r.step(tgt)
+            losses.append(r.loss)
+        self.t += 1
+        H.hyrf_adam_step(self.groups, 1.0, self.betas[0], self.betas[1], self.eps, self.t,
+                         grad_scale=1.0 / len(self.views))
+        return losses
