@@ -421,6 +421,106 @@ hyrf_status hyrf_loss(const hyrf_loss_args* a, void* workspace, size_t ws_bytes,
  * aligned; m and v are caller-owned state (zero before the first step).
  * Errors: HYRF_ERR_INVALID_ARG for a bad count, hyper-parameter or pointer.
  * ---------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------
+ * Adaptive density control. The paper keeps 3DGS's schedule (Sec. 3.3 end:
+ * periodic reset of the explicit opacity, pruning of low-opacity Gaussians;
+ * densification "as the original 3DGS", Sec. 2 and Sec. 4.1). Three calls:
+ *
+ * hyrf_densify_stats, after a view's reverse pass: for every visible
+ * Gaussian with at least one tile, accum[g] += |dL/d mean2d| measured in
+ * NDC units (the pixel-space gradient times (W/2, H/2)) and count[g] += 1.
+ *
+ * hyrf_densify_plan: one action per Gaussian g (the visible rows of the last
+ * hyrf_query_fields give its opacity and scale; other Gaussians are kept):
+ *   prune  (HYRF_DENSIFY_PRUNE) if opacity < min_opacity, else if
+ *   count > 0 and accum / count >= grad_threshold:
+ *     split (HYRF_DENSIFY_SPLIT) if max(scale) > dense_scale, else
+ *     clone (HYRF_DENSIFY_CLONE); otherwise keep.
+ * It writes action [N], row [N] (the visible row of g, or -1), offset
+ * [N + 1] (exclusive scan of the output multiplicity 1 / 0 / 2 / 2) and
+ * *n_out = offset[N] (device). The caller reads n_out to size the new arrays.
+ *
+ * hyrf_densify_apply: writes the new per-Gaussian arrays. Gaussian g's
+ * outputs start at offset[g], in the old order: kept -> 1 copy; clone -> the
+ * original then an identical copy; split -> two Gaussians at
+ * p + R(q) (s * z_k) (z_k = noise[g][k][0..3), k = 0, 1, the visible row's
+ * scale s and rotation q) whose explicit scale logit is lowered by
+ * split_log_scale (ln 1.6 shrinks small scales by 1.6, as 3DGS's 1 / (0.8 x 2)).
+ * Optimiser state arrays (kind HYRF_REMAP_STATE) start at zero for every new
+ * Gaussian (clone copies, both split halves) and keep their values for kept
+ * Gaussians and clone originals.
+ * ---------------------------------------------------------------------- */
+#define HYRF_DENSIFY_KEEP 0
+#define HYRF_DENSIFY_PRUNE 1
+#define HYRF_DENSIFY_CLONE 2
+#define HYRF_DENSIFY_SPLIT 3
+#define HYRF_REMAP_MAX 24
+#define HYRF_REMAP_PARAM 0      /* copied (clone: both) */
+#define HYRF_REMAP_STATE 1      /* copied for kept / clone originals, zero for new Gaussians */
+#define HYRF_REMAP_POSITION 2   /* width 3; split halves are sampled */
+#define HYRF_REMAP_SCALE_LOGIT 3 /* width 1; split halves lowered by split_log_scale */
+
+typedef struct {
+  int32_t n;
+  const int32_t* vis_ids;    /* [N] */
+  const int32_t* n_vis;      /* [1] */
+  const float* d_mean2d;     /* [V][2] pixel units, from hyrf_rasterize_backward */
+  const int32_t* ntiles;     /* [V] from hyrf_project */
+  int32_t width, height;
+  float* accum;              /* [N] accumulate */
+  int32_t* count;            /* [N] accumulate */
+} hyrf_densify_stats_args;
+
+hyrf_status hyrf_densify_stats(const hyrf_densify_stats_args* a, void* stream);
+
+typedef struct {
+  int32_t n;
+  const int32_t* vis_ids;    /* [N] */
+  const int32_t* n_vis;      /* [1] */
+  const float* alpha;        /* [V] opacity of the visible rows */
+  const float* scale;        /* [V][3] */
+  const float* accum;        /* [N] */
+  const int32_t* count;      /* [N] */
+  float grad_threshold, dense_scale, min_opacity;
+  uint8_t* action;           /* out [N] */
+  int32_t* row;              /* out [N] */
+  int64_t* offset;           /* out [N + 1] */
+  int64_t* n_out;            /* out [1] */
+} hyrf_densify_plan_args;
+
+size_t hyrf_densify_plan_workspace_size(const hyrf_densify_plan_args* a);
+hyrf_status hyrf_densify_plan(const hyrf_densify_plan_args* a, void* workspace, size_t ws_bytes,
+                              void* stream);
+
+typedef struct {
+  const float* src;          /* [N][width] */
+  float* dst;                /* [n_out][width] */
+  int32_t width;             /* 1..4 */
+  int32_t kind;              /* HYRF_REMAP_* */
+} hyrf_remap_array;
+
+typedef struct {
+  int32_t n;
+  const uint8_t* action;     /* [N] from the plan */
+  const int32_t* row;        /* [N] */
+  const int64_t* offset;     /* [N + 1] */
+  const float* scale;        /* [V][3] of the visible rows */
+  const float* quat;         /* [V][4] */
+  const float* noise;        /* [N][2][3] standard normal draws (caller-drawn) */
+  float split_log_scale;
+  int32_t n_arrays;
+  hyrf_remap_array arrays[HYRF_REMAP_MAX];
+} hyrf_densify_apply_args;
+
+hyrf_status hyrf_densify_apply(const hyrf_densify_apply_args* a, void* stream);
+
+/* hyrf_reset_opacity: the periodic reset of the explicit opacity (Sec. 3.3
+ * end): alpha_e[g] = min(alpha_e[g], max_logit) for all n Gaussians (3DGS
+ * resets to opacity 0.01, max_logit = logit(0.01)); the Adam moments of
+ * alpha_e (m, v; may be NULL) restart from zero. */
+hyrf_status hyrf_reset_opacity(float* alpha_e, int64_t n, float max_logit, float* m, float* v,
+                               void* stream);
+
 #define HYRF_ADAM_MAX_TENSORS 32
 typedef struct {
   float* param;              /* [n] float32 master values, updated in place */

@@ -466,6 +466,57 @@ def adam_step(p, grad, m, v, lr, b1, b2, eps, t, grad_scale=1.0):
     return p, m, v
 
 
+def densify_stats(n, vis_ids, d_mean2d, ntiles, width, height, accum, count):
+    """Adds one view's positional-gradient statistics (FP32 replay); returns
+    (accum, count) as new arrays."""
+    vis = np.ascontiguousarray(vis_ids, dtype=np.int32)
+    dm = np.ascontiguousarray(d_mean2d, dtype=np.float32)
+    nt = np.ascontiguousarray(ntiles, dtype=np.int32)
+    acc = np.array(accum, dtype=np.float32)
+    cnt = np.array(count, dtype=np.int32)
+    rc = lib().orc_densify_stats(n, len(vis), _ptr(vis, _i32p), _ptr(dm, _f32p), _ptr(nt, _i32p), width, height,
+                                 _ptr(acc, _f32p), _ptr(cnt, _i32p))
+    assert rc == 0
+    return acc, cnt
+
+
+def densify_plan(n, vis_ids, alpha, scale, accum, count, grad_threshold, dense_scale, min_opacity):
+    """(action [n] u8, row [n] i32, offset [n+1] i64, new count)."""
+    vis = np.ascontiguousarray(vis_ids, dtype=np.int32)
+    al = np.ascontiguousarray(alpha, dtype=np.float32)
+    sc = np.ascontiguousarray(scale, dtype=np.float32)
+    acc = np.ascontiguousarray(accum, dtype=np.float32)
+    cnt = np.ascontiguousarray(count, dtype=np.int32)
+    action = np.zeros(n, dtype=np.uint8)
+    row = np.zeros(n, dtype=np.int32)
+    offset = np.zeros(n + 1, dtype=np.int64)
+    f = lib().orc_densify_plan
+    f.restype = C.c_int64
+    total = f(n, len(vis), _ptr(vis, _i32p), _ptr(al, _f32p), _ptr(sc, _f32p), _ptr(acc, _f32p),
+              _ptr(cnt, _i32p), C.c_float(grad_threshold), C.c_float(dense_scale), C.c_float(min_opacity),
+              _ptr(action, _u8p), _ptr(row, _i32p), _ptr(offset, C.POINTER(C.c_int64)))
+    assert total >= 0
+    return action, row, offset, int(total)
+
+
+def densify_apply(action, row, offset, scale, quat, noise, split_log_scale, src, kind):
+    """New array for one per-Gaussian array src [n, w] (kind 0 parameter,
+    1 optimiser state, 2 position, 3 explicit scale logit)."""
+    n = len(action)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    w = 1 if src.ndim == 1 else src.shape[1]
+    dst = np.zeros((int(offset[n]), w))
+    keep = _Keep()
+    a = np.ascontiguousarray(action, dtype=np.uint8)
+    r = np.ascontiguousarray(row, dtype=np.int32)
+    o = np.ascontiguousarray(offset, dtype=np.int64)
+    rc = lib().orc_densify_apply(n, _ptr(a, _u8p), _ptr(r, _i32p), _ptr(o, C.POINTER(C.c_int64)),
+                                 keep.d(scale), keep.d(quat), keep.d(noise), C.c_double(split_log_scale), w,
+                                 kind, _ptr(src, _f64p), _ptr(dst, _f64p))
+    assert rc == 0
+    return dst if src.ndim > 1 else dst[:, 0]
+
+
 def ssim(x, y):
     keep = _Keep()
     H, W = x.shape[:2]

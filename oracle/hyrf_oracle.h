@@ -39,6 +39,9 @@
  *                    the loss w.r.t. every parameter class
  *   Adam             first-step closed form p - lr g / (|g| + eps); constant
  *                    gradient over t steps; zero gradient decays the moments
+ *   density control  hand-built keep / prune / clone / split cases; counts
+ *                    and offsets by brute force; split halves at p + s * z
+ *                    for the identity rotation, mirrored for q and -q
  */
 #ifndef HYRF_ORACLE_H
 #define HYRF_ORACLE_H
@@ -234,6 +237,28 @@ double orc_ssim(int32_t width, int32_t height, const double* x, const double* y)
  * p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
 int32_t orc_adam_step(int64_t n, double* p, const double* grad, double* m, double* v, double lr,
                       double b1, double b2, double eps, int32_t t, double grad_scale);
+
+/* ---------------- training: adaptive density control (3DGS rules) ------ */
+/* Statistics of one view, FP32 replay: for visible row i with ntiles > 0,
+ * g = vis_ids[i]: accum[g] += sqrt((dm_x W/2)^2 + (dm_y H/2)^2) (each
+ * product and sum rounded to float), count[g] += 1. */
+int32_t orc_densify_stats(int32_t n, int32_t n_vis, const int32_t* vis_ids, const float* d_mean2d,
+                          const int32_t* ntiles, int32_t width, int32_t height, float* accum,
+                          int32_t* count);
+/* Decision per Gaussian (0 keep, 1 prune, 2 clone, 3 split), FP32 replay of
+ * the comparisons; row [n] (visible row or -1), offset [n + 1]. Returns the
+ * new count. */
+int64_t orc_densify_plan(int32_t n, int32_t n_vis, const int32_t* vis_ids, const float* alpha,
+                         const float* scale, const float* accum, const int32_t* count, float grad_threshold,
+                         float dense_scale, float min_opacity, uint8_t* action, int32_t* row,
+                         int64_t* offset);
+/* New arrays per the plan (FP64 positions of the split halves
+ * p + R(q) (s * z_k)); kinds: 0 parameter, 1 optimiser state, 2 position,
+ * 3 explicit scale logit. */
+int32_t orc_densify_apply(int32_t n, const uint8_t* action, const int32_t* row, const int64_t* offset,
+                          const double* scale, const double* quat, const double* noise,
+                          double split_log_scale, int32_t width, int32_t kind, const double* src,
+                          double* dst);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ UNITS = {
     "fields_tc_bwd": ("fields_tc_bwd.cu", []),
     "gather": ("gather.cu", []),
     "optim": ("optim.cu", []),
+    "densify": ("densify.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
     "noalloc": ("noalloc.cu", []),

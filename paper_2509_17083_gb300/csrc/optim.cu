@@ -12,14 +12,14 @@ struct AdamLaunch {
   hyrf_adam_tensor t[HYRF_ADAM_MAX_TENSORS];
   int64_t first_block[HYRF_ADAM_MAX_TENSORS + 1];  // prefix of blocks per tensor
   int count;
-  float lr, b1, b2, eps, c1, c2, gs;                // c1 = 1 - b1^t, c2 = 1 - b2^t
+  float lr, b1, b2, omb1, omb2, eps, c1, c2, gs;    // omb = 1 - b; c1 = 1 - b1^t, c2 = 1 - b2^t
 };
 
 __device__ __forceinline__ float adam_one(float& p, float g, float& m, float& v, const AdamLaunch& A,
                                           float lr) {
   g *= A.gs;
-  m = A.b1 * m + (1.0f - A.b1) * g;
-  v = A.b2 * v + (1.0f - A.b2) * g * g;
+  m = A.b1 * m + A.omb1 * g;
+  v = A.b2 * v + A.omb2 * g * g;
   const float mh = m / A.c1, vh = v / A.c2;
   p -= lr * mh / (sqrtf(vh) + A.eps);
   return p;
@@ -80,6 +80,8 @@ extern "C" hyrf_status hyrf_adam_step(const hyrf_adam_tensor* tensors, int32_t c
   A.b2 = hp->beta2;
   A.eps = hp->eps;
   A.gs = hp->grad_scale;
+  A.omb1 = (float)(1.0 - (double)hp->beta1);  // exact difference, then one rounding
+  A.omb2 = (float)(1.0 - (double)hp->beta2);
   A.c1 = (float)(1.0 - pow((double)hp->beta1, (double)hp->step));
   A.c2 = (float)(1.0 - pow((double)hp->beta2, (double)hp->step));
   int64_t blocks = 0;

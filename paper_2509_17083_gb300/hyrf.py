@@ -122,7 +122,34 @@ class hyrf_loss_args(C.Structure):
                 ("lambda_", C.c_float), ("grad_scale", C.c_float), ("loss", _vp), ("d_C", _vp)]
 
 
+class hyrf_densify_stats_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("vis_ids", _vp), ("n_vis", _vp), ("d_mean2d", _vp), ("ntiles", _vp),
+                ("width", C.c_int32), ("height", C.c_int32), ("accum", _vp), ("count", _vp)]
+
+
+class hyrf_densify_plan_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("vis_ids", _vp), ("n_vis", _vp), ("alpha", _vp), ("scale", _vp),
+                ("accum", _vp), ("count", _vp), ("grad_threshold", C.c_float), ("dense_scale", C.c_float),
+                ("min_opacity", C.c_float), ("action", _vp), ("row", _vp), ("offset", _vp), ("n_out", _vp)]
+
+
+class hyrf_remap_array(C.Structure):
+    _fields_ = [("src", _vp), ("dst", _vp), ("width", C.c_int32), ("kind", C.c_int32)]
+
+
+REMAP_MAX = 24
+DENSIFY_KEEP, DENSIFY_PRUNE, DENSIFY_CLONE, DENSIFY_SPLIT = 0, 1, 2, 3
+REMAP_PARAM, REMAP_STATE, REMAP_POSITION, REMAP_SCALE_LOGIT = 0, 1, 2, 3
+
+
+class hyrf_densify_apply_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("action", _vp), ("row", _vp), ("offset", _vp), ("scale", _vp),
+                ("quat", _vp), ("noise", _vp), ("split_log_scale", C.c_float), ("n_arrays", C.c_int32),
+                ("arrays", hyrf_remap_array * REMAP_MAX)]
+
+
 _ARGS = {
+    "hyrf_densify_plan": hyrf_densify_plan_args,
     "hyrf_query_fields": hyrf_query_fields_args,
     "hyrf_query_fields_backward": hyrf_query_fields_backward_args,
     "hyrf_project": hyrf_project_args,
@@ -165,6 +192,12 @@ def lib():
         L.hyrf_read_status.restype = C.c_int32
         L.hyrf_error_string.argtypes = [C.c_int32]
         L.hyrf_error_string.restype = C.c_char_p
+        L.hyrf_densify_stats.argtypes = [C.POINTER(hyrf_densify_stats_args), _vp]
+        L.hyrf_densify_stats.restype = C.c_int32
+        L.hyrf_densify_apply.argtypes = [C.POINTER(hyrf_densify_apply_args), _vp]
+        L.hyrf_densify_apply.restype = C.c_int32
+        L.hyrf_reset_opacity.argtypes = [_vp, C.c_int64, C.c_float, _vp, _vp, _vp]
+        L.hyrf_reset_opacity.restype = C.c_int32
         L.hyrf_bin_sort_noalloc.argtypes = [C.POINTER(hyrf_bin_sort_args), _vp]
         L.hyrf_bin_sort_noalloc.restype = C.c_int32
         L.hyrf_launch_count.argtypes = []
@@ -371,6 +404,42 @@ def hyrf_bin_sort(ws=None, stream=None, **kw):
 
 def hyrf_bin_sort_backward(ws=None, stream=None, **kw):
     return call("hyrf_bin_sort_backward", _fill(hyrf_bin_sort_args(), kw), ws, stream)
+
+
+def _check(name, st):
+    if st != HYRF_OK:
+        raise HyrfError(f"{name}: {lib().hyrf_error_string(st).decode()} ({st})")
+
+
+def hyrf_densify_stats(stream=None, **kw):
+    """Accumulate the view-space positional gradient statistics of one view."""
+    _check("hyrf_densify_stats",
+           lib().hyrf_densify_stats(C.byref(_fill(hyrf_densify_stats_args(), kw)), stream_handle(stream)))
+
+
+def hyrf_densify_plan(ws=None, stream=None, **kw):
+    """Per-Gaussian keep / prune / clone / split and the output offsets."""
+    return call("hyrf_densify_plan", _fill(hyrf_densify_plan_args(), kw), ws, stream)
+
+
+def hyrf_densify_apply(arrays, stream=None, **kw):
+    """Rewrite per-Gaussian arrays: arrays = [(src, dst, kind), ...] with
+    src [N, w] / dst [N', w] float32 tensors (w = 1 for flat tensors)."""
+    a = _fill(hyrf_densify_apply_args(), kw)
+    if len(arrays) > REMAP_MAX:
+        raise HyrfError("too many arrays")
+    a.n_arrays = len(arrays)
+    for d, (src, dst, kind) in zip(a.arrays, arrays):
+        d.src, d.dst = ptr(src), ptr(dst)
+        d.width = 1 if src.dim() == 1 else int(src.shape[1])
+        d.kind = int(kind)
+    _check("hyrf_densify_apply", lib().hyrf_densify_apply(C.byref(a), stream_handle(stream)))
+
+
+def hyrf_reset_opacity(alpha_e, max_logit, m=None, v=None, stream=None):
+    """alpha_e = min(alpha_e, max_logit); the Adam moments restart from zero."""
+    _check("hyrf_reset_opacity", lib().hyrf_reset_opacity(ptr(alpha_e), int(alpha_e.numel()), float(max_logit),
+                                                          ptr(m), ptr(v), stream_handle(stream)))
 
 
 def hyrf_bin_sort_noalloc(stream=None, **kw):

@@ -314,14 +314,83 @@ class Trainer:
             add(W, gW, lr["mlp"], shadow=W if model.bf16 else None)
             add(b, gb, lr["mlp"])
 
+        self._per_gaussian = 4  # the first four groups are [N]-shaped explicit parameters
+        self.reset_stats()
+
+    def reset_stats(self):
+        n, d = self.m.n, self.m.device
+        self.accum = torch.zeros(max(n, 1), device=d)
+        self.count = torch.zeros(max(n, 1), dtype=torch.int32, device=d)
+
     def step(self, targets):
-        """One iteration over all views; returns the per-view loss tensors."""
+        """One iteration over all views; returns the per-view loss tensors.
+        Also accumulates each view's densification statistics."""
         self.m.zero_grad()
         losses = []
         for r, tgt in zip(self.views, targets):
             r.step(tgt)
+            H.hyrf_densify_stats(n=self.m.n, vis_ids=r.vis_ids, n_vis=r.n_vis, d_mean2d=r.d_mean2d,
+                                 ntiles=r.ntiles, width=r.W, height=r.H, accum=self.accum, count=self.count)
             losses.append(r.loss)
         self.t += 1
         H.hyrf_adam_step(self.groups, 1.0, self.betas[0], self.betas[1], self.eps, self.t,
                          grad_scale=1.0 / len(self.views))
         return losses
+
+    def reset_opacity(self, opacity=0.01):
+        """Periodic reset of the explicit opacity (3DGS: to 0.01)."""
+        g = self.groups[1]
+        H.hyrf_reset_opacity(self.m.alpha_e, math.log(opacity / (1.0 - opacity)), g["m"], g["v"])
+
+    def densify(self, targets, grad_threshold=2e-4, dense_scale=None, min_opacity=0.005, noise_seed=0):
+        """Clone / split / prune (3DGS rules; decisions from the first view's
+        last forward) and rebuild every per-Gaussian buffer. Returns the new
+        Gaussian count. The views' buffers are re-created and re-fitted."""
+        m, r = self.m, self.views[0]
+        n, d = m.n, m.device
+        fl = m.fl
+        extent = float(max(fl.box_hi[k] - fl.box_lo[k] for k in range(3)))
+        if dense_scale is None:
+            dense_scale = 0.01 * extent  # 3DGS percent_dense x scene extent
+        action = torch.empty(n, dtype=torch.uint8, device=d)
+        row = torch.empty(n, dtype=torch.int32, device=d)
+        offset = torch.empty(n + 1, dtype=torch.int64, device=d)
+        n_out = torch.empty(1, dtype=torch.int64, device=d)
+        H.hyrf_densify_plan(n=n, vis_ids=r.vis_ids, n_vis=r.n_vis, alpha=r.alpha, scale=r.scale,
+                            accum=self.accum, count=self.count, grad_threshold=grad_threshold,
+                            dense_scale=dense_scale, min_opacity=min_opacity, action=action, row=row,
+                            offset=offset, n_out=n_out)
+        n2 = int(n_out.item())
+        gen = torch.Generator(device=d)
+        gen.manual_seed(noise_seed)
+        noise = torch.randn(n, 2, 3, device=d, generator=gen)
+        kinds = [H.REMAP_POSITION, H.REMAP_PARAM, H.REMAP_SCALE_LOGIT, H.REMAP_PARAM]
+        arrays, new = [], []
+        for k, grp in enumerate(self.groups[:self._per_gaussian]):
+            p = grp["param"].view(n, -1)
+            trio = []
+            for src, kind in ((p, kinds[k]), (grp["m"].view(n, -1), H.REMAP_STATE),
+                              (grp["v"].view(n, -1), H.REMAP_STATE)):
+                dst = torch.empty((n2, src.shape[1]), device=d)
+                arrays.append((src, dst, kind))
+                trio.append(dst)
+            new.append(trio)
+        H.hyrf_densify_apply(arrays, n=n, action=action, row=row, offset=offset, scale=r.scale, quat=r.quat,
+                             noise=noise, split_log_scale=math.log(1.6))
+        shapes = [(n2, 3), (n2,), (n2,), (n2, 3)]
+        names = ["pos", "alpha_e", "scale_e", "color_e"]
+        for k, (name, (p2, m2, v2)) in enumerate(zip(names, new)):
+            p2, m2, v2 = (x.view(shapes[k]).contiguous() for x in (p2, m2, v2))
+            setattr(m, name, p2)
+            m.grad[name] = torch.zeros_like(p2)
+            self.groups[k].update(param=p2, grad=m.grad[name], m=m2, v=v2)
+        m.n = n2
+        self.reset_stats()
+        views = []
+        for old, tgt in zip(self.views, targets):
+            nr = ViewRenderer(m, old.cam, old.bg, lam=old.lam, loss_scale=old.loss_scale,
+                              save_features=old.save_features, workspaces=old.ws)
+            nr.fit_capacity(tgt)
+            views.append(nr)
+        self.views = views
+        return n2

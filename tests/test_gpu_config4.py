@@ -21,6 +21,12 @@ from tests.gpu_util import cuda_f32, np_, rel_l2
 
 pytestmark = pytest.mark.gpu
 
+# Float atomics add in a different order on every run: a coarse-level table
+# entry sums ~1e6 contributions of both signs per step (8 views x 1M+
+# Gaussians), whose order-dependent rounding (~sqrt(1e6) x 2^-24 of the
+# partial sums) reaches ~1e-4 of the entry. Images and integers are exact.
+ORDER_TOL = 5e-4
+
 
 def _setup(save_features, n=3_000_000):
     w = synth.config4(n=n)
@@ -82,7 +88,7 @@ def test_eight_view_step_replays_as_one_cuda_graph():
         assert np.array_equal(np_(r.C), img)
     got = _grads(m)
     for k, v in ref.items():
-        assert rel_l2(got[k], v) < 1e-5, k
+        assert rel_l2(got[k], v) < ORDER_TOL, k
     # timing: graph replay against eager issue of the same work
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
@@ -115,4 +121,4 @@ def test_saved_features_against_recompute_memory_and_gradients():
           f"recompute {peak_re / 2**30:.2f} GiB")
     assert peak_re < peak_save
     for k, v in g_save.items():
-        assert rel_l2(g_re[k], v) < 1e-5, k
+        assert rel_l2(g_re[k], v) < ORDER_TOL, k

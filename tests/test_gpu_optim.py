@@ -26,13 +26,15 @@ def test_adam_matches_oracle_over_ragged_tensors():
             t["shadow"] = torch.zeros(n, dtype=torch.bfloat16, device=dev)
         ts.append(t)
         ref.append([p.astype(np.float64), np.zeros(n), np.zeros(n)])
-    lr, b1, b2, eps, gs = 1e-3, 0.9, 0.999, 1e-8, 0.5
+    # the hyper-parameters cross the C ABI as float32: the oracle takes the
+    # same float32 values (0.999 as float32 is 0.99900001287...)
+    lr, b1, b2, eps, gs = [float(np.float32(x)) for x in (1e-3, 0.9, 0.999, 1e-8, 0.5)]
     for step in range(1, 4):
         for t, r in zip(ts, ref):
             g = (rng.standard_normal(t["param"].numel()) * 1e-2).astype(np.float32)
             t["grad"].copy_(torch.tensor(g, device=dev))
-            r[0], r[1], r[2] = oracle.adam_step(r[0], g, r[1], r[2], lr * t["lr_scale"], b1, b2, eps, step,
-                                                grad_scale=gs)
+            lrt = float(np.float32(lr) * np.float32(t["lr_scale"]))
+            r[0], r[1], r[2] = oracle.adam_step(r[0], g, r[1], r[2], lrt, b1, b2, eps, step, grad_scale=gs)
         H.hyrf_adam_step(ts, lr, b1, b2, eps, step, grad_scale=gs)
         torch.cuda.synchronize()
     for t, r in zip(ts, ref):

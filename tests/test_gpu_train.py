@@ -65,3 +65,34 @@ def test_bf16_and_fp32_training_agree(runs):
     _, _, pb = runs["bf16"]
     _, _, pf = runs["f32"]
     assert abs(pb - pf) < 0.5, (pb, pf)
+
+
+def test_training_with_density_control():
+    """Densify (clone / split), prune and reset opacity during training: the
+    Gaussian count changes, every buffer is rebuilt consistently and the loss
+    keeps falling."""
+    w = synth.config3(n=30000, width=301, height=203, log2_T=15, n_clusters=32, precision="bf16")
+    rng = np.random.default_rng(52)
+    g = w.gaussians
+    teacher = dataclasses.replace(w, gaussians=dataclasses.replace(
+        g, color_e=rng.standard_normal(g.color_e.shape).astype(np.float32)))
+    tm = DeviceModel(teacher)
+    tr = ViewRenderer(tm, w.cams[0], w.bg)
+    tr.fit_capacity()
+    target = tr.forward(None).clone()
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+    r.fit_capacity(target)
+    trainer = Trainer(m, [r])
+    losses, counts = [], [m.n]
+    for k in range(1, 61):
+        losses.append(float(trainer.step([target])[0].item()))
+        assert H.read_status(trainer.views[0].status) == 0
+        if k % 15 == 0:
+            counts.append(trainer.densify([target], grad_threshold=2e-6))
+            assert trainer.m.n == counts[-1] and trainer.m.pos.shape[0] == counts[-1]
+        if k == 30:
+            trainer.reset_opacity()
+    assert counts[1] != counts[0], counts
+    assert max(counts) > counts[0], counts  # some Gaussians were cloned or split
+    assert np.mean(losses[-5:]) < 0.8 * np.mean(losses[:5]), (losses[:5], losses[-5:])
