@@ -36,6 +36,8 @@ def parse():
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-s", type=float, default=15.0)
+    p.add_argument("--ablation", action="store_true",
+                   help="render FPS and fwd+bwd it/s of the Tab. 5 ablations on the 360-degree variant")
     return p.parse_args()
 
 
@@ -197,12 +199,8 @@ def run_ours(args):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                     evs.setdefault(k, []).append(e0)
-            fs = m.fields_struct()
             mark("query_fwd")
-            H.hyrf_query_fields(ws=r.ws["q"], n=m.n, pos=m.pos, alpha_e=m.alpha_e,
-                                scale_e=m.scale_e, color_e=m.color_e, cam=r.ccam, fields=fs,
-                                vis_ids=r.vis_ids, n_vis=r.n_vis, alpha=r.alpha, scale=r.scale,
-                                quat=r.quat, color=r.color, status=r.status, features=r.feat_q)
+            H.hyrf_query_fields(ws=r.ws["q"], **r.query_kwargs())
             mark("query_fwd"); mark("project_fwd")
             r.project()
             mark("project_fwd"); mark("bin_sort")
@@ -228,15 +226,7 @@ def run_ours(args):
                                     d_conic=r.d_conic, d_pos=m.grad["pos"], d_scale=r.d_scale,
                                     d_quat=r.d_quat, status=r.status)
             mark("project_bwd"); mark("query_bwd")
-            H.hyrf_query_fields_backward(ws=r.ws["qb"], n=m.n, pos=m.pos, alpha_e=m.alpha_e,
-                                         scale_e=m.scale_e, color_e=m.color_e, cam=r.ccam,
-                                         fields=fs, vis_ids=r.vis_ids, n_vis=r.n_vis,
-                                         d_alpha=r.d_alpha, d_scale=r.d_scale, d_quat=r.d_quat,
-                                         d_color=r.d_color, d_pos=m.grad["pos"],
-                                         d_alpha_e=m.grad["alpha_e"], d_scale_e=m.grad["scale_e"],
-                                         d_color_e=m.grad["color_e"], grads=g,
-                                         loss_scale=r.loss_scale, status=r.status,
-                                         features=r.feat_q)
+            H.hyrf_query_fields_backward(ws=r.ws["qb"], **r.query_backward_kwargs())
             mark("query_bwd")
             return evs
 
@@ -396,6 +386,69 @@ def roofline(R, peaks, prec):
             "peak_source": src}
 
 
+# ---------------------------------------------------------------- ablations (Tab. 5)
+
+# The paper's Tab. 5 render FPS (Tanks & Temples, RTX 3090), for the ratios.
+PAPER_TAB5_FPS = {"full": 106, "w/o Decouple.": 101, "w/o Explicit": 121, "w/o Neural": 127,
+                  "w/o Background": 112, "w/o Pre-culling": 27}
+
+
+def run_ablation(args):
+    import torch
+    from paper_2509_17083_gb300 import hyrf as H
+    from paper_2509_17083_gb300 import synth
+    from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    H.lib()
+    w = synth.config3_360(n=args.n, precision="bf16")
+    tgt = torch.as_tensor(w.targets[0]).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    variants = [("full", {}, False), ("w/o Decouple.", {}, True), ("w/o Explicit", dict(explicit=False), False),
+                ("w/o Neural", dict(neural=False), False), ("w/o Background", dict(background=False), False),
+                ("w/o Pre-culling", dict(precull=False), False)]
+    steps = max(5, args.steps // 4)
+    out = {}
+    for name, kw, coupled in variants:
+        m = DeviceModel(w, coupled=coupled)
+        r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale, **kw)
+        r.fit_capacity(tgt)
+        res = {}
+        for mode in ("render", "train"):
+            for _ in range(3):
+                r.forward(tgt) if mode == "render" else r.step(tgt)
+            times = []
+            for _ in range(steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if mode == "render":
+                    r.forward(None, want_keys=False)
+                else:
+                    m.zero_grad()
+                    r.step(tgt)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            res["render_fps" if mode == "render" else "iters_per_s"] = round(1000.0 / float(np.mean(times)), 2)
+        res["visible"] = int(r.n_vis.item())
+        res["status"] = H.read_status(r.status)
+        out[name] = res
+        del r, m
+        torch.cuda.empty_cache()
+    base = out["full"]
+    for name, res in out.items():
+        res["fps_ratio"] = round(res["render_fps"] / base["render_fps"], 3)
+        res["its_ratio"] = round(res["iters_per_s"] / base["iters_per_s"], 3)
+        res["paper_fps_ratio"] = round(PAPER_TAB5_FPS[name] / PAPER_TAB5_FPS["full"], 3)
+    print(json.dumps({"metric": "Tab. 5 ablations: render FPS and fwd+bwd iters/s, BF16 fields",
+                      "config": {"workload": "config3 scene replicated around the camera (360 deg, ~25 % "
+                                             "in view), 1M Gaussians, 1237x822, 2^19 grids",
+                                 "steps": steps, "l2": "flushed between timed steps"},
+                      "variants": out}))
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def cpu_baseline(args, budget_s=15.0, w=None, frac=1.0):
@@ -500,5 +553,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.ablation:
+        run_ablation(a)
     else:
         run_ours(a)

@@ -142,6 +142,12 @@ typedef struct {
    * Gaussian i. Passing the buffer on to hyrf_query_fields_backward saves
    * that call the gather (memory for time; NULL: the backward gathers). */
   void* features;
+  /* Ablations of Tab. 5 ("w/o Neural", "w/o Explicit"): explicit_only = 1
+   * skips the fields (alpha = sigma(alpha_e), scale = sigma(s_e) on all
+   * three axes, rotation (1, 0, 0, 0), colour = sigma(c_e): isotropic,
+   * diffuse 3DGS; `fields` is not read). NULL alpha_e / scale_e / color_e
+   * mean zero explicit parts (neural only). 0 and non-NULL: HyRF. */
+  int32_t explicit_only;
 } hyrf_query_fields_args;
 
 size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a);
@@ -179,6 +185,9 @@ typedef struct {
    * call of the same view, with the tables unchanged since; NULL: the hash
    * features are gathered again. */
   const void* features;
+  /* As in the forward. NULL d_alpha_e / d_scale_e / d_color_e (or explicit
+   * inputs) skip those gradients. */
+  int32_t explicit_only;
 } hyrf_query_fields_backward_args;
 
 size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a);
@@ -346,6 +355,8 @@ hyrf_status hyrf_rasterize_backward(const hyrf_rasterize_backward_args* a, void*
  * mode 0 queries the field per pixel; mode 1 evaluates it on a map_h x
  * map_w equirectangular map of directions and samples it bilinearly.
  * ---------------------------------------------------------------------- */
+/* mode 2: no background (Tab. 5 "w/o Background"): C = C_fg, and the
+ * reverse gives dL/dC_fg = dL/dC, dL/dT_final = 0, no field gradients. */
 typedef struct {
   int32_t mode, map_h, map_w;
   float radius;

@@ -29,6 +29,7 @@ UNITS = {
     "gather": ("gather.cu", []),
     "optim": ("optim.cu", []),
     "densify": ("densify.cu", []),
+    "explicit": ("explicit.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
     "noalloc": ("noalloc.cu", []),

@@ -20,6 +20,10 @@ hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int
 hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t s);
 hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
 hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s);
+hyrf_status launch_query_explicit(const hyrf_query_fields_args& a, cudaStream_t s);
+hyrf_status launch_query_explicit_bwd(const hyrf_query_fields_backward_args& a, cudaStream_t s);
+hyrf_status launch_bg_none(const hyrf_composite_background_args& a, cudaStream_t s);
+hyrf_status launch_bg_none_bwd(const hyrf_composite_background_backward_args& b, cudaStream_t s);
 size_t tc_fwd_feature_bytes(int64_t rows, int fields);
 size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features);
 hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
@@ -151,6 +155,7 @@ extern "C" {
 
 size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a) {
   if (!a || a->n < 0) return 0;
+  if (a->explicit_only) return align_up(precull_workspace(a->n));
   FieldsDev F;
   const bool tc = make_fields(a->fields, F, true) && F.cm.bf16;
   return align_up(precull_workspace(a->n)) + (tc && !a->features ? tc_fwd_feature_bytes(a->n, 2) : 0);
@@ -159,11 +164,15 @@ size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a) {
 hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t ws_bytes,
                               void* stream) {
   if (!a || a->n < 0 || !cam_ok(a->cam)) return HYRF_ERR_INVALID_ARG;
-  if (a->n > 0 && (!a->pos || !a->alpha_e || !a->scale_e || !a->color_e || !a->vis_ids || !a->alpha ||
-                   !a->scale || !a->quat || !a->color))
+  if (a->n > 0 && (!a->pos || !a->vis_ids || !a->alpha || !a->scale || !a->quat || !a->color))
     return HYRF_ERR_INVALID_ARG;
   if (!a->n_vis || !ws_ok(ws, ws_bytes, hyrf_query_fields_workspace_size(a)))
     return HYRF_ERR_INVALID_ARG;
+  if (a->explicit_only) {  // "w/o Neural": no field is read
+    if (a->features) return HYRF_ERR_INVALID_ARG;
+    hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
+    return st != HYRF_OK ? st : launch_query_explicit(*a, S(stream));
+  }
   FieldsDev F;
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
@@ -177,7 +186,7 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
 }
 
 size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a) {
-  if (!a) return 0;
+  if (!a || a->explicit_only) return 0;
   FieldsDev F;
   if (!make_fields(a->fields, F, true) || a->n < 0) return 0;
   return F.cm.bf16 ? tc_bwd_workspace(F, true, a->n, a->features != nullptr) : align_up(slab_bytes(F, true));
@@ -186,10 +195,10 @@ size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backwar
 hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a, void* ws,
                                        size_t ws_bytes, void* stream) {
   if (!a || a->n < 0 || !cam_ok(a->cam) || !(a->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
-  if (a->n > 0 && (!a->pos || !a->alpha_e || !a->scale_e || !a->color_e || !a->vis_ids || !a->n_vis ||
-                   !a->d_alpha || !a->d_scale || !a->d_quat || !a->d_color || !a->d_pos ||
-                   !a->d_alpha_e || !a->d_scale_e || !a->d_color_e))
+  if (a->n > 0 && (!a->pos || !a->vis_ids || !a->n_vis || !a->d_alpha || !a->d_scale || !a->d_quat ||
+                   !a->d_color || !a->d_pos))
     return HYRF_ERR_INVALID_ARG;
+  if (a->explicit_only) return launch_query_explicit_bwd(*a, S(stream));
   FieldsDev F;
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
@@ -304,7 +313,8 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
   if (!(a->bg.radius > 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (a->bg.mode == 1 && (a->bg.map_h <= 0 || a->bg.map_w <= 0 || a->bg.map_h > 4096 || a->bg.map_w > 4096))
     return HYRF_ERR_INVALID_ARG;
-  if (a->bg.mode != 0 && a->bg.mode != 1) return HYRF_ERR_INVALID_ARG;
+  if (a->bg.mode != 0 && a->bg.mode != 1 && a->bg.mode != 2) return HYRF_ERR_INVALID_ARG;
+  if (a->bg.mode == 2) return a->features ? HYRF_ERR_INVALID_ARG : HYRF_OK;  // no field is read
   if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
   if (F.cm.bf16 && a->fields.rad.n_levels != 16) return HYRF_ERR_UNSUPPORTED;
   if (a->features && (a->bg.mode != 0 || !F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
@@ -312,6 +322,7 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
 }
 
 size_t hyrf_composite_background_workspace_size(const hyrf_composite_background_args* a) {
+  if (a && a->bg.mode == 2) return 0;
   FieldsDev F;
   if (!a || !make_fields(a->fields, F, false)) return 0;
   return bg_workspace(*a, F, false);
@@ -322,6 +333,7 @@ hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, v
   FieldsDev F;
   hyrf_status st = bg_check(a, F);
   if (st != HYRF_OK) return st;
+  if (a->bg.mode == 2) return a->C ? launch_bg_none(*a, S(stream)) : HYRF_ERR_INVALID_ARG;
   if (!a->C || !ws_ok(ws, ws_bytes, bg_workspace(*a, F, false))) return HYRF_ERR_INVALID_ARG;
   if (!bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (a->bg.mode == 0 && F.cm.bf16) return launch_bg_exact_fwd_tc(*a, F, ws, S(stream));
@@ -330,6 +342,7 @@ hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, v
 
 size_t hyrf_composite_background_backward_workspace_size(
     const hyrf_composite_background_backward_args* b) {
+  if (b && b->fwd.bg.mode == 2) return 0;
   FieldsDev F;
   if (!b || !make_fields(b->fwd.fields, F, false)) return 0;
   return bg_workspace(b->fwd, F, true);
@@ -342,6 +355,7 @@ hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_b
   hyrf_status st = bg_check(&b->fwd, F);
   if (st != HYRF_OK) return st;
   if (!b->d_C || !b->d_T_final || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (b->fwd.bg.mode == 2) return launch_bg_none_bwd(*b, S(stream));
   if (!ws_ok(ws, ws_bytes, bg_workspace(b->fwd, F, true))) return HYRF_ERR_INVALID_ARG;
   if (!bf16_weights_ok(b->fwd.fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (b->fwd.bg.mode == 0 && F.cm.bf16) return launch_bg_bwd_tc(*b, F, ws, S(stream));

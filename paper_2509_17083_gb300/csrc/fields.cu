@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev c
       mlp_fwd<NC, WID, NH, 3, WT>(F.cm, fc, col, kFwdPitch, co);
     }
     // Eq. 7 aggregation with the explicit parameters.
-    io.alpha[i] = sigmoidf_(go[0] + io.alpha_e[g]);
-    const float se = io.scale_e[g];
+    io.alpha[i] = sigmoidf_(go[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
+    const float se = io.scale_e ? io.scale_e[g] : 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(go[1 + k] + se);
     const float rn = sqrtf(go[4] * go[4] + go[5] * go[5] + go[6] * go[6] + go[7] * go[7]);
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev c
 #pragma unroll
     for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = go[4 + k] / den;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) io.color[3 * i + k] = sigmoidf_(co[k] + io.color_e[3 * (int64_t)g + k]);
+    for (int k = 0; k < 3; ++k) io.color[3 * i + k] = sigmoidf_(co[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
   }
 }
 
@@ -206,10 +206,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       for (int k = 0; k < 4; ++k) dq[k] = io.d_quat[4 * i + k] * ls;
 #pragma unroll
       for (int k = 0; k < 3; ++k) dcol[k] = io.d_color[3 * i + k] * ls;
-      ae = io.alpha_e[g];
-      se = io.scale_e[g];
+      ae = io.alpha_e ? io.alpha_e[g] : 0.0f;
+      se = io.scale_e ? io.scale_e[g] : 0.0f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) ce[k] = io.color_e[3 * (int64_t)g + k];
+      for (int k = 0; k < 3; ++k) ce[k] = io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f;
     }
     float dy[3] = {0.0f, 0.0f, 0.0f};
     // ---------------- geometry decoder (Eq. 4) and the reverse of Eq. 7
@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
         for (int k = 0; k < 8; ++k) dz8[k] = 0.0f;
       }
       if (ok) {
-        io.d_alpha_e[g] += dz8[0] * inv_ls;
-        io.d_scale_e[g] += (dz8[1] + dz8[2] + dz8[3]) * inv_ls;
+        if (io.d_alpha_e) io.d_alpha_e[g] += dz8[0] * inv_ls;
+        if (io.d_scale_e) io.d_scale_e[g] += (dz8[1] + dz8[2] + dz8[3]) * inv_ls;
       }
       float dx[NG];
       decoder_bwd<NG, WID, NH, 8, WT>(F.gm, act, dzb, dz8, slab, SL, 0, dx);
@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       }
       if (ok) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) io.d_color_e[3 * (int64_t)g + k] += dz3[k] * inv_ls;
+        if (io.d_color_e)
+          for (int k = 0; k < 3; ++k) io.d_color_e[3 * (int64_t)g + k] += dz3[k] * inv_ls;
       }
       float dx[NC];
       decoder_bwd<NC, WID, NH, 3, WT>(F.cm, act, dzb, dz3, slab, SL, 1, dx);

@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
     if (ok) {
       if (geo) {
         // Eq. 7: alpha, scale from the geometry decoder, rotation normalised
-        io.alpha[i] = sigmoidf_(o[0] + b2[0] + io.alpha_e[g]);
-        const float se = io.scale_e[g];
+        io.alpha[i] = sigmoidf_(o[0] + b2[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
+        const float se = io.scale_e ? io.scale_e[g] : 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(o[1 + k] + b2[1 + k] + se);
         float q[4];
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
       } else {
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-          io.color[3 * i + k] = sigmoidf_(o[k] + b2[k] + io.color_e[3 * (int64_t)g + k]);
+          io.color[3 * i + k] = sigmoidf_(o[k] + b2[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
       }
     }
     fence_before();

@@ -144,8 +144,8 @@ struct GeoGauss {
     for (int k = 0; k < 3; ++k) R.ds[k] = R.ok ? P.d_scale[3 * idx + k] : 0.0f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) R.dq[k] = R.ok ? P.d_quat[4 * idx + k] : 0.0f;
-    R.ae = R.ok ? P.alpha_e[R.g] : 0.0f;
-    R.se = R.ok ? P.scale_e[R.g] : 0.0f;
+    R.ae = R.ok && P.alpha_e ? P.alpha_e[R.g] : 0.0f;
+    R.se = R.ok && P.scale_e ? P.scale_e[R.g] : 0.0f;
   }
   // Reverse of Eq. 7 for alpha, scale and rotation; o = raw decoder outputs.
   __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
@@ -172,8 +172,8 @@ struct GeoGauss {
       for (int k = 0; k < 8; ++k) dz[k] = 0.0f;
       return;
     }
-    P.d_alpha_e[R.g] += dz[0];
-    P.d_scale_e[R.g] += dz[1] + dz[2] + dz[3];
+    if (P.d_alpha_e) P.d_alpha_e[R.g] += dz[0];
+    if (P.d_scale_e) P.d_scale_e[R.g] += dz[1] + dz[2] + dz[3];
   }
   // dx = dX columns [16h, 16h + 16)
   __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx,
@@ -205,7 +205,7 @@ struct ColGauss {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         R.dc[k] = R.ok ? P.d_color[3 * idx + k] : 0.0f;
-        R.ce[k] = R.ok ? P.color_e[3 * (int64_t)R.g + k] : 0.0f;
+        R.ce[k] = R.ok && P.color_e ? P.color_e[3 * (int64_t)R.g + k] : 0.0f;
       }
       return;
     }
@@ -228,7 +228,7 @@ struct ColGauss {
       const float c = sigmoidf_(o[k] + R.ce[k]);
       dz[k] = R.ok ? R.dc[k] * c * (1.0f - c) : 0.0f;
     }
-    if (R.ok) {
+    if (R.ok && P.d_color_e) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) P.d_color_e[3 * (int64_t)R.g + k] += dz[k];
     }

@@ -58,7 +58,7 @@ class hyrf_query_fields_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("pos", _vp), ("alpha_e", _vp), ("scale_e", _vp),
                 ("color_e", _vp), ("cam", hyrf_camera), ("fields", hyrf_fields),
                 ("vis_ids", _vp), ("n_vis", _vp), ("alpha", _vp), ("scale", _vp), ("quat", _vp),
-                ("color", _vp), ("status", _vp), ("features", _vp)]
+                ("color", _vp), ("status", _vp), ("features", _vp), ("explicit_only", C.c_int32)]
 
 
 class hyrf_query_fields_backward_args(C.Structure):
@@ -67,7 +67,7 @@ class hyrf_query_fields_backward_args(C.Structure):
                 ("vis_ids", _vp), ("n_vis", _vp), ("d_alpha", _vp), ("d_scale", _vp),
                 ("d_quat", _vp), ("d_color", _vp), ("d_pos", _vp), ("d_alpha_e", _vp),
                 ("d_scale_e", _vp), ("d_color_e", _vp), ("grads", hyrf_field_grads),
-                ("loss_scale", C.c_float), ("status", _vp), ("features", _vp)]
+                ("loss_scale", C.c_float), ("status", _vp), ("features", _vp), ("explicit_only", C.c_int32)]
 
 
 class hyrf_project_args(C.Structure):

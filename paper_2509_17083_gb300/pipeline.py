@@ -22,7 +22,11 @@ def _t(a, device, dtype=torch.float32):
 
 
 class DeviceModel:
-    def __init__(self, workload, device="cuda"):
+    """coupled=True: one hash grid serves both decoders (Tab. 5 "w/o
+    Decouple."): the geometry decoder reads the radiance grid and both
+    gradients land in one buffer."""
+
+    def __init__(self, workload, device="cuda", coupled=False):
         self.device = device
         self.workload = workload
         g = workload.gaussians
@@ -35,8 +39,9 @@ class DeviceModel:
         self.fl = fl
         self.bf16 = workload.precision == "bf16"
         tdt = torch.bfloat16 if self.bf16 else torch.float32
-        self.geo_table = _t(fl.geo.table, device, tdt)
+        self.coupled = bool(coupled)
         self.rad_table = _t(fl.rad.table, device, tdt)
+        self.geo_table = self.rad_table if self.coupled else _t(fl.geo.table, device, tdt)
         wdt = torch.bfloat16 if self.bf16 else torch.float32
         self.geo_W = [_t(w, device, wdt) for w in fl.geo_mlp.W]
         self.geo_b = [_t(b, device) for b in fl.geo_mlp.b]
@@ -52,12 +57,13 @@ class DeviceModel:
             self.grad = dict(
                 pos=torch.zeros_like(self.pos), alpha_e=torch.zeros_like(self.alpha_e),
                 scale_e=torch.zeros_like(self.scale_e), color_e=torch.zeros_like(self.color_e),
-                geo_table=torch.zeros(self.geo_table.shape, device=d),
                 rad_table=torch.zeros(self.rad_table.shape, device=d),
                 geo_W=[torch.zeros(w.shape, device=d) for w in self.geo_W],
                 geo_b=[torch.zeros_like(b) for b in self.geo_b],
                 col_W=[torch.zeros(w.shape, device=d) for w in self.col_W],
                 col_b=[torch.zeros_like(b) for b in self.col_b])
+            self.grad["geo_table"] = (self.grad["rad_table"] if self.coupled
+                                      else torch.zeros(self.geo_table.shape, device=d))
         else:
             for v in self.grad.values():
                 if isinstance(v, list):
@@ -71,7 +77,7 @@ class DeviceModel:
         s = H.hyrf_fields()
         s.box_lo[:] = [float(x) for x in fl.box_lo]
         s.box_hi[:] = [float(x) for x in fl.box_hi]
-        s.geo = H.grid(self.geo_table, fl.geo, self.dtype_code)
+        s.geo = H.grid(self.geo_table, fl.rad if self.coupled else fl.geo, self.dtype_code)
         s.rad = H.grid(self.rad_table, fl.rad, self.dtype_code)
         s.geo_mlp = H.mlp(self.geo_W, self.geo_b, fl.geo_mlp, self.dtype_code)
         s.col_mlp = H.mlp(self.col_W, self.col_b, fl.col_mlp, self.dtype_code)
@@ -99,10 +105,15 @@ class ViewRenderer:
     features gathered by the forward (2 x 64 B per Gaussian, 64 B per pixel)
     for the backward, which then skips its gather; off = gather again
     (recompute). workspaces: a scratch dict shared with other views
-    (shared_workspaces())."""
+    (shared_workspaces()).
+
+    Ablations of Tab. 5: neural=False (explicit-only isotropic Gaussians),
+    explicit=False (neural terms only), background=False (C = C_fg),
+    precull=False (every Gaussian in front of the near plane is queried)."""
 
     def __init__(self, model: DeviceModel, cam, bg, lam=0.0, loss_scale=1.0, capacity=None,
-                 save_features=None, workspaces=None):
+                 save_features=None, workspaces=None, neural=True, explicit=True, background=True,
+                 precull=True):
         self.m = model
         self.cam = cam
         self.bg = bg
@@ -133,19 +144,24 @@ class ViewRenderer:
         # scratch of the library calls; views that run one after the other on
         # one stream may share one dict (see shared_workspaces)
         self.ws = workspaces if workspaces is not None else shared_workspaces(d)
+        self.neural, self.explicit = bool(neural), bool(explicit)
+        self.background, self.precull = bool(background), bool(precull)
         if save_features is None:
-            save_features = model.bf16
+            save_features = model.bf16 and self.neural
         if save_features and not model.bf16:
             raise ValueError("save_features needs BF16 fields")
         self.save_features = bool(save_features)
         self.feat_q = self.feat_b = None
         if self.save_features:
             self.feat_q = torch.empty(2 * max(n, 1) * 32, dtype=torch.bfloat16, device=d)
-            if int(bg.mode) == 0:
+            if int(bg.mode) == 0 and self.background:
                 self.feat_b = torch.empty(W * Hh * 32, dtype=torch.bfloat16, device=d)
         self.set_capacity(capacity if capacity is not None else max(4 * n, 1 << 16))
         self.ccam = H.camera(cam)
-        self.cbg = H.hyrf_background(int(bg.mode), int(bg.map_h), int(bg.map_w), float(bg.radius))
+        if not self.precull:
+            self.ccam.cull_tol = 1e30
+        self.cbg = H.hyrf_background(int(bg.mode) if self.background else 2, int(bg.map_h), int(bg.map_w),
+                                     float(bg.radius))
 
     def set_capacity(self, cap):
         self.capacity = int(cap)
@@ -171,13 +187,31 @@ class ViewRenderer:
                         features=self.feat_b))
         return a
 
-    def forward(self, target=None, want_keys=True):
+    def query_kwargs(self):
+        """Arguments of hyrf_query_fields for this view."""
         m = self.m
-        fs = m.fields_struct()
-        H.hyrf_query_fields(ws=self.ws["q"], n=m.n, pos=m.pos, alpha_e=m.alpha_e, scale_e=m.scale_e,
-                            color_e=m.color_e, cam=self.ccam, fields=fs, vis_ids=self.vis_ids,
-                            n_vis=self.n_vis, alpha=self.alpha, scale=self.scale, quat=self.quat,
-                            color=self.color, status=self.status, features=self.feat_q)
+        e = self.explicit
+        return dict(n=m.n, pos=m.pos, alpha_e=m.alpha_e if e else None, scale_e=m.scale_e if e else None,
+                    color_e=m.color_e if e else None, cam=self.ccam, fields=m.fields_struct(),
+                    vis_ids=self.vis_ids, n_vis=self.n_vis, alpha=self.alpha, scale=self.scale, quat=self.quat,
+                    color=self.color, status=self.status, features=self.feat_q,
+                    explicit_only=0 if self.neural else 1)
+
+    def query_backward_kwargs(self):
+        """Arguments of hyrf_query_fields_backward for this view."""
+        m = self.m
+        e = self.explicit
+        return dict(n=m.n, pos=m.pos, alpha_e=m.alpha_e if e else None, scale_e=m.scale_e if e else None,
+                    color_e=m.color_e if e else None, cam=self.ccam, fields=m.fields_struct(),
+                    vis_ids=self.vis_ids, n_vis=self.n_vis, d_alpha=self.d_alpha, d_scale=self.d_scale,
+                    d_quat=self.d_quat, d_color=self.d_color, d_pos=m.grad["pos"],
+                    d_alpha_e=m.grad["alpha_e"] if e else None, d_scale_e=m.grad["scale_e"] if e else None,
+                    d_color_e=m.grad["color_e"] if e else None, grads=m.grads_struct(),
+                    loss_scale=self.loss_scale, status=self.status, features=self.feat_q,
+                    explicit_only=0 if self.neural else 1)
+
+    def forward(self, target=None, want_keys=True):
+        H.hyrf_query_fields(ws=self.ws["q"], **self.query_kwargs())
         self.project()
         self.bin_sort(want_keys)
         H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
@@ -231,17 +265,7 @@ class ViewRenderer:
 
     def backward_fields(self):
         """Reverse of the field query (decoders, hash encodings, aggregation)."""
-        m = self.m
-        g = m.grads_struct()
-        H.hyrf_query_fields_backward(ws=self.ws["qb"], n=m.n, pos=m.pos, alpha_e=m.alpha_e,
-                                     scale_e=m.scale_e, color_e=m.color_e, cam=self.ccam,
-                                     fields=m.fields_struct(), vis_ids=self.vis_ids,
-                                     n_vis=self.n_vis, d_alpha=self.d_alpha, d_scale=self.d_scale,
-                                     d_quat=self.d_quat, d_color=self.d_color, d_pos=m.grad["pos"],
-                                     d_alpha_e=m.grad["alpha_e"], d_scale_e=m.grad["scale_e"],
-                                     d_color_e=m.grad["color_e"], grads=g,
-                                     loss_scale=self.loss_scale, status=self.status,
-                                     features=self.feat_q)
+        H.hyrf_query_fields_backward(ws=self.ws["qb"], **self.query_backward_kwargs())
 
     def step(self, target):
         """One training iteration of the view: forward, loss, backward."""
@@ -307,6 +331,8 @@ class Trainer:
         add(model.scale_e, g["scale_e"], lr["scale_e"])
         add(model.color_e, g["color_e"], lr["color_e"])
         for name in ("geo_table", "rad_table"):
+            if name == "geo_table" and model.coupled:
+                continue  # one grid serves both decoders
             t = getattr(model, name)
             add(t, g[name], lr["table"], shadow=t if model.bf16 else None)
         for W, gW, b, gb in zip(model.geo_W + model.col_W, g["geo_W"] + g["col_W"],

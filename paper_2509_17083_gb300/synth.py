@@ -299,6 +299,34 @@ def config3(n=1_000_000, width=1237, height=822, log2_T=19, n_clusters=256, prec
                     1024.0 if precision == "bf16" else 1.0)
 
 
+def config3_360(n=1_000_000, width=1237, height=822, log2_T=19, n_clusters=256, precision="bf16",
+                table_init=1e-4, seed=0):
+    """The config-3 scene replicated around the camera: four groups of n/4
+    Gaussians, group k turned by k x 90 deg about the camera's vertical axis,
+    so that about a quarter lies in the view (a 360-degree capture, as the
+    Tanks & Temples scenes of the paper's ablation, Tab. 5)."""
+    rng = _rng(seed)
+    cam = pinhole(width, height, 60.0)
+    parts = []
+    for k in range(4):
+        p = cluster_points(rng, n // 4 + (1 if k < n % 4 else 0), n_clusters // 4, cam).astype(np.float64)
+        a = k * 0.5 * np.pi
+        Ry = np.array([[np.cos(a), 0.0, np.sin(a)], [0.0, 1.0, 0.0], [-np.sin(a), 0.0, np.cos(a)]])
+        c = cam.center()
+        parts.append(((p - c) @ Ry.T + c).astype(np.float32))
+    pos = np.concatenate(parts, 0)
+    pos = pos[rng.permutation(len(pos))]
+    g = explicit_params(rng, pos)
+    lo, hi = percentile_box(pos)
+    fl = make_fields(rng, lo, hi, 16, log2_T, 64, 2, table_init)
+    if precision == "bf16":
+        fl = to_bf16(fl)
+    tr = _rng(seed + 1)
+    return Workload(f"config3-360: 1M Gaussians around the camera @1237x822, {precision.upper()}", g, fl,
+                    [cam], Background(mode=0), [noise_target(tr, cam)], 0.0, precision,
+                    1024.0 if precision == "bf16" else 1.0)
+
+
 def config4(n=3_000_000, width=1297, height=840, log2_T=21, n_clusters=1024, n_views=8,
             precision="bf16", table_init=1e-4, seed=0):
     """3M Gaussians in 1024 clusters inside a radius-2 ball at the origin,
