@@ -283,6 +283,32 @@ def run_ours(args):
             e1.record(stream)
             torch.cuda.synchronize()
             fwd_ms.append(e0.elapsed_time(e1))
+        # render-time background skip (tau_T = 0.2, the paper's value; BF16 only)
+        tau_ms = []
+        if prec == "bf16":
+            for _ in range(max(3, args.steps // 2)):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.forward(None, want_keys=False, tau_T=0.2)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tau_ms.append(e0.elapsed_time(e1))
+        # the 8-bit grid codec (render only)
+        u8_ms = []
+        if prec == "bf16":
+            m.quantize_u8()
+            for _ in range(max(3, args.steps // 2)):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.forward(None, want_keys=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                u8_ms.append(e0.elapsed_time(e1))
+            m.quantize_u8(False)
         # end to end through the C ABI with host buffers: target H2D, loss D2H per step
         pinned = torch.as_tensor(w.targets[0]).pin_memory()
         dev_tgt = torch.empty_like(tgt)
@@ -305,6 +331,8 @@ def run_ours(args):
         psnr = float(-10.0 * torch.log10(((C - tgt) ** 2).mean()).item())
         evals = int(r.n_contrib.sum().item())
         results[prec] = dict(ms=ms, fwd_ms=float(np.mean(fwd_ms)), e2e_ms=float(np.mean(e2e_ms)),
+                             tau_ms=float(np.mean(tau_ms)) if tau_ms else None,
+                             u8_ms=float(np.mean(u8_ms)) if u8_ms else None,
                              stage_ms=stage_ms, launches_per_step=launches / args.steps,
                              n_vis=nv, instances=K, status=st, clocks=clocks, wall_s=t_wall,
                              loss=float(r.loss.item()),
@@ -333,6 +361,8 @@ def run_ours(args):
                       "l2": "flushed between timed steps (256 MiB write)",
                       "parallelism": f"replicas x{ws}"},
            "render_fps": round(ws * 1000.0 / R["fwd_ms"], 2),
+           "render_fps_tau_T_0.2": round(ws * 1000.0 / R["tau_ms"], 2) if R.get("tau_ms") else None,
+           "render_fps_u8_grids": round(ws * 1000.0 / R["u8_ms"], 2) if R.get("u8_ms") else None,
            "stage_ms": {k: round(v, 4) for k, v in R["stage_ms"].items()},
            "kernels": kern,
            "psnr_db": round(R["psnr"], 4),
@@ -411,7 +441,19 @@ def run_ablation(args):
     steps = max(5, args.steps // 4)
     out = {}
     for name, kw, coupled in variants:
-        m = DeviceModel(w, coupled=coupled)
+        wv = w
+        if not kw.get("explicit", True):
+            # without explicit parts the decoders' output biases carry the
+            # explicit initial values (mean logits), so that the neural-only
+            # Gaussians start with the same opacities, sizes and colours
+            import dataclasses
+            fl = w.fields
+            gb = [b.copy() for b in fl.geo_mlp.b]
+            gb[-1][0] += float(np.mean(w.gaussians.alpha_e))
+            gb[-1][1:4] += float(np.mean(w.gaussians.scale_e))
+            wv = dataclasses.replace(w, fields=dataclasses.replace(
+                fl, geo_mlp=dataclasses.replace(fl.geo_mlp, b=gb)))
+        m = DeviceModel(wv, coupled=coupled)
         r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale, **kw)
         r.fit_capacity(tgt)
         res = {}

@@ -55,7 +55,7 @@ typedef enum {
   HYRF_ERR_TIMEOUT = 32,  /* device: a bounded wait on a tensor-core completion gave up */
 } hyrf_status;
 
-typedef enum { HYRF_F32 = 0, HYRF_BF16 = 1 } hyrf_dtype;
+typedef enum { HYRF_F32 = 0, HYRF_BF16 = 1, HYRF_U8 = 2 } hyrf_dtype;
 
 /* Pinhole camera, world to camera x_c = R x_w + t (Eq. 8). Pixel (i, j)
  * samples the image plane at (i + 0.5, j + 0.5); u = fx x_c/z_c + cx.
@@ -71,14 +71,17 @@ typedef struct {
 } hyrf_camera;
 
 /* Multi-resolution hash grid (Eq. 3): table [n_levels][2^log2_T][n_feat] of
- * `dtype` (HYRF_F32 or HYRF_BF16). Level l has resolution
- * floor(base_res * growth^l) and is stored densely when its (res+1)^3
- * vertices fit in 2^log2_T entries, else spatially hashed. n_feat must be 2. */
+ * `dtype`. Level l has resolution floor(base_res * growth^l) and is stored
+ * densely when its (res+1)^3 vertices fit in 2^log2_T entries, else
+ * spatially hashed. n_feat must be 2. HYRF_U8 (render only; the 8-bit
+ * min-max codec of the compressed model, Sec. 4.4): uint8 codes, value =
+ * qparams[2 l] + qparams[2 l + 1] * code (see hyrf_quantize_grid). */
 typedef struct {
   const void* table;
   int32_t n_levels, log2_T, n_feat, base_res;
   float growth;
   int32_t dtype;
+  const float* qparams;      /* HYRF_U8: [n_levels][2] (lo, step) device; else NULL */
 } hyrf_grid;
 
 /* Decoder MLP (Eqs. 4, 6; Sec. 4.1): n_hidden ReLU layers of `width`, then a
@@ -356,10 +359,16 @@ hyrf_status hyrf_rasterize_backward(const hyrf_rasterize_backward_args* a, void*
  * map_w equirectangular map of directions and samples it bilinearly.
  * ---------------------------------------------------------------------- */
 /* mode 2: no background (Tab. 5 "w/o Background"): C = C_fg, and the
- * reverse gives dL/dC_fg = dL/dC, dL/dT_final = 0, no field gradients. */
+ * reverse gives dL/dC_fg = dL/dC, dL/dT_final = 0, no field gradients.
+ * tau_T > 0 (mode 0, BF16 fields, forward only): the paper's render-time
+ * rule (Sec. 3.4, tau_T = 0.2 in its experiments) queries the background
+ * only at pixels with T_final >= tau_T; elsewhere C = C_fg. A reverse call
+ * with tau_T > 0 is rejected (training composites the background
+ * everywhere). */
 typedef struct {
   int32_t mode, map_h, map_w;
   float radius;
+  float tau_T;
 } hyrf_background;
 
 typedef struct {
@@ -374,7 +383,8 @@ typedef struct {
    * bf16, 16-byte aligned, caller-owned. The forward writes the radiance
    * hash features of every pixel's sphere hit; the backward, which gets
    * these arguments as `fwd`, reads them instead of gathering again (the
-   * buffer must still hold the forward's values). */
+   * buffer must still hold the forward's values). A forward with
+   * bg.tau_T > 0 does not write it. */
   void* features;
 } hyrf_composite_background_args;
 
@@ -531,6 +541,15 @@ hyrf_status hyrf_densify_apply(const hyrf_densify_apply_args* a, void* stream);
  * alpha_e (m, v; may be NULL) restart from zero. */
 hyrf_status hyrf_reset_opacity(float* alpha_e, int64_t n, float max_logit, float* m, float* v,
                                void* stream);
+
+/* hyrf_quantize_grid: the 8-bit min-max codec of a hash table (Sec. 4.4's
+ * compressed model quantises the grids). Per level l over its T x 2 values:
+ * lo = min, hi = max, step = (hi - lo) / 255 (float), code = rint((x - lo)
+ * / step) clamped to [0, 255] (0 when step = 0). table: [n_levels][T][2]
+ * float32 (dtype HYRF_F32) or bf16 (HYRF_BF16); codes [n_levels][T][2]
+ * uint8 out; qparams [n_levels][2] float32 out. */
+hyrf_status hyrf_quantize_grid(const void* table, int32_t dtype, int32_t n_levels, int32_t log2_T,
+                               uint8_t* codes, float* qparams, void* stream);
 
 #define HYRF_ADAM_MAX_TENSORS 32
 typedef struct {

@@ -454,6 +454,21 @@ def loss(C_img, target, lam):
     return L, dC
 
 
+def quantize_grid(table):
+    """8-bit min-max codes of a [L, T, 2] table: (codes uint8, qparams
+    [L, 2] float32, decoded float64)."""
+    t = np.ascontiguousarray(table, dtype=np.float32)
+    L = t.shape[0]
+    per = t[0].size
+    codes = np.zeros(t.shape, dtype=np.uint8)
+    q = np.zeros((L, 2), dtype=np.float32)
+    dec = np.zeros(t.shape)
+    rc = lib().orc_quantize_grid(L, C.c_int64(per), _ptr(t, _f32p), _ptr(codes, _u8p), _ptr(q, _f32p),
+                                 _ptr(dec, _f64p))
+    assert rc == 0
+    return codes, q, dec
+
+
 def adam_step(p, grad, m, v, lr, b1, b2, eps, t, grad_scale=1.0):
     """One Adam step (Kingma & Ba, Algorithm 1) on float64 copies; returns
     the updated (p, m, v)."""

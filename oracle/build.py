@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["oracle_fields.cpp", "oracle_render.cpp", "oracle_optim.cpp"]
+SOURCES = ["oracle_fields.cpp", "oracle_render.cpp", "oracle_optim.cpp", "oracle_codec.cpp"]
 HEADERS = ["hyrf_oracle.h", "oracle_internal.h"]
 OUT_DIR = os.path.join(HERE, "_build")
 OUT = os.path.join(OUT_DIR, "liborc.so")

@@ -39,6 +39,8 @@
  *                    the loss w.r.t. every parameter class
  *   Adam             first-step closed form p - lr g / (|g| + eps); constant
  *                    gradient over t steps; zero gradient decays the moments
+ *   8-bit codec      codes of an affine ramp; min/max map to 0/255;
+ *                    round trip within step / 2
  *   density control  hand-built keep / prune / clone / split cases; counts
  *                    and offsets by brute force; split halves at p + s * z
  *                    for the identity rotation, mirrored for q and -q
@@ -229,6 +231,14 @@ double orc_loss(int32_t width, int32_t height, const double* C, const double* ta
 /* SSIM alone (11x11 Gaussian window, sigma 1.5, zero padding), mean over
  * pixels and channels. */
 double orc_ssim(int32_t width, int32_t height, const double* x, const double* y);
+
+/* ---------------- 8-bit min-max codec of a grid (Sec. 4.4) -------------- */
+/* Per level of per_level values: lo = min, step = (max - lo) / 255 (float),
+ * code = rint((x - lo) / step) in [0, 255] (0 if step = 0); FP32 replay.
+ * qparams [n_levels][2] = (lo, step); decoded (optional) = lo + step code
+ * in FP64. */
+int32_t orc_quantize_grid(int32_t n_levels, int64_t per_level, const float* table, uint8_t* codes,
+                          float* qparams, double* decoded);
 
 /* ---------------- training: Adam (Kingma & Ba, Algorithm 1) ------------- */
 /* One Adam step of n parameters in place (3DGS and Instant-NGP train with

@@ -344,6 +344,13 @@ int32_t orc_project_f32(int32_t n, const float* pos, const float* scale, const f
     float tc[3];
     cam_point_f32(c, p, tc);
     const float x = tc[0], y = tc[1], z = tc[2];
+    if (!(z > c.z_near)) {  // behind the near plane: no footprint (3DGS's own near culling)
+      rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
+      ntiles[i] = 0;
+      depth[i] = z;
+      flag[i] = 0;
+      continue;
+    }
     const float u = c.fx * x / z + c.cx;
     const float v = c.fy * y / z + c.cy;
     const float limx = 1.3f * (0.5f * (float)c.W / c.fx);

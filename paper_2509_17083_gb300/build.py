@@ -30,6 +30,7 @@ UNITS = {
     "optim": ("optim.cu", []),
     "densify": ("densify.cu", []),
     "explicit": ("explicit.cu", []),
+    "codec": ("codec.cu", []),
     "proj_bwd": ("proj_bwd.cu", []),
     "sort": ("sort.cu", []),
     "noalloc": ("noalloc.cu", []),

@@ -201,6 +201,7 @@ hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a,
   if (a->explicit_only) return launch_query_explicit_bwd(*a, S(stream));
   FieldsDev F;
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
+  if (F.geo.u8 || F.rad.u8) return HYRF_ERR_UNSUPPORTED;  // the 8-bit codec renders only
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
     return HYRF_ERR_UNSUPPORTED;
   if (!ws_ok(ws, ws_bytes, hyrf_query_fields_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
@@ -318,6 +319,8 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
   if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
   if (F.cm.bf16 && a->fields.rad.n_levels != 16) return HYRF_ERR_UNSUPPORTED;
   if (a->features && (a->bg.mode != 0 || !F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
+  if (!(a->bg.tau_T >= 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (a->bg.tau_T > 0.0f && (a->bg.mode != 0 || !F.cm.bf16)) return HYRF_ERR_UNSUPPORTED;
   return HYRF_OK;
 }
 
@@ -356,6 +359,8 @@ hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_b
   if (st != HYRF_OK) return st;
   if (!b->d_C || !b->d_T_final || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (b->fwd.bg.mode == 2) return launch_bg_none_bwd(*b, S(stream));
+  if (b->fwd.bg.tau_T > 0.0f) return HYRF_ERR_INVALID_ARG;  // render-only rule
+  if (F.rad.u8) return HYRF_ERR_UNSUPPORTED;                 // the 8-bit codec renders only
   if (!ws_ok(ws, ws_bytes, bg_workspace(b->fwd, F, true))) return HYRF_ERR_INVALID_ARG;
   if (!bf16_weights_ok(b->fwd.fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (b->fwd.bg.mode == 0 && F.cm.bf16) return launch_bg_bwd_tc(*b, F, ws, S(stream));

@@ -17,12 +17,15 @@ constexpr int kPEPad = 32;       // width of the positional-encoding block of th
 
 // One hash grid as the kernels see it (built on the host from hyrf_grid).
 struct GridDev {
-  const void* table;   // [L][T][2] float or bf16
+  const void* table;   // [L][T][2] float, bf16 or uint8 codes
   uint32_t T;          // entries per level (power of two)
   uint32_t mask;       // T - 1
   uint32_t dense;      // bit l: level l is stored densely
   int L;
   int bf16;
+  int u8;              // uint8 codes with per-level (lo, step) in q
+  int log2T;
+  const float* q;
   int res[kMaxLevels]; // level resolution floor(base * growth^l)
 };
 

@@ -81,6 +81,11 @@ __device__ __forceinline__ float corner_w(const float f[3], int c) {
 }
 
 __device__ __forceinline__ float2 load_entry(const GridDev& G, size_t e) {
+  if (G.u8) {
+    const uchar2 c = __ldg(reinterpret_cast<const uchar2*>(G.table) + e);
+    const float2 q = __ldg(reinterpret_cast<const float2*>(G.q) + (e >> G.log2T));
+    return make_float2(fmaf(q.y, (float)c.x, q.x), fmaf(q.y, (float)c.y, q.x));
+  }
   if (G.bf16) {
     const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(G.table) + e);
     return __bfloat1622float2(v);

@@ -601,7 +601,8 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
     }
     if (!g.table || g.n_levels < 1 || g.n_levels > kMaxLevels || g.n_feat != 2 || g.log2_T < 4 ||
         g.log2_T > 26 || g.base_res < 1 || !(g.growth >= 1.0f) ||
-        (g.dtype != HYRF_F32 && g.dtype != HYRF_BF16))
+        (g.dtype != HYRF_F32 && g.dtype != HYRF_BF16 && g.dtype != HYRF_U8) ||
+        (g.dtype == HYRF_U8 && !g.qparams))
       return false;
     GridDev& o = *gd[k];
     o.table = g.table;
@@ -609,6 +610,9 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
     o.T = 1u << g.log2_T;
     o.mask = o.T - 1u;
     o.bf16 = g.dtype == HYRF_BF16;
+    o.u8 = g.dtype == HYRF_U8;
+    o.q = g.qparams;
+    o.log2T = g.log2_T;
     o.dense = 0;
     for (int l = 0; l < g.n_levels; ++l) {
       const double r = std::floor((double)g.base_res * std::pow((double)g.growth, (double)l));
@@ -704,13 +708,13 @@ hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float r
 }
 
 size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features);
-size_t tc_fwd_feature_bytes(int64_t rows, int fields);
+size_t tc_bg_fwd_workspace(int64_t P, bool have_features, bool skip);
 
 size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward) {
   if (a.bg.mode == 0 && F.cm.bf16) {  // tensor-core path: gathered features (+ gradients)
     const int64_t P = (int64_t)a.cam.width * a.cam.height;
-    const bool have = a.features != nullptr;
-    return backward ? tc_bwd_workspace(F, false, P, have) : (have ? 0 : tc_fwd_feature_bytes(P, 1));
+    const bool have = a.features != nullptr, skip = a.bg.tau_T > 0.0f;
+    return backward ? tc_bwd_workspace(F, false, P, have) : tc_bg_fwd_workspace(P, have && !skip, skip);
   }
   Carver c(nullptr);
   if (a.bg.mode == 1) {

@@ -201,6 +201,8 @@ constexpr uint32_t kBgTmemCols = 128;
 
 __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
                                                            const uint32_t* __restrict__ Xb,
+                                                           const int32_t* __restrict__ px_ids,
+                                                           const int32_t* __restrict__ n_px,
                                                            const float* __restrict__ C_fg,
                                                            const float* __restrict__ T_final,
                                                            float* __restrict__ C, int32_t* status) {
@@ -234,15 +236,17 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
   const uint32_t tm = tmem_base;
   const uint32_t lane = ((uint32_t)(w * 32)) << 16;
   const int P = cam.W * cam.H;
-  const int ntile = (P + 127) / 128;
+  const int rows = px_ids ? min(*n_px, P) : P;  // listed pixels, or all
+  const int ntile = (rows + 127) / 128;
   uint32_t phase = 0;
   bool failed = false;
   for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
-    const int p = tile * 128 + t;
-    const bool ok = p < P;
-    const int pp = ok ? p : 0;
+    const int row = tile * 128 + t;
+    const bool ok = row < rows;
+    const int pp = ok ? (px_ids ? px_ids[row] : row) : 0;
+    const int p = pp;
     {
-      load_row32<64>(sm + bAc, t, Xb + (size_t)pp * 16, ok);
+      load_row32<64>(sm + bAc, t, Xb + (size_t)(ok ? row : 0) * 16, ok);
       float ps[3], dir[3], pe[32];
       bg_ray(cam, F, radius, pp % cam.W, pp / cam.W, ps, dir);
       pos_enc(dir, pe);
@@ -321,7 +325,7 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
   uint32_t* X = a.features ? static_cast<uint32_t*>(a.features) : c.take<uint32_t>((size_t)2 * a.n * 16);
   uint32_t *Xg = X, *Xr = X + (size_t)a.n * 16;
   const CamDev cam = to_dev(a.cam);
-  const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status};
+  const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status, nullptr, nullptr};
   hyrf_status st = launch_gather(F, cam, RS, a.n, Xg, Xr, s);
   if (st != HYRF_OK) return st;
   tc::QueryIO io{a.n,     a.pos, a.alpha_e, a.scale_e, a.color_e, a.vis_ids, a.n_vis,
@@ -334,12 +338,74 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
   return HYRF_OK;
 }
 
+// Render-time background skip (tau_T > 0): C = C_fg where T_final < tau_T;
+// the other pixels are listed, in image order within each CTA, for the
+// gather and the decoder.
+__global__ void __launch_bounds__(256) k_bg_select(int P, float tau, const float* __restrict__ T_final,
+                                                   const float* __restrict__ C_fg, float* __restrict__ C,
+                                                   int32_t* __restrict__ list, int32_t* __restrict__ count) {
+  __shared__ int wsum[8];
+  __shared__ int base;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int p0 = blockIdx.x * 256; p0 < P; p0 += gridDim.x * 256) {
+    const int p = p0 + t;
+    const bool in = p < P;
+    const bool keep = in && T_final[p] >= tau;
+    if (in && !keep) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k];
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    if (t == 0) {
+      int tot = 0;
+      for (int q = 0; q < 8; ++q) {
+        const int c = wsum[q];
+        wsum[q] = tot;
+        tot += c;
+      }
+      base = atomicAdd(count, tot);
+    }
+    __syncthreads();
+    if (keep) list[base + wsum[w] + __popc(bal & ((1u << lane) - 1u))] = p;
+    __syncthreads();
+  }
+}
+
+// Workspace of the BF16 exact background forward: features, and with tau_T
+// the pixel list and its count.
+size_t tc_bg_fwd_workspace(int64_t P, bool have_features, bool skip) {
+  Carver c(nullptr);
+  if (!have_features) c.take<uint32_t>((size_t)P * 16);
+  if (skip) {
+    c.take<int32_t>((size_t)P);
+    c.take<int32_t>(1);
+  }
+  return c.size();
+}
+
 hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
                                    cudaStream_t s) {
   const CamDev cam = to_dev(a.cam);
   const int P = cam.W * cam.H;
-  uint32_t* Xb = static_cast<uint32_t*>(a.features ? a.features : ws);
-  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status};
+  const bool skip = a.bg.tau_T > 0.0f;
+  Carver c(ws);
+  // with the skip the rows are the listed pixels: the caller's feature buffer
+  // (pixel-indexed, for the reverse) is not written
+  uint32_t* Xb = a.features && !skip ? static_cast<uint32_t*>(a.features) : c.take<uint32_t>((size_t)P * 16);
+  int32_t* list = nullptr;
+  int32_t* count = nullptr;
+  if (skip) {
+    list = c.take<int32_t>((size_t)P);
+    count = c.take<int32_t>(1);
+    cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+    int blocks = (P + 255) / 256;
+    if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+    HYRF_LAUNCH("k_bg_select", s,
+                k_bg_select<<<blocks, 256, 0, s>>>(P, a.bg.tau_T, a.T_final, a.C_fg, a.C, list, count));
+  }
+  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, list, count};
   hyrf_status st = launch_gather(F, cam, RS, P, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
   set_smem_limit<tc::k_bg_exact_fwd_tc>(tc::kBgSmem);
@@ -347,8 +413,8 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
   int grid = num_sms() * 4;
   if (tiles < grid) grid = tiles;
   HYRF_LAUNCH("k_bg_exact_fwd_tc", s,
-              tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, a.C_fg, a.T_final,
-                                                                  a.C, a.status));
+              tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, list, count, a.C_fg,
+                                                                  a.T_final, a.C, a.status));
   return HYRF_OK;
 }
 

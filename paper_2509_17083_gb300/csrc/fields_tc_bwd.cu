@@ -608,7 +608,7 @@ hyrf_status launch_query_bwd_tc(const hyrf_query_fields_backward_args& a, const 
   uint32_t *Xg = X, *Xr = X + (size_t)a.n * 16;
   float *dXg = dX, *dXr = dX + (size_t)a.n * 32;
   cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
-  const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status};
+  const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status, nullptr, nullptr};
   hyrf_status st = saved ? HYRF_OK : launch_gather(F, cam, RS, a.n, Xg, Xr, s);
   if (st != HYRF_OK) return st;
   tc::GaussP P{a.n,       a.pos,     a.alpha_e, a.scale_e, a.color_e, a.vis_ids,   a.n_vis,
@@ -635,7 +635,7 @@ hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, c
   uint32_t* Xb = saved ? static_cast<uint32_t*>(a.features) : c.take<uint32_t>((size_t)P_ * 16);
   float* dXb = c.take<float>((size_t)P_ * 32);
   cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
-  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status};
+  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
   hyrf_status st = saved ? HYRF_OK : launch_gather(F, cam, RS, P_, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
   tc::PixelP P{a.bg.radius, a.T_final, b.d_C, Xb, dXb, b.d_C_fg, b.d_T_final};

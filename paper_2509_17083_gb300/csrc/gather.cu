@@ -31,7 +31,8 @@ constexpr int kLevels = 16;  // levels (warps)
 constexpr int kThreads = kRows * kLevels;
 
 __device__ __forceinline__ int row_count(const RowSource& S, const CamDev& cam) {
-  return S.pixels ? cam.W * cam.H : min(*S.n_vis, S.n);
+  if (!S.pixels) return min(*S.n_vis, S.n);
+  return S.px_ids ? min(*S.n_px, cam.W * cam.H) : cam.W * cam.H;
 }
 
 // Contracted position (and, for Gaussians, the Gaussian index and the
@@ -42,7 +43,7 @@ __device__ __forceinline__ void row_point(const RowSource& S, const FieldsDev& F
   ok = row < nrows;
   g = 0;
   if (S.pixels) {
-    const int p = ok ? row : 0;
+    const int p = ok ? (S.px_ids ? S.px_ids[row] : row) : 0;
     float ps[3], dir[3];
     tc::bg_ray(cam, F, S.radius, p % cam.W, p / cam.W, ps, dir);
     contract_n(ps, y);

@@ -182,6 +182,13 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
     float tc[3];
     cam_point(c, p, tc);
     const float x = tc[0], y = tc[1], z = tc[2];
+    if (!(z > c.z_near)) {  // behind the near plane (rows kept without the pre-cull): no footprint
+      o.ntiles[i] = 0;
+      o.rect[4 * i] = o.rect[4 * i + 1] = o.rect[4 * i + 2] = o.rect[4 * i + 3] = 0;
+      o.depth[i] = z;
+      if (o.flag) o.flag[i] = 0;
+      continue;
+    }
     const float u = c.fx * x / z + c.cx;
     const float v = c.fy * y / z + c.cy;
     const float limx = 1.3f * (0.5f * (float)c.W / c.fx);

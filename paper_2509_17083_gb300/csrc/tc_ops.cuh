@@ -26,6 +26,8 @@ struct RowSource {
   const float* pos;         // [n][3]
   float radius;             // background sphere radius (pixels)
   int32_t* status;
+  const int32_t* px_ids;    // pixels: optional list of the pixels to process
+  const int32_t* n_px;      // its device count
 };
 
 // gather.cu: bf16 features X [rows][32] per field, and the reverse scatter

@@ -21,6 +21,7 @@ HYRF_ERR_BOUNDS = 16
 HYRF_ERR_TIMEOUT = 32
 HYRF_F32 = 0
 HYRF_BF16 = 1
+HYRF_U8 = 2
 TILE = 16
 
 _vp = C.c_void_p
@@ -35,7 +36,7 @@ class hyrf_camera(C.Structure):
 class hyrf_grid(C.Structure):
     _fields_ = [("table", _vp), ("n_levels", C.c_int32), ("log2_T", C.c_int32),
                 ("n_feat", C.c_int32), ("base_res", C.c_int32), ("growth", C.c_float),
-                ("dtype", C.c_int32)]
+                ("dtype", C.c_int32), ("qparams", _vp)]
 
 
 class hyrf_mlp(C.Structure):
@@ -104,7 +105,7 @@ class hyrf_rasterize_backward_args(C.Structure):
 
 class hyrf_background(C.Structure):
     _fields_ = [("mode", C.c_int32), ("map_h", C.c_int32), ("map_w", C.c_int32),
-                ("radius", C.c_float)]
+                ("radius", C.c_float), ("tau_T", C.c_float)]
 
 
 class hyrf_composite_background_args(C.Structure):
@@ -196,6 +197,8 @@ def lib():
         L.hyrf_densify_stats.restype = C.c_int32
         L.hyrf_densify_apply.argtypes = [C.POINTER(hyrf_densify_apply_args), _vp]
         L.hyrf_densify_apply.restype = C.c_int32
+        L.hyrf_quantize_grid.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]
+        L.hyrf_quantize_grid.restype = C.c_int32
         L.hyrf_reset_opacity.argtypes = [_vp, C.c_int64, C.c_float, _vp, _vp, _vp]
         L.hyrf_reset_opacity.restype = C.c_int32
         L.hyrf_bin_sort_noalloc.argtypes = [C.POINTER(hyrf_bin_sort_args), _vp]
@@ -338,13 +341,20 @@ def camera(cam):
     return c
 
 
-def grid(table, g, dtype):
+def grid(table, g, dtype, qparams=None):
     s = hyrf_grid()
     s.table = ptr(table)
     s.n_levels, s.log2_T, s.n_feat, s.base_res = g.n_levels, g.log2_T, g.n_feat, g.base_res
     s.growth = g.growth
     s.dtype = dtype
+    s.qparams = ptr(qparams)
     return s
+
+
+def hyrf_quantize_grid(table, dtype, n_levels, log2_T, codes, qparams, stream=None):
+    """8-bit min-max codes of a hash table (per level lo and step)."""
+    _check("hyrf_quantize_grid", lib().hyrf_quantize_grid(ptr(table), int(dtype), int(n_levels), int(log2_T),
+                                                          ptr(codes), ptr(qparams), stream_handle(stream)))
 
 
 def mlp(Ws, bs, m, dtype):

@@ -48,6 +48,7 @@ class DeviceModel:
         self.col_W = [_t(w, device, wdt) for w in fl.col_mlp.W]
         self.col_b = [_t(b, device) for b in fl.col_mlp.b]
         self.dtype_code = H.HYRF_BF16 if self.bf16 else H.HYRF_F32
+        self.codes = None  # (geo codes, geo qparams, rad codes, rad qparams) once quantised
         self.grad = {}
         self.zero_grad()
 
@@ -77,12 +78,31 @@ class DeviceModel:
         s = H.hyrf_fields()
         s.box_lo[:] = [float(x) for x in fl.box_lo]
         s.box_hi[:] = [float(x) for x in fl.box_hi]
-        s.geo = H.grid(self.geo_table, fl.rad if self.coupled else fl.geo, self.dtype_code)
-        s.rad = H.grid(self.rad_table, fl.rad, self.dtype_code)
+        if self.codes is not None:  # the 8-bit codec (render only)
+            gc, gq, rc, rq = self.codes
+            s.geo = H.grid(gc, fl.rad if self.coupled else fl.geo, H.HYRF_U8, gq)
+            s.rad = H.grid(rc, fl.rad, H.HYRF_U8, rq)
+        else:
+            s.geo = H.grid(self.geo_table, fl.rad if self.coupled else fl.geo, self.dtype_code)
+            s.rad = H.grid(self.rad_table, fl.rad, self.dtype_code)
         s.geo_mlp = H.mlp(self.geo_W, self.geo_b, fl.geo_mlp, self.dtype_code)
         s.col_mlp = H.mlp(self.col_W, self.col_b, fl.col_mlp, self.dtype_code)
         s.pe_freq, s.pe_pad = fl.pe_freq, fl.pe_pad
         return s
+
+    def quantize_u8(self, on=True):
+        """Switch the grids to their 8-bit min-max codes (render only; the
+        float tables stay and are used again after quantize_u8(False))."""
+        if not on:
+            self.codes = None
+            return
+        out = []
+        for t, g in ((self.geo_table, self.fl.geo), (self.rad_table, self.fl.rad)):
+            codes = torch.empty(t.shape, dtype=torch.uint8, device=self.device)
+            q = torch.empty(g.n_levels, 2, dtype=torch.float32, device=self.device)
+            H.hyrf_quantize_grid(t, self.dtype_code, g.n_levels, g.log2_T, codes, q)
+            out += [codes, q]
+        self.codes = tuple(out)
 
     def grads_struct(self):
         g = self.grad
@@ -158,8 +178,12 @@ class ViewRenderer:
                 self.feat_b = torch.empty(W * Hh * 32, dtype=torch.bfloat16, device=d)
         self.set_capacity(capacity if capacity is not None else max(4 * n, 1 << 16))
         self.ccam = H.camera(cam)
+        # the field query's camera: without the pre-cull every Gaussian is
+        # queried (the projection still drops those behind the near plane)
+        self.ccam_q = H.camera(cam)
         if not self.precull:
-            self.ccam.cull_tol = 1e30
+            self.ccam_q.cull_tol = 1e30
+            self.ccam_q.z_near = -1e30
         self.cbg = H.hyrf_background(int(bg.mode) if self.background else 2, int(bg.map_h), int(bg.map_w),
                                      float(bg.radius))
 
@@ -178,11 +202,12 @@ class ViewRenderer:
                         T_final=self.T_final, n_contrib=self.n_contrib, status=self.status))
         return a
 
-    def _bg_args(self):
+    def _bg_args(self, tau_T=0.0):
         a = H.hyrf_composite_background_args()
         a.cam = self.ccam
         a.fields = self.m.fields_struct()
         a.bg = self.cbg
+        a.bg.tau_T = float(tau_T)
         H._fill(a, dict(C_fg=self.C_fg, T_final=self.T_final, C=self.C, status=self.status,
                         features=self.feat_b))
         return a
@@ -192,7 +217,7 @@ class ViewRenderer:
         m = self.m
         e = self.explicit
         return dict(n=m.n, pos=m.pos, alpha_e=m.alpha_e if e else None, scale_e=m.scale_e if e else None,
-                    color_e=m.color_e if e else None, cam=self.ccam, fields=m.fields_struct(),
+                    color_e=m.color_e if e else None, cam=self.ccam_q, fields=m.fields_struct(),
                     vis_ids=self.vis_ids, n_vis=self.n_vis, alpha=self.alpha, scale=self.scale, quat=self.quat,
                     color=self.color, status=self.status, features=self.feat_q,
                     explicit_only=0 if self.neural else 1)
@@ -202,7 +227,7 @@ class ViewRenderer:
         m = self.m
         e = self.explicit
         return dict(n=m.n, pos=m.pos, alpha_e=m.alpha_e if e else None, scale_e=m.scale_e if e else None,
-                    color_e=m.color_e if e else None, cam=self.ccam, fields=m.fields_struct(),
+                    color_e=m.color_e if e else None, cam=self.ccam_q, fields=m.fields_struct(),
                     vis_ids=self.vis_ids, n_vis=self.n_vis, d_alpha=self.d_alpha, d_scale=self.d_scale,
                     d_quat=self.d_quat, d_color=self.d_color, d_pos=m.grad["pos"],
                     d_alpha_e=m.grad["alpha_e"] if e else None, d_scale_e=m.grad["scale_e"] if e else None,
@@ -210,12 +235,14 @@ class ViewRenderer:
                     loss_scale=self.loss_scale, status=self.status, features=self.feat_q,
                     explicit_only=0 if self.neural else 1)
 
-    def forward(self, target=None, want_keys=True):
+    def forward(self, target=None, want_keys=True, tau_T=0.0):
+        """The forward path; tau_T > 0 (render only) queries the background
+        only where T_final >= tau_T."""
         H.hyrf_query_fields(ws=self.ws["q"], **self.query_kwargs())
         self.project()
         self.bin_sort(want_keys)
         H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
-        H.call("hyrf_composite_background", self._bg_args(), self.ws["b"])
+        H.call("hyrf_composite_background", self._bg_args(tau_T), self.ws["b"])
         if target is not None:
             self.loss_fn(target)
         return self.C

@@ -103,3 +103,27 @@ def test_no_background_is_foreground():
                                          grads=m.grads_struct(), loss_scale=1.0)
     torch.cuda.synchronize()
     assert torch.equal(r.C, r.dC) and float(r.dT.abs().max()) == 0.0
+
+
+def test_no_precull_queries_every_gaussian_and_projection_drops_the_rest():
+    w = synth.config3_360(n=8000, width=200, height=150, log2_T=14, n_clusters=16, precision="f32")
+    cam = w.cams[0]
+    m = DeviceModel(w)
+    r = ViewRenderer(m, cam, w.bg, precull=False)
+    r.fit_capacity()
+    r.forward(None)
+    torch.cuda.synchronize()
+    n = w.gaussians.n
+    assert int(r.n_vis.item()) == n
+    assert np.array_equal(np_(r.vis_ids)[:n], np.arange(n))
+    rng = np.random.default_rng(8)
+    s = np.exp(rng.uniform(-5, -2, (n, 3))).astype(np.float32)
+    q = synth.random_quats(rng, n)
+    r.scale[:n].copy_(torch.tensor(s, device="cuda"))
+    r.quat[:n].copy_(torch.tensor(q, device="cuda"))
+    r.project()
+    torch.cuda.synchronize()
+    rect, ntiles, depth, flag = oracle.project_f32(w.gaussians.pos, s, q, cam)
+    assert np.array_equal(np_(r.rect)[:n], rect) and np.array_equal(np_(r.ntiles)[:n], ntiles)
+    behind = depth <= cam.z_near
+    assert behind.sum() > n // 4 and (ntiles[behind] == 0).all()

@@ -142,3 +142,64 @@ def test_saved_features_match_regathered():
     assert np.array_equal(out[0][0], out[1][0])
     for k, g in out[0][1].items():
         assert rel_l2(g, out[1][1][k]) < 1e-5, k
+
+
+def test_background_skip_below_tau_T():
+    """Render-time rule: the background is queried only where T_final >=
+    tau_T; elsewhere C = C_fg. The reverse refuses the skip."""
+    w = _workload("bf16", init=0.3, n=1000, W=160, H_=120)
+    cam = w.cams[0]
+    m = DeviceModel(w)
+    r = ViewRenderer(m, cam, w.bg)
+    rng = np.random.default_rng(71)
+    Cfg = rng.uniform(0, 1, (120, 160, 3)).astype(np.float32)
+    T = rng.uniform(0, 1, (120, 160)).astype(np.float32)
+    r.C_fg.copy_(cuda_f32(Cfg))
+    r.T_final.copy_(cuda_f32(T))
+    r.status.zero_()
+    H.call("hyrf_composite_background", r._bg_args(0.2), r.ws["b"])
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    C_or, _ = oracle.background(cam, w.fields, w.bg, Cfg, T)
+    skip = T < np.float32(0.2)
+    assert 0.1 < skip.mean() < 0.3
+    got = np_(r.C)
+    assert np.array_equal(got[skip], Cfg[skip])
+    assert np.abs(got[~skip] - C_or[~skip]).max() < TOL_IMG_BF16_TRAINED
+    with pytest.raises(H.HyrfError):
+        H.hyrf_composite_background_backward(r._bg_args(0.2), ws=r.ws["bb"], d_C=r.dC, d_C_fg=None,
+                                             d_T_final=r.dT, grads=m.grads_struct(), loss_scale=1.0)
+
+
+def test_u8_codec_codes_and_render_match_oracle():
+    """8-bit min-max grid codec: codes and level ranges bit for bit against
+    the oracle's float replay; a render with the coded grids (decoded inside
+    the gathers) against the oracle rendering with the decoded tables."""
+    w = _workload("bf16", init=0.3, n=20000, W=257, H_=171)
+    m = DeviceModel(w)
+    m.quantize_u8()
+    torch.cuda.synchronize()
+    fl = w.fields
+    dec = {}
+    for name, k in (("geo", 0), ("rad", 2)):
+        codes, q, d = oracle.quantize_grid(getattr(fl, name).table)
+        assert np.array_equal(np_(m.codes[k]), codes), name
+        assert np.array_equal(np_(m.codes[k + 1]).view(np.uint32), q.view(np.uint32)), name
+        dec[name] = d.astype(np.float32)
+    import dataclasses
+    flq = dataclasses.replace(fl, geo=dataclasses.replace(fl.geo, table=dec["geo"]),
+                              rad=dataclasses.replace(fl.rad, table=dec["rad"]))
+    wq = dataclasses.replace(w, fields=flq)
+    r = ViewRenderer(m, w.cams[0], w.bg)
+    r.fit_capacity()
+    r.status.zero_()
+    r.forward(None)
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    fw = oracle.render(wq.gaussians, wq.fields, w.cams[0], w.bg)
+    mask = oracle.decision_safe_mask(fw, w.cams[0], fields=wq.fields, bg=w.bg, bg_relu_margin=RELU_MARGIN_BF16[1])
+    err = np.abs(np_(r.C) - fw["C"]).max(-1)
+    assert err[mask].max() < TOL_IMG_BF16_TRAINED, err[mask].max()
+    # the codec renders only
+    with pytest.raises(H.HyrfError):
+        r.backward_fields()
