@@ -36,6 +36,8 @@ def parse():
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-s", type=float, default=15.0)
+    p.add_argument("--layout", default="input", choices=["input", "morton"],
+                   help="storage order of the Gaussians (morton: hyrf_spatial_order once at load)")
     p.add_argument("--ablation", action="store_true",
                    help="render FPS and fwd+bwd it/s of the Tab. 5 ablations on the 360-degree variant")
     return p.parse_args()
@@ -174,6 +176,8 @@ def run_ours(args):
     for prec in precisions:
         w = synth.config3(n=args.n, precision=prec, seed=local)
         m = DeviceModel(w, device=dev)
+        if args.layout == "morton":
+            m.spatial_order()  # one-time layout step at load, outside the timed region
         r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
         tgt = torch.as_tensor(w.targets[0]).to(dev)
         try:
@@ -358,7 +362,7 @@ def run_ours(args):
            "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": head, "gaussians": args.n,
                       "image": "1237x822", "visible": R["n_vis"], "instances": R["instances"],
-                      "l2": "flushed between timed steps (256 MiB write)",
+                      "l2": "flushed between timed steps (256 MiB write)", "layout": args.layout,
                       "parallelism": f"replicas x{ws}"},
            "render_fps": round(ws * 1000.0 / R["fwd_ms"], 2),
            "render_fps_tau_T_0.2": round(ws * 1000.0 / R["tau_ms"], 2) if R.get("tau_ms") else None,

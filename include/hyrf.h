@@ -120,7 +120,10 @@ typedef struct {
 
 /* ------------------------------------------------------------------------
  * hyrf_query_fields: visibility pre-culling (Eqs. 8-9) of all N Gaussians,
- * ascending compaction of the kept ones, then for each kept Gaussian the
+ * ascending compaction of the kept ones (a negative cam.z_near keeps
+ * Gaussians behind the camera too: the "w/o Pre-culling" ablation sets
+ * z_near = -1e30 and a huge cull_tol to query every Gaussian), then for each
+ * kept Gaussian the
  * contraction (Eq. 2), both hash encodings (Eq. 3), both decoders
  * (Eqs. 4-6) and the aggregation with the explicit parameters (Eq. 7).
  * ---------------------------------------------------------------------- */
@@ -550,6 +553,29 @@ hyrf_status hyrf_reset_opacity(float* alpha_e, int64_t n, float max_logit, float
  * uint8 out; qparams [n_levels][2] float32 out. */
 hyrf_status hyrf_quantize_grid(const void* table, int32_t dtype, int32_t n_levels, int32_t log2_T,
                                uint8_t* codes, float* qparams, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Storage order (no counterpart in the paper; a data-layout step of this
+ * library). hyrf_spatial_order: perm[k] = the Gaussian that comes k-th in
+ * the Morton (Z-curve) order of its contracted position (App. A.1, Eq. 2)
+ * quantised to 10 bits per axis; ties keep the input order. Storing the
+ * Gaussians in this order puts neighbours next to each other, so the hash
+ * gathers and scatters of consecutive rows share cache lines.
+ * hyrf_permute_rows: dst[k] = src[perm[k]] for every array (width floats
+ * per row; kind ignored), count <= HYRF_REMAP_MAX.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;
+  const float* pos;          /* [N][3] */
+  float box_lo[3], box_hi[3];
+  int32_t* perm;             /* out [N] */
+} hyrf_spatial_order_args;
+
+size_t hyrf_spatial_order_workspace_size(const hyrf_spatial_order_args* a);
+hyrf_status hyrf_spatial_order(const hyrf_spatial_order_args* a, void* workspace, size_t ws_bytes,
+                               void* stream);
+hyrf_status hyrf_permute_rows(const int32_t* perm, int32_t n, const hyrf_remap_array* arrays, int32_t count,
+                              void* stream);
 
 #define HYRF_ADAM_MAX_TENSORS 32
 typedef struct {

@@ -129,6 +129,16 @@ static bool cam_ok(const hyrf_camera& c) {
          c.fy > 0.0f && c.z_near >= 0.0f && c.cull_tol >= 0.0f;
 }
 
+// The field query's camera may carry a negative near distance: the pre-cull
+// then keeps Gaussians behind the camera too (the "w/o Pre-culling"
+// ablation queries every Gaussian; the projection drops them).
+static bool query_cam_ok(const hyrf_camera& c) {
+  hyrf_camera d = c;
+  if (!(c.z_near == c.z_near)) return false;
+  d.z_near = 0.0f;
+  return cam_ok(d);
+}
+
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // bf16 decoder weights are staged with 16-byte vector loads
@@ -163,7 +173,7 @@ size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a) {
 
 hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t ws_bytes,
                               void* stream) {
-  if (!a || a->n < 0 || !cam_ok(a->cam)) return HYRF_ERR_INVALID_ARG;
+  if (!a || a->n < 0 || !query_cam_ok(a->cam)) return HYRF_ERR_INVALID_ARG;
   if (a->n > 0 && (!a->pos || !a->vis_ids || !a->alpha || !a->scale || !a->quat || !a->color))
     return HYRF_ERR_INVALID_ARG;
   if (!a->n_vis || !ws_ok(ws, ws_bytes, hyrf_query_fields_workspace_size(a)))
@@ -177,6 +187,8 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
     return HYRF_ERR_UNSUPPORTED;
+  // both grids of one type; 8-bit codes only with the tensor-core decoders
+  if (F.geo.bf16 != F.rad.bf16 || F.geo.u8 != F.rad.u8 || (F.rad.u8 && !F.cm.bf16)) return HYRF_ERR_UNSUPPORTED;
   if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (a->features && (!F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
@@ -194,7 +206,7 @@ size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backwar
 
 hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a, void* ws,
                                        size_t ws_bytes, void* stream) {
-  if (!a || a->n < 0 || !cam_ok(a->cam) || !(a->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (!a || a->n < 0 || !query_cam_ok(a->cam) || !(a->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (a->n > 0 && (!a->pos || !a->vis_ids || !a->n_vis || !a->d_alpha || !a->d_scale || !a->d_quat ||
                    !a->d_color || !a->d_pos))
     return HYRF_ERR_INVALID_ARG;
@@ -318,6 +330,7 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
   if (a->bg.mode == 2) return a->features ? HYRF_ERR_INVALID_ARG : HYRF_OK;  // no field is read
   if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
   if (F.cm.bf16 && a->fields.rad.n_levels != 16) return HYRF_ERR_UNSUPPORTED;
+  if (F.rad.u8 && (!F.cm.bf16 || a->bg.mode != 0)) return HYRF_ERR_UNSUPPORTED;
   if (a->features && (a->bg.mode != 0 || !F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   if (!(a->bg.tau_T >= 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (a->bg.tau_T > 0.0f && (a->bg.mode != 0 || !F.cm.bf16)) return HYRF_ERR_UNSUPPORTED;

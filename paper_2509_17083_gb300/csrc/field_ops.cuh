@@ -80,12 +80,23 @@ __device__ __forceinline__ float corner_w(const float f[3], int c) {
          ((c & 4) ? f[2] : 1.0f - f[2]);
 }
 
-__device__ __forceinline__ float2 load_entry(const GridDev& G, size_t e) {
-  if (G.u8) {
+// Entry e of a table whose type is known at compile time: 0 float32,
+// 1 bf16, 2 uint8 codes (value = lo + step * code, per level).
+template <int DT>
+__device__ __forceinline__ float2 load_entry_t(const GridDev& G, size_t e) {
+  if constexpr (DT == 2) {
     const uchar2 c = __ldg(reinterpret_cast<const uchar2*>(G.table) + e);
     const float2 q = __ldg(reinterpret_cast<const float2*>(G.q) + (e >> G.log2T));
     return make_float2(fmaf(q.y, (float)c.x, q.x), fmaf(q.y, (float)c.y, q.x));
+  } else if constexpr (DT == 1) {
+    return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(G.table) + e));
+  } else {
+    return __ldg(reinterpret_cast<const float2*>(G.table) + e);
   }
+}
+
+// float32 or bf16 table (runtime flag), for the fused FP32 kernels.
+__device__ __forceinline__ float2 load_entry(const GridDev& G, size_t e) {
   if (G.bf16) {
     const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(G.table) + e);
     return __bfloat1622float2(v);

@@ -65,13 +65,14 @@ __device__ __forceinline__ void row_point(const RowSource& S, const FieldsDev& F
 
 // Eq. 3 at one level: the two interpolated features, summed over the corners
 // in the same order as the fused field kernels.
+template <int DT>
 __device__ __forceinline__ float2 level_feature(const GridDev& G, int l, const float y[3]) {
   uint32_t idx[8];
   float f[3];
   level_cell(G, l, y, idx, f);
   float2 e[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) e[c] = load_entry(G, (size_t)l * G.T + idx[c]);
+  for (int c = 0; c < 8; ++c) e[c] = load_entry_t<DT>(G, (size_t)l * G.T + idx[c]);
   float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -123,7 +124,7 @@ __device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, u
 // Reverse of level_feature: (d0, d1) = dL/d features of level l. Adds
 // w_c (d0, d1) to the table gradient of every corner and returns the level's
 // dL/dy if WANT_DY. COHERENT: lanes hold neighbouring points (run_atomic).
-template <bool COHERENT, bool WANT_DY>
+template <bool COHERENT, bool WANT_DY, int DT>
 __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const float y[3], float d0, float d1,
                                               float* __restrict__ gtab, float dy[3]) {
   if (WANT_DY) dy[0] = dy[1] = dy[2] = 0.0f;
@@ -145,7 +146,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
     else if (g0 != 0.0f || g1 != 0.0f)
       atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
     if (WANT_DY) {
-      const float2 v = load_entry(G, e);
+      const float2 v = load_entry_t<DT>(G, e);
       const float dot = v.x * d0 + v.y * d1;
       const float wx = (c & 1) ? f[0] : 1.0f - f[0];
       const float wy = (c & 2) ? f[1] : 1.0f - f[1];
@@ -165,7 +166,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
 
 // Features of both fields (Gaussians) or of the radiance field only (pixels).
 // X*: [rows][16] uint32 = [rows][32] bf16, level-major (2l, 2l+1).
-template <bool BOTH>
+template <bool BOTH, int DT>
 __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
     k_gather(FieldsDev F, CamDev cam, RowSource S, uint32_t* __restrict__ Xg, uint32_t* __restrict__ Xr) {
   __shared__ float ys[kRows][3];
@@ -185,10 +186,10 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
   __syncthreads();
   const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
   if (BOTH) {
-    const float2 a = level_feature(F.geo, l, y);
+    const float2 a = level_feature<DT>(F.geo, l, y);
     xs[0][lane][l] = tc::pack2(a.x, a.y);
   }
-  const float2 b = level_feature(F.rad, l, y);
+  const float2 b = level_feature<DT>(F.rad, l, y);
   xs[1][lane][l] = tc::pack2(b.x, b.y);
   __syncthreads();
   // coalesced write-out: thread t -> row t/16, word t%16
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
 // Reverse of k_gather. dXg/dXr: [rows][32] f32 feature gradients (already
 // unscaled; streamed with evict-first loads). Gaussians: both fields, and
 // d_pos[g] += J^T sum_l dL/dy_l; pixels: the radiance field.
-template <bool GAUSS>
+template <bool GAUSS, int DT>
 __global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
     k_scatter(FieldsDev F, CamDev cam, RowSource S, const float* __restrict__ dXg,
               const float* __restrict__ dXr, float* __restrict__ g_geo, float* __restrict__ g_rad,
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
     const float2 dg = ok ? __ldcs(reinterpret_cast<const float2*>(dXg + o)) : zero;
     const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
     float dy[3], dy2[3];
-    level_scatter<false, true>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
-    level_scatter<false, true>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
+    level_scatter<false, true, DT>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
+    level_scatter<false, true, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
 #pragma unroll
     for (int k = 0; k < 3; ++k) dys[l][lane][k] = dy[k] + dy2[k];
     __syncthreads();
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
   } else {
     const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
     float dy[3];
-    level_scatter<true, false>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
+    level_scatter<true, false, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
   }
 }
 
@@ -270,15 +271,39 @@ int grid_for(int rows) { return rows > 0 ? (rows + kRows - 1) / kRows : 0; }
 // rows: an upper bound of the device row count (n for Gaussians, W*H for
 // pixels). Gaussians gather and scatter both fields, pixels the radiance
 // field only.
+template <int DT>
+static hyrf_status gather_dt(const FieldsDev& F, const CamDev& cam, const RowSource& S, int grid, uint32_t* Xg,
+                             uint32_t* Xr, cudaStream_t s) {
+  if (!S.pixels)
+    HYRF_LAUNCH("k_gather<gaussians>", s, k_gather<true, DT><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
+  else
+    HYRF_LAUNCH("k_gather<pixels>", s, k_gather<false, DT><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
+  return HYRF_OK;
+}
+
+template <int DT>
+static hyrf_status scatter_dt(const FieldsDev& F, const CamDev& cam, const RowSource& S, int grid,
+                              const float* dXg, const float* dXr, float* g_geo, float* g_rad, float* d_pos,
+                              cudaStream_t s) {
+  if (!S.pixels)
+    HYRF_LAUNCH("k_scatter<gaussians>", s,
+                k_scatter<true, DT><<<grid, kThreads, 0, s>>>(F, cam, S, dXg, dXr, g_geo, g_rad, d_pos));
+  else
+    HYRF_LAUNCH("k_scatter<pixels>", s,
+                k_scatter<false, DT><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, dXr, nullptr, g_rad, nullptr));
+  return HYRF_OK;
+}
+
+// rows: an upper bound of the device row count (n for Gaussians, W*H for
+// pixels). Gaussians gather and scatter both fields, pixels the radiance
+// field only. The table type (both grids alike) picks the instantiation.
 hyrf_status launch_gather(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows, uint32_t* Xg,
                           uint32_t* Xr, cudaStream_t s) {
   const int grid = grid_for(rows);
   if (grid == 0) return HYRF_OK;
-  if (!S.pixels)
-    HYRF_LAUNCH("k_gather<gaussians>", s, k_gather<true><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
-  else
-    HYRF_LAUNCH("k_gather<pixels>", s, k_gather<false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
-  return HYRF_OK;
+  if (F.rad.u8) return gather_dt<2>(F, cam, S, grid, Xg, Xr, s);
+  if (F.rad.bf16) return gather_dt<1>(F, cam, S, grid, Xg, Xr, s);
+  return gather_dt<0>(F, cam, S, grid, Xg, Xr, s);
 }
 
 hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows,
@@ -286,13 +311,9 @@ hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSourc
                            cudaStream_t s) {
   const int grid = grid_for(rows);
   if (grid == 0) return HYRF_OK;
-  if (!S.pixels)
-    HYRF_LAUNCH("k_scatter<gaussians>", s,
-                k_scatter<true><<<grid, kThreads, 0, s>>>(F, cam, S, dXg, dXr, g_geo, g_rad, d_pos));
-  else
-    HYRF_LAUNCH("k_scatter<pixels>", s,
-                k_scatter<false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, dXr, nullptr, g_rad, nullptr));
-  return HYRF_OK;
+  if (F.rad.u8) return HYRF_ERR_UNSUPPORTED;  // the codec renders only
+  if (F.rad.bf16) return scatter_dt<1>(F, cam, S, grid, dXg, dXr, g_geo, g_rad, d_pos, s);
+  return scatter_dt<0>(F, cam, S, grid, dXg, dXr, g_geo, g_rad, d_pos, s);
 }
 
 }  // namespace hyrf

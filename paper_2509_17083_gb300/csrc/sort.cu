@@ -503,4 +503,120 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   return HYRF_OK;
 }
 
+// ---------------------------------------------------------------- storage order
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {  // bit i -> bit 3i
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Morton code of the contracted position (App. A.1 normalisation, Eq. 2
+// with the +0.5 offset), 10 bits per axis; vals = identity.
+__global__ void __launch_bounds__(256) k_morton(int n, const float* __restrict__ pos, float3 lo, float3 sx,
+                                                uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float x[3] = {(pos[3 * (int64_t)i] - lo.x) * sx.x - 1.0f, (pos[3 * (int64_t)i + 1] - lo.y) * sx.y - 1.0f,
+                        (pos[3 * (int64_t)i + 2] - lo.z) * sx.z - 1.0f};
+    const float r = sqrtf(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    const float g = r <= 1.0f ? 1.0f : (2.0f - 1.0f / r) / r;
+    uint32_t q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float y = 0.25f * g * x[k] + 0.5f;
+      q[k] = (uint32_t)fminf(fmaxf(y * 1024.0f, 0.0f), 1023.0f);
+    }
+    keys[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+    vals[i] = i;
+  }
+}
+
+__global__ void k_set_count(int32_t* c, int n) { *c = n; }
+
+struct PermuteArgs {
+  hyrf_remap_array a[HYRF_REMAP_MAX];
+  int count;
+};
+
+__global__ void __launch_bounds__(256) k_permute_rows(const int32_t* __restrict__ perm, int n, PermuteArgs P) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int64_t g = perm[k];
+    if (g < 0 || g >= n) continue;
+    for (int j = 0; j < P.count; ++j) {
+      const hyrf_remap_array& A = P.a[j];
+      for (int c = 0; c < A.width; ++c) A.dst[(int64_t)k * A.width + c] = A.src[g * A.width + c];
+    }
+  }
+}
+
+static size_t order_ws(int n, Carver& c, uint32_t** ka, uint32_t** kb, int32_t** vb, uint32_t** hist,
+                       uint32_t** totals) {
+  *ka = c.take<uint32_t>(n);
+  *kb = c.take<uint32_t>(n);
+  *vb = c.take<int32_t>(n);
+  *hist = c.take<uint32_t>((size_t)256 * radix_ctas(n));
+  *totals = c.take<uint32_t>(256);
+  c.take<int32_t>(1);  // device count
+  return c.size();
+}
+
 }  // namespace hyrf
+
+using namespace hyrf;
+
+extern "C" size_t hyrf_spatial_order_workspace_size(const hyrf_spatial_order_args* a) {
+  if (!a || a->n < 0) return 0;
+  Carver c(nullptr);
+  uint32_t *ka, *kb, *h, *t;
+  int32_t* vb;
+  return order_ws(a->n, c, &ka, &kb, &vb, &h, &t);
+}
+
+extern "C" hyrf_status hyrf_spatial_order(const hyrf_spatial_order_args* a, void* ws, size_t ws_bytes,
+                                          void* stream) {
+  if (!a || a->n < 0) return HYRF_ERR_INVALID_ARG;
+  if (a->n == 0) return HYRF_OK;
+  if (!a->pos || !a->perm || !ws || ws_bytes < hyrf_spatial_order_workspace_size(a)) return HYRF_ERR_INVALID_ARG;
+  float sx[3];
+  for (int k = 0; k < 3; ++k) {
+    const float e = a->box_hi[k] - a->box_lo[k];
+    if (!(e > 0.0f)) return HYRF_ERR_INVALID_ARG;
+    sx[k] = 2.0f / e;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carver c(ws);
+  uint32_t *ka, *kb, *hist, *totals;
+  int32_t* vb;
+  order_ws(a->n, c, &ka, &kb, &vb, &hist, &totals);
+  // the device count the radix passes read sits at the end of the workspace
+  int32_t* count = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + c.size() - 256);
+  HYRF_LAUNCH("k_set_count", s, k_set_count<<<1, 1, 0, s>>>(count, a->n));
+  int blocks = (a->n + 255) / 256;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  HYRF_LAUNCH("k_morton", s,
+              k_morton<<<blocks, 256, 0, s>>>(a->n, a->pos, make_float3(a->box_lo[0], a->box_lo[1], a->box_lo[2]),
+                                               make_float3(sx[0], sx[1], sx[2]), ka, a->perm));
+  return radix_sort(ka, a->perm, kb, vb, count, a->n, 30, hist, totals, s);
+}
+
+extern "C" hyrf_status hyrf_permute_rows(const int32_t* perm, int32_t n, const hyrf_remap_array* arrays,
+                                         int32_t count, void* stream) {
+  if (n < 0 || count < 0 || count > HYRF_REMAP_MAX || (n > 0 && !perm) || (count > 0 && !arrays))
+    return HYRF_ERR_INVALID_ARG;
+  PermuteArgs P{};
+  for (int j = 0; j < count; ++j) {
+    if (!arrays[j].src || !arrays[j].dst || arrays[j].width < 1 || arrays[j].width > 4 || arrays[j].src == arrays[j].dst)
+      return HYRF_ERR_INVALID_ARG;
+    P.a[j] = arrays[j];
+  }
+  P.count = count;
+  if (n == 0 || count == 0) return HYRF_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int blocks = (n + 255) / 256;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  HYRF_LAUNCH("k_permute_rows", s, k_permute_rows<<<blocks, 256, 0, s>>>(perm, n, P));
+  return HYRF_OK;
+}

@@ -149,7 +149,13 @@ class hyrf_densify_apply_args(C.Structure):
                 ("arrays", hyrf_remap_array * REMAP_MAX)]
 
 
+class hyrf_spatial_order_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("box_lo", C.c_float * 3), ("box_hi", C.c_float * 3),
+                ("perm", _vp)]
+
+
 _ARGS = {
+    "hyrf_spatial_order": hyrf_spatial_order_args,
     "hyrf_densify_plan": hyrf_densify_plan_args,
     "hyrf_query_fields": hyrf_query_fields_args,
     "hyrf_query_fields_backward": hyrf_query_fields_backward_args,
@@ -197,6 +203,8 @@ def lib():
         L.hyrf_densify_stats.restype = C.c_int32
         L.hyrf_densify_apply.argtypes = [C.POINTER(hyrf_densify_apply_args), _vp]
         L.hyrf_densify_apply.restype = C.c_int32
+        L.hyrf_permute_rows.argtypes = [_vp, C.c_int32, C.POINTER(hyrf_remap_array), C.c_int32, _vp]
+        L.hyrf_permute_rows.restype = C.c_int32
         L.hyrf_quantize_grid.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]
         L.hyrf_quantize_grid.restype = C.c_int32
         L.hyrf_reset_opacity.argtypes = [_vp, C.c_int64, C.c_float, _vp, _vp, _vp]
@@ -444,6 +452,25 @@ def hyrf_densify_apply(arrays, stream=None, **kw):
         d.width = 1 if src.dim() == 1 else int(src.shape[1])
         d.kind = int(kind)
     _check("hyrf_densify_apply", lib().hyrf_densify_apply(C.byref(a), stream_handle(stream)))
+
+
+def hyrf_spatial_order(ws=None, stream=None, **kw):
+    """Morton order of the contracted positions: fills perm."""
+    a = hyrf_spatial_order_args()
+    lo, hi = kw.pop("box_lo"), kw.pop("box_hi")
+    a.box_lo[:] = [float(x) for x in lo]
+    a.box_hi[:] = [float(x) for x in hi]
+    return call("hyrf_spatial_order", _fill(a, kw), ws, stream)
+
+
+def hyrf_permute_rows(perm, pairs, stream=None):
+    """dst[k] = src[perm[k]] for every (src, dst) pair of float32 tensors."""
+    arr = (hyrf_remap_array * max(1, len(pairs)))()
+    for d, (src, dst) in zip(arr, pairs):
+        d.src, d.dst = ptr(src), ptr(dst)
+        d.width = 1 if src.dim() == 1 else int(src.shape[1])
+    _check("hyrf_permute_rows", lib().hyrf_permute_rows(ptr(perm), int(perm.numel()), arr, len(pairs),
+                                                        stream_handle(stream)))
 
 
 def hyrf_reset_opacity(alpha_e, max_logit, m=None, v=None, stream=None):

@@ -90,6 +90,26 @@ class DeviceModel:
         s.pe_freq, s.pe_pad = fl.pe_freq, fl.pe_pad
         return s
 
+    def spatial_order(self):
+        """Store the Gaussians in the Morton order of their contracted
+        positions (hyrf_spatial_order; a layout step, the scene is unchanged).
+        Returns perm: new index k holds the Gaussian that was perm[k].
+        Gradient buffers restart from zero; call before building a Trainer."""
+        n, d = self.n, self.device
+        perm = torch.empty(max(n, 1), dtype=torch.int32, device=d)
+        H.hyrf_spatial_order(n=n, pos=self.pos, box_lo=self.fl.box_lo, box_hi=self.fl.box_hi, perm=perm)
+        pairs, new = [], []
+        for name in ("pos", "alpha_e", "scale_e", "color_e"):
+            src = getattr(self, name)
+            dst = torch.empty_like(src)
+            pairs.append((src.view(n, -1), dst.view(n, -1)))
+            new.append((name, dst))
+        H.hyrf_permute_rows(perm[:n], pairs)
+        for name, dst in new:
+            setattr(self, name, dst)
+            self.grad[name] = torch.zeros_like(dst)
+        return perm[:n]
+
     def quantize_u8(self, on=True):
         """Switch the grids to their 8-bit min-max codes (render only; the
         float tables stay and are used again after quantize_u8(False))."""

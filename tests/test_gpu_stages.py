@@ -347,3 +347,22 @@ def test_kernel_timer_counts_each_launch(lib):
     r.forward()                              # disabled: nothing recorded
     torch.cuda.synchronize()
     assert H.hyrf_timer_read() == {}
+
+
+# ------------------------------------------------------------------ storage order
+
+def test_spatial_order_is_a_locality_preserving_permutation(lib):
+    w = synth.config3(n=200_000, width=320, height=240, log2_T=14, n_clusters=64, precision="f32")
+    m = DeviceModel(w)
+    before = np_(m.pos).copy()
+    cols = {k: np_(getattr(m, k)).copy() for k in ("alpha_e", "scale_e", "color_e")}
+    perm = np_(m.spatial_order())
+    torch.cuda.synchronize()
+    n = len(before)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    assert np.array_equal(np_(m.pos), before[perm])
+    for k, v in cols.items():
+        assert np.array_equal(np_(getattr(m, k)), v[perm]), k
+    step_new = np.linalg.norm(np.diff(np_(m.pos), axis=0), axis=1).mean()
+    step_old = np.linalg.norm(np.diff(before, axis=0), axis=1).mean()
+    assert step_new < 0.1 * step_old, (step_new, step_old)
