@@ -36,8 +36,9 @@ def parse():
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-s", type=float, default=15.0)
-    p.add_argument("--layout", default="input", choices=["input", "morton"],
-                   help="storage order of the Gaussians (morton: hyrf_spatial_order once at load)")
+    p.add_argument("--layout", default="morton", choices=["input", "morton"],
+                   help="storage order of the Gaussians: morton = hyrf_spatial_order once at load (a "
+                        "layout step outside the timed region), input = the generator's random order")
     p.add_argument("--ablation", action="store_true",
                    help="render FPS and fwd+bwd it/s of the Tab. 5 ablations on the 360-degree variant")
     return p.parse_args()
