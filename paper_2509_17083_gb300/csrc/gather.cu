@@ -17,9 +17,10 @@
 //
 // A row is a visible Gaussian (position via vis_ids) or a pixel (the hit of
 // its ray with the background sphere, App. A.2). A lane works on one row at a
-// fixed level, so for pixels, whose neighbours are adjacent lanes, runs of
-// lanes hit the same corner at all but the finest levels; the scatter sums
-// each run with shuffles and issues one atomic per run.
+// fixed level, so when neighbouring rows are neighbours in space (pixels of
+// an image row; Gaussians stored in Morton order), runs of lanes hit the
+// same corner at all but the finest levels; the scatter sums each run with
+// shuffles and issues one atomic per run.
 #include "tc_ops.cuh"
 
 namespace hyrf {
@@ -129,9 +130,10 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
                                               float* __restrict__ gtab, float dy[3]) {
   if (WANT_DY) dy[0] = dy[1] = dy[2] = 0.0f;
   // A zero feature gradient adds nothing to the table and nothing to dL/dy
-  // (every term carries d0 or d1): skip the level. Not in COHERENT mode,
-  // whose lanes must all reach the shuffles.
-  if (!COHERENT && d0 == 0.0f && d1 == 0.0f) return;
+  // (every term carries d0 or d1): skip the level; in COHERENT mode, whose
+  // lanes must all reach the shuffles, only when the whole warp may.
+  const bool zero = d0 == 0.0f && d1 == 0.0f;
+  if (COHERENT ? __all_sync(0xffffffffu, zero) : zero) return;
   uint32_t idx[8];
   float f[3];
   level_cell(G, l, y, idx, f);
@@ -145,7 +147,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
       run_atomic(gtab, e, idx[c], g0, g1);
     else if (g0 != 0.0f || g1 != 0.0f)
       atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
-    if (WANT_DY) {
+    if (WANT_DY && !zero) {
       const float2 v = load_entry_t<DT>(G, e);
       const float dot = v.x * d0 + v.y * d1;
       const float wx = (c & 1) ? f[0] : 1.0f - f[0];
@@ -240,8 +242,8 @@ __global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
     const float2 dg = ok ? __ldcs(reinterpret_cast<const float2*>(dXg + o)) : zero;
     const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
     float dy[3], dy2[3];
-    level_scatter<false, true, DT>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
-    level_scatter<false, true, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
+    level_scatter<true, true, DT>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
+    level_scatter<true, true, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
 #pragma unroll
     for (int k = 0; k < 3; ++k) dys[l][lane][k] = dy[k] + dy2[k];
     __syncthreads();

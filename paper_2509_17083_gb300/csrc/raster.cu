@@ -25,31 +25,8 @@ __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
     rec[3 * i] = make_float4(mean2d[2 * i], mean2d[2 * i + 1], conic[3 * i], conic[3 * i + 1]);
     rec[3 * i + 1] = make_float4(conic[3 * i + 2], alpha[i], color[3 * i], color[3 * i + 1]);
-    // Half extents of the box around the ellipse where o G >= 1/255 (beyond
-    // it no pixel passes the alpha test): d^T A d <= tau, tau = 2 ln(255 o),
-    // A = conic; extent sqrt(tau (A^-1)_xx) in x. Widened by 1 % + 1 px so
-    // that no rounding of the per-pixel test can reach outside; infinite
-    // when the conic is not positive definite, negative when o < 1/255.
-    const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2], o = alpha[i];
-    const float det = a * c - b * b;
-    float ex = INFINITY, ey = INFINITY;
-    if (o < 0.99f / 255.0f) {  // alpha = min(0.99, o G) < 1/255 everywhere (G <= 1)
-      ex = ey = -1.0f;
-    } else if (det > 0.0f && a > 0.0f && c > 0.0f) {
-      const float tau = fmaxf(2.0f * logf(255.0f * o), 0.0f);
-      ex = 1.01f * sqrtf(tau * c / det) + 1.0f;
-      ey = 1.01f * sqrtf(tau * a / det) + 1.0f;
-    }
-    rec[3 * i + 2] = make_float4(color[3 * i + 2], ex, ey, 0.0f);
+    rec[3 * i + 2] = make_float4(color[3 * i + 2], 0.0f, 0.0f, 0.0f);
   }
-}
-
-// True if the Gaussian's alpha >= 1/255 box (record r0, r2) misses the
-// pixel-centre block [x0, x1] x [y0, y1]: then it contributes to none of
-// those pixels and the warp skips it.
-__device__ __forceinline__ bool box_misses(const float4& r0, const float4& r2, float x0, float x1, float y0,
-                                           float y1) {
-  return r2.y < 0.0f || r0.x + r2.y < x0 || r0.x - r2.y > x1 || r0.y + r2.z < y0 || r0.y - r2.z > y1;
 }
 
 // exp of the (non-positive) splat exponent with the hardware exponential
@@ -79,8 +56,6 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
   const int py = (tile / TX) * kTile + (t / kTile);
   const bool inside = px < W && py < H;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  // the warp's pixel-centre block: 16 columns x 2 rows
-  const float wx0 = (float)((tile % TX) * kTile) + 0.5f, wy0 = (float)(py & ~1) + 0.5f;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
   float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
   int last = 0;
@@ -103,9 +78,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
     __syncthreads();
     const int cnt = min(256, end - b0);
     for (int j = 0; j < cnt && !done; ++j) {
-      const float4 r0 = s0[j];
-      if (box_misses(r0, s2[j], wx0, wx0 + 15.0f, wy0, wy0 + 1.0f)) continue;  // warp-uniform
-      const float4 r1 = s1[j];
+      const float4 r0 = s0[j], r1 = s1[j];
       const float dx = r0.x - fx, dy = r0.y - fy;
       const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
       if (power > 0.0f) continue;
@@ -250,8 +223,6 @@ __global__ void __launch_bounds__(kBwdRasterThreads) k_raster_bwd(
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int px = (tile % TX) * kTile + (lane & 15);
   const int py = (tile / TX) * kTile + 4 * wp + (lane >> 4);
-  // the warp's pixel-centre block: 16 columns x 4 rows
-  const float bx0 = (float)((tile % TX) * kTile) + 0.5f, by0 = (float)((tile / TX) * kTile + 4 * wp) + 0.5f;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
   PixBack A, Bq;
   pix_init(A, px, py, W, H, T_final, n_contrib, dC, dT);
@@ -282,10 +253,8 @@ __global__ void __launch_bounds__(kBwdRasterThreads) k_raster_bwd(
     __syncthreads();
     for (int j = min(b1, wstop) - b0 - 1; j >= 0; --j) {
       const int pos = b0 - start + j;  // list position
-      const float4 r0 = s0[j], r2 = s2[j];
-      if (box_misses(r0, r2, bx0, bx0 + 15.0f, by0, by0 + 3.0f)) continue;  // warp-uniform
-      const float4 r1 = s1[j];
-      const float cb = r2.x;
+      const float4 r0 = s0[j], r1 = s1[j];
+      const float cb = s2[j].x;
       float acc[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
       const bool ca = pix_step(A, pos, r0, r1, cb, acc);
       const bool cbq = pix_step(Bq, pos, r0, r1, cb, acc);
