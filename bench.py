@@ -204,6 +204,10 @@ def run_ours(args):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                     evs.setdefault(k, []).append(e0)
+            overlap = r._overlap()
+            if overlap:  # background features gathered on the side stream
+                r.side.wait_stream(stream)
+                H.hyrf_gather_background(r._bg_args(), stream=r.side)
             mark("query_fwd")
             H.hyrf_query_fields(ws=r.ws["q"], **r.query_kwargs())
             mark("query_fwd"); mark("project_fwd")
@@ -213,14 +217,19 @@ def run_ours(args):
             mark("bin_sort"); mark("raster_fwd")
             H.call("hyrf_rasterize", r._raster_args(), r.ws["r"])
             mark("raster_fwd"); mark("bg_fwd")
-            H.call("hyrf_composite_background", r._bg_args(), r.ws["b"])
+            bg = r._bg_args()
+            if overlap:
+                stream.wait_stream(r.side)
+                bg.features_ready = 1
+            H.call("hyrf_composite_background", bg, r.ws["b"])
             mark("bg_fwd"); mark("loss")
             r.loss_fn(tgt)
             mark("loss")
             g = m.grads_struct()
             mark("bg_bwd")
             H.hyrf_composite_background_backward(r._bg_args(), ws=r.ws["bb"], d_C=r.dC, d_C_fg=None,
-                                                 d_T_final=r.dT, grads=g, loss_scale=r.loss_scale)
+                                                 d_T_final=r.dT, grads=g, loss_scale=r.loss_scale,
+                                                 scatter_stream=r._side_handle())
             mark("bg_bwd"); mark("raster_bwd")
             H.hyrf_rasterize_backward(r._raster_args(), ws=r.ws["rb"], d_C_fg=r.dC, d_T_final=r.dT,
                                       d_mean2d=r.d_mean2d, d_conic=r.d_conic, d_alpha=r.d_alpha,
@@ -232,6 +241,7 @@ def run_ours(args):
                                     d_quat=r.d_quat, status=r.status)
             mark("project_bwd"); mark("query_bwd")
             H.hyrf_query_fields_backward(ws=r.ws["qb"], **r.query_backward_kwargs())
+            r.join()
             mark("query_bwd")
             return evs
 

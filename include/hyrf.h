@@ -389,9 +389,17 @@ typedef struct {
    * buffer must still hold the forward's values). A forward with
    * bg.tau_T > 0 does not write it. */
   void* features;
+  /* 1: `features` already holds this view's features (filled by
+   * hyrf_gather_background, e.g. on another stream while the foreground is
+   * rendered): the forward skips its gather. */
+  int32_t features_ready;
 } hyrf_composite_background_args;
 
 size_t hyrf_composite_background_workspace_size(const hyrf_composite_background_args* a);
+/* The radiance hash features of every pixel's sphere hit into a->features
+ * (mode 0, BF16 fields, tau_T = 0): the gather of hyrf_composite_background,
+ * callable ahead of it (it reads neither C_fg nor T_final). */
+hyrf_status hyrf_gather_background(const hyrf_composite_background_args* a, void* stream);
 hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, void* workspace,
                                       size_t ws_bytes, void* stream);
 
@@ -405,6 +413,12 @@ typedef struct {
   float* d_T_final;          /* out [H][W] */
   hyrf_field_grads grads;    /* accumulate */
   float loss_scale;
+  /* Optional (BF16 exact mode): a second stream for the radiance-table
+   * gradient scatter, which then runs after this call's decoder work (an
+   * event orders it) and concurrently with whatever the caller issues next
+   * on `stream`. The caller must order its use of grads.rad_table after
+   * scatter_stream (e.g. make `stream` wait on it). */
+  void* scatter_stream;
 } hyrf_composite_background_backward_args;
 
 size_t hyrf_composite_background_backward_workspace_size(

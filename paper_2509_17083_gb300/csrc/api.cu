@@ -23,6 +23,7 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
 hyrf_status launch_query_explicit(const hyrf_query_fields_args& a, cudaStream_t s);
 hyrf_status launch_query_explicit_bwd(const hyrf_query_fields_backward_args& a, cudaStream_t s);
 hyrf_status launch_bg_none(const hyrf_composite_background_args& a, cudaStream_t s);
+hyrf_status launch_bg_gather(const hyrf_composite_background_args& a, const FieldsDev& F, cudaStream_t s);
 hyrf_status launch_bg_none_bwd(const hyrf_composite_background_backward_args& b, cudaStream_t s);
 size_t tc_fwd_feature_bytes(int64_t rows, int fields);
 size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features);
@@ -50,6 +51,32 @@ hyrf_status launch_loss(const hyrf_loss_args& a, void* ws, cudaStream_t s);
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- stream forks
+hyrf_status fork_stream(cudaStream_t before, cudaStream_t after) {
+  constexpr int kPool = 64;
+  static std::mutex mu;
+  static cudaEvent_t pool[64][kPool];
+  static int next[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HYRF_ERR_CUDA;
+  cudaEvent_t ev;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cudaEvent_t& slot = pool[dev][next[dev]];
+    if (!slot && cudaEventCreateWithFlags(&slot, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return HYRF_ERR_CUDA;
+    }
+    ev = slot;
+    next[dev] = (next[dev] + 1) % kPool;
+  }
+  if (cudaEventRecord(ev, before) != cudaSuccess || cudaStreamWaitEvent(after, ev, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return HYRF_ERR_CUDA;
+  }
+  return HYRF_OK;
+}
 
 // ---------------------------------------------------------------- kernel timer
 namespace {
@@ -354,6 +381,14 @@ hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, v
   if (!bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (a->bg.mode == 0 && F.cm.bf16) return launch_bg_exact_fwd_tc(*a, F, ws, S(stream));
   return launch_bg_fwd(*a, F, ws, S(stream));
+}
+
+hyrf_status hyrf_gather_background(const hyrf_composite_background_args* a, void* stream) {
+  FieldsDev F;
+  hyrf_status st = bg_check(a, F);
+  if (st != HYRF_OK) return st;
+  if (a->bg.mode != 0 || !F.cm.bf16 || !a->features || a->bg.tau_T > 0.0f) return HYRF_ERR_INVALID_ARG;
+  return launch_bg_gather(*a, F, S(stream));
 }
 
 size_t hyrf_composite_background_backward_workspace_size(

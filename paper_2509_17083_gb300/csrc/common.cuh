@@ -99,6 +99,11 @@ struct Carver {
 
 int num_sms();
 
+// Order `after` behind the work issued so far on `before` (an event from a
+// small library pool, recorded on `before`, waited on by `after`); works
+// during CUDA graph capture, where it forks `after` into the graph.
+hyrf_status fork_stream(cudaStream_t before, cudaStream_t after);
+
 // Raise a kernel's dynamic shared-memory limit once per device: the
 // attribute persists, so later calls (for instance during CUDA graph
 // capture) make no API call.

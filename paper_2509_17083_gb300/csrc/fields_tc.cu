@@ -385,6 +385,12 @@ size_t tc_bg_fwd_workspace(int64_t P, bool have_features, bool skip) {
   return c.size();
 }
 
+hyrf_status launch_bg_gather(const hyrf_composite_background_args& a, const FieldsDev& F, cudaStream_t s) {
+  const CamDev cam = to_dev(a.cam);
+  const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
+  return launch_gather(F, cam, RS, cam.W * cam.H, nullptr, static_cast<uint32_t*>(a.features), s);
+}
+
 hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
                                    cudaStream_t s) {
   const CamDev cam = to_dev(a.cam);
@@ -406,7 +412,8 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
                 k_bg_select<<<blocks, 256, 0, s>>>(P, a.bg.tau_T, a.T_final, a.C_fg, a.C, list, count));
   }
   const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, list, count};
-  hyrf_status st = launch_gather(F, cam, RS, P, nullptr, Xb, s);
+  const bool ready = a.features && a.features_ready && !skip;  // gathered ahead (hyrf_gather_background)
+  hyrf_status st = ready ? HYRF_OK : launch_gather(F, cam, RS, P, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
   set_smem_limit<tc::k_bg_exact_fwd_tc>(tc::kBgSmem);
   int tiles = (P + 127) / 128;

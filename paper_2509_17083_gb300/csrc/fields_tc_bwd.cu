@@ -641,9 +641,18 @@ hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, c
   tc::PixelP P{a.bg.radius, a.T_final, b.d_C, Xb, dXb, b.d_C_fg, b.d_T_final};
   st = launch_dec_bwd<tc::BgPixel>(P, F, cam, b.loss_scale, SL, slabs, a.status, s);
   if (st != HYRF_OK) return st;
-  st = launch_scatter(F, cam, RS, P_, nullptr, dXb, nullptr, b.grads.rad_table, nullptr, s);
+  // decoder gradients first (a plain read-modify-write of the caller's
+  // buffers, kept on the caller's stream); the table scatter (atomics only)
+  // may then run on the caller's second stream
+  st = launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
   if (st != HYRF_OK) return st;
-  return launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
+  cudaStream_t ss = s;
+  if (b.scatter_stream) {
+    ss = static_cast<cudaStream_t>(b.scatter_stream);
+    st = fork_stream(s, ss);
+    if (st != HYRF_OK) return st;
+  }
+  return launch_scatter(F, cam, RS, P_, nullptr, dXb, nullptr, b.grads.rad_table, nullptr, ss);
 }
 
 }  // namespace hyrf

@@ -110,12 +110,14 @@ class hyrf_background(C.Structure):
 
 class hyrf_composite_background_args(C.Structure):
     _fields_ = [("cam", hyrf_camera), ("fields", hyrf_fields), ("bg", hyrf_background),
-                ("C_fg", _vp), ("T_final", _vp), ("C", _vp), ("status", _vp), ("features", _vp)]
+                ("C_fg", _vp), ("T_final", _vp), ("C", _vp), ("status", _vp), ("features", _vp),
+                ("features_ready", C.c_int32)]
 
 
 class hyrf_composite_background_backward_args(C.Structure):
     _fields_ = [("fwd", hyrf_composite_background_args), ("d_C", _vp), ("d_C_fg", _vp),
-                ("d_T_final", _vp), ("grads", hyrf_field_grads), ("loss_scale", C.c_float)]
+                ("d_T_final", _vp), ("grads", hyrf_field_grads), ("loss_scale", C.c_float),
+                ("scatter_stream", _vp)]
 
 
 class hyrf_loss_args(C.Structure):
@@ -203,6 +205,8 @@ def lib():
         L.hyrf_densify_stats.restype = C.c_int32
         L.hyrf_densify_apply.argtypes = [C.POINTER(hyrf_densify_apply_args), _vp]
         L.hyrf_densify_apply.restype = C.c_int32
+        L.hyrf_gather_background.argtypes = [C.POINTER(hyrf_composite_background_args), _vp]
+        L.hyrf_gather_background.restype = C.c_int32
         L.hyrf_permute_rows.argtypes = [_vp, C.c_int32, C.POINTER(hyrf_remap_array), C.c_int32, _vp]
         L.hyrf_permute_rows.restype = C.c_int32
         L.hyrf_quantize_grid.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]
@@ -461,6 +465,12 @@ def hyrf_spatial_order(ws=None, stream=None, **kw):
     a.box_lo[:] = [float(x) for x in lo]
     a.box_hi[:] = [float(x) for x in hi]
     return call("hyrf_spatial_order", _fill(a, kw), ws, stream)
+
+
+def hyrf_gather_background(args, stream=None):
+    """Fill args.features with the background hash features (ahead of
+    hyrf_composite_background with features_ready = 1)."""
+    _check("hyrf_gather_background", lib().hyrf_gather_background(C.byref(args), stream_handle(stream)))
 
 
 def hyrf_permute_rows(perm, pairs, stream=None):

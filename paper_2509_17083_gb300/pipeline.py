@@ -192,6 +192,9 @@ class ViewRenderer:
             raise ValueError("save_features needs BF16 fields")
         self.save_features = bool(save_features)
         self.feat_q = self.feat_b = None
+        # second stream: the background's feature gather ahead of the
+        # foreground, and its table-gradient scatter behind it
+        self.side = torch.cuda.Stream(device=d) if str(d).startswith("cuda") else None
         if self.save_features:
             self.feat_q = torch.empty(2 * max(n, 1) * 32, dtype=torch.bfloat16, device=d)
             if int(bg.mode) == 0 and self.background:
@@ -232,6 +235,9 @@ class ViewRenderer:
                         features=self.feat_b))
         return a
 
+    def _side_handle(self):
+        return self.side.cuda_stream if self._overlap() else None
+
     def query_kwargs(self):
         """Arguments of hyrf_query_fields for this view."""
         m = self.m
@@ -255,14 +261,28 @@ class ViewRenderer:
                     loss_scale=self.loss_scale, status=self.status, features=self.feat_q,
                     explicit_only=0 if self.neural else 1)
 
+    def _overlap(self, tau_T=0.0):
+        """The background features can be gathered on the side stream."""
+        return self.feat_b is not None and self.side is not None and tau_T == 0.0
+
     def forward(self, target=None, want_keys=True, tau_T=0.0):
         """The forward path; tau_T > 0 (render only) queries the background
-        only where T_final >= tau_T."""
+        only where T_final >= tau_T. The background's feature gather runs on
+        the side stream while the foreground is rendered."""
+        main = torch.cuda.current_stream() if self.side is not None else None
+        overlap = self._overlap(tau_T)
+        if overlap:
+            self.side.wait_stream(main)  # after earlier updates of the tables
+            H.hyrf_gather_background(self._bg_args(), stream=self.side)
         H.hyrf_query_fields(ws=self.ws["q"], **self.query_kwargs())
         self.project()
         self.bin_sort(want_keys)
         H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
-        H.call("hyrf_composite_background", self._bg_args(tau_T), self.ws["b"])
+        bg = self._bg_args(tau_T)
+        if overlap:
+            main.wait_stream(self.side)
+            bg.features_ready = 1
+        H.call("hyrf_composite_background", bg, self.ws["b"])
         if target is not None:
             self.loss_fn(target)
         return self.C
@@ -290,6 +310,13 @@ class ViewRenderer:
         """Reverse of every stage; dL/dC must be in self.dC. Adds into model.grad."""
         self.backward_render()
         self.backward_fields()
+        self.join()
+
+    def join(self):
+        """Order the caller's stream after the side stream's work (the
+        background table scatter of backward_render)."""
+        if self.side is not None:
+            torch.cuda.current_stream().wait_stream(self.side)
 
     def backward_render(self):
         """Reverse of background, compositing and projection: fills the
@@ -301,7 +328,8 @@ class ViewRenderer:
         g = m.grads_struct()
         H.hyrf_composite_background_backward(self._bg_args(), ws=self.ws["bb"], d_C=self.dC,
                                              d_C_fg=None, d_T_final=self.dT, grads=g,
-                                             loss_scale=self.loss_scale)
+                                             loss_scale=self.loss_scale,
+                                             scatter_stream=self._side_handle())
         H.hyrf_rasterize_backward(self._raster_args(), ws=self.ws["rb"], d_C_fg=self.dC,
                                   d_T_final=self.dT, d_mean2d=self.d_mean2d, d_conic=self.d_conic,
                                   d_alpha=self.d_alpha, d_color=self.d_color)
