@@ -87,8 +87,11 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
                                                        const uint32_t* __restrict__ totals) {
   __shared__ uint32_t base[256];
   __shared__ uint32_t sub_total[256];
+  __shared__ uint32_t lstart[256];   // digit starts within the sub-tile
   __shared__ uint32_t whist[8][256];
   __shared__ uint32_t wsum[8];
+  __shared__ uint32_t sk[kSub];      // the sub-tile in digit order
+  __shared__ int32_t sv[kSub];
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int lane = t & 31, w = t >> 5;
   // digit base = exclusive scan of the digit totals + this CTA's column prefix
@@ -134,6 +137,7 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
       __syncwarp();
     }
     __syncthreads();
+    uint32_t tot;
     {
       uint32_t run = 0;
 #pragma unroll
@@ -143,14 +147,41 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
         run += c;
       }
       sub_total[t] = run;
+      tot = run;
+    }
+    // exclusive scan of the digit counts: where each digit starts in the
+    // sub-tile
+    {
+      uint32_t x = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) wsum[w] = x;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int j = 0; j < w; ++j) before += wsum[j];
+      lstart[t] = before + x - tot;
     }
     __syncthreads();
+    // stage the sub-tile in digit order, then write each digit's run to
+    // consecutive global positions (coalesced)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (!valid[r]) continue;
-      const uint32_t pos = base[dig[r]] + whist[w][dig[r]] + rank[r];
-      keys_out[pos] = key[r];
-      vals_out[pos] = val[r];
+      const uint32_t lp = lstart[dig[r]] + whist[w][dig[r]] + rank[r];
+      sk[lp] = key[r];
+      sv[lp] = val[r];
+    }
+    __syncthreads();
+    const int cnt = (int)((end - sub) < kSub ? (end - sub) : kSub);
+    for (int i = t; i < cnt; i += kRT) {
+      const uint32_t k = sk[i];
+      const uint32_t d = (k >> shift) & mask;
+      const uint32_t pos = base[d] + ((uint32_t)i - lstart[d]);
+      keys_out[pos] = k;
+      vals_out[pos] = sv[i];
     }
     __syncthreads();
     base[t] += sub_total[t];
@@ -427,7 +458,7 @@ size_t bin_sort_workspace(int n, int64_t cap) {
 // count is even and in (kb, vb) when it is odd.
 static hyrf_status radix_sort(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* vb,
                               const int32_t* n_ptr, int cap, int nbits, uint32_t* hist,
-                              uint32_t* totals, cudaStream_t s) {
+                              uint32_t* totals, cudaStream_t s, const char* name = "k_radix_scatter") {
   const int G = radix_ctas(cap);
   const int passes = (nbits + 7) / 8;
   uint32_t* src_k = (passes & 1) ? kb : ka;
@@ -442,7 +473,7 @@ static hyrf_status radix_sort(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* 
                 k_radix_hist<<<G, kRT, 0, s>>>(src_k, n_ptr, cap, shift, mask, hist));
     HYRF_LAUNCH("k_radix_colscan", s,
                 k_radix_colscan<<<256, kRT, 0, s>>>(hist, G, totals));
-    HYRF_LAUNCH("k_radix_scatter", s,
+    HYRF_LAUNCH(name, s,
                 k_radix_scatter<<<G, kRT, 0, s>>>(src_k, src_v, dst_k, dst_v, n_ptr, cap, shift, mask, hist,
                                       totals));
     uint32_t* tk = src_k;
@@ -470,7 +501,8 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   const int eb = (n + 255) / 256 < num_sms() * 8 ? (n + 255) / 256 : num_sms() * 8;
   HYRF_LAUNCH("k_depth_keys", s,
               k_depth_keys<<<eb, 256, 0, s>>>(a.depth, a.n_vis, n, w.dk_a, w.dv_a));
-  hyrf_status st = radix_sort(w.dk_a, w.dv_a, w.dk_b, w.dv_b, a.n_vis, n, 32, w.hist, w.totals, s);
+  hyrf_status st = radix_sort(w.dk_a, w.dv_a, w.dk_b, w.dv_b, a.n_vis, n, 32, w.hist, w.totals, s,
+                              "k_radix_scatter<depth>");
   if (st != HYRF_OK) return st;
   // 2. instance offsets in depth order, K, and emission
   const int sc = (n + kScanChunk - 1) / kScanChunk;
@@ -490,7 +522,8 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
               k_expand<<<(int)(xb < 0x7fffffff ? xb : 0x7fffffff), 256, 0, s>>>(
                   a.rect, w.dv_a, a.n_vis, n, w.off, a.n_instances, capi, a.tiles_x, emit_k, emit_v));
   // 3. stable sort of the instances on their tile bits
-  st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s);
+  st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s,
+                  "k_radix_scatter<tile>");
   if (st != HYRF_OK) return st;
   // 4. per-tile ranges and (optionally) the composed 64-bit keys
   const int kb = (int)((cap + 255) / 256 < num_sms() * 8 ? (cap + 255) / 256 : num_sms() * 8);
