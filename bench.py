@@ -39,6 +39,9 @@ def parse():
     p.add_argument("--layout", default="morton", choices=["input", "morton"],
                    help="storage order of the Gaussians: morton = hyrf_spatial_order once at load (a "
                         "layout step outside the timed region), input = the generator's random order")
+    p.add_argument("--config", type=int, default=3, choices=[3, 4, 5],
+                   help="3: the headline line; 4: 8-view step as one CUDA graph (3M Gaussians, memory "
+                        "saved vs recompute); 5: 6M Gaussians at 1920x1080 with 1%% degenerate ones")
     p.add_argument("--ablation", action="store_true",
                    help="render FPS and fwd+bwd it/s of the Tab. 5 ablations on the 360-degree variant")
     return p.parse_args()
@@ -407,7 +410,10 @@ def run_ours(args):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload; an entry is removed when
 # the kernel changes after its capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/kernels_config3_bf16.md: 37.3 MB read + 0.007 MB written
+    ("k_raster_bwd", "bf16"): 37_310_000,
+}
 
 
 def roofline(R, peaks, prec):
@@ -429,6 +435,97 @@ def roofline(R, peaks, prec):
             "unit": "GB/s", "frac": round(gbs / hbm, 4) if gbs else None,
             "traffic": tr, "algorithmic_bytes": work, "avg_launch_ms": round(avg_ms, 4),
             "peak_source": src}
+
+
+# ---------------------------------------------------------------- configs 4 and 5
+
+def run_config(args):
+    import torch
+    from paper_2509_17083_gb300 import hyrf as H
+    from paper_2509_17083_gb300 import synth
+    from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer, shared_workspaces
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    H.lib()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    steps = max(3, args.steps // 10)
+
+    def timed(fn, k):
+        for _ in range(max(3, args.warmup // 5)):
+            fn()
+        ms = []
+        for _ in range(k):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+
+    if args.config == 5:
+        w = synth.config5()
+        m = DeviceModel(w)
+        m.spatial_order()
+        r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+        tgt = torch.as_tensor(w.targets[0]).cuda()
+        r.fit_capacity(tgt)
+
+        def step():
+            m.zero_grad()
+            r.step(tgt)
+        ms = timed(step, steps)
+        fwd = timed(lambda: r.forward(None, want_keys=False), steps)
+        tau = timed(lambda: r.forward(None, want_keys=False, tau_T=0.2), steps)
+        out = {"metric": "fwd+bwd iters/s & render FPS, 6M Gaussians @1920x1080, BF16 fields", "value": round(1000 / ms, 3),
+               "unit": "iters/s", "ms_per_step": round(ms, 3), "render_fps": round(1000 / fwd, 2),
+               "render_fps_tau_T_0.2": round(1000 / tau, 2), "visible": int(r.n_vis.item()),
+               "instances": int(r.n_inst.item()), "status": H.read_status(r.status),
+               "config": {"workload": "config5: 6M Gaussians (40 % beyond depth 50), 1920x1080, 2^22 grids",
+                          "layout": "morton", "steps": steps}}
+        print(json.dumps(out))
+        return
+    # config 4: 8 views, one CUDA graph per step; saved features vs recompute
+    res = {}
+    for save in (True, False):
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats()
+        w = synth.config4()
+        m = DeviceModel(w)
+        m.spatial_order()
+        ws = shared_workspaces()
+        views = []
+        for cam, t in zip(w.cams, w.targets):
+            r = ViewRenderer(m, cam, w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale, save_features=save,
+                             workspaces=ws)
+            tt = torch.as_tensor(t).cuda()
+            r.fit_capacity(tt)
+            views.append((r, tt))
+
+        def step():
+            m.zero_grad()
+            for r, tt in views:
+                r.step(tt)
+        step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        ms = timed(g.replay, steps)
+        res["saved" if save else "recompute"] = dict(ms_per_step=round(ms, 3), views_per_s=round(8000 / ms, 2),
+                                                     peak_gib=round(torch.cuda.max_memory_allocated() / 2**30, 2))
+        del g, views, m
+    print(json.dumps({"metric": "8-view fwd+bwd step as one CUDA graph, 3M Gaussians @1297x840, BF16 fields",
+                      "value": res["saved"]["views_per_s"], "unit": "views/s",
+                      "config": {"workload": "config4: 3M Gaussians in a radius-2 ball, 8 ring cameras, 2^21 grids",
+                                 "layout": "morton", "steps": steps},
+                      "features": res}))
 
 
 # ---------------------------------------------------------------- ablations (Tab. 5)
@@ -612,5 +709,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.ablation:
         run_ablation(a)
+    elif a.config != 3:
+        run_config(a)
     else:
         run_ours(a)
