@@ -47,6 +47,22 @@ def parse():
     return p.parse_args()
 
 
+def replica_max(x, device="cpu"):
+    """The maximum of x over the ranks of the default process group (the
+    slowest replica sets the step time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ms_per_step, n_replicas):
+    """Iterations per second of the whole job: every replica runs its own
+    view, all finish within the slowest one's step time."""
+    return n_replicas * 1000.0 / ms_per_step
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -287,9 +303,7 @@ def run_ours(args):
         K = int(r.n_inst.item())
         ms = float(np.mean(step_ms))
         if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = replica_max(ms, dev)
         # render-only (forward, no backward), same flush protocol
         fwd_ms = []
         for _ in range(max(3, args.steps // 2)):
@@ -362,7 +376,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
     head = "bf16" if "bf16" in results and "ms" in results["bf16"] else "f32"
     R = results[head]
-    value = ws * 1000.0 / R["ms"]
+    value = whole_job_rate(R["ms"], ws)
     roof = roofline(R, peaks, head)
     per_step = {k: n * t for k, (n, t) in R["kernels"].items()}
     tot = sum(per_step.values()) or 1.0
