@@ -314,8 +314,10 @@ class ViewRenderer:
 
     def join(self):
         """Order the caller's stream after the side stream's work (the
-        background table scatter of backward_render)."""
-        if self.side is not None:
+        background table scatter of backward_render). Only when the side
+        stream is in use: waiting on an idle stream would, during CUDA graph
+        capture, depend on work outside the graph."""
+        if self._overlap():
             torch.cuda.current_stream().wait_stream(self.side)
 
     def backward_render(self):

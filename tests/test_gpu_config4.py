@@ -122,3 +122,22 @@ def test_saved_features_against_recompute_memory_and_gradients():
     assert peak_re < peak_save
     for k, v in g_save.items():
         assert rel_l2(g_re[k], v) < ORDER_TOL, k
+
+
+def test_recompute_views_capture_as_one_cuda_graph():
+    """Without saved features the views use no second stream; the step still
+    captures (a join on an idle stream would break the capture)."""
+    w, m, views = _setup(False, n=200_000)
+    _step(m, views)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            _step(m, views)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    for r, _ in views:
+        assert H.read_status(r.status) == 0
