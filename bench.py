@@ -341,6 +341,27 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 u8_ms.append(e0.elapsed_time(e1))
             m.quantize_u8(False)
+        # the IEEE-half render path (f16 grids and decoders), same scene
+        f16_ms = []
+        if prec == "bf16":
+            wf = synth.config3(n=args.n, precision="f16", seed=local)
+            mf = DeviceModel(wf, device=dev)
+            if args.layout == "morton":
+                mf.spatial_order()
+            rf = ViewRenderer(mf, wf.cams[0], wf.bg)
+            rf.fit_capacity()
+            for _ in range(3):
+                rf.forward(None, want_keys=False)
+            for _ in range(max(3, args.steps // 2)):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rf.forward(None, want_keys=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                f16_ms.append(e0.elapsed_time(e1))
+            del rf, mf
         # end to end through the C ABI with host buffers: target H2D, loss D2H per step
         pinned = torch.as_tensor(w.targets[0]).pin_memory()
         dev_tgt = torch.empty_like(tgt)
@@ -365,6 +386,7 @@ def run_ours(args):
         results[prec] = dict(ms=ms, fwd_ms=float(np.mean(fwd_ms)), e2e_ms=float(np.mean(e2e_ms)),
                              tau_ms=float(np.mean(tau_ms)) if tau_ms else None,
                              u8_ms=float(np.mean(u8_ms)) if u8_ms else None,
+                             f16_ms=float(np.mean(f16_ms)) if f16_ms else None,
                              stage_ms=stage_ms, launches_per_step=launches / args.steps,
                              n_vis=nv, instances=K, status=st, clocks=clocks, wall_s=t_wall,
                              loss=float(r.loss.item()),
@@ -395,6 +417,7 @@ def run_ours(args):
            "render_fps": round(ws * 1000.0 / R["fwd_ms"], 2),
            "render_fps_tau_T_0.2": round(ws * 1000.0 / R["tau_ms"], 2) if R.get("tau_ms") else None,
            "render_fps_u8_grids": round(ws * 1000.0 / R["u8_ms"], 2) if R.get("u8_ms") else None,
+           "render_fps_f16_fields": round(ws * 1000.0 / R["f16_ms"], 2) if R.get("f16_ms") else None,
            "stage_ms": {k: round(v, 4) for k, v in R["stage_ms"].items()},
            "kernels": kern,
            "psnr_db": round(R["psnr"], 4),

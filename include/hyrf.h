@@ -55,7 +55,9 @@ typedef enum {
   HYRF_ERR_TIMEOUT = 32,  /* device: a bounded wait on a tensor-core completion gave up */
 } hyrf_status;
 
-typedef enum { HYRF_F32 = 0, HYRF_BF16 = 1, HYRF_U8 = 2 } hyrf_dtype;
+/* HYRF_F16 (grids and decoder weights; render only, the real-time path of
+ * the paper's speed claims): IEEE half instead of bfloat16 operands. */
+typedef enum { HYRF_F32 = 0, HYRF_BF16 = 1, HYRF_U8 = 2, HYRF_F16 = 3 } hyrf_dtype;
 
 /* Pinhole camera, world to camera x_c = R x_w + t (Eq. 8). Pixel (i, j)
  * samples the image plane at (i + 0.5, j + 0.5); u = fx x_c/z_c + cx.
@@ -563,7 +565,7 @@ hyrf_status hyrf_reset_opacity(float* alpha_e, int64_t n, float max_logit, float
  * compressed model quantises the grids). Per level l over its T x 2 values:
  * lo = min, hi = max, step = (hi - lo) / 255 (float), code = rint((x - lo)
  * / step) clamped to [0, 255] (0 when step = 0). table: [n_levels][T][2]
- * float32 (dtype HYRF_F32) or bf16 (HYRF_BF16); codes [n_levels][T][2]
+ * float32, bf16 or f16 (dtype); codes [n_levels][T][2]
  * uint8 out; qparams [n_levels][2] float32 out. */
 hyrf_status hyrf_quantize_grid(const void* table, int32_t dtype, int32_t n_levels, int32_t log2_T,
                                uint8_t* codes, float* qparams, void* stream);

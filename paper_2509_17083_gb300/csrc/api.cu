@@ -170,7 +170,7 @@ static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 
 // bf16 decoder weights are staged with 16-byte vector loads
 static bool bf16_weights_ok(const hyrf_mlp& m) {
-  if (m.dtype != HYRF_BF16) return true;
+  if (m.dtype != HYRF_BF16 && m.dtype != HYRF_F16) return true;
   for (int l = 0; l <= m.n_hidden && l < 3; ++l)
     if (!aligned(m.W[l], 16)) return false;
   return true;
@@ -214,8 +214,11 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
     return HYRF_ERR_UNSUPPORTED;
-  // both grids of one type; 8-bit codes only with the tensor-core decoders
-  if (F.geo.bf16 != F.rad.bf16 || F.geo.u8 != F.rad.u8 || (F.rad.u8 && !F.cm.bf16)) return HYRF_ERR_UNSUPPORTED;
+  // both grids of one type; 8-bit codes only with the tensor-core decoders;
+  // f16 decoders with f16 or 8-bit grids, f16 grids only with f16 decoders
+  if (F.geo.bf16 != F.rad.bf16 || F.geo.u8 != F.rad.u8 || F.geo.f16 != F.rad.f16 || F.gm.f16 != F.cm.f16 ||
+      (F.rad.u8 && !F.cm.bf16) || (F.cm.f16 && !(F.rad.f16 || F.rad.u8)) || (F.rad.f16 && !F.cm.f16))
+    return HYRF_ERR_UNSUPPORTED;
   if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (a->features && (!F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
@@ -240,7 +243,7 @@ hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a,
   if (a->explicit_only) return launch_query_explicit_bwd(*a, S(stream));
   FieldsDev F;
   if (!make_fields(a->fields, F, true)) return HYRF_ERR_UNSUPPORTED;
-  if (F.geo.u8 || F.rad.u8) return HYRF_ERR_UNSUPPORTED;  // the 8-bit codec renders only
+  if (F.geo.u8 || F.rad.u8 || F.rad.f16 || F.cm.f16) return HYRF_ERR_UNSUPPORTED;  // render-only types
   if (F.gm.bf16 != F.cm.bf16 || (F.cm.bf16 && a->fields.rad.n_levels != 16))
     return HYRF_ERR_UNSUPPORTED;
   if (!ws_ok(ws, ws_bytes, hyrf_query_fields_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
@@ -358,6 +361,8 @@ static hyrf_status bg_check(const hyrf_composite_background_args* a, FieldsDev& 
   if (!make_fields(a->fields, F, false)) return HYRF_ERR_UNSUPPORTED;
   if (F.cm.bf16 && a->fields.rad.n_levels != 16) return HYRF_ERR_UNSUPPORTED;
   if (F.rad.u8 && (!F.cm.bf16 || a->bg.mode != 0)) return HYRF_ERR_UNSUPPORTED;
+  if ((F.cm.f16 && (a->bg.mode != 0 || !(F.rad.f16 || F.rad.u8))) || (F.rad.f16 && !F.cm.f16))
+    return HYRF_ERR_UNSUPPORTED;
   if (a->features && (a->bg.mode != 0 || !F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
   if (!(a->bg.tau_T >= 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (a->bg.tau_T > 0.0f && (a->bg.mode != 0 || !F.cm.bf16)) return HYRF_ERR_UNSUPPORTED;
@@ -408,7 +413,7 @@ hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_b
   if (!b->d_C || !b->d_T_final || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (b->fwd.bg.mode == 2) return launch_bg_none_bwd(*b, S(stream));
   if (b->fwd.bg.tau_T > 0.0f) return HYRF_ERR_INVALID_ARG;  // render-only rule
-  if (F.rad.u8) return HYRF_ERR_UNSUPPORTED;                 // the 8-bit codec renders only
+  if (F.rad.u8 || F.rad.f16 || F.cm.f16) return HYRF_ERR_UNSUPPORTED;  // render-only types
   if (!ws_ok(ws, ws_bytes, bg_workspace(b->fwd, F, true))) return HYRF_ERR_INVALID_ARG;
   if (!bf16_weights_ok(b->fwd.fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (b->fwd.bg.mode == 0 && F.cm.bf16) return launch_bg_bwd_tc(*b, F, ws, S(stream));

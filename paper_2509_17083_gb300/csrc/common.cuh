@@ -2,6 +2,7 @@
 #pragma once
 #include <atomic>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +24,7 @@ struct GridDev {
   uint32_t dense;      // bit l: level l is stored densely
   int L;
   int bf16;
+  int f16;
   int u8;              // uint8 codes with per-level (lo, step) in q
   int log2T;
   const float* q;
@@ -34,7 +36,8 @@ struct MlpDev {
   const void* W[3];
   const float* b[3];
   int n_in, width, n_hidden, n_out;
-  int bf16;
+  int bf16;            // 16-bit weights: bf16, or f16 when f16 is set (render only)
+  int f16;
 };
 
 struct FieldsDev {

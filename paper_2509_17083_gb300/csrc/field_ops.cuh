@@ -81,10 +81,12 @@ __device__ __forceinline__ float corner_w(const float f[3], int c) {
 }
 
 // Entry e of a table whose type is known at compile time: 0 float32,
-// 1 bf16, 2 uint8 codes (value = lo + step * code, per level).
+// 1 bf16, 2 uint8 codes (value = lo + step * code, per level), 3 f16.
 template <int DT>
 __device__ __forceinline__ float2 load_entry_t(const GridDev& G, size_t e) {
-  if constexpr (DT == 2) {
+  if constexpr (DT == 3) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(G.table) + e));
+  } else if constexpr (DT == 2) {
     const uchar2 c = __ldg(reinterpret_cast<const uchar2*>(G.table) + e);
     const float2 q = __ldg(reinterpret_cast<const float2*>(G.q) + (e >> G.log2T));
     return make_float2(fmaf(q.y, (float)c.x, q.x), fmaf(q.y, (float)c.y, q.x));

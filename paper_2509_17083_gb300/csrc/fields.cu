@@ -601,7 +601,7 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
     }
     if (!g.table || g.n_levels < 1 || g.n_levels > kMaxLevels || g.n_feat != 2 || g.log2_T < 4 ||
         g.log2_T > 26 || g.base_res < 1 || !(g.growth >= 1.0f) ||
-        (g.dtype != HYRF_F32 && g.dtype != HYRF_BF16 && g.dtype != HYRF_U8) ||
+        (g.dtype != HYRF_F32 && g.dtype != HYRF_BF16 && g.dtype != HYRF_U8 && g.dtype != HYRF_F16) ||
         (g.dtype == HYRF_U8 && !g.qparams))
       return false;
     GridDev& o = *gd[k];
@@ -610,6 +610,7 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
     o.T = 1u << g.log2_T;
     o.mask = o.T - 1u;
     o.bf16 = g.dtype == HYRF_BF16;
+    o.f16 = g.dtype == HYRF_F16;
     o.u8 = g.dtype == HYRF_U8;
     o.q = g.qparams;
     o.log2T = g.log2_T;
@@ -639,7 +640,7 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
     if (!((m.n_hidden == 1 && m.width == 32) || (m.n_hidden == 2 && m.width == 64))) return false;
     for (int l = 0; l <= m.n_hidden; ++l)
       if (!m.W[l] || !m.b[l]) return false;
-    if (m.dtype != HYRF_F32 && m.dtype != HYRF_BF16) return false;
+    if (m.dtype != HYRF_F32 && m.dtype != HYRF_BF16 && m.dtype != HYRF_F16) return false;
     MlpDev& o = *md[k];
     for (int l = 0; l < 3; ++l) {
       o.W[l] = l <= m.n_hidden ? m.W[l] : nullptr;
@@ -649,7 +650,8 @@ bool make_fields(const hyrf_fields& f, FieldsDev& d, bool need_geo) {
     o.width = m.width;
     o.n_hidden = m.n_hidden;
     o.n_out = m.n_out;
-    o.bf16 = m.dtype == HYRF_BF16;
+    o.bf16 = m.dtype == HYRF_BF16 || m.dtype == HYRF_F16;  // 16-bit: the tensor-core path
+    o.f16 = m.dtype == HYRF_F16;
   }
   if (f.pe_freq != kPEFreq || f.pe_pad != kPEPad) return false;
   const int L = f.rad.n_levels;

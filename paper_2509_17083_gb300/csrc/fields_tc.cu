@@ -47,6 +47,7 @@ constexpr int oW0g = 0, oW1g = oW0g + 64 * 32 * 2, oW2g = oW1g + 64 * 64 * 2, oW
               oBias = oHc + 128 * 64 * 2, kQuerySmem = oBias + 288 * 4;
 constexpr uint32_t kQueryTmemCols = 256;
 
+template <bool H16>
 __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam, QueryIO io) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar;
@@ -118,41 +119,41 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
       const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
       float pe[32];
       pos_enc(dir, pe);
-      store_cols<64, 32, 32>(sm + oAc, r, pe);
+      store_cols<64, 32, 32, H16>(sm + oAc, r, pe);
     }
     fence_smem_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<64, 32>(tm + 0, sm + oAg, sm + oW0g);
-      gemm<64, 64>(tm + 64, sm + oAc, sm + oW0c);
+      gemm<64, 32, H16>(tm + 0, sm + oAg, sm + oW0g);
+      gemm<64, 64, H16>(tm + 64, sm + oAc, sm + oW0c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu64(tm + lane + colD, b0, Hs, r);
+    epilogue_relu64<H16>(tm + lane + colD, b0, Hs, r);
     fence_smem_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<64, 64>(tm + 0, sm + oHg, sm + oW1g);
-      gemm<64, 64>(tm + 64, sm + oHc, sm + oW1c);
+      gemm<64, 64, H16>(tm + 0, sm + oHg, sm + oW1g);
+      gemm<64, 64, H16>(tm + 64, sm + oHc, sm + oW1c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu64(tm + lane + colD, b1, Hs, r);
+    epilogue_relu64<H16>(tm + lane + colD, b1, Hs, r);
     fence_smem_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<16, 64>(tm + 128, sm + oHg, sm + oW2g);
-      gemm<16, 64>(tm + 144, sm + oHc, sm + oW2c);
+      gemm<16, 64, H16>(tm + 128, sm + oHg, sm + oW2g);
+      gemm<16, 64, H16>(tm + 144, sm + oHc, sm + oW2c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
@@ -199,6 +200,7 @@ constexpr int bW0c = 0, bW1c = bW0c + 64 * 64 * 2, bW2c = bW1c + 64 * 64 * 2, bA
               bHc = bAc + 128 * 64 * 2, bBias = bHc + 128 * 64 * 2, kBgSmem = bBias + 144 * 4;
 constexpr uint32_t kBgTmemCols = 128;
 
+template <bool H16>
 __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
                                                            const uint32_t* __restrict__ Xb,
                                                            const int32_t* __restrict__ px_ids,
@@ -250,38 +252,38 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
       float ps[3], dir[3], pe[32];
       bg_ray(cam, F, radius, pp % cam.W, pp / cam.W, ps, dir);
       pos_enc(dir, pe);
-      store_cols<64, 32, 32>(sm + bAc, t, pe);
+      store_cols<64, 32, 32, H16>(sm + bAc, t, pe);
     }
     fence_smem_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<64, 64>(tm, sm + bAc, sm + bW0c);
+      gemm<64, 64, H16>(tm, sm + bAc, sm + bW0c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu64(tm + lane, b0, sm + bHc, t);
+    epilogue_relu64<H16>(tm + lane, b0, sm + bHc, t);
     fence_smem_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<64, 64>(tm, sm + bHc, sm + bW1c);
+      gemm<64, 64, H16>(tm, sm + bHc, sm + bW1c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu64(tm + lane, b1, sm + bHc, t);
+    epilogue_relu64<H16>(tm + lane, b1, sm + bHc, t);
     fence_smem_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<16, 64>(tm + 64, sm + bHc, sm + bW2c);
+      gemm<16, 64, H16>(tm + 64, sm + bHc, sm + bW2c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
@@ -330,11 +332,16 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
   if (st != HYRF_OK) return st;
   tc::QueryIO io{a.n,     a.pos, a.alpha_e, a.scale_e, a.color_e, a.vis_ids, a.n_vis,
                  Xg,      Xr,    a.alpha,   a.scale,   a.quat,    a.color,   a.status};
-  set_smem_limit<tc::k_query_fwd_tc>(tc::kQuerySmem);
   int tiles = (a.n + 127) / 128;
   int grid = num_sms() * 2;
   if (tiles < grid) grid = tiles;
-  HYRF_LAUNCH("k_query_fwd_tc", s, tc::k_query_fwd_tc<<<grid, 256, tc::kQuerySmem, s>>>(F, cam, io));
+  if (F.cm.f16) {
+    set_smem_limit<tc::k_query_fwd_tc<true>>(tc::kQuerySmem);
+    HYRF_LAUNCH("k_query_fwd_tc", s, tc::k_query_fwd_tc<true><<<grid, 256, tc::kQuerySmem, s>>>(F, cam, io));
+  } else {
+    set_smem_limit<tc::k_query_fwd_tc<false>>(tc::kQuerySmem);
+    HYRF_LAUNCH("k_query_fwd_tc", s, tc::k_query_fwd_tc<false><<<grid, 256, tc::kQuerySmem, s>>>(F, cam, io));
+  }
   return HYRF_OK;
 }
 
@@ -415,13 +422,20 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
   const bool ready = a.features && a.features_ready && !skip;  // gathered ahead (hyrf_gather_background)
   hyrf_status st = ready ? HYRF_OK : launch_gather(F, cam, RS, P, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
-  set_smem_limit<tc::k_bg_exact_fwd_tc>(tc::kBgSmem);
   int tiles = (P + 127) / 128;
   int grid = num_sms() * 4;
   if (tiles < grid) grid = tiles;
-  HYRF_LAUNCH("k_bg_exact_fwd_tc", s,
-              tc::k_bg_exact_fwd_tc<<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, list, count, a.C_fg,
-                                                                  a.T_final, a.C, a.status));
+  if (F.cm.f16) {
+    set_smem_limit<tc::k_bg_exact_fwd_tc<true>>(tc::kBgSmem);
+    HYRF_LAUNCH("k_bg_exact_fwd_tc", s,
+                tc::k_bg_exact_fwd_tc<true><<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, list, count,
+                                                                          a.C_fg, a.T_final, a.C, a.status));
+  } else {
+    set_smem_limit<tc::k_bg_exact_fwd_tc<false>>(tc::kBgSmem);
+    HYRF_LAUNCH("k_bg_exact_fwd_tc", s,
+                tc::k_bg_exact_fwd_tc<false><<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, list, count,
+                                                                           a.C_fg, a.T_final, a.C, a.status));
+  }
   return HYRF_OK;
 }
 

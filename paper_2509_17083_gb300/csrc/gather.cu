@@ -167,8 +167,9 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
 }
 
 // Features of both fields (Gaussians) or of the radiance field only (pixels).
-// X*: [rows][16] uint32 = [rows][32] bf16, level-major (2l, 2l+1).
-template <bool BOTH, int DT>
+// X*: [rows][16] uint32 = [rows][32] bf16 (f16 when H16: the decoders'
+// operand type), level-major (2l, 2l+1).
+template <bool BOTH, int DT, bool H16>
 __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
     k_gather(FieldsDev F, CamDev cam, RowSource S, uint32_t* __restrict__ Xg, uint32_t* __restrict__ Xr) {
   __shared__ float ys[kRows][3];
@@ -189,10 +190,10 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
   const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
   if (BOTH) {
     const float2 a = level_feature<DT>(F.geo, l, y);
-    xs[0][lane][l] = tc::pack2(a.x, a.y);
+    xs[0][lane][l] = tc::pack2<H16>(a.x, a.y);
   }
   const float2 b = level_feature<DT>(F.rad, l, y);
-  xs[1][lane][l] = tc::pack2(b.x, b.y);
+  xs[1][lane][l] = tc::pack2<H16>(b.x, b.y);
   __syncthreads();
   // coalesced write-out: thread t -> row t/16, word t%16
   const int r = threadIdx.x >> 4, wd = threadIdx.x & 15;
@@ -273,13 +274,14 @@ int grid_for(int rows) { return rows > 0 ? (rows + kRows - 1) / kRows : 0; }
 // rows: an upper bound of the device row count (n for Gaussians, W*H for
 // pixels). Gaussians gather and scatter both fields, pixels the radiance
 // field only.
-template <int DT>
+template <int DT, bool H16>
 static hyrf_status gather_dt(const FieldsDev& F, const CamDev& cam, const RowSource& S, int grid, uint32_t* Xg,
                              uint32_t* Xr, cudaStream_t s) {
   if (!S.pixels)
-    HYRF_LAUNCH("k_gather<gaussians>", s, k_gather<true, DT><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
+    HYRF_LAUNCH("k_gather<gaussians>", s, k_gather<true, DT, H16><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
   else
-    HYRF_LAUNCH("k_gather<pixels>", s, k_gather<false, DT><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
+    HYRF_LAUNCH("k_gather<pixels>", s,
+                k_gather<false, DT, H16><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
   return HYRF_OK;
 }
 
@@ -303,9 +305,15 @@ hyrf_status launch_gather(const FieldsDev& F, const CamDev& cam, const RowSource
                           uint32_t* Xr, cudaStream_t s) {
   const int grid = grid_for(rows);
   if (grid == 0) return HYRF_OK;
-  if (F.rad.u8) return gather_dt<2>(F, cam, S, grid, Xg, Xr, s);
-  if (F.rad.bf16) return gather_dt<1>(F, cam, S, grid, Xg, Xr, s);
-  return gather_dt<0>(F, cam, S, grid, Xg, Xr, s);
+  if (F.cm.f16) {  // the real-time f16 path: f16 or 8-bit grids
+    if (F.rad.u8) return gather_dt<2, true>(F, cam, S, grid, Xg, Xr, s);
+    if (F.rad.f16) return gather_dt<3, true>(F, cam, S, grid, Xg, Xr, s);
+    return HYRF_ERR_UNSUPPORTED;
+  }
+  if (F.rad.u8) return gather_dt<2, false>(F, cam, S, grid, Xg, Xr, s);
+  if (F.rad.bf16) return gather_dt<1, false>(F, cam, S, grid, Xg, Xr, s);
+  if (F.rad.f16) return HYRF_ERR_UNSUPPORTED;
+  return gather_dt<0, false>(F, cam, S, grid, Xg, Xr, s);
 }
 
 hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows,
@@ -313,7 +321,7 @@ hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSourc
                            cudaStream_t s) {
   const int grid = grid_for(rows);
   if (grid == 0) return HYRF_OK;
-  if (F.rad.u8) return HYRF_ERR_UNSUPPORTED;  // the codec renders only
+  if (F.rad.u8 || F.rad.f16 || F.cm.f16) return HYRF_ERR_UNSUPPORTED;  // render-only types
   if (F.rad.bf16) return scatter_dt<1>(F, cam, S, grid, dXg, dXr, g_geo, g_rad, d_pos, s);
   return scatter_dt<0>(F, cam, S, grid, dXg, dXr, g_geo, g_rad, d_pos, s);
 }

@@ -56,12 +56,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// kind::f16 instruction descriptor: D f32, A and B bf16, M = 128; A and B
-// K-major unless AMN / BMN (MN-major).
-template <int N, bool AMN = false, bool BMN = false>
+// kind::f16 instruction descriptor: D f32, A and B bf16 (or both f16 when
+// H16), M = 128; A and B K-major unless AMN / BMN (MN-major).
+template <int N, bool AMN = false, bool BMN = false, bool H16 = false>
 __device__ __forceinline__ constexpr uint32_t idesc() {
   static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((AMN ? 1u : 0u) << 15) | ((BMN ? 1u : 0u) << 16) |
+  constexpr uint32_t fmt = H16 ? 0u : ((1u << 7) | (1u << 10));
+  return (1u << 4) | fmt | ((AMN ? 1u : 0u) << 15) | ((BMN ? 1u : 0u) << 16) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
@@ -111,19 +112,26 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
 }
 
 // D[128 x N] (+)= A[128 x K] B[N x K]^T with both operands K-major in smem.
-template <int N, int K>
+template <int N, int K, bool H16 = false>
 __device__ __forceinline__ void gemm(uint32_t d, const uint8_t* A, const uint8_t* B) {
 #pragma unroll
   for (int ks = 0; ks < K / 16; ++ks) {
     const uint64_t da = sdesc(saddr(A) + ks * 256, 128, (K / 8) * 128);
     const uint64_t db = sdesc(saddr(B) + ks * 256, 128, (K / 8) * 128);
-    mma(d, da, db, idesc<N>(), ks > 0 ? 1u : 0u);
+    mma(d, da, db, idesc<N, false, false, H16>(), ks > 0 ? 1u : 0u);
   }
 }
 
+// Two operand values (bf16, or f16 when H16), round to nearest even.
+template <bool H16 = false>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
+  if constexpr (H16) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
 }
 
 // Row r of a K-major bf16 tile from 8*n floats.
@@ -140,16 +148,16 @@ __device__ __forceinline__ void store_row(uint8_t* tile, int r, const float* v) 
   }
 }
 
-// Columns [C0, C0 + NC) of row r of a K-major bf16 tile from NC floats.
-template <int K, int C0, int NC>
+// Columns [C0, C0 + NC) of row r of a K-major bf16 (f16) tile from NC floats.
+template <int K, int C0, int NC, bool H16 = false>
 __device__ __forceinline__ void store_cols(uint8_t* tile, int r, const float* v) {
 #pragma unroll
   for (int kc = 0; kc < NC / 8; ++kc) {
     uint4 u;
-    u.x = pack2(v[8 * kc], v[8 * kc + 1]);
-    u.y = pack2(v[8 * kc + 2], v[8 * kc + 3]);
-    u.z = pack2(v[8 * kc + 4], v[8 * kc + 5]);
-    u.w = pack2(v[8 * kc + 6], v[8 * kc + 7]);
+    u.x = pack2<H16>(v[8 * kc], v[8 * kc + 1]);
+    u.y = pack2<H16>(v[8 * kc + 2], v[8 * kc + 3]);
+    u.z = pack2<H16>(v[8 * kc + 4], v[8 * kc + 5]);
+    u.w = pack2<H16>(v[8 * kc + 6], v[8 * kc + 7]);
     *reinterpret_cast<uint4*>(tile + kmaj(r, C0 + 8 * kc, K)) = u;
   }
 }
@@ -179,7 +187,9 @@ __device__ __forceinline__ void stage_w(uint8_t* tile, const void* W, int rows_r
   }
 }
 
-// ReLU(D + b) of this thread's 64 accumulator columns -> its row of H.
+// ReLU(D + b) of this thread's 64 accumulator columns -> its row of H
+// (bf16, or f16 when H16).
+template <bool H16 = false>
 __device__ __forceinline__ void epilogue_relu64(uint32_t taddr, const float* b, uint8_t* H, int r) {
 #pragma unroll
   for (int c0 = 0; c0 < 64; c0 += 16) {
@@ -190,10 +200,10 @@ __device__ __forceinline__ void epilogue_relu64(uint32_t taddr, const float* b, 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       uint4 u;
-      u.x = pack2(v[8 * h], v[8 * h + 1]);
-      u.y = pack2(v[8 * h + 2], v[8 * h + 3]);
-      u.z = pack2(v[8 * h + 4], v[8 * h + 5]);
-      u.w = pack2(v[8 * h + 6], v[8 * h + 7]);
+      u.x = pack2<H16>(v[8 * h], v[8 * h + 1]);
+      u.y = pack2<H16>(v[8 * h + 2], v[8 * h + 3]);
+      u.z = pack2<H16>(v[8 * h + 4], v[8 * h + 5]);
+      u.w = pack2<H16>(v[8 * h + 6], v[8 * h + 7]);
       *reinterpret_cast<uint4*>(H + kmaj(r, c0 + 8 * h, 64)) = u;
     }
   }

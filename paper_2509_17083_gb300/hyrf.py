@@ -22,6 +22,7 @@ HYRF_ERR_TIMEOUT = 32
 HYRF_F32 = 0
 HYRF_BF16 = 1
 HYRF_U8 = 2
+HYRF_F16 = 3
 TILE = 16
 
 _vp = C.c_void_p

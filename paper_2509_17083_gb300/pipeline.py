@@ -38,16 +38,17 @@ class DeviceModel:
         self.color_e = _t(g.color_e, device)
         self.fl = fl
         self.bf16 = workload.precision == "bf16"
-        tdt = torch.bfloat16 if self.bf16 else torch.float32
+        self.f16 = workload.precision == "f16"  # render only
+        tdt = torch.bfloat16 if self.bf16 else (torch.float16 if self.f16 else torch.float32)
         self.coupled = bool(coupled)
         self.rad_table = _t(fl.rad.table, device, tdt)
         self.geo_table = self.rad_table if self.coupled else _t(fl.geo.table, device, tdt)
-        wdt = torch.bfloat16 if self.bf16 else torch.float32
+        wdt = tdt
         self.geo_W = [_t(w, device, wdt) for w in fl.geo_mlp.W]
         self.geo_b = [_t(b, device) for b in fl.geo_mlp.b]
         self.col_W = [_t(w, device, wdt) for w in fl.col_mlp.W]
         self.col_b = [_t(b, device) for b in fl.col_mlp.b]
-        self.dtype_code = H.HYRF_BF16 if self.bf16 else H.HYRF_F32
+        self.dtype_code = H.HYRF_BF16 if self.bf16 else (H.HYRF_F16 if self.f16 else H.HYRF_F32)
         self.codes = None  # (geo codes, geo qparams, rad codes, rad qparams) once quantised
         self.grad = {}
         self.zero_grad()

@@ -192,6 +192,23 @@ def make_fields(rng, box_lo, box_hi, n_levels, log2_T, width, n_hidden, table_in
                   geo=geo, rad=rad, geo_mlp=gm, col_mlp=cm, pe_freq=pe_freq, pe_pad=pe_pad)
 
 
+def f16_round(a):
+    """Round float32 values to the nearest IEEE half (ties to even), kept as float32."""
+    return np.ascontiguousarray(a, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def to_f16(fields: Fields) -> Fields:
+    """Same fields with tables and decoder weights rounded to IEEE half."""
+    def g(h):
+        return HashGrid(h.n_levels, h.log2_T, f16_round(h.table), h.n_feat, h.base_res, h.growth)
+
+    def m(x):
+        return MLP(x.n_in, x.width, x.n_hidden, x.n_out, [f16_round(w) for w in x.W],
+                   [b.copy() for b in x.b])
+    return Fields(fields.box_lo, fields.box_hi, g(fields.geo), g(fields.rad), m(fields.geo_mlp),
+                  m(fields.col_mlp), fields.pe_freq, fields.pe_pad)
+
+
 def to_bf16(fields: Fields) -> Fields:
     """Same fields with tables and decoder weights rounded to bfloat16."""
     def g(h):
@@ -293,6 +310,8 @@ def config3(n=1_000_000, width=1237, height=822, log2_T=19, n_clusters=256, prec
     fl = make_fields(rng, lo, hi, 16, log2_T, 64, 2, table_init)
     if precision == "bf16":
         fl = to_bf16(fl)
+    elif precision == "f16":
+        fl = to_f16(fl)
     tr = _rng(seed + 1)
     return Workload(f"config3: 1M Gaussians @1237x822, {precision.upper()} fields", g, fl, [cam],
                     Background(mode=0), [noise_target(tr, cam)], 0.0, precision,

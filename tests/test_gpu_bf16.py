@@ -203,3 +203,26 @@ def test_u8_codec_codes_and_render_match_oracle():
     # the codec renders only
     with pytest.raises(H.HyrfError):
         r.backward_fields()
+
+
+def test_f16_render_path_matches_oracle():
+    """Render-only real-time path with IEEE-half grids and decoders (f16
+    tensor-core operands): the image against the oracle on the same
+    half-rounded parameters, within the BF16 bound; the reverse refuses."""
+    w = synth.config3(n=20000, width=257, height=171, log2_T=15, n_clusters=32, precision="f16", table_init=0.3)
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg)
+    assert r.feat_q is None  # nothing saved for a reverse pass
+    r.fit_capacity()
+    r.status.zero_()
+    r.forward(None)
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    fw = oracle.render(w.gaussians, w.fields, w.cams[0], w.bg)
+    mask = oracle.decision_safe_mask(fw, w.cams[0], fields=w.fields, bg=w.bg, bg_relu_margin=1e-3)
+    err = np.abs(np_(r.C) - fw["C"]).max(-1)
+    assert err[mask].max() < TOL_IMG_BF16_TRAINED, err[mask].max()
+    # IEEE half carries 3 more mantissa bits than bf16: typical errors are smaller
+    assert np.median(err[mask]) < 2e-4, np.median(err[mask])
+    with pytest.raises(H.HyrfError):
+        r.backward_fields()
