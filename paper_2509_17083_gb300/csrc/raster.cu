@@ -1,12 +1,16 @@
 // Front-to-back alpha compositing of Eq. 1 per 16x16 tile, and its reverse.
-// One CTA of 256 threads per tile, one pixel per thread. The visible
-// Gaussians' screen-space records are first packed into 48-byte rows
-// (three float4: {u, v, conic a, conic b}, {conic c, opacity, r, g}, {b})
-// so that a tile stages a batch of 256 of them into shared memory with
-// three vector loads per thread. The forward ends a tile early once every
-// pixel has stopped (CTA-wide vote). The reverse walks each pixel's list
-// back to front, recovering T from the stored T_final by division, reduces
-// the per-Gaussian gradients across each warp and adds them with atomics.
+// The forward runs one CTA of 256 threads per tile, one pixel per thread.
+// The visible Gaussians' screen-space records are first packed into
+// 48-byte rows (three float4: {u, v, conic a, conic b}, {conic c, opacity,
+// r, g}, {b, p_min}) so that a tile stages a batch of 256 of them into
+// shared memory with three vector loads per thread; p_min is a lower bound
+// of the exponent below which the opacity test must fail, so most
+// (pixel, Gaussian) pairs are rejected before the exponential. The forward
+// ends a tile early once every pixel has stopped (CTA-wide vote). The
+// reverse walks each pixel's list back to front, recovering T from the
+// stored T_final by division, with several pixels of one column per thread,
+// reduces the per-Gaussian gradients across each warp and adds them with
+// atomics.
 #include "common.cuh"
 
 namespace hyrf {
@@ -14,6 +18,40 @@ namespace hyrf {
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
+
+// exp of the (non-positive) splat exponent with the hardware exponential
+// (relative error ~1e-6 here, far inside the compositing tolerances); the
+// forward and the reverse pass evaluate it identically, so their
+// threshold decisions agree bit for bit.
+__device__ __forceinline__ float splat_exp(float power) { return __expf(power); }
+
+// Exponent of the 2D Gaussian at offset (dx, dy) = mean - pixel centre,
+// from the pixel-independent parts (conic a) dx dx and (conic b) dx of the
+// column, with a fixed operation order shared by the forward and the
+// reverse pass.
+__device__ __forceinline__ float splat_power(float cadx2, float cbdx, float cc, float dy) {
+  const float q = fmaf(cc * dy, dy, cadx2);
+  return fmaf(-0.5f, q, -(cbdx * dy));
+}
+
+// p_min of a Gaussian with opacity o: for an exponent below it,
+// o exp(power) < 1/255 holds with a margin (1e-3 in the exponent, three
+// orders above the error of the hardware exponential and of the products),
+// so the opacity test of Eq. 1 fails and the exponential is not needed.
+// +inf when no exponent can pass (o <= 1/255 or o not a number).
+__device__ __forceinline__ float splat_pmin(float o) {
+  return o > kAlphaMin ? logf(kAlphaMin / o) - 1e-3f : INFINITY;
+}
+
+// Opacity test of Eq. 1 at one pixel: alpha = min(0.99, o G) with
+// G = exp(power); false when power > 0 or alpha < 1/255 (exactly the
+// decision of the unscreened test: p_min only skips certain failures).
+__device__ __forceinline__ bool splat_alpha(float power, float pmin, float o, float& G, float& alpha) {
+  if (!(power >= pmin && power <= 0.0f)) return false;
+  G = splat_exp(power);
+  alpha = fminf(kAlphaMax, o * G);
+  return alpha >= kAlphaMin;
+}
 
 __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis, int n,
                                               const float* __restrict__ mean2d,
@@ -25,21 +63,8 @@ __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
     rec[3 * i] = make_float4(mean2d[2 * i], mean2d[2 * i + 1], conic[3 * i], conic[3 * i + 1]);
     rec[3 * i + 1] = make_float4(conic[3 * i + 2], alpha[i], color[3 * i], color[3 * i + 1]);
-    rec[3 * i + 2] = make_float4(color[3 * i + 2], 0.0f, 0.0f, 0.0f);
+    rec[3 * i + 2] = make_float4(color[3 * i + 2], splat_pmin(alpha[i]), 0.0f, 0.0f);
   }
-}
-
-// exp of the (non-positive) splat exponent with the hardware exponential
-// (relative error ~1e-6 here, far inside the compositing tolerances); the
-// forward and the reverse pass evaluate it identically, so their
-// threshold decisions agree bit for bit.
-__device__ __forceinline__ float splat_exp(float power) { return __expf(power); }
-
-// Exponent of the 2D Gaussian at offset (dx, dy) = mean - pixel centre, with
-// a fixed multiply-add order shared by the forward and the reverse pass.
-__device__ __forceinline__ float splat_power(float ca, float cb, float cc, float dx, float dy) {
-  const float q = fmaf(cc * dy, dy, ca * dx * dx);
-  return fmaf(-0.5f, q, -(cb * dx * dy));
 }
 
 __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ ranges,
@@ -69,6 +94,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
         set_status(status, HYRF_ERR_BOUNDS);
         s0[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         s1[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // opacity 0: never contributes
+        s2[t] = make_float4(0.0f, INFINITY, 0.0f, 0.0f);
       } else {
         s0[t] = rec[3 * g];
         s1[t] = rec[3 * g + 1];
@@ -80,10 +106,9 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
     for (int j = 0; j < cnt && !done; ++j) {
       const float4 r0 = s0[j], r1 = s1[j];
       const float dx = r0.x - fx, dy = r0.y - fy;
-      const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
-      if (power > 0.0f) continue;
-      const float alpha = fminf(kAlphaMax, r1.y * splat_exp(power));
-      if (alpha < kAlphaMin) continue;
+      const float power = splat_power(r0.z * dx * dx, r0.w * dx, r1.x, dy);
+      float G, alpha;
+      if (!splat_alpha(power, s2[j].y, r1.y, G, alpha)) continue;
       const float test_T = T * (1.0f - alpha);
       if (test_T < kTMin) {
         done = true;
@@ -139,114 +164,84 @@ __device__ __forceinline__ int col8(int lane) {
   return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-// State of one pixel's back-to-front walk: T before the current Gaussian
-// (recovered from T_final), the colour composited behind it (normalised by T
-// after it), the previous contributor, and the pixel's upstream gradients.
-struct PixBack {
-  float fx, fy, Tf, T, g0, g1, g2, gT, a0, a1, a2, la, lc0, lc1, lc2;
-  int last;
-};
+// Reverse of Eq. 1 per tile: each pixel walks its list back to front from
+// its last contributor, recovering T before each Gaussian from T after it
+// (division by 1 - alpha) and the colour composited behind it through
+// S = (colour behind) . dL/dC, so that
+//   dL/dalpha = (c . dL/dC - S) T - dL/dT_final T_final / (1 - alpha).
+// A thread holds P pixels of one column (rows r, r + 2, ..., r + 2(P - 1))
+// and WARPS warps share a tile; the x offset dx of a Gaussian is common to
+// the thread's pixels, so the conic and mean gradients are accumulated as
+// sums D0 = sum dp, D1 = sum dp dy, D2 = sum dp dy^2 (dp = dL/dpower) and
+// expanded once per Gaussian before the warp reduction.
+#ifndef HYRF_RASTER_BWD_WARPS
+#define HYRF_RASTER_BWD_WARPS 4
+#endif
+constexpr int kBwdRasterWarps = HYRF_RASTER_BWD_WARPS;
+static_assert(kBwdRasterWarps == 1 || kBwdRasterWarps == 2 || kBwdRasterWarps == 4 || kBwdRasterWarps == 8,
+              "warps per tile must divide the 8 row pairs of a tile");
 
-__device__ __forceinline__ void pix_init(PixBack& q, int px, int py, int W, int H,
-                                         const float* __restrict__ T_final,
-                                         const int32_t* __restrict__ n_contrib,
-                                         const float* __restrict__ dC, const float* __restrict__ dT) {
-  const bool inside = px < W && py < H;
-  const int p = inside ? py * W + px : 0;
-  q.fx = (float)px + 0.5f;
-  q.fy = (float)py + 0.5f;
-  q.Tf = inside ? T_final[p] : 1.0f;
-  q.T = q.Tf;
-  q.last = inside ? n_contrib[p] : 0;
-  q.g0 = inside ? dC[3 * p] : 0.0f;
-  q.g1 = inside ? dC[3 * p + 1] : 0.0f;
-  q.g2 = inside ? dC[3 * p + 2] : 0.0f;
-  q.gT = inside ? dT[p] : 0.0f;
-  q.a0 = q.a1 = q.a2 = q.la = q.lc0 = q.lc1 = q.lc2 = 0.0f;
-}
-
-// Reverse of one (pixel, Gaussian) compositing step at list position pos:
-// adds dL/d(mean2d u, v, conic a, b, c, opacity, colour r, g, b) of this
-// pixel to acc; false if the Gaussian did not contribute to the pixel.
-__device__ __forceinline__ bool pix_step(PixBack& q, int pos, const float4& r0, const float4& r1, float cb,
-                                         float* acc) {
-  if (pos >= q.last) return false;
-  const float dx = r0.x - q.fx, dy = r0.y - q.fy;
-  const float power = splat_power(r0.z, r0.w, r1.x, dx, dy);
-  if (power > 0.0f) return false;
-  const float G = splat_exp(power);
-  const float oG = r1.y * G;
-  const float alpha = fminf(kAlphaMax, oG);
-  if (alpha < kAlphaMin) return false;
-  const float inv = __fdividef(1.0f, 1.0f - alpha);  // 1 - alpha >= 0.01
-  q.T = q.T * inv;                                   // T before this Gaussian
-  q.a0 = q.la * q.lc0 + (1.0f - q.la) * q.a0;
-  q.a1 = q.la * q.lc1 + (1.0f - q.la) * q.a1;
-  q.a2 = q.la * q.lc2 + (1.0f - q.la) * q.a2;
-  q.la = alpha;
-  q.lc0 = r1.z;
-  q.lc1 = r1.w;
-  q.lc2 = cb;
-  const float w = alpha * q.T;
-  acc[6] += w * q.g0;
-  acc[7] += w * q.g1;
-  acc[8] += w * q.g2;
-  float dal = ((r1.z - q.a0) * q.g0 + (r1.w - q.a1) * q.g1 + (cb - q.a2) * q.g2) * q.T;
-  dal -= q.gT * q.Tf * inv;
-  if (oG <= kAlphaMax) {
-    acc[5] += dal * G;
-    const float dp = dal * alpha;
-    acc[0] += dp * (-(r0.z * dx) - r0.w * dy);
-    acc[1] += dp * (-(r1.x * dy) - r0.w * dx);
-    acc[2] += dp * (-0.5f * dx * dx);
-    acc[3] += dp * (-(dx * dy));
-    acc[4] += dp * (-0.5f * dy * dy);
-  }
-  return true;
-}
-
-// Two pixels per thread, (x, y) and (x, y + 2): a warp covers four rows of the
-// tile, so each warp-level reduction of a Gaussian's gradient sums 64 pixels.
-constexpr int kBwdRasterThreads = 128;
-
-__global__ void __launch_bounds__(kBwdRasterThreads) k_raster_bwd(
+template <int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
     const float4* __restrict__ rec, int W, int H, int TX, const float* __restrict__ T_final,
     const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
     const float* __restrict__ dT, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
     float* __restrict__ d_alpha, float* __restrict__ d_color) {
-  constexpr int B = 256;  // Gaussians staged per batch
-  __shared__ float4 s0[B], s1[B], s2[B];
+  constexpr int P = 8 / WARPS;       // pixels per thread
+  constexpr int NT = 32 * WARPS;     // threads per tile
+  constexpr int B = 256;             // Gaussians staged per batch
+  __shared__ float4 s0[B], s1[B];
+  __shared__ float2 s2[B];
   __shared__ int sg[B];
   __shared__ int max_last;
   const int tile = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int px = (tile % TX) * kTile + (lane & 15);
-  const int py = (tile / TX) * kTile + 4 * wp + (lane >> 4);
+  const int py0 = (tile / TX) * kTile + (kTile / WARPS) * wp + (lane >> 4);
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
-  PixBack A, Bq;
-  pix_init(A, px, py, W, H, T_final, n_contrib, dC, dT);
-  pix_init(Bq, px, py + 2, W, H, T_final, n_contrib, dC, dT);
-  const int mylast = max(A.last, Bq.last);
+  const float fx = (float)px + 0.5f;
+  float fy[P], T[P], g0[P], g1[P], g2[P], gTf[P], S[P], la[P], ls[P];
+  int last[P];
+  int mylast = 0;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int py = py0 + 2 * k;
+    const bool inside = px < W && py < H;
+    const int p = inside ? py * W + px : 0;
+    fy[k] = (float)py + 0.5f;
+    const float Tf = inside ? T_final[p] : 1.0f;
+    T[k] = Tf;
+    last[k] = inside ? n_contrib[p] : 0;
+    g0[k] = inside ? dC[3 * p] : 0.0f;
+    g1[k] = inside ? dC[3 * p + 1] : 0.0f;
+    g2[k] = inside ? dC[3 * p + 2] : 0.0f;
+    gTf[k] = (inside ? dT[p] : 0.0f) * Tf;
+    S[k] = la[k] = ls[k] = 0.0f;
+    mylast = max(mylast, last[k]);
+  }
+  // no pixel of this warp used list positions >= wstop (warp-uniform)
+  const int wlast = __reduce_max_sync(0xffffffffu, mylast);
+  const int wstop = start + wlast;
   if (t == 0) max_last = 0;
   __syncthreads();
-  atomicMax(&max_last, mylast);
+  if (lane == 0) atomicMax(&max_last, wlast);
   __syncthreads();
-  const int stop = min(end, start + max_last);  // no pixel of the tile used positions >= stop
-  // nor did any pixel of this warp use positions >= wstop (warp-uniform bound)
-  const int wstop = start + __reduce_max_sync(0xffffffffu, mylast);
+  const int stop = min(end, start + max_last);  // nor did any pixel of the tile use positions >= stop
   for (int b1 = stop; b1 > start; b1 -= B) {
     const int b0 = max(start, b1 - B);
     __syncthreads();
-    for (int e = t; e < b1 - b0; e += kBwdRasterThreads) {
+    for (int e = t; e < b1 - b0; e += NT) {
       int g = vals[b0 + e];
       if (g < 0 || g >= n) {
         g = -1;
-        s1[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // opacity 0: never contributes
+        s1[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s2[e] = make_float2(0.0f, INFINITY);  // never contributes
       } else {
         s0[e] = rec[3 * g];
         s1[e] = rec[3 * g + 1];
-        s2[e] = rec[3 * g + 2];
+        const float4 r2 = rec[3 * g + 2];
+        s2[e] = make_float2(r2.x, r2.y);
       }
       sg[e] = g;
     }
@@ -254,14 +249,53 @@ __global__ void __launch_bounds__(kBwdRasterThreads) k_raster_bwd(
     for (int j = min(b1, wstop) - b0 - 1; j >= 0; --j) {
       const int pos = b0 - start + j;  // list position
       const float4 r0 = s0[j], r1 = s1[j];
-      const float cb = s2[j].x;
-      float acc[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-      const bool ca = pix_step(A, pos, r0, r1, cb, acc);
-      const bool cbq = pix_step(Bq, pos, r0, r1, cb, acc);
-      if (__any_sync(0xffffffffu, ca || cbq)) {
-        // mean2d (2), conic (3), opacity, colour r, g: one sum per lane group
-        const float s8 = reduce8(acc);
-        const float sb = warp_sum(acc[8]);
+      const float2 r2 = s2[j];
+      const float dx = r0.x - fx;
+      const float cadx2 = r0.z * dx * dx, cbdx = r0.w * dx;
+      float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, dop = 0.0f, dc0 = 0.0f, dc1 = 0.0f, dc2 = 0.0f;
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const float dy = r0.y - fy[k];
+        const float power = splat_power(cadx2, cbdx, r1.x, dy);
+        float G = 0.0f, alpha = 0.0f;
+        const bool c = pos < last[k] && splat_alpha(power, r2.y, r1.y, G, alpha);
+        if (__any_sync(0xffffffffu, c) && c) {
+          any = true;
+          const float inv = __fdividef(1.0f, 1.0f - alpha);  // 1 - alpha >= 0.01
+          T[k] *= inv;                                       // T before this Gaussian
+          S[k] = fmaf(la[k], ls[k] - S[k], S[k]);            // behind: previous contributor over the rest
+          const float cg = fmaf(r2.x, g2[k], fmaf(r1.w, g1[k], r1.z * g0[k]));
+          la[k] = alpha;
+          ls[k] = cg;
+          const float w = alpha * T[k];
+          dc0 = fmaf(w, g0[k], dc0);
+          dc1 = fmaf(w, g1[k], dc1);
+          dc2 = fmaf(w, g2[k], dc2);
+          const float dal = fmaf(-gTf[k], inv, (cg - S[k]) * T[k]);
+          if (r1.y * G <= kAlphaMax) {  // alpha not clamped
+            dop = fmaf(dal, G, dop);
+            const float dp = dal * alpha;
+            const float e = dp * dy;
+            D0 += dp;
+            D1 += e;
+            D2 = fmaf(e, dy, D2);
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, any)) {
+        // mean2d (u, v), conic (a, b, c), opacity, colour r, g; colour b apart
+        float v[8];
+        v[0] = -(r0.z * dx) * D0 - r0.w * D1;
+        v[1] = -(r1.x * D1) - cbdx * D0;
+        v[2] = -0.5f * dx * dx * D0;
+        v[3] = -dx * D1;
+        v[4] = -0.5f * D2;
+        v[5] = dop;
+        v[6] = dc0;
+        v[7] = dc1;
+        const float s8 = reduce8(v);
+        const float sb = warp_sum(dc2);
         const int g = sg[j];
         if (g >= 0) {
           if ((lane & 3) == 0) {
@@ -316,7 +350,7 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
   HYRF_LAUNCH("k_raster_bwd", s,
-              k_raster_bwd<<<TX * TY, kBwdRasterThreads, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
+              k_raster_bwd<kBwdRasterWarps><<<TX * TY, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
                                        a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
                                        b.d_alpha, b.d_color));
   return HYRF_OK;
