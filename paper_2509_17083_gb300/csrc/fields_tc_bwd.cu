@@ -16,8 +16,8 @@
 // transposed copy exists; dW products read the row tiles as MN-major
 // operands with M = 128 output rows, of which only the decoder's real
 // outputs are used. Each dW comes out of tensor memory after its product
-// and is added (plain read-modify-write) into this CTA's f32 slab; one
-// reduction kernel sums the slabs. Bias gradients are column sums of dZ.
+// and is added (vector reductions) into this CTA's f32 slab; one reduction
+// kernel sums the slabs. Bias gradients are column sums of dZ.
 // Hidden activations are recomputed, never stored in global memory.
 #include "tc_ops.cuh"
 
@@ -158,11 +158,12 @@ struct GeoGauss {
     }
     const float rn = sqrtf(o[4] * o[4] + o[5] * o[5] + o[6] * o[6] + o[7] * o[7]);
     if (rn > 1e-12f) {
+      const float irn = 1.0f / rn;
       float qd = 0.0f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) qd += o[4 + k] / rn * R.dq[k];
+      for (int k = 0; k < 4; ++k) qd += o[4 + k] * irn * R.dq[k];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) dz[4 + k] = (R.dq[k] - o[4 + k] / rn * qd) / rn;
+      for (int k = 0; k < 4; ++k) dz[4 + k] = (R.dq[k] - o[4 + k] * irn * qd) * irn;
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) dz[4 + k] = R.dq[k] / 1e-12f;
@@ -172,8 +173,9 @@ struct GeoGauss {
       for (int k = 0; k < 8; ++k) dz[k] = 0.0f;
       return;
     }
-    if (P.d_alpha_e) P.d_alpha_e[R.g] += dz[0];
-    if (P.d_scale_e) P.d_scale_e[R.g] += dz[1] + dz[2] + dz[3];
+    // one row per Gaussian: the adds never meet; reductions do not wait
+    if (P.d_alpha_e) atomicAdd(P.d_alpha_e + R.g, dz[0]);
+    if (P.d_scale_e) atomicAdd(P.d_scale_e + R.g, dz[1] + dz[2] + dz[3]);
   }
   // dx = dX columns [16h, 16h + 16)
   __device__ static void finish(const Params& P, const FieldsDev&, const CamDev&, Row& R, const float* dx,
@@ -230,7 +232,7 @@ struct ColGauss {
     }
     if (R.ok && P.d_color_e) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) P.d_color_e[3 * (int64_t)R.g + k] += dz[k];
+      for (int k = 0; k < 3; ++k) atomicAdd(P.d_color_e + 3 * (int64_t)R.g + k, dz[k]);
     }
   }
   // dx = dX columns [32h, 32h + 32)
@@ -246,7 +248,7 @@ struct ColGauss {
     pos_enc_bwd(R.dir, dx, ddir);
     const float dd = R.dir[0] * ddir[0] + R.dir[1] * ddir[1] + R.dir[2] * ddir[2];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) P.d_pos[3 * (int64_t)R.g + j] += (ddir[j] - R.dir[j] * dd) / R.vn;
+    for (int j = 0; j < 3; ++j) atomicAdd(P.d_pos + 3 * (int64_t)R.g + j, (ddir[j] - R.dir[j] * dd) / R.vn);
   }
 };
 
@@ -340,14 +342,13 @@ constexpr uint32_t kBwdTmemCols = 128;  // [0, 64): products, [64, 128): dW
 // column c0.
 template <int NC>
 __device__ __forceinline__ void epilogue_relu(uint32_t taddr, const float* b, uint8_t* H, int r, int c0) {
+  float v[NC];
+  ldcols<NC>(taddr, v);
 #pragma unroll
-  for (int c = 0; c < NC; c += 16) {
-    float v[16];
-    ld16(taddr + c, v);
+  for (int c = 0; c < NC; c += 8) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b[c0 + c + j], 0.0f);
-    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, 64)) = pack8(v);
-    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c + 8, 64)) = pack8(v + 8);
+    for (int j = 0; j < 8; ++j) v[c + j] = fmaxf(v[c + j] + b[c0 + c + j], 0.0f);
+    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, 64)) = pack8(v + c);
   }
 }
 
@@ -358,44 +359,37 @@ __device__ __forceinline__ void epilogue_relu(uint32_t taddr, const float* b, ui
 template <int NC>
 __device__ __forceinline__ void relu_back(uint32_t taddr, uint8_t* Hbuf, int r, bool ok, float* db, int c0) {
   const int lane = threadIdx.x & 31;
+  float v[NC];
+  ldcols<NC>(taddr, v);
 #pragma unroll
   for (int c = 0; c < NC; c += 16) {
-    float v[16], hv[16];
-    ld16(taddr + c, v);
+    float hv[16];
     unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c, 64)), hv);
     unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)), hv + 8);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = (ok && hv[j] > 0.0f) ? v[j] : 0.0f;
-    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c, 64)) = pack8(v);
-    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)) = pack8(v + 8);
-    const float sum = col_sum16(v);
+    for (int j = 0; j < 16; ++j) v[c + j] = (ok && hv[j] > 0.0f) ? v[c + j] : 0.0f;
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c, 64)) = pack8(v + c);
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)) = pack8(v + c + 8);
+    const float sum = col_sum16(v + c);
     if ((lane & 1) == 0) atomicAdd(db + c0 + c + col_of_lane(lane), sum);
   }
 }
 
 // Columns [c0, c0 + NC) of the dW rows < rows_used (TMEM lanes) x N columns,
-// added to the CTA slab (row stride N). Warps of both halves share lanes.
+// added to the CTA slab (row stride N) with vector reductions (no value
+// comes back, so the tile does not wait for the L2 round trip; the slab is
+// private to the CTA, so nothing contends). Warps of both halves share lanes.
 template <int N, int NC>
 __device__ __forceinline__ void flush_dw(uint32_t tm_w, int rows_used, float* slab_W, int c0) {
   const int q = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
   if (q * 32 >= rows_used) return;  // warp-uniform
   const int o = q * 32 + lane;
+  float v[NC];
+  ldcols<NC>(tm_w + ((uint32_t)(q * 32) << 16) + c0, v);
+  if (o < rows_used) {
+    float4* d = reinterpret_cast<float4*>(slab_W + o * N + c0);  // slab rows are 16-byte aligned
 #pragma unroll
-  for (int c = 0; c < NC; c += 16) {
-    float v[16];
-    ld16(tm_w + ((uint32_t)(q * 32) << 16) + c0 + c, v);
-    if (o < rows_used) {
-      float4* d = reinterpret_cast<float4*>(slab_W + o * N + c0 + c);  // slab rows are 16-byte aligned
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float4 x = d[k];
-        x.x += v[4 * k];
-        x.y += v[4 * k + 1];
-        x.z += v[4 * k + 2];
-        x.w += v[4 * k + 3];
-        d[k] = x;
-      }
-    }
+    for (int k = 0; k < NC / 4; ++k) atomicAdd(d + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
   }
 }
 
@@ -536,8 +530,7 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
     {
       constexpr int HALF = S::DXC / 2;
       float dx[HALF];
-#pragma unroll
-      for (int c0 = 0; c0 < HALF; c0 += 16) ld16(tm + lane_off + h * HALF + c0, dx + c0);
+      ldcols<HALF>(tm + lane_off + h * HALF, dx);
 #pragma unroll
       for (int k = 0; k < HALF; ++k) dx[k] *= inv_ls;
       S::finish(P, F, cam, R, dx, h);

@@ -111,6 +111,37 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 32 consecutive f32 accumulator columns of this thread's TMEM lane, one
+// load and one wait.
+__device__ __forceinline__ void ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// NC consecutive accumulator columns (16 or a multiple of 32) with as few
+// load-and-wait round trips as the load shapes allow.
+template <int NC>
+__device__ __forceinline__ void ldcols(uint32_t taddr, float* v) {
+  static_assert(NC == 16 || NC % 32 == 0, "columns");
+  if constexpr (NC == 16) {
+    ld16(taddr, v);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; c += 32) ld32(taddr + c, v + c);
+  }
+}
+
 // D[128 x N] (+)= A[128 x K] B[N x K]^T with both operands K-major in smem.
 template <int N, int K, bool H16 = false>
 __device__ __forceinline__ void gemm(uint32_t d, const uint8_t* A, const uint8_t* B) {
@@ -192,13 +223,13 @@ __device__ __forceinline__ void stage_w(uint8_t* tile, const void* W, int rows_r
 template <bool H16 = false>
 __device__ __forceinline__ void epilogue_relu64(uint32_t taddr, const float* b, uint8_t* H, int r) {
 #pragma unroll
-  for (int c0 = 0; c0 < 64; c0 += 16) {
-    float v[16];
-    ld16(taddr + c0, v);
+  for (int c0 = 0; c0 < 64; c0 += 32) {
+    float v[32];
+    ld32(taddr + c0, v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + b[c0 + j], 0.0f);
+    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + b[c0 + j], 0.0f);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
       uint4 u;
       u.x = pack2<H16>(v[8 * h], v[8 * h + 1]);
       u.y = pack2<H16>(v[8 * h + 2], v[8 * h + 3]);
