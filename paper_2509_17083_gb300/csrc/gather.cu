@@ -84,6 +84,36 @@ __device__ __forceinline__ float2 level_feature(const GridDev& G, int l, const f
   return make_float2(a0, a1);
 }
 
+// Eq. 3 at one level in two grids with the same cell arithmetic (same
+// levels, resolutions, table size and dense levels): each corner's index
+// and weight serve both tables. Same sums, in the same order, as two calls
+// of level_feature.
+template <int DT>
+__device__ __forceinline__ void level_feature2(const GridDev& A, const GridDev& B, int l, const float y[3],
+                                               float2& fa, float2& fb) {
+  uint32_t idx[8];
+  float f[3];
+  level_cell(A, l, y, idx, f);
+  float2 ea[8], eb[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const size_t e = (size_t)l * A.T + idx[c];
+    ea[c] = load_entry_t<DT>(A, e);
+    eb[c] = load_entry_t<DT>(B, e);
+  }
+  float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = corner_w(f, c);
+    a0 = fmaf(w, ea[c].x, a0);
+    a1 = fmaf(w, ea[c].y, a1);
+    b0 = fmaf(w, eb[c].x, b0);
+    b1 = fmaf(w, eb[c].y, b1);
+  }
+  fa = make_float2(a0, a1);
+  fb = make_float2(b0, b1);
+}
+
 // One float2 atomic per run of consecutive lanes that target the same table
 // entry e: lanes hold neighbouring pixels of an image row, so lanes sharing
 // a cell form runs. Each run's contributions are summed by a segmented
@@ -166,11 +196,86 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
   }
 }
 
+// run_atomic for the same entry e of two tables (ga, gb) at once: the runs
+// are found once and the four sums scanned together.
+__device__ __forceinline__ void run_atomic2(float* __restrict__ ga, float* __restrict__ gb, size_t e, uint32_t key,
+                                            float a0, float a1, float b0, float b1) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint32_t prev = __shfl_up_sync(full, key, 1);
+  const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
+  bool issue = true;
+  if (heads == 1u) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(full, a0, o);
+      a1 += __shfl_xor_sync(full, a1, o);
+      b0 += __shfl_xor_sync(full, b0, o);
+      b1 += __shfl_xor_sync(full, b1, o);
+    }
+    issue = lane == 0;
+  } else if (heads != full) {
+    const int start = 31 - __clz(heads & (full >> (31 - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float x0 = __shfl_up_sync(full, a0, o), x1 = __shfl_up_sync(full, a1, o);
+      const float z0 = __shfl_up_sync(full, b0, o), z1 = __shfl_up_sync(full, b1, o);
+      if (lane - o >= start) {
+        a0 += x0;
+        a1 += x1;
+        b0 += z0;
+        b1 += z1;
+      }
+    }
+    issue = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  }
+  if (!issue) return;
+  if (a0 != 0.0f || a1 != 0.0f) atomicAdd(reinterpret_cast<float2*>(ga) + e, make_float2(a0, a1));
+  if (b0 != 0.0f || b1 != 0.0f) atomicAdd(reinterpret_cast<float2*>(gb) + e, make_float2(b0, b1));
+}
+
+// level_scatter of two grids with the same cell arithmetic (Gaussians,
+// coherent lanes): (a0, a1) and (b0, b1) are the feature gradients of grid
+// A and B; dy receives the sum of both grids' dL/dy.
+template <int DT>
+__device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& B, int l, const float y[3],
+                                               float2 da, float2 db, float* __restrict__ ga,
+                                               float* __restrict__ gb, float dy[3]) {
+  dy[0] = dy[1] = dy[2] = 0.0f;
+  const bool zero = da.x == 0.0f && da.y == 0.0f && db.x == 0.0f && db.y == 0.0f;
+  if (__all_sync(0xffffffffu, zero)) return;
+  uint32_t idx[8];
+  float f[3];
+  level_cell(A, l, y, idx, f);
+  float g[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const size_t e = (size_t)l * A.T + idx[c];
+    const float w = corner_w(f, c);
+    run_atomic2(ga, gb, e, idx[c], w * da.x, w * da.y, w * db.x, w * db.y);
+    if (!zero) {
+      const float2 va = load_entry_t<DT>(A, e), vb = load_entry_t<DT>(B, e);
+      const float dot = va.x * da.x + va.y * da.y + (vb.x * db.x + vb.y * db.y);
+      const float wx = (c & 1) ? f[0] : 1.0f - f[0];
+      const float wy = (c & 2) ? f[1] : 1.0f - f[1];
+      const float wz = (c & 4) ? f[2] : 1.0f - f[2];
+      g[0] += dot * ((c & 1) ? 1.0f : -1.0f) * wy * wz;
+      g[1] += dot * ((c & 2) ? 1.0f : -1.0f) * wx * wz;
+      g[2] += dot * ((c & 4) ? 1.0f : -1.0f) * wx * wy;
+    }
+  }
+  const float N = (float)A.res[l];
+  dy[0] = g[0] * N;
+  dy[1] = g[1] * N;
+  dy[2] = g[2] * N;
+}
+
 // Features of both fields (Gaussians) or of the radiance field only (pixels).
 // X*: [rows][16] uint32 = [rows][32] bf16 (f16 when H16: the decoders'
 // operand type), level-major (2l, 2l+1).
-template <bool BOTH, int DT, bool H16>
-__global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
+// SAME: both grids have the same cell arithmetic (level_feature2).
+template <bool BOTH, int DT, bool H16, bool SAME>
+__global__ void __launch_bounds__(kThreads, 4)
     k_gather(FieldsDev F, CamDev cam, RowSource S, uint32_t* __restrict__ Xg, uint32_t* __restrict__ Xr) {
   __shared__ float ys[kRows][3];
   __shared__ uint32_t xs[2][kRows][kLevels + 1];
@@ -188,12 +293,19 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
   }
   __syncthreads();
   const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
-  if (BOTH) {
-    const float2 a = level_feature<DT>(F.geo, l, y);
+  if (BOTH && SAME) {
+    float2 a, b;
+    level_feature2<DT>(F.geo, F.rad, l, y, a, b);
     xs[0][lane][l] = tc::pack2<H16>(a.x, a.y);
+    xs[1][lane][l] = tc::pack2<H16>(b.x, b.y);
+  } else {
+    if (BOTH) {
+      const float2 a = level_feature<DT>(F.geo, l, y);
+      xs[0][lane][l] = tc::pack2<H16>(a.x, a.y);
+    }
+    const float2 b = level_feature<DT>(F.rad, l, y);
+    xs[1][lane][l] = tc::pack2<H16>(b.x, b.y);
   }
-  const float2 b = level_feature<DT>(F.rad, l, y);
-  xs[1][lane][l] = tc::pack2<H16>(b.x, b.y);
   __syncthreads();
   // coalesced write-out: thread t -> row t/16, word t%16
   const int r = threadIdx.x >> 4, wd = threadIdx.x & 15;
@@ -206,9 +318,10 @@ __global__ void __launch_bounds__(kThreads, BOTH ? 3 : 4)
 
 // Reverse of k_gather. dXg/dXr: [rows][32] f32 feature gradients (already
 // unscaled; streamed with evict-first loads). Gaussians: both fields, and
-// d_pos[g] += J^T sum_l dL/dy_l; pixels: the radiance field.
-template <bool GAUSS, int DT>
-__global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
+// d_pos[g] += J^T sum_l dL/dy_l; pixels: the radiance field. SAME: both
+// grids have the same cell arithmetic (level_scatter2).
+template <bool GAUSS, int DT, bool SAME>
+__global__ void __launch_bounds__(kThreads, 4)
     k_scatter(FieldsDev F, CamDev cam, RowSource S, const float* __restrict__ dXg,
               const float* __restrict__ dXr, float* __restrict__ g_geo, float* __restrict__ g_rad,
               float* __restrict__ d_pos) {
@@ -243,8 +356,13 @@ __global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
     const float2 dg = ok ? __ldcs(reinterpret_cast<const float2*>(dXg + o)) : zero;
     const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
     float dy[3], dy2[3];
-    level_scatter<true, true, DT>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
-    level_scatter<true, true, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
+    if (SAME) {
+      level_scatter2<DT>(F.geo, F.rad, l, y, dg, dr, g_geo, g_rad, dy);
+      dy2[0] = dy2[1] = dy2[2] = 0.0f;
+    } else {
+      level_scatter<true, true, DT>(F.geo, l, y, dg.x, dg.y, g_geo, dy);
+      level_scatter<true, true, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy2);
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) dys[l][lane][k] = dy[k] + dy2[k];
     __syncthreads();
@@ -258,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, GAUSS ? 3 : 4)
       const float* J = Js[lane];
       const int g = gs[lane];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) d_pos[3 * (int64_t)g + j] += J[j] * s[0] + J[3 + j] * s[1] + J[6 + j] * s[2];
+      for (int j = 0; j < 3; ++j) atomicAdd(d_pos + 3 * (int64_t)g + j, J[j] * s[0] + J[3 + j] * s[1] + J[6 + j] * s[2]);
     }
   } else {
     const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
@@ -274,14 +392,26 @@ int grid_for(int rows) { return rows > 0 ? (rows + kRows - 1) / kRows : 0; }
 // rows: an upper bound of the device row count (n for Gaussians, W*H for
 // pixels). Gaussians gather and scatter both fields, pixels the radiance
 // field only.
+// Both grids index their tables identically at every level.
+static bool same_cells(const GridDev& a, const GridDev& b) {
+  if (a.L != b.L || a.T != b.T || a.dense != b.dense) return false;
+  for (int l = 0; l < a.L; ++l)
+    if (a.res[l] != b.res[l]) return false;
+  return true;
+}
+
 template <int DT, bool H16>
 static hyrf_status gather_dt(const FieldsDev& F, const CamDev& cam, const RowSource& S, int grid, uint32_t* Xg,
                              uint32_t* Xr, cudaStream_t s) {
-  if (!S.pixels)
-    HYRF_LAUNCH("k_gather<gaussians>", s, k_gather<true, DT, H16><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
-  else
+  if (S.pixels)
     HYRF_LAUNCH("k_gather<pixels>", s,
-                k_gather<false, DT, H16><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
+                k_gather<false, DT, H16, false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, Xr));
+  else if (same_cells(F.geo, F.rad))
+    HYRF_LAUNCH("k_gather<gaussians>", s,
+                k_gather<true, DT, H16, true><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
+  else
+    HYRF_LAUNCH("k_gather<gaussians>", s,
+                k_gather<true, DT, H16, false><<<grid, kThreads, 0, s>>>(F, cam, S, Xg, Xr));
   return HYRF_OK;
 }
 
@@ -289,12 +419,15 @@ template <int DT>
 static hyrf_status scatter_dt(const FieldsDev& F, const CamDev& cam, const RowSource& S, int grid,
                               const float* dXg, const float* dXr, float* g_geo, float* g_rad, float* d_pos,
                               cudaStream_t s) {
-  if (!S.pixels)
-    HYRF_LAUNCH("k_scatter<gaussians>", s,
-                k_scatter<true, DT><<<grid, kThreads, 0, s>>>(F, cam, S, dXg, dXr, g_geo, g_rad, d_pos));
-  else
+  if (S.pixels)
     HYRF_LAUNCH("k_scatter<pixels>", s,
-                k_scatter<false, DT><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, dXr, nullptr, g_rad, nullptr));
+                k_scatter<false, DT, false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, dXr, nullptr, g_rad, nullptr));
+  else if (same_cells(F.geo, F.rad))
+    HYRF_LAUNCH("k_scatter<gaussians>", s,
+                k_scatter<true, DT, true><<<grid, kThreads, 0, s>>>(F, cam, S, dXg, dXr, g_geo, g_rad, d_pos));
+  else
+    HYRF_LAUNCH("k_scatter<gaussians>", s,
+                k_scatter<true, DT, false><<<grid, kThreads, 0, s>>>(F, cam, S, dXg, dXr, g_geo, g_rad, d_pos));
   return HYRF_OK;
 }
 
