@@ -35,6 +35,9 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "bf16", "f32"])
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-graph", dest="graph", action="store_false",
+                   help="issue every call of the timed step from the host instead of replaying the "
+                        "step captured as one CUDA graph")
     p.add_argument("--cpu-sample-s", type=float, default=15.0)
     p.add_argument("--layout", default="morton", choices=["input", "morton"],
                    help="storage order of the Gaussians: morton = hyrf_spatial_order once at load (a "
@@ -172,7 +175,7 @@ def run_ours(args):
     import torch
     from paper_2509_17083_gb300 import hyrf as H
     from paper_2509_17083_gb300 import synth
-    from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer
+    from paper_2509_17083_gb300.pipeline import DeviceModel, StepGraph, ViewRenderer
 
     ws, rank, local = dist_env()
     if not torch.cuda.is_available():
@@ -267,6 +270,12 @@ def run_ours(args):
         for _ in range(max(3, args.warmup)):
             timed_step(False)
         torch.cuda.synchronize()
+        # the step as one CUDA graph (the pipeline's StepGraph: zero_grad,
+        # forward with the loss, every reverse call), over a fixed target
+        sg = StepGraph(r, tgt) if args.graph else None
+        for _ in range(3 if sg else 0):
+            sg.replay()
+        torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
         l0 = H.launch_count()
@@ -279,14 +288,32 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            evs = timed_step(True)
+            if sg:
+                sg.replay()
+            else:
+                evs = timed_step(True)
             e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
+            if not sg:
+                for k, (a, b) in evs.items():
+                    ev[k].append(a.elapsed_time(b))
+        t_wall = time.perf_counter() - t_wall
+        launches = sg.launches * args.steps if sg else H.launch_count() - l0
+        # eager issue of the same step with stage marks: stage times, and the
+        # step time without the graph
+        eager_ms = []
+        for _ in range(max(3, args.steps // 2) if sg else 0):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            evs = timed_step(True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            eager_ms.append(e0.elapsed_time(e1))
             for k, (a, b) in evs.items():
                 ev[k].append(a.elapsed_time(b))
-        t_wall = time.perf_counter() - t_wall
-        launches = H.launch_count() - l0
         # the same steps again with the library's kernel timer on (CUDA events
         # around every launch, on its stream): per-kernel durations
         H.hyrf_timer_read()
@@ -304,42 +331,37 @@ def run_ours(args):
         ms = float(np.mean(step_ms))
         if ws > 1:
             ms = replica_max(ms, dev)
-        # render-only (forward, no backward), same flush protocol
-        fwd_ms = []
-        for _ in range(max(3, args.steps // 2)):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r.forward(None, want_keys=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            fwd_ms.append(e0.elapsed_time(e1))
-        # render-time background skip (tau_T = 0.2, the paper's value; BF16 only)
-        tau_ms = []
-        if prec == "bf16":
-            for _ in range(max(3, args.steps // 2)):
+        def render_ms(rr, tau_T=0.0):
+            """Mean forward-only time (render FPS), same flush protocol; the
+            forward replayed as one CUDA graph unless --no-graph."""
+            for _ in range(3):
+                rr.forward(None, want_keys=False, tau_T=tau_T)
+            g = StepGraph(rr, train=False, tau_T=tau_T) if args.graph else None
+            out = []
+            for i in range(3 + max(3, args.steps // 2)):
                 flush.fill_(1)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                r.forward(None, want_keys=False, tau_T=0.2)
+                if g:
+                    g.replay()
+                else:
+                    rr.forward(None, want_keys=False, tau_T=tau_T)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                tau_ms.append(e0.elapsed_time(e1))
+                if i >= 3:
+                    out.append(e0.elapsed_time(e1))
+            return float(np.mean(out))
+
+        # render-only (forward, no backward)
+        fwd_ms = [render_ms(r)]
+        # render-time background skip (tau_T = 0.2, the paper's value; BF16 only)
+        tau_ms = [render_ms(r, 0.2)] if prec == "bf16" else []
         # the 8-bit grid codec (render only)
         u8_ms = []
         if prec == "bf16":
             m.quantize_u8()
-            for _ in range(max(3, args.steps // 2)):
-                flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                r.forward(None, want_keys=False)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                u8_ms.append(e0.elapsed_time(e1))
+            u8_ms = [render_ms(r)]
             m.quantize_u8(False)
         # the IEEE-half render path (f16 grids and decoders), same scene
         f16_ms = []
@@ -350,21 +372,13 @@ def run_ours(args):
                 mf.spatial_order()
             rf = ViewRenderer(mf, wf.cams[0], wf.bg)
             rf.fit_capacity()
-            for _ in range(3):
-                rf.forward(None, want_keys=False)
-            for _ in range(max(3, args.steps // 2)):
-                flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                rf.forward(None, want_keys=False)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                f16_ms.append(e0.elapsed_time(e1))
+            f16_ms = [render_ms(rf)]
             del rf, mf
-        # end to end through the C ABI with host buffers: target H2D, loss D2H per step
+        # end to end through the pipeline API with host buffers: the step's
+        # target copied host -> device into the graph's target buffer, the
+        # step replayed, its loss copied device -> host
         pinned = torch.as_tensor(w.targets[0]).pin_memory()
-        dev_tgt = torch.empty_like(tgt)
+        dev_tgt = sg.target if sg else torch.empty_like(tgt)
         host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
         torch.cuda.synchronize()
         e2e_ms = []
@@ -373,17 +387,22 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             dev_tgt.copy_(pinned, non_blocking=True)
-            r.forward(dev_tgt, want_keys=False)
-            m.zero_grad()
-            r.backward()
+            if sg:
+                sg.replay()
+            else:
+                r.forward(dev_tgt, want_keys=False)
+                m.zero_grad()
+                r.backward()
             host_loss.copy_(r.loss, non_blocking=True)
             torch.cuda.synchronize()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        del sg
         stage_ms = {k: float(np.mean(v)) for k, v in ev.items() if v}
         C = r.C.float()
         psnr = float(-10.0 * torch.log10(((C - tgt) ** 2).mean()).item())
         evals = int(r.n_contrib.sum().item())
         results[prec] = dict(ms=ms, fwd_ms=float(np.mean(fwd_ms)), e2e_ms=float(np.mean(e2e_ms)),
+                             eager_ms=float(np.mean(eager_ms)) if eager_ms else None,
                              tau_ms=float(np.mean(tau_ms)) if tau_ms else None,
                              u8_ms=float(np.mean(u8_ms)) if u8_ms else None,
                              f16_ms=float(np.mean(f16_ms)) if f16_ms else None,
@@ -408,6 +427,8 @@ def run_ours(args):
     rf = R["kernels"].get("k_raster_fwd")
     out = {"metric": METRIC, "value": round(value, 3), "unit": "iters/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(R["ms"], 4),
+           "step_issue": "one CUDA graph per step" if args.graph else "eager",
+           "eager_ms_per_step": round(R["eager_ms"], 4) if R.get("eager_ms") else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": head, "gaussians": args.n,

@@ -169,36 +169,43 @@ __device__ __forceinline__ int col8(int lane) {
 // (division by 1 - alpha) and the colour composited behind it through
 // S = (colour behind) . dL/dC, so that
 //   dL/dalpha = (c . dL/dC - S) T - dL/dT_final T_final / (1 - alpha).
-// A thread holds P pixels of one column (rows r, r + 2, ..., r + 2(P - 1))
-// and WARPS warps share a tile; the x offset dx of a Gaussian is common to
+// A thread holds P pixels of one column (rows r, r + 2, ..., r + 2(P - 1));
+// a CTA of WARPS warps covers WARPS x 2P rows of a tile, so a tile takes
+// 16 / (2 P WARPS) CTAs (smaller CTAs leave less work in the last ones to
+// finish on each SM); the x offset dx of a Gaussian is common to
 // the thread's pixels, so the conic and mean gradients are accumulated as
 // sums D0 = sum dp, D1 = sum dp dy, D2 = sum dp dy^2 (dp = dL/dpower) and
 // expanded once per Gaussian before the warp reduction.
 #ifndef HYRF_RASTER_BWD_WARPS
 #define HYRF_RASTER_BWD_WARPS 4
 #endif
+#ifndef HYRF_RASTER_BWD_PIXELS
+#define HYRF_RASTER_BWD_PIXELS 2
+#endif
 constexpr int kBwdRasterWarps = HYRF_RASTER_BWD_WARPS;
-static_assert(kBwdRasterWarps == 1 || kBwdRasterWarps == 2 || kBwdRasterWarps == 4 || kBwdRasterWarps == 8,
-              "warps per tile must divide the 8 row pairs of a tile");
+constexpr int kBwdRasterPixels = HYRF_RASTER_BWD_PIXELS;
+static_assert(kTile % (2 * kBwdRasterWarps * kBwdRasterPixels) == 0,
+              "a CTA covers a whole number of row pairs of a tile");
+constexpr int kBwdCtasPerTile = kTile / (2 * kBwdRasterWarps * kBwdRasterPixels);
 
-template <int WARPS>
+template <int WARPS, int P>
 __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
     const float4* __restrict__ rec, int W, int H, int TX, const float* __restrict__ T_final,
     const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
     const float* __restrict__ dT, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
     float* __restrict__ d_alpha, float* __restrict__ d_color) {
-  constexpr int P = 8 / WARPS;       // pixels per thread
-  constexpr int NT = 32 * WARPS;     // threads per tile
+  constexpr int NT = 32 * WARPS;     // threads per CTA
+  constexpr int CPT = kTile / (2 * WARPS * P);  // CTAs per tile
   constexpr int B = 256;             // Gaussians staged per batch
   __shared__ float4 s0[B], s1[B];
   __shared__ float2 s2[B];
   __shared__ int sg[B];
   __shared__ int max_last;
-  const int tile = blockIdx.x;
+  const int tile = blockIdx.x / CPT, sub = blockIdx.x % CPT;
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int px = (tile % TX) * kTile + (lane & 15);
-  const int py0 = (tile / TX) * kTile + (kTile / WARPS) * wp + (lane >> 4);
+  const int py0 = (tile / TX) * kTile + (sub * WARPS + wp) * 2 * P + (lane >> 4);
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
   const float fx = (float)px + 0.5f;
   float fy[P], T[P], g0[P], g1[P], g2[P], gTf[P], S[P], la[P], ls[P];
@@ -350,7 +357,8 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
   HYRF_LAUNCH("k_raster_bwd", s,
-              k_raster_bwd<kBwdRasterWarps><<<TX * TY, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
+              k_raster_bwd<kBwdRasterWarps, kBwdRasterPixels>
+              <<<TX * TY * kBwdCtasPerTile, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
                                        a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
                                        b.d_alpha, b.d_color));
   return HYRF_OK;

@@ -372,6 +372,43 @@ class ViewRenderer:
         raise H.HyrfError("instance capacity could not be fitted")
 
 
+class StepGraph:
+    """One iteration of a view captured once as a CUDA graph: training
+    (model.zero_grad, forward with the loss over a fixed target buffer,
+    every reverse call) or, with train=False, the render-only forward
+    (tau_T as in ViewRenderer.forward). Every library call is asynchronous
+    on its stream and reads no host value, so the graph replays exactly the
+    eager work; replay() launches it on the current stream. Write each
+    step's target into .target (same shape, device) before replaying.
+    Capture after one eager iteration, so that capacities and workspaces
+    are settled; capture again after changing the model's storage (e.g. the
+    8-bit codes)."""
+
+    def __init__(self, renderer, target=None, train=True, zero_grad=True, want_keys=False, tau_T=0.0):
+        if train and target is None:
+            raise ValueError("a training step needs a target buffer")
+        self.r = renderer
+        self.target = target
+        self.graph = torch.cuda.CUDAGraph()
+        main = torch.cuda.current_stream()
+        cap = torch.cuda.Stream(device=renderer.C.device)
+        cap.wait_stream(main)
+        n0 = H.launch_count()
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(self.graph, stream=cap):
+                if train and zero_grad:
+                    renderer.m.zero_grad()
+                renderer.forward(target if train else None, want_keys=want_keys, tau_T=tau_T)
+                if train:
+                    renderer.backward()
+        main.wait_stream(cap)
+        self.launches = H.launch_count() - n0  # library kernels per replay
+
+    def replay(self):
+        self.graph.replay()
+        return self.r.loss
+
+
 class Trainer:
     """Training iterations of several views with the fused Adam update
     (hyrf_adam_step). The gradients of all views are accumulated, averaged

@@ -111,3 +111,46 @@ def test_two_iterations_are_identical_in_integers():
     assert np.array_equal(np_(r.keys)[:n1], k1[:n1])
     assert np.array_equal(np_(r.vals)[:n1], v1[:n1])
     assert np.array_equal(np_(r.ranges), rg1)
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_step_graph_replays_the_eager_step(precision):
+    """The training iteration captured as one CUDA graph (StepGraph): a
+    replay gives the eager step's image and integers exactly and its
+    gradients up to the order of float atomics; a new target written into
+    the graph's buffer is used by the next replay."""
+    from paper_2509_17083_gb300.pipeline import StepGraph
+    w = synth.config3(n=30000, width=301, height=203, log2_T=15, n_clusters=32, precision=precision,
+                      table_init=0.3)
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+    tgt = cuda_f32(w.targets[0])
+    r.fit_capacity(tgt)
+    r.status.zero_()
+    m.zero_grad()
+    r.forward(tgt, want_keys=False)
+    r.backward()
+    torch.cuda.synchronize()
+    img, nc, loss = np_(r.C).copy(), np_(r.n_contrib).copy(), float(r.loss.item())
+    ref = {k: np_(v).copy() for k, v in m.grad.items() if not isinstance(v, list)}
+    sg = StepGraph(r, tgt)
+    assert sg.launches > 20
+    for _ in range(2):
+        r.C.zero_()
+        sg.replay()
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    assert np.array_equal(np_(r.C), img)
+    assert np.array_equal(np_(r.n_contrib), nc)
+    assert abs(float(r.loss.item()) - loss) <= 1e-6 * abs(loss)
+    for k, v in ref.items():
+        assert rel_l2(np_(m.grad[k]), v) < 1e-4, k
+    # a new target through the graph's buffer
+    t2 = torch.rand_like(tgt)
+    sg.target.copy_(t2)
+    sg.replay()
+    torch.cuda.synchronize()
+    l2 = float(r.loss.item())
+    r.forward(t2, want_keys=False)
+    torch.cuda.synchronize()
+    assert abs(float(r.loss.item()) - l2) <= 1e-6 * abs(l2)
