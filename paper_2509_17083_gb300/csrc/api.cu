@@ -43,7 +43,7 @@ hyrf_status launch_bg_bwd(const hyrf_composite_background_backward_args& b, cons
                           void* ws, cudaStream_t s);
 size_t bin_sort_workspace(int n, int64_t cap);
 hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t s);
-size_t raster_workspace(int n);
+size_t raster_workspace(int n, int width, int height, bool reverse);
 hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream_t s);
 hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, cudaStream_t s);
 size_t loss_workspace(const hyrf_loss_args& a);
@@ -323,7 +323,7 @@ static hyrf_status raster_check(const hyrf_rasterize_args* a) {
 }
 
 size_t hyrf_rasterize_workspace_size(const hyrf_rasterize_args* a) {
-  return a ? raster_workspace(a->n) : 0;
+  return a ? raster_workspace(a->n, a->width, a->height, false) : 0;
 }
 
 hyrf_status hyrf_rasterize(const hyrf_rasterize_args* a, void* ws, size_t ws_bytes, void* stream) {
@@ -334,7 +334,7 @@ hyrf_status hyrf_rasterize(const hyrf_rasterize_args* a, void* ws, size_t ws_byt
 }
 
 size_t hyrf_rasterize_backward_workspace_size(const hyrf_rasterize_backward_args* a) {
-  return a ? raster_workspace(a->fwd.n) : 0;
+  return a ? raster_workspace(a->fwd.n, a->fwd.width, a->fwd.height, true) : 0;
 }
 
 hyrf_status hyrf_rasterize_backward(const hyrf_rasterize_backward_args* a, void* ws, size_t ws_bytes,

@@ -10,7 +10,8 @@
 // reverse walks each pixel's list back to front, recovering T from the
 // stored T_final by division, with several pixels of one column per thread,
 // reduces the per-Gaussian gradients across each warp and adds them with
-// atomics.
+// atomics; its CTAs take the tiles in decreasing order of their longest
+// pixel list, so that the last CTAs to run on each SM are short ones.
 #include "common.cuh"
 
 namespace hyrf {
@@ -191,8 +192,8 @@ constexpr int kBwdCtasPerTile = kTile / (2 * kBwdRasterWarps * kBwdRasterPixels)
 template <int WARPS, int P>
 __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
-    const float4* __restrict__ rec, int W, int H, int TX, const float* __restrict__ T_final,
-    const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
+    const float4* __restrict__ rec, int W, int H, int TX, const int32_t* __restrict__ order,
+    const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
     const float* __restrict__ dT, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
     float* __restrict__ d_alpha, float* __restrict__ d_color) {
   constexpr int NT = 32 * WARPS;     // threads per CTA
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
   __shared__ float2 s2[B];
   __shared__ int sg[B];
   __shared__ int max_last;
-  const int tile = blockIdx.x / CPT, sub = blockIdx.x % CPT;
+  const int tile = order[blockIdx.x / CPT], sub = blockIdx.x % CPT;
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int px = (tile % TX) * kTile + (lane & 15);
   const int py0 = (tile / TX) * kTile + (sub * WARPS + wp) * 2 * P + (lane >> 4);
@@ -322,10 +323,74 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
 
 // ---------------------------------------------------------------- host side
 
-size_t raster_workspace(int n) {
+size_t raster_workspace(int n, int width, int height, bool reverse) {
   Carver c(nullptr);
   c.take<float4>((size_t)3 * (n > 0 ? n : 1));
+  if (reverse) {
+    const int64_t tiles = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
+    c.take<int32_t>(2 * (size_t)(tiles > 0 ? tiles : 1));  // work key, order
+  }
   return c.size();
+}
+
+// Work class of each tile for the reverse: the bit length of its longest
+// pixel list (the reverse walks every pixel's list from its end).
+__global__ void __launch_bounds__(256) k_tile_work(const int32_t* __restrict__ n_contrib, int W, int H, int TX,
+                                                   int32_t* __restrict__ key) {
+  __shared__ int wmax[8];
+  const int tile = blockIdx.x, t = threadIdx.x;
+  const int px = (tile % TX) * kTile + (t % kTile), py = (tile / TX) * kTile + (t / kTile);
+  const int v = (px < W && py < H) ? n_contrib[py * W + px] : 0;
+  const int m = __reduce_max_sync(0xffffffffu, v);
+  if ((t & 31) == 0) wmax[t >> 5] = m;
+  __syncthreads();
+  if (t == 0) {
+    int mm = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mm = max(mm, wmax[i]);
+    key[tile] = mm > 0 ? __clz(mm) : 32;  // smaller key = more work
+  }
+}
+
+// Tiles ordered by increasing key (bucket sort over 33 classes, one CTA;
+// the order inside a class is that of the atomics and does not matter: the
+// tiles are independent).
+__global__ void __launch_bounds__(1024) k_tile_order(const int32_t* __restrict__ key, int ntiles,
+                                                     int32_t* __restrict__ order) {
+  __shared__ int cnt[33], off[33];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int rounds = (ntiles + 1023) / 1024;
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * 1024 + threadIdx.x;
+    const bool ok = t < ntiles;
+    const int k = ok ? min(max(key[t], 0), 32) : 0;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    const unsigned peers = __match_any_sync(0xffffffffu, ok ? k : 64 + lane) & act;
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt[k], __popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < 33; ++k) {
+      off[k] = run;
+      run += cnt[k];
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * 1024 + threadIdx.x;
+    const bool ok = t < ntiles;
+    const int k = ok ? min(max(key[t], 0), 32) : 0;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    const unsigned peers = __match_any_sync(0xffffffffu, ok ? k : 64 + lane) & act;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (ok && lane == leader) base = atomicAdd(&off[k], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, ok ? leader : lane);
+    if (ok) order[base + __popc(peers & ((1u << lane) - 1u))] = t;
+  }
 }
 
 static hyrf_status pack(const hyrf_rasterize_args& a, float4* rec, cudaStream_t s) {
@@ -354,11 +419,15 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   const int TX = (a.width + kTile - 1) / kTile, TY = (a.height + kTile - 1) / kTile;
   Carver c(ws);
   float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
+  int32_t* key = c.take<int32_t>((size_t)TX * TY);
+  int32_t* order = c.take<int32_t>((size_t)TX * TY);
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
+  HYRF_LAUNCH("k_tile_work", s, k_tile_work<<<TX * TY, 256, 0, s>>>(a.n_contrib, a.width, a.height, TX, key));
+  HYRF_LAUNCH("k_tile_order", s, k_tile_order<<<1, 1024, 0, s>>>(key, TX * TY, order));
   HYRF_LAUNCH("k_raster_bwd", s,
               k_raster_bwd<kBwdRasterWarps, kBwdRasterPixels>
-              <<<TX * TY * kBwdCtasPerTile, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.T_final,
+              <<<TX * TY * kBwdCtasPerTile, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, order, a.T_final,
                                        a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
                                        b.d_alpha, b.d_color));
   return HYRF_OK;
