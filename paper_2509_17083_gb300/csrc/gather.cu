@@ -248,21 +248,30 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
   float f[3];
   level_cell(A, l, y, idx, f);
   float g[3] = {0.0f, 0.0f, 0.0f};
+  // dL/dy first: the corner values of both tables are loaded together (one
+  // round trip), not each behind the previous corner's atomics
+  if (!zero) {
+    float dot[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const size_t e = (size_t)l * A.T + idx[c];
-    const float w = corner_w(f, c);
-    run_atomic2(ga, gb, e, idx[c], w * da.x, w * da.y, w * db.x, w * db.y);
-    if (!zero) {
+    for (int c = 0; c < 8; ++c) {
+      const size_t e = (size_t)l * A.T + idx[c];
       const float2 va = load_entry_t<DT>(A, e), vb = load_entry_t<DT>(B, e);
-      const float dot = va.x * da.x + va.y * da.y + (vb.x * db.x + vb.y * db.y);
+      dot[c] = va.x * da.x + va.y * da.y + (vb.x * db.x + vb.y * db.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
       const float wx = (c & 1) ? f[0] : 1.0f - f[0];
       const float wy = (c & 2) ? f[1] : 1.0f - f[1];
       const float wz = (c & 4) ? f[2] : 1.0f - f[2];
-      g[0] += dot * ((c & 1) ? 1.0f : -1.0f) * wy * wz;
-      g[1] += dot * ((c & 2) ? 1.0f : -1.0f) * wx * wz;
-      g[2] += dot * ((c & 4) ? 1.0f : -1.0f) * wx * wy;
+      g[0] += dot[c] * ((c & 1) ? 1.0f : -1.0f) * wy * wz;
+      g[1] += dot[c] * ((c & 2) ? 1.0f : -1.0f) * wx * wz;
+      g[2] += dot[c] * ((c & 4) ? 1.0f : -1.0f) * wx * wy;
     }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = corner_w(f, c);
+    run_atomic2(ga, gb, (size_t)l * A.T + idx[c], idx[c], w * da.x, w * da.y, w * db.x, w * db.y);
   }
   const float N = (float)A.res[l];
   dy[0] = g[0] * N;
