@@ -212,13 +212,11 @@ def run_ours(args):
             raise
         stream = torch.cuda.current_stream()
         names = ["query_fwd", "project_fwd", "bin_sort", "raster_fwd", "bg_fwd", "loss",
-                 "bg_bwd", "raster_bwd", "project_bwd", "query_bwd"]
+                 "render_bwd", "query_bwd"]
         ev = {k: [] for k in names}
 
         def timed_step(record):
             m.zero_grad()
-            for t in (r.d_mean2d, r.d_conic, r.d_alpha, r.d_color):
-                t.zero_()
             evs = {}
 
             def mark(k):
@@ -247,22 +245,12 @@ def run_ours(args):
             mark("bg_fwd"); mark("loss")
             r.loss_fn(tgt)
             mark("loss")
-            g = m.grads_struct()
-            mark("bg_bwd")
-            H.hyrf_composite_background_backward(r._bg_args(), ws=r.ws["bb"], d_C=r.dC, d_C_fg=None,
-                                                 d_T_final=r.dT, grads=g, loss_scale=r.loss_scale,
-                                                 scatter_stream=r._side_handle())
-            mark("bg_bwd"); mark("raster_bwd")
-            H.hyrf_rasterize_backward(r._raster_args(), ws=r.ws["rb"], d_C_fg=r.dC, d_T_final=r.dT,
-                                      d_mean2d=r.d_mean2d, d_conic=r.d_conic, d_alpha=r.d_alpha,
-                                      d_color=r.d_color)
-            mark("raster_bwd"); mark("project_bwd")
-            H.hyrf_project_backward(n=m.n, pos=m.pos, vis_ids=r.vis_ids, n_vis=r.n_vis,
-                                    scale=r.scale, quat=r.quat, cam=r.ccam, d_mean2d=r.d_mean2d,
-                                    d_conic=r.d_conic, d_pos=m.grad["pos"], d_scale=r.d_scale,
-                                    d_quat=r.d_quat, status=r.status)
-            mark("project_bwd"); mark("query_bwd")
-            H.hyrf_query_fields_backward(ws=r.ws["qb"], **r.query_backward_kwargs())
+            # reverse of background, compositing and projection (the
+            # background's on the second stream), then of the field query
+            mark("render_bwd")
+            r.backward_render()
+            mark("render_bwd"); mark("query_bwd")
+            r.backward_fields()
             r.join()
             mark("query_bwd")
             return evs

@@ -344,11 +344,19 @@ hyrf_status hyrf_rasterize(const hyrf_rasterize_args* a, void* workspace, size_t
 typedef struct {
   hyrf_rasterize_args fwd;   /* the forward's arguments; its outputs are inputs here */
   const float* d_C_fg;       /* [H][W][3] */
-  const float* d_T_final;    /* [H][W] */
+  const float* d_T_final;    /* [H][W], or NULL with C below */
   float* d_mean2d;           /* accumulate [V][2] */
   float* d_conic;            /* accumulate [V][3] */
   float* d_alpha;            /* accumulate [V] */
   float* d_color;            /* accumulate [V][3] */
+  /* Optional (used when d_T_final is NULL): the composited image C of
+   * hyrf_composite_background, [H][W][3]. Eq. 11 gives C - C_fg =
+   * T_final c_s, so dL/dT_final T_final = dL/dC . (C - C_fg) per pixel
+   * (d_C_fg = dL/dC) and this call need not wait for the background's
+   * reverse, which may then run on another stream with its d_T_final
+   * NULL. The product is formed from the rounded C (absolute error of a
+   * few ulp of C). */
+  const float* C;
 } hyrf_rasterize_backward_args;
 
 size_t hyrf_rasterize_backward_workspace_size(const hyrf_rasterize_backward_args* a);
@@ -405,14 +413,18 @@ hyrf_status hyrf_gather_background(const hyrf_composite_background_args* a, void
 hyrf_status hyrf_composite_background(const hyrf_composite_background_args* a, void* workspace,
                                       size_t ws_bytes, void* stream);
 
-/* Reverse: dL/dC -> dL/dT_final (out), dL/dC_fg (out, = dL/dC; may be NULL
+/* Reverse: dL/dC -> dL/dT_final (out; may be NULL when the compositing
+ * reverse takes the composited image instead, see
+ * hyrf_rasterize_backward_args.C), dL/dC_fg (out, = dL/dC; may be NULL
  * when the caller passes dL/dC on as dL/dC_fg) and the radiance-field and
- * colour-decoder gradients (accumulate, into grads.rad_table / col_*). */
+ * colour-decoder gradients (accumulate, into grads.rad_table / col_*;
+ * decoder gradients are added atomically, so another call accumulating
+ * into the same buffers may run concurrently on another stream). */
 typedef struct {
   hyrf_composite_background_args fwd;
   const float* d_C;          /* [H][W][3] */
   float* d_C_fg;             /* out [H][W][3], may be NULL */
-  float* d_T_final;          /* out [H][W] */
+  float* d_T_final;          /* out [H][W], may be NULL */
   hyrf_field_grads grads;    /* accumulate */
   float loss_scale;
   /* Optional (BF16 exact mode): a second stream for the radiance-table

@@ -342,7 +342,7 @@ hyrf_status hyrf_rasterize_backward(const hyrf_rasterize_backward_args* a, void*
   if (!a) return HYRF_ERR_INVALID_ARG;
   hyrf_status st = raster_check(&a->fwd);
   if (st != HYRF_OK) return st;
-  if (!a->d_C_fg || !a->d_T_final) return HYRF_ERR_INVALID_ARG;
+  if (!a->d_C_fg || (!a->d_T_final && !a->C)) return HYRF_ERR_INVALID_ARG;
   if (a->fwd.n > 0 && (!a->d_mean2d || !a->d_conic || !a->d_alpha || !a->d_color))
     return HYRF_ERR_INVALID_ARG;
   if (!ws_ok(ws, ws_bytes, hyrf_rasterize_backward_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
@@ -410,7 +410,7 @@ hyrf_status hyrf_composite_background_backward(const hyrf_composite_background_b
   FieldsDev F;
   hyrf_status st = bg_check(&b->fwd, F);
   if (st != HYRF_OK) return st;
-  if (!b->d_C || !b->d_T_final || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
+  if (!b->d_C || !(b->loss_scale > 0.0f)) return HYRF_ERR_INVALID_ARG;
   if (b->fwd.bg.mode == 2) return launch_bg_none_bwd(*b, S(stream));
   if (b->fwd.bg.tau_T > 0.0f) return HYRF_ERR_INVALID_ARG;  // render-only rule
   if (F.rad.u8 || F.rad.f16 || F.cm.f16) return HYRF_ERR_UNSUPPORTED;  // render-only types

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_bg_none(int64_t m, const float* __restr
 __global__ void __launch_bounds__(256) k_bg_none_bwd(int64_t P, const float* __restrict__ dC,
                                                      float* __restrict__ dC_fg, float* __restrict__ dT) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-    dT[i] = 0.0f;
+    if (dT) dT[i] = 0.0f;
     if (dC_fg) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) dC_fg[3 * i + k] = dC[3 * i + k];

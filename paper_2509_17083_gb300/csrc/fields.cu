@@ -308,7 +308,7 @@ __global__ void k_slab_reduce(const float* __restrict__ slabs, int nslabs, SlabL
     if (!dst) continue;
     float s = 0.0f;
     for (int c = 0; c < nslabs; ++c) s += slabs[(size_t)c * SL.total + e];
-    *dst += s * scale;
+    atomicAdd(dst, s * scale);  // other reverse calls may add into the same weights concurrently
   }
 }
 #endif
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256) k_bg_map_bwd_pix(FieldsDev F, CamDev cam,
       dt += g[k] * cs[k];
       if (dC_fg) dC_fg[3 * (int64_t)p + k] = g[k];
     }
-    dT[p] = dt;
+    if (dT) dT[p] = dt;
 #pragma unroll
     for (int ka = 0; ka < 2; ++ka)
 #pragma unroll
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
         dcs[k] = g * T;
         if (ok && dC_fg) dC_fg[3 * (int64_t)ee + k] = g;
       }
-      if (ok) dT[ee] = dt;
+      if (ok && dT) dT[ee] = dt;
     } else {
 #pragma unroll
       for (int k = 0; k < 3; ++k) dcs[k] = ok ? dmap[3 * ee + k] : 0.0f;

@@ -300,7 +300,7 @@ struct BgPixel {
       dz[k] = R.g[k] * R.T * cs * (1.0f - cs);
     }
     if (R.ok) {
-      P.dT[R.p] = dt;
+      if (P.dT) P.dT[R.p] = dt;
       if (P.dC_fg) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) P.dC_fg[3 * (int64_t)R.p + k] = R.g[k];

@@ -194,8 +194,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     const int32_t* __restrict__ ranges, const int32_t* __restrict__ vals, int n,
     const float4* __restrict__ rec, int W, int H, int TX, const int32_t* __restrict__ order,
     const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
-    const float* __restrict__ dT, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
-    float* __restrict__ d_alpha, float* __restrict__ d_color) {
+    const float* __restrict__ dT, const float* __restrict__ Cimg, const float* __restrict__ C_fg,
+    float* __restrict__ d_mean2d, float* __restrict__ d_conic, float* __restrict__ d_alpha,
+    float* __restrict__ d_color) {
   constexpr int NT = 32 * WARPS;     // threads per CTA
   constexpr int CPT = kTile / (2 * WARPS * P);  // CTAs per tile
   constexpr int B = 256;             // Gaussians staged per batch
@@ -224,7 +225,14 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     g0[k] = inside ? dC[3 * p] : 0.0f;
     g1[k] = inside ? dC[3 * p + 1] : 0.0f;
     g2[k] = inside ? dC[3 * p + 2] : 0.0f;
-    gTf[k] = (inside ? dT[p] : 0.0f) * Tf;
+    if (!inside) {
+      gTf[k] = 0.0f;
+    } else if (dT) {
+      gTf[k] = dT[p] * Tf;
+    } else {  // dL/dT_final T_final = dL/dC . (C - C_fg), Eq. 11
+      gTf[k] = g0[k] * (Cimg[3 * p] - C_fg[3 * p]) + g1[k] * (Cimg[3 * p + 1] - C_fg[3 * p + 1]) +
+               g2[k] * (Cimg[3 * p + 2] - C_fg[3 * p + 2]);
+    }
     S[k] = la[k] = ls[k] = 0.0f;
     mylast = max(mylast, last[k]);
   }
@@ -428,8 +436,8 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   HYRF_LAUNCH("k_raster_bwd", s,
               k_raster_bwd<kBwdRasterWarps, kBwdRasterPixels>
               <<<TX * TY * kBwdCtasPerTile, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, order, a.T_final,
-                                       a.n_contrib, b.d_C_fg, b.d_T_final, b.d_mean2d, b.d_conic,
-                                       b.d_alpha, b.d_color));
+                                       a.n_contrib, b.d_C_fg, b.d_T_final, b.C, a.C_fg, b.d_mean2d,
+                                       b.d_conic, b.d_alpha, b.d_color));
   return HYRF_OK;
 }
 

@@ -101,7 +101,7 @@ class hyrf_rasterize_args(C.Structure):
 
 class hyrf_rasterize_backward_args(C.Structure):
     _fields_ = [("fwd", hyrf_rasterize_args), ("d_C_fg", _vp), ("d_T_final", _vp),
-                ("d_mean2d", _vp), ("d_conic", _vp), ("d_alpha", _vp), ("d_color", _vp)]
+                ("d_mean2d", _vp), ("d_conic", _vp), ("d_alpha", _vp), ("d_color", _vp), ("C", _vp)]
 
 
 class hyrf_background(C.Structure):

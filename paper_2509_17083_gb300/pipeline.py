@@ -236,9 +236,6 @@ class ViewRenderer:
                         features=self.feat_b))
         return a
 
-    def _side_handle(self):
-        return self.side.cuda_stream if self._overlap() else None
-
     def query_kwargs(self):
         """Arguments of hyrf_query_fields for this view."""
         m = self.m
@@ -329,13 +326,25 @@ class ViewRenderer:
         for t in (self.d_mean2d, self.d_conic, self.d_alpha, self.d_color):
             t.zero_()
         g = m.grads_struct()
-        H.hyrf_composite_background_backward(self._bg_args(), ws=self.ws["bb"], d_C=self.dC,
-                                             d_C_fg=None, d_T_final=self.dT, grads=g,
-                                             loss_scale=self.loss_scale,
-                                             scatter_stream=self._side_handle())
-        H.hyrf_rasterize_backward(self._raster_args(), ws=self.ws["rb"], d_C_fg=self.dC,
-                                  d_T_final=self.dT, d_mean2d=self.d_mean2d, d_conic=self.d_conic,
-                                  d_alpha=self.d_alpha, d_color=self.d_color)
+        if self._overlap():
+            # the background's whole reverse on the side stream, concurrently
+            # with the compositing reverse, which takes dL/dT_final T_final
+            # from the composited image (C - C_fg = T_final c_s, Eq. 11)
+            # instead of waiting for the background's dL/dT_final
+            self.side.wait_stream(torch.cuda.current_stream())
+            H.hyrf_composite_background_backward(self._bg_args(), ws=self.ws["bb"], stream=self.side,
+                                                 d_C=self.dC, d_C_fg=None, d_T_final=None, grads=g,
+                                                 loss_scale=self.loss_scale)
+            H.hyrf_rasterize_backward(self._raster_args(), ws=self.ws["rb"], d_C_fg=self.dC,
+                                      d_T_final=None, C=self.C, d_mean2d=self.d_mean2d,
+                                      d_conic=self.d_conic, d_alpha=self.d_alpha, d_color=self.d_color)
+        else:
+            H.hyrf_composite_background_backward(self._bg_args(), ws=self.ws["bb"], d_C=self.dC,
+                                                 d_C_fg=None, d_T_final=self.dT, grads=g,
+                                                 loss_scale=self.loss_scale)
+            H.hyrf_rasterize_backward(self._raster_args(), ws=self.ws["rb"], d_C_fg=self.dC,
+                                      d_T_final=self.dT, d_mean2d=self.d_mean2d, d_conic=self.d_conic,
+                                      d_alpha=self.d_alpha, d_color=self.d_color)
         H.hyrf_project_backward(ws=self.ws["p"], n=m.n, pos=m.pos, vis_ids=self.vis_ids,
                                 n_vis=self.n_vis, scale=self.scale, quat=self.quat, cam=self.ccam,
                                 d_mean2d=self.d_mean2d, d_conic=self.d_conic, d_pos=m.grad["pos"],

@@ -154,3 +154,54 @@ def test_step_graph_replays_the_eager_step(precision):
     r.forward(t2, want_keys=False)
     torch.cuda.synchronize()
     assert abs(float(r.loss.item()) - l2) <= 1e-6 * abs(l2)
+
+
+def test_background_reverse_beside_compositing_reverse():
+    """The pipeline's overlapped reverse (background reverse on the second
+    stream with d_T_final NULL, compositing reverse from the composited
+    image, C - C_fg = T_final c_s) against the sequential one (the
+    background's dL/dT_final into the compositing reverse, its table
+    scatter forked onto the second stream through scatter_stream)."""
+    w = synth.config3(n=30000, width=301, height=203, log2_T=15, n_clusters=32, precision="bf16",
+                      table_init=0.3)
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+    assert r._overlap()
+    tgt = cuda_f32(w.targets[0])
+    r.fit_capacity(tgt)
+    r.status.zero_()
+    m.zero_grad()
+    r.forward(tgt, want_keys=False)
+    r.backward()
+    torch.cuda.synchronize()
+    got = {k: np_(v).copy() for k, v in m.grad.items() if not isinstance(v, list)}
+    got["col_W0"] = np_(m.grad["col_W"][0]).copy()
+    img = {k: np_(getattr(r, k)).copy() for k in ("d_mean2d", "d_conic", "d_alpha", "d_color")}
+    # sequential reference
+    m.zero_grad()
+    for t in (r.d_mean2d, r.d_conic, r.d_alpha, r.d_color):
+        t.zero_()
+    g = m.grads_struct()
+    H.hyrf_composite_background_backward(r._bg_args(), ws=r.ws["bb"], d_C=r.dC, d_C_fg=None,
+                                         d_T_final=r.dT, grads=g, loss_scale=r.loss_scale,
+                                         scatter_stream=r.side.cuda_stream)
+    H.hyrf_rasterize_backward(r._raster_args(), ws=r.ws["rb"], d_C_fg=r.dC, d_T_final=r.dT,
+                              d_mean2d=r.d_mean2d, d_conic=r.d_conic, d_alpha=r.d_alpha, d_color=r.d_color)
+    H.hyrf_project_backward(ws=r.ws["p"], n=m.n, pos=m.pos, vis_ids=r.vis_ids, n_vis=r.n_vis, scale=r.scale,
+                            quat=r.quat, cam=r.ccam, d_mean2d=r.d_mean2d, d_conic=r.d_conic,
+                            d_pos=m.grad["pos"], d_scale=r.d_scale, d_quat=r.d_quat, status=r.status)
+    r.backward_fields()
+    torch.cuda.current_stream().wait_stream(r.side)
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    for k, v in img.items():
+        assert rel_l2(v, np_(getattr(r, k))) < 1e-4, k
+    ref = {k: np_(v) for k, v in m.grad.items() if not isinstance(v, list)}
+    ref["col_W0"] = np_(m.grad["col_W"][0])
+    for k, v in ref.items():
+        assert rel_l2(got[k], v) < 1e-4, k
+    # a reverse with neither d_T_final nor the image is refused
+    with pytest.raises(H.HyrfError):
+        H.hyrf_rasterize_backward(r._raster_args(), ws=r.ws["rb"], d_C_fg=r.dC, d_T_final=None,
+                                  d_mean2d=r.d_mean2d, d_conic=r.d_conic, d_alpha=r.d_alpha,
+                                  d_color=r.d_color)
