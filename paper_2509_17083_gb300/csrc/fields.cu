@@ -294,8 +294,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
 
 
 #if HYRF_FIELDS_PART == 0
+// Element e of every slab, summed over the slab range of this CTA row
+// (blockIdx.y of gridDim.y parts) and added atomically to the target: the
+// parts and other reverse calls accumulating into the same weights add in
+// any order.
 __global__ void k_slab_reduce(const float* __restrict__ slabs, int nslabs, SlabLayout SL,
                               SlabTargets T, float scale) {
+  const int per = (nslabs + gridDim.y - 1) / gridDim.y;
+  const int c0 = blockIdx.y * per, c1 = min(nslabs, c0 + per);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < SL.total; e += gridDim.x * blockDim.x) {
     float* dst = nullptr;
     for (int d = 0; d < 2; ++d)
@@ -307,8 +313,8 @@ __global__ void k_slab_reduce(const float* __restrict__ slabs, int nslabs, SlabL
       }
     if (!dst) continue;
     float s = 0.0f;
-    for (int c = 0; c < nslabs; ++c) s += slabs[(size_t)c * SL.total + e];
-    atomicAdd(dst, s * scale);  // other reverse calls may add into the same weights concurrently
+    for (int c = c0; c < c1; ++c) s += slabs[(size_t)c * SL.total + e];
+    if (c1 > c0) atomicAdd(dst, s * scale);
   }
 }
 #endif
@@ -686,8 +692,10 @@ SlabTargets slab_targets(const hyrf_field_grads& g, bool geo) {
 
 hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout& SL,
                                const SlabTargets& T, float scale, cudaStream_t s) {
-  HYRF_LAUNCH("k_slab_reduce", s,
-              k_slab_reduce<<<64, 256, 0, s>>>(slabs, nslabs, SL, T, scale));
+  if (SL.total <= 0 || nslabs <= 0) return HYRF_OK;
+  // columns of 256 elements x 8 parts of the slab range
+  const dim3 grid((SL.total + 255) / 256, 8);
+  HYRF_LAUNCH("k_slab_reduce", s, k_slab_reduce<<<grid, 256, 0, s>>>(slabs, nslabs, SL, T, scale));
   return HYRF_OK;
 }
 

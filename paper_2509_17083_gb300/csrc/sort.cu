@@ -314,6 +314,43 @@ __device__ __forceinline__ int last_le(const A& a, int lo, int hi, uint32_t e) {
   return lo;
 }
 
+// last_le of two values at once by the whole CTA: threads [0, 128) search
+// v[0], threads [128, 256) v[1], each round probing 128 evenly spaced
+// positions of the current interval (three rounds for two million entries,
+// instead of twenty dependent loads). Result in res[0], res[1].
+__device__ __forceinline__ void last_le2_cta(const uint32_t* __restrict__ a, int n, uint32_t v0, uint32_t v1,
+                                             int* res) {
+  __shared__ int lo[2], hi[2], best[2];
+  const int t = threadIdx.x, q = t >> 7, i = t & 127;
+  if (t < 2) {
+    lo[t] = 0;
+    hi[t] = n - 1;
+  }
+  __syncthreads();
+  for (;;) {
+    const int l = lo[q], h = hi[q];
+    const bool more = h > l;
+    if (i == 0) best[q] = 0;
+    __syncthreads();
+    if (more) {
+      const int64_t span = (int64_t)h - l + 1;
+      const int pos = l + (int)(span * i / 128);
+      if (a[pos] <= (q ? v1 : v0)) atomicMax(&best[q], i);
+    }
+    __syncthreads();
+    if (i == 0 && more) {
+      const int64_t span = (int64_t)h - l + 1;
+      const int b = best[q];
+      lo[q] = l + (int)(span * b / 128);
+      hi[q] = b < 127 ? l + (int)(span * (b + 1) / 128) - 1 : h;
+      if (hi[q] < lo[q]) hi[q] = lo[q];
+    }
+    __syncthreads();
+    if (lo[0] == hi[0] && lo[1] == hi[1]) break;  // CTA-uniform
+  }
+  if (t < 2) res[t] = lo[t];
+}
+
 constexpr int kExpandItems = 2048;  // instances per CTA
 constexpr int kExpandSlice = 2048;  // sorted Gaussians cached per CTA
 
@@ -339,10 +376,7 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
   if (e0 >= K || n == 0) return;  // CTA-uniform
   const int e1 = (int)(e0 + kExpandItems < K ? e0 + kExpandItems : K);
   const int t = threadIdx.x;
-  if (t == 0) {
-    range[0] = last_le(off, 0, n - 1, (uint32_t)e0);
-    range[1] = last_le(off, range[0], n - 1, (uint32_t)(e1 - 1));
-  }
+  last_le2_cta(off, n, (uint32_t)e0, (uint32_t)(e1 - 1), range);
   __syncthreads();
   const int jlo = range[0], jhi = range[1];
   const int L = jhi - jlo + 1;
