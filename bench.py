@@ -302,8 +302,13 @@ def run_ours(args):
             eager_ms.append(e0.elapsed_time(e1))
             for k, (a, b) in evs.items():
                 ev[k].append(a.elapsed_time(b))
-        # the same steps again with the library's kernel timer on (CUDA events
-        # around every launch, on its stream): per-kernel durations
+        # the same steps again, every call on one stream (so that no kernel
+        # shares the GPU with another), with the library's kernel timer on
+        # (CUDA events around every launch, on its stream): per-kernel
+        # durations
+        r.serial = True
+        for _ in range(3):
+            timed_step(False)
         H.hyrf_timer_read()
         H.hyrf_timer_enable(True)
         for _ in range(args.steps):
@@ -311,6 +316,7 @@ def run_ours(args):
             timed_step(False)
         torch.cuda.synchronize()
         H.hyrf_timer_enable(False)
+        r.serial = False
         ktimes = H.hyrf_timer_read()
         clocks = sampler.stop() if prec == precisions[0] else None
         st = H.read_status(r.status)
@@ -465,7 +471,8 @@ NCU_TRAFFIC = {
 
 def roofline(R, peaks, prec):
     """Roofline of the kernel with the largest time per step, from the
-    library's own CUDA-event kernel timer over the timed region."""
+    library's own CUDA-event kernel timer over the steps of the timer pass
+    (the timed step's calls, issued on one stream)."""
     hbm = peaks.get("hbm_gbs")
     src = "of measured" if hbm else "of fallback"
     hbm = hbm or 6800.0

@@ -196,6 +196,7 @@ class ViewRenderer:
         # second stream: the background's feature gather ahead of the
         # foreground, and its table-gradient scatter behind it
         self.side = torch.cuda.Stream(device=d) if str(d).startswith("cuda") else None
+        self.serial = False
         if self.save_features:
             self.feat_q = torch.empty(2 * max(n, 1) * 32, dtype=torch.bfloat16, device=d)
             if int(bg.mode) == 0 and self.background:
@@ -260,8 +261,9 @@ class ViewRenderer:
                     explicit_only=0 if self.neural else 1)
 
     def _overlap(self, tau_T=0.0):
-        """The background features can be gathered on the side stream."""
-        return self.feat_b is not None and self.side is not None and tau_T == 0.0
+        """The background's gather and reverse can run on the side stream
+        (unless .serial is set: everything on the caller's stream)."""
+        return self.feat_b is not None and self.side is not None and tau_T == 0.0 and not self.serial
 
     def forward(self, target=None, want_keys=True, tau_T=0.0):
         """The forward path; tau_T > 0 (render only) queries the background
