@@ -65,13 +65,17 @@ __device__ __forceinline__ void level_cell(const GridDev& G, int l, const float 
     i0[d] = (uint32_t)fl;
     f[d] = u - fl;
   }
-  const bool dense = (G.dense >> l) & 1u;
   const uint32_t n1 = (uint32_t)N + 1u;
+  if ((G.dense >> l) & 1u) {  // uniform over a level: one of the two index forms only
+    const uint32_t b = i0[0] + i0[1] * n1 + i0[2] * n1 * n1;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const uint32_t ix = i0[0] + (c & 1), iy = i0[1] + ((c >> 1) & 1), iz = i0[2] + ((c >> 2) & 1);
-    idx[c] = dense ? ix + iy * n1 + iz * n1 * n1
-                   : ((ix * 1u) ^ (iy * 2654435761u) ^ (iz * 805459861u)) & G.mask;
+    for (int c = 0; c < 8; ++c) idx[c] = b + (c & 1) + ((c >> 1) & 1) * n1 + ((c >> 2) & 1) * n1 * n1;
+  } else {
+    const uint32_t hy0 = i0[1] * 2654435761u, hy1 = (i0[1] + 1u) * 2654435761u;
+    const uint32_t hz0 = i0[2] * 805459861u, hz1 = (i0[2] + 1u) * 805459861u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      idx[c] = ((i0[0] + (c & 1)) ^ ((c & 2) ? hy1 : hy0) ^ ((c & 4) ? hz1 : hz0)) & G.mask;
   }
 }
 

@@ -499,9 +499,12 @@ static hyrf_status radix_sort(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* 
   int32_t* src_v = (passes & 1) ? vb : va;
   uint32_t* dst_k = (passes & 1) ? ka : kb;
   int32_t* dst_v = (passes & 1) ? va : vb;
+  // the bits split evenly over the passes (12 tile bits: 6 + 6, so that
+  // each digit's run in a sub-tile is long enough for coalesced writes)
+  const int per = (nbits + passes - 1) / passes;
   for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    const int bits = nbits - shift < 8 ? nbits - shift : 8;
+    const int shift = per * p;
+    const int bits = nbits - shift < per ? nbits - shift : per;
     const uint32_t mask = (1u << bits) - 1u;
     HYRF_LAUNCH("k_radix_hist", s,
                 k_radix_hist<<<G, kRT, 0, s>>>(src_k, n_ptr, cap, shift, mask, hist));
