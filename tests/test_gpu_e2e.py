@@ -142,7 +142,8 @@ def test_step_graph_replays_the_eager_step(precision):
     assert H.read_status(r.status) == 0
     assert np.array_equal(np_(r.C), img)
     assert np.array_equal(np_(r.n_contrib), nc)
-    assert abs(float(r.loss.item()) - loss) <= 1e-6 * abs(loss)
+    # the loss is a sum of per-CTA partial sums added with float atomics
+    assert abs(float(r.loss.item()) - loss) <= 1e-5 * abs(loss)
     for k, v in ref.items():
         assert rel_l2(np_(m.grad[k]), v) < 1e-4, k
     # a new target through the graph's buffer
@@ -153,7 +154,7 @@ def test_step_graph_replays_the_eager_step(precision):
     l2 = float(r.loss.item())
     r.forward(t2, want_keys=False)
     torch.cuda.synchronize()
-    assert abs(float(r.loss.item()) - l2) <= 1e-6 * abs(l2)
+    assert abs(float(r.loss.item()) - l2) <= 1e-5 * abs(l2)
 
 
 def test_background_reverse_beside_compositing_reverse():
