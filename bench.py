@@ -235,7 +235,7 @@ def run_ours(args):
             mark("project_fwd"); mark("bin_sort")
             r.bin_sort(want_keys=False)
             mark("bin_sort"); mark("raster_fwd")
-            H.call("hyrf_rasterize", r._raster_args(), r.ws["r"])
+            r.rasterize()
             mark("raster_fwd"); mark("bg_fwd")
             bg = r._bg_args()
             if overlap:

@@ -333,11 +333,32 @@ typedef struct {
   float* T_final;            /* out [H][W] */
   int32_t* n_contrib;        /* out [H][W] list position of the last contributor + 1 */
   int32_t* status;
+  /* Optional [tiles] permutation of the tile indices: the order in which
+   * the CTAs take the tiles (the result does not depend on it). NULL:
+   * index order in the forward; the reverse then orders the tiles itself
+   * (longest pixel list first, from n_contrib). A forward given the order
+   * that hyrf_tile_order computed from a previous frame's n_contrib runs
+   * its long tiles first; the reverse given the order of this frame's
+   * n_contrib skips computing it. Entries outside [0, tiles) set
+   * HYRF_ERR_BOUNDS and are skipped. */
+  const int32_t* tile_order;
 } hyrf_rasterize_args;
 
 size_t hyrf_rasterize_workspace_size(const hyrf_rasterize_args* a);
 hyrf_status hyrf_rasterize(const hyrf_rasterize_args* a, void* workspace, size_t ws_bytes,
                            void* stream);
+
+/* Tile order for hyrf_rasterize(_backward): the tiles by decreasing bit
+ * length of their longest pixel list (n_contrib of a forward); order[tiles]
+ * out, a permutation (order inside a class of equal length unspecified). */
+typedef struct {
+  int32_t width, height, tile;
+  const int32_t* n_contrib;  /* [H][W] */
+  int32_t* order;            /* out [tiles] */
+} hyrf_tile_order_args;
+
+size_t hyrf_tile_order_workspace_size(const hyrf_tile_order_args* a);
+hyrf_status hyrf_tile_order(const hyrf_tile_order_args* a, void* workspace, size_t ws_bytes, void* stream);
 
 /* Reverse of hyrf_rasterize, back to front, recovering T from T_final:
  * dL/d(C_fg, T_final) -> dL/d(mean2d, conic, alpha, color) (accumulate). */

@@ -45,6 +45,8 @@ size_t bin_sort_workspace(int n, int64_t cap);
 hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t s);
 size_t raster_workspace(int n, int width, int height, bool reverse);
 hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream_t s);
+size_t tile_order_workspace(int width, int height);
+hyrf_status launch_tile_order(const hyrf_tile_order_args& a, void* ws, cudaStream_t s);
 hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, cudaStream_t s);
 size_t loss_workspace(const hyrf_loss_args& a);
 hyrf_status launch_loss(const hyrf_loss_args& a, void* ws, cudaStream_t s);
@@ -320,6 +322,17 @@ static hyrf_status raster_check(const hyrf_rasterize_args* a) {
   if (a->n > 0 && (!a->vals || !a->mean2d || !a->conic || !a->alpha || !a->color))
     return HYRF_ERR_INVALID_ARG;
   return HYRF_OK;
+}
+
+size_t hyrf_tile_order_workspace_size(const hyrf_tile_order_args* a) {
+  return a && a->width > 0 && a->height > 0 ? tile_order_workspace(a->width, a->height) : 0;
+}
+
+hyrf_status hyrf_tile_order(const hyrf_tile_order_args* a, void* ws, size_t ws_bytes, void* stream) {
+  if (!a || a->width <= 0 || a->height <= 0 || a->tile != kTile || !a->n_contrib || !a->order)
+    return HYRF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, hyrf_tile_order_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_tile_order(*a, ws, S(stream));
 }
 
 size_t hyrf_rasterize_workspace_size(const hyrf_rasterize_args* a) {

@@ -71,12 +71,17 @@ __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis,
 __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ ranges,
                                                     const int32_t* __restrict__ vals, int n,
                                                     const float4* __restrict__ rec, int W, int H,
-                                                    int TX, float* __restrict__ C_fg,
+                                                    int TX, const int32_t* __restrict__ order,
+                                                    float* __restrict__ C_fg,
                                                     float* __restrict__ T_final,
                                                     int32_t* __restrict__ n_contrib,
                                                     int32_t* status) {
   __shared__ float4 s0[256], s1[256], s2[256];
-  const int tile = blockIdx.x;
+  const int tile = order ? order[blockIdx.x] : (int)blockIdx.x;
+  if (tile < 0 || tile >= gridDim.x) {  // CTA-uniform
+    if (threadIdx.x == 0) set_status(status, HYRF_ERR_BOUNDS);
+    return;
+  }
   const int t = threadIdx.x;
   const int px = (tile % TX) * kTile + (t % kTile);
   const int py = (tile / TX) * kTile + (t / kTile);
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib, const float* __restrict__ dC,
     const float* __restrict__ dT, const float* __restrict__ Cimg, const float* __restrict__ C_fg,
     float* __restrict__ d_mean2d, float* __restrict__ d_conic, float* __restrict__ d_alpha,
-    float* __restrict__ d_color) {
+    float* __restrict__ d_color, int32_t* status) {
   constexpr int NT = 32 * WARPS;     // threads per CTA
   constexpr int CPT = kTile / (2 * WARPS * P);  // CTAs per tile
   constexpr int B = 256;             // Gaussians staged per batch
@@ -205,6 +210,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
   __shared__ int sg[B];
   __shared__ int max_last;
   const int tile = order[blockIdx.x / CPT], sub = blockIdx.x % CPT;
+  if (tile < 0 || tile >= (int)(gridDim.x / CPT)) {  // CTA-uniform
+    if (threadIdx.x == 0) set_status(status, HYRF_ERR_BOUNDS);
+    return;
+  }
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int px = (tile % TX) * kTile + (lane & 15);
   const int py0 = (tile / TX) * kTile + (sub * WARPS + wp) * 2 * P + (lane >> 4);
@@ -341,6 +350,13 @@ size_t raster_workspace(int n, int width, int height, bool reverse) {
   return c.size();
 }
 
+size_t tile_order_workspace(int width, int height) {
+  const int64_t tiles = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
+  Carver c(nullptr);
+  c.take<int32_t>((size_t)(tiles > 0 ? tiles : 1));
+  return c.size();
+}
+
 // Work class of each tile for the reverse: the bit length of its longest
 // pixel list (the reverse walks every pixel's list from its end).
 __global__ void __launch_bounds__(256) k_tile_work(const int32_t* __restrict__ n_contrib, int W, int H, int TX,
@@ -410,6 +426,15 @@ static hyrf_status pack(const hyrf_rasterize_args& a, float4* rec, cudaStream_t 
   return HYRF_OK;
 }
 
+hyrf_status launch_tile_order(const hyrf_tile_order_args& a, void* ws, cudaStream_t s) {
+  const int TX = (a.width + kTile - 1) / kTile, TY = (a.height + kTile - 1) / kTile;
+  Carver c(ws);
+  int32_t* key = c.take<int32_t>((size_t)TX * TY);
+  HYRF_LAUNCH("k_tile_work", s, k_tile_work<<<TX * TY, 256, 0, s>>>(a.n_contrib, a.width, a.height, TX, key));
+  HYRF_LAUNCH("k_tile_order", s, k_tile_order<<<1, 1024, 0, s>>>(key, TX * TY, a.order));
+  return HYRF_OK;
+}
+
 hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream_t s) {
   const int TX = (a.width + kTile - 1) / kTile, TY = (a.height + kTile - 1) / kTile;
   Carver c(ws);
@@ -417,7 +442,8 @@ hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
   HYRF_LAUNCH("k_raster_fwd", s,
-              k_raster_fwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.C_fg,
+              k_raster_fwd<<<TX * TY, 256, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, a.tile_order,
+                                                   a.C_fg,
                                        a.T_final, a.n_contrib, a.status));
   return HYRF_OK;
 }
@@ -431,13 +457,17 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   int32_t* order = c.take<int32_t>((size_t)TX * TY);
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
-  HYRF_LAUNCH("k_tile_work", s, k_tile_work<<<TX * TY, 256, 0, s>>>(a.n_contrib, a.width, a.height, TX, key));
-  HYRF_LAUNCH("k_tile_order", s, k_tile_order<<<1, 1024, 0, s>>>(key, TX * TY, order));
+  if (a.tile_order) {
+    order = const_cast<int32_t*>(a.tile_order);
+  } else {
+    HYRF_LAUNCH("k_tile_work", s, k_tile_work<<<TX * TY, 256, 0, s>>>(a.n_contrib, a.width, a.height, TX, key));
+    HYRF_LAUNCH("k_tile_order", s, k_tile_order<<<1, 1024, 0, s>>>(key, TX * TY, order));
+  }
   HYRF_LAUNCH("k_raster_bwd", s,
               k_raster_bwd<kBwdRasterWarps, kBwdRasterPixels>
               <<<TX * TY * kBwdCtasPerTile, 32 * kBwdRasterWarps, 0, s>>>(a.ranges, a.vals, a.n, rec, a.width, a.height, TX, order, a.T_final,
                                        a.n_contrib, b.d_C_fg, b.d_T_final, b.C, a.C_fg, b.d_mean2d,
-                                       b.d_conic, b.d_alpha, b.d_color));
+                                       b.d_conic, b.d_alpha, b.d_color, a.status));
   return HYRF_OK;
 }
 

@@ -96,7 +96,12 @@ class hyrf_rasterize_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_vis", _vp), ("ranges", _vp), ("vals", _vp), ("mean2d", _vp),
                 ("conic", _vp), ("alpha", _vp), ("color", _vp), ("width", C.c_int32),
                 ("height", C.c_int32), ("tile", C.c_int32), ("C_fg", _vp), ("T_final", _vp),
-                ("n_contrib", _vp), ("status", _vp)]
+                ("n_contrib", _vp), ("status", _vp), ("tile_order", _vp)]
+
+
+class hyrf_tile_order_args(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("tile", C.c_int32), ("n_contrib", _vp),
+                ("order", _vp)]
 
 
 class hyrf_rasterize_backward_args(C.Structure):
@@ -168,6 +173,7 @@ _ARGS = {
     "hyrf_bin_sort_backward": hyrf_bin_sort_args,
     "hyrf_rasterize": hyrf_rasterize_args,
     "hyrf_rasterize_backward": hyrf_rasterize_backward_args,
+    "hyrf_tile_order": hyrf_tile_order_args,
     "hyrf_composite_background": hyrf_composite_background_args,
     "hyrf_composite_background_backward": hyrf_composite_background_backward_args,
     "hyrf_loss": hyrf_loss_args,
@@ -502,6 +508,12 @@ def hyrf_bin_sort_noalloc(stream=None, **kw):
 
 def hyrf_rasterize(ws=None, stream=None, **kw):
     return call("hyrf_rasterize", _fill(hyrf_rasterize_args(), kw), ws, stream)
+
+
+def hyrf_tile_order(ws=None, stream=None, **kw):
+    """Tiles by decreasing bit length of their longest pixel list (n_contrib)."""
+    kw.setdefault("tile", TILE)
+    return call("hyrf_tile_order", _fill(hyrf_tile_order_args(), kw), ws, stream)
 
 
 def hyrf_rasterize_backward(fwd, ws=None, stream=None, **kw):

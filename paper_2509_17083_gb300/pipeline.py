@@ -136,7 +136,7 @@ def shared_workspaces(device="cuda"):
     several ViewRenderers that run one after the other on one stream to share
     it (with save_features off, the gathered hash features then live only in
     this scratch: memory for time)."""
-    return {k: H.Workspace(device) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l")}
+    return {k: H.Workspace(device) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l", "to")}
 
 
 class ViewRenderer:
@@ -174,6 +174,11 @@ class ViewRenderer:
         self.rect, self.ntiles = z(n, 4, dt=i32), z(n, dt=i32)
         self.flag = z(max(n, 1), dt=torch.uint8)
         self.ranges = z(self.TX * self.TY, 2, dt=i32)
+        # the compositing passes take the tiles in this order: index order at
+        # first, then longest pixel list first from the last forward's
+        # n_contrib (the forward uses the previous frame's, the reverse the
+        # current one)
+        self.tile_order = torch.arange(self.TX * self.TY, dtype=i32, device=d)
         self.n_inst = z(1, dt=i32)
         self.C_fg, self.T_final = z(Hh, W, 3), z(Hh, W)
         self.n_contrib = z(Hh, W, dt=i32)
@@ -224,8 +229,16 @@ class ViewRenderer:
         H._fill(a, dict(n=self.m.n, n_vis=self.n_vis, ranges=self.ranges, vals=self.vals,
                         mean2d=self.mean2d, conic=self.conic, alpha=self.alpha, color=self.color,
                         width=self.W, height=self.H, tile=H.TILE, C_fg=self.C_fg,
-                        T_final=self.T_final, n_contrib=self.n_contrib, status=self.status))
+                        T_final=self.T_final, n_contrib=self.n_contrib, status=self.status,
+                        tile_order=self.tile_order))
         return a
+
+    def rasterize(self):
+        """Compositing forward, then the tile order of its n_contrib (for the
+        reverse and the next forward)."""
+        H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
+        H.hyrf_tile_order(ws=self.ws["to"], width=self.W, height=self.H, n_contrib=self.n_contrib,
+                          order=self.tile_order)
 
     def _bg_args(self, tau_T=0.0):
         a = H.hyrf_composite_background_args()
@@ -277,7 +290,7 @@ class ViewRenderer:
         H.hyrf_query_fields(ws=self.ws["q"], **self.query_kwargs())
         self.project()
         self.bin_sort(want_keys)
-        H.call("hyrf_rasterize", self._raster_args(), self.ws["r"])
+        self.rasterize()
         bg = self._bg_args(tau_T)
         if overlap:
             main.wait_stream(self.side)

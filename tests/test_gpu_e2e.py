@@ -206,3 +206,43 @@ def test_background_reverse_beside_compositing_reverse():
         H.hyrf_rasterize_backward(r._raster_args(), ws=r.ws["rb"], d_C_fg=r.dC, d_T_final=None,
                                   d_mean2d=r.d_mean2d, d_conic=r.d_conic, d_alpha=r.d_alpha,
                                   d_color=r.d_color)
+
+
+def test_tile_order_is_a_permutation_and_leaves_the_image_unchanged():
+    """hyrf_tile_order: a permutation of the tiles, non-increasing in the bit
+    length of each tile's longest pixel list. The compositing forward gives
+    the same image, T_final and n_contrib bit for bit in index order, in
+    that order and in a random one; an out-of-range entry is reported
+    (HYRF_ERR_BOUNDS) and its CTA skipped."""
+    w = synth.config3(n=30000, width=301, height=203, log2_T=15, n_clusters=32, precision="bf16",
+                      table_init=0.3)
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg)
+    r.fit_capacity()
+    r.forward(None, want_keys=False)
+    torch.cuda.synchronize()
+    nt = r.TX * r.TY
+    order = np_(r.tile_order).copy()
+    assert np.array_equal(np.sort(order), np.arange(nt))
+    nc = np_(r.n_contrib)
+    pad = np.zeros((r.TY * 16, r.TX * 16), np.int64)
+    pad[:nc.shape[0], :nc.shape[1]] = nc
+    tmax = pad.reshape(r.TY, 16, r.TX, 16).max(axis=(1, 3)).reshape(-1)
+    bits = np.array([int(v).bit_length() for v in tmax])
+    assert np.all(np.diff(bits[order]) <= 0)
+    ref = [np_(x).copy() for x in (r.C_fg, r.T_final, r.n_contrib)]
+    for o in (np.arange(nt), np.random.default_rng(3).permutation(nt)):
+        r.tile_order.copy_(torch.as_tensor(o, dtype=torch.int32))
+        for x in (r.C_fg, r.T_final, r.n_contrib):
+            x.zero_()
+        H.call("hyrf_rasterize", r._raster_args(), r.ws["r"])
+        torch.cuda.synchronize()
+        for a, b in zip((r.C_fg, r.T_final, r.n_contrib), ref):
+            assert np.array_equal(np_(a), b)
+    bad = np.arange(nt)
+    bad[5] = nt + 7
+    r.tile_order.copy_(torch.as_tensor(bad, dtype=torch.int32))
+    r.status.zero_()
+    H.call("hyrf_rasterize", r._raster_args(), r.ws["r"])
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) & H.HYRF_ERR_BOUNDS
