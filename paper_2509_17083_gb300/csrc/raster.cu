@@ -246,6 +246,21 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
     mylast = max(mylast, last[k]);
   }
   // no pixel of this warp used list positions >= wstop (warp-uniform)
+  // the gradient this lane adds after each reduction: value col8(lane) of
+  // (mean2d u, v, conic a, b, c, opacity, colour r, g) at base + stride g;
+  // lane 1 adds colour b
+  float* gbase;
+  int gstride;
+  {
+    const int c = col8(lane);
+    gbase = c < 2 ? d_mean2d + c : c < 5 ? d_conic + (c - 2) : c == 5 ? d_alpha : d_color + (c - 6);
+    gstride = c < 2 ? 2 : c == 5 ? 1 : 3;
+    if (lane == 1) {
+      gbase = d_color + 2;
+      gstride = 3;
+    }
+  }
+  const bool adds = (lane & 3) == 0 || lane == 1;
   const int wlast = __reduce_max_sync(0xffffffffu, mylast);
   const int wstop = start + wlast;
   if (t == 0) max_last = 0;
@@ -322,17 +337,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
         const float s8 = reduce8(v);
         const float sb = warp_sum(dc2);
         const int g = sg[j];
-        if (g >= 0) {
-          if ((lane & 3) == 0) {
-            const int c = col8(lane);
-            float* dst = c < 2 ? d_mean2d + 2 * g + c
-                         : c < 5 ? d_conic + 3 * g + (c - 2)
-                         : c == 5 ? d_alpha + g
-                                  : d_color + 3 * g + (c - 6);
-            atomicAdd(dst, s8);
-          }
-          if (lane == 1) atomicAdd(d_color + 3 * g + 2, sb);
-        }
+        if (g >= 0 && adds) atomicAdd(gbase + (size_t)gstride * g, lane == 1 ? sb : s8);
       }
     }
   }
