@@ -342,11 +342,21 @@ __global__ void __launch_bounds__(kThreads, 4)
   const int nrows = row_count(S, cam);
   const int row0 = blockIdx.x * kRows;
   if (row0 >= nrows) return;  // CTA-uniform
+  const int row = row0 + lane;
+  // this thread's feature gradients, loaded while warp 0 finds the rows'
+  // points (kept only for rows found valid)
+  const size_t o = (size_t)(row < nrows ? row : row0) * 32 + 2 * l;
+  const float2 zero = make_float2(0.0f, 0.0f);
+  float2 dg0 = zero, dr0 = zero;
+  if (row < nrows) {
+    if (GAUSS) dg0 = __ldcs(reinterpret_cast<const float2*>(dXg + o));
+    dr0 = __ldcs(reinterpret_cast<const float2*>(dXr + o));
+  }
   if (l == 0) {
     float y[3], J[9];
     int g;
     bool ok;
-    row_point(S, F, cam, row0 + lane, nrows, y, GAUSS ? J : nullptr, g, ok);
+    row_point(S, F, cam, row, nrows, y, GAUSS ? J : nullptr, g, ok);
 #pragma unroll
     for (int k = 0; k < 3; ++k) ys[lane][k] = y[k];
     if (GAUSS) {
@@ -356,14 +366,11 @@ __global__ void __launch_bounds__(kThreads, 4)
     gs[lane] = ok ? g : -1;
   }
   __syncthreads();
-  const int row = row0 + lane;
   const bool ok = gs[lane] >= 0;
   const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
-  const size_t o = (size_t)row * 32 + 2 * l;
-  const float2 zero = make_float2(0.0f, 0.0f);
   if (GAUSS) {
-    const float2 dg = ok ? __ldcs(reinterpret_cast<const float2*>(dXg + o)) : zero;
-    const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
+    const float2 dg = ok ? dg0 : zero;
+    const float2 dr = ok ? dr0 : zero;
     float dy[3], dy2[3];
     if (SAME) {
       level_scatter2<DT>(F.geo, F.rad, l, y, dg, dr, g_geo, g_rad, dy);
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       for (int j = 0; j < 3; ++j) atomicAdd(d_pos + 3 * (int64_t)g + j, J[j] * s[0] + J[3 + j] * s[1] + J[6 + j] * s[2]);
     }
   } else {
-    const float2 dr = ok ? __ldcs(reinterpret_cast<const float2*>(dXr + o)) : zero;
+    const float2 dr = ok ? dr0 : zero;
     float dy[3];
     level_scatter<true, false, DT>(F.rad, l, y, dr.x, dr.y, g_rad, dy);
   }
