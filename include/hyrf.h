@@ -652,6 +652,12 @@ hyrf_status hyrf_adam_step(const hyrf_adam_tensor* tensors, int32_t count,
  * failed). */
 hyrf_status hyrf_read_status(const int32_t* status, void* stream, int32_t* host_out);
 const char* hyrf_error_string(int32_t status);
+/* Check of the library's bounded waits: one CTA waits on an mbarrier that
+ * nothing completes, polling it `polls` times as the tensor-core kernels
+ * poll their completion barriers (there 2^24 times), then gives up the
+ * way they do: HYRF_ERR_TIMEOUT is OR-ed into *status (device word) and the
+ * kernel returns, leaving the context usable. polls in [1, 2^24]. */
+hyrf_status hyrf_check_bounded_wait(int32_t* status, uint32_t polls, void* stream);
 /* Number of kernel launches issued by this library since load (host
  * counter; for launch accounting in benchmarks). */
 uint64_t hyrf_launch_count(void);

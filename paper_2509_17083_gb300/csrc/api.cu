@@ -46,6 +46,7 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
 size_t raster_workspace(int n, int width, int height, bool reverse);
 hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream_t s);
 size_t tile_order_workspace(int width, int height);
+hyrf_status launch_wait_check(int32_t* status, uint32_t polls, cudaStream_t s);
 hyrf_status launch_tile_order(const hyrf_tile_order_args& a, void* ws, cudaStream_t s);
 hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, cudaStream_t s);
 size_t loss_workspace(const hyrf_loss_args& a);
@@ -326,6 +327,11 @@ static hyrf_status raster_check(const hyrf_rasterize_args* a) {
 
 size_t hyrf_tile_order_workspace_size(const hyrf_tile_order_args* a) {
   return a && a->width > 0 && a->height > 0 ? tile_order_workspace(a->width, a->height) : 0;
+}
+
+hyrf_status hyrf_check_bounded_wait(int32_t* status, uint32_t polls, void* stream) {
+  if (!status || polls < 1 || polls > (1u << 24)) return HYRF_ERR_INVALID_ARG;
+  return launch_wait_check(status, polls, S(stream));
 }
 
 hyrf_status hyrf_tile_order(const hyrf_tile_order_args* a, void* ws, size_t ws_bytes, void* stream) {

@@ -310,6 +310,19 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kBgTmemCols));
 }
 
+// The bounded wait of the tensor-core kernels on a barrier that nothing
+// completes (hyrf_check_bounded_wait): gives up after `polls` polls, sets
+// HYRF_ERR_TIMEOUT and returns.
+__global__ void __launch_bounds__(128) k_wait_check(int32_t* status, uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  if (!wait_phase(&bar, 0u, polls) && threadIdx.x == 0) set_status(status, HYRF_ERR_TIMEOUT);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- launchers
@@ -436,6 +449,11 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
                 tc::k_bg_exact_fwd_tc<false><<<grid, 128, tc::kBgSmem, s>>>(F, cam, a.bg.radius, Xb, list, count,
                                                                            a.C_fg, a.T_final, a.C, a.status));
   }
+  return HYRF_OK;
+}
+
+hyrf_status launch_wait_check(int32_t* status, uint32_t polls, cudaStream_t s) {
+  HYRF_LAUNCH("k_wait_check", s, tc::k_wait_check<<<1, 128, 0, s>>>(status, polls));
   return HYRF_OK;
 }
 

@@ -86,11 +86,11 @@ __device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Bounded wait on the given phase; returns false (on every thread) if any
-// thread of the CTA gave up.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase) {
+// Bounded wait on the given phase (at most `polls` polls); returns false
+// (on every thread) if any thread of the CTA gave up.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase, uint32_t polls = kSpin) {
   bool ok = false;
-  for (uint32_t it = 0; it < kSpin && !ok; ++it) ok = try_wait(bar, phase);
+  for (uint32_t it = 0; it < polls && !ok; ++it) ok = try_wait(bar, phase);
   return !__syncthreads_or(!ok);
 }
 

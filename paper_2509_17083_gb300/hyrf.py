@@ -230,6 +230,8 @@ def lib():
         L.hyrf_timer_enable.restype = None
         L.hyrf_timer_read.argtypes = [C.POINTER(hyrf_kernel_time), C.c_int]
         L.hyrf_timer_read.restype = C.c_int
+        L.hyrf_check_bounded_wait.argtypes = [_vp, C.c_uint32, _vp]
+        L.hyrf_check_bounded_wait.restype = C.c_int32
         _lib = L
     return _lib
 
@@ -291,6 +293,13 @@ def read_status(status, stream=None):
 
 def error_string(st):
     return lib().hyrf_error_string(st).decode()
+
+
+def hyrf_check_bounded_wait(status, polls, stream=None):
+    """One CTA's bounded wait on a barrier nothing completes (sets
+    HYRF_ERR_TIMEOUT in the device status word after `polls` polls)."""
+    _check("hyrf_check_bounded_wait",
+           lib().hyrf_check_bounded_wait(ptr(status), int(polls), stream_handle(stream)))
 
 
 def launch_count():

@@ -366,3 +366,17 @@ def test_spatial_order_is_a_locality_preserving_permutation(lib):
     step_new = np.linalg.norm(np.diff(np_(m.pos), axis=0), axis=1).mean()
     step_old = np.linalg.norm(np.diff(before, axis=0), axis=1).mean()
     assert step_new < 0.1 * step_old, (step_new, step_old)
+
+
+def test_bounded_wait_gives_up_with_a_status():
+    """The tensor-core kernels' bounded wait, on a barrier that nothing
+    completes: the kernel gives up after its polls, reports
+    HYRF_ERR_TIMEOUT in the status word and the context stays usable."""
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.hyrf_check_bounded_wait(st, 1000)
+    assert H.read_status(st) & H.HYRF_ERR_TIMEOUT
+    st.zero_()
+    torch.cuda.synchronize()  # the context still works
+    assert H.read_status(st) == 0
+    with pytest.raises(H.HyrfError):
+        H.hyrf_check_bounded_wait(st, 0)
