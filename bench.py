@@ -224,12 +224,8 @@ def run_ours(args):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                     evs.setdefault(k, []).append(e0)
-            overlap = r._overlap()
-            if overlap:  # background features gathered on the side stream
-                r.side.wait_stream(stream)
-                H.hyrf_gather_background(r._bg_args(), stream=r.side)
             mark("query_fwd")
-            H.hyrf_query_fields(ws=r.ws["q"], **r.query_kwargs())
+            r.forward_fields()
             mark("query_fwd"); mark("project_fwd")
             r.project()
             mark("project_fwd"); mark("bin_sort")
@@ -237,11 +233,7 @@ def run_ours(args):
             mark("bin_sort"); mark("raster_fwd")
             r.rasterize()
             mark("raster_fwd"); mark("bg_fwd")
-            bg = r._bg_args()
-            if overlap:
-                stream.wait_stream(r.side)
-                bg.features_ready = 1
-            H.call("hyrf_composite_background", bg, r.ws["b"])
+            r.composite()
             mark("bg_fwd"); mark("loss")
             r.loss_fn(tgt)
             mark("loss")

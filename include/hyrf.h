@@ -156,7 +156,25 @@ typedef struct {
    * diffuse 3DGS; `fields` is not read). NULL alpha_e / scale_e / color_e
    * mean zero explicit parts (neural only). 0 and non-NULL: HyRF. */
   int32_t explicit_only;
+  /* 1: vis_ids / n_vis already hold this call's pre-culled set (from
+   * hyrf_precull with the same n, pos and cam): the pre-cull is skipped. */
+  int32_t vis_ready;
 } hyrf_query_fields_args;
+
+/* hyrf_precull: the pre-culling and ascending compaction of
+ * hyrf_query_fields (Eqs. 8-9) as a call of its own, for callers that start
+ * depth ordering (hyrf_depth_order) beside the field query, which then
+ * takes vis_ready = 1. */
+typedef struct {
+  int32_t n;                 /* N */
+  const float* pos;          /* [N][3] */
+  hyrf_camera cam;
+  int32_t* vis_ids;          /* out [N] */
+  int32_t* n_vis;            /* out [1] */
+} hyrf_precull_args;
+
+size_t hyrf_precull_workspace_size(const hyrf_precull_args* a);
+hyrf_status hyrf_precull(const hyrf_precull_args* a, void* workspace, size_t ws_bytes, void* stream);
 
 size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a);
 hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* workspace, size_t ws_bytes,
@@ -279,7 +297,30 @@ typedef struct {
   int32_t* ranges;           /* out [tiles_y*tiles_x][2] */
   int32_t* n_instances;      /* out [1] K (clamped to capacity; HYRF_ERR_OVERFLOW if above) */
   int32_t* status;
+  /* Optional [V]: the visible rows in depth order from hyrf_depth_order
+   * (same camera and visible set); the call then skips its own depth sort
+   * (the result is identical). NULL: sorted here. */
+  const int32_t* depth_order;
 } hyrf_bin_sort_args;
+
+/* hyrf_depth_order: the visible rows ordered by camera-space depth exactly
+ * as hyrf_bin_sort orders them (keys: the FP32 depth z of hyrf_project,
+ * computed with the same operations from the positions; stable, ties by
+ * visible index). It needs only the positions, so it can run beside the
+ * field query (which the projection's rectangles need); hyrf_bin_sort then
+ * takes the result in depth_order. order[V] out. */
+typedef struct {
+  int32_t n;                 /* N (capacity) */
+  const float* pos;          /* [N][3] */
+  const int32_t* vis_ids;    /* [N] */
+  const int32_t* n_vis;      /* [1] */
+  hyrf_camera cam;
+  int32_t* order;            /* out [N]: first *n_vis valid */
+  int32_t* status;
+} hyrf_depth_order_args;
+
+size_t hyrf_depth_order_workspace_size(const hyrf_depth_order_args* a);
+hyrf_status hyrf_depth_order(const hyrf_depth_order_args* a, void* workspace, size_t ws_bytes, void* stream);
 
 size_t hyrf_bin_sort_workspace_size(const hyrf_bin_sort_args* a);
 hyrf_status hyrf_bin_sort(const hyrf_bin_sort_args* a, void* workspace, size_t ws_bytes,

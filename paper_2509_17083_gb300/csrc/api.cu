@@ -11,6 +11,8 @@ namespace hyrf {
 
 // launchers (one per translation unit)
 size_t precull_workspace(int n);
+size_t depth_order_workspace(int n);
+hyrf_status launch_depth_order(const hyrf_depth_order_args& a, void* ws, cudaStream_t s);
 hyrf_status launch_precull(const CamDev& cam, const float* pos, int n, int32_t* vis_ids,
                            int32_t* n_vis, void* ws, cudaStream_t s);
 hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int32_t* vis_ids,
@@ -210,7 +212,8 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
     return HYRF_ERR_INVALID_ARG;
   if (a->explicit_only) {  // "w/o Neural": no field is read
     if (a->features) return HYRF_ERR_INVALID_ARG;
-    hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
+    hyrf_status st = a->vis_ready ? HYRF_OK
+                                  : launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
     return st != HYRF_OK ? st : launch_query_explicit(*a, S(stream));
   }
   FieldsDev F;
@@ -224,10 +227,33 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
     return HYRF_ERR_UNSUPPORTED;
   if (!bf16_weights_ok(a->fields.geo_mlp) || !bf16_weights_ok(a->fields.col_mlp)) return HYRF_ERR_INVALID_ARG;
   if (a->features && (!F.cm.bf16 || !aligned(a->features, 16))) return HYRF_ERR_INVALID_ARG;
-  hyrf_status st = launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
+  hyrf_status st = a->vis_ready ? HYRF_OK
+                                : launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
   if (st != HYRF_OK) return st;
   // BF16 decoders run on the tensor cores, FP32 decoders on the CUDA cores
   return F.cm.bf16 ? launch_query_fwd_tc(*a, F, ws, S(stream)) : launch_query_fwd(*a, F, S(stream));
+}
+
+size_t hyrf_precull_workspace_size(const hyrf_precull_args* a) {
+  return a && a->n >= 0 ? align_up(precull_workspace(a->n)) : 0;
+}
+
+hyrf_status hyrf_precull(const hyrf_precull_args* a, void* ws, size_t ws_bytes, void* stream) {
+  if (!a || a->n < 0 || !query_cam_ok(a->cam) || !a->n_vis) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->pos || !a->vis_ids)) return HYRF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, hyrf_precull_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
+}
+
+size_t hyrf_depth_order_workspace_size(const hyrf_depth_order_args* a) {
+  return a && a->n >= 0 ? depth_order_workspace(a->n) : 0;
+}
+
+hyrf_status hyrf_depth_order(const hyrf_depth_order_args* a, void* ws, size_t ws_bytes, void* stream) {
+  if (!a || a->n < 0 || !query_cam_ok(a->cam) || !a->n_vis) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->pos || !a->vis_ids || !a->order)) return HYRF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, hyrf_depth_order_workspace_size(a))) return HYRF_ERR_INVALID_ARG;
+  return launch_depth_order(*a, ws, S(stream));
 }
 
 size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backward_args* a) {

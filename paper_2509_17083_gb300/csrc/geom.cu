@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
       set_status(status, HYRF_ERR_BOUNDS);
       o.ntiles[i] = 0;
       o.rect[4 * i] = o.rect[4 * i + 1] = o.rect[4 * i + 2] = o.rect[4 * i + 3] = 0;
+      o.depth[i] = 0.0f;
       continue;
     }
     const float p[3] = {pos[3 * (int64_t)g], pos[3 * (int64_t)g + 1], pos[3 * (int64_t)g + 2]};
@@ -289,6 +290,37 @@ hyrf_status launch_precull(const CamDev& cam, const float* pos, int n, int32_t* 
               k_scan_small<<<1, 1024, 0, s>>>(counts, chunks, n_vis));
   HYRF_LAUNCH("k_precull_scatter", s,
               k_precull_scatter<<<chunks, 256, 0, s>>>(cam, pos, n, counts, vis_ids));
+  return HYRF_OK;
+}
+
+// Camera-space depth z of every visible row: the z of cam_point, as in
+// k_project (this file's operation order), so that the depth keys of
+// hyrf_depth_order and of hyrf_project agree bit for bit.
+__global__ void __launch_bounds__(256) k_depth_of(CamDev c, int n, const float* __restrict__ pos,
+                                                  const int32_t* __restrict__ vis_ids,
+                                                  const int32_t* __restrict__ n_vis, float* __restrict__ depth,
+                                                  int32_t* status) {
+  const int nv = min(*n_vis, n);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    const int g = vis_ids[i];
+    if (g < 0 || g >= n) {
+      set_status(status, HYRF_ERR_BOUNDS);
+      depth[i] = 0.0f;
+      continue;
+    }
+    const float p[3] = {pos[3 * (int64_t)g], pos[3 * (int64_t)g + 1], pos[3 * (int64_t)g + 2]};
+    float tc[3];
+    cam_point(c, p, tc);
+    depth[i] = tc[2];
+  }
+}
+
+hyrf_status launch_depth_of(const CamDev& cam, int n, const float* pos, const int32_t* vis_ids,
+                            const int32_t* n_vis, float* depth, int32_t* status, cudaStream_t s) {
+  if (n == 0) return HYRF_OK;
+  int blocks = (n + 255) / 256;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  HYRF_LAUNCH("k_depth_of", s, k_depth_of<<<blocks, 256, 0, s>>>(cam, n, pos, vis_ids, n_vis, depth, status));
   return HYRF_OK;
 }
 

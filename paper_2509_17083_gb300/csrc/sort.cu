@@ -487,6 +487,8 @@ size_t bin_sort_workspace(int n, int64_t cap) {
   return c.size();
 }
 
+
+
 // Stable LSD radix sort of (keys, vals) on bits [0, nbits); the result ends in
 // (ka, va); (kb, vb) is scratch. The input must be in (ka, va) when the pass
 // count is even and in (kb, vb) when it is odd.
@@ -534,17 +536,23 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
     cudaMemsetAsync(a.n_instances, 0, sizeof(int32_t), s);
     return cudaPeekAtLastError() == cudaSuccess ? HYRF_OK : HYRF_ERR_CUDA;
   }
-  // 1. depth keys of the visible Gaussians, sorted (4 x 8 bits)
-  const int eb = (n + 255) / 256 < num_sms() * 8 ? (n + 255) / 256 : num_sms() * 8;
-  HYRF_LAUNCH("k_depth_keys", s,
-              k_depth_keys<<<eb, 256, 0, s>>>(a.depth, a.n_vis, n, w.dk_a, w.dv_a));
-  hyrf_status st = radix_sort(w.dk_a, w.dv_a, w.dk_b, w.dv_b, a.n_vis, n, 32, w.hist, w.totals, s,
-                              "k_radix_scatter<depth>");
-  if (st != HYRF_OK) return st;
+  // 1. depth keys of the visible Gaussians, sorted (4 x 8 bits), unless the
+  // caller ordered them already (hyrf_depth_order)
+  hyrf_status st = HYRF_OK;
+  const int32_t* ord = a.depth_order;
+  if (!ord) {
+    const int eb = (n + 255) / 256 < num_sms() * 8 ? (n + 255) / 256 : num_sms() * 8;
+    HYRF_LAUNCH("k_depth_keys", s,
+                k_depth_keys<<<eb, 256, 0, s>>>(a.depth, a.n_vis, n, w.dk_a, w.dv_a));
+    st = radix_sort(w.dk_a, w.dv_a, w.dk_b, w.dv_b, a.n_vis, n, 32, w.hist, w.totals, s,
+                    "k_radix_scatter<depth>");
+    if (st != HYRF_OK) return st;
+    ord = w.dv_a;
+  }
   // 2. instance offsets in depth order, K, and emission
   const int sc = (n + kScanChunk - 1) / kScanChunk;
   HYRF_LAUNCH("k_count_sums", s,
-              k_count_sums<<<sc, 256, 0, s>>>(a.ntiles, w.dv_a, a.n_vis, n, w.sums));
+              k_count_sums<<<sc, 256, 0, s>>>(a.ntiles, ord, a.n_vis, n, w.sums));
   HYRF_LAUNCH("k_scan_sums", s,
               k_scan_sums<<<1, 1024, 0, s>>>(w.sums, sc, cap, a.n_instances, a.status));
   const int tbits = bits_for(n_tiles);
@@ -552,12 +560,12 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   uint32_t* emit_k = (tpasses & 1) ? w.tk_b : w.tk_a;
   int32_t* emit_v = (tpasses & 1) ? w.tv_b : a.vals;
   HYRF_LAUNCH("k_offsets", s,
-              k_offsets<<<sc, 256, 0, s>>>(a.ntiles, w.dv_a, a.n_vis, n, w.sums, sc, w.off));
+              k_offsets<<<sc, 256, 0, s>>>(a.ntiles, ord, a.n_vis, n, w.sums, sc, w.off));
   const int capi = (int)(cap < 0x7fffffff ? cap : 0x7fffffff);
   const int64_t xb = (cap + kExpandItems - 1) / kExpandItems;
   HYRF_LAUNCH("k_expand", s,
               k_expand<<<(int)(xb < 0x7fffffff ? xb : 0x7fffffff), 256, 0, s>>>(
-                  a.rect, w.dv_a, a.n_vis, n, w.off, a.n_instances, capi, a.tiles_x, emit_k, emit_v));
+                  a.rect, ord, a.n_vis, n, w.off, a.n_instances, capi, a.tiles_x, emit_k, emit_v));
   // 3. stable sort of the instances on their tile bits
   st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s,
                   "k_radix_scatter<tile>");
@@ -571,6 +579,51 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
                 k_keys64<<<kb, 256, 0, s>>>(w.tk_a, a.vals, a.depth, a.n_instances, capi, a.keys));
   }
   return HYRF_OK;
+}
+
+// ---------------------------------------------------------------- depth order alone
+
+hyrf_status launch_depth_of(const CamDev& cam, int n, const float* pos, const int32_t* vis_ids,
+                            const int32_t* n_vis, float* depth, int32_t* status, cudaStream_t s);
+
+struct DepthWs {
+  float* depth;
+  uint32_t *k_a, *k_b;
+  int32_t* v_b;
+  uint32_t *hist, *totals;
+};
+
+static DepthWs carve_depth(Carver& c, int n) {
+  DepthWs w;
+  const int m = n > 0 ? n : 1;
+  w.depth = c.take<float>(m);
+  w.k_a = c.take<uint32_t>(m);
+  w.k_b = c.take<uint32_t>(m);
+  w.v_b = c.take<int32_t>(m);
+  w.hist = c.take<uint32_t>((size_t)256 * radix_ctas(m));
+  w.totals = c.take<uint32_t>(256);
+  return w;
+}
+
+size_t depth_order_workspace(int n) {
+  Carver c(nullptr);
+  carve_depth(c, n);
+  return c.size();
+}
+
+// The depth keys and the four 8-bit passes of launch_bin_sort's step 1, on
+// depths computed from the positions (the same FP32 z as the projection).
+hyrf_status launch_depth_order(const hyrf_depth_order_args& a, void* ws, cudaStream_t s) {
+  const int n = a.n;
+  if (n == 0) return HYRF_OK;
+  Carver c(ws);
+  DepthWs w = carve_depth(c, n);
+  hyrf_status st = launch_depth_of(to_dev(a.cam), n, a.pos, a.vis_ids, a.n_vis, w.depth, a.status, s);
+  if (st != HYRF_OK) return st;
+  const int eb = (n + 255) / 256 < num_sms() * 8 ? (n + 255) / 256 : num_sms() * 8;
+  HYRF_LAUNCH("k_depth_keys", s, k_depth_keys<<<eb, 256, 0, s>>>(w.depth, a.n_vis, n, w.k_a, a.order));
+  return radix_sort(w.k_a, a.order, w.k_b, w.v_b, a.n_vis, n, 32, w.hist, w.totals, s,
+                    "k_radix_scatter<depth>");
 }
 
 // ---------------------------------------------------------------- storage order

@@ -60,7 +60,12 @@ class hyrf_query_fields_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("pos", _vp), ("alpha_e", _vp), ("scale_e", _vp),
                 ("color_e", _vp), ("cam", hyrf_camera), ("fields", hyrf_fields),
                 ("vis_ids", _vp), ("n_vis", _vp), ("alpha", _vp), ("scale", _vp), ("quat", _vp),
-                ("color", _vp), ("status", _vp), ("features", _vp), ("explicit_only", C.c_int32)]
+                ("color", _vp), ("status", _vp), ("features", _vp), ("explicit_only", C.c_int32),
+                ("vis_ready", C.c_int32)]
+
+
+class hyrf_precull_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("cam", hyrf_camera), ("vis_ids", _vp), ("n_vis", _vp)]
 
 
 class hyrf_query_fields_backward_args(C.Structure):
@@ -89,7 +94,12 @@ class hyrf_bin_sort_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_vis", _vp), ("rect", _vp), ("ntiles", _vp), ("depth", _vp),
                 ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("capacity", C.c_int64),
                 ("keys", _vp), ("vals", _vp), ("ranges", _vp), ("n_instances", _vp),
-                ("status", _vp)]
+                ("status", _vp), ("depth_order", _vp)]
+
+
+class hyrf_depth_order_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", _vp), ("vis_ids", _vp), ("n_vis", _vp), ("cam", hyrf_camera),
+                ("order", _vp), ("status", _vp)]
 
 
 class hyrf_rasterize_args(C.Structure):
@@ -174,6 +184,8 @@ _ARGS = {
     "hyrf_rasterize": hyrf_rasterize_args,
     "hyrf_rasterize_backward": hyrf_rasterize_backward_args,
     "hyrf_tile_order": hyrf_tile_order_args,
+    "hyrf_precull": hyrf_precull_args,
+    "hyrf_depth_order": hyrf_depth_order_args,
     "hyrf_composite_background": hyrf_composite_background_args,
     "hyrf_composite_background_backward": hyrf_composite_background_backward_args,
     "hyrf_loss": hyrf_loss_args,
@@ -438,6 +450,16 @@ def hyrf_project_backward(ws=None, stream=None, **kw):
 
 def hyrf_bin_sort(ws=None, stream=None, **kw):
     return call("hyrf_bin_sort", _fill(hyrf_bin_sort_args(), kw), ws, stream)
+
+
+def hyrf_precull(ws=None, stream=None, **kw):
+    """Pre-cull and ascending compaction alone (query_fields with vis_ready=1 then skips it)."""
+    return call("hyrf_precull", _fill(hyrf_precull_args(), kw), ws, stream)
+
+
+def hyrf_depth_order(ws=None, stream=None, **kw):
+    """The visible rows in hyrf_bin_sort's depth order, from the positions."""
+    return call("hyrf_depth_order", _fill(hyrf_depth_order_args(), kw), ws, stream)
 
 
 def hyrf_bin_sort_backward(ws=None, stream=None, **kw):

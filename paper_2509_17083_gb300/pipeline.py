@@ -136,7 +136,7 @@ def shared_workspaces(device="cuda"):
     several ViewRenderers that run one after the other on one stream to share
     it (with save_features off, the gathered hash features then live only in
     this scratch: memory for time)."""
-    return {k: H.Workspace(device) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l", "to")}
+    return {k: H.Workspace(device) for k in ("q", "qb", "p", "s", "r", "rb", "b", "bb", "l", "to", "pc", "do")}
 
 
 class ViewRenderer:
@@ -179,6 +179,8 @@ class ViewRenderer:
         # n_contrib (the forward uses the previous frame's, the reverse the
         # current one)
         self.tile_order = torch.arange(self.TX * self.TY, dtype=i32, device=d)
+        self.depth_order = z(max(n, 1), dt=i32)  # visible rows by depth (hyrf_depth_order)
+        self._depth_ready = False
         self.n_inst = z(1, dt=i32)
         self.C_fg, self.T_final = z(Hh, W, 3), z(Hh, W)
         self.n_contrib = z(Hh, W, dt=i32)
@@ -201,6 +203,7 @@ class ViewRenderer:
         # second stream: the background's feature gather ahead of the
         # foreground, and its table-gradient scatter behind it
         self.side = torch.cuda.Stream(device=d) if str(d).startswith("cuda") else None
+        self._depth_done = torch.cuda.Event() if self.side is not None else None
         self.serial = False
         if self.save_features:
             self.feat_q = torch.empty(2 * max(n, 1) * 32, dtype=torch.bfloat16, device=d)
@@ -280,25 +283,43 @@ class ViewRenderer:
 
     def forward(self, target=None, want_keys=True, tau_T=0.0):
         """The forward path; tau_T > 0 (render only) queries the background
-        only where T_final >= tau_T. The background's feature gather runs on
-        the side stream while the foreground is rendered."""
-        main = torch.cuda.current_stream() if self.side is not None else None
-        overlap = self._overlap(tau_T)
-        if overlap:
-            self.side.wait_stream(main)  # after earlier updates of the tables
-            H.hyrf_gather_background(self._bg_args(), stream=self.side)
-        H.hyrf_query_fields(ws=self.ws["q"], **self.query_kwargs())
+        only where T_final >= tau_T. With the side stream, the depth order
+        and the background's feature gather run beside the field query."""
+        self.forward_fields(tau_T)
         self.project()
         self.bin_sort(want_keys)
         self.rasterize()
-        bg = self._bg_args(tau_T)
-        if overlap:
-            main.wait_stream(self.side)
-            bg.features_ready = 1
-        H.call("hyrf_composite_background", bg, self.ws["b"])
+        self.composite(tau_T)
         if target is not None:
             self.loss_fn(target)
         return self.C
+
+    def forward_fields(self, tau_T=0.0):
+        """Pre-cull and field query of the Gaussians. With the side stream
+        the pre-cull runs first (hyrf_precull); the depth order
+        (hyrf_depth_order: positions only) and the background's feature
+        gather then run on the side stream while the fields are queried."""
+        self._depth_ready = self._overlap(tau_T)
+        if not self._depth_ready:
+            H.hyrf_query_fields(ws=self.ws["q"], **self.query_kwargs())
+            return
+        m = self.m
+        H.hyrf_precull(ws=self.ws["pc"], n=m.n, pos=m.pos, cam=self.ccam_q, vis_ids=self.vis_ids, n_vis=self.n_vis)
+        self.side.wait_stream(torch.cuda.current_stream())  # after the pre-cull and earlier table updates
+        H.hyrf_depth_order(ws=self.ws["do"], stream=self.side, n=m.n, pos=m.pos, vis_ids=self.vis_ids,
+                           n_vis=self.n_vis, cam=self.ccam, order=self.depth_order, status=self.status)
+        self._depth_done.record(self.side)  # the binning waits for this, not for the gather
+        H.hyrf_gather_background(self._bg_args(), stream=self.side)
+        H.hyrf_query_fields(ws=self.ws["q"], vis_ready=1, **self.query_kwargs())
+
+    def composite(self, tau_T=0.0):
+        """The background blend (Eqs. 10-11); with the side stream, after its
+        feature gather."""
+        bg = self._bg_args(tau_T)
+        if self._overlap(tau_T):
+            torch.cuda.current_stream().wait_stream(self.side)
+            bg.features_ready = 1
+        H.call("hyrf_composite_background", bg, self.ws["b"])
 
     def project(self):
         m = self.m
@@ -308,11 +329,18 @@ class ViewRenderer:
                        ntiles=self.ntiles, fp64_flag=self.flag, status=self.status)
 
     def bin_sort(self, want_keys=True):
+        """Tile binning; takes the side stream's depth order when forward_fields
+        started one (identical result)."""
+        order = None
+        if self._depth_ready:
+            torch.cuda.current_stream().wait_event(self._depth_done)
+            order = self.depth_order
+            self._depth_ready = False  # one binning per depth order
         H.hyrf_bin_sort(ws=self.ws["s"], n=self.m.n, n_vis=self.n_vis, rect=self.rect,
                         ntiles=self.ntiles, depth=self.depth, tiles_x=self.TX, tiles_y=self.TY,
                         capacity=self.capacity, keys=self.keys if want_keys else None,
                         vals=self.vals, ranges=self.ranges, n_instances=self.n_inst,
-                        status=self.status)
+                        status=self.status, depth_order=order)
 
     def loss_fn(self, target, grad=True):
         H.hyrf_loss(ws=self.ws["l"], width=self.W, height=self.H, C=self.C, target=target,

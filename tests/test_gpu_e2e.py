@@ -246,3 +246,37 @@ def test_tile_order_is_a_permutation_and_leaves_the_image_unchanged():
     H.call("hyrf_rasterize", r._raster_args(), r.ws["r"])
     torch.cuda.synchronize()
     assert H.read_status(r.status) & H.HYRF_ERR_BOUNDS
+
+
+def test_separate_precull_and_depth_order_match_the_single_calls():
+    """hyrf_precull + hyrf_query_fields(vis_ready=1) give the visible set
+    and the field outputs of the single call bit for bit; hyrf_bin_sort with
+    the depth order of hyrf_depth_order (computed from the positions, on the
+    second stream in the pipeline) gives the instances and ranges of its own
+    depth sort bit for bit."""
+    w = synth.config3(n=30000, width=301, height=203, log2_T=15, n_clusters=32, precision="bf16",
+                      table_init=0.3)
+    m = DeviceModel(w)
+    r = ViewRenderer(m, w.cams[0], w.bg)
+    assert r._overlap()
+    r.fit_capacity()
+    r.status.zero_()
+    r.forward(None, want_keys=True)  # the split path: pre-cull, depth order beside the query
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    split = {k: np_(getattr(r, k)).copy() for k in ("vis_ids", "n_vis", "alpha", "scale", "quat", "color",
+                                                      "vals", "ranges", "n_inst", "keys")}
+    nv, K = int(split["n_vis"][0]), int(split["n_inst"][0])
+    # the single calls
+    H.hyrf_query_fields(ws=r.ws["q"], **r.query_kwargs())
+    r.project()
+    r._depth_ready = False
+    r.bin_sort(want_keys=True)
+    torch.cuda.synchronize()
+    assert int(r.n_vis.item()) == nv and int(r.n_inst.item()) == K
+    for k in ("vis_ids", "alpha", "scale", "quat", "color"):
+        a = np_(getattr(r, k))
+        assert np.array_equal(a[:nv], split[k][:nv]), k
+    assert np.array_equal(np_(r.vals)[:K], split["vals"][:K])
+    assert np.array_equal(np_(r.keys)[:K], split["keys"][:K])
+    assert np.array_equal(np_(r.ranges), split["ranges"])
