@@ -10,7 +10,8 @@
 namespace hyrf {
 
 constexpr int kRT = 256;         // radix threads per CTA
-constexpr int kSub = 1024;       // elements per scatter sub-tile (8 warps x 4 rounds x 32)
+constexpr int kSub = 2048;       // elements per scatter sub-tile (8 warps x 8 rounds x 32)
+constexpr int kRounds = kSub / 256;
 constexpr int kMaxRadixCTAs = 2048;
 
 __device__ __forceinline__ int dev_chunk(int n, int G) {
@@ -116,13 +117,13 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
   const int64_t start = (int64_t)b * chunk;
   const int64_t end = (start + chunk < (int64_t)n) ? start + chunk : (int64_t)n;
   for (int64_t sub = start; sub < end; sub += kSub) {
-    uint32_t key[4], rank[4];
-    int32_t val[4];
-    uint32_t dig[4];
-    bool valid[4];
+    uint32_t key[kRounds], rank[kRounds];
+    int32_t val[kRounds];
+    uint32_t dig[kRounds];
+    bool valid[kRounds];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int64_t idx = sub + w * 128 + r * 32 + lane;
+    for (int r = 0; r < kRounds; ++r) {
+      const int64_t idx = sub + w * (32 * kRounds) + r * 32 + lane;
       valid[r] = idx < end;
       key[r] = valid[r] ? keys_in[idx] : 0u;
       val[r] = valid[r] ? vals_in[idx] : 0;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
     // stage the sub-tile in digit order, then write each digit's run to
     // consecutive global positions (coalesced)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < kRounds; ++r) {
       if (!valid[r]) continue;
       const uint32_t lp = lstart[dig[r]] + whist[w][dig[r]] + rank[r];
       sk[lp] = key[r];
