@@ -10,8 +10,10 @@
 // reverse walks each pixel's list back to front, recovering T from the
 // stored T_final by division, with several pixels of one column per thread,
 // reduces the per-Gaussian gradients across each warp and adds them with
-// atomics; its CTAs take the tiles in decreasing order of their longest
-// pixel list, so that the last CTAs to run on each SM are short ones.
+// atomics. Both passes can take the tiles in decreasing order of their
+// longest pixel list (k_tile_work / k_tile_order: a previous frame's for
+// the forward, the current one for the reverse), so that the last CTAs to
+// run on each SM are short ones.
 #include "common.cuh"
 
 namespace hyrf {

@@ -2,9 +2,11 @@
 // and composited per pixel). Instances carry the 64-bit key
 // (tile << 32) | float_bits(depth); their stable order is produced by LSD
 // radix passes: four 8-bit passes over the 32 depth bits of the visible
-// Gaussians, emission of each Gaussian's tiles in that order, then the tile
-// bits over the instances. Every pass is reduce-then-scan (histogram,
-// per-digit column scan, stable scatter), so no kernel waits on another CTA.
+// Gaussians (here, or beforehand by hyrf_depth_order from the positions),
+// emission of each Gaussian's tiles in that order, then the tile bits over
+// the instances (split evenly over the passes). Every pass is
+// reduce-then-scan (histogram, per-digit column scan, stable scatter), so
+// no kernel waits on another CTA.
 #include "common.cuh"
 
 namespace hyrf {
