@@ -280,3 +280,34 @@ def test_separate_precull_and_depth_order_match_the_single_calls():
     assert np.array_equal(np_(r.vals)[:K], split["vals"][:K])
     assert np.array_equal(np_(r.keys)[:K], split["keys"][:K])
     assert np.array_equal(np_(r.ranges), split["ranges"])
+
+
+def test_view_with_every_gaussian_culled():
+    """Edge case: the camera looks away from the scene, so the pre-cull keeps
+    no Gaussian (n_vis = 0, K = 0). The step runs every stage on empty sets:
+    the image is the background alone (against the oracle), no Gaussian
+    receives a gradient, the background field does, and no status bit is
+    set."""
+    import dataclasses
+    w = synth.config3(n=20000, width=161, height=113, log2_T=15, n_clusters=16, precision="bf16",
+                      table_init=0.3)
+    cam = w.cams[0]
+    away = dataclasses.replace(cam, R=(np.diag([-1.0, 1.0, -1.0]) @ cam.R).astype(np.float32))
+    w = dataclasses.replace(w, cams=[away])
+    m = DeviceModel(w)
+    r = ViewRenderer(m, away, w.bg, lam=w.ssim_lambda, loss_scale=w.loss_scale)
+    tgt = cuda_f32(w.targets[0])
+    r.set_capacity(1 << 16)
+    r.status.zero_()
+    m.zero_grad()
+    r.forward(tgt, want_keys=False)
+    r.backward()
+    torch.cuda.synchronize()
+    assert H.read_status(r.status) == 0
+    assert int(r.n_vis.item()) == 0 and int(r.n_inst.item()) == 0
+    assert np.all(np_(r.T_final) == 1.0) and np.all(np_(r.n_contrib) == 0) and np.all(np_(r.C_fg) == 0.0)
+    fw = oracle.render(w.gaussians, w.fields, away, w.bg)
+    assert np.abs(np_(r.C) - fw["C"]).max() < 4e-3
+    for k in ("pos", "alpha_e", "scale_e", "color_e"):
+        assert not np.any(np_(m.grad[k])), k
+    assert np.any(np_(m.grad["rad_table"]))
