@@ -416,11 +416,31 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ til
                                                 const int32_t* __restrict__ n_ptr, int cap,
                                                 int n_tiles, int32_t* __restrict__ ranges) {
   const int K = clamp_n(n_ptr, cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-    const uint32_t t = tile_keys[k];
-    if (t >= (uint32_t)n_tiles) continue;
-    if (k == 0 || tile_keys[k - 1] != t) ranges[2 * t] = k;
-    if (k == K - 1 || tile_keys[k + 1] != t) ranges[2 * t + 1] = k + 1;
+  constexpr uint32_t kNone = 0xffffffffu;  // outside [0, K): differs from every tile
+  // four consecutive keys per thread (one 16-byte load; the workspace is
+  // 256-byte aligned) and their two neighbours
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; 4 * q < K; q += gridDim.x * blockDim.x) {
+    const int k0 = 4 * q;
+    uint32_t v[6];
+    if (k0 + 4 <= K) {
+      const uint4 u = *reinterpret_cast<const uint4*>(tile_keys + k0);
+      v[1] = u.x;
+      v[2] = u.y;
+      v[3] = u.z;
+      v[4] = u.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[1 + j] = k0 + j < K ? tile_keys[k0 + j] : kNone;
+    }
+    v[0] = k0 > 0 ? tile_keys[k0 - 1] : kNone;
+    v[5] = k0 + 4 < K ? tile_keys[k0 + 4] : kNone;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t t = v[1 + j];
+      if (k0 + j >= K || t >= (uint32_t)n_tiles) continue;
+      if (v[j] != t) ranges[2 * t] = k0 + j;
+      if (v[j + 2] != t) ranges[2 * t + 1] = k0 + j + 1;
+    }
   }
 }
 
@@ -575,8 +595,9 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   if (st != HYRF_OK) return st;
   // 4. per-tile ranges and (optionally) the composed 64-bit keys
   const int kb = (int)((cap + 255) / 256 < num_sms() * 8 ? (cap + 255) / 256 : num_sms() * 8);
+  const int rb = (int)((cap + 1023) / 1024 < num_sms() * 8 ? (cap + 1023) / 1024 : num_sms() * 8);
   HYRF_LAUNCH("k_ranges", s,
-              k_ranges<<<kb, 256, 0, s>>>(w.tk_a, a.n_instances, capi, n_tiles, a.ranges));
+              k_ranges<<<rb, 256, 0, s>>>(w.tk_a, a.n_instances, capi, n_tiles, a.ranges));
   if (a.keys) {
     HYRF_LAUNCH("k_keys64", s,
                 k_keys64<<<kb, 256, 0, s>>>(w.tk_a, a.vals, a.depth, a.n_instances, capi, a.keys));
