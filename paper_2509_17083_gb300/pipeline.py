@@ -54,25 +54,31 @@ class DeviceModel:
         self.zero_grad()
 
     def zero_grad(self):
+        """Zero every gradient buffer. They are f32 views of one flat buffer
+        (each 256-byte aligned), so this is one fill; buffers replaced later
+        (density control, storage order) are zeroed one by one."""
         d = self.device
         if not self.grad:
-            self.grad = dict(
-                pos=torch.zeros_like(self.pos), alpha_e=torch.zeros_like(self.alpha_e),
-                scale_e=torch.zeros_like(self.scale_e), color_e=torch.zeros_like(self.color_e),
-                rad_table=torch.zeros(self.rad_table.shape, device=d),
-                geo_W=[torch.zeros(w.shape, device=d) for w in self.geo_W],
-                geo_b=[torch.zeros_like(b) for b in self.geo_b],
-                col_W=[torch.zeros(w.shape, device=d) for w in self.col_W],
-                col_b=[torch.zeros_like(b) for b in self.col_b])
-            self.grad["geo_table"] = (self.grad["rad_table"] if self.coupled
-                                      else torch.zeros(self.geo_table.shape, device=d))
-        else:
-            for v in self.grad.values():
-                if isinstance(v, list):
-                    for x in v:
-                        x.zero_()
-                else:
-                    v.zero_()
+            shapes = dict(pos=self.pos.shape, alpha_e=self.alpha_e.shape, scale_e=self.scale_e.shape,
+                          color_e=self.color_e.shape, rad_table=self.rad_table.shape)
+            if not self.coupled:
+                shapes["geo_table"] = self.geo_table.shape
+            lists = dict(geo_W=[w.shape for w in self.geo_W], geo_b=[b.shape for b in self.geo_b],
+                         col_W=[w.shape for w in self.col_W], col_b=[b.shape for b in self.col_b])
+            flat = _FlatGrads([*shapes.values(), *[x for v in lists.values() for x in v]], d)
+            views = iter(flat.views)
+            self.grad = {k: next(views) for k in shapes}
+            for k, v in lists.items():
+                self.grad[k] = [next(views) for _ in v]
+            if self.coupled:
+                self.grad["geo_table"] = self.grad["rad_table"]
+            self._flat = flat
+            return
+        self._flat.zero_()
+        for v in self.grad.values():
+            for x in (v if isinstance(v, list) else [v]):
+                if not self._flat.owns(x):
+                    x.zero_()
 
     def fields_struct(self):
         fl = self.fl
@@ -108,7 +114,7 @@ class DeviceModel:
         H.hyrf_permute_rows(perm[:n], pairs)
         for name, dst in new:
             setattr(self, name, dst)
-            self.grad[name] = torch.zeros_like(dst)
+            self.grad[name].zero_()  # same shape: the buffer stays
         return perm[:n]
 
     def quantize_u8(self, on=True):
@@ -129,6 +135,26 @@ class DeviceModel:
         g = self.grad
         return H.field_grads(g["geo_table"], g["rad_table"], g["geo_W"], g["geo_b"], g["col_W"],
                              g["col_b"])
+
+
+class _FlatGrads:
+    """f32 buffers of the given shapes as views of one zero-initialised
+    allocation, each starting on a 256-byte boundary."""
+
+    def __init__(self, shapes, device):
+        offs, total = [], 0
+        for sh in shapes:
+            offs.append(total)
+            total += (math.prod(sh) + 63) // 64 * 64
+        self.buf = torch.zeros(max(total, 1), device=device)
+        self.views = [self.buf.narrow(0, o, math.prod(sh)).view(sh) for o, sh in zip(offs, shapes)]
+        self._ids = {id(v) for v in self.views}
+
+    def zero_(self):
+        self.buf.zero_()
+
+    def owns(self, t):
+        return id(t) in self._ids
 
 
 def shared_workspaces(device="cuda"):
@@ -187,7 +213,8 @@ class ViewRenderer:
         self.C = z(Hh, W, 3)
         self.loss = z(1)
         self.dC, self.dT = z(Hh, W, 3), z(Hh, W)
-        self.d_mean2d, self.d_conic, self.d_alpha, self.d_color = z(n, 2), z(n, 3), z(n), z(n, 3)
+        self._dvis = _FlatGrads([(n, 2), (n, 3), (n,), (n, 3)], d)  # zeroed by one fill
+        self.d_mean2d, self.d_conic, self.d_alpha, self.d_color = self._dvis.views
         self.d_scale, self.d_quat = z(n, 3), z(n, 4)
         # scratch of the library calls; views that run one after the other on
         # one stream may share one dict (see shared_workspaces)
@@ -366,8 +393,7 @@ class ViewRenderer:
         visible Gaussians' dL/d(alpha, scale, quat, color) and adds the
         projection's dL/dpos."""
         m = self.m
-        for t in (self.d_mean2d, self.d_conic, self.d_alpha, self.d_color):
-            t.zero_()
+        self._dvis.zero_()
         g = m.grads_struct()
         if self._overlap():
             # the background's whole reverse on the side stream, concurrently

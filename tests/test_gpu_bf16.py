@@ -119,8 +119,11 @@ def test_bf16_psnr_within_005_db_of_fp32():
 
 def test_saved_features_match_regathered():
     """The backward fed with the forward's saved hash features equals the
-    backward that gathers them again (same bf16 features; only the order of
-    float atomics differs)."""
+    backward that gathers them again (same bf16 features). The two differ in
+    the order of float atomics and, with saved features, in running the
+    background's reverse beside the compositing reverse, whose dL/dT_final
+    T_final then comes from the composited image (C - C_fg, rounded): a few
+    1e-6 relative, so gradients are held to 1e-4."""
     w = _workload("bf16", n=20000, W=257, H_=171)
     out = []
     for save in (True, False):
@@ -141,7 +144,7 @@ def test_saved_features_match_regathered():
         out.append((np_(r.C), flat))
     assert np.array_equal(out[0][0], out[1][0])
     for k, g in out[0][1].items():
-        assert rel_l2(g, out[1][1][k]) < 1e-5, k
+        assert rel_l2(g, out[1][1][k]) < 1e-4, k
 
 
 def test_background_skip_below_tau_T():
