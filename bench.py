@@ -5,10 +5,14 @@ exact neural background, L1 loss), on synthetic seeded data.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|f32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
 
-One "step" = query_fields -> project -> bin_sort -> rasterize ->
-composite_background -> loss -> every reverse call, inputs resident in HBM.
-L2 is flushed (256 MiB write) between timed steps. Prints one JSON line.
-Multi-GPU: independent replicas (one view per rank), no collective.
+One "step" = gradient zeroing -> pre-cull -> query_fields (the depth order
+and the background's feature gather beside it on a second stream) ->
+project -> bin_sort -> rasterize -> composite_background -> loss -> every
+reverse call (the background's on the second stream), inputs resident in
+HBM, replayed as one CUDA graph (pipeline.StepGraph; --no-graph issues the
+calls one by one). L2 is flushed (256 MiB write) between timed steps.
+Prints one JSON line. Multi-GPU: independent replicas (one view per rank),
+no collective.
 """
 import argparse
 import json
