@@ -36,3 +36,27 @@ def test_two_replicas_take_the_slowest_step():
     mp.start_processes(_rank, args=(ws, _free_port(), out), nprocs=ws, start_method="spawn", join=True)
     assert dict(out) == {0: 2.5, 1: 2.5}
     assert bench.whole_job_rate(2.5, ws) == pytest.approx(800.0)
+
+
+def test_flat_gradient_views_are_aligned_and_disjoint():
+    """The pipeline's gradient buffers are views of one allocation: each
+    starts on a 256-byte boundary, none overlaps another, and one fill
+    zeroes them all."""
+    import torch
+    from paper_2509_17083_gb300.pipeline import _FlatGrads
+    shapes = [(7, 3), (5,), (16, 2048, 2), (64, 32), (3, 64), (1,), (0, 2)]
+    f = _FlatGrads(shapes, "cpu")
+    base = f.buf.data_ptr()
+    spans = []
+    for v, sh in zip(f.views, shapes):
+        assert tuple(v.shape) == sh
+        off = v.data_ptr() - base
+        assert off % 256 == 0
+        spans.append((off, off + v.numel() * 4))
+        v.fill_(1.0)
+    spans.sort()
+    assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+    assert sum(v.numel() for v in f.views) == int(f.buf.sum().item())
+    f.zero_()
+    assert not any(v.any() for v in f.views)
+    assert f.owns(f.views[0]) and not f.owns(torch.zeros(3))
