@@ -6,7 +6,7 @@
 // that wants the opposite: as many independent loads and atomics in flight as
 // possible. So they run here, in their own kernels, with one thread per
 // (row, level) pair: a CTA holds 32 rows (the lanes) x 16 levels (the warps),
-// 512 threads, 3-4 CTAs per SM.
+// 512 threads, 4 CTAs per SM.
 //
 //   k_gather   rows -> bf16 features X [rows][32] per field (row-major; the
 //              decoder kernels stage them into their operand tiles)
