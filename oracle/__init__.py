@@ -46,7 +46,8 @@ class _Grid(C.Structure):
 
 class _Mlp(C.Structure):
     _fields_ = [("n_in", C.c_int32), ("width", C.c_int32), ("n_hidden", C.c_int32),
-                ("n_out", C.c_int32), ("W", _f64p * 3), ("b", _f64p * 3)]
+                ("n_out", C.c_int32), ("W", _f64p * 3), ("b", _f64p * 3),
+                ("relu_replay", C.c_int32)]
 
 
 class _MlpGrad(C.Structure):
@@ -74,6 +75,7 @@ def lib():
         _lib.orc_ssim.restype = C.c_double
         _lib.orc_bin_sort.restype = C.c_int64
         _lib.orc_level_index.restype = C.c_uint32
+        _lib.orc_branch_sum.restype = C.c_uint64
     return _lib
 
 
@@ -121,9 +123,39 @@ def _grid(g, keep):
     return s
 
 
-def _mlp(m, keep):
+# Precision in which the decoders' ReLU branches are decided (orc_mlp.relu_replay).
+_RELU_REPLAY = {"f64": 0, "bf16": 1}
+
+
+def branch_sum_reset():
+    lib().orc_branch_sum_reset()
+
+
+def branch_sum():
+    """Sum of a 64-bit mix of every decoder evaluation's ReLU branch pattern
+    since the last branch_sum_reset (changes when any branch changes)."""
+    return int(lib().orc_branch_sum())
+
+
+def replay_relu(fields, precision="bf16"):
+    """A shallow copy of `fields` whose decoders decide every hidden unit's
+    ReLU branch as a kernel with `precision` operands does ("bf16": layer
+    inputs and hidden outputs rounded to bfloat16, sums exact) and evaluate
+    FP64 values on those branches; "f64" is the plain FP64 decoder. The
+    reading: where floating point decides a branch, the oracle takes it in the
+    kernel's precision (as the FP32 replays of the integer decisions do)."""
+    import copy
+    if precision not in _RELU_REPLAY:
+        raise ValueError(precision)
+    f = copy.copy(fields)
+    f.relu_precision = precision
+    return f
+
+
+def _mlp(m, keep, relu="f64"):
     s = _Mlp()
     s.n_in, s.width, s.n_hidden, s.n_out = m.n_in, m.width, m.n_hidden, m.n_out
+    s.relu_replay = _RELU_REPLAY[relu]
     for l in range(m.n_hidden + 1):
         s.W[l] = keep.d(np.asarray(m.W[l], dtype=np.float64))
         s.b[l] = keep.d(np.asarray(m.b[l], dtype=np.float64))
@@ -137,8 +169,9 @@ def fields_struct(fl, keep):
         s.box.hi[k] = float(fl.box_hi[k])
     s.geo = _grid(fl.geo, keep)
     s.rad = _grid(fl.rad, keep)
-    s.geo_mlp = _mlp(fl.geo_mlp, keep)
-    s.col_mlp = _mlp(fl.col_mlp, keep)
+    relu = getattr(fl, "relu_precision", "f64")
+    s.geo_mlp = _mlp(fl.geo_mlp, keep, relu)
+    s.col_mlp = _mlp(fl.col_mlp, keep, relu)
     s.pe_freq, s.pe_pad = fl.pe_freq, fl.pe_pad
     return s
 
@@ -196,9 +229,9 @@ def level_index(grid, l, ix, iy, iz):
     return lib().orc_level_index(C.byref(g), l, ix, iy, iz)
 
 
-def mlp_forward(mlp, x):
+def mlp_forward(mlp, x, relu="f64"):
     keep = _Keep()
-    m = _mlp(mlp, keep)
+    m = _mlp(mlp, keep, relu)
     x, xp = _d(x)
     y = np.zeros(mlp.n_out)
     lib().orc_mlp_forward(C.byref(m), xp, _ptr(y, _f64p))

@@ -78,11 +78,22 @@ typedef struct {
 } orc_grid;
 
 /* Decoder MLP (Eqs. 4 and 6): n_hidden ReLU layers of `width`, linear output.
- * W[0]: [width][n_in], W[l]: [width][width], W[n_hidden]: [n_out][width]. */
+ * W[0]: [width][n_in], W[l]: [width][width], W[n_hidden]: [n_out][width].
+ * relu_replay selects the precision in which each hidden unit's ReLU branch
+ * (active or not) is decided; the values themselves are always FP64:
+ *   0: from the FP64 pre-activation;
+ *   1: from a replay of the layers as a BF16-operand kernel evaluates them:
+ *      every layer input rounded to bfloat16 (through float, ties to even),
+ *      products summed exactly, the ReLU output rounded to bfloat16 before
+ *      the next layer. A kernel that accumulates in FP32 then takes the same
+ *      branches except where a pre-activation lies within FP32 rounding of
+ *      zero, so the FP64 values differ from it by rounding, not by a flipped
+ *      branch. */
 typedef struct {
   int32_t n_in, width, n_hidden, n_out;
   const double* W[3];
   const double* b[3];
+  int32_t relu_replay;
 } orc_mlp;
 
 typedef struct {
@@ -141,11 +152,20 @@ int32_t orc_query_fields_backward(int32_t n, const double* pos, const double* al
                                   const orc_mlp_grad* d_geo_mlp, const orc_mlp_grad* d_col_mlp);
 
 /* Smallest relative ReLU margin of each point's decoders: over every hidden
- * unit, min |z| / (sum_i |W_i x_i| + |b|), where z is the pre-activation (a
- * diagnostic used to find points whose ReLU decisions a lower-precision
- * evaluation could flip). margin_geo[n], margin_col[n]. */
+ * unit, min |z| / (sum_i |W_i a_i| + |b|), where z is the pre-activation the
+ * unit's branch is decided on and a the layer input (FP64, or the replay's
+ * values when relu_replay is set): a diagnostic used to find points whose
+ * ReLU branches another evaluation could take differently.
+ * margin_geo[n], margin_col[n]. */
 int32_t orc_decoder_margins(int32_t n, const double* pos, const orc_camera* cam,
                             const orc_fields* fl, double* margin_geo, double* margin_col);
+
+/* Running sum, over every decoder evaluation since the last reset, of a
+ * 64-bit mix of that evaluation's hidden ReLU branch pattern (a diagnostic
+ * for finite-difference drivers: a step that changes any branch anywhere
+ * changes the sum). */
+void orc_branch_sum_reset(void);
+uint64_t orc_branch_sum(void);
 
 /* ---------------- stage 3: projection (EWA, 3DGS conventions) ----------- */
 /* FP64: mean2d[n][2], conic[n][3] (a, b, c of the inverse 2D covariance),

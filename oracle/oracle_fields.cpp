@@ -2,6 +2,7 @@
 // Test infrastructure only (see hyrf_oracle.h). Plain FP64, one point at a time.
 #include "oracle_internal.h"
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -134,14 +135,44 @@ static void layer_dims(const orc_mlp& m, int l, int& n_out, int& n_in) {
   n_out = (l == m.n_hidden) ? m.n_out : m.width;
 }
 
-// Smallest relative margin of the hidden pre-activations of one decoder.
-static double mlp_margin(const orc_mlp& m, const double* x) {
+// Round to the nearest bfloat16 through float (ties to even), as a kernel
+// that converts its FP32 values to bfloat16 does.
+static double to_bf16(double v) {
+  float f = (float)v;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Sum of the branch-pattern mixes of every decoder evaluation (see
+// orc_branch_sum); atomic so that evaluations on several threads add up.
+static std::atomic<uint64_t> g_branch_sum{0};
+
+// splitmix64 finaliser: a 64-bit mix of the pattern's running hash.
+static uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// ReLU branches of the hidden units for input x: on[l][o] = 1 where unit o of
+// hidden layer l is active, decided in the precision m.relu_replay selects
+// (see hyrf_oracle.h). Returns the smallest relative margin
+// min |z| / (sum_i |W_i a_i| + |b|) of the pre-activations decided on.
+static double relu_branches(const orc_mlp& m, const double* x, std::vector<std::vector<char>>& on) {
+  const bool rep = m.relu_replay == 1;
   std::vector<double> a(x, x + m.n_in), next;
+  if (rep)
+    for (double& v : a) v = to_bf16(v);
   double mg = 1e300;
+  on.assign(m.n_hidden, {});
   for (int l = 0; l < m.n_hidden; ++l) {
     int no, ni;
     layer_dims(m, l, no, ni);
     next.assign(no, 0.0);
+    on[l].assign(no, 0);
     for (int o = 0; o < no; ++o) {
       double z = m.b[l][o], mag = std::fabs(m.b[l][o]);
       for (int i = 0; i < ni; ++i) {
@@ -149,16 +180,33 @@ static double mlp_margin(const orc_mlp& m, const double* x) {
         mag += std::fabs(m.W[l][(size_t)o * ni + i] * a[i]);
       }
       if (mag > 0.0) mg = std::min(mg, std::fabs(z) / mag);
-      next[o] = z > 0.0 ? z : 0.0;
+      on[l][o] = z > 0.0;
+      double h = z > 0.0 ? z : 0.0;
+      next[o] = rep ? to_bf16(h) : h;
     }
     a.swap(next);
   }
+  uint64_t h = 0x9e3779b97f4a7c15ull;
+  for (const auto& layer : on)
+    for (char b : layer) h = mix64(h ^ (uint64_t)(b + 1));
+  g_branch_sum.fetch_add(h, std::memory_order_relaxed);
   return mg;
 }
 
-// Forward keeping every layer input (acts[l]) and pre-activation (pre[l]).
-void mlp_forward_acts(const orc_mlp& m, const double* x, std::vector<std::vector<double>>& acts,
-                      std::vector<std::vector<double>>& pre, double* y) {
+static double mlp_margin(const orc_mlp& m, const double* x) {
+  std::vector<std::vector<char>> on;
+  return relu_branches(m, x, on);
+}
+
+// Forward keeping every layer input (acts[l]), pre-activation (pre[l]) and
+// ReLU branch (on[l]). The values are FP64; each hidden unit passes its
+// pre-activation where its branch is active, else 0 (Sec. 4.1: ReLU hidden
+// layers, linear output).
+static void mlp_forward_acts(const orc_mlp& m, const double* x,
+                             std::vector<std::vector<double>>& acts,
+                             std::vector<std::vector<double>>& pre,
+                             std::vector<std::vector<char>>& on, double* y) {
+  relu_branches(m, x, on);
   acts.assign(m.n_hidden + 1, {});
   pre.assign(m.n_hidden + 1, {});
   acts[0].assign(x, x + m.n_in);
@@ -173,7 +221,7 @@ void mlp_forward_acts(const orc_mlp& m, const double* x, std::vector<std::vector
     }
     if (l < m.n_hidden) {
       acts[l + 1].resize(no);
-      for (int o = 0; o < no; ++o) acts[l + 1][o] = pre[l][o] > 0.0 ? pre[l][o] : 0.0;
+      for (int o = 0; o < no; ++o) acts[l + 1][o] = on[l][o] ? pre[l][o] : 0.0;
     }
   }
   for (int o = 0; o < m.n_out; ++o) y[o] = pre[m.n_hidden][o];
@@ -181,15 +229,17 @@ void mlp_forward_acts(const orc_mlp& m, const double* x, std::vector<std::vector
 
 void mlp_forward(const orc_mlp& m, const double* x, double* y) {
   std::vector<std::vector<double>> acts, pre;
-  mlp_forward_acts(m, x, acts, pre, y);
+  std::vector<std::vector<char>> on;
+  mlp_forward_acts(m, x, acts, pre, on, y);
 }
 
 // Reverse pass: accumulates dW, db (if grad is given) and writes dL/dx.
 void mlp_backward(const orc_mlp& m, const double* x, const double* dy, const orc_mlp_grad* grad,
                   double* dx) {
   std::vector<std::vector<double>> acts, pre;
+  std::vector<std::vector<char>> on;
   std::vector<double> y(m.n_out);
-  mlp_forward_acts(m, x, acts, pre, y.data());
+  mlp_forward_acts(m, x, acts, pre, on, y.data());
   std::vector<double> dz(dy, dy + m.n_out);
   for (int l = m.n_hidden; l >= 0; --l) {
     int no, ni;
@@ -206,9 +256,9 @@ void mlp_backward(const orc_mlp& m, const double* x, const double* dy, const orc
     if (l == 0) {
       for (int i = 0; i < ni; ++i) dx[i] = da[i];
     } else {
-      // ReLU of layer l-1: derivative 1 where the pre-activation is > 0.
+      // ReLU of hidden layer l-1: derivative 1 on its active branch.
       dz.assign(ni, 0.0);
-      for (int i = 0; i < ni; ++i) dz[i] = pre[l - 1][i] > 0.0 ? da[i] : 0.0;
+      for (int i = 0; i < ni; ++i) dz[i] = on[l - 1][i] ? da[i] : 0.0;
     }
   }
 }
@@ -310,6 +360,10 @@ uint32_t orc_level_index(const orc_grid* g, int32_t l, uint32_t ix, uint32_t iy,
 void orc_mlp_forward(const orc_mlp* m, const double* x, double* y) { mlp_forward(*m, x, y); }
 
 void orc_pos_enc(const double d[3], int32_t n_freq, double* out) { pos_enc(d, n_freq, out); }
+
+void orc_branch_sum_reset(void) { g_branch_sum.store(0); }
+
+uint64_t orc_branch_sum(void) { return g_branch_sum.load(); }
 
 static bool fields_ok(const orc_fields* fl) {
   if (!fl) return false;

@@ -191,6 +191,20 @@ using namespace hyrf;
 
 #define S(x) static_cast<cudaStream_t>(x)
 
+namespace hyrf {
+// Host-side argument checks shared by hyrf_bin_sort, its reverse and
+// hyrf_bin_sort_noalloc (no device work, no workspace).
+hyrf_status bin_sort_check(const hyrf_bin_sort_args* a) {
+  if (!a || a->n < 0 || a->tiles_x <= 0 || a->tiles_y <= 0 || a->capacity < 0 ||
+      a->capacity > 0x7fffffffLL || (int64_t)a->tiles_x * a->tiles_y > (1 << 24))
+    return HYRF_ERR_INVALID_ARG;
+  if (!a->n_vis || !a->ranges || !a->n_instances) return HYRF_ERR_INVALID_ARG;
+  if (a->n > 0 && (!a->rect || !a->ntiles || !a->depth)) return HYRF_ERR_INVALID_ARG;
+  if (a->capacity > 0 && !a->vals) return HYRF_ERR_INVALID_ARG;
+  return HYRF_OK;
+}
+}  // namespace hyrf
+
 extern "C" {
 
 // ------------------------------------------------------------------ query fields
@@ -316,15 +330,6 @@ size_t hyrf_bin_sort_workspace_size(const hyrf_bin_sort_args* a) {
   return a && a->n >= 0 && a->capacity >= 0 ? bin_sort_workspace(a->n, a->capacity) : 0;
 }
 
-static hyrf_status bin_sort_check(const hyrf_bin_sort_args* a) {
-  if (!a || a->n < 0 || a->tiles_x <= 0 || a->tiles_y <= 0 || a->capacity < 0 ||
-      a->capacity > 0x7fffffffLL || (int64_t)a->tiles_x * a->tiles_y > (1 << 24))
-    return HYRF_ERR_INVALID_ARG;
-  if (!a->n_vis || !a->ranges || !a->n_instances) return HYRF_ERR_INVALID_ARG;
-  if (a->n > 0 && (!a->rect || !a->ntiles || !a->depth)) return HYRF_ERR_INVALID_ARG;
-  if (a->capacity > 0 && !a->vals) return HYRF_ERR_INVALID_ARG;
-  return HYRF_OK;
-}
 
 hyrf_status hyrf_bin_sort(const hyrf_bin_sort_args* a, void* ws, size_t ws_bytes, void* stream) {
   hyrf_status st = bin_sort_check(a);

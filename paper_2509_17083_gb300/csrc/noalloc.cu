@@ -8,6 +8,7 @@
 namespace hyrf {
 
 size_t bin_sort_workspace(int n, int64_t cap);
+hyrf_status bin_sort_check(const hyrf_bin_sort_args* a);
 hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t s);
 
 // The scratch array. Every GPU that loads the library holds it until the
@@ -46,7 +47,7 @@ extern "C" hyrf_status hyrf_bin_sort_noalloc(const hyrf_bin_sort_args* a, void* 
   if (!a) return HYRF_ERR_INVALID_ARG;
   if (a->n > HYRF_NOALLOC_MAX_GAUSSIANS || a->capacity > HYRF_NOALLOC_MAX_INSTANCES)
     return HYRF_ERR_INVALID_ARG;
-  hyrf_status st = hyrf_bin_sort_backward(a, nullptr, 0, stream);  // argument checks only
+  hyrf_status st = bin_sort_check(a);  // host-side argument checks, no device work
   if (st != HYRF_OK) return st;
   if (bin_sort_workspace(a->n, a->capacity) > (size_t)HYRF_NOALLOC_SCRATCH_BYTES)
     return HYRF_ERR_INVALID_ARG;

@@ -264,6 +264,21 @@ def noise_target(rng, cam):
     return rng.uniform(0.0, 1.0, (cam.height, cam.width, 3)).astype(np.float32)
 
 
+def teacher_of(w, seed=2, sigma=0.3):
+    """The workload's scene with its explicit colour and opacity logits moved
+    by N(0, sigma^2) draws (a stand-in for the ground-truth image of a scene
+    the student nearly fits): rendering it gives a target image a few tens of
+    dB from the student's, against which PSNR differences of a hundredth of
+    a dB are measurable."""
+    import dataclasses
+    rng = _rng(seed)
+    g = w.gaussians
+    g2 = dataclasses.replace(
+        g, color_e=(g.color_e + sigma * rng.standard_normal(g.color_e.shape)).astype(np.float32),
+        alpha_e=(g.alpha_e + sigma * rng.standard_normal(g.alpha_e.shape)).astype(np.float32))
+    return dataclasses.replace(w, gaussians=g2)
+
+
 # ---------------------------------------------------------------------------
 # The five workloads. Each accepts size overrides so tests can run the same
 # generator at sizes the oracle finishes in seconds.

@@ -16,6 +16,14 @@ TOL_IMG_F32_TRAINED = 2e-3
 TOL_GRAD_F32_TRAINED = 1e-2
 TOL_Q_F32 = 2e-6        # field-query outputs, configs' initialisation
 TOL_Q_F32_TRAINED = 2e-4
+# BF16 decoders against the oracle that takes its ReLU branches in the
+# kernel's precision (oracle.replay_relu(fields, "bf16")): a row or pixel is
+# left out of a gradient comparison only when one of its hidden
+# pre-activations lies within this relative margin of zero in the replay.
+# What is left to flip a branch is the FP32 hash coordinate of the kernel
+# (features off by ~1e-3 of a bfloat16 step, which moves a pre-activation by
+# ~1e-4 of its magnitude at most) and FP32 accumulation (~1e-7).
+RELU_REPLAY_MARGIN_BF16 = 2e-4
 
 
 def np_(t):
@@ -28,6 +36,13 @@ def rel_l2(a, b):
     b = np.asarray(b, np.float64).ravel()
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def psnr(a, b):
+    """PSNR in dB of image a against image b (values clipped to [0, 1])."""
+    a = np.clip(np.asarray(a, np.float64), 0.0, 1.0)
+    b = np.clip(np.asarray(b, np.float64), 0.0, 1.0)
+    return float(-10.0 * np.log10(np.mean((a - b) ** 2)))
 
 
 def cuda_f32(a):

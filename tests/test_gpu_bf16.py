@@ -3,7 +3,7 @@ the forward, FP32 accumulation and compositing, loss scale 1024) against the
 FP64 oracle evaluated on the same bf16 parameter values.
 
 Tolerances: image 2e-3 absolute, gradients 2e-2 relative L2, and the PSNR
-against the target within 0.05 dB of the FP32 path's.
+against a teacher image within 0.05 dB of the FP32 path's.
 """
 import numpy as np
 import pytest
@@ -13,7 +13,8 @@ import oracle
 from paper_2509_17083_gb300 import hyrf as H
 from paper_2509_17083_gb300 import synth
 from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer
-from tests.gpu_util import TOL_GRAD_BF16, TOL_IMG_BF16, cuda_f32, np_, rel_l2
+from tests.gpu_util import (RELU_REPLAY_MARGIN_BF16, TOL_GRAD_BF16, TOL_IMG_BF16, cuda_f32, np_,
+                             psnr, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -46,10 +47,6 @@ def _render(w, mask=None, backward=True, qmask=None):
     return m, r
 
 
-# bf16 activations carry ~2^-9 relative rounding per value: Gaussians with a
-# hidden pre-activation within 3e-3 (relative) of the ReLU kink are left out
-# of the decoder-backward comparison on both sides.
-RELU_MARGIN_BF16 = (3e-3, 3e-3)
 # Trained-like tables add the FP32 hash-coordinate error (up to ~2e-3 of
 # image, see gpu_util) to the bf16 budget; with corner values spread ~0.3
 # the bf16-rounded features and hidden activations move the decoder outputs
@@ -78,43 +75,65 @@ def test_query_fields_tensor_cores_match_oracle():
 
 @pytest.mark.parametrize("init", [1e-4, 0.3])
 def test_bf16_iteration_matches_oracle(init):
+    """Whole iteration (Sec. 3.1 Eq. 1, Sec. 3.2 Eqs. 2-7, Sec. 3.3 Eqs.
+    10-12) against the FP64 oracle that takes its decoders' ReLU branches as
+    the BF16 kernels take them. The image is compared on every pixel whose
+    compositing decisions and tile membership are away from their thresholds
+    (ReLU is continuous: a branch changes the image by rounding only); the
+    gradients leave out, on both sides, the pixels and Gaussian rows whose
+    replayed pre-activations lie within RELU_REPLAY_MARGIN_BF16 of a kink."""
     w = _workload("bf16", init=init)
-    fw = oracle.render(w.gaussians, w.fields, w.cams[0], w.bg)
-    mask = oracle.decision_safe_mask(fw, w.cams[0], fields=w.fields, bg=w.bg,
-                                     bg_relu_margin=RELU_MARGIN_BF16[1])
-    assert mask.mean() > 0.05, mask.mean()
-    qmask = oracle.relu_safe_mask(w.gaussians, w.fields, w.cams[0], fw["ids"], *RELU_MARGIN_BF16)
-    assert qmask.sum() > 1000, qmask.sum()
-    m, r = _render(w, mask.astype(np.float32), qmask=qmask)
+    fr = oracle.replay_relu(w.fields, "bf16")
+    cam = w.cams[0]
+    fw = oracle.render(w.gaussians, fr, cam, w.bg)
+    img_mask = oracle.decision_safe_mask(fw, cam)
+    assert img_mask.mean() >= 0.9, img_mask.mean()
+    grad_mask = img_mask & (oracle.bg_margins(cam, fr, w.bg) > RELU_REPLAY_MARGIN_BF16)
+    assert grad_mask.mean() >= 0.75, grad_mask.mean()
+    qmask = oracle.relu_safe_mask(w.gaussians, fr, cam, fw["ids"], RELU_REPLAY_MARGIN_BF16,
+                                  RELU_REPLAY_MARGIN_BF16)
+    assert qmask.mean() >= 0.75, qmask.mean()
+    m, r = _render(w, grad_mask.astype(np.float32), qmask=qmask)
     assert H.read_status(r.status) == 0
-    L, fw, grads, _ = oracle.loss_and_grads(w.gaussians, w.fields, w.cams[0], w.bg, w.targets[0],
-                                            w.ssim_lambda, dC_mask=mask, query_mask=qmask)
+    L, fw, grads, _ = oracle.loss_and_grads(w.gaussians, fr, cam, w.bg, w.targets[0],
+                                            w.ssim_lambda, dC_mask=grad_mask, query_mask=qmask)
     err = np.abs(np_(r.C) - fw["C"]).max(-1)
     tol = TOL_IMG_BF16 if init <= 1e-3 else TOL_IMG_BF16_TRAINED
-    assert err[mask].max() < tol, err[mask].max()
+    assert err[img_mask].max() < tol, err[img_mask].max()
     g = m.grad
+    tol = TOL_GRAD_BF16_TRAINED if init > 1e-3 else TOL_GRAD_BF16
+    errs = {}
     for key in ("pos", "alpha_e", "scale_e", "color_e", "geo_table", "rad_table"):
-        e = rel_l2(np_(g[key]), grads[key])
-        tol = TOL_GRAD_BF16_TRAINED if init > 1e-3 else TOL_GRAD_BF16
-        assert e < tol, (key, e)
+        errs[key] = rel_l2(np_(g[key]), grads[key])
     for key in ("geo_W", "col_W", "geo_b", "col_b"):
         for l in range(3):
-            e = rel_l2(np_(g[key][l]), grads[key][l])
-            assert e < (TOL_GRAD_BF16_TRAINED if init > 1e-3 else TOL_GRAD_BF16), (key, l, e)
+            errs[f"{key}{l}"] = rel_l2(np_(g[key][l]), grads[key][l])
+    print(f"bf16 iteration init={init}: image {img_mask.mean():.3f} of pixels, max err "
+          f"{err[img_mask].max():.2e}; gradients over {grad_mask.mean():.3f} of pixels, "
+          f"{qmask.mean():.3f} of rows; worst {max(errs, key=errs.get)} {max(errs.values()):.2e}")
+    for key, e in errs.items():
+        assert e < tol, (key, e)
 
 
 def test_bf16_psnr_within_005_db_of_fp32():
-    def psnr(img, tgt):
-        mse = float(np.mean((np.clip(img, 0, 1) - tgt) ** 2))
-        return -10.0 * np.log10(mse)
-    wb = _workload("bf16", init=0.3)
+    """Eq. 12's image term measured as PSNR against a teacher image (the same
+    scene with its explicit colour and opacity logits moved by N(0, 0.3^2),
+    rendered on the FP32 path, ~30 dB from the student): the BF16 render's
+    PSNR is within 0.05 dB of the FP32 render's, and the two renders agree to
+    above 60 dB PSNR with each other."""
     wf = _workload("f32", init=0.3)
+    wb = _workload("bf16", init=0.3)
+    # the bf16 workload is the f32 one with tables/weights rounded
+    _, rt = _render(synth.teacher_of(wf), backward=False)
+    teacher = np_(rt.C)
     _, rb = _render(wb, backward=False)
     _, rf = _render(wf, backward=False)
-    # the same scene: the bf16 workload is the f32 one with tables/weights rounded
-    pb = psnr(np_(rb.C), wb.targets[0])
-    pf = psnr(np_(rf.C), wf.targets[0])
+    pb, pf = psnr(np_(rb.C), teacher), psnr(np_(rf.C), teacher)
+    pbf = psnr(np_(rb.C), np_(rf.C))
+    print(f"PSNR vs teacher: bf16 {pb:.4f} dB, f32 {pf:.4f} dB; bf16 vs f32 {pbf:.2f} dB")
+    assert 20.0 < pf < 45.0, pf  # the teacher is near, not identical
     assert abs(pb - pf) <= 0.05, (pb, pf)
+    assert pbf > 60.0, pbf
 
 
 def test_saved_features_match_regathered():
@@ -200,7 +219,8 @@ def test_u8_codec_codes_and_render_match_oracle():
     torch.cuda.synchronize()
     assert H.read_status(r.status) == 0
     fw = oracle.render(wq.gaussians, wq.fields, w.cams[0], w.bg)
-    mask = oracle.decision_safe_mask(fw, w.cams[0], fields=wq.fields, bg=w.bg, bg_relu_margin=RELU_MARGIN_BF16[1])
+    mask = oracle.decision_safe_mask(fw, w.cams[0])  # ReLU is continuous: images need no ReLU margin
+    assert mask.mean() >= 0.9, mask.mean()
     err = np.abs(np_(r.C) - fw["C"]).max(-1)
     assert err[mask].max() < TOL_IMG_BF16_TRAINED, err[mask].max()
     # the codec renders only
@@ -222,7 +242,8 @@ def test_f16_render_path_matches_oracle():
     torch.cuda.synchronize()
     assert H.read_status(r.status) == 0
     fw = oracle.render(w.gaussians, w.fields, w.cams[0], w.bg)
-    mask = oracle.decision_safe_mask(fw, w.cams[0], fields=w.fields, bg=w.bg, bg_relu_margin=1e-3)
+    mask = oracle.decision_safe_mask(fw, w.cams[0])
+    assert mask.mean() >= 0.9, mask.mean()
     err = np.abs(np_(r.C) - fw["C"]).max(-1)
     assert err[mask].max() < TOL_IMG_BF16_TRAINED, err[mask].max()
     # IEEE half carries 3 more mantissa bits than bf16: typical errors are smaller

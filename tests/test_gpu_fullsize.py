@@ -27,13 +27,12 @@ import oracle
 from paper_2509_17083_gb300 import hyrf as H
 from paper_2509_17083_gb300 import synth
 from paper_2509_17083_gb300.pipeline import DeviceModel, ViewRenderer
-from tests.gpu_util import TOL_GRAD_BF16, TOL_GRAD_F32, TOL_IMG_F32, cuda_f32, cuda_i32, np_, rel_l2
+from tests.gpu_util import (RELU_REPLAY_MARGIN_BF16, TOL_GRAD_BF16, TOL_GRAD_F32, TOL_IMG_F32, cuda_f32,
+                             cuda_i32, np_, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
-# bf16 decoders: relative ReLU margin below which a row is left out (as in
-# the small BF16 tests), and the trained-like table spread used here
-RELU_MARGIN_BF16 = (3e-3, 3e-3)
+# the trained-like table spread used here
 TABLE_INIT = 0.3
 N_SAMPLE = 4096
 
@@ -174,13 +173,14 @@ def test_fullsize_field_query_reverse_sampled(scene):
     g = w.gaussians
     cam = w.cams[0]
     nv = len(ids)
-    # trained-like tables put ~9 of 10 rows within the bf16 ReLU margin of a
-    # kink somewhere in their 128 hidden units: sample widely, keep the safe
-    rows = _sample(ids, 24, 16 * N_SAMPLE)
+    # the oracle takes the decoders' ReLU branches as the BF16 kernels do;
+    # rows with a replayed pre-activation near a kink are left out
+    fr = oracle.replay_relu(w.fields, "bf16")
+    rows = _sample(ids, 24, 2 * N_SAMPLE)
     sel = ids[rows]
-    ok = oracle.relu_safe_mask(g, w.fields, cam, sel, *RELU_MARGIN_BF16)
+    ok = oracle.relu_safe_mask(g, fr, cam, sel, RELU_REPLAY_MARGIN_BF16, RELU_REPLAY_MARGIN_BF16)
     rows, sel = rows[ok > 0], sel[ok > 0]
-    assert len(rows) > N_SAMPLE // 2, len(rows)
+    assert len(rows) > 1.5 * N_SAMPLE, len(rows)
     rng = np.random.default_rng(25)
     up = [(rng.standard_normal((len(rows),) + sh) * 1e-3).astype(np.float32)
           for sh in [(), (3,), (4,), (3,)]]
@@ -199,7 +199,7 @@ def test_fullsize_field_query_reverse_sampled(scene):
     torch.cuda.synchronize()
     assert H.read_status(r.status) == 0
     ref = oracle.query_fields_backward(g.pos[sel].astype(np.float64), g.alpha_e[sel], g.scale_e[sel],
-                                       g.color_e[sel], cam, w.fields, *[u.astype(np.float64) for u in up])
+                                       g.color_e[sel], cam, fr, *[u.astype(np.float64) for u in up])
     full = {k: np.zeros(np.asarray(getattr(g, k)).shape) for k in ("pos", "alpha_e", "scale_e", "color_e")}
     for k in full:
         full[k][sel] = ref[k]
@@ -238,12 +238,16 @@ def test_fullsize_background_crops(scene):
     crops = [(int(i * (W // 4) + rng.integers(0, W // 4 - cw)), int(j * (H_ // 2) + rng.integers(0, H_ // 2 - ch)))
              for i in range(4) for j in range(2)]
     dC = np.zeros((H_, W, 3), np.float32)
+    fr = oracle.replay_relu(w.fields, "bf16")
+    kept = []
     for (x0, y0) in crops:
         cc = _crop(cam, x0, y0, cw, ch)
         C, _ = oracle.background(cc, w.fields, w.bg, Cfg[y0:y0 + ch, x0:x0 + cw], T[y0:y0 + ch, x0:x0 + cw])
         assert np.abs(Cg[y0:y0 + ch, x0:x0 + cw] - C).max() < 2e-3  # bf16 decoder
-        safe = oracle.bg_margins(cc, w.fields, w.bg) > RELU_MARGIN_BF16[1]
+        safe = oracle.bg_margins(cc, fr, w.bg) > RELU_REPLAY_MARGIN_BF16
+        kept.append(safe.mean())
         dC[y0:y0 + ch, x0:x0 + cw] = rng.standard_normal((ch, cw, 3)) * safe[..., None]
+    assert np.mean(kept) > 0.75, kept
     r.dC.copy_(cuda_f32(dC))
     m.zero_grad()
     H.hyrf_composite_background_backward(r._bg_args(), ws=r.ws["bb"], d_C=r.dC, d_C_fg=None,
@@ -253,7 +257,7 @@ def test_fullsize_background_crops(scene):
     tab, cW, cb = None, None, None
     for (x0, y0) in crops:
         cc = _crop(cam, x0, y0, cw, ch)
-        ref = oracle.background_backward(cc, w.fields, w.bg, T[y0:y0 + ch, x0:x0 + cw],
+        ref = oracle.background_backward(cc, fr, w.bg, T[y0:y0 + ch, x0:x0 + cw],
                                          dC[y0:y0 + ch, x0:x0 + cw])
         e = np.abs(np_(r.dT)[y0:y0 + ch, x0:x0 + cw] - ref["T_final"]).max()
         assert e < 2e-3 * max(1.0, np.abs(ref["T_final"]).max()), e

@@ -46,11 +46,13 @@ def test_flat_gradient_views_are_aligned_and_disjoint():
     from paper_2509_17083_gb300.pipeline import _FlatGrads
     shapes = [(7, 3), (5,), (16, 2048, 2), (64, 32), (3, 64), (1,), (0, 2)]
     f = _FlatGrads(shapes, "cpu")
-    base = f.buf.data_ptr()
     spans = []
     for v, sh in zip(f.views, shapes):
         assert tuple(v.shape) == sh
-        off = v.data_ptr() - base
+        assert v.untyped_storage().data_ptr() == f.buf.untyped_storage().data_ptr()
+        # the offset within the allocation (a zero-element view may report a
+        # null data pointer, so the storage offset is the measure)
+        off = v.storage_offset() * 4
         assert off % 256 == 0
         spans.append((off, off + v.numel() * 4))
         v.fill_(1.0)
