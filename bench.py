@@ -200,7 +200,7 @@ def decoder_macs(mlp):
     return sum(a * b for a, b in zip(dims, dims[1:]))
 
 
-def kernel_work(nv, K, P, tiles, bf16, pairs=0, macs=(0, 0)):
+def kernel_work(nv, K, P, tiles, bf16, pairs=0, macs=(0, 0), active=None):
     """Algorithmic work per launch of the main kernels on the axis that
     bounds each: ("hbm", bytes) for the gathers, scatters, field kernels of
     the FP32 path and the sort (every input read once, every output written
@@ -209,7 +209,11 @@ def kernel_work(nv, K, P, tiles, bf16, pairs=0, macs=(0, 0)):
     the reverse recomputes the forward and forms dX and dW: 3x); ("alu",
     FP32 FLOPs) for the compositing (FP32_FLOPS_PER_PAIR). Units: visible
     Gaussian (nv), tile instance (K), pixel (P), evaluated pair (pairs);
-    macs = (geometry, colour) decoder multiply-accumulates per row."""
+    macs = (geometry, colour) decoder multiply-accumulates per row; active =
+    visible Gaussians with a non-zero upstream gradient (the Gaussian
+    decoders' reverse and the scatter run on those rows only: the others
+    add exactly zero)."""
+    active = nv if active is None else active
     L = 16
     ent = 4 if bf16 else 8                     # bytes per 2-feature table entry
     gather = L * 8 * ent                       # one field, 8 corners per level
@@ -225,8 +229,10 @@ def kernel_work(nv, K, P, tiles, bf16, pairs=0, macs=(0, 0)):
         "k_gather<gaussians>": nv * (4 + 12 + 2 * (gather + feat)),
         "k_gather<pixels>": P * (gather + feat),
         # scatter: feature gradients in, float2 atomics, corner values re-read
-        # for dL/dp (Gaussians), d_pos RMW
-        "k_scatter<gaussians>": nv * (4 + 12 + 2 * (dfeat + scatter + gather) + 24),
+        # for dL/dp (Gaussians), d_pos RMW; rows without gradient read their
+        # feature gradients only
+        # (the rows with a gradient only: list, feature gradients, atomics)
+        "k_scatter<gaussians>": active * (4 + 4 + 12 + 2 * (dfeat + scatter + gather) + 24),
         "k_scatter<pixels>": P * (dfeat + scatter),
         # radix scatter: 4-B key and 4-B value read and written per element
         # (depth passes over the visible Gaussians, tile passes over the
@@ -240,8 +246,9 @@ def kernel_work(nv, K, P, tiles, bf16, pairs=0, macs=(0, 0)):
     tensor = {
         "k_query_fwd_tc": nv * (mg + mc) * 2,
         "k_bg_exact_fwd_tc": P * mc * 2,
-        "k_decoder_bwd_tc<GeoGauss>": nv * mg * 3 * 2,
-        "k_decoder_bwd_tc<ColGauss>": nv * mc * 3 * 2,
+        # the Gaussian reverse runs on the rows with a gradient only
+        "k_decoder_bwd_tc<GeoGauss>": active * mg * 3 * 2,
+        "k_decoder_bwd_tc<ColGauss>": active * mc * 3 * 2,
         "k_decoder_bwd_tc<BgPixel>": P * mc * 3 * 2,
     }
     alu = {k: pairs * f for k, f in FP32_FLOPS_PER_PAIR.items()}
@@ -539,6 +546,8 @@ def run_ours(args):
         images[prec] = C
         psnr = float(-10.0 * torch.log10(((C - teacher.clamp(0, 1)) ** 2).mean()).item())
         evals = int(r.n_contrib.sum().item())
+        active = int(((r.d_alpha[:nv] != 0) | (r.d_color[:nv] != 0).any(1) | (r.d_scale[:nv] != 0).any(1)
+                      | (r.d_quat[:nv] != 0).any(1)).sum().item())
         fl = w.fields
         results[prec] = dict(ms=ms, fwd_ms=float(np.mean(fwd_ms)), e2e_ms=float(np.mean(e2e_ms)),
                              eager_ms=float(np.mean(eager_ms)) if eager_ms else None,
@@ -552,7 +561,9 @@ def run_ours(args):
                              kernels={k: (n / args.steps, t / n) for k, (n, t) in ktimes.items()},
                              work=kernel_work(nv, K, w.cams[0].width * w.cams[0].height,
                                               int(r.ranges.shape[0]), prec == "bf16", pairs=evals,
-                                              macs=(decoder_macs(fl.geo_mlp), decoder_macs(fl.col_mlp))))
+                                              macs=(decoder_macs(fl.geo_mlp), decoder_macs(fl.col_mlp)),
+                                              active=active),
+                             active=active)
         del r, m
         torch.cuda.empty_cache()
     head = "bf16" if "bf16" in results and "ms" in results["bf16"] else "f32"
@@ -565,6 +576,7 @@ def run_ours(args):
     kern = {k: {"ms_per_step": round(per_step[k], 4), "share": round(per_step[k] / tot, 4),
                 "launches_per_step": round(R["kernels"][k][0], 2)} for k in top}
     rf = R["kernels"].get("k_raster_fwd")
+    R_run_extra = {"gaussians_with_gradient": R.get("active")}
     out = {"metric": cfg["metric"], "value": round(value, 3), "unit": "iters/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(R["ms"], 4),
            "step_issue": "one CUDA graph per step" if args.graph else "eager",
@@ -575,7 +587,7 @@ def run_ours(args):
            "run": {"precision": head, "visible": R["n_vis"], "instances": R["instances"],
                    "layout": args.layout, "parallelism": f"replicas x{ws}", "view": (
                        "one fixed camera: each forward takes its tiles in the order of the previous "
-                       "replay's pixel lists, which on a fixed view are the current ones")},
+                       "replay's pixel lists, which on a fixed view are the current ones"), **R_run_extra},
            "render_fps": round(ws * 1000.0 / R["fwd_ms"], 2),
            "render_fps_tau_T_0.2": round(ws * 1000.0 / R["tau_ms"], 2) if R.get("tau_ms") else None,
            "render_fps_u8_grids": round(ws * 1000.0 / R["u8_ms"], 2) if R.get("u8_ms") else None,

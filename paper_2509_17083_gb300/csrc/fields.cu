@@ -54,6 +54,10 @@ struct QueryBwdIO {
   float* g_rad_table;
   float loss_scale;
   int32_t* status;
+  // Optional list of the visible rows to process (those with a non-zero
+  // upstream gradient; the others add exactly zero) and its device count.
+  const int32_t* list;
+  const int32_t* n_list;
 };
 
 __device__ __forceinline__ void cam_center(const CamDev& c, float pc[3]) {
@@ -179,12 +183,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
   float* slab = slabs + (size_t)blockIdx.x * SL.total;
   const int t = threadIdx.x;
   const int nv = min(*io.n_vis, io.n);
+  const int nr = io.list ? min(*io.n_list, nv) : nv;
   const float ls = io.loss_scale, inv_ls = 1.0f / io.loss_scale;
   float pc[3];
   cam_center(cam, pc);
-  for (int base = blockIdx.x * kBwdThreads; base < nv; base += gridDim.x * kBwdThreads) {
-    const int i = base + t;
-    bool ok = i < nv;
+  for (int base = blockIdx.x * kBwdThreads; base < nr; base += gridDim.x * kBwdThreads) {
+    bool ok = base + t < nr;
+    const int i = ok ? (io.list ? io.list[base + t] : base + t) : 0;
+    if (ok && (i < 0 || i >= nv)) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      ok = false;
+    }
     int g = ok ? io.vis_ids[i] : 0;
     if (ok && (g < 0 || g >= io.n)) {
       set_status(io.status, HYRF_ERR_BOUNDS);
@@ -769,15 +778,36 @@ hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F
   }
 }
 
+size_t active_rows_workspace(int n);
+hyrf_status launch_active_rows(int n, const int32_t* n_vis, const float* d_alpha, const float* d_scale,
+                               const float* d_quat, const float* d_color, Carver& c, int32_t** list,
+                               int32_t** n_list, cudaStream_t s);
+
+// FP32 reverse workspace: CTA slabs and the list of rows with a gradient.
+size_t query_bwd_workspace(const FieldsDev& F, int n) {
+  Carver c(nullptr);
+  c.take<char>(slab_bytes(F, true));
+  c.take<char>(active_rows_workspace(n));
+  return c.size();
+}
+
 hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const FieldsDev& F,
                              void* ws, cudaStream_t s) {
   QueryBwdIO io{a.n,        a.pos,       a.alpha_e,   a.scale_e,   a.color_e,
                 a.vis_ids,  a.n_vis,     a.d_alpha,   a.d_scale,   a.d_quat,
                 a.d_color,  a.d_pos,     a.d_alpha_e, a.d_scale_e, a.d_color_e,
-                a.grads.geo_table, a.grads.rad_table, a.loss_scale, a.status};
+                a.grads.geo_table, a.grads.rad_table, a.loss_scale, a.status, nullptr, nullptr};
   const CamDev cam = to_dev(a.cam);
   if (a.n == 0) return HYRF_OK;
-  float* slabs = static_cast<float*>(ws);
+  Carver c(ws);
+  float* slabs = reinterpret_cast<float*>(c.take<char>(slab_bytes(F, true)));
+  Carver ca(c.take<char>(active_rows_workspace(a.n)));
+  int32_t *list = nullptr, *n_list = nullptr;
+  hyrf_status st = launch_active_rows(a.n, a.n_vis, a.d_alpha, a.d_scale, a.d_quat, a.d_color, ca, &list,
+                                      &n_list, s);
+  if (st != HYRF_OK) return st;
+  io.list = list;
+  io.n_list = n_list;
   switch (part_of(a.fields, F)) {
     case 1: return query_bwd_p1(F, cam, io, a.grads, slabs, s);
     case 2: return query_bwd_p2(F, cam, io, a.grads, slabs, s);

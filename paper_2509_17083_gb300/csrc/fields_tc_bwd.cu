@@ -13,12 +13,13 @@
 //   positional-encoding part of the colour decoder to dL/dposition here
 //
 // dX products read the forward weight tile as an MN-major B operand, so no
-// transposed copy exists; dW products read the row tiles as MN-major
-// operands with M = 128 output rows, of which only the decoder's real
-// outputs are used. Each dW comes out of tensor memory after its product
-// and is added (vector reductions) into this CTA's f32 slab; one reduction
-// kernel sums the slabs. Bias gradients are column sums of dZ.
-// Hidden activations are recomputed, never stored in global memory.
+// transposed copy exists. Weight gradients are formed transposed, dW^T =
+// A^T dZ with the layer input A read as an MN-major operand (M = 128 output
+// rows: A's columns and, from a column of ones the row tiles carry, the bias
+// gradient), and stay in tensor memory over every tile the persistent CTA
+// takes; at the end each CTA writes them to its f32 slab and one reduction
+// kernel sums the slabs. Hidden activations are recomputed, never stored in
+// global memory.
 #include "tc_ops.cuh"
 
 namespace hyrf {
@@ -92,6 +93,12 @@ struct GaussP {
   float* d_scale_e;
   float* d_color_e;
   int32_t* status;
+  // Optional list of the visible rows to process (those with a non-zero
+  // upstream gradient) and its device count; NULL: every visible row. Row k
+  // of dXg / dXr belongs to list[k]; Xg / Xr and the upstream gradients are
+  // indexed by visible row.
+  const int32_t* list;
+  const int32_t* n_list;
 };
 
 __device__ __forceinline__ void store_dx16(float* dst, const float* dx) {
@@ -104,14 +111,22 @@ __device__ __forceinline__ void store_dx16(float* dst, const float* dx) {
 // begin() fills the row's operand columns and the state its half needs;
 // dz_out() runs on half 0 only; finish() gets the half's share of dX.
 
-__device__ __forceinline__ bool gauss_row(const GaussP& P, int idx, bool ok, int& g) {
-  g = ok ? P.vis_ids[idx] : 0;
-  if (ok && (g < 0 || g >= P.n)) {
+// Visible row v of list position idx, and its Gaussian g; false (with v =
+// g = 0) past the end or for an out-of-range index.
+__device__ __forceinline__ bool gauss_row(const GaussP& P, int idx, bool ok, int& v, int& g) {
+  v = ok ? (P.list ? P.list[idx] : idx) : 0;
+  g = ok && v >= 0 && v < P.n ? P.vis_ids[v] : 0;
+  if (ok && (v < 0 || v >= P.n || g < 0 || g >= P.n)) {
     set_status(P.status, HYRF_ERR_BOUNDS);
-    g = 0;
+    v = g = 0;
     return false;
   }
   return ok;
+}
+
+__device__ __forceinline__ int gauss_count(const GaussP& P) {
+  const int nv = min(*P.n_vis, P.n);
+  return P.list ? min(*P.n_list, nv) : nv;
 }
 
 // Geometry decoder at visible Gaussians: inputs enc(y; Theta_geo), outputs
@@ -125,25 +140,26 @@ struct GeoGauss {
     bool ok;
     float da, ds[3], dq[4], ae, se;
   };
-  __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
+  __device__ static int count(const Params& P) { return gauss_count(P); }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.gm; }
   __device__ static void begin(const Params& P, const FieldsDev&, const CamDev&, int idx, bool ok, Row& R,
                                uint8_t* X, int r, int h) {
     R.i = idx;
-    R.ok = gauss_row(P, idx, ok, R.g);
+    int v;
+    R.ok = gauss_row(P, idx, ok, v, R.g);
     // half h copies feature columns [16h, 16h + 16)
-    const uint4* src = reinterpret_cast<const uint4*>(P.Xg + (size_t)idx * 16) + 2 * h;
+    const uint4* src = reinterpret_cast<const uint4*>(P.Xg + (size_t)v * 16) + 2 * h;
 #pragma unroll
     for (int kc = 0; kc < 2; ++kc) {
       const uint4 v = R.ok ? __ldcs(src + kc) : make_uint4(0u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4*>(X + kmaj(r, 16 * h + 8 * kc, IN)) = v;
+      *reinterpret_cast<uint4*>(X + kmaj(r, 16 * h + 8 * kc, IN + 8)) = v;
     }
     if (h != 0) return;
-    R.da = R.ok ? P.d_alpha[idx] : 0.0f;
+    R.da = R.ok ? P.d_alpha[v] : 0.0f;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) R.ds[k] = R.ok ? P.d_scale[3 * idx + k] : 0.0f;
+    for (int k = 0; k < 3; ++k) R.ds[k] = R.ok ? P.d_scale[3 * v + k] : 0.0f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) R.dq[k] = R.ok ? P.d_quat[4 * idx + k] : 0.0f;
+    for (int k = 0; k < 4; ++k) R.dq[k] = R.ok ? P.d_quat[4 * v + k] : 0.0f;
     R.ae = R.ok && P.alpha_e ? P.alpha_e[R.g] : 0.0f;
     R.se = R.ok && P.scale_e ? P.scale_e[R.g] : 0.0f;
   }
@@ -196,17 +212,18 @@ struct ColGauss {
     bool ok;
     float dir[3], vn, dc[3], ce[3];
   };
-  __device__ static int count(const Params& P) { return min(*P.n_vis, P.n); }
+  __device__ static int count(const Params& P) { return gauss_count(P); }
   __device__ static const MlpDev& mlp(const FieldsDev& F) { return F.cm; }
   __device__ static void begin(const Params& P, const FieldsDev& F, const CamDev& cam, int idx, bool ok,
                                Row& R, uint8_t* X, int r, int h) {
     R.i = idx;
-    R.ok = gauss_row(P, idx, ok, R.g);
+    int v;
+    R.ok = gauss_row(P, idx, ok, v, R.g);
     if (h == 0) {
-      load_row32<IN>(X, r, P.Xr + (size_t)idx * 16, R.ok);
+      load_row32<IN + 8>(X, r, P.Xr + (size_t)v * 16, R.ok);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        R.dc[k] = R.ok ? P.d_color[3 * idx + k] : 0.0f;
+        R.dc[k] = R.ok ? P.d_color[3 * v + k] : 0.0f;
         R.ce[k] = R.ok && P.color_e ? P.color_e[3 * (int64_t)R.g + k] : 0.0f;
       }
       return;
@@ -216,13 +233,13 @@ struct ColGauss {
     for (int k = 0; k < 3; ++k) p[k] = R.ok ? P.pos[3 * (int64_t)R.g + k] : F.lo[k] + 1.0f / F.sx[k];
     float pc[3];
     cam_center(cam, pc);
-    const float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
-    R.vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const float d[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+    R.vn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) R.dir[k] = v[k] / R.vn;
+    for (int k = 0; k < 3; ++k) R.dir[k] = d[k] / R.vn;
     float pe[32];
     pos_enc(R.dir, pe);
-    store_cols<IN, 32, 32>(X, r, pe);
+    store_cols<IN + 8, 32, 32>(X, r, pe);
   }
   __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
 #pragma unroll
@@ -280,7 +297,7 @@ struct BgPixel {
     R.ok = ok;
     R.p = ok ? idx : 0;
     if (h == 0) {
-      load_row32<IN>(X, r, P.Xb + (size_t)R.p * 16, ok);
+      load_row32<IN + 8>(X, r, P.Xb + (size_t)R.p * 16, ok);
       R.T = ok ? P.T_final[R.p] : 0.0f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) R.g[k] = ok ? P.dC[3 * (int64_t)R.p + k] : 0.0f;
@@ -289,7 +306,7 @@ struct BgPixel {
     float ps[3], dir[3], pe[32];
     bg_ray(cam, F, P.radius, R.p % cam.W, R.p / cam.W, ps, dir);
     pos_enc(dir, pe);
-    store_cols<IN, 32, 32>(X, r, pe);
+    store_cols<IN + 8, 32, 32>(X, r, pe);
   }
   __device__ static void dz_out(const Params& P, Row& R, const float* o, float* dz) {
     float dt = 0.0f;
@@ -325,22 +342,30 @@ __device__ __forceinline__ int point_count(const typename S::Params& P, const Ca
 
 // ---------------------------------------------------------------- the kernel
 
-// Shared-memory map. The dW products read their dZ operand with 128 output
-// rows; rows beyond the real outputs come from the following bytes (always
-// inside this map: each dZ tile is followed by another tile or the guard).
+// Shared-memory map. The row tiles X, H1 and H2 carry 8 columns past their
+// data: a column of ones (column IN, resp. 64) and seven zeros, so that the
+// weight-gradient products A^T dZ also give the bias gradients (the row of
+// ones sums dZ over the tile's points). Those products read A with 128
+// output rows; rows past a tile's columns come from the bytes that follow it
+// (always inside this map: each tile is followed by another or the guard).
 template <int IN>
 struct BwdSmem {
+  static constexpr int XP = IN + 8, HP = 64 + 8;
   static constexpr int W0 = 0, W1 = W0 + 64 * IN * 2, W2 = W1 + 64 * 64 * 2, X = W2 + 16 * 64 * 2,
-                       H1 = X + 128 * IN * 2, H2 = H1 + 128 * 64 * 2, Z2 = H2 + 128 * 64 * 2,
-                       GUARD = Z2 + 128 * 16 * 2, BIAS = GUARD + 2048, DB = BIAS + 144 * 4,
-                       SIZE = DB + 144 * 4;
+                       H1 = X + 128 * XP * 2, H2 = H1 + 128 * HP * 2, Z2 = H2 + 128 * HP * 2,
+                       GUARD = Z2 + 128 * 16 * 2, BIAS = GUARD + 2048, SIZE = BIAS + 144 * 4;
 };
-constexpr uint32_t kBwdTmemCols = 128;  // [0, 64): products, [64, 128): dW
+// Tensor memory of a CTA: [0, 64) the products of the current tile; the
+// weight gradients (transposed: lane = input column, column = output),
+// accumulated over every tile the CTA takes: dW2^T [64, 80), dW1^T
+// [80, 144), dW0^T [144, 208).
+constexpr uint32_t kBwdTmemCols = 256;
+constexpr uint32_t kTmW2 = 64, kTmW1 = 80, kTmW0 = 144;
 
 // ReLU(D + b) of NC accumulator columns [c0, c0 + NC) of this thread's lane
-// -> the same columns of its row of the 64-column tile H. taddr points at
+// -> the same columns of its row of the HP-column tile H. taddr points at
 // column c0.
-template <int NC>
+template <int NC, int HP>
 __device__ __forceinline__ void epilogue_relu(uint32_t taddr, const float* b, uint8_t* H, int r, int c0) {
   float v[NC];
   ldcols<NC>(taddr, v);
@@ -348,48 +373,55 @@ __device__ __forceinline__ void epilogue_relu(uint32_t taddr, const float* b, ui
   for (int c = 0; c < NC; c += 8) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[c + j] = fmaxf(v[c + j] + b[c0 + c + j], 0.0f);
-    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, 64)) = pack8(v + c);
+    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, HP)) = pack8(v + c);
   }
 }
 
 // ReLU mask from the bf16 activations of this row, applied to NC columns
 // [c0, c0 + NC) of D read from tensor memory (taddr at column c0); the
-// masked gradient replaces the activations in place (bf16) and its column
-// sums go to db[c0 + ...].
-template <int NC>
-__device__ __forceinline__ void relu_back(uint32_t taddr, uint8_t* Hbuf, int r, bool ok, float* db, int c0) {
-  const int lane = threadIdx.x & 31;
+// masked gradient replaces the activations in place (bf16).
+template <int NC, int HP>
+__device__ __forceinline__ void relu_back(uint32_t taddr, uint8_t* Hbuf, int r, bool ok, int c0) {
   float v[NC];
   ldcols<NC>(taddr, v);
 #pragma unroll
-  for (int c = 0; c < NC; c += 16) {
-    float hv[16];
-    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c, 64)), hv);
-    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)), hv + 8);
+  for (int c = 0; c < NC; c += 8) {
+    float hv[8];
+    unpack8(*reinterpret_cast<const uint4*>(Hbuf + kmaj(r, c0 + c, HP)), hv);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[c + j] = (ok && hv[j] > 0.0f) ? v[c + j] : 0.0f;
-    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c, 64)) = pack8(v + c);
-    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c + 8, 64)) = pack8(v + c + 8);
-    const float sum = col_sum16(v + c);
-    if ((lane & 1) == 0) atomicAdd(db + c0 + c + col_of_lane(lane), sum);
+    for (int j = 0; j < 8; ++j) v[c + j] = (ok && hv[j] > 0.0f) ? v[c + j] : 0.0f;
+    *reinterpret_cast<uint4*>(Hbuf + kmaj(r, c0 + c, HP)) = pack8(v + c);
   }
 }
 
-// Columns [c0, c0 + NC) of the dW rows < rows_used (TMEM lanes) x N columns,
-// added to the CTA slab (row stride N) with vector reductions (no value
-// comes back, so the tile does not wait for the L2 round trip; the slab is
-// private to the CTA, so nothing contends). Warps of both halves share lanes.
-template <int N, int NC>
-__device__ __forceinline__ void flush_dw(uint32_t tm_w, int rows_used, float* slab_W, int c0) {
-  const int q = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
-  if (q * 32 >= rows_used) return;  // warp-uniform
-  const int o = q * 32 + lane;
-  float v[NC];
-  ldcols<NC>(tm_w + ((uint32_t)(q * 32) << 16) + c0, v);
-  if (o < rows_used) {
-    float4* d = reinterpret_cast<float4*>(slab_W + o * N + c0);  // slab rows are 16-byte aligned
+// Columns 8 * (this thread's share) of a ones-column block: column `at` of
+// the row's tile is 1, the seven after it 0.
+template <int P_>
+__device__ __forceinline__ void ones_block(uint8_t* tile, int r, int at) {
+  float v[8] = {1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  *reinterpret_cast<uint4*>(tile + kmaj(r, at, P_)) = pack8(v);
+}
+
+// One transposed weight-gradient accumulator (lanes 0 .. NI - 1: input
+// column i, lane NI: the bias; columns: outputs 0 .. NO - 1) written into
+// the CTA's slab, W [NO][NI] and b [NO] (plain stores: the slab is this
+// CTA's alone and every entry of it is written here). Zeros if the CTA took
+// no tile.
+template <int NCOL>
+__device__ __forceinline__ void store_dw(uint32_t tm_acc, int NI, int NO, float* slab_W, float* slab_b, bool any) {
+  const int w = threadIdx.x >> 5, q = w & 3, h = w >> 2, lane = threadIdx.x & 31;
+  constexpr int HALF = NCOL >= 32 ? NCOL / 2 : NCOL;
+  if (q * 32 > NI || (NCOL < 32 && h != 0)) return;  // warp-uniform
+  const int i = q * 32 + lane, c0 = NCOL >= 32 ? h * HALF : 0;
+  float v[HALF];
+  ldcols<HALF>(tm_acc + ((uint32_t)(q * 32) << 16) + c0, v);
 #pragma unroll
-    for (int k = 0; k < NC / 4; ++k) atomicAdd(d + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+  for (int k = 0; k < HALF; ++k) {
+    const int o = c0 + k;
+    if (o >= NO) break;
+    const float x = any ? v[k] : 0.0f;
+    if (i < NI) slab_W[o * NI + i] = x;
+    else if (i == NI) slab_b[o] = x;
   }
 }
 
@@ -402,31 +434,33 @@ __device__ __forceinline__ void sync_for_mma() {
 
 // 256 threads: row r = t % 128 of the tile, half h = t / 128. Warps w and
 // w + 4 read the same TMEM lanes (32 (w % 4) ...) and split the columns.
+// Persistent: the CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// and keeps its weight and bias gradients in tensor memory until the end.
 template <class S>
-__global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P, FieldsDev F, CamDev cam,
+__global__ void __launch_bounds__(256, 2) k_decoder_bwd_tc(typename S::Params P, FieldsDev F, CamDev cam,
                                                            float loss_scale, SlabLayout SL, float* slabs,
                                                            int32_t* status) {
   constexpr int IN = S::IN, OUT = S::OUT;
   using L = BwdSmem<IN>;
+  constexpr int XP = L::XP, HP = L::HP;
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
   const int t = threadIdx.x, w = t >> 5, h = t >> 7, r = t & 127;
   const MlpDev& M = S::mlp(F);
   float* bias = reinterpret_cast<float*>(sm + L::BIAS);
-  float* db = reinterpret_cast<float*>(sm + L::DB);  // db0 [0,64), db1 [64,128), db2 [128,144)
   stage_w<64, IN>(sm + L::W0, M.W[0], 64);
   stage_w<64, 64>(sm + L::W1, M.W[1], 64);
   stage_w<16, 64>(sm + L::W2, M.W[2], OUT);
   if (t < 64) {
     bias[t] = M.b[0][t];
     bias[64 + t] = M.b[1][t];
-    db[t] = 0.0f;
-    db[64 + t] = 0.0f;
   }
-  if (t < 16) {
-    bias[128 + t] = t < OUT ? M.b[2][t] : 0.0f;
-    db[128 + t] = 0.0f;
+  if (t < 16) bias[128 + t] = t < OUT ? M.b[2][t] : 0.0f;
+  if (h == 0) ones_block<XP>(sm + L::X, r, IN);
+  else {
+    ones_block<HP>(sm + L::H1, r, 64);
+    ones_block<HP>(sm + L::H2, r, 64);
   }
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)));
@@ -438,7 +472,7 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   sync_for_mma();
-  const uint32_t tm = tmem_base, tmW = tmem_base + 64;
+  const uint32_t tm = tmem_base;
   const uint32_t lane_off = ((uint32_t)((w & 3) * 32)) << 16;
   float* slab = slabs + (size_t)blockIdx.x * SL.total;
   const float inv_ls = 1.0f / loss_scale;
@@ -446,7 +480,7 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
   const int ntile = (n + 127) / 128;
   const int hc = 32 * h;  // this half's first column of 64
   uint32_t phase = 0;
-  bool failed = false;
+  bool failed = false, any = false;
   for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
     const int idx = tile * 128 + r;
     const bool ok = idx < n;
@@ -455,25 +489,25 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
     // ---- forward recompute
     sync_for_mma();
     if (t == 0) {
-      gemm<64, IN>(tm, sm + L::X, sm + L::W0);
+      gemm_ap<64, IN, XP>(tm, sm + L::X, sm + L::W0);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu<32>(tm + lane_off + hc, bias, sm + L::H1, r, hc);
+    epilogue_relu<32, HP>(tm + lane_off + hc, bias, sm + L::H1, r, hc);
     sync_for_mma();
     if (t == 0) {
-      gemm<64, 64>(tm, sm + L::H1, sm + L::W1);
+      gemm_ap<64, 64, HP>(tm, sm + L::H1, sm + L::W1);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    epilogue_relu<32>(tm + lane_off + hc, bias + 64, sm + L::H2, r, hc);
+    epilogue_relu<32, HP>(tm + lane_off + hc, bias + 64, sm + L::H2, r, hc);
     sync_for_mma();
     if (t == 0) {
-      gemm<16, 64>(tm, sm + L::H2, sm + L::W2);
+      gemm_ap<16, 64, HP>(tm, sm + L::H2, sm + L::W2);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
@@ -489,44 +523,40 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
       for (int k = 0; k < 16; ++k) dz[k] = k < OUT ? dz[k] * loss_scale : 0.0f;
       *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 0, 16)) = pack8(dz);
       *reinterpret_cast<uint4*>(sm + L::Z2 + kmaj(r, 8, 16)) = pack8(dz + 8);
-      const float sum = col_sum16(dz);
-      const int c = col_of_lane(t & 31);
-      if ((t & 1) == 0 && c < OUT) atomicAdd(db + 128 + c, sum);
     }
-    // ---- layer 2: dH2 = dZ2 W2, dW2 += dZ2^T H2
+    // ---- layer 2: dH2 = dZ2 W2, dW2^T (and db2) += [H2 1]^T dZ2
     sync_for_mma();
     if (t == 0) {
-      gemm_dx<64, 16>(tm, sm + L::Z2, sm + L::W2, false);
-      gemm_dw<64, 16>(tmW, sm + L::Z2, sm + L::H2, false);
+      gemm_dx_ap<64, 16, 16>(tm, sm + L::Z2, sm + L::W2);
+      gemm_at<16, HP, 16>(tm + kTmW2, sm + L::H2, sm + L::Z2, any);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    relu_back<32>(tm + lane_off + hc, sm + L::H2, r, ok, db + 64, hc);  // dZ1 replaces H2
-    flush_dw<64, 32>(tmW, OUT, slab + SL.off_W[S::DEC][2], hc);
-    // ---- layer 1: dH1 = dZ1 W1, dW1 += dZ1^T H1
+    relu_back<32, HP>(tm + lane_off + hc, sm + L::H2, r, ok, hc);  // dZ1 replaces H2
+    // ---- layer 1: dH1 = dZ1 W1, dW1^T (and db1) += [H1 1]^T dZ1
     sync_for_mma();
     if (t == 0) {
-      gemm_dx<64, 64>(tm, sm + L::H2, sm + L::W1, false);
-      gemm_dw<64, 64>(tmW, sm + L::H2, sm + L::H1, false);
+      gemm_dx_ap<64, 64, HP>(tm, sm + L::H2, sm + L::W1);
+      gemm_at<64, HP, HP>(tm + kTmW1, sm + L::H1, sm + L::H2, any);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
-    relu_back<32>(tm + lane_off + hc, sm + L::H1, r, ok, db, hc);  // dZ0 replaces H1
-    flush_dw<64, 32>(tmW, 64, slab + SL.off_W[S::DEC][1], hc);
-    // ---- layer 0: dX = dZ0 W0, dW0 += dZ0^T X
+    relu_back<32, HP>(tm + lane_off + hc, sm + L::H1, r, ok, hc);  // dZ0 replaces H1
+    // ---- layer 0: dX = dZ0 W0, dW0^T (and db0) += [X 1]^T dZ0
     sync_for_mma();
     if (t == 0) {
-      gemm_dx<IN, 64>(tm, sm + L::H1, sm + L::W0, false);
-      gemm_dw<IN, 64>(tmW, sm + L::H1, sm + L::X, false);
+      gemm_dx_ap<IN, 64, HP>(tm, sm + L::H1, sm + L::W0);
+      gemm_at<64, XP, HP>(tm + kTmW0, sm + L::X, sm + L::H1, any);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
+    any = true;
     {
       constexpr int HALF = S::DXC / 2;
       float dx[HALF];
@@ -535,7 +565,6 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
       for (int k = 0; k < HALF; ++k) dx[k] *= inv_ls;
       S::finish(P, F, cam, R, dx, h);
     }
-    flush_dw<IN, IN / 2>(tmW, 64, slab + SL.off_W[S::DEC][0], h * (IN / 2));
     fence_before();
   }
   if (failed) {
@@ -546,15 +575,124 @@ __global__ void __launch_bounds__(256, 3) k_decoder_bwd_tc(typename S::Params P,
   fence_before();
   __syncthreads();
   fence_after();
-  if (t < 64) {
-    slab[SL.off_b[S::DEC][0] + t] += db[t];
-    slab[SL.off_b[S::DEC][1] + t] += db[64 + t];
-  }
-  if (t < OUT) slab[SL.off_b[S::DEC][2] + t] += db[128 + t];
+  // the CTA's weight and bias gradients (x loss scale) into its slab
+  const int d = S::DEC;
+  store_dw<16>(tm + kTmW2, 64, OUT, slab + SL.off_W[d][2], slab + SL.off_b[d][2], any && !failed);
+  store_dw<64>(tm + kTmW1, 64, 64, slab + SL.off_W[d][1], slab + SL.off_b[d][1], any && !failed);
+  store_dw<64>(tm + kTmW0, IN, 64, slab + SL.off_W[d][0], slab + SL.off_b[d][0], any && !failed);
+  fence_before();
+  __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kBwdTmemCols));
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------- rows with a gradient
+
+// Visible rows whose upstream gradient (dL/d opacity, scale, rotation or
+// colour) is not exactly zero (a NaN counts as non-zero). For every other
+// row the reverse of the aggregation, of both decoders and of the gather
+// adds exactly zero (dZ = 0, so dX = 0 and the row's share of dW and of the
+// table gradients is 0), so the reverse runs on the listed rows only, in
+// ascending order (the storage order the gather's coherence relies on).
+constexpr int kActChunk = 2048;  // rows per compaction CTA (256 threads x 8)
+
+struct GradRows {
+  int n;
+  const int32_t* n_vis;
+  const float* d_alpha;  // [n]
+  const float* d_scale;  // [n][3]
+  const float* d_quat;   // [n][4]
+  const float* d_color;  // [n][3]
+};
+
+__device__ __forceinline__ bool row_has_grad(const GradRows& P, int i) {
+  bool a = P.d_alpha[i] != 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) a |= (P.d_scale[3 * i + k] != 0.0f) | (P.d_color[3 * i + k] != 0.0f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a |= P.d_quat[4 * i + k] != 0.0f;
+  return a;
+}
+
+__global__ void __launch_bounds__(256) k_active_count(GradRows P, int32_t* __restrict__ counts) {
+  __shared__ int red[8];
+  const int nv = min(*P.n_vis, P.n);
+  const int base = blockIdx.x * kActChunk;
+  int c = 0;
+  for (int k = 0; k < kActChunk / 256; ++k) {
+    const int i = base + k * 256 + threadIdx.x;
+    if (i < nv && row_has_grad(P, i)) ++c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// Ordered compaction: the rows of chunk b land at offsets[b] + rank.
+__global__ void __launch_bounds__(256) k_active_list(GradRows P, const int32_t* __restrict__ offsets,
+                                                     int32_t* __restrict__ list) {
+  __shared__ int wsum[8];
+  const int nv = min(*P.n_vis, P.n);
+  const int base = blockIdx.x * kActChunk;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int run = offsets[blockIdx.x];
+  for (int k = 0; k < kActChunk / 256; ++k) {
+    const int i = base + k * 256 + threadIdx.x;
+    const bool f = i < nv && row_has_grad(P, i);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[w] = __popc(m);
+    __syncthreads();
+    int before = 0, tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      before += j < w ? wsum[j] : 0;
+      tot += wsum[j];
+    }
+    if (f) list[run + before + __popc(m & ((1u << lane) - 1u))] = i;
+    run += tot;
+    __syncthreads();
+  }
+}
+
+hyrf_status launch_scan_small(int32_t* counts, int m, int32_t* total, cudaStream_t s);
+
+static int act_chunks(int n) { return n > 0 ? (n + kActChunk - 1) / kActChunk : 0; }
+
+// Workspace of the list of rows with a gradient (n rows at most).
+size_t active_rows_workspace(int n) {
+  Carver c(nullptr);
+  c.take<int32_t>((size_t)act_chunks(n) + 1);
+  c.take<int32_t>(1);
+  c.take<int32_t>((size_t)(n > 0 ? n : 1));
+  return c.size();
+}
+
+// The visible rows with a non-zero upstream gradient, ascending, into the
+// workspace carved by `c` (active_rows_workspace); *list / *n_list point
+// at the list and its device count.
+hyrf_status launch_active_rows(int n, const int32_t* n_vis, const float* d_alpha, const float* d_scale,
+                               const float* d_quat, const float* d_color, Carver& c, int32_t** list,
+                               int32_t** n_list, cudaStream_t s) {
+  const int chunks = act_chunks(n);
+  int32_t* offsets = c.take<int32_t>((size_t)chunks + 1);
+  *n_list = c.take<int32_t>(1);
+  *list = c.take<int32_t>((size_t)(n > 0 ? n : 1));
+  if (chunks == 0) return cudaMemsetAsync(*n_list, 0, sizeof(int32_t), s) == cudaSuccess ? HYRF_OK : HYRF_ERR_CUDA;
+  const GradRows P{n, n_vis, d_alpha, d_scale, d_quat, d_color};
+  HYRF_LAUNCH("k_active_count", s, k_active_count<<<chunks, 256, 0, s>>>(P, offsets));
+  hyrf_status st = launch_scan_small(offsets, chunks, *n_list, s);
+  if (st != HYRF_OK) return st;
+  HYRF_LAUNCH("k_active_list", s, k_active_list<<<chunks, 256, 0, s>>>(P, offsets, *list));
+  return HYRF_OK;
+}
 
 // ---------------------------------------------------------------- launchers
 
@@ -564,14 +702,20 @@ hyrf_status launch_slab_reduce(const float* slabs, int nslabs, const SlabLayout&
                                const SlabTargets& T, float scale, cudaStream_t s);
 SlabTargets slab_targets(const hyrf_field_grads& g, bool geo);
 
+// Persistent CTAs of the tensor-core reverse: two per SM (each holds 256
+// tensor-memory columns; the shared-memory request below keeps a third
+// from being placed on the SM). Each writes every entry of its slab.
+static int tc_bwd_ctas() { return 2 * num_sms(); }
+constexpr int kBwdSmemMin = 80 * 1024;
+
 template <class S>
 static hyrf_status launch_dec_bwd(const typename S::Params& P, const FieldsDev& F, const CamDev& cam,
                                   float ls, const SlabLayout& SL, float* slabs, int32_t* status,
                                   cudaStream_t s) {
-  constexpr int smem = tc::BwdSmem<S::IN>::SIZE;
+  constexpr int smem = tc::BwdSmem<S::IN>::SIZE > kBwdSmemMin ? tc::BwdSmem<S::IN>::SIZE : kBwdSmemMin;
   set_smem_limit<tc::k_decoder_bwd_tc<S>>(smem);
   HYRF_LAUNCH(S::kName, s,
-              tc::k_decoder_bwd_tc<S><<<bwd_ctas(), 256, smem, s>>>(P, F, cam, ls, SL, slabs, status));
+              tc::k_decoder_bwd_tc<S><<<tc_bwd_ctas(), 256, smem, s>>>(P, F, cam, ls, SL, slabs, status));
   return HYRF_OK;
 }
 
@@ -584,6 +728,7 @@ size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_fe
   const int fields = geo ? 2 : 1;
   if (!have_features) c.take<uint32_t>((size_t)fields * rows * 16);
   c.take<float>((size_t)fields * rows * 32);
+  if (geo) c.take<char>(active_rows_workspace((int)rows));  // the Gaussian rows with a gradient
   return c.size();
 }
 
@@ -600,20 +745,27 @@ hyrf_status launch_query_bwd_tc(const hyrf_query_fields_backward_args& a, const 
   float* dX = c.take<float>((size_t)2 * a.n * 32);
   uint32_t *Xg = X, *Xr = X + (size_t)a.n * 16;
   float *dXg = dX, *dXr = dX + (size_t)a.n * 32;
-  cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
+  Carver ca(c.take<char>(active_rows_workspace(a.n)));
   const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status, nullptr, nullptr};
   hyrf_status st = saved ? HYRF_OK : launch_gather(F, cam, RS, a.n, Xg, Xr, s);
   if (st != HYRF_OK) return st;
   tc::GaussP P{a.n,       a.pos,     a.alpha_e, a.scale_e, a.color_e, a.vis_ids,   a.n_vis,
                a.d_alpha, a.d_scale, a.d_quat,  a.d_color, Xg,        Xr,          dXg,
-               dXr,       a.d_pos,   a.d_alpha_e, a.d_scale_e, a.d_color_e, a.status};
+               dXr,       a.d_pos,   a.d_alpha_e, a.d_scale_e, a.d_color_e, a.status, nullptr, nullptr};
+  // the rows with a non-zero upstream gradient, in ascending order
+  int32_t *list = nullptr, *n_list = nullptr;
+  st = launch_active_rows(a.n, a.n_vis, a.d_alpha, a.d_scale, a.d_quat, a.d_color, ca, &list, &n_list, s);
+  if (st != HYRF_OK) return st;
+  P.list = list;
+  P.n_list = n_list;
   st = launch_dec_bwd<tc::GeoGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
   if (st != HYRF_OK) return st;
   st = launch_dec_bwd<tc::ColGauss>(P, F, cam, a.loss_scale, SL, slabs, a.status, s);
   if (st != HYRF_OK) return st;
-  st = launch_scatter(F, cam, RS, a.n, dXg, dXr, a.grads.geo_table, a.grads.rad_table, a.d_pos, s);
+  const RowSource RSL{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status, list, n_list};
+  st = launch_scatter(F, cam, RSL, a.n, dXg, dXr, a.grads.geo_table, a.grads.rad_table, a.d_pos, s);
   if (st != HYRF_OK) return st;
-  return launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(a.grads, true), 1.0f / a.loss_scale, s);
+  return launch_slab_reduce(slabs, tc_bwd_ctas(), SL, slab_targets(a.grads, true), 1.0f / a.loss_scale, s);
 }
 
 hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
@@ -627,7 +779,6 @@ hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, c
   const bool saved = a.features != nullptr;
   uint32_t* Xb = saved ? static_cast<uint32_t*>(a.features) : c.take<uint32_t>((size_t)P_ * 16);
   float* dXb = c.take<float>((size_t)P_ * 32);
-  cudaMemsetAsync(slabs, 0, (size_t)bwd_ctas() * SL.total * sizeof(float), s);
   const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
   hyrf_status st = saved ? HYRF_OK : launch_gather(F, cam, RS, P_, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
@@ -637,7 +788,7 @@ hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, c
   // decoder gradients first (a plain read-modify-write of the caller's
   // buffers, kept on the caller's stream); the table scatter (atomics only)
   // may then run on the caller's second stream
-  st = launch_slab_reduce(slabs, bwd_ctas(), SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
+  st = launch_slab_reduce(slabs, tc_bwd_ctas(), SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
   if (st != HYRF_OK) return st;
   cudaStream_t ss = s;
   if (b.scatter_stream) {

@@ -32,8 +32,8 @@ constexpr int kLevels = 16;  // levels (warps)
 constexpr int kThreads = kRows * kLevels;
 
 __device__ __forceinline__ int row_count(const RowSource& S, const CamDev& cam) {
-  if (!S.pixels) return min(*S.n_vis, S.n);
-  return S.px_ids ? min(*S.n_px, cam.W * cam.H) : cam.W * cam.H;
+  const int all = S.pixels ? cam.W * cam.H : min(*S.n_vis, S.n);
+  return S.list ? min(*S.n_list, all) : all;
 }
 
 // Contracted position (and, for Gaussians, the Gaussian index and the
@@ -44,14 +44,15 @@ __device__ __forceinline__ void row_point(const RowSource& S, const FieldsDev& F
   ok = row < nrows;
   g = 0;
   if (S.pixels) {
-    const int p = ok ? (S.px_ids ? S.px_ids[row] : row) : 0;
+    const int p = ok ? (S.list ? S.list[row] : row) : 0;
     float ps[3], dir[3];
     tc::bg_ray(cam, F, S.radius, p % cam.W, p / cam.W, ps, dir);
     contract_n(ps, y);
     return;
   }
   if (ok) {
-    g = S.vis_ids[row];
+    const int v = S.list ? S.list[row] : row;
+    g = (v >= 0 && v < S.n) ? S.vis_ids[v] : -1;
     if (g < 0 || g >= S.n) {
       set_status(S.status, HYRF_ERR_BOUNDS);
       ok = false;

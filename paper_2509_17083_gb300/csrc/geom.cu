@@ -269,6 +269,12 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
 
 // ---------------------------------------------------------------- launchers
 
+// Exclusive scan of m per-chunk counts in place, total to *total (one CTA).
+hyrf_status launch_scan_small(int32_t* counts, int m, int32_t* total, cudaStream_t s) {
+  HYRF_LAUNCH("k_scan_small", s, k_scan_small<<<1, 1024, 0, s>>>(counts, m, total));
+  return HYRF_OK;
+}
+
 size_t precull_workspace(int n) {
   Carver c(nullptr);
   c.take<int32_t>((n + kChunk - 1) / kChunk + 1);

@@ -56,6 +56,24 @@ __device__ __forceinline__ bool splat_alpha(float power, float pmin, float o, fl
   return alpha >= kAlphaMin;
 }
 
+// Asynchronous global -> shared copies (cp.async, L1-allocating): a batch
+// of records lands in shared memory while the previous batch is composited.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most N of this thread's most recent groups are in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis, int n,
                                               const float* __restrict__ mean2d,
                                               const float* __restrict__ conic,
@@ -70,6 +88,10 @@ __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis,
   }
 }
 
+// One CTA per tile, one pixel per thread. The tile's list is taken in
+// batches of 256 records; batch b + 1 is copied into the other half of a
+// double buffer (cp.async, one record per thread) while batch b is
+// composited, and the list index of batch b + 2 is fetched meanwhile.
 __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ ranges,
                                                     const int32_t* __restrict__ vals, int n,
                                                     const float4* __restrict__ rec, int W, int H,
@@ -78,7 +100,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
                                                     float* __restrict__ T_final,
                                                     int32_t* __restrict__ n_contrib,
                                                     int32_t* status) {
-  __shared__ float4 s0[256], s1[256], s2[256];
+  __shared__ float4 s0[2][256], s1[2][256], s2[2][256];
   const int tile = order ? order[blockIdx.x] : (int)blockIdx.x;
   if (tile < 0 || tile >= gridDim.x) {  // CTA-uniform
     if (threadIdx.x == 0) set_status(status, HYRF_ERR_BOUNDS);
@@ -90,33 +112,52 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
   const bool inside = px < W && py < H;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  const int nb = (end - start + 255) / 256;
+  // record of list position start + 256 b + t into buffer b & 1; g is its
+  // Gaussian (from vals), or -1 past the end of the list
+  auto stage = [&](int b, int g) {
+    const int buf = b & 1;
+    if (g < 0) return;
+    if (g >= n) {
+      set_status(status, HYRF_ERR_BOUNDS);
+      s0[buf][t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      s1[buf][t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // opacity 0: never contributes
+      s2[buf][t] = make_float4(0.0f, INFINITY, 0.0f, 0.0f);
+      return;
+    }
+    cp_async16(&s0[buf][t], rec + 3 * (size_t)g);
+    cp_async16(&s1[buf][t], rec + 3 * (size_t)g + 1);
+    cp_async16(&s2[buf][t], rec + 3 * (size_t)g + 2);
+  };
+  auto index = [&](int b) {
+    const int k = start + 256 * b + t;
+    if (b >= nb || k >= end) return -1;
+    const int g = vals[k];
+    return g < 0 ? n : g;  // out of range either way: stage() reports it
+  };
   float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
   int last = 0;
   bool done = !inside;
-  for (int b0 = start; b0 < end; b0 += 256) {
+  stage(0, index(0));
+  cp_async_commit();
+  int g_next = index(1);
+  for (int b = 0; b < nb; ++b) {
+    // also: every thread is done with batch b - 1, whose buffer the copies
+    // of batch b + 1 overwrite
     if (__syncthreads_count(done) == 256) break;
-    const int k = b0 + t;
-    if (k < end) {
-      int g = vals[k];
-      if (g < 0 || g >= n) {
-        set_status(status, HYRF_ERR_BOUNDS);
-        s0[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        s1[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // opacity 0: never contributes
-        s2[t] = make_float4(0.0f, INFINITY, 0.0f, 0.0f);
-      } else {
-        s0[t] = rec[3 * g];
-        s1[t] = rec[3 * g + 1];
-        s2[t] = rec[3 * g + 2];
-      }
-    }
-    __syncthreads();
+    stage(b + 1, g_next);
+    cp_async_commit();
+    g_next = index(b + 2);
+    cp_async_wait<1>();  // this thread's copies of batch b have landed
+    __syncthreads();     // and everyone's
+    const int buf = b & 1, b0 = start + 256 * b;
     const int cnt = min(256, end - b0);
     for (int j = 0; j < cnt && !done; ++j) {
-      const float4 r0 = s0[j], r1 = s1[j];
+      const float4 r0 = s0[buf][j], r1 = s1[buf][j];
       const float dx = r0.x - fx, dy = r0.y - fy;
       const float power = splat_power(r0.z * dx * dx, r0.w * dx, r1.x, dy);
       float G, alpha;
-      if (!splat_alpha(power, s2[j].y, r1.y, G, alpha)) continue;
+      if (!splat_alpha(power, s2[buf][j].y, r1.y, G, alpha)) continue;
       const float test_T = T * (1.0f - alpha);
       if (test_T < kTMin) {
         done = true;
@@ -125,11 +166,12 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
       const float w = alpha * T;
       c0 = fmaf(r1.z, w, c0);
       c1 = fmaf(r1.w, w, c1);
-      c2 = fmaf(s2[j].x, w, c2);
+      c2 = fmaf(s2[buf][j].x, w, c2);
       T = test_T;
       last = b0 - start + j + 1;
     }
   }
+  cp_async_wait<0>();  // no copy outlives the CTA
   if (inside) {
     const int p = py * W + px;
     C_fg[3 * p] = c0;
@@ -207,9 +249,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
   constexpr int NT = 32 * WARPS;     // threads per CTA
   constexpr int CPT = kTile / (2 * WARPS * P);  // CTAs per tile
   constexpr int B = 256;             // Gaussians staged per batch
-  __shared__ float4 s0[B], s1[B];
-  __shared__ float2 s2[B];
-  __shared__ int sg[B];
+  __shared__ float4 s0[2][B], s1[2][B];
+  __shared__ float2 s2[2][B];
+  __shared__ int sg[2][B];
   __shared__ int max_last;
   const int tile = order[blockIdx.x / CPT], sub = blockIdx.x % CPT;
   if (tile < 0 || tile >= (int)(gridDim.x / CPT)) {  // CTA-uniform
@@ -270,28 +312,56 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
   if (lane == 0) atomicMax(&max_last, wlast);
   __syncthreads();
   const int stop = min(end, start + max_last);  // nor did any pixel of the tile use positions >= stop
-  for (int b1 = stop; b1 > start; b1 -= B) {
-    const int b0 = max(start, b1 - B);
-    __syncthreads();
-    for (int e = t; e < b1 - b0; e += NT) {
-      int g = vals[b0 + e];
-      if (g < 0 || g >= n) {
-        g = -1;
-        s1[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        s2[e] = make_float2(0.0f, INFINITY);  // never contributes
-      } else {
-        s0[e] = rec[3 * g];
-        s1[e] = rec[3 * g + 1];
-        const float4 r2 = rec[3 * g + 2];
-        s2[e] = make_float2(r2.x, r2.y);
-      }
-      sg[e] = g;
+  // batches of B list positions from the back: batch k is [b0, b1) with
+  // b1 = stop - k B; batch k + 1 is copied into the other half of a double
+  // buffer (cp.async, NT records at a time) while batch k is walked, and the
+  // list indices of batch k + 2 are fetched meanwhile
+  const int nbk = stop > start ? (stop - start + B - 1) / B : 0;
+  constexpr int kNone = -2;  // no list position here
+  constexpr int EPT = B / NT;  // records per thread and batch
+  auto index = [&](int k, int* g) {
+    const int b1 = stop - k * B, b0 = max(start, b1 - B);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = t + u * NT;
+      g[u] = (k < nbk && e < b1 - b0) ? vals[b0 + e] : kNone;
     }
-    __syncthreads();
+  };
+  auto stage = [&](int k, const int* g) {
+    const int buf = k & 1;
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = t + u * NT;
+      if (g[u] == kNone) continue;
+      if (g[u] < 0 || g[u] >= n) {
+        s1[buf][e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s2[buf][e] = make_float2(0.0f, INFINITY);  // never contributes
+        sg[buf][e] = -1;
+      } else {
+        cp_async16(&s0[buf][e], rec + 3 * (size_t)g[u]);
+        cp_async16(&s1[buf][e], rec + 3 * (size_t)g[u] + 1);
+        cp_async8(&s2[buf][e], rec + 3 * (size_t)g[u] + 2);
+        sg[buf][e] = g[u];
+      }
+    }
+  };
+  int gn[EPT];
+  index(0, gn);
+  stage(0, gn);
+  cp_async_commit();
+  index(1, gn);
+  for (int k = 0; k < nbk; ++k) {
+    const int b1 = stop - k * B, b0 = max(start, b1 - B), buf = k & 1;
+    __syncthreads();  // batch k - 1 is walked: its buffer takes batch k + 1
+    stage(k + 1, gn);
+    cp_async_commit();
+    index(k + 2, gn);
+    cp_async_wait<1>();  // this thread's copies of batch k have landed
+    __syncthreads();     // and everyone's
     for (int j = min(b1, wstop) - b0 - 1; j >= 0; --j) {
       const int pos = b0 - start + j;  // list position
-      const float4 r0 = s0[j], r1 = s1[j];
-      const float2 r2 = s2[j];
+      const float4 r0 = s0[buf][j], r1 = s1[buf][j];
+      const float2 r2 = s2[buf][j];
       const float dx = r0.x - fx;
       const float cadx2 = r0.z * dx * dx, cbdx = r0.w * dx;
       float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, dop = 0.0f, dc0 = 0.0f, dc1 = 0.0f, dc2 = 0.0f;
@@ -338,11 +408,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
         v[7] = dc1;
         const float s8 = reduce8(v);
         const float sb = warp_sum(dc2);
-        const int g = sg[j];
+        const int g = sg[buf][j];
         if (g >= 0 && adds) atomicAdd(gbase + (size_t)gstride * g, lane == 1 ? sb : s8);
       }
     }
   }
+  cp_async_wait<0>();  // no copy outlives the CTA
 }
 
 // ---------------------------------------------------------------- host side

@@ -26,8 +26,11 @@ struct RowSource {
   const float* pos;         // [n][3]
   float radius;             // background sphere radius (pixels)
   int32_t* status;
-  const int32_t* px_ids;    // pixels: optional list of the pixels to process
-  const int32_t* n_px;      // its device count
+  // Optional list of the rows to process (pixels, or indices into vis_ids)
+  // and its device count; NULL: every row. Row k of the features X written
+  // and of the feature gradients dX read belongs to list[k].
+  const int32_t* list;
+  const int32_t* n_list;
 };
 
 // gather.cu: bf16 features X [rows][32] per field, and the reverse scatter
@@ -153,6 +156,19 @@ __device__ __forceinline__ void gemm(uint32_t d, const uint8_t* A, const uint8_t
   }
 }
 
+// As gemm, with A stored with AP >= K columns per row (its core-matrix row
+// groups AP / 8 * 128 bytes apart); the first K columns are multiplied.
+template <int N, int K, int AP>
+__device__ __forceinline__ void gemm_ap(uint32_t d, const uint8_t* A, const uint8_t* B) {
+  static_assert(AP >= K && AP % 8 == 0, "A columns");
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint64_t da = sdesc(saddr(A) + ks * 256, 128, (AP / 8) * 128);
+    const uint64_t db = sdesc(saddr(B) + ks * 256, 128, (K / 8) * 128);
+    mma(d, da, db, idesc<N>(), ks > 0 ? 1u : 0u);
+  }
+}
+
 // Two operand values (bf16, or f16 when H16), round to nearest even.
 template <bool H16 = false>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
@@ -255,6 +271,35 @@ __device__ __forceinline__ void gemm_dx(uint32_t d, const uint8_t* dZ, const uin
     const uint64_t da = sdesc(saddr(dZ) + ks * 256, 128, (K / 8) * 128);
     const uint64_t db = sdesc(saddr(W) + ks * 2 * (N / 8) * 128, (N / 8) * 128, 128);
     mma(d, da, db, idesc<N, false, true>(), (acc || ks > 0) ? 1u : 0u);
+  }
+}
+
+// As gemm_dx, with dZ stored with AP >= K columns per row.
+template <int N, int K, int AP>
+__device__ __forceinline__ void gemm_dx_ap(uint32_t d, const uint8_t* dZ, const uint8_t* W) {
+  static_assert(AP >= K && AP % 8 == 0, "dZ columns");
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint64_t da = sdesc(saddr(dZ) + ks * 256, 128, (AP / 8) * 128);
+    const uint64_t db = sdesc(saddr(W) + ks * 2 * (N / 8) * 128, (N / 8) * 128, 128);
+    mma(d, da, db, idesc<N, false, true>(), ks > 0 ? 1u : 0u);
+  }
+}
+
+// Transposed weight-gradient product over the 128 points (rows) of a tile,
+// D[128 x N] (+)= A^T dZ: A a point-row tile of AP columns read as an
+// MN-major A operand (D row m = column m of A; rows m >= AP read the bytes
+// that follow the tile and are never used), dZ a point-row tile of BP >= N
+// columns read as an MN-major B operand (its first N columns). With a
+// column of ones in A, that row of D is the column sum of dZ.
+template <int N, int AP, int BP>
+__device__ __forceinline__ void gemm_at(uint32_t d, const uint8_t* A, const uint8_t* dZ, bool acc) {
+  static_assert(AP % 8 == 0 && BP % 8 == 0 && BP >= N, "columns");
+#pragma unroll
+  for (int ks = 0; ks < 128 / 16; ++ks) {
+    const uint64_t da = sdesc(saddr(A) + ks * 2 * (AP / 8) * 128, (AP / 8) * 128, 128);
+    const uint64_t db = sdesc(saddr(dZ) + ks * 2 * (BP / 8) * 128, (BP / 8) * 128, 128);
+    mma(d, da, db, idesc<N, true, true>(), (acc || ks > 0) ? 1u : 0u);
   }
 }
 
