@@ -20,7 +20,8 @@ hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int
                            float* conic, float* depth, int32_t* rect, int32_t* ntiles, uint8_t* flag,
                            int32_t* status, cudaStream_t s);
 hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t s);
-hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s);
+hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s);
+size_t query_fwd_workspace_f32(const hyrf_fields& f, const FieldsDev& F, int n);
 hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s);
 hyrf_status launch_query_explicit(const hyrf_query_fields_args& a, cudaStream_t s);
 hyrf_status launch_query_explicit_bwd(const hyrf_query_fields_backward_args& a, cudaStream_t s);
@@ -215,7 +216,8 @@ size_t hyrf_query_fields_workspace_size(const hyrf_query_fields_args* a) {
   if (a->explicit_only) return align_up(precull_workspace(a->n));
   FieldsDev F;
   const bool tc = make_fields(a->fields, F, true) && F.cm.bf16;
-  return align_up(precull_workspace(a->n)) + (tc && !a->features ? tc_fwd_feature_bytes(a->n, 2) : 0);
+  return align_up(precull_workspace(a->n)) + (tc && !a->features ? tc_fwd_feature_bytes(a->n, 2) : 0) +
+         (tc ? 0 : query_fwd_workspace_f32(a->fields, F, a->n));
 }
 
 hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t ws_bytes,
@@ -246,7 +248,7 @@ hyrf_status hyrf_query_fields(const hyrf_query_fields_args* a, void* ws, size_t 
                                 : launch_precull(to_dev(a->cam), a->pos, a->n, a->vis_ids, a->n_vis, ws, S(stream));
   if (st != HYRF_OK) return st;
   // BF16 decoders run on the tensor cores, FP32 decoders on the CUDA cores
-  return F.cm.bf16 ? launch_query_fwd_tc(*a, F, ws, S(stream)) : launch_query_fwd(*a, F, S(stream));
+  return F.cm.bf16 ? launch_query_fwd_tc(*a, F, ws, S(stream)) : launch_query_fwd(*a, F, ws, S(stream));
 }
 
 size_t hyrf_precull_workspace_size(const hyrf_precull_args* a) {

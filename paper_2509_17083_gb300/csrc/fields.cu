@@ -1,13 +1,18 @@
 // Field query (Sec. 3.2, Eqs. 2-7) and neural background (Sec. 3.3,
 // Eqs. 10-11, App. A.2): FP32 CUDA-core kernels, forward and backward.
-// Backward kernels recompute the decoder activations, keep them in shared
-// memory as [feature][point] tiles, and reduce the weight gradients per CTA
-// into a private float32 slab (no atomics); one reduction kernel adds the
-// slabs into the caller's gradient buffers.
+// Forward: for 16-level grids with 2 x 64 decoders the hash gather runs in
+// its own full-occupancy kernel (k_gather_f32, gather.cu) and the decoders
+// here read its f32 features (k_query_dec, k_bg_dec); other shapes use the
+// fused kernels (gather and decoders in one thread per point). Backward
+// kernels recompute the decoder activations, keep them in shared memory as
+// [feature][point] tiles, and reduce the weight gradients per CTA into a
+// private float32 slab (no atomics); one reduction kernel adds the slabs
+// into the caller's gradient buffers. The field-query reverse runs on the
+// visible rows with a non-zero upstream gradient only.
 #include <cmath>
 #include <type_traits>
 
-#include "field_ops.cuh"
+#include "tc_ops.cuh"
 
 // This file is compiled several times: part 0 holds the host-side dispatch,
 // the shape-independent kernels and their launch wrappers; parts 1-3 each
@@ -18,6 +23,10 @@
 #endif
 
 namespace hyrf {
+
+// gather.cu: the hash gather with f32 features out (the FP32 split path).
+hyrf_status launch_gather_f32(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows, float* Xg,
+                              float* Xr, cudaStream_t s);
 
 struct QueryFwdIO {
   int n;
@@ -68,6 +77,36 @@ __device__ __forceinline__ void cam_center(const CamDev& c, float pc[3]) {
 constexpr int kFwdThreads = 128;
 constexpr int kFwdPitch = kFwdThreads + 1;
 
+// Eq. 7: the decoder outputs (go: alpha_n, s_n[3], r_n[4]; co: c_n[3])
+// aggregated with the explicit parameters of Gaussian g into visible row i.
+__device__ __forceinline__ void aggregate(const QueryFwdIO& io, int i, int g, const float* go, const float* co) {
+  io.alpha[i] = sigmoidf_(go[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
+  const float se = io.scale_e ? io.scale_e[g] : 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(go[1 + k] + se);
+  const float rn = sqrtf(go[4] * go[4] + go[5] * go[5] + go[6] * go[6] + go[7] * go[7]);
+  const float den = fmaxf(rn, 1e-12f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = go[4 + k] / den;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) io.color[3 * i + k] = sigmoidf_(co[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
+}
+
+// N consecutive floats (16-byte aligned) into registers.
+template <int N>
+__device__ __forceinline__ void load_row(const float* __restrict__ src, float* x) {
+  static_assert(N % 4 == 0, "row length");
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < N / 4; ++k) {
+    const float4 v = __ldcs(s4 + k);
+    x[4 * k] = v.x;
+    x[4 * k + 1] = v.y;
+    x[4 * k + 2] = v.z;
+    x[4 * k + 3] = v.w;
+  }
+}
+
 template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev cam, QueryFwdIO io) {
   constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
@@ -101,17 +140,47 @@ __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev c
       pos_enc(dir, fc + NG);
       mlp_fwd<NC, WID, NH, 3, WT>(F.cm, fc, col, kFwdPitch, co);
     }
-    // Eq. 7 aggregation with the explicit parameters.
-    io.alpha[i] = sigmoidf_(go[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
-    const float se = io.scale_e ? io.scale_e[g] : 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(go[1 + k] + se);
-    const float rn = sqrtf(go[4] * go[4] + go[5] * go[5] + go[6] * go[6] + go[7] * go[7]);
-    const float den = fmaxf(rn, 1e-12f);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = go[4 + k] / den;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) io.color[3 * i + k] = sigmoidf_(co[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
+    aggregate(io, i, g, go, co);
+  }
+}
+
+// FP32 split path: the decoders of the field query on the features that
+// k_gather_f32 (gather.cu) wrote, X [n_vis][2 NL] per field (the same FP32
+// contraction and interpolation as encode()), one thread per visible row.
+template <int NL, int WID, int NH, class WT>
+__global__ void __launch_bounds__(kFwdThreads) k_query_dec(FieldsDev F, CamDev cam, QueryFwdIO io,
+                                                          const float* __restrict__ Xg,
+                                                          const float* __restrict__ Xr) {
+  constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
+  __shared__ float hid[WID * kFwdPitch];
+  float* col = hid + threadIdx.x;
+  const int nv = min(*io.n_vis, io.n);
+  float pc[3];
+  cam_center(cam, pc);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    const int g = io.vis_ids[i];
+    if (g < 0 || g >= io.n) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      continue;
+    }
+    float go[8];
+    {
+      float fg[NG];
+      load_row<NG>(Xg + (size_t)i * NG, fg);
+      mlp_fwd<NG, WID, NH, 8, WT>(F.gm, fg, col, kFwdPitch, go);
+    }
+    float co[3];
+    {
+      float fc[NC];
+      load_row<NG>(Xr + (size_t)i * NG, fc);
+      const float p[3] = {io.pos[3 * (int64_t)g], io.pos[3 * (int64_t)g + 1], io.pos[3 * (int64_t)g + 2]};
+      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+      const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+      pos_enc(dir, fc + NG);
+      mlp_fwd<NC, WID, NH, 3, WT>(F.cm, fc, col, kFwdPitch, co);
+    }
+    aggregate(io, i, g, go, co);
   }
 }
 
@@ -433,6 +502,30 @@ __global__ void __launch_bounds__(kFwdThreads) k_bg_exact_fwd(FieldsDev F, CamDe
   }
 }
 
+// FP32 split path, exact background: the colour decoder at every pixel's
+// sphere hit on the features k_gather_f32 wrote, Xb [W H][2 NL].
+template <int NL, int WID, int NH, class WT>
+__global__ void __launch_bounds__(kFwdThreads) k_bg_dec(FieldsDev F, CamDev cam, float radius,
+                                                       const float* __restrict__ Xb,
+                                                       const float* __restrict__ C_fg,
+                                                       const float* __restrict__ T_final,
+                                                       float* __restrict__ C) {
+  constexpr int NG = 2 * NL, NC = NG + kPEPad;
+  __shared__ float hid[WID * kFwdPitch];
+  float* col = hid + threadIdx.x;
+  const int P = cam.W * cam.H;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float ps[3], dir[3], x0[NC], out[3];
+    bg_ray(cam, F, radius, p % cam.W, p / cam.W, ps, dir);
+    load_row<NG>(Xb + (size_t)p * NG, x0);
+    pos_enc(dir, x0 + NG);
+    mlp_fwd<NC, WID, NH, 3, WT>(F.cm, x0, col, kFwdPitch, out);
+    const float T = T_final[p];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * sigmoidf_(out[k]);
+  }
+}
+
 template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kFwdThreads) k_bg_map_texels(FieldsDev F, int Hb, int Wb, float radius,
                                                                float* __restrict__ map) {
@@ -729,12 +822,25 @@ hyrf_status launch_bg_map_bwd_pix(const FieldsDev& F, const CamDev& cam, float r
 size_t tc_bwd_workspace(const FieldsDev& F, bool geo, int64_t rows, bool have_features);
 size_t tc_bg_fwd_workspace(int64_t P, bool have_features, bool skip);
 
+static int part_of(const hyrf_fields& f, const FieldsDev& F);
+
+// FP32 shapes that take the split path (gather kernel + decoder kernel):
+// 16 levels, 2 x 64 decoders (part 2); f32 feature bytes of `rows` rows.
+static bool f32_split(const hyrf_fields& f, const FieldsDev& F) { return part_of(f, F) == 2; }
+static size_t f32_feature_bytes(int64_t rows, int fields) { return align_up((size_t)fields * rows * 32 * 4); }
+
+size_t query_fwd_workspace_f32(const hyrf_fields& f, const FieldsDev& F, int n) {
+  return f32_split(f, F) ? f32_feature_bytes(n, 2) : 0;
+}
+
 size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward) {
   if (a.bg.mode == 0 && F.cm.bf16) {  // tensor-core path: gathered features (+ gradients)
     const int64_t P = (int64_t)a.cam.width * a.cam.height;
     const bool have = a.features != nullptr, skip = a.bg.tau_T > 0.0f;
     return backward ? tc_bwd_workspace(F, false, P, have) : tc_bg_fwd_workspace(P, have && !skip, skip);
   }
+  if (a.bg.mode == 0 && !backward && f32_split(a.fields, F))
+    return f32_feature_bytes((int64_t)a.cam.width * a.cam.height, 1);
   Carver c(nullptr);
   if (a.bg.mode == 1) {
     c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);  // map
@@ -745,7 +851,7 @@ size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F,
 }
 
 #define HYRF_DECLARE_PART(P)                                                                      \
-  hyrf_status query_fwd_p##P(const FieldsDev&, const CamDev&, const QueryFwdIO&, cudaStream_t);   \
+  hyrf_status query_fwd_p##P(const FieldsDev&, const CamDev&, const QueryFwdIO&, float*, cudaStream_t); \
   hyrf_status query_bwd_p##P(const FieldsDev&, const CamDev&, const QueryBwdIO&,                  \
                              const hyrf_field_grads&, float*, cudaStream_t);                      \
   hyrf_status bg_fwd_p##P(const hyrf_composite_background_args&, const FieldsDev&, void*,          \
@@ -765,15 +871,28 @@ static int part_of(const hyrf_fields& f, const FieldsDev& F) {
   return 0;
 }
 
-hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, cudaStream_t s) {
+size_t precull_workspace(int n);
+
+// ws: the field query's workspace (the pre-cull's part first, then, for the
+// split shapes, the f32 features of both fields).
+hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s) {
   QueryFwdIO io{a.n,      a.pos,   a.alpha_e, a.scale_e, a.color_e, a.vis_ids,
                 a.n_vis,  a.alpha, a.scale,   a.quat,    a.color,   a.status};
   const CamDev cam = to_dev(a.cam);
   if (a.n == 0) return HYRF_OK;
+  float* X = nullptr;
+  if (f32_split(a.fields, F)) {
+    Carver c(ws);
+    c.take<char>(precull_workspace(a.n));
+    X = reinterpret_cast<float*>(c.take<char>(f32_feature_bytes(a.n, 2)));
+    const RowSource RS{0, a.n, a.vis_ids, a.n_vis, a.pos, 0.0f, a.status, nullptr, nullptr};
+    hyrf_status st = launch_gather_f32(F, cam, RS, a.n, X, X + (size_t)a.n * 32, s);
+    if (st != HYRF_OK) return st;
+  }
   switch (part_of(a.fields, F)) {
-    case 1: return query_fwd_p1(F, cam, io, s);
-    case 2: return query_fwd_p2(F, cam, io, s);
-    case 3: return query_fwd_p3(F, cam, io, s);
+    case 1: return query_fwd_p1(F, cam, io, X, s);
+    case 2: return query_fwd_p2(F, cam, io, X, s);
+    case 3: return query_fwd_p3(F, cam, io, X, s);
     default: return HYRF_ERR_UNSUPPORTED;
   }
 }
@@ -847,11 +966,17 @@ hyrf_status launch_bg_bwd(const hyrf_composite_background_backward_args& b, cons
 #endif
 
 template <int NL, int WID, int NH, class WT>
-static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const QueryFwdIO& io,
+static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const QueryFwdIO& io, float* X,
                                   cudaStream_t s) {
   if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
     return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
   } else {
+    if (X) {  // split path: features gathered by k_gather_f32
+      HYRF_LAUNCH("k_query_dec", s,
+                  k_query_dec<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(
+                      F, cam, io, X, X + (size_t)io.n * 2 * NL));
+      return HYRF_OK;
+    }
     HYRF_LAUNCH("k_query_fwd", s,
                 k_query_fwd<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(F, cam, io));
     return HYRF_OK;
@@ -879,6 +1004,15 @@ static hyrf_status bg_fwd_impl(const hyrf_composite_background_args& a, const Fi
   if (a.bg.mode == 0) {
     if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
       return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
+    } else if constexpr (NL == 16 && WID == 64 && NH == 2) {  // split path
+      float* Xb = static_cast<float*>(ws);
+      const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
+      hyrf_status st = launch_gather_f32(F, cam, RS, P, nullptr, Xb, s);
+      if (st != HYRF_OK) return st;
+      HYRF_LAUNCH("k_bg_dec", s,
+                  k_bg_dec<NL, WID, NH, WT><<<fwd_blocks(P, kFwdThreads), kFwdThreads, 0, s>>>(
+                      F, cam, a.bg.radius, Xb, a.C_fg, a.T_final, a.C));
+      return HYRF_OK;
     } else {
       HYRF_LAUNCH("k_bg_exact_fwd", s,
                   k_bg_exact_fwd<NL, WID, NH, WT><<<fwd_blocks(P, kFwdThreads), kFwdThreads, 0, s>>>(
@@ -940,8 +1074,8 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
 #define HYRF_PASTE(a, b) HYRF_PASTE2(a, b)
 
 hyrf_status HYRF_PASTE(query_fwd_p, HYRF_FIELDS_PART)(const FieldsDev& F, const CamDev& cam,
-                                                      const QueryFwdIO& io, cudaStream_t s) {
-  return query_fwd_impl<HYRF_SHAPE>(F, cam, io, s);
+                                                      const QueryFwdIO& io, float* X, cudaStream_t s) {
+  return query_fwd_impl<HYRF_SHAPE>(F, cam, io, X, s);
 }
 hyrf_status HYRF_PASTE(query_bwd_p, HYRF_FIELDS_PART)(const FieldsDev& F, const CamDev& cam,
                                                       const QueryBwdIO& io,

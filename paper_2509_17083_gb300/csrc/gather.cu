@@ -326,6 +326,47 @@ __global__ void __launch_bounds__(kThreads, 4)
   }
 }
 
+// FP32 path: the same gather from f32 tables with f32 features out, X*:
+// [rows][32] float (level-major, features 2l and 2l + 1), for the decoders
+// on the CUDA cores.
+template <bool BOTH, bool SAME>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_gather_f32(FieldsDev F, CamDev cam, RowSource S, float2* __restrict__ Xg, float2* __restrict__ Xr) {
+  __shared__ float ys[kRows][3];
+  __shared__ float2 xs[2][kRows][kLevels + 1];
+  const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
+  const int nrows = row_count(S, cam);
+  const int row0 = blockIdx.x * kRows;
+  if (row0 >= nrows) return;  // CTA-uniform
+  if (l == 0) {
+    float y[3];
+    int g;
+    bool ok;
+    row_point(S, F, cam, row0 + lane, nrows, y, nullptr, g, ok);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ys[lane][k] = y[k];
+  }
+  __syncthreads();
+  const float y[3] = {ys[lane][0], ys[lane][1], ys[lane][2]};
+  if (BOTH && SAME) {
+    float2 a, b;
+    level_feature2<0>(F.geo, F.rad, l, y, a, b);
+    xs[0][lane][l] = a;
+    xs[1][lane][l] = b;
+  } else {
+    if (BOTH) xs[0][lane][l] = level_feature<0>(F.geo, l, y);
+    xs[1][lane][l] = level_feature<0>(F.rad, l, y);
+  }
+  __syncthreads();
+  // coalesced write-out: thread t -> row t/16, level t%16
+  const int r = threadIdx.x >> 4, wd = threadIdx.x & 15;
+  if (row0 + r < nrows) {
+    const size_t o = (size_t)(row0 + r) * 16 + wd;
+    if (BOTH) __stcs(Xg + o, xs[0][r][wd]);
+    __stcs(Xr + o, xs[1][r][wd]);
+  }
+}
+
 // Reverse of k_gather. dXg/dXr: [rows][32] f32 feature gradients (already
 // unscaled; streamed with evict-first loads). Gaussians: both fields, and
 // d_pos[g] += J^T sum_l dL/dy_l; pixels: the radiance field. SAME: both
@@ -464,6 +505,23 @@ hyrf_status launch_gather(const FieldsDev& F, const CamDev& cam, const RowSource
   if (F.rad.bf16) return gather_dt<1, false>(F, cam, S, grid, Xg, Xr, s);
   if (F.rad.f16) return HYRF_ERR_UNSUPPORTED;
   return gather_dt<0, false>(F, cam, S, grid, Xg, Xr, s);
+}
+
+// f32 tables, f32 features (the FP32 path's split field query).
+hyrf_status launch_gather_f32(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows, float* Xg,
+                              float* Xr, cudaStream_t s) {
+  const int grid = grid_for(rows);
+  if (grid == 0) return HYRF_OK;
+  if (F.rad.u8 || F.rad.bf16 || F.rad.f16 || F.rad.L != kLevels) return HYRF_ERR_UNSUPPORTED;
+  float2* g2 = reinterpret_cast<float2*>(Xg);
+  float2* r2 = reinterpret_cast<float2*>(Xr);
+  if (S.pixels)
+    HYRF_LAUNCH("k_gather_f32<pixels>", s, k_gather_f32<false, false><<<grid, kThreads, 0, s>>>(F, cam, S, nullptr, r2));
+  else if (same_cells(F.geo, F.rad))
+    HYRF_LAUNCH("k_gather_f32<gaussians>", s, k_gather_f32<true, true><<<grid, kThreads, 0, s>>>(F, cam, S, g2, r2));
+  else
+    HYRF_LAUNCH("k_gather_f32<gaussians>", s, k_gather_f32<true, false><<<grid, kThreads, 0, s>>>(F, cam, S, g2, r2));
+  return HYRF_OK;
 }
 
 hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows,

@@ -67,6 +67,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+// 16 bytes through L2 only (no L1 line allocated).
+__device__ __forceinline__ void cp_async16_l2(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // Wait until at most N of this thread's most recent groups are in flight.
 template <int N>
@@ -89,9 +93,10 @@ __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis,
 }
 
 // One CTA per tile, one pixel per thread. The tile's list is taken in
-// batches of 256 records; batch b + 1 is copied into the other half of a
-// double buffer (cp.async, one record per thread) while batch b is
-// composited, and the list index of batch b + 2 is fetched meanwhile.
+// batches of 256 records (cp.async, one record per thread, into a double
+// buffer). Most tiles stop within their first batch or two, so the first
+// batch is loaded alone; from the second on, batch b + 1 is copied into the
+// other half of the buffer while batch b is composited.
 __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ ranges,
                                                     const int32_t* __restrict__ vals, int n,
                                                     const float4* __restrict__ rec, int W, int H,
@@ -135,21 +140,23 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const int32_t* __restrict__ 
     const int g = vals[k];
     return g < 0 ? n : g;  // out of range either way: stage() reports it
   };
+  auto fetch = [&](int b) {
+    stage(b, index(b));
+    cp_async_commit();
+  };
   float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
   int last = 0;
   bool done = !inside;
-  stage(0, index(0));
-  cp_async_commit();
-  int g_next = index(1);
+  fetch(0);
   for (int b = 0; b < nb; ++b) {
     // also: every thread is done with batch b - 1, whose buffer the copies
     // of batch b + 1 overwrite
     if (__syncthreads_count(done) == 256) break;
-    stage(b + 1, g_next);
-    cp_async_commit();
-    g_next = index(b + 2);
-    cp_async_wait<1>();  // this thread's copies of batch b have landed
-    __syncthreads();     // and everyone's
+    if (b == 1) fetch(1);
+    if (b >= 1) fetch(b + 1);
+    if (b == 0) cp_async_wait<0>();
+    else cp_async_wait<1>();  // this thread's copies of batch b have landed
+    __syncthreads();          // and everyone's
     const int buf = b & 1, b0 = start + 256 * b;
     const int cnt = min(256, end - b0);
     for (int j = 0; j < cnt && !done; ++j) {
@@ -338,8 +345,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
         s2[buf][e] = make_float2(0.0f, INFINITY);  // never contributes
         sg[buf][e] = -1;
       } else {
-        cp_async16(&s0[buf][e], rec + 3 * (size_t)g[u]);
-        cp_async16(&s1[buf][e], rec + 3 * (size_t)g[u] + 1);
+        cp_async16_l2(&s0[buf][e], rec + 3 * (size_t)g[u]);
+        cp_async16_l2(&s1[buf][e], rec + 3 * (size_t)g[u] + 1);
         cp_async8(&s2[buf][e], rec + 3 * (size_t)g[u] + 2);
         sg[buf][e] = g[u];
       }
