@@ -258,12 +258,29 @@ __device__ __forceinline__ float dot_row(const WT* __restrict__ W, int o, const 
 
 // Hidden layer: col[o * pitch] = ReLU(W[o] . x + b[o]) for o < OUT. x is in
 // registers; the output goes to this thread's shared-memory column.
+// Four outputs at a time (four independent accumulation chains; each
+// output sums its products in the same order as dot_row).
 template <int IN, int OUT, class WT>
 __device__ __forceinline__ void dense_col(const WT* __restrict__ W, const float* __restrict__ b,
                                           const float* x, float* col, int pitch) {
-  static_assert(IN % 4 == 0, "IN must be a multiple of 4");
-#pragma unroll 2
-  for (int o = 0; o < OUT; ++o) col[o * pitch] = fmaxf(dot_row<IN>(W, o, x) + __ldg(b + o), 0.0f);
+  static_assert(IN % 4 == 0 && OUT % 4 == 0, "IN and OUT must be multiples of 4");
+#pragma unroll 1
+  for (int o = 0; o < OUT; o += 4) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < IN / 4; ++i) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 w = w4(W, (o + u) * IN + 4 * i);
+        acc[u] = fmaf(w.x, x[4 * i], acc[u]);
+        acc[u] = fmaf(w.y, x[4 * i + 1], acc[u]);
+        acc[u] = fmaf(w.z, x[4 * i + 2], acc[u]);
+        acc[u] = fmaf(w.w, x[4 * i + 3], acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) col[(o + u) * pitch] = fmaxf(acc[u] + __ldg(b + o + u), 0.0f);
+  }
 }
 
 // Output layer (small OUT, registers): y = W x + b.

@@ -24,6 +24,8 @@
 
 namespace hyrf {
 
+size_t slab_bytes(const FieldsDev& F, bool geo);
+
 // gather.cu: the hash gather with f32 features out (the FP32 split path).
 hyrf_status launch_gather_f32(const FieldsDev& F, const CamDev& cam, const RowSource& S, int rows, float* Xg,
                               float* Xr, cudaStream_t s);
@@ -616,12 +618,16 @@ __global__ void __launch_bounds__(256) k_bg_map_bwd_pix(FieldsDev F, CamDev cam,
 // Reverse of the colour field at background points: MODE 0 = one point per
 // pixel (exact mode, also writes dL/dT_final and dL/dC_fg), MODE 1 = one
 // point per map texel with the texel gradient given in dmap.
-template <int NL, int WID, int NH, int MODE, class WT>
+// SPLIT (exact mode, FP32 split path): the features come from k_gather_f32
+// (Xb [W H][2 NL]) and the feature gradients go to dXb [W H][2 NL] for the
+// table scatter (k_scatter, gather.cu) instead of being gathered and
+// scattered here.
+template <int NL, int WID, int NH, int MODE, class WT, bool SPLIT = false>
 __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     FieldsDev F, CamDev cam, float radius, int Hb, int Wb, const float* __restrict__ T_final,
     const float* __restrict__ dC, float* __restrict__ dC_fg, float* __restrict__ dT,
     const float* __restrict__ dmap, float* __restrict__ g_rad_table, float loss_scale,
-    SlabLayout SL, float* slabs) {
+    SlabLayout SL, float* slabs, const float* __restrict__ Xb = nullptr, float* __restrict__ dXb = nullptr) {
   extern __shared__ float sm[];
   constexpr int NG = 2 * NL, NC = NG + kPEPad;
   float* act = sm;
@@ -643,7 +649,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
       texel_point(ee / Wb, ee % Wb, Hb, Wb, radius, y, dir);
     }
     float x0[NC], out[3], dz3[3];
-    encode<NL>(F.rad, y, x0);
+    if constexpr (SPLIT) {
+      load_row<NG>(Xb + (size_t)ee * NG, x0);
+    } else {
+      encode<NL>(F.rad, y, x0);
+    }
     pos_enc(dir, x0 + NG);
     decoder_fwd_store<NC, WID, NH, 3, WT>(F.cm, x0, act, out);
     float cs[3];
@@ -671,7 +681,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     if (ok) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
-      encode_bwd<NL, true>(F.rad, y, dx, g_rad_table, nullptr);
+      if constexpr (SPLIT) {
+        float4* d4 = reinterpret_cast<float4*>(dXb + (size_t)ee * NG);
+#pragma unroll
+        for (int k = 0; k < NG / 4; ++k) __stcs(d4 + k, make_float4(dx[4 * k], dx[4 * k + 1], dx[4 * k + 2], dx[4 * k + 3]));
+      } else {
+        encode_bwd<NL, true>(F.rad, y, dx, g_rad_table, nullptr);
+      }
     }
   }
 }
@@ -839,8 +855,15 @@ size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F,
     const bool have = a.features != nullptr, skip = a.bg.tau_T > 0.0f;
     return backward ? tc_bwd_workspace(F, false, P, have) : tc_bg_fwd_workspace(P, have && !skip, skip);
   }
-  if (a.bg.mode == 0 && !backward && f32_split(a.fields, F))
-    return f32_feature_bytes((int64_t)a.cam.width * a.cam.height, 1);
+  if (a.bg.mode == 0 && f32_split(a.fields, F)) {  // split path: features (+ gradients, slabs)
+    const int64_t P = (int64_t)a.cam.width * a.cam.height;
+    if (!backward) return f32_feature_bytes(P, 1);
+    Carver c(nullptr);
+    c.take<char>(slab_bytes(F, false));
+    c.take<char>(f32_feature_bytes(P, 1));
+    c.take<char>(f32_feature_bytes(P, 1));
+    return c.size();
+  }
   Carver c(nullptr);
   if (a.bg.mode == 1) {
     c.take<float>((size_t)a.bg.map_h * a.bg.map_w * 3);  // map
@@ -1036,6 +1059,28 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
   const CamDev cam = to_dev(a.cam);
   const SlabLayout SL = make_slab_layout(nullptr, &F.cm);
   const int ctas = bwd_ctas();
+  if constexpr (NL == 16 && WID == 64 && NH == 2 && std::is_same<WT, float>::value) {
+    if (a.bg.mode == 0) {  // split path: gather, decoder reverse, scatter
+      const int P = cam.W * cam.H;
+      Carver c(ws);
+      float* slabs = reinterpret_cast<float*>(c.take<char>(slab_bytes(F, false)));
+      float* Xb = reinterpret_cast<float*>(c.take<char>((size_t)P * 32 * 4));
+      float* dXb = reinterpret_cast<float*>(c.take<char>((size_t)P * 32 * 4));
+      cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
+      const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
+      hyrf_status st = launch_gather_f32(F, cam, RS, P, nullptr, Xb, s);
+      if (st != HYRF_OK) return st;
+      const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
+      set_smem_limit<k_bg_field_bwd<NL, WID, NH, 0, WT, true>>((int)smem);
+      HYRF_LAUNCH("k_bg_dec_bwd", s,
+                  k_bg_field_bwd<NL, WID, NH, 0, WT, true><<<ctas, kBwdThreads, smem, s>>>(
+                      F, cam, a.bg.radius, 0, 0, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, nullptr, nullptr,
+                      b.loss_scale, SL, slabs, Xb, dXb));
+      st = launch_slab_reduce(slabs, ctas, SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
+      if (st != HYRF_OK) return st;
+      return launch_scatter(F, cam, RS, P, nullptr, dXb, nullptr, b.grads.rad_table, nullptr, s);
+    }
+  }
   Carver c(ws);
   float* map = nullptr;
   float* dmap = nullptr;

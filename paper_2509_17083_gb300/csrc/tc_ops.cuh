@@ -44,7 +44,10 @@ hyrf_status launch_scatter(const FieldsDev& F, const CamDev& cam, const RowSourc
 
 namespace tc {
 
-constexpr uint32_t kSpin = 1u << 24;
+// Polls of a bounded mbarrier wait before it gives up: each poll
+// (mbarrier.try_wait, which may suspend the thread) takes ~3.8 us on a
+// GB300, so a wait that never completes ends after ~4 s.
+constexpr uint32_t kSpin = 1u << 20;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);

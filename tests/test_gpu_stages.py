@@ -380,3 +380,25 @@ def test_bounded_wait_gives_up_with_a_status():
     assert H.read_status(st) == 0
     with pytest.raises(H.HyrfError):
         H.hyrf_check_bounded_wait(st, 0)
+
+
+def test_bounded_wait_time_per_poll():
+    """Wall time of one poll of the bounded wait (mbarrier.try_wait, which may
+    suspend the thread for a hardware-chosen time), from CUDA events around
+    waits of 2^14 and 2^16 polls: the tensor-core kernels give up after 2^20
+    polls, so a wait that never completes ends after 2^20 times this."""
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.hyrf_check_bounded_wait(st, 16)  # load the kernel
+    torch.cuda.synchronize()
+    ms = {}
+    for polls in (1 << 14, 1 << 16):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.hyrf_check_bounded_wait(st, polls)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[polls] = e0.elapsed_time(e1)
+    assert H.read_status(st) & H.HYRF_ERR_TIMEOUT
+    per_poll_us = (ms[1 << 16] - ms[1 << 14]) * 1e3 / ((1 << 16) - (1 << 14))
+    print(f"bounded wait: {per_poll_us * 1e3:.1f} ns per poll; 2^20 polls = {per_poll_us * (1 << 20) / 1e6:.2f} s")
+    assert per_poll_us > 0
