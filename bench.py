@@ -269,7 +269,11 @@ def fp32_peak_tflops(sm_mhz, n_sm):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload; an entry is removed when
 # the kernel changes after its capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # the compositing reverse (one launch of the step driver's config-3
+    # training step): 57,568,000 B read + 435,968 B written
+    ("k_raster_bwd", "bf16"): 58_003_968,
+}
 
 
 def rooflines(R, peaks, prec, sm_mhz, n_sm):

@@ -39,7 +39,7 @@ hyrf_status launch_query_bwd_tc(const hyrf_query_fields_backward_args& a, const 
 hyrf_status launch_bg_bwd_tc(const hyrf_composite_background_backward_args& b, const FieldsDev& F,
                              void* ws, cudaStream_t s);
 size_t slab_bytes(const FieldsDev& F, bool geo);
-size_t query_bwd_workspace(const FieldsDev& F, int n);
+size_t query_bwd_workspace(const hyrf_fields& f, const FieldsDev& F, int n);
 size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F, bool backward);
 hyrf_status launch_bg_fwd(const hyrf_composite_background_args& a, const FieldsDev& F, void* ws,
                           cudaStream_t s);
@@ -277,7 +277,7 @@ size_t hyrf_query_fields_backward_workspace_size(const hyrf_query_fields_backwar
   if (!a || a->explicit_only) return 0;
   FieldsDev F;
   if (!make_fields(a->fields, F, true) || a->n < 0) return 0;
-  return F.cm.bf16 ? tc_bwd_workspace(F, true, a->n, a->features != nullptr) : query_bwd_workspace(F, a->n);
+  return F.cm.bf16 ? tc_bwd_workspace(F, true, a->n, a->features != nullptr) : query_bwd_workspace(a->fields, F, a->n);
 }
 
 hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a, void* ws,

@@ -109,6 +109,14 @@ __device__ __forceinline__ void load_row(const float* __restrict__ src, float* x
   }
 }
 
+// N floats from registers to a 16-byte aligned row (streaming stores).
+template <int N>
+__device__ __forceinline__ void store_row(float* __restrict__ dst, const float* x) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int k = 0; k < N / 4; ++k) __stcs(d4 + k, make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]));
+}
+
 template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev cam, QueryFwdIO io) {
   constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
@@ -244,9 +252,18 @@ constexpr int query_bwd_smem_floats() {
   return (2 * NL + kPEPad + NH * WID) * kActPitch + WID * kActPitch;
 }
 
-template <int NL, int WID, int NH, class WT>
+// SPLIT (FP32 split path): row k of the list takes its features from X*[k]
+// (k_gather_f32 over the listed rows) and leaves its feature gradients in
+// dX*[k] for the table scatter (k_scatter, gather.cu, which also adds the
+// contraction's share of dL/dp); only the positional encoding's share of
+// dL/dp is added here.
+template <int NL, int WID, int NH, class WT, bool SPLIT = false>
 __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev cam, QueryBwdIO io,
-                                                           SlabLayout SL, float* slabs) {
+                                                           SlabLayout SL, float* slabs,
+                                                           const float* __restrict__ Xg = nullptr,
+                                                           const float* __restrict__ Xr = nullptr,
+                                                           float* __restrict__ dXg = nullptr,
+                                                           float* __restrict__ dXr = nullptr) {
   extern __shared__ float sm[];
   constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
   float* act = sm;
@@ -275,7 +292,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     for (int k = 0; k < 3; ++k)
       p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];  // box centre when idle
     float y[3], J[9];
-    contract_p(F, p, y, J);
+    if constexpr (!SPLIT) contract_p(F, p, y, J);
+    const size_t k_row = (size_t)(base + t);  // list position (the split path's X / dX row)
     float da = 0.0f, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dcol[3] = {0, 0, 0};
     float ae = 0.0f, se = 0.0f, ce[3] = {0, 0, 0};
     if (ok) {
@@ -295,7 +313,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     // ---------------- geometry decoder (Eq. 4) and the reverse of Eq. 7
     {
       float x0[NG], out[8], dz8[8];
-      encode<NL>(F.geo, y, x0);
+      if constexpr (SPLIT) {
+        load_row<NG>(Xg + (ok ? k_row : 0) * NG, x0);
+      } else {
+        encode<NL>(F.geo, y, x0);
+      }
       decoder_fwd_store<NG, WID, NH, 8, WT>(F.gm, x0, act, out);
       const float a = sigmoidf_(out[0] + ae);
       dz8[0] = da * a * (1.0f - a);
@@ -328,7 +350,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       if (ok) {
 #pragma unroll
         for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
-        encode_bwd<NL>(F.geo, y, dx, io.g_geo_table, dy);
+        if constexpr (SPLIT) {
+          store_row<NG>(dXg + k_row * NG, dx);
+        } else {
+          encode_bwd<NL>(F.geo, y, dx, io.g_geo_table, dy);
+        }
       }
     }
     // ---------------- colour decoder (Eqs. 5-6) and the reverse of Eq. 7
@@ -338,7 +364,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     float dp[3] = {0.0f, 0.0f, 0.0f};
     {
       float x0[NC], out[3], dz3[3];
-      encode<NL>(F.rad, y, x0);
+      if constexpr (SPLIT) {
+        load_row<NG>(Xr + (ok ? k_row : 0) * NG, x0);
+      } else {
+        encode<NL>(F.rad, y, x0);
+      }
       pos_enc(dir, x0 + NG);
       decoder_fwd_store<NC, WID, NH, 3, WT>(F.cm, x0, act, out);
 #pragma unroll
@@ -356,7 +386,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       if (ok) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) dx[k] *= inv_ls;
-        encode_bwd<NL>(F.rad, y, dx, io.g_rad_table, dy);
+        if constexpr (SPLIT) {
+          store_row<NG>(dXr + k_row * NG, dx);
+        } else {
+          encode_bwd<NL>(F.rad, y, dx, io.g_rad_table, dy);
+        }
         float ddir[3];
         pos_enc_bwd(dir, dx + NG, ddir);
         const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
@@ -365,9 +399,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       }
     }
     if (ok) {
+      if constexpr (SPLIT) {
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        io.d_pos[3 * (int64_t)g + j] += dp[j] + J[j] * dy[0] + J[3 + j] * dy[1] + J[6 + j] * dy[2];
+        for (int j = 0; j < 3; ++j) io.d_pos[3 * (int64_t)g + j] += dp[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          io.d_pos[3 * (int64_t)g + j] += dp[j] + J[j] * dy[0] + J[3 + j] * dy[1] + J[6 + j] * dy[2];
+      }
     }
   }
 }
@@ -876,7 +915,7 @@ size_t bg_workspace(const hyrf_composite_background_args& a, const FieldsDev& F,
 #define HYRF_DECLARE_PART(P)                                                                      \
   hyrf_status query_fwd_p##P(const FieldsDev&, const CamDev&, const QueryFwdIO&, float*, cudaStream_t); \
   hyrf_status query_bwd_p##P(const FieldsDev&, const CamDev&, const QueryBwdIO&,                  \
-                             const hyrf_field_grads&, float*, cudaStream_t);                      \
+                             const hyrf_field_grads&, float*, float*, cudaStream_t);              \
   hyrf_status bg_fwd_p##P(const hyrf_composite_background_args&, const FieldsDev&, void*,          \
                           cudaStream_t);                                                          \
   hyrf_status bg_bwd_p##P(const hyrf_composite_background_backward_args&, const FieldsDev&, void*, \
@@ -925,11 +964,13 @@ hyrf_status launch_active_rows(int n, const int32_t* n_vis, const float* d_alpha
                                const float* d_quat, const float* d_color, Carver& c, int32_t** list,
                                int32_t** n_list, cudaStream_t s);
 
-// FP32 reverse workspace: CTA slabs and the list of rows with a gradient.
-size_t query_bwd_workspace(const FieldsDev& F, int n) {
+// FP32 reverse workspace: CTA slabs, the list of rows with a gradient and,
+// for the split shapes, f32 features and feature gradients of both fields.
+size_t query_bwd_workspace(const hyrf_fields& f, const FieldsDev& F, int n) {
   Carver c(nullptr);
   c.take<char>(slab_bytes(F, true));
   c.take<char>(active_rows_workspace(n));
+  if (f32_split(f, F)) c.take<char>(f32_feature_bytes(n, 4));
   return c.size();
 }
 
@@ -950,10 +991,11 @@ hyrf_status launch_query_bwd(const hyrf_query_fields_backward_args& a, const Fie
   if (st != HYRF_OK) return st;
   io.list = list;
   io.n_list = n_list;
+  float* X = f32_split(a.fields, F) ? reinterpret_cast<float*>(c.take<char>(f32_feature_bytes(a.n, 4))) : nullptr;
   switch (part_of(a.fields, F)) {
-    case 1: return query_bwd_p1(F, cam, io, a.grads, slabs, s);
-    case 2: return query_bwd_p2(F, cam, io, a.grads, slabs, s);
-    case 3: return query_bwd_p3(F, cam, io, a.grads, slabs, s);
+    case 1: return query_bwd_p1(F, cam, io, a.grads, slabs, X, s);
+    case 2: return query_bwd_p2(F, cam, io, a.grads, slabs, X, s);
+    case 3: return query_bwd_p3(F, cam, io, a.grads, slabs, X, s);
     default: return HYRF_ERR_UNSUPPORTED;
   }
 }
@@ -1008,11 +1050,27 @@ static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const Q
 
 template <int NL, int WID, int NH, class WT>
 static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const QueryBwdIO& io,
-                                  const hyrf_field_grads& grads, float* slabs, cudaStream_t s) {
+                                  const hyrf_field_grads& grads, float* slabs, float* X, cudaStream_t s) {
   const SlabLayout SL = make_slab_layout(&F.gm, &F.cm);
   const int ctas = bwd_ctas();
   cudaMemsetAsync(slabs, 0, (size_t)ctas * SL.total * sizeof(float), s);
   const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
+  if constexpr (NL == 16 && WID == 64 && NH == 2 && std::is_same<WT, float>::value) {
+    if (X) {  // split path: the listed rows' features gathered into X, gradients to dX, then scattered
+      const size_t rows = (size_t)io.n * 2 * NL;
+      float *Xg = X, *Xr = X + rows, *dXg = X + 2 * rows, *dXr = X + 3 * rows;
+      const RowSource RS{0, io.n, io.vis_ids, io.n_vis, io.pos, 0.0f, io.status, io.list, io.n_list};
+      hyrf_status st = launch_gather_f32(F, cam, RS, io.n, Xg, Xr, s);
+      if (st != HYRF_OK) return st;
+      set_smem_limit<k_query_bwd<NL, WID, NH, WT, true>>((int)smem);
+      HYRF_LAUNCH("k_query_dec_bwd", s,
+                  k_query_bwd<NL, WID, NH, WT, true><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs, Xg, Xr,
+                                                                                    dXg, dXr));
+      st = launch_slab_reduce(slabs, ctas, SL, slab_targets(grads, true), 1.0f / io.loss_scale, s);
+      if (st != HYRF_OK) return st;
+      return launch_scatter(F, cam, RS, io.n, dXg, dXr, io.g_geo_table, io.g_rad_table, io.d_pos, s);
+    }
+  }
   set_smem_limit<k_query_bwd<NL, WID, NH, WT>>((int)smem);
   HYRF_LAUNCH("k_query_bwd", s,
               k_query_bwd<NL, WID, NH, WT><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs));
@@ -1124,9 +1182,9 @@ hyrf_status HYRF_PASTE(query_fwd_p, HYRF_FIELDS_PART)(const FieldsDev& F, const 
 }
 hyrf_status HYRF_PASTE(query_bwd_p, HYRF_FIELDS_PART)(const FieldsDev& F, const CamDev& cam,
                                                       const QueryBwdIO& io,
-                                                      const hyrf_field_grads& g, float* slabs,
+                                                      const hyrf_field_grads& g, float* slabs, float* X,
                                                       cudaStream_t s) {
-  return query_bwd_impl<HYRF_SHAPE>(F, cam, io, g, slabs, s);
+  return query_bwd_impl<HYRF_SHAPE>(F, cam, io, g, slabs, X, s);
 }
 hyrf_status HYRF_PASTE(bg_fwd_p, HYRF_FIELDS_PART)(const hyrf_composite_background_args& a,
                                                    const FieldsDev& F, void* ws, cudaStream_t s) {
