@@ -230,6 +230,14 @@ hyrf_status hyrf_query_fields_backward(const hyrf_query_fields_backward_args* a,
  * Integer outputs follow a fixed FP32 operation order (no contraction), so
  * they are reproducible bit for bit; when |det Sigma'| < 1e-2 a c the conic
  * is recomputed in FP64 (fp64_flag = 1).
+ * With `footprint` given, the binning is culled to the Gaussian's
+ * opacity-aware footprint (Eq. 1 skips a pixel where o exp(-q/2) < 1/255,
+ * q = d^T conic d): per tile row of the rectangle, only the tile columns
+ * whose pixel centres meet the ellipse q <= t, t = 1.02 x 2 ln(255 o) +
+ * 0.05 (o = alpha[i], or 1 when alpha is NULL; no tile when o < 1/255;
+ * near-singular Gaussians keep their rectangle), and ntiles counts those.
+ * Every dropped tile has alpha < 1/255 at each of its pixels, so the image
+ * is unchanged. hyrf_bin_sort must then be given mean2d and footprint.
  * ---------------------------------------------------------------------- */
 typedef struct {
   int32_t n;                 /* N (capacity of the V arrays) */
@@ -244,9 +252,11 @@ typedef struct {
   float* conic;              /* out [V][3] (a, b, c) of Sigma'^-1 */
   float* depth;              /* out [V] camera-space z */
   int32_t* rect;             /* out [V][4] (x0, y0, x1, y1) in tiles, half-open */
-  int32_t* ntiles;           /* out [V] (x1-x0)(y1-y0), 0 if empty */
+  int32_t* ntiles;           /* out [V] (x1-x0)(y1-y0), 0 if empty; the footprint's tile count with `footprint` */
   uint8_t* fp64_flag;        /* out [V], may be NULL */
   int32_t* status;
+  const float* alpha;        /* [V] opacity for the footprint; may be NULL (o = 1) */
+  float* footprint;          /* out [V][4] (Sigma'_xx, Sigma'_xy, Sigma'_yy, t), 16-byte aligned; NULL: no culling */
 } hyrf_project_args;
 
 size_t hyrf_project_workspace_size(const hyrf_project_args* a);
@@ -301,6 +311,11 @@ typedef struct {
    * (same camera and visible set); the call then skips its own depth sort
    * (the result is identical). NULL: sorted here. */
   const int32_t* depth_order;
+  /* Optional, together: mean2d [V][2] and footprint [V][4] from
+   * hyrf_project (with ntiles counted on the footprint); each rectangle row
+   * then yields only its footprint's tile columns. NULL: whole rectangles. */
+  const float* mean2d;
+  const float* footprint;
 } hyrf_bin_sort_args;
 
 /* hyrf_depth_order: the visible rows ordered by camera-space depth exactly

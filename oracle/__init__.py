@@ -340,22 +340,40 @@ def project(pos, scale, quat, cam):
 
 
 def project_f32(pos, scale, quat, cam, tile=TILE):
-    """FP32 replay of the projection's integer outputs: rect [n,4], ntiles [n],
-    depth (float32) [n], near-singular flag [n]."""
+    """FP32 replay of the projection's integer outputs: rect [n,4], ntiles [n]
+    (rectangle areas), depth (float32) [n], near-singular flag [n]."""
+    rect, ntiles, depth, flag, _, _ = _project_f32(pos, scale, quat, cam, tile, None, False)
+    return rect, ntiles, depth, flag
+
+
+def project_f32_footprint(pos, scale, quat, cam, alpha=None, tile=TILE):
+    """FP32 replay of the projection with the binning's opacity-aware
+    footprint (opacity alpha [n], or 1 when None): rect [n,4], ntiles [n]
+    (tiles of the footprint), depth [n], flag [n], mean2d (float32) [n,2],
+    footprint (float32) [n,4]."""
+    return _project_f32(pos, scale, quat, cam, tile, alpha, True)
+
+
+def _project_f32(pos, scale, quat, cam, tile, alpha, footprint):
     n = len(pos)
     pos = np.ascontiguousarray(pos, dtype=np.float32)
     scale = np.ascontiguousarray(scale, dtype=np.float32)
     quat = np.ascontiguousarray(quat, dtype=np.float32)
+    al = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float32)
     c = camera(cam)
     rect = np.zeros((n, 4), dtype=np.int32)
     ntiles = np.zeros(n, dtype=np.int32)
     depth = np.zeros(n, dtype=np.float32)
     flag = np.zeros(n, dtype=np.uint8)
-    rc = lib().orc_project_f32(n, _ptr(pos, _f32p), _ptr(scale, _f32p), _ptr(quat, _f32p),
-                               C.byref(c), tile, _ptr(rect, _i32p), _ptr(ntiles, _i32p),
-                               _ptr(depth, _f32p), _ptr(flag, _u8p))
+    mean2d = np.zeros((n, 2), dtype=np.float32) if footprint else None
+    foot = np.zeros((n, 4), dtype=np.float32) if footprint else None
+    rc = lib().orc_project_f32_fp(n, _ptr(pos, _f32p), _ptr(scale, _f32p), _ptr(quat, _f32p),
+                                  None if al is None else _ptr(al, _f32p), C.byref(c), tile,
+                                  _ptr(rect, _i32p), _ptr(ntiles, _i32p), _ptr(depth, _f32p),
+                                  _ptr(flag, _u8p), None if mean2d is None else _ptr(mean2d, _f32p),
+                                  None if foot is None else _ptr(foot, _f32p))
     assert rc == 0
-    return rect, ntiles, depth, flag
+    return rect, ntiles, depth, flag, mean2d, foot
 
 
 def project_backward(pos, scale, quat, cam, d_mean2d, d_conic):
@@ -374,8 +392,10 @@ def tiles_of(width, height, tile=TILE):
     return (width + tile - 1) // tile, (height + tile - 1) // tile
 
 
-def bin_sort(rect, depth_f32, tiles_x, tiles_y):
-    """Stable sort of (tile << 32 | depth bits) instance keys: keys, vals, ranges [tiles,2]."""
+def bin_sort(rect, depth_f32, tiles_x, tiles_y, mean2d=None, footprint=None, tile=TILE):
+    """Stable sort of (tile << 32 | depth bits) instance keys: keys, vals,
+    ranges [tiles,2]. With mean2d and footprint (project_f32_footprint) each
+    rectangle row yields only its footprint's tiles."""
     rect = np.ascontiguousarray(rect, dtype=np.int32)
     depth_f32 = np.ascontiguousarray(depth_f32, dtype=np.float32)
     n = len(rect)
@@ -386,9 +406,16 @@ def bin_sort(rect, depth_f32, tiles_x, tiles_y):
     keys = np.zeros(max(cap, 1), dtype=np.uint64)
     vals = np.zeros(max(cap, 1), dtype=np.int32)
     ranges = np.zeros((tiles_x * tiles_y, 2), dtype=np.int32)
-    K = lib().orc_bin_sort(n, _ptr(rect, _i32p), _ptr(depth_f32, _f32p), tiles_x, tiles_y, cap,
-                           _ptr(keys, _u64p), _ptr(vals, _i32p), _ptr(ranges, _i32p))
-    assert K == cap
+    if footprint is None:
+        m2 = fp = None
+    else:
+        m2 = np.ascontiguousarray(mean2d, dtype=np.float32)
+        fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    K = lib().orc_bin_sort_fp(n, _ptr(rect, _i32p), _ptr(depth_f32, _f32p),
+                              None if m2 is None else _ptr(m2, _f32p), None if fp is None else _ptr(fp, _f32p),
+                              tile, tiles_x, tiles_y, cap, _ptr(keys, _u64p), _ptr(vals, _i32p),
+                              _ptr(ranges, _i32p))
+    assert 0 <= K <= cap and (footprint is not None or K == cap)
     return keys[:K], vals[:K], ranges
 
 
@@ -584,9 +611,10 @@ def render(g, fields, cam, bg, tile=TILE):
                                              np.asarray(g.scale_e)[ids],
                                              np.asarray(g.color_e)[ids], cam, fields)
     mean2d, conic, depth = project(pos, scale, quat, cam)
-    rect, ntiles, depth32, flag = project_f32(pos32[ids], scale, quat, cam, tile)
+    # binning with the opacity-aware footprint, as the GPU path bins
+    rect, ntiles, depth32, flag, m32, foot = project_f32_footprint(pos32[ids], scale, quat, cam, alpha, tile)
     TX, TY = tiles_of(cam.width, cam.height, tile)
-    keys, vals, ranges = bin_sort(rect, depth32, TX, TY)
+    keys, vals, ranges = bin_sort(rect, depth32, TX, TY, m32, foot, tile)
     C_fg, T_final, n_contrib, margin = rasterize(cam.width, cam.height, ranges, vals, mean2d,
                                                  conic, alpha, color, tile)
     C_img, c_s = background(cam, fields, bg, C_fg, T_final)

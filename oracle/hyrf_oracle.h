@@ -179,6 +179,17 @@ int32_t orc_project_f32(int32_t n, const float* pos, const float* scale, const f
                         const orc_camera* cam, int32_t tile, int32_t* rect, int32_t* ntiles,
                         float* depth, uint8_t* flag);
 
+/* As orc_project_f32, with the binning's opacity-aware footprint: with foot
+ * given, ntiles counts only the tiles of the rectangle whose pixel centres
+ * meet the ellipse q <= t (q = d^T Sigma'^-1 d, t = 1.02 x 2 ln(255 o) +
+ * 0.05, o = alpha[i] or 1 when alpha is NULL; no footprint when o < 1/255;
+ * near-singular Gaussians keep their rectangle, t = +inf), and foot[n][4] =
+ * (Sigma'_xx, Sigma'_xy, Sigma'_yy, t) in FP32; mean2d[n][2] (may be NULL)
+ * receives the FP32 pixel position. */
+int32_t orc_project_f32_fp(int32_t n, const float* pos, const float* scale, const float* quat,
+                           const float* alpha, const orc_camera* cam, int32_t tile, int32_t* rect,
+                           int32_t* ntiles, float* depth, uint8_t* flag, float* mean2d, float* foot);
+
 int32_t orc_project_backward(int32_t n, const double* pos, const double* scale,
                              const double* quat, const orc_camera* cam,
                              const double* d_mean2d, const double* d_conic,
@@ -191,6 +202,13 @@ int32_t orc_project_backward(int32_t n, const double* pos, const double* scale,
 int64_t orc_bin_sort(int32_t n, const int32_t* rect, const float* depth, int32_t tiles_x,
                      int32_t tiles_y, int64_t cap, uint64_t* keys, int32_t* vals,
                      int32_t* ranges);
+
+/* As orc_bin_sort, with the instances of each rectangle row limited to the
+ * footprint's tile columns (mean2d and foot from orc_project_f32_fp; NULL
+ * foot: whole rectangles). */
+int64_t orc_bin_sort_fp(int32_t n, const int32_t* rect, const float* depth, const float* mean2d,
+                        const float* foot, int32_t tile, int32_t tiles_x, int32_t tiles_y, int64_t cap,
+                        uint64_t* keys, int32_t* vals, int32_t* ranges);
 
 /* ---------------- stage 5: front-to-back compositing (Eq. 1) ------------ */
 /* C_fg[H][W][3], T_final[H][W], n_contrib[H][W] (list position of the last

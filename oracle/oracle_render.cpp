@@ -331,9 +331,88 @@ int32_t orc_project(int32_t n, const double* pos, const double* scale, const dou
 
 // FP32 replay of the integer outputs of the projection. The operation order
 // below is the specification the GPU kernel follows.
+// ---- opacity-aware footprint (FP32 replay of the binning's culling) ----
+//
+// Eq. 1 skips a pixel where alpha = o exp(-q / 2) < 1/255 with
+// q = d^T Sigma'^-1 d, so a Gaussian shows nowhere with q > 2 ln(255 o).
+// The footprint keeps, per tile row of the rectangle, the tile columns
+// whose pixel-centre box meets the ellipse q <= t with t = 1.02 x 2 ln(255 o)
+// + 0.05 (a margin far above FP32 rounding). Written with plain FP32 + - * /
+// sqrt in a fixed order (no fused multiply-add) so the GPU's binning takes
+// the same decisions bit for bit.
+
+// t for opacity o (-1: no footprint at all, o < 1/255). ln x by the
+// exponent and the series ln m = 2 atanh(s), s = (m - 1) / (m + 1), to s^9
+// (Abramowitz & Stegun 4.1.27; truncation below 2e-6 for m in [1, 2)).
+static float fp_qlimit(float o) {
+  if (!(o >= 1.0f / 255.0f)) return -1.0f;
+  const float x = 255.0f * o;  // >= 1
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  const int e = (int)((u >> 23) & 0xffu) - 127;
+  const uint32_t um = (u & 0x7fffffu) | 0x3f800000u;
+  float m;
+  std::memcpy(&m, &um, 4);  // x = m 2^e, m in [1, 2)
+  const float s = (m - 1.0f) / (m + 1.0f);
+  const float s2 = s * s;
+  float pz = 1.0f / 9.0f;
+  pz = pz * s2 + 1.0f / 7.0f;
+  pz = pz * s2 + 1.0f / 5.0f;
+  pz = pz * s2 + 1.0f / 3.0f;
+  pz = pz * s2 + 1.0f;
+  const float ln = (float)e * 0.693147180559945f + 2.0f * s * pz;
+  return 1.02f * (2.0f * ln) + 0.05f;
+}
+
+// Tile columns [*tx0, *tx1) of tile row ty (within [cx0, cx1)) whose pixel
+// centres (16 tx + 0.5 ... 16 tx + 15.5) meet the ellipse
+// {(u, v) + d : d^T Sigma'^-1 d <= t}, Sigma' = [[a, b], [b, c]]: the ellipse
+// cut to the row's pixel-centre strip spans x in [u + xmin, u + xmax], where
+// the boundary at height dy is x = (b / c) dy +- sqrt((a - b^2 / c)(t - dy^2 / c))
+// and the extremes +-sqrt(t a) sit at dy = +-b sqrt(t / a). t = +inf: the
+// whole row of the rectangle.
+static void fp_row_span(float u, float v, float a, float b, float c, float t, int ty, int tile, int cx0,
+                        int cx1, int* tx0, int* tx1) {
+  *tx0 = *tx1 = cx0;
+  if (!(t >= 0.0f)) return;
+  if (std::isinf(t)) {
+    *tx1 = cx1;
+    return;
+  }
+  const float tw = (float)tile;
+  const float Y0 = (float)(ty * tile) + 0.5f, Y1 = Y0 + (tw - 1.0f);
+  const float dy0 = Y0 - v, dy1 = Y1 - v;
+  const float hy = std::sqrt(t * c);
+  const float ya = std::fmax(dy0, -hy), yb = std::fmin(dy1, hy);
+  if (!(ya <= yb)) return;
+  const float k = b / c;
+  const float mm = std::fmax(a - b * k, 0.0f);
+  const float wa = std::sqrt(std::fmax(mm * (t - ya * ya / c), 0.0f));
+  const float wb = std::sqrt(std::fmax(mm * (t - yb * yb / c), 0.0f));
+  const float hx = std::sqrt(t * a);
+  const float yr = b * std::sqrt(t / a);
+  const float xmax = (yr >= ya && yr <= yb) ? hx : std::fmax(k * ya + wa, k * yb + wb);
+  const float xmin = (-yr >= ya && -yr <= yb) ? -hx : std::fmin(k * ya - wa, k * yb - wb);
+  float f0 = std::ceil(((u + xmin) - (tw - 0.5f)) / tw);
+  float f1 = std::floor(((u + xmax) - 0.5f) / tw) + 1.0f;
+  f0 = std::fmin(std::fmax(f0, (float)cx0), (float)cx1);
+  f1 = std::fmin(std::fmax(f1, (float)cx0), (float)cx1);
+  if (f1 > f0) {
+    *tx0 = (int)f0;
+    *tx1 = (int)f1;
+  }
+}
+
 int32_t orc_project_f32(int32_t n, const float* pos, const float* scale, const float* quat,
                         const orc_camera* cam, int32_t tile, int32_t* rect, int32_t* ntiles,
                         float* depth, uint8_t* flag) {
+  return orc_project_f32_fp(n, pos, scale, quat, nullptr, cam, tile, rect, ntiles, depth, flag, nullptr,
+                            nullptr);
+}
+
+int32_t orc_project_f32_fp(int32_t n, const float* pos, const float* scale, const float* quat,
+                           const float* alpha, const orc_camera* cam, int32_t tile, int32_t* rect,
+                           int32_t* ntiles, float* depth, uint8_t* flag, float* mean2d, float* foot) {
   if (n < 0 || !cam || tile <= 0) return -1;
   CamF c = cam_f32(*cam);
   const int TX = (c.W + tile - 1) / tile, TY = (c.H + tile - 1) / tile;
@@ -403,7 +482,28 @@ int32_t orc_project_f32(int32_t n, const float* pos, const float* scale, const f
     rect[4 * i + 3] = iy1;
     ntiles[i] = (ix1 > ix0 && iy1 > iy0) ? (ix1 - ix0) * (iy1 - iy0) : 0;
     depth[i] = z;
-    flag[i] = std::fabs(det) < 1e-2f * a * cc ? 1 : 0;
+    const bool near_singular = std::fabs(det) < 1e-2f * a * cc;
+    flag[i] = near_singular ? 1 : 0;
+    if (foot) {
+      // the footprint; near-singular Gaussians keep their whole rectangle
+      // (their conic comes from an FP64 recomputation of Sigma')
+      const float t = near_singular ? INFINITY : fp_qlimit(alpha ? alpha[i] : 1.0f);
+      foot[4 * i] = a;
+      foot[4 * i + 1] = b;
+      foot[4 * i + 2] = cc;
+      foot[4 * i + 3] = t;
+      int cnt = 0;
+      for (int ty = iy0; ty < iy1; ++ty) {
+        int t0, t1;
+        fp_row_span(u, v, a, b, cc, t, ty, tile, ix0, ix1, &t0, &t1);
+        cnt += t1 - t0;
+      }
+      ntiles[i] = cnt;
+    }
+    if (mean2d) {
+      mean2d[2 * i] = u;
+      mean2d[2 * i + 1] = v;
+    }
   }
   return 0;
 }
@@ -493,16 +593,26 @@ int32_t orc_project_backward(int32_t n, const double* pos, const double* scale,
 int64_t orc_bin_sort(int32_t n, const int32_t* rect, const float* depth, int32_t tiles_x,
                      int32_t tiles_y, int64_t cap, uint64_t* keys, int32_t* vals,
                      int32_t* ranges) {
-  if (n < 0 || tiles_x <= 0 || tiles_y <= 0) return -2;
+  return orc_bin_sort_fp(n, rect, depth, nullptr, nullptr, 16, tiles_x, tiles_y, cap, keys, vals, ranges);
+}
+
+int64_t orc_bin_sort_fp(int32_t n, const int32_t* rect, const float* depth, const float* mean2d,
+                        const float* foot, int32_t tile, int32_t tiles_x, int32_t tiles_y, int64_t cap,
+                        uint64_t* keys, int32_t* vals, int32_t* ranges) {
+  if (n < 0 || tiles_x <= 0 || tiles_y <= 0 || tile <= 0) return -2;
   std::vector<std::pair<uint64_t, int32_t>> inst;
   for (int g = 0; g < n; ++g) {
     const int32_t* r = rect + 4 * g;
     if (!(r[2] > r[0] && r[3] > r[1])) continue;
     uint32_t bits;
     std::memcpy(&bits, depth + g, 4);
-    for (int ty = r[1]; ty < r[3]; ++ty)
-      for (int tx = r[0]; tx < r[2]; ++tx)
-        inst.push_back({((uint64_t)(ty * tiles_x + tx) << 32) | bits, g});
+    for (int ty = r[1]; ty < r[3]; ++ty) {
+      int t0 = r[0], t1 = r[2];
+      if (foot)
+        fp_row_span(mean2d[2 * g], mean2d[2 * g + 1], foot[4 * g], foot[4 * g + 1], foot[4 * g + 2],
+                    foot[4 * g + 3], ty, tile, r[0], r[2], &t0, &t1);
+      for (int tx = t0; tx < t1; ++tx) inst.push_back({((uint64_t)(ty * tiles_x + tx) << 32) | bits, g});
+    }
   }
   std::stable_sort(inst.begin(), inst.end(),
                    [](const std::pair<uint64_t, int32_t>& A, const std::pair<uint64_t, int32_t>& B) {

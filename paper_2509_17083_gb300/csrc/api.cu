@@ -18,7 +18,7 @@ hyrf_status launch_precull(const CamDev& cam, const float* pos, int n, int32_t* 
 hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int32_t* vis_ids,
                            const int32_t* n_vis, const float* scale, const float* quat, float* mean2d,
                            float* conic, float* depth, int32_t* rect, int32_t* ntiles, uint8_t* flag,
-                           int32_t* status, cudaStream_t s);
+                           int32_t* status, const float* alpha, float* footprint, cudaStream_t s);
 hyrf_status launch_project_bwd(const hyrf_project_backward_args& a, cudaStream_t s);
 hyrf_status launch_query_fwd(const hyrf_query_fields_args& a, const FieldsDev& F, void* ws, cudaStream_t s);
 size_t query_fwd_workspace_f32(const hyrf_fields& f, const FieldsDev& F, int n);
@@ -203,6 +203,8 @@ hyrf_status bin_sort_check(const hyrf_bin_sort_args* a) {
   if (!a->n_vis || !a->ranges || !a->n_instances) return HYRF_ERR_INVALID_ARG;
   if (a->n > 0 && (!a->rect || !a->ntiles || !a->depth)) return HYRF_ERR_INVALID_ARG;
   if (a->capacity > 0 && !a->vals) return HYRF_ERR_INVALID_ARG;
+  if ((a->mean2d == nullptr) != (a->footprint == nullptr)) return HYRF_ERR_INVALID_ARG;
+  if (a->footprint && !aligned(a->footprint, 16)) return HYRF_ERR_INVALID_ARG;
   return HYRF_OK;
 }
 }  // namespace hyrf
@@ -309,9 +311,10 @@ hyrf_status hyrf_project(const hyrf_project_args* a, void* ws, size_t ws_bytes, 
   if (a->n > 0 && (!a->pos || !a->vis_ids || !a->n_vis || !a->scale || !a->quat || !a->mean2d ||
                    !a->conic || !a->depth || !a->rect || !a->ntiles))
     return HYRF_ERR_INVALID_ARG;
+  if (a->footprint && !aligned(a->footprint, 16)) return HYRF_ERR_INVALID_ARG;
   return launch_project(to_dev(a->cam), a->n, a->pos, a->vis_ids, a->n_vis, a->scale, a->quat,
                         a->mean2d, a->conic, a->depth, a->rect, a->ntiles, a->fp64_flag, a->status,
-                        S(stream));
+                        a->alpha, a->footprint, S(stream));
 }
 
 size_t hyrf_project_backward_workspace_size(const hyrf_project_backward_args*) { return 0; }

@@ -1,0 +1,81 @@
+// Opacity-aware footprint of a projected Gaussian: the tiles of its
+// rectangle that it can show in. Eq. 1 skips a pixel where
+// alpha = o exp(-q / 2) < 1/255, q = d^T Sigma'^-1 d, so nothing of the
+// Gaussian shows where q > 2 ln(255 o). Per tile row of the rectangle, the
+// binning keeps the tile columns whose pixel-centre box meets the ellipse
+// q <= t, t = 1.02 x 2 ln(255 o) + 0.05 (the margin sits far above FP32
+// rounding, so every tile dropped has alpha well below 1/255 at each of its
+// pixels: the image is that of the whole rectangle).
+//
+// The projection counts these tiles (ntiles) and the instance expansion
+// emits them; both call the functions below, which use correctly rounded
+// FP32 operations in a fixed order (the _rn intrinsics are never fused into
+// multiply-adds, whatever the unit's compile flags), so their decisions
+// agree with each other and with the oracle's FP32 replay bit for bit.
+#pragma once
+#include "common.cuh"
+
+namespace hyrf {
+
+// t for opacity o; -1 when o < 1/255 (no footprint). ln x = e ln 2 + ln m
+// for x = m 2^e, m in [1, 2), and ln m = 2 atanh(s), s = (m - 1) / (m + 1),
+// by its series to s^9 (Abramowitz & Stegun 4.1.27; truncation < 2e-6).
+__device__ __forceinline__ float fp_qlimit(float o) {
+  if (!(o >= 1.0f / 255.0f)) return -1.0f;
+  const float x = __fmul_rn(255.0f, o);  // >= 1
+  const uint32_t u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xffu) - 127;
+  const float m = __uint_as_float((u & 0x7fffffu) | 0x3f800000u);
+  const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float s2 = __fmul_rn(s, s);
+  float pz = 1.0f / 9.0f;
+  pz = __fadd_rn(__fmul_rn(pz, s2), 1.0f / 7.0f);
+  pz = __fadd_rn(__fmul_rn(pz, s2), 1.0f / 5.0f);
+  pz = __fadd_rn(__fmul_rn(pz, s2), 1.0f / 3.0f);
+  pz = __fadd_rn(__fmul_rn(pz, s2), 1.0f);
+  const float ln = __fadd_rn(__fmul_rn((float)e, 0.693147180559945f), __fmul_rn(__fmul_rn(2.0f, s), pz));
+  return __fadd_rn(__fmul_rn(1.02f, __fmul_rn(2.0f, ln)), 0.05f);
+}
+
+// Tile columns [tx0, tx1) of tile row ty, within [cx0, cx1), whose pixel
+// centres (tile tx + 0.5 ... tile tx + tile - 0.5) meet the ellipse
+// {(u, v) + d : d^T Sigma'^-1 d <= t}, Sigma' = [[a, b], [b, c]]. Cut to
+// the row's pixel-centre strip, the ellipse spans x in [u + xmin, u + xmax]:
+// its boundary at height dy is x = (b / c) dy +- sqrt((a - b^2 / c)(t - dy^2 / c))
+// and its extremes +-sqrt(t a) lie at dy = +-b sqrt(t / a). t = +inf: the
+// whole row of the rectangle; t < 0: nothing.
+__device__ __forceinline__ void fp_row_span(float u, float v, float a, float b, float c, float t, int ty,
+                                            int tile, int cx0, int cx1, int& tx0, int& tx1) {
+  tx0 = tx1 = cx0;
+  if (!(t >= 0.0f)) return;
+  if (isinf(t)) {
+    tx1 = cx1;
+    return;
+  }
+  const float tw = (float)tile;
+  const float Y0 = __fadd_rn((float)(ty * tile), 0.5f);
+  const float Y1 = __fadd_rn(Y0, __fsub_rn(tw, 1.0f));
+  const float dy0 = __fsub_rn(Y0, v), dy1 = __fsub_rn(Y1, v);
+  const float hy = __fsqrt_rn(__fmul_rn(t, c));
+  const float ya = fmaxf(dy0, -hy), yb = fminf(dy1, hy);
+  if (!(ya <= yb)) return;
+  const float k = __fdiv_rn(b, c);
+  const float mm = fmaxf(__fsub_rn(a, __fmul_rn(b, k)), 0.0f);
+  const float wa = __fsqrt_rn(fmaxf(__fmul_rn(mm, __fsub_rn(t, __fdiv_rn(__fmul_rn(ya, ya), c))), 0.0f));
+  const float wb = __fsqrt_rn(fmaxf(__fmul_rn(mm, __fsub_rn(t, __fdiv_rn(__fmul_rn(yb, yb), c))), 0.0f));
+  const float hx = __fsqrt_rn(__fmul_rn(t, a));
+  const float yr = __fmul_rn(b, __fsqrt_rn(__fdiv_rn(t, a)));
+  const float kya = __fmul_rn(k, ya), kyb = __fmul_rn(k, yb);
+  const float xmax = (yr >= ya && yr <= yb) ? hx : fmaxf(__fadd_rn(kya, wa), __fadd_rn(kyb, wb));
+  const float xmin = (-yr >= ya && -yr <= yb) ? -hx : fminf(__fsub_rn(kya, wa), __fsub_rn(kyb, wb));
+  float f0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(u, xmin), __fsub_rn(tw, 0.5f)), tw));
+  float f1 = __fadd_rn(floorf(__fdiv_rn(__fsub_rn(__fadd_rn(u, xmax), 0.5f), tw)), 1.0f);
+  f0 = fminf(fmaxf(f0, (float)cx0), (float)cx1);
+  f1 = fminf(fmaxf(f1, (float)cx0), (float)cx1);
+  if (f1 > f0) {
+    tx0 = (int)f0;
+    tx1 = (int)f1;
+  }
+}
+
+}  // namespace hyrf

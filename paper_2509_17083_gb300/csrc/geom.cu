@@ -4,7 +4,7 @@
 // below is rounded on its own, in source order, so that visibility, tile
 // rectangles and depth keys are reproducible bit for bit. The operation
 // order is part of the library's contract.
-#include "common.cuh"
+#include "footprint.cuh"
 
 namespace hyrf {
 
@@ -121,6 +121,8 @@ struct ProjOut {
   int32_t* rect;
   int32_t* ntiles;
   uint8_t* flag;
+  const float* alpha;  // opacity for the footprint (NULL: 1)
+  float4* foot;        // footprint out (NULL: whole rectangles)
 };
 
 // FP64 recomputation of Sigma' and its inverse for near-singular Gaussians.
@@ -262,7 +264,20 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
     o.rect[4 * i + 1] = iy0;
     o.rect[4 * i + 2] = ix1;
     o.rect[4 * i + 3] = iy1;
-    o.ntiles[i] = (ix1 > ix0 && iy1 > iy0) ? (ix1 - ix0) * (iy1 - iy0) : 0;
+    int nt = (ix1 > ix0 && iy1 > iy0) ? (ix1 - ix0) * (iy1 - iy0) : 0;
+    if (o.foot) {
+      // the footprint (footprint.cuh); near-singular Gaussians keep their
+      // rectangle (their conic comes from an FP64 recomputation of Sigma')
+      const float t = near_singular ? INFINITY : fp_qlimit(o.alpha ? o.alpha[i] : 1.0f);
+      o.foot[i] = make_float4(a, b, cc, t);
+      nt = 0;
+      for (int ty = iy0; ty < iy1; ++ty) {
+        int t0, t1;
+        fp_row_span(u, v, a, b, cc, t, ty, kTile, ix0, ix1, t0, t1);
+        nt += t1 - t0;
+      }
+    }
+    o.ntiles[i] = nt;
     if (o.flag) o.flag[i] = near_singular ? 1 : 0;
   }
 }
@@ -333,10 +348,10 @@ hyrf_status launch_depth_of(const CamDev& cam, int n, const float* pos, const in
 hyrf_status launch_project(const CamDev& cam, int n, const float* pos, const int32_t* vis_ids,
                            const int32_t* n_vis, const float* scale, const float* quat, float* mean2d,
                            float* conic, float* depth, int32_t* rect, int32_t* ntiles, uint8_t* flag,
-                           int32_t* status, cudaStream_t s) {
+                           int32_t* status, const float* alpha, float* footprint, cudaStream_t s) {
   if (n == 0) return HYRF_OK;
   const int TX = (cam.W + kTile - 1) / kTile, TY = (cam.H + kTile - 1) / kTile;
-  ProjOut o{mean2d, conic, depth, rect, ntiles, flag};
+  ProjOut o{mean2d, conic, depth, rect, ntiles, flag, alpha, reinterpret_cast<float4*>(footprint)};
   int blocks = (n + 255) / 256;
   blocks = blocks < num_sms() * 8 ? blocks : num_sms() * 8;
   HYRF_LAUNCH("k_project", s,

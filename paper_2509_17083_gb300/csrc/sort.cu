@@ -7,7 +7,7 @@
 // the instances (split evenly over the passes). Every pass is
 // reduce-then-scan (histogram, per-digit column scan, stable scatter), so
 // no kernel waits on another CTA.
-#include "common.cuh"
+#include "footprint.cuh"
 
 namespace hyrf {
 
@@ -369,7 +369,9 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
                                                 const uint32_t* __restrict__ off,
                                                 const int32_t* __restrict__ k_ptr, int cap_k, int TX,
                                                 uint32_t* __restrict__ tile_keys,
-                                                int32_t* __restrict__ tile_vals) {
+                                                int32_t* __restrict__ tile_vals,
+                                                const float2* __restrict__ mean2d,
+                                                const float4* __restrict__ foot) {
   __shared__ uint32_t soff[kExpandSlice + 1];
   __shared__ int32_t sid[kExpandSlice];
   __shared__ int range[2];
@@ -407,6 +409,26 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
     const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2);
     const int wdt = x1 - x0;
     if (wdt <= 0) continue;  // rect inconsistent with ntiles: nothing sensible to emit
+    if (foot) {
+      // r-th tile of the footprint: walk its rows (footprint.cuh), the same
+      // spans the projection counted
+      const int y1 = __ldg(rect + 4 * g + 3);
+      const float2 m = mean2d[g];
+      const float4 f = foot[g];
+      uint32_t key = (uint32_t)(y0 * TX + x0);  // (only if ntiles disagrees with the spans: a tile of the rectangle)
+      for (int ty = y0; ty < y1; ++ty) {
+        int t0, t1;
+        fp_row_span(m.x, m.y, f.x, f.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
+        if (r < t1 - t0) {
+          key = (uint32_t)(ty * TX + t0 + r);
+          break;
+        }
+        r -= t1 - t0;
+      }
+      tile_keys[e] = key;
+      tile_vals[e] = g;
+      continue;
+    }
     tile_keys[e] = (uint32_t)((y0 + r / wdt) * TX + x0 + r % wdt);
     tile_vals[e] = g;
   }
@@ -588,7 +610,8 @@ hyrf_status launch_bin_sort(const hyrf_bin_sort_args& a, void* ws, cudaStream_t 
   const int64_t xb = (cap + kExpandItems - 1) / kExpandItems;
   HYRF_LAUNCH("k_expand", s,
               k_expand<<<(int)(xb < 0x7fffffff ? xb : 0x7fffffff), 256, 0, s>>>(
-                  a.rect, ord, a.n_vis, n, w.off, a.n_instances, capi, a.tiles_x, emit_k, emit_v));
+                  a.rect, ord, a.n_vis, n, w.off, a.n_instances, capi, a.tiles_x, emit_k, emit_v,
+                  reinterpret_cast<const float2*>(a.mean2d), reinterpret_cast<const float4*>(a.footprint)));
   // 3. stable sort of the instances on their tile bits
   st = radix_sort(w.tk_a, a.vals, w.tk_b, w.tv_b, a.n_instances, capi, tbits, w.hist, w.totals, s,
                   "k_radix_scatter<tile>");

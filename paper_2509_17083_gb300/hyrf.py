@@ -81,7 +81,7 @@ class hyrf_project_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("pos", _vp), ("vis_ids", _vp), ("n_vis", _vp), ("scale", _vp),
                 ("quat", _vp), ("cam", hyrf_camera), ("tile", C.c_int32), ("mean2d", _vp),
                 ("conic", _vp), ("depth", _vp), ("rect", _vp), ("ntiles", _vp),
-                ("fp64_flag", _vp), ("status", _vp)]
+                ("fp64_flag", _vp), ("status", _vp), ("alpha", _vp), ("footprint", _vp)]
 
 
 class hyrf_project_backward_args(C.Structure):
@@ -94,7 +94,7 @@ class hyrf_bin_sort_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_vis", _vp), ("rect", _vp), ("ntiles", _vp), ("depth", _vp),
                 ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("capacity", C.c_int64),
                 ("keys", _vp), ("vals", _vp), ("ranges", _vp), ("n_instances", _vp),
-                ("status", _vp), ("depth_order", _vp)]
+                ("status", _vp), ("depth_order", _vp), ("mean2d", _vp), ("footprint", _vp)]
 
 
 class hyrf_depth_order_args(C.Structure):

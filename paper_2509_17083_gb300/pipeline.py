@@ -198,6 +198,9 @@ class ViewRenderer:
         self.alpha, self.scale, self.quat, self.color = z(n), z(n, 3), z(n, 4), z(n, 3)
         self.mean2d, self.conic, self.depth = z(n, 2), z(n, 3), z(n)
         self.rect, self.ntiles = z(n, 4, dt=i32), z(n, dt=i32)
+        # opacity-aware footprint of each projected Gaussian (hyrf_project):
+        # the binning keeps only the tiles it can show in
+        self.footprint = z(max(n, 1), 4)
         self.flag = z(max(n, 1), dt=torch.uint8)
         self.ranges = z(self.TX * self.TY, 2, dt=i32)
         # the compositing passes take the tiles in this order: index order at
@@ -353,7 +356,8 @@ class ViewRenderer:
         H.hyrf_project(ws=self.ws["p"], n=m.n, pos=m.pos, vis_ids=self.vis_ids, n_vis=self.n_vis,
                        scale=self.scale, quat=self.quat, cam=self.ccam, tile=H.TILE,
                        mean2d=self.mean2d, conic=self.conic, depth=self.depth, rect=self.rect,
-                       ntiles=self.ntiles, fp64_flag=self.flag, status=self.status)
+                       ntiles=self.ntiles, fp64_flag=self.flag, status=self.status, alpha=self.alpha,
+                       footprint=self.footprint)
 
     def bin_sort(self, want_keys=True):
         """Tile binning; takes the side stream's depth order when forward_fields
@@ -367,7 +371,7 @@ class ViewRenderer:
                         ntiles=self.ntiles, depth=self.depth, tiles_x=self.TX, tiles_y=self.TY,
                         capacity=self.capacity, keys=self.keys if want_keys else None,
                         vals=self.vals, ranges=self.ranges, n_instances=self.n_inst,
-                        status=self.status, depth_order=order)
+                        status=self.status, depth_order=order, mean2d=self.mean2d, footprint=self.footprint)
 
     def loss_fn(self, target, grad=True):
         H.hyrf_loss(ws=self.ws["l"], width=self.W, height=self.H, C=self.C, target=target,

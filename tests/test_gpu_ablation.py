@@ -119,11 +119,13 @@ def test_no_precull_queries_every_gaussian_and_projection_drops_the_rest():
     rng = np.random.default_rng(8)
     s = np.exp(rng.uniform(-5, -2, (n, 3))).astype(np.float32)
     q = synth.random_quats(rng, n)
+    op = (1.0 / (1.0 + np.exp(-rng.standard_normal(n)))).astype(np.float32)
     r.scale[:n].copy_(torch.tensor(s, device="cuda"))
     r.quat[:n].copy_(torch.tensor(q, device="cuda"))
+    r.alpha[:n].copy_(torch.tensor(op, device="cuda"))
     r.project()
     torch.cuda.synchronize()
-    rect, ntiles, depth, flag = oracle.project_f32(w.gaussians.pos, s, q, cam)
+    rect, ntiles, depth, flag, _, _ = oracle.project_f32_footprint(w.gaussians.pos, s, q, cam, op)
     assert np.array_equal(np_(r.rect)[:n], rect) and np.array_equal(np_(r.ntiles)[:n], ntiles)
     behind = depth <= cam.z_near
     assert behind.sum() > n // 4 and (ntiles[behind] == 0).all()

@@ -66,11 +66,13 @@ def test_config5_degenerate_projection_and_sort_bit_exact(scene):
     pos, s, q, deg_rows = _geometry(w, ids)
     assert len(deg_rows) > 10_000
     nv = len(ids)
-    rect, ntiles, depth, flag = oracle.project_f32(pos, s, q, cam)
+    op = (1.0 / (1.0 + np.exp(-1.5 * np.random.default_rng(61).standard_normal(nv)))).astype(np.float32)
+    rect, ntiles, depth, flag, m2, foot = oracle.project_f32_footprint(pos, s, q, cam, op)
     if int(ntiles.sum()) > r.capacity:
         r.set_capacity(int(ntiles.sum()) + 4096)
     r.scale[:nv].copy_(cuda_f32(s))
     r.quat[:nv].copy_(cuda_f32(q))
+    r.alpha[:nv].copy_(cuda_f32(op))
     r.status.zero_()
     r.project()
     r.bin_sort(want_keys=True)
@@ -88,8 +90,9 @@ def test_config5_degenerate_projection_and_sort_bit_exact(scene):
     cg = np_(r.conic)[:nv].astype(np.float64)
     err = (np.abs(cg - conic) / np.abs(conic).max(1, keepdims=True)).max(1)
     assert err[f].max() < 1e-5, err[f].max()
+    assert np.array_equal(np_(r.footprint)[:nv].view(np.uint32), foot.view(np.uint32))
     TX, TY = oracle.tiles_of(cam.width, cam.height)
-    keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY)
+    keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY, m2, foot)
     K = len(keys)
     assert st == 0
     assert int(r.n_inst.item()) == K

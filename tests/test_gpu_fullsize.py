@@ -69,25 +69,34 @@ def _stage_geometry(w, ids):
     return w.gaussians.pos[ids].astype(np.float32), s, q
 
 
+def _stage_opacity(nv):
+    """Seeded opacities for the footprint (sigma of N(0, 1.5^2) logits)."""
+    rng = np.random.default_rng(20)
+    return (1.0 / (1.0 + np.exp(-1.5 * rng.standard_normal(nv)))).astype(np.float32)
+
+
 def test_fullsize_project_and_bin_sort_bit_exact(scene):
     w, m, r, ids = scene
     cam = w.cams[0]
     pos, s, q = _stage_geometry(w, ids)
     nv = len(ids)
+    op = _stage_opacity(nv)
     r.scale[:nv].copy_(cuda_f32(s))
     r.quat[:nv].copy_(cuda_f32(q))
+    r.alpha[:nv].copy_(cuda_f32(op))
     r.status.zero_()
     r.project()
     r.bin_sort(want_keys=True)
     torch.cuda.synchronize()
     assert H.read_status(r.status) == 0
-    rect, ntiles, depth, flag = oracle.project_f32(pos, s, q, cam)
+    rect, ntiles, depth, flag, m2, foot = oracle.project_f32_footprint(pos, s, q, cam, op)
     assert np.array_equal(np_(r.rect)[:nv], rect)
     assert np.array_equal(np_(r.ntiles)[:nv], ntiles)
     assert np.array_equal(np_(r.depth)[:nv].view(np.uint32), depth.view(np.uint32))
     assert np.array_equal(np_(r.flag)[:nv], flag)
+    assert np.array_equal(np_(r.footprint)[:nv].view(np.uint32), foot.view(np.uint32))
     TX, TY = oracle.tiles_of(cam.width, cam.height)
-    keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY)
+    keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY, m2, foot)
     K = len(keys)
     assert int(r.n_inst.item()) == K and K > 5_000_000
     assert np.array_equal(np_(r.keys)[:K].view(np.uint64), keys)

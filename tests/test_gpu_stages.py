@@ -114,6 +114,57 @@ def test_project_bit_exact_integers_and_fp64_floats(lib):
     assert err[flag == 1].max() < 1e-5, err[flag == 1].max()
 
 
+def test_project_footprint_and_bin_sort_bit_exact(lib):
+    """The binning's opacity-aware footprint: the projection's tile counts
+    and footprint values, and the instance lists hyrf_bin_sort emits from
+    them, bit for bit against the oracle's FP32 replay."""
+    rng = np.random.default_rng(14)
+    cam = synth.look_at([0.4, -0.3, -1.0], [0, 0, 4], 333, 211, 65.0)
+    n = 20000
+    pos, s, q = _proj_inputs(rng, n, cam)
+    s[:, 0] *= np.exp(rng.uniform(0.0, 2.5, n)).astype(np.float32)  # anisotropic
+    op = (1.0 / (1.0 + np.exp(-1.5 * rng.standard_normal(n)))).astype(np.float32)
+    op[:50] = 1.0 / 300.0  # below 1/255: no footprint
+    dev = "cuda"
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    nv = torch.tensor([n], dtype=torch.int32, device=dev)
+    out = dict(mean2d=torch.zeros(n, 2, device=dev), conic=torch.zeros(n, 3, device=dev),
+               depth=torch.zeros(n, device=dev), rect=torch.zeros(n, 4, dtype=torch.int32, device=dev),
+               ntiles=torch.zeros(n, dtype=torch.int32, device=dev),
+               fp64_flag=torch.zeros(n, dtype=torch.uint8, device=dev), footprint=torch.zeros(n, 4, device=dev))
+    H.hyrf_project(n=n, pos=cuda_f32(pos), vis_ids=ids, n_vis=nv, scale=cuda_f32(s), quat=cuda_f32(q),
+                   cam=H.camera(cam), tile=16, alpha=cuda_f32(op), **out)
+    torch.cuda.synchronize()
+    rect, ntiles, depth, flag, m2, foot = oracle.project_f32_footprint(pos, s, q, cam, op)
+    assert np.array_equal(np_(out["rect"]), rect)
+    assert np.array_equal(np_(out["ntiles"]), ntiles)
+    assert np.array_equal(np_(out["fp64_flag"]), flag)
+    assert np.array_equal(np_(out["footprint"]).view(np.uint32), foot.view(np.uint32))
+    assert np.array_equal(np_(out["mean2d"]).view(np.uint32), m2.view(np.uint32))
+    area = np.where(rect[:, 2] > rect[:, 0], (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]), 0)
+    assert ntiles.sum() < 0.9 * area.sum() and (ntiles[:50] == 0).all()
+    TX, TY = oracle.tiles_of(cam.width, cam.height)
+    keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY, m2, foot)
+    K = len(keys)
+    got = dict(keys=torch.zeros(K + 8, dtype=torch.int64, device=dev),
+               vals=torch.zeros(K + 8, dtype=torch.int32, device=dev),
+               ranges=torch.zeros(TX * TY, 2, dtype=torch.int32, device=dev),
+               n_instances=torch.zeros(1, dtype=torch.int32, device=dev),
+               status=torch.zeros(1, dtype=torch.int32, device=dev))
+    H.hyrf_bin_sort(n=n, n_vis=nv, rect=out["rect"], ntiles=out["ntiles"], depth=out["depth"], tiles_x=TX,
+                    tiles_y=TY, capacity=K + 8, mean2d=out["mean2d"], footprint=out["footprint"], **got)
+    torch.cuda.synchronize()
+    assert H.read_status(got["status"]) == 0
+    assert int(got["n_instances"].item()) == K
+    assert np.array_equal(np_(got["keys"])[:K].view(np.uint64), keys)
+    assert np.array_equal(np_(got["vals"])[:K], vals)
+    assert np.array_equal(np_(got["ranges"]), ranges)
+    # mean2d and footprint go together
+    with pytest.raises(H.HyrfError):
+        H.hyrf_bin_sort(n=n, n_vis=nv, rect=out["rect"], ntiles=out["ntiles"], depth=out["depth"], tiles_x=TX,
+                        tiles_y=TY, capacity=K + 8, footprint=out["footprint"], **got)
+
+
 def test_project_backward_matches_oracle(lib):
     rng = np.random.default_rng(12)
     cam = synth.look_at([0.4, -0.3, -1.0], [0, 0, 4], 160, 120, 65.0)
