@@ -287,7 +287,8 @@ hyrf_status hyrf_project_backward(const hyrf_project_backward_args* a, void* wor
 
 /* ------------------------------------------------------------------------
  * hyrf_bin_sort: tile instances of every visible Gaussian (one per tile of
- * its rectangle, emitted in (Gaussian, tile row-major) order), ordered by
+ * its rectangle, or of its footprint when mean2d and footprint are given
+ * (see hyrf_project), emitted in (Gaussian, tile row-major) order), ordered by
  * the 64-bit key (tile << 32) | float_bits(depth) with a stable LSD radix
  * sort, and the per-tile [start, end) ranges. The 32 depth bits are sorted
  * on the V Gaussians before the instances are emitted (identical result to

@@ -486,8 +486,10 @@ int32_t orc_project_f32_fp(int32_t n, const float* pos, const float* scale, cons
     flag[i] = near_singular ? 1 : 0;
     if (foot) {
       // the footprint; near-singular Gaussians keep their whole rectangle
-      // (their conic comes from an FP64 recomputation of Sigma')
-      const float t = near_singular ? INFINITY : fp_qlimit(alpha ? alpha[i] : 1.0f);
+      // (their conic comes from an FP64 recomputation of Sigma') unless
+      // o < 1/255, where no pixel shows them at all
+      float t = fp_qlimit(alpha ? alpha[i] : 1.0f);
+      if (near_singular && t >= 0.0f) t = INFINITY;
       foot[4 * i] = a;
       foot[4 * i + 1] = b;
       foot[4 * i + 2] = cc;

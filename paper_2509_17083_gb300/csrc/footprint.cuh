@@ -37,14 +37,33 @@ __device__ __forceinline__ float fp_qlimit(float o) {
   return __fadd_rn(__fmul_rn(1.02f, __fmul_rn(2.0f, ln)), 0.05f);
 }
 
+// Per-Gaussian constants of the row spans: the ellipse's half-height
+// hy = sqrt(t c), the slope k = b / c of its centre line, mm = a - b k, its
+// half-width hx = sqrt(t a) and the height yr = b sqrt(t / a) of its
+// rightmost point.
+struct FootRows {
+  float hy, k, mm, hx, yr;
+};
+
+__device__ __forceinline__ FootRows fp_rows(float a, float b, float c, float t) {
+  FootRows f;
+  f.hy = __fsqrt_rn(__fmul_rn(t, c));
+  f.k = __fdiv_rn(b, c);
+  f.mm = fmaxf(__fsub_rn(a, __fmul_rn(b, f.k)), 0.0f);
+  f.hx = __fsqrt_rn(__fmul_rn(t, a));
+  f.yr = __fmul_rn(b, __fsqrt_rn(__fdiv_rn(t, a)));
+  return f;
+}
+
 // Tile columns [tx0, tx1) of tile row ty, within [cx0, cx1), whose pixel
 // centres (tile tx + 0.5 ... tile tx + tile - 0.5) meet the ellipse
-// {(u, v) + d : d^T Sigma'^-1 d <= t}, Sigma' = [[a, b], [b, c]]. Cut to
-// the row's pixel-centre strip, the ellipse spans x in [u + xmin, u + xmax]:
-// its boundary at height dy is x = (b / c) dy +- sqrt((a - b^2 / c)(t - dy^2 / c))
-// and its extremes +-sqrt(t a) lie at dy = +-b sqrt(t / a). t = +inf: the
-// whole row of the rectangle; t < 0: nothing.
-__device__ __forceinline__ void fp_row_span(float u, float v, float a, float b, float c, float t, int ty,
+// {(u, v) + d : d^T Sigma'^-1 d <= t}, Sigma' = [[a, b], [b, c]] (f from
+// fp_rows). Cut to the row's pixel-centre strip, the ellipse spans x in
+// [u + xmin, u + xmax]: its boundary at height dy is
+// x = (b / c) dy +- sqrt((a - b^2 / c)(t - dy^2 / c)) and its extremes
+// +-sqrt(t a) lie at dy = +-b sqrt(t / a). t = +inf: the whole row of the
+// rectangle; t < 0: nothing.
+__device__ __forceinline__ void fp_row_span(const FootRows& f, float u, float v, float c, float t, int ty,
                                             int tile, int cx0, int cx1, int& tx0, int& tx1) {
   tx0 = tx1 = cx0;
   if (!(t >= 0.0f)) return;
@@ -56,18 +75,13 @@ __device__ __forceinline__ void fp_row_span(float u, float v, float a, float b, 
   const float Y0 = __fadd_rn((float)(ty * tile), 0.5f);
   const float Y1 = __fadd_rn(Y0, __fsub_rn(tw, 1.0f));
   const float dy0 = __fsub_rn(Y0, v), dy1 = __fsub_rn(Y1, v);
-  const float hy = __fsqrt_rn(__fmul_rn(t, c));
-  const float ya = fmaxf(dy0, -hy), yb = fminf(dy1, hy);
+  const float ya = fmaxf(dy0, -f.hy), yb = fminf(dy1, f.hy);
   if (!(ya <= yb)) return;
-  const float k = __fdiv_rn(b, c);
-  const float mm = fmaxf(__fsub_rn(a, __fmul_rn(b, k)), 0.0f);
-  const float wa = __fsqrt_rn(fmaxf(__fmul_rn(mm, __fsub_rn(t, __fdiv_rn(__fmul_rn(ya, ya), c))), 0.0f));
-  const float wb = __fsqrt_rn(fmaxf(__fmul_rn(mm, __fsub_rn(t, __fdiv_rn(__fmul_rn(yb, yb), c))), 0.0f));
-  const float hx = __fsqrt_rn(__fmul_rn(t, a));
-  const float yr = __fmul_rn(b, __fsqrt_rn(__fdiv_rn(t, a)));
-  const float kya = __fmul_rn(k, ya), kyb = __fmul_rn(k, yb);
-  const float xmax = (yr >= ya && yr <= yb) ? hx : fmaxf(__fadd_rn(kya, wa), __fadd_rn(kyb, wb));
-  const float xmin = (-yr >= ya && -yr <= yb) ? -hx : fminf(__fsub_rn(kya, wa), __fsub_rn(kyb, wb));
+  const float wa = __fsqrt_rn(fmaxf(__fmul_rn(f.mm, __fsub_rn(t, __fdiv_rn(__fmul_rn(ya, ya), c))), 0.0f));
+  const float wb = __fsqrt_rn(fmaxf(__fmul_rn(f.mm, __fsub_rn(t, __fdiv_rn(__fmul_rn(yb, yb), c))), 0.0f));
+  const float kya = __fmul_rn(f.k, ya), kyb = __fmul_rn(f.k, yb);
+  const float xmax = (f.yr >= ya && f.yr <= yb) ? f.hx : fmaxf(__fadd_rn(kya, wa), __fadd_rn(kyb, wb));
+  const float xmin = (-f.yr >= ya && -f.yr <= yb) ? -f.hx : fminf(__fsub_rn(kya, wa), __fsub_rn(kyb, wb));
   float f0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(u, xmin), __fsub_rn(tw, 0.5f)), tw));
   float f1 = __fadd_rn(floorf(__fdiv_rn(__fsub_rn(__fadd_rn(u, xmax), 0.5f), tw)), 1.0f);
   f0 = fminf(fmaxf(f0, (float)cx0), (float)cx1);

@@ -268,13 +268,17 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
     if (o.foot) {
       // the footprint (footprint.cuh); near-singular Gaussians keep their
       // rectangle (their conic comes from an FP64 recomputation of Sigma')
-      const float t = near_singular ? INFINITY : fp_qlimit(o.alpha ? o.alpha[i] : 1.0f);
+      float t = fp_qlimit(o.alpha ? o.alpha[i] : 1.0f);
+      if (near_singular && t >= 0.0f) t = INFINITY;
       o.foot[i] = make_float4(a, b, cc, t);
       nt = 0;
-      for (int ty = iy0; ty < iy1; ++ty) {
-        int t0, t1;
-        fp_row_span(u, v, a, b, cc, t, ty, kTile, ix0, ix1, t0, t1);
-        nt += t1 - t0;
+      if (t >= 0.0f) {
+        const FootRows fr = fp_rows(a, b, cc, t);
+        for (int ty = iy0; ty < iy1; ++ty) {
+          int t0, t1;
+          fp_row_span(fr, u, v, cc, t, ty, kTile, ix0, ix1, t0, t1);
+          nt += t1 - t0;
+        }
       }
     }
     o.ntiles[i] = nt;

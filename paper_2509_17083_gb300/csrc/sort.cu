@@ -394,6 +394,59 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
     if (t == 0) soff[L] = off[jhi + 1];
   }
   __syncthreads();
+  if (foot) {
+    // footprints: each thread takes whole Gaussians of the CTA's range, walks
+    // their rows once (footprint.cuh: the spans the projection counted) and
+    // stages their instances that fall in [e0, e1) in shared memory; the CTA
+    // then writes the range out coalesced
+    __shared__ uint32_t skey[kExpandItems];
+    __shared__ int32_t sval[kExpandItems];
+    for (int j = jlo + t; j <= jhi; j += 256) {
+      const int g = cached ? sid[j - jlo] : order[j];
+      const int base = (int)(cached ? soff[j - jlo] : off[j]);
+      const int end = (int)(cached ? soff[j - jlo + 1] : off[j + 1]);
+      const int lo = base > (int)e0 ? base : (int)e0, hi = end < e1 ? end : e1;
+      if (lo >= hi) continue;
+      int key = 0, gg = 0, k = base;  // safe values should the spans disagree with ntiles
+      if (g >= 0 && g < cap_n) {
+        const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2),
+                  y1 = __ldg(rect + 4 * g + 3);
+        const float2 m = mean2d[g];
+        const float4 f = foot[g];
+        gg = g;
+        key = y0 * TX + x0;
+        if (f.w >= 0.0f) {
+          const FootRows fr = fp_rows(f.x, f.y, f.z, f.w);
+          for (int ty = y0; ty < y1 && k < hi; ++ty) {
+            int t0, t1;
+            fp_row_span(fr, m.x, m.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
+            const int rowk = ty * TX;
+            // instances k .. k + (t1 - t0) - 1 of this row: skip to lo
+            int tx = t0;
+            if (k < lo) {
+              const int skip = lo - k < t1 - t0 ? lo - k : t1 - t0;
+              tx += skip;
+              k += skip;
+            }
+            for (; tx < t1 && k < hi; ++tx, ++k) {
+              skey[k - (int)e0] = (uint32_t)(rowk + tx);
+              sval[k - (int)e0] = g;
+            }
+          }
+        }
+      }
+      for (k = k > lo ? k : lo; k < hi; ++k) {
+        skey[k - (int)e0] = (uint32_t)key;
+        sval[k - (int)e0] = gg;
+      }
+    }
+    __syncthreads();
+    for (int e = (int)e0 + t; e < e1; e += 256) {
+      tile_keys[e] = skey[e - (int)e0];
+      tile_vals[e] = sval[e - (int)e0];
+    }
+    return;
+  }
   for (int e = (int)e0 + t; e < e1; e += 256) {
     int g, r;
     if (cached) {
@@ -409,26 +462,6 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
     const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2);
     const int wdt = x1 - x0;
     if (wdt <= 0) continue;  // rect inconsistent with ntiles: nothing sensible to emit
-    if (foot) {
-      // r-th tile of the footprint: walk its rows (footprint.cuh), the same
-      // spans the projection counted
-      const int y1 = __ldg(rect + 4 * g + 3);
-      const float2 m = mean2d[g];
-      const float4 f = foot[g];
-      uint32_t key = (uint32_t)(y0 * TX + x0);  // (only if ntiles disagrees with the spans: a tile of the rectangle)
-      for (int ty = y0; ty < y1; ++ty) {
-        int t0, t1;
-        fp_row_span(m.x, m.y, f.x, f.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
-        if (r < t1 - t0) {
-          key = (uint32_t)(ty * TX + t0 + r);
-          break;
-        }
-        r -= t1 - t0;
-      }
-      tile_keys[e] = key;
-      tile_vals[e] = g;
-      continue;
-    }
     tile_keys[e] = (uint32_t)((y0 + r / wdt) * TX + x0 + r % wdt);
     tile_vals[e] = g;
   }

@@ -112,12 +112,13 @@ def test_fullsize_rasterize_forward_and_reverse(scene):
     nv = len(ids)
     mean2d, conic, _ = oracle.project(pos.astype(np.float64), s.astype(np.float64), q.astype(np.float64),
                                       cam)
-    rect, _, depth, _ = oracle.project_f32(pos, s, q, cam)
-    TX, TY = oracle.tiles_of(W, H_)
-    _, vals, ranges = oracle.bin_sort(rect, depth, TX, TY)
     rng = np.random.default_rng(22)
     op = 1.0 / (1.0 + np.exp(-rng.standard_normal(nv)))
     col = rng.uniform(0.0, 1.0, (nv, 3))
+    # the instance lists the pipeline bins: opacity-aware footprints
+    rect, _, depth, _, fm2, foot = oracle.project_f32_footprint(pos, s, q, cam, op.astype(np.float32))
+    TX, TY = oracle.tiles_of(W, H_)
+    _, vals, ranges = oracle.bin_sort(rect, depth, TX, TY, fm2, foot)
     m2, c2, op, col = [np.asarray(x, np.float32) for x in (mean2d, conic, op, col)]
     # the renderer's buffers carry these stage inputs through the same calls
     r.mean2d[:nv].copy_(cuda_f32(m2))
