@@ -356,6 +356,45 @@ __device__ __forceinline__ void last_le2_cta(const uint32_t* __restrict__ a, int
 
 constexpr int kExpandItems = 2048;  // instances per CTA
 constexpr int kExpandSlice = 2048;  // sorted Gaussians cached per CTA
+constexpr int kExpandRows = 2048;   // footprint tile rows cached per CTA
+
+// Exclusive prefix sums of a[0, n) in place, n <= 2048, by a 256-thread CTA
+// (eight consecutive entries per thread); a[n] = the total, also returned.
+// Called by every thread of the CTA.
+__device__ __forceinline__ uint32_t cta_excl_scan2048(uint32_t* a, int n, uint32_t* wsum) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  uint32_t v[8], s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = 8 * t + q;
+    v[q] = i < n ? a[i] : 0u;
+    s += v[q];
+  }
+  uint32_t inc = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  uint32_t run = inc - s, tot = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t x = wsum[q];
+    if (q < w) run += x;
+    tot += x;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = 8 * t + q;
+    if (i < n) a[i] = run;
+    run += v[q];
+  }
+  if (t == 0) a[n] = tot;
+  __syncthreads();
+  return tot;
+}
 
 // Each CTA writes a fixed range of instances (balanced however unequal the
 // Gaussians' footprints are): it finds the sorted Gaussians that own its
@@ -395,19 +434,69 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
   }
   __syncthreads();
   if (foot) {
-    // footprints: each thread takes whole Gaussians of the CTA's range, walks
-    // their rows once (footprint.cuh: the spans the projection counted) and
-    // stages their instances that fall in [e0, e1) in shared memory; the CTA
-    // then writes the range out coalesced
-    __shared__ uint32_t skey[kExpandItems];
-    __shared__ int32_t sval[kExpandItems];
+    // footprints: one thread per (Gaussian, tile row) of the CTA's range
+    // computes the row's span (footprint.cuh: the spans the projection
+    // counted), a scan of the span lengths gives each row's first instance,
+    // then one thread per instance writes its key and value (coalesced).
+    __shared__ uint32_t rstart[kExpandRows + 1];
+    __shared__ uint32_t rtile[kExpandRows];
+    __shared__ int32_t rg[kExpandRows];
+    __shared__ uint32_t wsum[8];
+    if (cached) {
+      const uint32_t base0 = soff[0];
+      __syncthreads();
+      uint32_t* srow = soff;  // rows per Gaussian, then their prefix sums
+      for (int i = t; i < L; i += 256) {
+        const int g = sid[i];
+        int rows = 0;
+        if (g >= 0 && g < cap_n) rows = max(__ldg(rect + 4 * g + 3) - __ldg(rect + 4 * g + 1), 0);
+        srow[i] = (uint32_t)rows;
+      }
+      __syncthreads();
+      const uint32_t R = cta_excl_scan2048(srow, L, wsum);
+      if (R <= (uint32_t)kExpandRows) {  // CTA-uniform
+        for (int r = t; r < (int)R; r += 256) {
+          const int i = last_le(srow, 0, L - 1, (uint32_t)r);
+          const int g = sid[i];
+          const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2);
+          const int ty = y0 + (r - (int)srow[i]);
+          const float2 m = mean2d[g];
+          const float4 f = foot[g];
+          int t0 = x0, t1 = x0;
+          if (f.w >= 0.0f)
+            fp_row_span(fp_rows(f.x, f.y, f.z, f.w), m.x, m.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
+          rstart[r] = (uint32_t)(t1 - t0);
+          rtile[r] = (uint32_t)(ty * TX + t0);
+          rg[r] = g;
+        }
+        __syncthreads();
+        cta_excl_scan2048(rstart, (int)R, wsum);
+        for (int e = (int)e0 + t; e < e1; e += 256) {
+          const uint32_t le = (uint32_t)e - base0;
+          uint32_t key = 0;
+          int32_t val = 0;  // valid indices should the spans disagree with ntiles
+          if (R > 0) {
+            const int r = last_le(rstart, 0, (int)R - 1, le);
+            const uint32_t k = le - rstart[r];
+            if (k < rstart[r + 1] - rstart[r]) {
+              key = rtile[r] + k;
+              val = rg[r];
+            }
+          }
+          tile_keys[e] = key;
+          tile_vals[e] = val;
+        }
+        return;
+      }
+    }
+    // very wide ranges (more Gaussians or rows than the CTA caches): one
+    // thread per Gaussian walks its rows and writes its instances in [e0, e1)
     for (int j = jlo + t; j <= jhi; j += 256) {
-      const int g = cached ? sid[j - jlo] : order[j];
-      const int base = (int)(cached ? soff[j - jlo] : off[j]);
-      const int end = (int)(cached ? soff[j - jlo + 1] : off[j + 1]);
+      const int g = order[j];
+      const int base = (int)off[j], end = (int)off[j + 1];
       const int lo = base > (int)e0 ? base : (int)e0, hi = end < e1 ? end : e1;
       if (lo >= hi) continue;
-      int key = 0, gg = 0, k = base;  // safe values should the spans disagree with ntiles
+      int key = 0, gg = 0, k = base;
       if (g >= 0 && g < cap_n) {
         const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2),
                   y1 = __ldg(rect + 4 * g + 3);
@@ -420,8 +509,6 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
           for (int ty = y0; ty < y1 && k < hi; ++ty) {
             int t0, t1;
             fp_row_span(fr, m.x, m.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
-            const int rowk = ty * TX;
-            // instances k .. k + (t1 - t0) - 1 of this row: skip to lo
             int tx = t0;
             if (k < lo) {
               const int skip = lo - k < t1 - t0 ? lo - k : t1 - t0;
@@ -429,21 +516,16 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
               k += skip;
             }
             for (; tx < t1 && k < hi; ++tx, ++k) {
-              skey[k - (int)e0] = (uint32_t)(rowk + tx);
-              sval[k - (int)e0] = g;
+              tile_keys[k] = (uint32_t)(ty * TX + tx);
+              tile_vals[k] = g;
             }
           }
         }
       }
       for (k = k > lo ? k : lo; k < hi; ++k) {
-        skey[k - (int)e0] = (uint32_t)key;
-        sval[k - (int)e0] = gg;
+        tile_keys[k] = (uint32_t)key;
+        tile_vals[k] = gg;
       }
-    }
-    __syncthreads();
-    for (int e = (int)e0 + t; e < e1; e += 256) {
-      tile_keys[e] = skey[e - (int)e0];
-      tile_vals[e] = sval[e - (int)e0];
     }
     return;
   }

@@ -114,17 +114,34 @@ def test_project_bit_exact_integers_and_fp64_floats(lib):
     assert err[flag == 1].max() < 1e-5, err[flag == 1].max()
 
 
-def test_project_footprint_and_bin_sort_bit_exact(lib):
-    """The binning's opacity-aware footprint: the projection's tile counts
-    and footprint values, and the instance lists hyrf_bin_sort emits from
-    them, bit for bit against the oracle's FP32 replay."""
-    rng = np.random.default_rng(14)
-    cam = synth.look_at([0.4, -0.3, -1.0], [0, 0, 4], 333, 211, 65.0)
-    n = 20000
+def _footprint_scene(kind, rng, n, cam):
     pos, s, q = _proj_inputs(rng, n, cam)
     s[:, 0] *= np.exp(rng.uniform(0.0, 2.5, n)).astype(np.float32)  # anisotropic
     op = (1.0 / (1.0 + np.exp(-1.5 * rng.standard_normal(n)))).astype(np.float32)
+    if kind == "tall":
+        # thin, faint, mostly upright Gaussians: many rectangle rows whose
+        # ellipse misses them (more tile rows than instances per expansion CTA)
+        s[:] = np.array([0.004, 0.6, 0.004], np.float32) * rng.uniform(0.5, 1.5, (n, 1)).astype(np.float32)
+        q = np.concatenate([np.ones((n, 1)), rng.normal(0.0, 0.01, (n, 3))], 1).astype(np.float32)
+        op = rng.uniform(0.0045, 0.01, n).astype(np.float32)
+    elif kind == "sparse":
+        # most Gaussians below 1/255: many zero-instance Gaussians per CTA range
+        op[rng.random(n) < 0.995] = 1.0 / 300.0
     op[:50] = 1.0 / 300.0  # below 1/255: no footprint
+    return pos, s, q, op
+
+
+@pytest.mark.parametrize("kind", ["mixed", "tall", "sparse"])
+def test_project_footprint_and_bin_sort_bit_exact(lib, kind):
+    """The binning's opacity-aware footprint: the projection's tile counts
+    and footprint values, and the instance lists hyrf_bin_sort emits from
+    them, bit for bit against the oracle's FP32 replay. "tall" and "sparse"
+    drive the expansion's wide-range path (more tile rows, or more
+    Gaussians, per CTA than it caches)."""
+    rng = np.random.default_rng(14)
+    cam = synth.look_at([0.4, -0.3, -1.0], [0, 0, 4], 333, 211, 65.0)
+    n = {"mixed": 20000, "tall": 12000, "sparse": 120000}[kind]
+    pos, s, q, op = _footprint_scene(kind, rng, n, cam)
     dev = "cuda"
     ids = torch.arange(n, dtype=torch.int32, device=dev)
     nv = torch.tensor([n], dtype=torch.int32, device=dev)
@@ -143,6 +160,11 @@ def test_project_footprint_and_bin_sort_bit_exact(lib):
     assert np.array_equal(np_(out["mean2d"]).view(np.uint32), m2.view(np.uint32))
     area = np.where(rect[:, 2] > rect[:, 0], (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]), 0)
     assert ntiles.sum() < 0.9 * area.sum() and (ntiles[:50] == 0).all()
+    rows = np.where(rect[:, 2] > rect[:, 0], rect[:, 3] - rect[:, 1], 0)
+    if kind == "tall":
+        assert rows.sum() > 1.5 * ntiles.sum(), (rows.sum(), ntiles.sum())
+    if kind == "sparse":
+        assert (ntiles == 0).sum() > 100 * (ntiles > 0).sum()
     TX, TY = oracle.tiles_of(cam.width, cam.height)
     keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY, m2, foot)
     K = len(keys)
