@@ -6,7 +6,10 @@
 // thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32) per
 // layer with the weights staged once per CTA as the B operand; the f32
 // accumulators live in tensor memory and come back with tcgen05.ld for the
-// bias + ReLU epilogue, which writes the next layer's bf16 A operand.
+// bias + ReLU epilogue, which writes the next layer's bf16 A operand. The
+// field query runs three CTAs per SM (inputs share the hidden activations'
+// buffers, 128 tensor-memory columns each) and fetches the next tile's rows
+// into registers while the current tile's MMA chain runs.
 //
 // Shared-memory operands use the no-swizzle K-major core-matrix layout: an
 // 8-row x 16-byte core matrix is 128 contiguous bytes; core matrices
@@ -40,15 +43,47 @@ struct QueryIO {
   int32_t* status;
 };
 
-// smem byte offsets
+// smem byte offsets. A tile's inputs (A operands) share the buffers of its
+// hidden activations: layer 0's MMA has finished reading them when the
+// epilogue overwrites them.
 constexpr int oW0g = 0, oW1g = oW0g + 64 * 32 * 2, oW2g = oW1g + 64 * 64 * 2, oW0c = oW2g + 16 * 64 * 2,
-              oW1c = oW0c + 64 * 64 * 2, oW2c = oW1c + 64 * 64 * 2, oAg = oW2c + 16 * 64 * 2,
-              oAc = oAg + 128 * 32 * 2, oHg = oAc + 128 * 64 * 2, oHc = oHg + 128 * 64 * 2,
-              oBias = oHc + 128 * 64 * 2, kQuerySmem = oBias + 288 * 4;
-constexpr uint32_t kQueryTmemCols = 256;
+              oW1c = oW0c + 64 * 64 * 2, oW2c = oW1c + 64 * 64 * 2, oHg = oW2c + 16 * 64 * 2,
+              oHc = oHg + 128 * 64 * 2, oAg = oHg, oAc = oHc, oBias = oHc + 128 * 64 * 2,
+              kQuerySmem = oBias + 288 * 4;
+// tensor memory: geometry accumulators in columns [0, 64), colour in
+// [64, 128); the output layers reuse [0, 16) and [64, 80)
+constexpr uint32_t kQueryTmemCols = 128;
+
+// One point's inputs, fetched a tile ahead into registers so that their
+// global loads overlap the previous tile's MMA chain.
+struct QueryRow {
+  uint4 x[4];  // 32 bf16 hash features
+  float p[3];  // position (colour rows)
+  int i, g;
+  bool ok;
+};
+
+__device__ __forceinline__ void fetch_row(const QueryIO& io, const FieldsDev& F, bool geo, int i, int nv,
+                                          QueryRow& q) {
+  q.i = i;
+  q.ok = i < nv;
+  q.g = q.ok ? io.vis_ids[i] : 0;
+  if (q.ok && (q.g < 0 || q.g >= io.n)) {
+    set_status(io.status, HYRF_ERR_BOUNDS);
+    q.ok = false;
+    q.g = 0;
+  }
+  const uint4* s4 = reinterpret_cast<const uint4*>((geo ? io.Xg : io.Xr) + (size_t)(q.ok ? i : 0) * 16);
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) q.x[kc] = q.ok ? __ldg(s4 + kc) : make_uint4(0u, 0u, 0u, 0u);
+  if (!geo) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q.p[k] = q.ok ? io.pos[3 * (int64_t)q.g + k] : F.lo[k] + 1.0f / F.sx[k];
+  }
+}
 
 template <bool H16>
-__global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam, QueryIO io) {
+__global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam, QueryIO io) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
@@ -88,7 +123,7 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
   fence_after();
   const uint32_t tm = tmem_base;
   const uint32_t lane = ((uint32_t)((w & 3) * 32)) << 16;
-  const uint32_t colD = geo ? 0u : 64u, colO = geo ? 128u : 144u;
+  const uint32_t colD = geo ? 0u : 64u;
   uint8_t* Hs = sm + (geo ? oHg : oHc);
   const float* b0 = geo ? b0g : b0c;
   const float* b1 = geo ? b1g : b1c;
@@ -99,22 +134,16 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
   const int ntile = (nv + 127) / 128;
   uint32_t phase = 0;
   bool failed = false;
+  QueryRow cur;
+  if ((int)blockIdx.x < ntile) fetch_row(io, F, geo, blockIdx.x * 128 + r, nv, cur);
   for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
-    const int i = tile * 128 + r;
-    bool ok = i < nv;
-    int g = ok ? io.vis_ids[i] : 0;
-    if (ok && (g < 0 || g >= io.n)) {
-      set_status(io.status, HYRF_ERR_BOUNDS);
-      ok = false;
-    }
-    if (geo) {
-      load_row32<32>(sm + oAg, r, io.Xg + (size_t)i * 16, ok);
-    } else {
-      load_row32<64>(sm + oAc, r, io.Xr + (size_t)i * 16, ok);
-      float p[3];
+    // this tile's rows -> A operands (the previous tile's last MMA, the
+    // only reader of these buffers, has completed)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];
-      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+    for (int kc = 0; kc < 4; ++kc)
+      *reinterpret_cast<uint4*>(sm + (geo ? oAg : oAc) + kmaj(r, 8 * kc, geo ? 32 : 64)) = cur.x[kc];
+    if (!geo) {
+      float v[3] = {cur.p[0] - pc[0], cur.p[1] - pc[1], cur.p[2] - pc[2]};
       const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
       float pe[32];
@@ -130,6 +159,9 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
       gemm<64, 64, H16>(tm + 64, sm + oAc, sm + oW0c);
       commit(&bar);
     }
+    // the next tile's inputs, in flight during this tile's MMA chain
+    const QueryRow q = cur;
+    if (tile + (int)gridDim.x < ntile) fetch_row(io, F, geo, (tile + gridDim.x) * 128 + r, nv, cur);
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
@@ -152,35 +184,38 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<16, 64, H16>(tm + 128, sm + oHg, sm + oW2g);
-      gemm<16, 64, H16>(tm + 144, sm + oHc, sm + oW2c);
+      gemm<16, 64, H16>(tm + 0, sm + oHg, sm + oW2g);
+      gemm<16, 64, H16>(tm + 64, sm + oHc, sm + oW2c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     float o[16];
-    ld16(tm + lane + colO, o);
-    if (ok) {
+    ld16(tm + lane + colD, o);
+    const int i = q.i, g = q.g;
+    if (q.ok) {
       if (geo) {
         // Eq. 7: alpha, scale from the geometry decoder, rotation normalised
         io.alpha[i] = sigmoidf_(o[0] + b2[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
         const float se = io.scale_e ? io.scale_e[g] : 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(o[1 + k] + b2[1 + k] + se);
-        float q[4];
+        float qq[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = o[4 + k] + b2[4 + k];
-        const float rn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int k = 0; k < 4; ++k) qq[k] = o[4 + k] + b2[4 + k];
+        const float rn = sqrtf(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
         const float den = fmaxf(rn, 1e-12f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = q[k] / den;
+        for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = qq[k] / den;
       } else {
 #pragma unroll
         for (int k = 0; k < 3; ++k)
           io.color[3 * i + k] = sigmoidf_(o[k] + b2[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
       }
     }
+    // (the next tile's first MMA, which overwrites these tensor-memory
+    // columns, is issued after its operand barrier)
     fence_before();
   }
   if (failed) {
@@ -196,12 +231,14 @@ __global__ void __launch_bounds__(256, 2) k_query_fwd_tc(FieldsDev F, CamDev cam
 
 // ---------------------------------------------------------------- background, exact mode
 
-constexpr int bW0c = 0, bW1c = bW0c + 64 * 64 * 2, bW2c = bW1c + 64 * 64 * 2, bAc = bW2c + 16 * 64 * 2,
-              bHc = bAc + 128 * 64 * 2, bBias = bHc + 128 * 64 * 2, kBgSmem = bBias + 144 * 4;
-constexpr uint32_t kBgTmemCols = 128;
+// The pixels' inputs share the hidden activations' buffer (bAc = bHc), and
+// the output layer reuses tensor-memory columns [0, 16): six CTAs per SM.
+constexpr int bW0c = 0, bW1c = bW0c + 64 * 64 * 2, bW2c = bW1c + 64 * 64 * 2, bHc = bW2c + 16 * 64 * 2,
+              bAc = bHc, bBias = bHc + 128 * 64 * 2, kBgSmem = bBias + 144 * 4;
+constexpr uint32_t kBgTmemCols = 64;
 
 template <bool H16>
-__global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
+__global__ void __launch_bounds__(128, 6) k_bg_exact_fwd_tc(FieldsDev F, CamDev cam, float radius,
                                                            const uint32_t* __restrict__ Xb,
                                                            const int32_t* __restrict__ px_ids,
                                                            const int32_t* __restrict__ n_px,
@@ -242,15 +279,27 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
   const int ntile = (rows + 127) / 128;
   uint32_t phase = 0;
   bool failed = false;
-  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+  // this thread's next row (pixel id and bf16 features), fetched a tile ahead
+  uint4 xn[4];
+  int pn = 0;
+  bool okn = false;
+  auto fetch = [&](int tile) {
     const int row = tile * 128 + t;
-    const bool ok = row < rows;
-    const int pp = ok ? (px_ids ? px_ids[row] : row) : 0;
-    const int p = pp;
+    okn = row < rows;
+    pn = okn ? (px_ids ? px_ids[row] : row) : 0;
+    const uint4* s4 = reinterpret_cast<const uint4*>(Xb + (size_t)(okn ? row : 0) * 16);
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) xn[kc] = okn ? __ldg(s4 + kc) : make_uint4(0u, 0u, 0u, 0u);
+  };
+  if ((int)blockIdx.x < ntile) fetch(blockIdx.x);
+  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const bool ok = okn;
+    const int p = pn;
     {
-      load_row32<64>(sm + bAc, t, Xb + (size_t)(ok ? row : 0) * 16, ok);
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) *reinterpret_cast<uint4*>(sm + bAc + kmaj(t, 8 * kc, 64)) = xn[kc];
       float ps[3], dir[3], pe[32];
-      bg_ray(cam, F, radius, pp % cam.W, pp / cam.W, ps, dir);
+      bg_ray(cam, F, radius, p % cam.W, p / cam.W, ps, dir);
       pos_enc(dir, pe);
       store_cols<64, 32, 32, H16>(sm + bAc, t, pe);
     }
@@ -262,6 +311,7 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
       gemm<64, 64, H16>(tm, sm + bAc, sm + bW0c);
       commit(&bar);
     }
+    if (tile + (int)gridDim.x < ntile) fetch(tile + gridDim.x);
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
@@ -283,20 +333,22 @@ __global__ void __launch_bounds__(128, 4) k_bg_exact_fwd_tc(FieldsDev F, CamDev 
     __syncthreads();
     fence_after();
     if (t == 0) {
-      gemm<16, 64, H16>(tm + 64, sm + bHc, sm + bW2c);
+      gemm<16, 64, H16>(tm, sm + bHc, sm + bW2c);
       commit(&bar);
     }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     float o[16];
-    ld16(tm + lane + 64, o);
+    ld16(tm + lane, o);
     if (ok) {
       const float T = T_final[p];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * sigmoidf_(o[k] + b2[k]);
     }
+    // (the next tile's first MMA, which overwrites these columns, is issued
+    // after its operand barrier)
     fence_before();
   }
   if (failed) {
@@ -346,7 +398,7 @@ hyrf_status launch_query_fwd_tc(const hyrf_query_fields_args& a, const FieldsDev
   tc::QueryIO io{a.n,     a.pos, a.alpha_e, a.scale_e, a.color_e, a.vis_ids, a.n_vis,
                  Xg,      Xr,    a.alpha,   a.scale,   a.quat,    a.color,   a.status};
   int tiles = (a.n + 127) / 128;
-  int grid = num_sms() * 2;
+  int grid = num_sms() * 3;
   if (tiles < grid) grid = tiles;
   if (F.cm.f16) {
     set_smem_limit<tc::k_query_fwd_tc<true>>(tc::kQuerySmem);
@@ -436,7 +488,7 @@ hyrf_status launch_bg_exact_fwd_tc(const hyrf_composite_background_args& a, cons
   hyrf_status st = ready ? HYRF_OK : launch_gather(F, cam, RS, P, nullptr, Xb, s);
   if (st != HYRF_OK) return st;
   int tiles = (P + 127) / 128;
-  int grid = num_sms() * 4;
+  int grid = num_sms() * 6;
   if (tiles < grid) grid = tiles;
   if (F.cm.f16) {
     set_smem_limit<tc::k_bg_exact_fwd_tc<true>>(tc::kBgSmem);

@@ -371,9 +371,14 @@ __device__ __forceinline__ void epilogue_relu(uint32_t taddr, const float* b, ui
   ldcols<NC>(taddr, v);
 #pragma unroll
   for (int c = 0; c < NC; c += 8) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[c + j] = fmaxf(v[c + j] + b[c0 + c + j], 0.0f);
-    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, HP)) = pack8(v + c);
+    const float4 bl = *reinterpret_cast<const float4*>(b + c0 + c),
+                 bh = *reinterpret_cast<const float4*>(b + c0 + c + 4);
+    uint4 u;
+    u.x = add_relu_pack2(v[c], v[c + 1], bl.x, bl.y);
+    u.y = add_relu_pack2(v[c + 2], v[c + 3], bl.z, bl.w);
+    u.z = add_relu_pack2(v[c + 4], v[c + 5], bh.x, bh.y);
+    u.w = add_relu_pack2(v[c + 6], v[c + 7], bh.z, bh.w);
+    *reinterpret_cast<uint4*>(H + kmaj(r, c0 + c, HP)) = u;
   }
 }
 

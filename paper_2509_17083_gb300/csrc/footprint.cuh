@@ -56,7 +56,7 @@ __device__ __forceinline__ FootRows fp_rows(float a, float b, float c, float t) 
 }
 
 // Tile columns [tx0, tx1) of tile row ty, within [cx0, cx1), whose pixel
-// centres (tile tx + 0.5 ... tile tx + tile - 0.5) meet the ellipse
+// centres (16 tx + 0.5 ... 16 tx + 15.5) meet the ellipse
 // {(u, v) + d : d^T Sigma'^-1 d <= t}, Sigma' = [[a, b], [b, c]] (f from
 // fp_rows). Cut to the row's pixel-centre strip, the ellipse spans x in
 // [u + xmin, u + xmax]: its boundary at height dy is
@@ -64,15 +64,15 @@ __device__ __forceinline__ FootRows fp_rows(float a, float b, float c, float t) 
 // +-sqrt(t a) lie at dy = +-b sqrt(t / a). t = +inf: the whole row of the
 // rectangle; t < 0: nothing.
 __device__ __forceinline__ void fp_row_span(const FootRows& f, float u, float v, float c, float t, int ty,
-                                            int tile, int cx0, int cx1, int& tx0, int& tx1) {
+                                            int cx0, int cx1, int& tx0, int& tx1) {
   tx0 = tx1 = cx0;
   if (!(t >= 0.0f)) return;
   if (isinf(t)) {
     tx1 = cx1;
     return;
   }
-  const float tw = (float)tile;
-  const float Y0 = __fadd_rn((float)(ty * tile), 0.5f);
+  const float tw = (float)kTile;
+  const float Y0 = __fadd_rn((float)(ty * kTile), 0.5f);
   const float Y1 = __fadd_rn(Y0, __fsub_rn(tw, 1.0f));
   const float dy0 = __fsub_rn(Y0, v), dy1 = __fsub_rn(Y1, v);
   const float ya = fmaxf(dy0, -f.hy), yb = fminf(dy1, f.hy);
@@ -82,8 +82,12 @@ __device__ __forceinline__ void fp_row_span(const FootRows& f, float u, float v,
   const float kya = __fmul_rn(f.k, ya), kyb = __fmul_rn(f.k, yb);
   const float xmax = (f.yr >= ya && f.yr <= yb) ? f.hx : fmaxf(__fadd_rn(kya, wa), __fadd_rn(kyb, wb));
   const float xmin = (-f.yr >= ya && -f.yr <= yb) ? -f.hx : fminf(__fsub_rn(kya, wa), __fsub_rn(kyb, wb));
-  float f0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(u, xmin), __fsub_rn(tw, 0.5f)), tw));
-  float f1 = __fadd_rn(floorf(__fdiv_rn(__fsub_rn(__fadd_rn(u, xmax), 0.5f), tw)), 1.0f);
+  // x / tw for the power-of-two tile width: the product by 1 / tw rounds the
+  // same real number, so it equals the quotient bit for bit
+  const float itw = 1.0f / (float)kTile;
+  static_assert((kTile & (kTile - 1)) == 0, "tile width must be a power of two");
+  float f0 = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(u, xmin), __fsub_rn(tw, 0.5f)), itw));
+  float f1 = __fadd_rn(floorf(__fmul_rn(__fsub_rn(__fadd_rn(u, xmax), 0.5f), itw)), 1.0f);
   f0 = fminf(fmaxf(f0, (float)cx0), (float)cx1);
   f1 = fminf(fmaxf(f1, (float)cx0), (float)cx1);
   if (f1 > f0) {

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
         const FootRows fr = fp_rows(a, b, cc, t);
         for (int ty = iy0; ty < iy1; ++ty) {
           int t0, t1;
-          fp_row_span(fr, u, v, cc, t, ty, kTile, ix0, ix1, t0, t1);
+          fp_row_span(fr, u, v, cc, t, ty, ix0, ix1, t0, t1);
           nt += t1 - t0;
         }
       }

@@ -464,27 +464,30 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
           const float4 f = foot[g];
           int t0 = x0, t1 = x0;
           if (f.w >= 0.0f)
-            fp_row_span(fp_rows(f.x, f.y, f.z, f.w), m.x, m.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
+            fp_row_span(fp_rows(f.x, f.y, f.z, f.w), m.x, m.y, f.z, f.w, ty, x0, x1, t0, t1);
           rstart[r] = (uint32_t)(t1 - t0);
           rtile[r] = (uint32_t)(ty * TX + t0);
           rg[r] = g;
         }
         __syncthreads();
-        cta_excl_scan2048(rstart, (int)R, wsum);
-        for (int e = (int)e0 + t; e < e1; e += 256) {
-          const uint32_t le = (uint32_t)e - base0;
-          uint32_t key = 0;
-          int32_t val = 0;  // valid indices should the spans disagree with ntiles
-          if (R > 0) {
-            const int r = last_le(rstart, 0, (int)R - 1, le);
-            const uint32_t k = le - rstart[r];
-            if (k < rstart[r + 1] - rstart[r]) {
-              key = rtile[r] + k;
-              val = rg[r];
-            }
+        const uint32_t total = cta_excl_scan2048(rstart, (int)R, wsum);
+        // each row writes its instances that fall in [e0, e1); consecutive
+        // rows of a warp cover consecutive instances
+        const uint32_t lo = (uint32_t)e0 - base0, hi = (uint32_t)e1 - base0;
+        for (int r = t; r < (int)R; r += 256) {
+          const uint32_t a0 = max(rstart[r], lo), a1 = min(rstart[r + 1], hi);
+          const uint32_t key0 = rtile[r] - rstart[r];
+          const int32_t g = rg[r];
+          for (uint32_t k = a0; k < a1; ++k) {
+            tile_keys[base0 + k] = key0 + k;
+            tile_vals[base0 + k] = g;
           }
-          tile_keys[e] = key;
-          tile_vals[e] = val;
+        }
+        // instances the spans do not reach (only if they disagree with
+        // ntiles): valid indices
+        for (uint32_t k = max(total, lo) + t; k < hi; k += 256) {
+          tile_keys[base0 + k] = 0u;
+          tile_vals[base0 + k] = 0;
         }
         return;
       }
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
           const FootRows fr = fp_rows(f.x, f.y, f.z, f.w);
           for (int ty = y0; ty < y1 && k < hi; ++ty) {
             int t0, t1;
-            fp_row_span(fr, m.x, m.y, f.z, f.w, ty, kTile, x0, x1, t0, t1);
+            fp_row_span(fr, m.x, m.y, f.z, f.w, ty, x0, x1, t0, t1);
             int tx = t0;
             if (k < lo) {
               const int skip = lo - k < t1 - t0 ? lo - k : t1 - t0;

@@ -237,6 +237,32 @@ __device__ __forceinline__ void stage_w(uint8_t* tile, const void* W, int rows_r
   }
 }
 
+// ReLU(x + bx), ReLU(y + by) rounded to the operand type (bf16, or f16 when
+// H16) and packed, x in the low half: one paired f32 add (two independent
+// round-to-nearest adds) and one converting instruction that clamps
+// negative values to zero. Same values as max(x + bx, 0) rounded to
+// nearest even.
+template <bool H16 = false>
+__device__ __forceinline__ uint32_t add_relu_pack2(float x, float y, float bx, float by) {
+  uint32_t r;
+  if constexpr (H16) {
+    asm("{\n.reg .b64 p, q;\n.reg .f32 lo, hi;\n"
+        "mov.b64 p, {%1, %2};\nmov.b64 q, {%3, %4};\n"
+        "add.rn.f32x2 p, p, q;\nmov.b64 {lo, hi}, p;\n"
+        "cvt.rn.relu.f16x2.f32 %0, hi, lo;\n}"
+        : "=r"(r)
+        : "f"(x), "f"(y), "f"(bx), "f"(by));
+  } else {
+    asm("{\n.reg .b64 p, q;\n.reg .f32 lo, hi;\n"
+        "mov.b64 p, {%1, %2};\nmov.b64 q, {%3, %4};\n"
+        "add.rn.f32x2 p, p, q;\nmov.b64 {lo, hi}, p;\n"
+        "cvt.rn.relu.bf16x2.f32 %0, hi, lo;\n}"
+        : "=r"(r)
+        : "f"(x), "f"(y), "f"(bx), "f"(by));
+  }
+  return r;
+}
+
 // ReLU(D + b) of this thread's 64 accumulator columns -> its row of H
 // (bf16, or f16 when H16).
 template <bool H16 = false>
@@ -245,15 +271,15 @@ __device__ __forceinline__ void epilogue_relu64(uint32_t taddr, const float* b, 
   for (int c0 = 0; c0 < 64; c0 += 32) {
     float v[32];
     ld32(taddr + c0, v);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + b[c0 + j], 0.0f);
+    const float4* b4 = reinterpret_cast<const float4*>(b + c0);
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
+      const float4 bl = b4[2 * h], bh = b4[2 * h + 1];
       uint4 u;
-      u.x = pack2<H16>(v[8 * h], v[8 * h + 1]);
-      u.y = pack2<H16>(v[8 * h + 2], v[8 * h + 3]);
-      u.z = pack2<H16>(v[8 * h + 4], v[8 * h + 5]);
-      u.w = pack2<H16>(v[8 * h + 6], v[8 * h + 7]);
+      u.x = add_relu_pack2<H16>(v[8 * h], v[8 * h + 1], bl.x, bl.y);
+      u.y = add_relu_pack2<H16>(v[8 * h + 2], v[8 * h + 3], bl.z, bl.w);
+      u.z = add_relu_pack2<H16>(v[8 * h + 4], v[8 * h + 5], bh.x, bh.y);
+      u.w = add_relu_pack2<H16>(v[8 * h + 6], v[8 * h + 7], bh.z, bh.w);
       *reinterpret_cast<uint4*>(H + kmaj(r, c0 + 8 * h, 64)) = u;
     }
   }
