@@ -256,7 +256,11 @@ typedef struct {
   uint8_t* fp64_flag;        /* out [V], may be NULL */
   int32_t* status;
   const float* alpha;        /* [V] opacity for the footprint; may be NULL (o = 1) */
-  float* footprint;          /* out [V][4] (Sigma'_xx, Sigma'_xy, Sigma'_yy, t), 16-byte aligned; NULL: no culling */
+  float* footprint;          /* out [V][12], 16-byte aligned; NULL: no culling. Per row:
+                              * (Sigma'_xx, Sigma'_xy, Sigma'_yy, t), then eight 32-bit words
+                              * of row spans when the rectangle has at most 16 rows and 255
+                              * columns (row j: word j/2, bits 16 (j%2) on; low byte = first
+                              * tile column - x0, high byte = length), zeros otherwise */
 } hyrf_project_args;
 
 size_t hyrf_project_workspace_size(const hyrf_project_args* a);
@@ -312,7 +316,7 @@ typedef struct {
    * (same camera and visible set); the call then skips its own depth sort
    * (the result is identical). NULL: sorted here. */
   const int32_t* depth_order;
-  /* Optional, together: mean2d [V][2] and footprint [V][4] from
+  /* Optional, together: mean2d [V][2] and footprint [V][12] from
    * hyrf_project (with ntiles counted on the footprint); each rectangle row
    * then yields only its footprint's tile columns. NULL: whole rectangles. */
   const float* mean2d;

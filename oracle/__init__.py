@@ -350,7 +350,8 @@ def project_f32_footprint(pos, scale, quat, cam, alpha=None, tile=TILE):
     """FP32 replay of the projection with the binning's opacity-aware
     footprint (opacity alpha [n], or 1 when None): rect [n,4], ntiles [n]
     (tiles of the footprint), depth [n], flag [n], mean2d (float32) [n,2],
-    footprint (float32) [n,4]."""
+    footprint records (float32) [n,12]: Sigma' (a, b, c), t, and eight words
+    of packed row spans (bit patterns)."""
     return _project_f32(pos, scale, quat, cam, tile, alpha, True)
 
 
@@ -366,7 +367,7 @@ def _project_f32(pos, scale, quat, cam, tile, alpha, footprint):
     depth = np.zeros(n, dtype=np.float32)
     flag = np.zeros(n, dtype=np.uint8)
     mean2d = np.zeros((n, 2), dtype=np.float32) if footprint else None
-    foot = np.zeros((n, 4), dtype=np.float32) if footprint else None
+    foot = np.zeros((n, 12), dtype=np.float32) if footprint else None
     rc = lib().orc_project_f32_fp(n, _ptr(pos, _f32p), _ptr(scale, _f32p), _ptr(quat, _f32p),
                                   None if al is None else _ptr(al, _f32p), C.byref(c), tile,
                                   _ptr(rect, _i32p), _ptr(ntiles, _i32p), _ptr(depth, _f32p),

@@ -183,9 +183,12 @@ int32_t orc_project_f32(int32_t n, const float* pos, const float* scale, const f
  * given, ntiles counts only the tiles of the rectangle whose pixel centres
  * meet the ellipse q <= t (q = d^T Sigma'^-1 d, t = 1.02 x 2 ln(255 o) +
  * 0.05, o = alpha[i] or 1 when alpha is NULL; no footprint when o < 1/255;
- * near-singular Gaussians keep their rectangle, t = +inf), and foot[n][4] =
- * (Sigma'_xx, Sigma'_xy, Sigma'_yy, t) in FP32; mean2d[n][2] (may be NULL)
- * receives the FP32 pixel position. */
+ * near-singular Gaussians keep their rectangle, t = +inf), and foot[n][12]
+ * receives (Sigma'_xx, Sigma'_xy, Sigma'_yy, t) in FP32 followed by eight
+ * words of row spans: when the rectangle has at most 16 rows and 255
+ * columns, row j's 16-bit field (word j / 2, bits from 16 (j % 2)) holds its
+ * first tile column minus x0 and, in the high byte, its length; otherwise
+ * zeros. mean2d[n][2] (may be NULL) receives the FP32 pixel position. */
 int32_t orc_project_f32_fp(int32_t n, const float* pos, const float* scale, const float* quat,
                            const float* alpha, const orc_camera* cam, int32_t tile, int32_t* rect,
                            int32_t* ntiles, float* depth, uint8_t* flag, float* mean2d, float* foot);

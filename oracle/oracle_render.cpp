@@ -490,16 +490,28 @@ int32_t orc_project_f32_fp(int32_t n, const float* pos, const float* scale, cons
       // o < 1/255, where no pixel shows them at all
       float t = fp_qlimit(alpha ? alpha[i] : 1.0f);
       if (near_singular && t >= 0.0f) t = INFINITY;
-      foot[4 * i] = a;
-      foot[4 * i + 1] = b;
-      foot[4 * i + 2] = cc;
-      foot[4 * i + 3] = t;
+      float* fr = foot + 12 * i;
+      fr[0] = a;
+      fr[1] = b;
+      fr[2] = cc;
+      fr[3] = t;
+      // row spans packed as 16-bit fields (first column - x0, length) when
+      // the rectangle has at most 16 rows and 255 columns; else zero words
+      uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const bool packed = iy1 - iy0 <= 16 && ix1 - ix0 <= 255;
       int cnt = 0;
-      for (int ty = iy0; ty < iy1; ++ty) {
-        int t0, t1;
-        fp_row_span(u, v, a, b, cc, t, ty, tile, ix0, ix1, &t0, &t1);
-        cnt += t1 - t0;
+      if (ix1 > ix0 && iy1 > iy0) {
+        for (int ty = iy0; ty < iy1; ++ty) {
+          int t0, t1;
+          fp_row_span(u, v, a, b, cc, t, ty, tile, ix0, ix1, &t0, &t1);
+          cnt += t1 - t0;
+          if (packed) {
+            const int j = ty - iy0;
+            w[j / 2] |= (uint32_t)((t0 - ix0) | ((t1 - t0) << 8)) << (16 * (j % 2));
+          }
+        }
       }
+      std::memcpy(fr + 4, w, sizeof(w));
       ntiles[i] = cnt;
     }
     if (mean2d) {
@@ -611,8 +623,8 @@ int64_t orc_bin_sort_fp(int32_t n, const int32_t* rect, const float* depth, cons
     for (int ty = r[1]; ty < r[3]; ++ty) {
       int t0 = r[0], t1 = r[2];
       if (foot)
-        fp_row_span(mean2d[2 * g], mean2d[2 * g + 1], foot[4 * g], foot[4 * g + 1], foot[4 * g + 2],
-                    foot[4 * g + 3], ty, tile, r[0], r[2], &t0, &t1);
+        fp_row_span(mean2d[2 * g], mean2d[2 * g + 1], foot[12 * g], foot[12 * g + 1], foot[12 * g + 2],
+                    foot[12 * g + 3], ty, tile, r[0], r[2], &t0, &t1);
       for (int tx = t0; tx < t1; ++tx) inst.push_back({((uint64_t)(ty * tiles_x + tx) << 32) | bits, g});
     }
   }

@@ -37,6 +37,20 @@ __device__ __forceinline__ float fp_qlimit(float o) {
   return __fadd_rn(__fmul_rn(1.02f, __fmul_rn(2.0f, ln)), 0.05f);
 }
 
+// Footprint record of a projected Gaussian: three float4 (48 bytes). The
+// first holds Sigma' (a, b, c) and t; the other two hold the row spans,
+// packed when the rectangle has at most kSpanRows rows and at most 255
+// columns (fp_packed): row j's 16-bit field (word j / 2, bits 16 (j % 2)
+// on) is its first tile column minus x0 in the low byte and its span length
+// in the high byte; unpacked records leave these words zero and their spans
+// are recomputed from the first float4.
+constexpr int kFootVec = 3;     // float4 per record
+constexpr int kSpanRows = 16;   // rows of packed spans
+
+__host__ __device__ __forceinline__ bool fp_packed(int rows, int cols) {
+  return rows <= kSpanRows && cols <= 255;
+}
+
 // Per-Gaussian constants of the row spans: the ellipse's half-height
 // hy = sqrt(t c), the slope k = b / c of its centre line, mm = a - b k, its
 // half-width hx = sqrt(t a) and the height yr = b sqrt(t / a) of its

@@ -122,7 +122,7 @@ struct ProjOut {
   int32_t* ntiles;
   uint8_t* flag;
   const float* alpha;  // opacity for the footprint (NULL: 1)
-  float4* foot;        // footprint out (NULL: whole rectangles)
+  float4* foot;        // footprint records out (footprint.cuh; NULL: whole rectangles)
 };
 
 // FP64 recomputation of Sigma' and its inverse for near-singular Gaussians.
@@ -270,16 +270,31 @@ __global__ void __launch_bounds__(256) k_project(CamDev c, int n, const float* _
       // rectangle (their conic comes from an FP64 recomputation of Sigma')
       float t = fp_qlimit(o.alpha ? o.alpha[i] : 1.0f);
       if (near_singular && t >= 0.0f) t = INFINITY;
-      o.foot[i] = make_float4(a, b, cc, t);
+      uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
       nt = 0;
-      if (t >= 0.0f) {
+      if (t >= 0.0f && iy1 > iy0 && ix1 > ix0) {
         const FootRows fr = fp_rows(a, b, cc, t);
-        for (int ty = iy0; ty < iy1; ++ty) {
-          int t0, t1;
-          fp_row_span(fr, u, v, cc, t, ty, ix0, ix1, t0, t1);
-          nt += t1 - t0;
+        if (fp_packed(iy1 - iy0, ix1 - ix0)) {
+#pragma unroll
+          for (int j = 0; j < kSpanRows; ++j) {
+            if (iy0 + j < iy1) {
+              int t0, t1;
+              fp_row_span(fr, u, v, cc, t, iy0 + j, ix0, ix1, t0, t1);
+              nt += t1 - t0;
+              w[j >> 1] |= (uint32_t)((t0 - ix0) | ((t1 - t0) << 8)) << (16 * (j & 1));
+            }
+          }
+        } else {
+          for (int ty = iy0; ty < iy1; ++ty) {
+            int t0, t1;
+            fp_row_span(fr, u, v, cc, t, ty, ix0, ix1, t0, t1);
+            nt += t1 - t0;
+          }
         }
       }
+      o.foot[kFootVec * i] = make_float4(a, b, cc, t);
+      reinterpret_cast<uint4*>(o.foot)[kFootVec * i + 1] = make_uint4(w[0], w[1], w[2], w[3]);
+      reinterpret_cast<uint4*>(o.foot)[kFootVec * i + 2] = make_uint4(w[4], w[5], w[6], w[7]);
     }
     o.ntiles[i] = nt;
     if (o.flag) o.flag[i] = near_singular ? 1 : 0;

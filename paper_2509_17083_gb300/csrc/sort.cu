@@ -357,6 +357,24 @@ __device__ __forceinline__ void last_le2_cta(const uint32_t* __restrict__ a, int
 constexpr int kExpandItems = 2048;  // instances per CTA
 constexpr int kExpandSlice = 2048;  // sorted Gaussians cached per CTA
 constexpr int kExpandRows = 2048;   // footprint tile rows cached per CTA
+constexpr int kExpandPer = kExpandItems / 256;  // instances per thread (packed footprints)
+
+// Offset from x0 and length of row j's span in a packed footprint record
+// (words 1..8 of the record: wa, wb; footprint.cuh).
+__device__ __forceinline__ void span_at(const uint4& wa, const uint4& wb, int j, int& off, int& len) {
+  const int k = j >> 1;
+  uint32_t w = wa.x;
+  w = k == 1 ? wa.y : w;
+  w = k == 2 ? wa.z : w;
+  w = k == 3 ? wa.w : w;
+  w = k == 4 ? wb.x : w;
+  w = k == 5 ? wb.y : w;
+  w = k == 6 ? wb.z : w;
+  w = k == 7 ? wb.w : w;
+  const uint32_t h = (w >> (16 * (j & 1))) & 0xffffu;
+  off = (int)(h & 0xffu);
+  len = (int)(h >> 8);
+}
 
 // Exclusive prefix sums of a[0, n) in place, n <= 2048, by a 256-thread CTA
 // (eight consecutive entries per thread); a[n] = the total, also returned.
@@ -434,15 +452,96 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
   }
   __syncthreads();
   if (foot) {
-    // footprints: one thread per (Gaussian, tile row) of the CTA's range
-    // computes the row's span (footprint.cuh: the spans the projection
-    // counted), a scan of the span lengths gives each row's first instance,
-    // then one thread per instance writes its key and value (coalesced).
+    // footprints. Packed records: each instance's tile from the row spans
+    // the projection stored. Otherwise one thread per (Gaussian, tile row)
+    // of the CTA's range computes the row's span (footprint.cuh: the spans
+    // the projection counted), a scan of the span lengths gives each row's
+    // first instance, and each row writes its instances.
     __shared__ uint32_t rstart[kExpandRows + 1];
     __shared__ uint32_t rtile[kExpandRows];
     __shared__ int32_t rg[kExpandRows];
     __shared__ uint32_t wsum[8];
     if (cached) {
+      // eight consecutive instances per thread: one search of the cached
+      // offsets finds the first one's Gaussian and a walk of its packed row
+      // spans (footprint.cuh) its row; the thread then steps along the
+      // spans, and to the next Gaussian, instance by instance. Keys and
+      // values are staged in shared memory and written out coalesced. A
+      // CTA whose range holds an unpacked record redoes the range below.
+      static_assert(kExpandRows >= kExpandItems, "staging");
+      bool unpacked = false;
+      const int q0 = (int)e0 + kExpandPer * t, q1 = min(q0 + kExpandPer, e1);
+      if (q0 < q1) {
+        int i = last_le(soff, 0, L - 1, (uint32_t)q0);
+        int rg_ = q0 - (int)soff[i];  // instance index within Gaussian i
+        int g = 0, cnt = 0, x0 = 0, y0 = 0, rows = 0, j = 0, c = 0, off = 0, len = 0;
+        bool ok = false;
+        uint4 wa = make_uint4(0u, 0u, 0u, 0u), wb = wa;
+        auto load = [&]() {  // Gaussian i's record; row and column of its instance rg_
+          g = sid[i];
+          cnt = (int)(soff[i + 1] - soff[i]);
+          ok = g >= 0 && g < cap_n;
+          rows = 0;
+          if (ok) {
+            // the span words are loaded with the rectangle (not after it:
+            // one memory latency per Gaussian, not two)
+            x0 = __ldg(rect + 4 * g);
+            y0 = __ldg(rect + 4 * g + 1);
+            const int x1 = __ldg(rect + 4 * g + 2), y1 = __ldg(rect + 4 * g + 3);
+            wa = __ldg(reinterpret_cast<const uint4*>(foot + kFootVec * g + 1));
+            wb = __ldg(reinterpret_cast<const uint4*>(foot + kFootVec * g + 2));
+            rows = y1 - y0;
+            if (!fp_packed(rows, x1 - x0)) {
+              unpacked = true;
+              rows = 0;
+            }
+          }
+          j = 0;
+          c = rg_;
+          span_at(wa, wb, 0, off, len);
+          while (j < rows && c >= len) {
+            c -= len;
+            if (++j < rows) span_at(wa, wb, j, off, len);
+          }
+        };
+        load();
+        for (int e = q0; e < q1; ++e) {
+          uint32_t key = 0u;  // valid indices should the spans disagree with ntiles
+          int32_t val = 0;
+          if (ok) {
+            key = j < rows ? (uint32_t)((y0 + j) * TX + x0 + off + c) : (uint32_t)(y0 * TX + x0);
+            val = g;
+          }
+          rtile[e - (int)e0] = key;
+          rg[e - (int)e0] = val;
+          if (e + 1 == q1) break;
+          if (++rg_ < cnt) {  // next instance of this Gaussian: next column, or next row with tiles
+            if (++c >= len && j < rows) {
+              c = 0;
+              while (++j < rows) {
+                span_at(wa, wb, j, off, len);
+                if (len > 0) break;
+              }
+            }
+          } else {  // next Gaussian with instances
+            do {
+              ++i;
+            } while (i < L - 1 && soff[i + 1] == soff[i]);
+            i = min(i, L - 1);  // (the offsets place instance e + 1 within the range)
+            rg_ = 0;
+            load();
+          }
+        }
+      }
+      if (__syncthreads_or(unpacked)) {
+        // (the row-parallel path below rewrites the whole range)
+      } else {
+        for (int e = (int)e0 + t; e < e1; e += 256) {
+          tile_keys[e] = rtile[e - (int)e0];
+          tile_vals[e] = rg[e - (int)e0];
+        }
+        return;
+      }
       const uint32_t base0 = soff[0];
       __syncthreads();
       uint32_t* srow = soff;  // rows per Gaussian, then their prefix sums
@@ -461,7 +560,7 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
           const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2);
           const int ty = y0 + (r - (int)srow[i]);
           const float2 m = mean2d[g];
-          const float4 f = foot[g];
+          const float4 f = foot[kFootVec * g];
           int t0 = x0, t1 = x0;
           if (f.w >= 0.0f)
             fp_row_span(fp_rows(f.x, f.y, f.z, f.w), m.x, m.y, f.z, f.w, ty, x0, x1, t0, t1);
@@ -504,7 +603,7 @@ __global__ void __launch_bounds__(256) k_expand(const int32_t* __restrict__ rect
         const int x0 = __ldg(rect + 4 * g), y0 = __ldg(rect + 4 * g + 1), x1 = __ldg(rect + 4 * g + 2),
                   y1 = __ldg(rect + 4 * g + 3);
         const float2 m = mean2d[g];
-        const float4 f = foot[g];
+        const float4 f = foot[kFootVec * g];
         gg = g;
         key = y0 * TX + x0;
         if (f.w >= 0.0f) {

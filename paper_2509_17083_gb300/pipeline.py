@@ -200,7 +200,7 @@ class ViewRenderer:
         self.rect, self.ntiles = z(n, 4, dt=i32), z(n, dt=i32)
         # opacity-aware footprint of each projected Gaussian (hyrf_project):
         # the binning keeps only the tiles it can show in
-        self.footprint = z(max(n, 1), 4)
+        self.footprint = z(max(n, 1), 12)
         self.flag = z(max(n, 1), dt=torch.uint8)
         self.ranges = z(self.TX * self.TY, 2, dt=i32)
         # the compositing passes take the tiles in this order: index order at

@@ -127,20 +127,28 @@ def _footprint_scene(kind, rng, n, cam):
     elif kind == "sparse":
         # most Gaussians below 1/255: many zero-instance Gaussians per CTA range
         op[rng.random(n) < 0.995] = 1.0 / 300.0
+    elif kind == "big":
+        # a few large Gaussians: rectangles of more than 16 tile rows, whose
+        # footprint records carry no packed spans
+        big = rng.random(n) < 0.01
+        s[big] *= 12.0
     op[:50] = 1.0 / 300.0  # below 1/255: no footprint
     return pos, s, q, op
 
 
-@pytest.mark.parametrize("kind", ["mixed", "tall", "sparse"])
+@pytest.mark.parametrize("kind", ["mixed", "tall", "sparse", "big"])
 def test_project_footprint_and_bin_sort_bit_exact(lib, kind):
     """The binning's opacity-aware footprint: the projection's tile counts
-    and footprint values, and the instance lists hyrf_bin_sort emits from
-    them, bit for bit against the oracle's FP32 replay. "tall" and "sparse"
-    drive the expansion's wide-range path (more tile rows, or more
-    Gaussians, per CTA than it caches)."""
+    and footprint records, and the instance lists hyrf_bin_sort emits from
+    them, bit for bit against the oracle's FP32 replay. "mixed" takes the
+    expansion's packed-span path; "tall" and "big" (rectangles of more than
+    16 tile rows) its row-parallel path, "tall" also beyond the rows a CTA
+    caches; "sparse" (more Gaussians per CTA range than it caches) the
+    per-Gaussian path."""
     rng = np.random.default_rng(14)
-    cam = synth.look_at([0.4, -0.3, -1.0], [0, 0, 4], 333, 211, 65.0)
-    n = {"mixed": 20000, "tall": 12000, "sparse": 120000}[kind]
+    H_ = {"mixed": 211, "tall": 420, "sparse": 211, "big": 420}[kind]
+    cam = synth.look_at([0.4, -0.3, -1.0], [0, 0, 4], 333, H_, 65.0)
+    n = {"mixed": 20000, "tall": 12000, "sparse": 120000, "big": 20000}[kind]
     pos, s, q, op = _footprint_scene(kind, rng, n, cam)
     dev = "cuda"
     ids = torch.arange(n, dtype=torch.int32, device=dev)
@@ -148,7 +156,7 @@ def test_project_footprint_and_bin_sort_bit_exact(lib, kind):
     out = dict(mean2d=torch.zeros(n, 2, device=dev), conic=torch.zeros(n, 3, device=dev),
                depth=torch.zeros(n, device=dev), rect=torch.zeros(n, 4, dtype=torch.int32, device=dev),
                ntiles=torch.zeros(n, dtype=torch.int32, device=dev),
-               fp64_flag=torch.zeros(n, dtype=torch.uint8, device=dev), footprint=torch.zeros(n, 4, device=dev))
+               fp64_flag=torch.zeros(n, dtype=torch.uint8, device=dev), footprint=torch.zeros(n, 12, device=dev))
     H.hyrf_project(n=n, pos=cuda_f32(pos), vis_ids=ids, n_vis=nv, scale=cuda_f32(s), quat=cuda_f32(q),
                    cam=H.camera(cam), tile=16, alpha=cuda_f32(op), **out)
     torch.cuda.synchronize()
@@ -165,6 +173,11 @@ def test_project_footprint_and_bin_sort_bit_exact(lib, kind):
         assert rows.sum() > 1.5 * ntiles.sum(), (rows.sum(), ntiles.sum())
     if kind == "sparse":
         assert (ntiles == 0).sum() > 100 * (ntiles > 0).sum()
+    unpacked = (rows > 16) | (rect[:, 2] - rect[:, 0] > 255)
+    if kind in ("tall", "big"):
+        assert unpacked.sum() > 20
+    else:
+        assert not unpacked.any()
     TX, TY = oracle.tiles_of(cam.width, cam.height)
     keys, vals, ranges = oracle.bin_sort(rect, depth, TX, TY, m2, foot)
     K = len(keys)

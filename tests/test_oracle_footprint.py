@@ -59,7 +59,7 @@ def test_footprint_against_brute_force(orc):
         x0, y0, x1, y1 = rect[g]
         if x1 <= x0 or y1 <= y0:
             continue
-        a, b, c, t = [float(x) for x in foot[g]]
+        a, b, c, t = [float(x) for x in foot[g, :4]]
         Sg = np.array([[a, b], [b, c]])
         Q = np.linalg.inv(Sg)
         u, v = float(m2[g, 0]), float(m2[g, 1])
@@ -85,6 +85,23 @@ def test_footprint_against_brute_force(orc):
                     assert qf.min() <= t * (1.0 + 1e-3) + 0.05, (g, tx, ty, qf.min(), t)
                 dropped += (not is_kept)
     assert checked > 1000 and dropped > 100, (checked, dropped)
+    # the packed row spans (rectangles of <= 16 rows, <= 255 columns) list
+    # exactly the kept tiles; other records carry zero span words
+    words = foot[:, 4:].view(np.uint32)
+    packed = 0
+    for g in range(len(pos)):
+        x0, y0, x1, y1 = rect[g]
+        if x1 <= x0 or y1 <= y0 or y1 - y0 > 16 or x1 - x0 > 255:
+            assert not words[g].any()
+            continue
+        packed += 1
+        tiles = set()
+        for j in range(y1 - y0):
+            h = (int(words[g, j // 2]) >> (16 * (j % 2))) & 0xFFFF
+            tiles |= {(y0 + j) * TX + x0 + (h & 0xFF) + k for k in range(h >> 8)}
+        assert tiles == {tt for (gg, tt) in kept if gg == g}, g
+        assert len(tiles) == nt[g]
+    assert packed > 100
 
 
 def test_footprint_lists_composite_like_rectangles(orc):
