@@ -2,8 +2,9 @@
 // Eqs. 10-11, App. A.2): FP32 CUDA-core kernels, forward and backward.
 // Forward: for 16-level grids with 2 x 64 decoders the hash gather runs in
 // its own full-occupancy kernel (k_gather_f32, gather.cu) and the decoders
-// here read its f32 features (k_query_dec, k_bg_dec); other shapes use the
-// fused kernels (gather and decoders in one thread per point). Backward
+// here read its f32 features (k_query_dec_f32, k_bg_dec_f32: register-tiled
+// CTA-wide products); other shapes use the fused kernels (gather and
+// decoders in one thread per point). Backward
 // kernels recompute the decoder activations, keep them in shared memory as
 // [feature][point] tiles, and reduce the weight gradients per CTA into a
 // private float32 slab (no atomics); one reduction kernel adds the slabs
@@ -144,46 +145,6 @@ __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev c
     {
       float fc[NC];
       encode<NL>(F.rad, y, fc);
-      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
-      const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
-      pos_enc(dir, fc + NG);
-      mlp_fwd<NC, WID, NH, 3, WT>(F.cm, fc, col, kFwdPitch, co);
-    }
-    aggregate(io, i, g, go, co);
-  }
-}
-
-// FP32 split path: the decoders of the field query on the features that
-// k_gather_f32 (gather.cu) wrote, X [n_vis][2 NL] per field (the same FP32
-// contraction and interpolation as encode()), one thread per visible row.
-template <int NL, int WID, int NH, class WT>
-__global__ void __launch_bounds__(kFwdThreads) k_query_dec(FieldsDev F, CamDev cam, QueryFwdIO io,
-                                                          const float* __restrict__ Xg,
-                                                          const float* __restrict__ Xr) {
-  constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
-  __shared__ float hid[WID * kFwdPitch];
-  float* col = hid + threadIdx.x;
-  const int nv = min(*io.n_vis, io.n);
-  float pc[3];
-  cam_center(cam, pc);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
-    const int g = io.vis_ids[i];
-    if (g < 0 || g >= io.n) {
-      set_status(io.status, HYRF_ERR_BOUNDS);
-      continue;
-    }
-    float go[8];
-    {
-      float fg[NG];
-      load_row<NG>(Xg + (size_t)i * NG, fg);
-      mlp_fwd<NG, WID, NH, 8, WT>(F.gm, fg, col, kFwdPitch, go);
-    }
-    float co[3];
-    {
-      float fc[NC];
-      load_row<NG>(Xr + (size_t)i * NG, fc);
-      const float p[3] = {io.pos[3 * (int64_t)g], io.pos[3 * (int64_t)g + 1], io.pos[3 * (int64_t)g + 2]};
       float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
       const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
@@ -543,27 +504,223 @@ __global__ void __launch_bounds__(kFwdThreads) k_bg_exact_fwd(FieldsDev F, CamDe
   }
 }
 
-// FP32 split path, exact background: the colour decoder at every pixel's
-// sphere hit on the features k_gather_f32 wrote, Xb [W H][2 NL].
-template <int NL, int WID, int NH, class WT>
-__global__ void __launch_bounds__(kFwdThreads) k_bg_dec(FieldsDev F, CamDev cam, float radius,
-                                                       const float* __restrict__ Xb,
-                                                       const float* __restrict__ C_fg,
-                                                       const float* __restrict__ T_final,
-                                                       float* __restrict__ C) {
-  constexpr int NG = 2 * NL, NC = NG + kPEPad;
-  __shared__ float hid[WID * kFwdPitch];
-  float* col = hid + threadIdx.x;
-  const int P = cam.W * cam.H;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    float ps[3], dir[3], x0[NC], out[3];
-    bg_ray(cam, F, radius, p % cam.W, p / cam.W, ps, dir);
-    load_row<NG>(Xb + (size_t)p * NG, x0);
-    pos_enc(dir, x0 + NG);
-    mlp_fwd<NC, WID, NH, 3, WT>(F.cm, x0, col, kFwdPitch, out);
-    const float T = T_final[p];
+// ---------------------------------------------------------------- FP32 decoders, register-tiled
+
+// Decoders of the FP32 split path (2 x 64 hidden units) as a CTA-wide
+// product: 256 threads take tiles of 256 rows; a tile's activations sit in
+// shared memory feature-major (act[feature][row]) and the weights
+// transposed (Wt[input][output]), staged once per CTA. A hidden layer is a
+// 256 x 64 product in 8 x 8 register blocks: per input feature a thread
+// reads 8 activations and 8 weights (four 16-byte loads) for 64 FMAs. Each
+// output sums its products in input order from zero and then adds the
+// bias, as dense_col and dot_row do, so the values equal those of the
+// one-thread-per-row decoders bit for bit.
+constexpr int kDecRows = 256;            // rows per tile = threads per CTA
+constexpr int kDecPitch = kDecRows + 4;  // floats per feature row of act
+
+template <int IN, int OP>
+struct DecSmemF32 {
+  static constexpr int act = 0, w0 = act + 64 * kDecPitch, w1 = w0 + IN * 64, w2 = w1 + 64 * 64,
+                       b0 = w2 + 64 * OP, b1 = b0 + 64, b2 = b1 + 64, floats = b2 + OP;
+};
+
+// Wt[i][o] = W[o][i] (W row-major [rows_real][IN]), zero for o >= rows_real.
+template <int OP, int IN>
+__device__ __forceinline__ void stage_wt(float* Wt, const float* __restrict__ W, int rows_real) {
+  for (int e = threadIdx.x; e < OP * IN; e += blockDim.x) {
+    const int o = e / IN, i = e % IN;
+    Wt[i * OP + o] = o < rows_real ? __ldg(W + o * IN + i) : 0.0f;
+  }
+}
+
+// Stage a decoder's three layers (weights transposed, biases; output
+// padded to OP) into the tile layout L.
+template <int IN, int OP, int OUT>
+__device__ __forceinline__ void stage_decoder(float* sm, const MlpDev& m) {
+  using L = DecSmemF32<IN, OP>;
+  stage_wt<64, IN>(sm + L::w0, static_cast<const float*>(m.W[0]), 64);
+  stage_wt<64, 64>(sm + L::w1, static_cast<const float*>(m.W[1]), 64);
+  stage_wt<OP, 64>(sm + L::w2, static_cast<const float*>(m.W[2]), OUT);
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+    sm[L::b0 + e] = m.b[0][e];
+    sm[L::b1 + e] = m.b[1][e];
+  }
+  for (int e = threadIdx.x; e < OP; e += blockDim.x) sm[L::b2 + e] = e < OUT ? m.b[2][e] : 0.0f;
+}
+
+// act[o][r] = ReLU(sum_i Wt[i][o] act[i][r] + b[o]), o < 64, for the
+// tile's 256 rows (in place: every thread reads the whole input first).
+template <int IN>
+__device__ __forceinline__ void dec_hidden(float* act, const float* Wt, const float* b) {
+  const int t = threadIdx.x, r0 = 8 * (t & 31), o0 = 8 * (t >> 5);
+  float acc[8][8];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * sigmoidf_(out[k]);
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 2
+  for (int k = 0; k < IN; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(act + k * kDecPitch + r0);
+    const float4 a1 = *reinterpret_cast<const float4*>(act + k * kDecPitch + r0 + 4);
+    const float4 w0 = *reinterpret_cast<const float4*>(Wt + k * 64 + o0);
+    const float4 w1 = *reinterpret_cast<const float4*>(Wt + k * 64 + o0 + 4);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(w[j], a[i], acc[i][j]);
+  }
+  __syncthreads();  // the whole input has been read
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float bj = b[o0 + j];
+    float* dst = act + (o0 + j) * kDecPitch + r0;
+    *reinterpret_cast<float4*>(dst) =
+        make_float4(fmaxf(acc[0][j] + bj, 0.0f), fmaxf(acc[1][j] + bj, 0.0f), fmaxf(acc[2][j] + bj, 0.0f),
+                    fmaxf(acc[3][j] + bj, 0.0f));
+    *reinterpret_cast<float4*>(dst + 4) =
+        make_float4(fmaxf(acc[4][j] + bj, 0.0f), fmaxf(acc[5][j] + bj, 0.0f), fmaxf(acc[6][j] + bj, 0.0f),
+                    fmaxf(acc[7][j] + bj, 0.0f));
+  }
+  __syncthreads();
+}
+
+// Output layer for this thread's row: out[o] = sum_k Wt2[k][o] act[k][r] + b[o].
+template <int OP>
+__device__ __forceinline__ void dec_out(const float* act, const float* Wt2, const float* b2, float* out) {
+  const int r = threadIdx.x;
+  float acc[OP];
+#pragma unroll
+  for (int o = 0; o < OP; ++o) acc[o] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < 64; ++k) {
+    const float h = act[k * kDecPitch + r];
+#pragma unroll
+    for (int q = 0; q < OP / 4; ++q) {
+      const float4 w = *reinterpret_cast<const float4*>(Wt2 + k * OP + 4 * q);
+      acc[4 * q] = fmaf(w.x, h, acc[4 * q]);
+      acc[4 * q + 1] = fmaf(w.y, h, acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(w.z, h, acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(w.w, h, acc[4 * q + 3]);
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < OP; ++o) out[o] = acc[o] + b2[o];
+}
+
+// Field query, one decoder per launch (GEO: the geometry decoder -> alpha,
+// scale, rotation; else the colour decoder -> colour), on the features
+// k_gather_f32 wrote (X [n_vis][32]); Eq. 7 as aggregate().
+template <bool GEO>
+__global__ void __launch_bounds__(kDecRows, 2) k_query_dec_f32(FieldsDev F, CamDev cam, QueryFwdIO io,
+                                                             const float* __restrict__ X) {
+  constexpr int IN = GEO ? 32 : 32 + kPEPad, OP = GEO ? 8 : 4, OUT = GEO ? 8 : 3;
+  using L = DecSmemF32<IN, OP>;
+  extern __shared__ __align__(16) float smf[];
+  float* act = smf + L::act;
+  stage_decoder<IN, OP, OUT>(smf, GEO ? F.gm : F.cm);
+  const int t = threadIdx.x;
+  const int nv = min(*io.n_vis, io.n);
+  const int ntile = (nv + kDecRows - 1) / kDecRows;
+  float pc[3];
+  cam_center(cam, pc);
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int i = tile * kDecRows + t;
+    int g = i < nv ? io.vis_ids[i] : -1;
+    if (i < nv && (g < 0 || g >= io.n)) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      g = -1;
+    }
+    // this row's input -> column t of act (zeros for rows without a point)
+    {
+      float x[32];
+      if (g >= 0) load_row<32>(X + (size_t)i * 32, x);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) act[k * kDecPitch + t] = g >= 0 ? x[k] : 0.0f;
+    }
+    if constexpr (!GEO) {
+      float pe[kPEPad];
+      const float p[3] = {g >= 0 ? io.pos[3 * (int64_t)g] : pc[0] + 1.0f,
+                          g >= 0 ? io.pos[3 * (int64_t)g + 1] : pc[1], g >= 0 ? io.pos[3 * (int64_t)g + 2] : pc[2]};
+      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+      const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+      pos_enc(dir, pe);
+#pragma unroll
+      for (int k = 0; k < kPEPad; ++k) act[(32 + k) * kDecPitch + t] = pe[k];
+    }
+    __syncthreads();
+    dec_hidden<IN>(act, smf + L::w0, smf + L::b0);
+    dec_hidden<64>(act, smf + L::w1, smf + L::b1);
+    float o[OP];
+    dec_out<OP>(act, smf + L::w2, smf + L::b2, o);
+    if (g >= 0) {
+      if constexpr (GEO) {
+        io.alpha[i] = sigmoidf_(o[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
+        const float se = io.scale_e ? io.scale_e[g] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(o[1 + k] + se);
+        const float rn = sqrtf(o[4] * o[4] + o[5] * o[5] + o[6] * o[6] + o[7] * o[7]);
+        const float den = fmaxf(rn, 1e-12f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) io.quat[4 * i + k] = o[4 + k] / den;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          io.color[3 * i + k] = sigmoidf_(o[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
+      }
+    }
+    __syncthreads();  // act is rewritten by the next tile
+  }
+}
+
+// Exact background (Eq. 11) on the features k_gather_f32 wrote at every
+// pixel's sphere hit (Xb [W H][32]): C = C_fg + T_final sigmoid(decoder).
+// NF: features per row (2 x 16 levels).
+template <int NF>
+__global__ void __launch_bounds__(kDecRows, 2) k_bg_dec_f32(FieldsDev F, CamDev cam, float radius,
+                                                          const float* __restrict__ Xb,
+                                                          const float* __restrict__ C_fg,
+                                                          const float* __restrict__ T_final,
+                                                          float* __restrict__ C) {
+  static_assert(NF == 32, "16-level grids");
+  constexpr int IN = NF + kPEPad, OP = 4;
+  using L = DecSmemF32<IN, OP>;
+  extern __shared__ __align__(16) float smf[];
+  float* act = smf + L::act;
+  stage_decoder<IN, OP, 3>(smf, F.cm);
+  const int t = threadIdx.x;
+  const int P = cam.W * cam.H;
+  const int ntile = (P + kDecRows - 1) / kDecRows;
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int p = tile * kDecRows + t;
+    const bool ok = p < P;
+    {
+      float x[32];
+      if (ok) load_row<32>(Xb + (size_t)p * 32, x);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) act[k * kDecPitch + t] = ok ? x[k] : 0.0f;
+      float ps[3], dir[3], pe[kPEPad];
+      const int q = ok ? p : 0;
+      bg_ray(cam, F, radius, q % cam.W, q / cam.W, ps, dir);
+      pos_enc(dir, pe);
+#pragma unroll
+      for (int k = 0; k < kPEPad; ++k) act[(32 + k) * kDecPitch + t] = pe[k];
+    }
+    __syncthreads();
+    dec_hidden<IN>(act, smf + L::w0, smf + L::b0);
+    dec_hidden<64>(act, smf + L::w1, smf + L::b1);
+    float o[OP];
+    dec_out<OP>(act, smf + L::w2, smf + L::b2, o);
+    if (ok) {
+      const float T = T_final[p];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) C[3 * (int64_t)p + k] = C_fg[3 * (int64_t)p + k] + T * sigmoidf_(o[k]);
+    }
+    __syncthreads();
   }
 }
 
@@ -1037,10 +1194,18 @@ static hyrf_status query_fwd_impl(const FieldsDev& F, const CamDev& cam, const Q
     return HYRF_ERR_UNSUPPORTED;  // bf16 decoders run on the tensor cores (fields_tc.cu)
   } else {
     if (X) {  // split path: features gathered by k_gather_f32
-      HYRF_LAUNCH("k_query_dec", s,
-                  k_query_dec<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(
-                      F, cam, io, X, X + (size_t)io.n * 2 * NL));
-      return HYRF_OK;
+      if constexpr (NL == 16 && WID == 64 && NH == 2) {  // register-tiled decoders
+        const int tiles = (io.n + kDecRows - 1) / kDecRows, grid = min(tiles, 2 * num_sms());
+        const int sg = DecSmemF32<32, 8>::floats * (int)sizeof(float);
+        const int sc = DecSmemF32<32 + kPEPad, 4>::floats * (int)sizeof(float);
+        set_smem_limit<k_query_dec_f32<true>>(sg);
+        set_smem_limit<k_query_dec_f32<false>>(sc);
+        HYRF_LAUNCH("k_query_dec_f32<geo>", s, k_query_dec_f32<true><<<grid, kDecRows, sg, s>>>(F, cam, io, X));
+        HYRF_LAUNCH("k_query_dec_f32<col>", s,
+                    k_query_dec_f32<false><<<grid, kDecRows, sc, s>>>(F, cam, io, X + (size_t)io.n * 2 * NL));
+        return HYRF_OK;
+      }
+      return HYRF_ERR_UNSUPPORTED;  // features are gathered only for the split shape
     }
     HYRF_LAUNCH("k_query_fwd", s,
                 k_query_fwd<NL, WID, NH, WT><<<fwd_blocks(io.n, kFwdThreads), kFwdThreads, 0, s>>>(F, cam, io));
@@ -1090,9 +1255,11 @@ static hyrf_status bg_fwd_impl(const hyrf_composite_background_args& a, const Fi
       const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
       hyrf_status st = launch_gather_f32(F, cam, RS, P, nullptr, Xb, s);
       if (st != HYRF_OK) return st;
-      HYRF_LAUNCH("k_bg_dec", s,
-                  k_bg_dec<NL, WID, NH, WT><<<fwd_blocks(P, kFwdThreads), kFwdThreads, 0, s>>>(
-                      F, cam, a.bg.radius, Xb, a.C_fg, a.T_final, a.C));
+      const int tiles = (P + kDecRows - 1) / kDecRows, grid = min(tiles, 2 * num_sms());
+      const int sb = DecSmemF32<2 * NL + kPEPad, 4>::floats * (int)sizeof(float);
+      set_smem_limit<k_bg_dec_f32<2 * NL>>(sb);
+      HYRF_LAUNCH("k_bg_dec_f32", s,
+                  k_bg_dec_f32<2 * NL><<<grid, kDecRows, sb, s>>>(F, cam, a.bg.radius, Xb, a.C_fg, a.T_final, a.C));
       return HYRF_OK;
     } else {
       HYRF_LAUNCH("k_bg_exact_fwd", s,
