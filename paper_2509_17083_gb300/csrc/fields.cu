@@ -724,6 +724,299 @@ __global__ void __launch_bounds__(kDecRows, 2) k_bg_dec_f32(FieldsDev F, CamDev 
   }
 }
 
+// ---------------------------------------------------------------- FP32 background reverse, register-tiled
+
+// Reverse of the exact background's colour decoder on 128-pixel tiles
+// (256 threads, one persistent CTA per SM): the forward is recomputed into
+// shared memory (input X, H1, H2 feature-major), then dZ flows back layer by
+// layer through the same tile; every product (forward, W^T dZ, dZ A^T) is a
+// CTA-wide product in register blocks. The weight and bias gradients stay
+// in registers over all of the CTA's tiles and are added to its slab once.
+constexpr int kBgbRows = 128;             // pixels per tile
+constexpr int kBgbPitch = kBgbRows + 4;   // floats per feature row of a tile buffer
+
+struct BgbSmem {  // offsets in floats
+  static constexpr int X = 0, H1 = X + 64 * kBgbPitch, H2 = H1 + 64 * kBgbPitch, DZ = H2 + 64 * kBgbPitch,
+                       Wt0 = DZ + 64 * kBgbPitch, Wt1 = Wt0 + 64 * 64, W0 = Wt1 + 64 * 64, W1 = W0 + 64 * 64,
+                       W2 = W1 + 64 * 64, Wt2 = W2 + 4 * 64, b0 = Wt2 + 64 * 4, b1 = b0 + 64, b2 = b1 + 64,
+                       floats = b2 + 4;
+};
+
+// acc[i][j] = sum_k Wk[k][o0 + j] A[k][r0 + i], k < K (Wk row pitch 64, A row
+// pitch kBgbPitch), in k order from zero.
+template <int K, int BO>
+__device__ __forceinline__ void bgb_prod(const float* A, const float* Wk, int r0, int o0, float (&acc)[8][BO]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < BO; ++j) acc[i][j] = 0.0f;
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kBgbPitch + r0);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kBgbPitch + r0 + 4);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    float w[BO];
+    if constexpr (BO == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(Wk + k * 64 + o0);
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    } else {
+      const float2 v = *reinterpret_cast<const float2*>(Wk + k * 64 + o0);
+      w[0] = v.x;
+      w[1] = v.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) acc[i][j] = fmaf(w[j], a[i], acc[i][j]);
+  }
+}
+
+// dW[o0 + a][i0 + c] += sum_r dZ[o0 + a][r] A[i0 + c][r] over the tile's rows.
+__device__ __forceinline__ void bgb_dw(const float* DZ, const float* A, int o0, int i0, float (&dw)[4][4]) {
+#pragma unroll 2
+  for (int r = 0; r < kBgbRows; r += 4) {
+    float4 d[4], x[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) d[a] = *reinterpret_cast<const float4*>(DZ + (o0 + a) * kBgbPitch + r);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = *reinterpret_cast<const float4*>(A + (i0 + c) * kBgbPitch + r);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        dw[a][c] = fmaf(d[a].x, x[c].x, dw[a][c]);
+        dw[a][c] = fmaf(d[a].y, x[c].y, dw[a][c]);
+        dw[a][c] = fmaf(d[a].z, x[c].z, dw[a][c]);
+        dw[a][c] = fmaf(d[a].w, x[c].w, dw[a][c]);
+      }
+  }
+}
+
+// sum_r buf[row][r] over the tile's rows.
+__device__ __forceinline__ float bgb_rowsum(const float* buf, int row) {
+  float s = 0.0f;
+#pragma unroll 4
+  for (int r = 0; r < kBgbRows; r += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(buf + row * kBgbPitch + r);
+    s += (v.x + v.y) + (v.z + v.w);
+  }
+  return s;
+}
+
+// NF: features per pixel (2 x 16 levels). dXb receives dL/dX / loss_scale;
+// the slab (colour decoder's entries, pre-zeroed) dL/dW * loss_scale.
+template <int NF>
+__global__ void __launch_bounds__(256, 1) k_bg_dec_bwd_f32(FieldsDev F, CamDev cam, float radius,
+                                                         const float* __restrict__ T_final,
+                                                         const float* __restrict__ dC, float* __restrict__ dC_fg,
+                                                         float* __restrict__ dT, float loss_scale, SlabLayout SL,
+                                                         float* __restrict__ slabs, const float* __restrict__ Xb,
+                                                         float* __restrict__ dXb) {
+  static_assert(NF == 32 && NF + kPEPad == 64, "16-level grids, 2 x 64 decoder");
+  using L = BgbSmem;
+  extern __shared__ __align__(16) float smf[];
+  float *X = smf + L::X, *H1 = smf + L::H1, *H2 = smf + L::H2, *DZ = smf + L::DZ;
+  const int t = threadIdx.x;
+  {
+    const float* W0g = static_cast<const float*>(F.cm.W[0]);
+    const float* W1g = static_cast<const float*>(F.cm.W[1]);
+    const float* W2g = static_cast<const float*>(F.cm.W[2]);
+    for (int e = t; e < 64 * 64; e += 256) {
+      const int o = e >> 6, i = e & 63;
+      const float v0 = __ldg(W0g + e), v1 = __ldg(W1g + e);
+      smf[L::W0 + e] = v0;
+      smf[L::Wt0 + i * 64 + o] = v0;
+      smf[L::W1 + e] = v1;
+      smf[L::Wt1 + i * 64 + o] = v1;
+    }
+    {
+      const int o = t >> 6, i = t & 63;
+      const float v = o < 3 ? __ldg(W2g + o * 64 + i) : 0.0f;
+      smf[L::W2 + t] = v;
+      smf[L::Wt2 + i * 4 + o] = v;
+    }
+    if (t < 64) {
+      smf[L::b0 + t] = F.cm.b[0][t];
+      smf[L::b1 + t] = F.cm.b[1][t];
+    }
+    if (t < 4) smf[L::b2 + t] = t < 3 ? F.cm.b[2][t] : 0.0f;
+  }
+  const int P = cam.W * cam.H;
+  const int ntile = (P + kBgbRows - 1) / kBgbRows;
+  const float inv_ls = 1.0f / loss_scale;
+  const int r0 = 8 * (t & 15), og = t >> 4;  // product blocks: rows r0.., outputs 4 og.. (2 og.. for dX)
+  const int dob = t >> 4, dib = t & 15;      // weight-gradient blocks: outputs 4 dob.., inputs 4 dib..
+  float dw0[4][4], dw1[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dw0[a][c] = dw1[a][c] = 0.0f;
+  float dw2 = 0.0f;  // output t >> 6, input t & 63
+  float db = 0.0f;   // t < 64: b1[t]; t < 128: b0[t - 64]; t < 131: b2[t - 128]
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int pbase = tile * kBgbRows;
+    // inputs: the pixel's features (threads < 128) and its direction's
+    // positional encoding (threads >= 128)
+    if (t < kBgbRows) {
+      const int p = pbase + t;
+      float x[32];
+      if (p < P) load_row<32>(Xb + (size_t)p * 32, x);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) X[k * kBgbPitch + t] = p < P ? x[k] : 0.0f;
+    } else {
+      const int r = t - kBgbRows, p = pbase + r, q = p < P ? p : 0;
+      float ps[3], dir[3], pe[kPEPad];
+      bg_ray(cam, F, radius, q % cam.W, q / cam.W, ps, dir);
+      pos_enc(dir, pe);
+#pragma unroll
+      for (int k = 0; k < kPEPad; ++k) X[(32 + k) * kBgbPitch + r] = pe[k];
+    }
+    __syncthreads();
+    // forward: H1 = ReLU(W0 X + b0), H2 = ReLU(W1 H1 + b1)
+#pragma unroll 1
+    for (int layer = 0; layer < 2; ++layer) {
+      const float* A = layer == 0 ? X : H1;
+      float* Hout = layer == 0 ? H1 : H2;
+      const float* b = smf + (layer == 0 ? L::b0 : L::b1);
+      float acc[8][4];
+      bgb_prod<64, 4>(A, smf + (layer == 0 ? L::Wt0 : L::Wt1), r0, 4 * og, acc);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float bj = b[4 * og + j];
+        float* dst = Hout + (4 * og + j) * kBgbPitch + r0;
+        *reinterpret_cast<float4*>(dst) = make_float4(fmaxf(acc[0][j] + bj, 0.0f), fmaxf(acc[1][j] + bj, 0.0f),
+                                                      fmaxf(acc[2][j] + bj, 0.0f), fmaxf(acc[3][j] + bj, 0.0f));
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(fmaxf(acc[4][j] + bj, 0.0f), fmaxf(acc[5][j] + bj, 0.0f),
+                                                          fmaxf(acc[6][j] + bj, 0.0f), fmaxf(acc[7][j] + bj, 0.0f));
+      }
+      __syncthreads();
+    }
+    // output layer, colour and dL/dz (Eq. 11; one thread per pixel)
+    if (t < kBgbRows) {
+      const int p = pbase + t;
+      const bool ok = p < P;
+      float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+      for (int k = 0; k < 64; ++k) {
+        const float h = H2[k * kBgbPitch + t];
+        const float4 w = *reinterpret_cast<const float4*>(smf + L::Wt2 + 4 * k);
+        o[0] = fmaf(w.x, h, o[0]);
+        o[1] = fmaf(w.y, h, o[1]);
+        o[2] = fmaf(w.z, h, o[2]);
+      }
+      float cs[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cs[k] = sigmoidf_(o[k] + smf[L::b2 + k]);
+      const float T = ok ? T_final[p] : 0.0f;
+      float dt = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float g = ok ? dC[3 * (int64_t)p + k] : 0.0f;
+        dt += g * cs[k];
+        if (ok && dC_fg) dC_fg[3 * (int64_t)p + k] = g;
+        DZ[k * kBgbPitch + t] = g * T * loss_scale * cs[k] * (1.0f - cs[k]);
+      }
+      DZ[3 * kBgbPitch + t] = 0.0f;
+      if (ok && dT) dT[p] = dt;
+    }
+    __syncthreads();
+    // output layer's gradients; dH2 = W2^T dz masked by H2 > 0
+    {
+      const int o = t >> 6, i = t & 63;
+#pragma unroll 4
+      for (int r = 0; r < kBgbRows; r += 4) {
+        const float4 d = *reinterpret_cast<const float4*>(DZ + o * kBgbPitch + r);
+        const float4 h = *reinterpret_cast<const float4*>(H2 + i * kBgbPitch + r);
+        dw2 = fmaf(d.x, h.x, dw2);
+        dw2 = fmaf(d.y, h.y, dw2);
+        dw2 = fmaf(d.z, h.z, dw2);
+        dw2 = fmaf(d.w, h.w, dw2);
+      }
+      if (t >= 128 && t < 131) db += bgb_rowsum(DZ, t - 128);
+    }
+    {
+      const int r = t & (kBgbRows - 1), half = t >> 7;
+      float dh[32];
+#pragma unroll
+      for (int m = 0; m < 32; ++m) dh[m] = 0.0f;
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const float d = DZ[o * kBgbPitch + r];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) dh[m] = fmaf(smf[L::W2 + o * 64 + 32 * half + m], d, dh[m]);
+      }
+      __syncthreads();  // dz of the output layer has been read
+#pragma unroll
+      for (int m = 0; m < 32; ++m) {
+        const int i = 32 * half + m;
+        DZ[i * kBgbPitch + r] = H2[i * kBgbPitch + r] > 0.0f ? dh[m] : 0.0f;
+      }
+    }
+    __syncthreads();
+    // second hidden layer's gradients; dH1 = W1^T dZ masked by H1 > 0
+    bgb_dw(DZ, H1, 4 * dob, 4 * dib, dw1);
+    if (t < 64) db += bgb_rowsum(DZ, t);
+    {
+      float acc[8][4];
+      bgb_prod<64, 4>(DZ, smf + L::W1, r0, 4 * og, acc);
+      __syncthreads();  // dZ has been read
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = 4 * og + j;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 m = *reinterpret_cast<const float4*>(H1 + i * kBgbPitch + r0 + 4 * h);
+          *reinterpret_cast<float4*>(DZ + i * kBgbPitch + r0 + 4 * h) =
+              make_float4(m.x > 0.0f ? acc[4 * h][j] : 0.0f, m.y > 0.0f ? acc[4 * h + 1][j] : 0.0f,
+                          m.z > 0.0f ? acc[4 * h + 2][j] : 0.0f, m.w > 0.0f ? acc[4 * h + 3][j] : 0.0f);
+        }
+      }
+    }
+    __syncthreads();
+    // first layer's gradients; dX = W0^T dZ for the features (inputs < 32)
+    bgb_dw(DZ, X, 4 * dob, 4 * dib, dw0);
+    if (t >= 64 && t < 128) db += bgb_rowsum(DZ, t - 64);
+    {
+      float acc[8][2];
+      bgb_prod<64, 2>(DZ, smf + L::W0, r0, 2 * og, acc);
+      __syncthreads();  // X has been read
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          *reinterpret_cast<float4*>(X + (2 * og + j) * kBgbPitch + r0 + 4 * h) =
+              make_float4(acc[4 * h][j] * inv_ls, acc[4 * h + 1][j] * inv_ls, acc[4 * h + 2][j] * inv_ls,
+                          acc[4 * h + 3][j] * inv_ls);
+    }
+    __syncthreads();
+    if (t < kBgbRows && pbase + t < P) {
+      float4* d4 = reinterpret_cast<float4*>(dXb + (size_t)(pbase + t) * 32);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        __stcs(d4 + k, make_float4(X[(4 * k) * kBgbPitch + t], X[(4 * k + 1) * kBgbPitch + t],
+                                   X[(4 * k + 2) * kBgbPitch + t], X[(4 * k + 3) * kBgbPitch + t]));
+    }
+    __syncthreads();  // X is rewritten by the next tile
+  }
+  float* slab = slabs + (size_t)blockIdx.x * SL.total;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int e = (4 * dob + a) * 64 + 4 * dib + c;
+      slab[SL.off_W[1][0] + e] += dw0[a][c];
+      slab[SL.off_W[1][1] + e] += dw1[a][c];
+    }
+  if ((t >> 6) < 3) slab[SL.off_W[1][2] + t] += dw2;
+  if (t < 64) slab[SL.off_b[1][1] + t] += db;
+  else if (t < 128) slab[SL.off_b[1][0] + t - 64] += db;
+  else if (t < 131) slab[SL.off_b[1][2] + t - 128] += db;
+}
+
 template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kFwdThreads) k_bg_map_texels(FieldsDev F, int Hb, int Wb, float radius,
                                                                float* __restrict__ map) {
@@ -814,16 +1107,12 @@ __global__ void __launch_bounds__(256) k_bg_map_bwd_pix(FieldsDev F, CamDev cam,
 // Reverse of the colour field at background points: MODE 0 = one point per
 // pixel (exact mode, also writes dL/dT_final and dL/dC_fg), MODE 1 = one
 // point per map texel with the texel gradient given in dmap.
-// SPLIT (exact mode, FP32 split path): the features come from k_gather_f32
-// (Xb [W H][2 NL]) and the feature gradients go to dXb [W H][2 NL] for the
-// table scatter (k_scatter, gather.cu) instead of being gathered and
-// scattered here.
-template <int NL, int WID, int NH, int MODE, class WT, bool SPLIT = false>
+template <int NL, int WID, int NH, int MODE, class WT>
 __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     FieldsDev F, CamDev cam, float radius, int Hb, int Wb, const float* __restrict__ T_final,
     const float* __restrict__ dC, float* __restrict__ dC_fg, float* __restrict__ dT,
     const float* __restrict__ dmap, float* __restrict__ g_rad_table, float loss_scale,
-    SlabLayout SL, float* slabs, const float* __restrict__ Xb = nullptr, float* __restrict__ dXb = nullptr) {
+    SlabLayout SL, float* slabs) {
   extern __shared__ float sm[];
   constexpr int NG = 2 * NL, NC = NG + kPEPad;
   float* act = sm;
@@ -845,11 +1134,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
       texel_point(ee / Wb, ee % Wb, Hb, Wb, radius, y, dir);
     }
     float x0[NC], out[3], dz3[3];
-    if constexpr (SPLIT) {
-      load_row<NG>(Xb + (size_t)ee * NG, x0);
-    } else {
-      encode<NL>(F.rad, y, x0);
-    }
+    encode<NL>(F.rad, y, x0);
     pos_enc(dir, x0 + NG);
     decoder_fwd_store<NC, WID, NH, 3, WT>(F.cm, x0, act, out);
     float cs[3];
@@ -877,13 +1162,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bg_field_bwd(
     if (ok) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
-      if constexpr (SPLIT) {
-        float4* d4 = reinterpret_cast<float4*>(dXb + (size_t)ee * NG);
-#pragma unroll
-        for (int k = 0; k < NG / 4; ++k) __stcs(d4 + k, make_float4(dx[4 * k], dx[4 * k + 1], dx[4 * k + 2], dx[4 * k + 3]));
-      } else {
-        encode_bwd<NL, true>(F.rad, y, dx, g_rad_table, nullptr);
-      }
+      encode_bwd<NL, true>(F.rad, y, dx, g_rad_table, nullptr);
     }
   }
 }
@@ -1295,13 +1574,14 @@ static hyrf_status bg_bwd_impl(const hyrf_composite_background_backward_args& b,
       const RowSource RS{1, 0, nullptr, nullptr, nullptr, a.bg.radius, a.status, nullptr, nullptr};
       hyrf_status st = launch_gather_f32(F, cam, RS, P, nullptr, Xb, s);
       if (st != HYRF_OK) return st;
-      const size_t smem = query_bwd_smem_floats<NL, WID, NH>() * sizeof(float);
-      set_smem_limit<k_bg_field_bwd<NL, WID, NH, 0, WT, true>>((int)smem);
-      HYRF_LAUNCH("k_bg_dec_bwd", s,
-                  k_bg_field_bwd<NL, WID, NH, 0, WT, true><<<ctas, kBwdThreads, smem, s>>>(
-                      F, cam, a.bg.radius, 0, 0, a.T_final, b.d_C, b.d_C_fg, b.d_T_final, nullptr, nullptr,
-                      b.loss_scale, SL, slabs, Xb, dXb));
-      st = launch_slab_reduce(slabs, ctas, SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
+      const int tiles = (P + kBgbRows - 1) / kBgbRows;
+      const int grid = min(min(ctas, num_sms()), tiles);
+      const int smem = BgbSmem::floats * (int)sizeof(float);
+      set_smem_limit<k_bg_dec_bwd_f32<2 * NL>>(smem);
+      HYRF_LAUNCH("k_bg_dec_bwd_f32", s,
+                  k_bg_dec_bwd_f32<2 * NL><<<grid, 256, smem, s>>>(F, cam, a.bg.radius, a.T_final, b.d_C, b.d_C_fg,
+                                                                b.d_T_final, b.loss_scale, SL, slabs, Xb, dXb));
+      st = launch_slab_reduce(slabs, grid, SL, slab_targets(b.grads, false), 1.0f / b.loss_scale, s);
       if (st != HYRF_OK) return st;
       return launch_scatter(F, cam, RS, P, nullptr, dXb, nullptr, b.grads.rad_table, nullptr, s);
     }
