@@ -55,30 +55,86 @@ constexpr int oW0g = 0, oW1g = oW0g + 64 * 32 * 2, oW2g = oW1g + 64 * 64 * 2, oW
 constexpr uint32_t kQueryTmemCols = 128;
 
 // One point's inputs, fetched a tile ahead into registers so that their
-// global loads overlap the previous tile's MMA chain.
+// global loads overlap the previous tile's MMA chain: its features (by row
+// index), position and explicit parameters (by its Gaussian id, itself
+// read one tile earlier still), so no load waits on another. Nothing
+// branches on a loaded value until the next tile uses it.
 struct QueryRow {
-  uint4 x[4];  // 32 bf16 hash features
-  float p[3];  // position (colour rows)
+  uint4 x[4];  // 32 bf16 hash features of this thread's field
+  float p[3];  // position
+  float e[3];  // explicit parameters: alpha_e, scale_e (geometry) or colour_e (colour)
   int i, g;
   bool ok;
 };
 
-__device__ __forceinline__ void fetch_row(const QueryIO& io, const FieldsDev& F, bool geo, int i, int nv,
-                                          QueryRow& q) {
+__device__ __forceinline__ void fetch_row(const QueryIO& io, bool geo, int i, int g, bool ok, QueryRow& q) {
   q.i = i;
-  q.ok = i < nv;
-  q.g = q.ok ? io.vis_ids[i] : 0;
-  if (q.ok && (q.g < 0 || q.g >= io.n)) {
-    set_status(io.status, HYRF_ERR_BOUNDS);
-    q.ok = false;
-    q.g = 0;
+  q.g = g;
+  q.ok = ok;
+  const int ii = ok ? i : 0, gg = ok ? g : 0;  // (row 0 and Gaussian 0 exist whenever a tile runs)
+  const uint4* s4 = reinterpret_cast<const uint4*>((geo ? io.Xg : io.Xr) + (size_t)ii * 16);
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) q.x[kc] = __ldg(s4 + kc);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) q.p[k] = io.pos[3 * (int64_t)gg + k];
+  if (geo) {
+    q.e[0] = io.alpha_e ? io.alpha_e[gg] : 0.0f;
+    q.e[1] = io.scale_e ? io.scale_e[gg] : 0.0f;
+    q.e[2] = 0.0f;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q.e[k] = io.color_e ? io.color_e[3 * (int64_t)gg + k] : 0.0f;
   }
-  const uint4* s4 = reinterpret_cast<const uint4*>((geo ? io.Xg : io.Xr) + (size_t)(q.ok ? i : 0) * 16);
+}
+
+// Visible row i of a tile (or none) and its Gaussian id g, read earlier:
+// whether the row is processed; an id out of range is reported.
+__device__ __forceinline__ bool row_ok(const QueryIO& io, int i, int nv, int g) {
+  if (i >= nv) return false;
+  if (g < 0 || g >= io.n) {
+    set_status(io.status, HYRF_ERR_BOUNDS);
+    return false;
+  }
+  return true;
+}
+
+// Half of the positional encoding of pos_enc (field_ops.cuh), columns
+// [16 HALF, 16 HALF + 16): the same sincospif calls, so the same values.
+template <int HALF>
+__device__ __forceinline__ void pos_enc_half(const float d[3], float* v) {
+  if constexpr (HALF == 0) {  // d, frequencies 1 and 2, and sin(4 pi d0)
 #pragma unroll
-  for (int kc = 0; kc < 4; ++kc) q.x[kc] = q.ok ? __ldg(s4 + kc) : make_uint4(0u, 0u, 0u, 0u);
-  if (!geo) {
+    for (int j = 0; j < 3; ++j) v[j] = d[j];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) q.p[k] = q.ok ? io.pos[3 * (int64_t)q.g + k] : F.lo[k] + 1.0f / F.sx[k];
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float sn, cs;
+        sincospif((float)(1 << k) * d[j], &sn, &cs);
+        v[3 + 6 * k + j] = sn;
+        v[3 + 6 * k + 3 + j] = cs;
+      }
+    float sn, cs;
+    sincospif(4.0f * d[0], &sn, &cs);
+    v[15] = sn;
+  } else {  // the rest of frequency 4, frequency 8, zero padding
+    static_assert(kPEFreq == 4 && kPEPad == 32, "positional-encoding layout");
+    float s2[3], c2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sincospif(4.0f * d[j], &s2[j], &c2[j]);
+    v[0] = s2[1];
+    v[1] = s2[2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[2 + j] = c2[j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float sn, cs;
+      sincospif(8.0f * d[j], &sn, &cs);
+      v[5 + j] = sn;
+      v[8 + j] = cs;
+    }
+#pragma unroll
+    for (int j = 11; j < 16; ++j) v[j] = 0.0f;
   }
 }
 
@@ -134,21 +190,38 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
   const int ntile = (nv + 127) / 128;
   uint32_t phase = 0;
   bool failed = false;
+  const int G = gridDim.x;
   QueryRow cur;
-  if ((int)blockIdx.x < ntile) fetch_row(io, F, geo, blockIdx.x * 128 + r, nv, cur);
-  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+  int gn = 0;  // Gaussian id of this thread's row of the next tile (read a tile ahead)
+  if ((int)blockIdx.x < ntile) {
+    const int i0 = blockIdx.x * 128 + r, i1 = (blockIdx.x + G) * 128 + r;
+    const int g0 = i0 < nv ? io.vis_ids[i0] : 0;
+    fetch_row(io, geo, i0, g0, row_ok(io, i0, nv, g0), cur);
+    if ((int)blockIdx.x + G < ntile && i1 < nv) gn = io.vis_ids[i1];
+  }
+  for (int tile = blockIdx.x; tile < ntile && !failed; tile += G) {
     // this tile's rows -> A operands (the previous tile's last MMA, the
-    // only reader of these buffers, has completed)
+    // only reader of these buffers, has completed): the features, and
+    // half of the colour input's positional encoding from each of the
+    // row's two threads
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc)
       *reinterpret_cast<uint4*>(sm + (geo ? oAg : oAc) + kmaj(r, 8 * kc, geo ? 32 : 64)) = cur.x[kc];
-    if (!geo) {
-      float v[3] = {cur.p[0] - pc[0], cur.p[1] - pc[1], cur.p[2] - pc[2]};
+    {
+      float p[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) p[k] = cur.ok ? cur.p[k] : F.lo[k] + 1.0f / F.sx[k];  // box centre when idle
+      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
       const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
-      float pe[32];
-      pos_enc(dir, pe);
-      store_cols<64, 32, 32, H16>(sm + oAc, r, pe);
+      float pe[16];
+      if (geo) {
+        pos_enc_half<0>(dir, pe);
+        store_cols<64, 32, 16, H16>(sm + oAc, r, pe);
+      } else {
+        pos_enc_half<1>(dir, pe);
+        store_cols<64, 48, 16, H16>(sm + oAc, r, pe);
+      }
     }
     fence_smem_async();
     fence_before();
@@ -159,9 +232,14 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
       gemm<64, 64, H16>(tm + 64, sm + oAc, sm + oW0c);
       commit(&bar);
     }
-    // the next tile's inputs, in flight during this tile's MMA chain
+    // the next tile's inputs, in flight during this tile's MMA chain, and
+    // the Gaussian ids of the one after
     const QueryRow q = cur;
-    if (tile + (int)gridDim.x < ntile) fetch_row(io, F, geo, (tile + gridDim.x) * 128 + r, nv, cur);
+    if (tile + G < ntile) {
+      const int i1 = (tile + G) * 128 + r, i2 = (tile + 2 * G) * 128 + r;
+      fetch_row(io, geo, i1, gn, row_ok(io, i1, nv, gn), cur);
+      gn = (tile + 2 * G < ntile && i2 < nv) ? io.vis_ids[i2] : 0;
+    }
     if (!wait_phase(&bar, phase)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
@@ -193,12 +271,12 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
     fence_after();
     float o[16];
     ld16(tm + lane + colD, o);
-    const int i = q.i, g = q.g;
+    const int i = q.i;
     if (q.ok) {
       if (geo) {
         // Eq. 7: alpha, scale from the geometry decoder, rotation normalised
-        io.alpha[i] = sigmoidf_(o[0] + b2[0] + (io.alpha_e ? io.alpha_e[g] : 0.0f));
-        const float se = io.scale_e ? io.scale_e[g] : 0.0f;
+        io.alpha[i] = sigmoidf_(o[0] + b2[0] + q.e[0]);
+        const float se = q.e[1];
 #pragma unroll
         for (int k = 0; k < 3; ++k) io.scale[3 * i + k] = sigmoidf_(o[1 + k] + b2[1 + k] + se);
         float qq[4];
@@ -211,7 +289,7 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
       } else {
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-          io.color[3 * i + k] = sigmoidf_(o[k] + b2[k] + (io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f));
+          io.color[3 * i + k] = sigmoidf_(o[k] + b2[k] + q.e[k]);
       }
     }
     // (the next tile's first MMA, which overwrites these tensor-memory
