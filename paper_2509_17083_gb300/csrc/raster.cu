@@ -56,6 +56,44 @@ __device__ __forceinline__ bool splat_alpha(float power, float pmin, float o, fl
   return alpha >= kAlphaMin;
 }
 
+// Paired FP32 arithmetic (two independent round-to-nearest operations per
+// instruction, the same values as the scalar ones): the compositing reverse
+// runs two pixels per thread through one instruction stream.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 p, q;\nmov.b64 p, {%2, %3};\nmov.b64 q, {%4, %5};\nadd.rn.f32x2 p, p, q;\n"
+      "mov.b64 {%0, %1}, p;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 p, q;\nmov.b64 p, {%2, %3};\nmov.b64 q, {%4, %5};\nsub.rn.f32x2 p, p, q;\n"
+      "mov.b64 {%0, %1}, p;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 p, q;\nmov.b64 p, {%2, %3};\nmov.b64 q, {%4, %5};\nmul.rn.f32x2 p, p, q;\n"
+      "mov.b64 {%0, %1}, p;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// a b + c
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n.reg .b64 p, q, r;\nmov.b64 p, {%2, %3};\nmov.b64 q, {%4, %5};\nmov.b64 r, {%6, %7};\n"
+      "fma.rn.f32x2 p, p, q, r;\nmov.b64 {%0, %1}, p;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 pbc(float s) { return make_float2(s, s); }
+
 // Asynchronous global -> shared copies (cp.async, L1-allocating): a batch
 // of records lands in shared memory while the previous batch is composited.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -373,32 +411,80 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
       const float cadx2 = r0.z * dx * dx, cbdx = r0.w * dx;
       float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, dop = 0.0f, dc0 = 0.0f, dc1 = 0.0f, dc2 = 0.0f;
       bool any = false;
+      if constexpr (P == 2) {
+        // both pixels through one instruction stream (paired FP32 operations,
+        // the same values as the per-pixel code below): a pixel that does
+        // not take this Gaussian keeps its state (selects) and adds zeros
+        const float2 dy = psub(pbc(r0.y), make_float2(fy[0], fy[1]));
+        const float2 pw = pfma(pbc(-0.5f), pfma(pmul(pbc(r1.x), dy), dy, pbc(cadx2)), pmul(pbc(-cbdx), dy));
+        float G0 = 0.0f, a0 = 0.0f, G1 = 0.0f, a1 = 0.0f;
+        const bool c0 = pos < last[0] && splat_alpha(pw.x, r2.y, r1.y, G0, a0);
+        const bool c1 = pos < last[1] && splat_alpha(pw.y, r2.y, r1.y, G1, a1);
+        if (__any_sync(0xffffffffu, c0 || c1)) {
+          any = c0 || c1;
+          const float2 G = make_float2(c0 ? G0 : 0.0f, c1 ? G1 : 0.0f);
+          const float2 al = make_float2(c0 ? a0 : 0.0f, c1 ? a1 : 0.0f);
+          const float2 om = psub(pbc(1.0f), al);  // >= 0.01
+          const float2 inv = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+          const float2 Tn = pmul(make_float2(T[0], T[1]), inv);  // T before this Gaussian
+          T[0] = c0 ? Tn.x : T[0];
+          T[1] = c1 ? Tn.y : T[1];
+          const float2 T2 = make_float2(T[0], T[1]);
+          const float2 So = make_float2(S[0], S[1]);
+          const float2 Sn = pfma(make_float2(la[0], la[1]), psub(make_float2(ls[0], ls[1]), So), So);
+          S[0] = c0 ? Sn.x : S[0];
+          S[1] = c1 ? Sn.y : S[1];
+          const float2 g0v = make_float2(g0[0], g0[1]), g1v = make_float2(g1[0], g1[1]),
+                       g2v = make_float2(g2[0], g2[1]);
+          const float2 cg = pfma(pbc(r2.x), g2v, pfma(pbc(r1.w), g1v, pmul(pbc(r1.z), g0v)));
+          la[0] = c0 ? al.x : la[0];
+          la[1] = c1 ? al.y : la[1];
+          ls[0] = c0 ? cg.x : ls[0];
+          ls[1] = c1 ? cg.y : ls[1];
+          const float2 w = pmul(al, T2);
+          dc0 = fmaf(w.y, g0v.y, w.x * g0v.x);
+          dc1 = fmaf(w.y, g1v.y, w.x * g1v.x);
+          dc2 = fmaf(w.y, g2v.y, w.x * g2v.x);
+          const float2 dal =
+              pfma(make_float2(-gTf[0], -gTf[1]), inv, pmul(psub(cg, make_float2(S[0], S[1])), T2));
+          const float2 oG = pmul(pbc(r1.y), G);  // alpha not clamped where o G <= 0.99
+          const float2 dm = make_float2(c0 && oG.x <= kAlphaMax ? dal.x : 0.0f,
+                                        c1 && oG.y <= kAlphaMax ? dal.y : 0.0f);
+          dop = fmaf(dm.y, G.y, dm.x * G.x);
+          const float2 dp = pmul(dm, al);
+          const float2 e = pmul(dp, dy);
+          D0 = dp.x + dp.y;
+          D1 = e.x + e.y;
+          D2 = fmaf(e.y, dy.y, e.x * dy.x);
+        }
+      } else {
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const float dy = r0.y - fy[k];
-        const float power = splat_power(cadx2, cbdx, r1.x, dy);
-        float G = 0.0f, alpha = 0.0f;
-        const bool c = pos < last[k] && splat_alpha(power, r2.y, r1.y, G, alpha);
-        if (__any_sync(0xffffffffu, c) && c) {
-          any = true;
-          const float inv = __fdividef(1.0f, 1.0f - alpha);  // 1 - alpha >= 0.01
-          T[k] *= inv;                                       // T before this Gaussian
-          S[k] = fmaf(la[k], ls[k] - S[k], S[k]);            // behind: previous contributor over the rest
-          const float cg = fmaf(r2.x, g2[k], fmaf(r1.w, g1[k], r1.z * g0[k]));
-          la[k] = alpha;
-          ls[k] = cg;
-          const float w = alpha * T[k];
-          dc0 = fmaf(w, g0[k], dc0);
-          dc1 = fmaf(w, g1[k], dc1);
-          dc2 = fmaf(w, g2[k], dc2);
-          const float dal = fmaf(-gTf[k], inv, (cg - S[k]) * T[k]);
-          if (r1.y * G <= kAlphaMax) {  // alpha not clamped
-            dop = fmaf(dal, G, dop);
-            const float dp = dal * alpha;
-            const float e = dp * dy;
-            D0 += dp;
-            D1 += e;
-            D2 = fmaf(e, dy, D2);
+        for (int k = 0; k < P; ++k) {
+          const float dy = r0.y - fy[k];
+          const float power = splat_power(cadx2, cbdx, r1.x, dy);
+          float G = 0.0f, alpha = 0.0f;
+          const bool c = pos < last[k] && splat_alpha(power, r2.y, r1.y, G, alpha);
+          if (__any_sync(0xffffffffu, c) && c) {
+            any = true;
+            const float inv = __fdividef(1.0f, 1.0f - alpha);  // 1 - alpha >= 0.01
+            T[k] *= inv;                                       // T before this Gaussian
+            S[k] = fmaf(la[k], ls[k] - S[k], S[k]);            // behind: previous contributor over the rest
+            const float cg = fmaf(r2.x, g2[k], fmaf(r1.w, g1[k], r1.z * g0[k]));
+            la[k] = alpha;
+            ls[k] = cg;
+            const float w = alpha * T[k];
+            dc0 = fmaf(w, g0[k], dc0);
+            dc1 = fmaf(w, g1[k], dc1);
+            dc2 = fmaf(w, g2[k], dc2);
+            const float dal = fmaf(-gTf[k], inv, (cg - S[k]) * T[k]);
+            if (r1.y * G <= kAlphaMax) {  // alpha not clamped
+              dop = fmaf(dal, G, dop);
+              const float dp = dal * alpha;
+              const float e = dp * dy;
+              D0 += dp;
+              D1 += e;
+              D2 = fmaf(e, dy, D2);
+            }
           }
         }
       }
