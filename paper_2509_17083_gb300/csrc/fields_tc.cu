@@ -98,53 +98,17 @@ __device__ __forceinline__ bool row_ok(const QueryIO& io, int i, int nv, int g) 
   return true;
 }
 
-// Half of the positional encoding of pos_enc (field_ops.cuh), columns
-// [16 HALF, 16 HALF + 16): the same sincospif calls, so the same values.
-template <int HALF>
-__device__ __forceinline__ void pos_enc_half(const float d[3], float* v) {
-  if constexpr (HALF == 0) {  // d, frequencies 1 and 2, and sin(4 pi d0)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) v[j] = d[j];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        float sn, cs;
-        sincospif((float)(1 << k) * d[j], &sn, &cs);
-        v[3 + 6 * k + j] = sn;
-        v[3 + 6 * k + 3 + j] = cs;
-      }
-    float sn, cs;
-    sincospif(4.0f * d[0], &sn, &cs);
-    v[15] = sn;
-  } else {  // the rest of frequency 4, frequency 8, zero padding
-    static_assert(kPEFreq == 4 && kPEPad == 32, "positional-encoding layout");
-    float s2[3], c2[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) sincospif(4.0f * d[j], &s2[j], &c2[j]);
-    v[0] = s2[1];
-    v[1] = s2[2];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) v[2 + j] = c2[j];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float sn, cs;
-      sincospif(8.0f * d[j], &sn, &cs);
-      v[5 + j] = sn;
-      v[8 + j] = cs;
-    }
-#pragma unroll
-    for (int j = 11; j < 16; ++j) v[j] = 0.0f;
-  }
-}
-
 template <bool H16>
 __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam, QueryIO io) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bars[2];  // one per decoder group
   __shared__ uint32_t tmem_base;
   const int t = threadIdx.x, w = t >> 5, r = t & 127;
   const bool geo = t < 128;
+  // the two decoders run as independent 128-thread groups: own MMA issuer,
+  // barrier and named barrier, so neither waits for the other's phases
+  const int gid = geo ? 1 : 2;
+  uint64_t* bar = &bars[geo ? 0 : 1];
   float* bias = reinterpret_cast<float*>(sm + oBias);
   float *b0g = bias, *b1g = bias + 64, *b2g = bias + 128, *b0c = bias + 144, *b1c = bias + 208,
         *b2c = bias + 272;
@@ -165,7 +129,8 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
     b2c[t] = t < 3 ? F.cm.b[2][t] : 0.0f;
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bars[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (w == 0) {
@@ -207,30 +172,25 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc)
       *reinterpret_cast<uint4*>(sm + (geo ? oAg : oAc) + kmaj(r, 8 * kc, geo ? 32 : 64)) = cur.x[kc];
-    {
+    if (!geo) {
       float p[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) p[k] = cur.ok ? cur.p[k] : F.lo[k] + 1.0f / F.sx[k];  // box centre when idle
       float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
       const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       const float dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
-      float pe[16];
-      if (geo) {
-        pos_enc_half<0>(dir, pe);
-        store_cols<64, 32, 16, H16>(sm + oAc, r, pe);
-      } else {
-        pos_enc_half<1>(dir, pe);
-        store_cols<64, 48, 16, H16>(sm + oAc, r, pe);
-      }
+      float pe[32];
+      pos_enc(dir, pe);
+      store_cols<64, 32, 32, H16>(sm + oAc, r, pe);
     }
     fence_smem_async();
     fence_before();
-    __syncthreads();
+    group_sync(gid);
     fence_after();
-    if (t == 0) {
-      gemm<64, 32, H16>(tm + 0, sm + oAg, sm + oW0g);
-      gemm<64, 64, H16>(tm + 64, sm + oAc, sm + oW0c);
-      commit(&bar);
+    if (r == 0) {
+      if (geo) gemm<64, 32, H16>(tm + 0, sm + oAg, sm + oW0g);
+      else gemm<64, 64, H16>(tm + 64, sm + oAc, sm + oW0c);
+      commit(bar);
     }
     // the next tile's inputs, in flight during this tile's MMA chain, and
     // the Gaussian ids of the one after
@@ -240,33 +200,33 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
       fetch_row(io, geo, i1, gn, row_ok(io, i1, nv, gn), cur);
       gn = (tile + 2 * G < ntile && i2 < nv) ? io.vis_ids[i2] : 0;
     }
-    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    if (!wait_phase_group(bar, phase, gid)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     epilogue_relu64<H16>(tm + lane + colD, b0, Hs, r);
     fence_smem_async();
     fence_before();
-    __syncthreads();
+    group_sync(gid);
     fence_after();
-    if (t == 0) {
-      gemm<64, 64, H16>(tm + 0, sm + oHg, sm + oW1g);
-      gemm<64, 64, H16>(tm + 64, sm + oHc, sm + oW1c);
-      commit(&bar);
+    if (r == 0) {
+      if (geo) gemm<64, 64, H16>(tm + 0, sm + oHg, sm + oW1g);
+      else gemm<64, 64, H16>(tm + 64, sm + oHc, sm + oW1c);
+      commit(bar);
     }
-    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    if (!wait_phase_group(bar, phase, gid)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     epilogue_relu64<H16>(tm + lane + colD, b1, Hs, r);
     fence_smem_async();
     fence_before();
-    __syncthreads();
+    group_sync(gid);
     fence_after();
-    if (t == 0) {
-      gemm<16, 64, H16>(tm + 0, sm + oHg, sm + oW2g);
-      gemm<16, 64, H16>(tm + 64, sm + oHc, sm + oW2c);
-      commit(&bar);
+    if (r == 0) {
+      if (geo) gemm<16, 64, H16>(tm + 0, sm + oHg, sm + oW2g);
+      else gemm<16, 64, H16>(tm + 64, sm + oHc, sm + oW2c);
+      commit(bar);
     }
-    if (!wait_phase(&bar, phase)) { failed = true; break; }
+    if (!wait_phase_group(bar, phase, gid)) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     float o[16];
@@ -299,7 +259,7 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
   if (failed) {
     set_status(io.status, HYRF_ERR_TIMEOUT);
     for (uint32_t it = 0; it < kSpin; ++it)
-      if (try_wait(&bar, phase)) break;
+      if (try_wait(bar, phase)) break;
   }
   fence_before();
   __syncthreads();
