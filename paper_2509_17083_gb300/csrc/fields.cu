@@ -110,14 +110,6 @@ __device__ __forceinline__ void load_row(const float* __restrict__ src, float* x
   }
 }
 
-// N floats from registers to a 16-byte aligned row (streaming stores).
-template <int N>
-__device__ __forceinline__ void store_row(float* __restrict__ dst, const float* x) {
-  float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-  for (int k = 0; k < N / 4; ++k) __stcs(d4 + k, make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]));
-}
-
 template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kFwdThreads) k_query_fwd(FieldsDev F, CamDev cam, QueryFwdIO io) {
   constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
@@ -213,18 +205,9 @@ constexpr int query_bwd_smem_floats() {
   return (2 * NL + kPEPad + NH * WID) * kActPitch + WID * kActPitch;
 }
 
-// SPLIT (FP32 split path): row k of the list takes its features from X*[k]
-// (k_gather_f32 over the listed rows) and leaves its feature gradients in
-// dX*[k] for the table scatter (k_scatter, gather.cu, which also adds the
-// contraction's share of dL/dp); only the positional encoding's share of
-// dL/dp is added here.
-template <int NL, int WID, int NH, class WT, bool SPLIT = false>
+template <int NL, int WID, int NH, class WT>
 __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev cam, QueryBwdIO io,
-                                                           SlabLayout SL, float* slabs,
-                                                           const float* __restrict__ Xg = nullptr,
-                                                           const float* __restrict__ Xr = nullptr,
-                                                           float* __restrict__ dXg = nullptr,
-                                                           float* __restrict__ dXr = nullptr) {
+                                                           SlabLayout SL, float* slabs) {
   extern __shared__ float sm[];
   constexpr int NG = 2 * NL, NC = 2 * NL + kPEPad;
   float* act = sm;
@@ -253,8 +236,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     for (int k = 0; k < 3; ++k)
       p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];  // box centre when idle
     float y[3], J[9];
-    if constexpr (!SPLIT) contract_p(F, p, y, J);
-    const size_t k_row = (size_t)(base + t);  // list position (the split path's X / dX row)
+    contract_p(F, p, y, J);
     float da = 0.0f, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dcol[3] = {0, 0, 0};
     float ae = 0.0f, se = 0.0f, ce[3] = {0, 0, 0};
     if (ok) {
@@ -274,11 +256,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     // ---------------- geometry decoder (Eq. 4) and the reverse of Eq. 7
     {
       float x0[NG], out[8], dz8[8];
-      if constexpr (SPLIT) {
-        load_row<NG>(Xg + (ok ? k_row : 0) * NG, x0);
-      } else {
-        encode<NL>(F.geo, y, x0);
-      }
+      encode<NL>(F.geo, y, x0);
       decoder_fwd_store<NG, WID, NH, 8, WT>(F.gm, x0, act, out);
       const float a = sigmoidf_(out[0] + ae);
       dz8[0] = da * a * (1.0f - a);
@@ -311,11 +289,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       if (ok) {
 #pragma unroll
         for (int k = 0; k < NG; ++k) dx[k] *= inv_ls;
-        if constexpr (SPLIT) {
-          store_row<NG>(dXg + k_row * NG, dx);
-        } else {
-          encode_bwd<NL>(F.geo, y, dx, io.g_geo_table, dy);
-        }
+        encode_bwd<NL>(F.geo, y, dx, io.g_geo_table, dy);
       }
     }
     // ---------------- colour decoder (Eqs. 5-6) and the reverse of Eq. 7
@@ -325,11 +299,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
     float dp[3] = {0.0f, 0.0f, 0.0f};
     {
       float x0[NC], out[3], dz3[3];
-      if constexpr (SPLIT) {
-        load_row<NG>(Xr + (ok ? k_row : 0) * NG, x0);
-      } else {
-        encode<NL>(F.rad, y, x0);
-      }
+      encode<NL>(F.rad, y, x0);
       pos_enc(dir, x0 + NG);
       decoder_fwd_store<NC, WID, NH, 3, WT>(F.cm, x0, act, out);
 #pragma unroll
@@ -347,11 +317,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       if (ok) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) dx[k] *= inv_ls;
-        if constexpr (SPLIT) {
-          store_row<NG>(dXr + k_row * NG, dx);
-        } else {
-          encode_bwd<NL>(F.rad, y, dx, io.g_rad_table, dy);
-        }
+        encode_bwd<NL>(F.rad, y, dx, io.g_rad_table, dy);
         float ddir[3];
         pos_enc_bwd(dir, dx + NG, ddir);
         const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
@@ -360,14 +326,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_query_bwd(FieldsDev F, CamDev c
       }
     }
     if (ok) {
-      if constexpr (SPLIT) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) io.d_pos[3 * (int64_t)g + j] += dp[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          io.d_pos[3 * (int64_t)g + j] += dp[j] + J[j] * dy[0] + J[3 + j] * dy[1] + J[6 + j] * dy[2];
-      }
+      for (int j = 0; j < 3; ++j)
+        io.d_pos[3 * (int64_t)g + j] += dp[j] + J[j] * dy[0] + J[3 + j] * dy[1] + J[6 + j] * dy[2];
     }
   }
 }
@@ -742,9 +703,9 @@ struct BgbSmem {  // offsets in floats
                        floats = b2 + 4;
 };
 
-// acc[i][j] = sum_k Wk[k][o0 + j] A[k][r0 + i], k < K (Wk row pitch 64, A row
+// acc[i][j] = sum_k Wk[k][o0 + j] A[k][r0 + i], k < K (Wk row pitch WP, A row
 // pitch kBgbPitch), in k order from zero.
-template <int K, int BO>
+template <int K, int BO, int WP = 64>
 __device__ __forceinline__ void bgb_prod(const float* A, const float* Wk, int r0, int o0, float (&acc)[8][BO]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -757,13 +718,13 @@ __device__ __forceinline__ void bgb_prod(const float* A, const float* Wk, int r0
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     float w[BO];
     if constexpr (BO == 4) {
-      const float4 v = *reinterpret_cast<const float4*>(Wk + k * 64 + o0);
+      const float4 v = *reinterpret_cast<const float4*>(Wk + k * WP + o0);
       w[0] = v.x;
       w[1] = v.y;
       w[2] = v.z;
       w[3] = v.w;
     } else {
-      const float2 v = *reinterpret_cast<const float2*>(Wk + k * 64 + o0);
+      const float2 v = *reinterpret_cast<const float2*>(Wk + k * WP + o0);
       w[0] = v.x;
       w[1] = v.y;
     }
@@ -775,18 +736,19 @@ __device__ __forceinline__ void bgb_prod(const float* A, const float* Wk, int r0
 }
 
 // dW[o0 + a][i0 + c] += sum_r dZ[o0 + a][r] A[i0 + c][r] over the tile's rows.
-__device__ __forceinline__ void bgb_dw(const float* DZ, const float* A, int o0, int i0, float (&dw)[4][4]) {
+template <int BA = 4, int BC = 4>
+__device__ __forceinline__ void bgb_dw(const float* DZ, const float* A, int o0, int i0, float (&dw)[BA][BC]) {
 #pragma unroll 2
   for (int r = 0; r < kBgbRows; r += 4) {
-    float4 d[4], x[4];
+    float4 d[BA], x[BC];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) d[a] = *reinterpret_cast<const float4*>(DZ + (o0 + a) * kBgbPitch + r);
+    for (int a = 0; a < BA; ++a) d[a] = *reinterpret_cast<const float4*>(DZ + (o0 + a) * kBgbPitch + r);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) x[c] = *reinterpret_cast<const float4*>(A + (i0 + c) * kBgbPitch + r);
+    for (int c = 0; c < BC; ++c) x[c] = *reinterpret_cast<const float4*>(A + (i0 + c) * kBgbPitch + r);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < BA; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < BC; ++c) {
         dw[a][c] = fmaf(d[a].x, x[c].x, dw[a][c]);
         dw[a][c] = fmaf(d[a].y, x[c].y, dw[a][c]);
         dw[a][c] = fmaf(d[a].z, x[c].z, dw[a][c]);
@@ -1015,6 +977,323 @@ __global__ void __launch_bounds__(256, 1) k_bg_dec_bwd_f32(FieldsDev F, CamDev c
   if (t < 64) slab[SL.off_b[1][1] + t] += db;
   else if (t < 128) slab[SL.off_b[1][0] + t - 64] += db;
   else if (t < 131) slab[SL.off_b[1][2] + t - 128] += db;
+}
+
+// ---------------------------------------------------------------- FP32 Gaussian reverse, register-tiled
+
+// The field query's reverse for one decoder (GEO: geometry, else colour) on
+// 128 listed rows per tile, as k_bg_dec_bwd_f32: the forward recomputed
+// into shared memory, the reverse of Eq. 7 per row, W^T dZ and dZ A^T as
+// CTA-wide products, the weight and bias gradients in registers over the
+// CTA's tiles and added to its slab (slab index slab0 + CTA) once. Row k of
+// the list takes its features from X[k] (k_gather_f32 over the listed rows)
+// and leaves their gradients in dX[k] for the table scatter; the colour
+// decoder adds the positional encoding's share of dL/dp here.
+template <int IN, int OP>
+struct QbSmem {  // offsets in floats
+  static constexpr int X = 0, H1 = X + 64 * kBgbPitch, H2 = H1 + 64 * kBgbPitch, DZ = H2 + 64 * kBgbPitch,
+                       Wt0 = DZ + 64 * kBgbPitch, Wt1 = Wt0 + IN * 64, W0 = Wt1 + 64 * 64, W1 = W0 + 64 * IN,
+                       W2 = W1 + 64 * 64, Wt2 = W2 + OP * 64, b0 = Wt2 + 64 * OP, b1 = b0 + 64, b2 = b1 + 64,
+                       floats = b2 + OP;
+};
+
+template <bool GEO>
+__global__ void __launch_bounds__(256, 1) k_query_dec_bwd_f32(FieldsDev F, CamDev cam, QueryBwdIO io,
+                                                            SlabLayout SL, float* __restrict__ slabs, int slab0,
+                                                            const float* __restrict__ X_in,
+                                                            float* __restrict__ dX_out) {
+  constexpr int IN = GEO ? 32 : 32 + kPEPad, OUT = GEO ? 8 : 3, OP = GEO ? 8 : 4, DEC = GEO ? 0 : 1;
+  using L = QbSmem<IN, OP>;
+  extern __shared__ __align__(16) float smf[];
+  float *X = smf + L::X, *H1 = smf + L::H1, *H2 = smf + L::H2, *DZ = smf + L::DZ;
+  const int t = threadIdx.x;
+  const MlpDev& m = GEO ? F.gm : F.cm;
+  {
+    const float* W0g = static_cast<const float*>(m.W[0]);
+    const float* W1g = static_cast<const float*>(m.W[1]);
+    const float* W2g = static_cast<const float*>(m.W[2]);
+    for (int e = t; e < 64 * IN; e += 256) {  // W0 [64][IN]
+      const int o = e / IN, i = e % IN;
+      const float v = __ldg(W0g + e);
+      smf[L::W0 + e] = v;
+      smf[L::Wt0 + i * 64 + o] = v;
+    }
+    for (int e = t; e < 64 * 64; e += 256) {
+      const float v = __ldg(W1g + e);
+      smf[L::W1 + e] = v;
+      smf[L::Wt1 + (e & 63) * 64 + (e >> 6)] = v;
+    }
+    for (int e = t; e < OP * 64; e += 256) {  // W2 [OUT][64], rows >= OUT zero
+      const int o = e >> 6, i = e & 63;
+      const float v = o < OUT ? __ldg(W2g + o * 64 + i) : 0.0f;
+      smf[L::W2 + e] = v;
+      smf[L::Wt2 + i * OP + o] = v;
+    }
+    if (t < 64) {
+      smf[L::b0 + t] = m.b[0][t];
+      smf[L::b1 + t] = m.b[1][t];
+    }
+    if (t < OP) smf[L::b2 + t] = t < OUT ? m.b[2][t] : 0.0f;
+  }
+  const int nv = min(*io.n_vis, io.n);
+  const int nr = io.list ? min(*io.n_list, nv) : nv;
+  const int ntile = (nr + kBgbRows - 1) / kBgbRows;
+  const float ls = io.loss_scale, inv_ls = 1.0f / io.loss_scale;
+  float pc[3];
+  cam_center(cam, pc);
+  const int r0 = 8 * (t & 15), og = t >> 4;
+  const int dob = t >> 4, dib = t & 15;
+  constexpr int BC0 = IN / 16;  // first layer's weight-gradient block: 4 outputs x BC0 inputs
+  float dw0[4][BC0], dw1[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int c = 0; c < BC0; ++c) dw0[a][c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dw1[a][c] = 0.0f;
+  }
+  constexpr int NW2 = OP * 64 / 256;  // output layer's weight gradients per thread
+  float dw2[NW2];
+#pragma unroll
+  for (int q = 0; q < NW2; ++q) dw2[q] = 0.0f;
+  float db = 0.0f;  // t < 64: b1[t]; t < 128: b0[t - 64]; t < 128 + OUT: b2[t - 128]
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    // this thread's row (threads t and t + 128 take row t & 127 of the tile)
+    const int rr = t & (kBgbRows - 1), krow = tile * kBgbRows + rr;
+    bool ok = krow < nr;
+    const int i = ok ? (io.list ? io.list[krow] : krow) : 0;
+    if (ok && (i < 0 || i >= nv)) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      ok = false;
+    }
+    const int g = ok ? io.vis_ids[i] : 0;
+    if (ok && (g < 0 || g >= io.n)) {
+      set_status(io.status, HYRF_ERR_BOUNDS);
+      ok = false;
+    }
+    float dir[3] = {1.0f, 0.0f, 0.0f}, vn = 1.0f;
+    if (t < kBgbRows) {  // features
+      float x[32];
+      load_row<32>(X_in + (size_t)(ok ? krow : 0) * 32, x);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) X[k * kBgbPitch + rr] = ok ? x[k] : 0.0f;
+    } else if (!GEO) {  // positional encoding of the direction from the camera
+      float p[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) p[k] = ok ? io.pos[3 * (int64_t)g + k] : F.lo[k] + 1.0f / F.sx[k];
+      float v[3] = {p[0] - pc[0], p[1] - pc[1], p[2] - pc[2]};
+      vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dir[k] = v[k] / vn;
+      float pe[kPEPad];
+      pos_enc(dir, pe);
+#pragma unroll
+      for (int k = 0; k < kPEPad; ++k) X[(32 + k) * kBgbPitch + rr] = pe[k];
+    }
+    __syncthreads();
+    // forward: H1 = ReLU(W0 X + b0), H2 = ReLU(W1 H1 + b1)
+#pragma unroll 1
+    for (int layer = 0; layer < 2; ++layer) {
+      const float* A = layer == 0 ? X : H1;
+      float* Hout = layer == 0 ? H1 : H2;
+      const float* b = smf + (layer == 0 ? L::b0 : L::b1);
+      float acc[8][4];
+      if (layer == 0) bgb_prod<IN, 4>(A, smf + L::Wt0, r0, 4 * og, acc);
+      else bgb_prod<64, 4>(A, smf + L::Wt1, r0, 4 * og, acc);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float bj = b[4 * og + j];
+        float* dst = Hout + (4 * og + j) * kBgbPitch + r0;
+        *reinterpret_cast<float4*>(dst) = make_float4(fmaxf(acc[0][j] + bj, 0.0f), fmaxf(acc[1][j] + bj, 0.0f),
+                                                      fmaxf(acc[2][j] + bj, 0.0f), fmaxf(acc[3][j] + bj, 0.0f));
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(fmaxf(acc[4][j] + bj, 0.0f), fmaxf(acc[5][j] + bj, 0.0f),
+                                                          fmaxf(acc[6][j] + bj, 0.0f), fmaxf(acc[7][j] + bj, 0.0f));
+      }
+      __syncthreads();
+    }
+    // output layer and the reverse of Eq. 7 (one thread per row)
+    if (t < kBgbRows) {
+      float out[OP];
+#pragma unroll
+      for (int o = 0; o < OP; ++o) out[o] = 0.0f;
+#pragma unroll 4
+      for (int k = 0; k < 64; ++k) {
+        const float h = H2[k * kBgbPitch + t];
+#pragma unroll
+        for (int q = 0; q < OP / 4; ++q) {
+          const float4 w = *reinterpret_cast<const float4*>(smf + L::Wt2 + k * OP + 4 * q);
+          out[4 * q] = fmaf(w.x, h, out[4 * q]);
+          out[4 * q + 1] = fmaf(w.y, h, out[4 * q + 1]);
+          out[4 * q + 2] = fmaf(w.z, h, out[4 * q + 2]);
+          out[4 * q + 3] = fmaf(w.w, h, out[4 * q + 3]);
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < OP; ++o) out[o] += smf[L::b2 + o];
+      float dz[OP];
+#pragma unroll
+      for (int o = 0; o < OP; ++o) dz[o] = 0.0f;
+      if constexpr (GEO) {
+        float da = 0.0f, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, ae = 0.0f, se = 0.0f;
+        if (ok) {
+          da = io.d_alpha[i] * ls;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) ds[k] = io.d_scale[3 * i + k] * ls;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) dq[k] = io.d_quat[4 * i + k] * ls;
+          ae = io.alpha_e ? io.alpha_e[g] : 0.0f;
+          se = io.scale_e ? io.scale_e[g] : 0.0f;
+        }
+        const float a = sigmoidf_(out[0] + ae);
+        dz[0] = da * a * (1.0f - a);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float sv = sigmoidf_(out[1 + k] + se);
+          dz[1 + k] = ds[k] * sv * (1.0f - sv);
+        }
+        const float rn = sqrtf(out[4] * out[4] + out[5] * out[5] + out[6] * out[6] + out[7] * out[7]);
+        if (rn > 1e-12f) {
+          float qd = 0.0f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) qd += out[4 + k] / rn * dq[k];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) dz[4 + k] = (dq[k] - out[4 + k] / rn * qd) / rn;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) dz[4 + k] = dq[k] / 1e-12f;
+        }
+        if (!ok) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) dz[k] = 0.0f;
+        } else {
+          if (io.d_alpha_e) io.d_alpha_e[g] += dz[0] * inv_ls;
+          if (io.d_scale_e) io.d_scale_e[g] += (dz[1] + dz[2] + dz[3]) * inv_ls;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float dcol = ok ? io.d_color[3 * i + k] * ls : 0.0f;
+          const float ce = ok && io.color_e ? io.color_e[3 * (int64_t)g + k] : 0.0f;
+          const float c = sigmoidf_(out[k] + ce);
+          dz[k] = ok ? dcol * c * (1.0f - c) : 0.0f;
+        }
+        if (ok && io.d_color_e) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) io.d_color_e[3 * (int64_t)g + k] += dz[k] * inv_ls;
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < OP; ++o) DZ[o * kBgbPitch + t] = dz[o];
+    }
+    __syncthreads();
+    // output layer's gradients; dH2 = W2^T dz masked by H2 > 0
+#pragma unroll
+    for (int q = 0; q < NW2; ++q) {
+      const int e = t + 256 * q, o = e >> 6, i2 = e & 63;
+#pragma unroll 4
+      for (int r = 0; r < kBgbRows; r += 4) {
+        const float4 d = *reinterpret_cast<const float4*>(DZ + o * kBgbPitch + r);
+        const float4 h = *reinterpret_cast<const float4*>(H2 + i2 * kBgbPitch + r);
+        dw2[q] = fmaf(d.x, h.x, dw2[q]);
+        dw2[q] = fmaf(d.y, h.y, dw2[q]);
+        dw2[q] = fmaf(d.z, h.z, dw2[q]);
+        dw2[q] = fmaf(d.w, h.w, dw2[q]);
+      }
+    }
+    if (t >= 128 && t < 128 + OUT) db += bgb_rowsum(DZ, t - 128);
+    {
+      const int half = t >> 7;
+      float dh[32];
+#pragma unroll
+      for (int mm = 0; mm < 32; ++mm) dh[mm] = 0.0f;
+#pragma unroll
+      for (int o = 0; o < OUT; ++o) {
+        const float d = DZ[o * kBgbPitch + rr];
+#pragma unroll
+        for (int mm = 0; mm < 32; ++mm) dh[mm] = fmaf(smf[L::W2 + o * 64 + 32 * half + mm], d, dh[mm]);
+      }
+      __syncthreads();  // dz of the output layer has been read
+#pragma unroll
+      for (int mm = 0; mm < 32; ++mm) {
+        const int i2 = 32 * half + mm;
+        DZ[i2 * kBgbPitch + rr] = H2[i2 * kBgbPitch + rr] > 0.0f ? dh[mm] : 0.0f;
+      }
+    }
+    __syncthreads();
+    // second hidden layer's gradients; dH1 = W1^T dZ masked by H1 > 0
+    bgb_dw(DZ, H1, 4 * dob, 4 * dib, dw1);
+    if (t < 64) db += bgb_rowsum(DZ, t);
+    {
+      float acc[8][4];
+      bgb_prod<64, 4>(DZ, smf + L::W1, r0, 4 * og, acc);
+      __syncthreads();  // dZ has been read
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i2 = 4 * og + j;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 mk = *reinterpret_cast<const float4*>(H1 + i2 * kBgbPitch + r0 + 4 * h);
+          *reinterpret_cast<float4*>(DZ + i2 * kBgbPitch + r0 + 4 * h) =
+              make_float4(mk.x > 0.0f ? acc[4 * h][j] : 0.0f, mk.y > 0.0f ? acc[4 * h + 1][j] : 0.0f,
+                          mk.z > 0.0f ? acc[4 * h + 2][j] : 0.0f, mk.w > 0.0f ? acc[4 * h + 3][j] : 0.0f);
+        }
+      }
+    }
+    __syncthreads();
+    // first layer's gradients; dX = W0^T dZ (every input: features and, for
+    // the colour decoder, the positional encoding)
+    bgb_dw<4, BC0>(DZ, X, 4 * dob, BC0 * dib, dw0);
+    if (t >= 64 && t < 128) db += bgb_rowsum(DZ, t - 64);
+    {
+      constexpr int BX = IN / 16;
+      float acc[8][BX];
+      bgb_prod<64, BX, IN>(DZ, smf + L::W0, r0, BX * og, acc);
+      __syncthreads();  // X has been read
+#pragma unroll
+      for (int j = 0; j < BX; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          *reinterpret_cast<float4*>(X + (BX * og + j) * kBgbPitch + r0 + 4 * h) =
+              make_float4(acc[4 * h][j] * inv_ls, acc[4 * h + 1][j] * inv_ls, acc[4 * h + 2][j] * inv_ls,
+                          acc[4 * h + 3][j] * inv_ls);
+    }
+    __syncthreads();
+    if (ok) {
+      if (t < kBgbRows) {
+        float4* d4 = reinterpret_cast<float4*>(dX_out + (size_t)krow * 32);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          __stcs(d4 + k, make_float4(X[(4 * k) * kBgbPitch + rr], X[(4 * k + 1) * kBgbPitch + rr],
+                                     X[(4 * k + 2) * kBgbPitch + rr], X[(4 * k + 3) * kBgbPitch + rr]));
+      } else if (!GEO) {  // dL/dp through the direction's positional encoding
+        float dpe[kPEPad], ddir[3];
+#pragma unroll
+        for (int k = 0; k < kPEPad; ++k) dpe[k] = X[(32 + k) * kBgbPitch + rr];
+        pos_enc_bwd(dir, dpe, ddir);
+        const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) io.d_pos[3 * (int64_t)g + k] += (ddir[k] - dir[k] * dd) / vn;
+      }
+    }
+    __syncthreads();  // X is rewritten by the next tile
+  }
+  float* slab = slabs + (size_t)(slab0 + blockIdx.x) * SL.total;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int c = 0; c < BC0; ++c) slab[SL.off_W[DEC][0] + (4 * dob + a) * IN + BC0 * dib + c] += dw0[a][c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) slab[SL.off_W[DEC][1] + (4 * dob + a) * 64 + 4 * dib + c] += dw1[a][c];
+  }
+#pragma unroll
+  for (int q = 0; q < NW2; ++q) {
+    const int e = t + 256 * q;
+    if ((e >> 6) < OUT) slab[SL.off_W[DEC][2] + e] += dw2[q];
+  }
+  if (t < 64) slab[SL.off_b[DEC][1] + t] += db;
+  else if (t < 128) slab[SL.off_b[DEC][0] + t - 64] += db;
+  else if (t < 128 + OUT) slab[SL.off_b[DEC][2] + t - 128] += db;
 }
 
 template <int NL, int WID, int NH, class WT>
@@ -1506,11 +1785,17 @@ static hyrf_status query_bwd_impl(const FieldsDev& F, const CamDev& cam, const Q
       const RowSource RS{0, io.n, io.vis_ids, io.n_vis, io.pos, 0.0f, io.status, io.list, io.n_list};
       hyrf_status st = launch_gather_f32(F, cam, RS, io.n, Xg, Xr, s);
       if (st != HYRF_OK) return st;
-      set_smem_limit<k_query_bwd<NL, WID, NH, WT, true>>((int)smem);
-      HYRF_LAUNCH("k_query_dec_bwd", s,
-                  k_query_bwd<NL, WID, NH, WT, true><<<ctas, kBwdThreads, smem, s>>>(F, cam, io, SL, slabs, Xg, Xr,
-                                                                                    dXg, dXr));
-      st = launch_slab_reduce(slabs, ctas, SL, slab_targets(grads, true), 1.0f / io.loss_scale, s);
+      const int tiles = (io.n + kBgbRows - 1) / kBgbRows;
+      const int grid = max(1, min(tiles, min(num_sms(), ctas / 2)));
+      const int sg = QbSmem<32, 8>::floats * (int)sizeof(float);
+      const int sc = QbSmem<32 + kPEPad, 4>::floats * (int)sizeof(float);
+      set_smem_limit<k_query_dec_bwd_f32<true>>(sg);
+      set_smem_limit<k_query_dec_bwd_f32<false>>(sc);
+      HYRF_LAUNCH("k_query_dec_bwd_f32<geo>", s,
+                  k_query_dec_bwd_f32<true><<<grid, 256, sg, s>>>(F, cam, io, SL, slabs, 0, Xg, dXg));
+      HYRF_LAUNCH("k_query_dec_bwd_f32<col>", s,
+                  k_query_dec_bwd_f32<false><<<grid, 256, sc, s>>>(F, cam, io, SL, slabs, grid, Xr, dXr));
+      st = launch_slab_reduce(slabs, 2 * grid, SL, slab_targets(grads, true), 1.0f / io.loss_scale, s);
       if (st != HYRF_OK) return st;
       return launch_scatter(F, cam, RS, io.n, dXg, dXr, io.g_geo_table, io.g_rad_table, io.d_pos, s);
     }

@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
   const int t = threadIdx.x, w = t >> 5, r = t & 127;
   const bool geo = t < 128;
   // the two decoders run as independent 128-thread groups: own MMA issuer,
-  // barrier and named barrier, so neither waits for the other's phases
-  const int gid = geo ? 1 : 2;
+  // barrier and named barrier (1, 2), so neither waits for the other's phases
   uint64_t* bar = &bars[geo ? 0 : 1];
   float* bias = reinterpret_cast<float*>(sm + oBias);
   float *b0g = bias, *b1g = bias + 64, *b2g = bias + 128, *b0c = bias + 144, *b1c = bias + 208,
@@ -185,7 +184,8 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
     }
     fence_smem_async();
     fence_before();
-    group_sync(gid);
+    if (geo) group_sync<1>();
+    else group_sync<2>();
     fence_after();
     if (r == 0) {
       if (geo) gemm<64, 32, H16>(tm + 0, sm + oAg, sm + oW0g);
@@ -200,33 +200,35 @@ __global__ void __launch_bounds__(256, 3) k_query_fwd_tc(FieldsDev F, CamDev cam
       fetch_row(io, geo, i1, gn, row_ok(io, i1, nv, gn), cur);
       gn = (tile + 2 * G < ntile && i2 < nv) ? io.vis_ids[i2] : 0;
     }
-    if (!wait_phase_group(bar, phase, gid)) { failed = true; break; }
+    if (!(geo ? wait_phase_group<1>(bar, phase) : wait_phase_group<2>(bar, phase))) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     epilogue_relu64<H16>(tm + lane + colD, b0, Hs, r);
     fence_smem_async();
     fence_before();
-    group_sync(gid);
+    if (geo) group_sync<1>();
+    else group_sync<2>();
     fence_after();
     if (r == 0) {
       if (geo) gemm<64, 64, H16>(tm + 0, sm + oHg, sm + oW1g);
       else gemm<64, 64, H16>(tm + 64, sm + oHc, sm + oW1c);
       commit(bar);
     }
-    if (!wait_phase_group(bar, phase, gid)) { failed = true; break; }
+    if (!(geo ? wait_phase_group<1>(bar, phase) : wait_phase_group<2>(bar, phase))) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     epilogue_relu64<H16>(tm + lane + colD, b1, Hs, r);
     fence_smem_async();
     fence_before();
-    group_sync(gid);
+    if (geo) group_sync<1>();
+    else group_sync<2>();
     fence_after();
     if (r == 0) {
       if (geo) gemm<16, 64, H16>(tm + 0, sm + oHg, sm + oW2g);
       else gemm<16, 64, H16>(tm + 64, sm + oHc, sm + oW2c);
       commit(bar);
     }
-    if (!wait_phase_group(bar, phase, gid)) { failed = true; break; }
+    if (!(geo ? wait_phase_group<1>(bar, phase) : wait_phase_group<2>(bar, phase))) { failed = true; break; }
     phase ^= 1u;
     fence_after();
     float o[16];

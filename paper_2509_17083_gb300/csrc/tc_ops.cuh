@@ -100,24 +100,29 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase, uint32
   return !__syncthreads_or(!ok);
 }
 
-// Named barrier over the 128 threads of one group of a CTA (ids from 1; id
-// 0 is __syncthreads), and its OR-reduction of a predicate.
-__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
-__device__ __forceinline__ bool group_or(int id, bool pred) {
+// Named barrier ID over the 128 threads of one group of a CTA (ids from 1;
+// id 0 is __syncthreads), and its OR-reduction of a predicate.
+template <int ID>
+__device__ __forceinline__ void group_sync() {
+  asm volatile("bar.sync %0, 128;" ::"n"(ID) : "memory");
+}
+template <int ID>
+__device__ __forceinline__ bool group_or(bool pred) {
   uint32_t r;
   asm volatile(
       "{\n.reg .pred a, b;\nsetp.ne.u32 a, %1, 0;\nbar.red.or.pred b, %2, 128, a;\nselp.u32 %0, 1, 0, b;\n}"
       : "=r"(r)
-      : "r"((uint32_t)pred), "r"(id)
+      : "r"((uint32_t)pred), "n"(ID)
       : "memory");
   return r != 0;
 }
 
-// wait_phase for one 128-thread group (named barrier id).
-__device__ __forceinline__ bool wait_phase_group(uint64_t* bar, uint32_t phase, int id, uint32_t polls = kSpin) {
+// wait_phase for the 128-thread group of named barrier ID.
+template <int ID>
+__device__ __forceinline__ bool wait_phase_group(uint64_t* bar, uint32_t phase, uint32_t polls = kSpin) {
   bool ok = false;
   for (uint32_t it = 0; it < polls && !ok; ++it) ok = try_wait(bar, phase);
-  return !group_or(id, !ok);
+  return !group_or<ID>(!ok);
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
