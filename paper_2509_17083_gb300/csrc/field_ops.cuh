@@ -54,7 +54,7 @@ __device__ __forceinline__ void contract_p(const FieldsDev& F, const float p[3],
 
 // Corner indices and fractional position of point y in level l.
 __device__ __forceinline__ void level_cell(const GridDev& G, int l, const float y[3], uint32_t idx[8],
-                                           float f[3]) {
+                                           float f[3], uint64_t* cell = nullptr) {
   const int N = G.res[l];
   uint32_t i0[3];
 #pragma unroll
@@ -65,6 +65,7 @@ __device__ __forceinline__ void level_cell(const GridDev& G, int l, const float 
     i0[d] = (uint32_t)fl;
     f[d] = u - fl;
   }
+  if (cell) *cell = (uint64_t)i0[0] | ((uint64_t)i0[1] << 21) | ((uint64_t)i0[2] << 42);  // N < 2^21
   const uint32_t n1 = (uint32_t)N + 1u;
   if ((G.dense >> l) & 1u) {  // uniform over a level: one of the two index forms only
     const uint32_t b = i0[0] + i0[1] * n1 + i0[2] * n1 * n1;

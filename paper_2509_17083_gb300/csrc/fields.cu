@@ -3,8 +3,9 @@
 // Forward: for 16-level grids with 2 x 64 decoders the hash gather runs in
 // its own full-occupancy kernel (k_gather_f32, gather.cu) and the decoders
 // here read its f32 features (k_query_dec_f32, k_bg_dec_f32: register-tiled
-// CTA-wide products); other shapes use the fused kernels (gather and
-// decoders in one thread per point). Backward
+// CTA-wide products) and their reverses (k_bg_dec_bwd_f32,
+// k_query_dec_bwd_f32) likewise; other shapes use the fused kernels (gather
+// and decoders in one thread per point). Backward
 // kernels recompute the decoder activations, keep them in shared memory as
 // [feature][point] tiles, and reduce the weight gradients per CTA into a
 // private float32 slab (no atomics); one reduction kernel adds the slabs

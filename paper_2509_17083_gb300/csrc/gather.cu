@@ -115,17 +115,23 @@ __device__ __forceinline__ void level_feature2(const GridDev& A, const GridDev& 
   fb = make_float2(b0, b1);
 }
 
-// One float2 atomic per run of consecutive lanes that target the same table
-// entry e: lanes hold neighbouring pixels of an image row, so lanes sharing
-// a cell form runs. Each run's contributions are summed by a segmented
-// shuffle scan and its last lane issues the atomic. A key that appears in
-// two separate runs is simply added twice. Warp-uniform fast paths: no run
-// longer than one lane, or one run over the whole warp.
-__device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, uint32_t key, float g0, float g1) {
+// Lanes that start a run of consecutive lanes in the same grid cell (cell
+// from level_cell): lanes hold neighbouring points (pixels of an image row;
+// Gaussians in Morton order), so lanes sharing a cell form runs, and every
+// corner of the cell has the same runs. Found once per level.
+__device__ __forceinline__ unsigned cell_heads(uint64_t cell) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t prev = __shfl_up_sync(0xffffffffu, cell, 1);
+  return __ballot_sync(0xffffffffu, lane == 0 || prev != cell);
+}
+
+// One float2 atomic per run (heads from cell_heads) of lanes that target
+// the same table entry e: each run's contributions are summed by a
+// segmented shuffle scan and its last lane issues the atomic. Warp-uniform
+// fast paths: no run longer than one lane, or one run over the whole warp.
+__device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, unsigned heads, float g0, float g1) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const uint32_t prev = __shfl_up_sync(full, key, 1);
-  const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
   if (heads == full) {
     if (g0 != 0.0f || g1 != 0.0f) atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
     return;
@@ -167,7 +173,9 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
   if (COHERENT ? __all_sync(0xffffffffu, zero) : zero) return;
   uint32_t idx[8];
   float f[3];
-  level_cell(G, l, y, idx, f);
+  uint64_t cell;
+  level_cell(G, l, y, idx, f, &cell);
+  const unsigned heads = COHERENT ? cell_heads(cell) : 0u;
   float g[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -175,7 +183,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
     const float w = corner_w(f, c);
     const float g0 = w * d0, g1 = w * d1;
     if (COHERENT)
-      run_atomic(gtab, e, idx[c], g0, g1);
+      run_atomic(gtab, e, heads, g0, g1);
     else if (g0 != 0.0f || g1 != 0.0f)
       atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
     if (WANT_DY && !zero) {
@@ -197,14 +205,12 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
   }
 }
 
-// run_atomic for the same entry e of two tables (ga, gb) at once: the runs
-// are found once and the four sums scanned together.
-__device__ __forceinline__ void run_atomic2(float* __restrict__ ga, float* __restrict__ gb, size_t e, uint32_t key,
+// run_atomic for the same entry e of two tables (ga, gb) at once: the four
+// sums scanned together.
+__device__ __forceinline__ void run_atomic2(float* __restrict__ ga, float* __restrict__ gb, size_t e, unsigned heads,
                                             float a0, float a1, float b0, float b1) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const uint32_t prev = __shfl_up_sync(full, key, 1);
-  const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
   bool issue = true;
   if (heads == 1u) {
 #pragma unroll
@@ -247,7 +253,9 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
   if (__all_sync(0xffffffffu, zero)) return;
   uint32_t idx[8];
   float f[3];
-  level_cell(A, l, y, idx, f);
+  uint64_t cell;
+  level_cell(A, l, y, idx, f, &cell);
+  const unsigned heads = cell_heads(cell);
   float g[3] = {0.0f, 0.0f, 0.0f};
   // dL/dy first: the corner values of both tables are loaded together (one
   // round trip), not each behind the previous corner's atomics
@@ -272,7 +280,7 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float w = corner_w(f, c);
-    run_atomic2(ga, gb, (size_t)l * A.T + idx[c], idx[c], w * da.x, w * da.y, w * db.x, w * db.y);
+    run_atomic2(ga, gb, (size_t)l * A.T + idx[c], heads, w * da.x, w * da.y, w * db.x, w * db.y);
   }
   const float N = (float)A.res[l];
   dy[0] = g[0] * N;
