@@ -242,11 +242,22 @@ __device__ __forceinline__ float reduce8(float* v) {
 #pragma unroll
   for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
     const bool up = lane & o;
+    float keep[4], got[4];
 #pragma unroll
     for (int j = 0; j < h; ++j) {
       const float send = up ? v[j] : v[j + h];
-      const float keep = up ? v[j + h] : v[j];
-      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      keep[j] = up ? v[j + h] : v[j];
+      got[j] = __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (h >= 2) {  // the sums two at a time (paired adds, same values)
+#pragma unroll
+      for (int j = 0; j < h; j += 2) {
+        const float2 s2 = padd(make_float2(keep[j], keep[j + 1]), make_float2(got[j], got[j + 1]));
+        v[j] = s2.x;
+        v[j + 1] = s2.y;
+      }
+    } else {
+      v[0] = keep[0] + got[0];
     }
   }
   float s = v[0];
