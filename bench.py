@@ -271,9 +271,9 @@ def fp32_peak_tflops(sm_mhz, n_sm):
 # the kernel changes after its capture.
 NCU_TRAFFIC = {
     # the compositing reverse (one launch of the step driver's config-3
-    # training step, footprint-culled lists): 55,584,256 B read + 260,352 B
-    # written
-    ("k_raster_bwd", "bf16"): 55_844_608,
+    # training step, footprint-culled lists, paired two-pixel reverse):
+    # 55,587,584 B read + 267,264 B written
+    ("k_raster_bwd", "bf16"): 55_854_848,
 }
 
 
