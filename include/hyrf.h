@@ -22,8 +22,9 @@
  *     bytes; workspace contents need not be preserved between calls.
  *   - Arrays are contiguous and row-major. float32 unless stated.
  *   - All launches go to `stream` (a cudaStream_t, passed as void*), in
- *     order; no call reads device memory on the host, so every call may be
- *     captured in a CUDA graph.
+ *     order; no stage call reads device memory on the host, so the stage
+ *     calls may be captured in a CUDA graph (this statement does not cover
+ *     hyrf_bin_sort_noalloc).
  *   - Return value: HYRF_OK, or HYRF_ERR_INVALID_ARG / HYRF_ERR_UNSUPPORTED
  *     for arguments rejected on the host (nothing is launched), or
  *     HYRF_ERR_CUDA if a launch failed. Errors found on the device
@@ -364,8 +365,7 @@ hyrf_status hyrf_bin_sort_backward(const hyrf_bin_sort_args* a, void* workspace,
  *     HYRF_NOALLOC_MAX_INSTANCES; larger requests return
  *     HYRF_ERR_INVALID_ARG and launch nothing.
  *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before
- *     any stream capture.
+ *     per device, with that device current).
  *   - All calls share the one array, which keeps whatever the last call left
  *     in it (no part of it is read before a call writes it). Calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on
