@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
       const float dx = r0.x - fx;
       const float cadx2 = r0.z * dx * dx, cbdx = r0.w * dx;
       float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, dop = 0.0f, dc0 = 0.0f, dc1 = 0.0f, dc2 = 0.0f;
-      bool any = false;
+      bool any = false, warp_any;  // warp_any: some lane of the warp took the Gaussian
       if constexpr (P == 2) {
         // both pixels through one instruction stream (paired FP32 operations,
         // the same values as the per-pixel code below): a pixel that does
@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
         float G0 = 0.0f, a0 = 0.0f, G1 = 0.0f, a1 = 0.0f;
         const bool c0 = pos < last[0] && splat_alpha(pw.x, r2.y, r1.y, G0, a0);
         const bool c1 = pos < last[1] && splat_alpha(pw.y, r2.y, r1.y, G1, a1);
-        if (__any_sync(0xffffffffu, c0 || c1)) {
-          any = c0 || c1;
+        warp_any = __any_sync(0xffffffffu, c0 || c1);
+        if (warp_any) {
           const float2 G = make_float2(c0 ? G0 : 0.0f, c1 ? G1 : 0.0f);
           const float2 al = make_float2(c0 ? a0 : 0.0f, c1 ? a1 : 0.0f);
           const float2 om = psub(pbc(1.0f), al);  // >= 0.01
@@ -498,8 +498,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_raster_bwd(
             }
           }
         }
+        warp_any = __any_sync(0xffffffffu, any);
       }
-      if (__any_sync(0xffffffffu, any)) {
+      if (warp_any) {
         // mean2d (u, v), conic (a, b, c), opacity, colour r, g; colour b apart
         float v[8];
         v[0] = -(r0.z * dx) * D0 - r0.w * D1;
