@@ -125,6 +125,41 @@ __device__ __forceinline__ unsigned cell_heads(uint64_t cell) {
   return __ballot_sync(0xffffffffu, lane == 0 || prev != cell);
 }
 
+// Sums over the 32 lanes of eight float2 values by recursive halving (a
+// lane keeps half of its partial sums and adds its partner's copy of that
+// half): the lanes with (lane & 3) == 0 return the sum of value
+// ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1).
+// Used when the whole warp is one run (every lane in one cell).
+__device__ __forceinline__ float2 warp_sum8x2(float2* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float2 send = up ? v[j] : v[j + h];
+      const float2 keep = up ? v[j + h] : v[j];
+      v[j] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, o),
+                         keep.y + __shfl_xor_sync(0xffffffffu, send.y, o));
+    }
+  }
+  float2 s = v[0];
+#pragma unroll
+  for (int o = 2; o >= 1; o >>= 1)
+    s = make_float2(s.x + __shfl_xor_sync(0xffffffffu, s.x, o), s.y + __shfl_xor_sync(0xffffffffu, s.y, o));
+  return s;
+}
+
+// Corner whose sum warp_sum8x2 leaves in this lane, and its table index.
+__device__ __forceinline__ uint32_t lane_corner_index(const uint32_t idx[8]) {
+  const int lane = threadIdx.x & 31;
+  const int c8 = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  uint32_t ic = idx[0];
+#pragma unroll
+  for (int c = 1; c < 8; ++c) ic = c == c8 ? idx[c] : ic;
+  return ic;
+}
+
 // One float2 atomic per run (heads from cell_heads) of lanes that target
 // the same table entry e: each run's contributions are summed by a
 // segmented shuffle scan and its last lane issues the atomic. Warp-uniform
@@ -176,16 +211,29 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
   uint64_t cell;
   level_cell(G, l, y, idx, f, &cell);
   const unsigned heads = COHERENT ? cell_heads(cell) : 0u;
+  const bool one_run = COHERENT && heads == 1u;  // the whole warp in one cell (warp-uniform)
+  if (one_run) {  // the eight corners' sums at once, one atomic per corner
+    float2 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float w = corner_w(f, c);
+      v[c] = make_float2(w * d0, w * d1);
+    }
+    const float2 sm = warp_sum8x2(v);
+    if ((threadIdx.x & 3) == 0 && (sm.x != 0.0f || sm.y != 0.0f))
+      atomicAdd(reinterpret_cast<float2*>(gtab) + (size_t)l * G.T + lane_corner_index(idx), sm);
+  }
   float g[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const size_t e = (size_t)l * G.T + idx[c];
     const float w = corner_w(f, c);
     const float g0 = w * d0, g1 = w * d1;
-    if (COHERENT)
-      run_atomic(gtab, e, heads, g0, g1);
-    else if (g0 != 0.0f || g1 != 0.0f)
+    if (COHERENT) {
+      if (!one_run) run_atomic(gtab, e, heads, g0, g1);
+    } else if (g0 != 0.0f || g1 != 0.0f) {
       atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
+    }
     if (WANT_DY && !zero) {
       const float2 v = load_entry_t<DT>(G, e);
       const float dot = v.x * d0 + v.y * d1;
@@ -256,6 +304,7 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
   uint64_t cell;
   level_cell(A, l, y, idx, f, &cell);
   const unsigned heads = cell_heads(cell);
+  const bool one_run = heads == 1u;  // the whole warp in one cell (warp-uniform)
   float g[3] = {0.0f, 0.0f, 0.0f};
   // dL/dy first: the corner values of both tables are loaded together (one
   // round trip), not each behind the previous corner's atomics
@@ -277,10 +326,26 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
       g[2] += dot[c] * ((c & 4) ? 1.0f : -1.0f) * wx * wy;
     }
   }
+  if (one_run) {  // the eight corners' sums at once, one atomic per corner and table
+    float2 va[8], vb[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float w = corner_w(f, c);
-    run_atomic2(ga, gb, (size_t)l * A.T + idx[c], heads, w * da.x, w * da.y, w * db.x, w * db.y);
+    for (int c = 0; c < 8; ++c) {
+      const float w = corner_w(f, c);
+      va[c] = make_float2(w * da.x, w * da.y);
+      vb[c] = make_float2(w * db.x, w * db.y);
+    }
+    const float2 sa = warp_sum8x2(va), sb = warp_sum8x2(vb);
+    if ((threadIdx.x & 3) == 0) {
+      const size_t e = (size_t)l * A.T + lane_corner_index(idx);
+      if (sa.x != 0.0f || sa.y != 0.0f) atomicAdd(reinterpret_cast<float2*>(ga) + e, sa);
+      if (sb.x != 0.0f || sb.y != 0.0f) atomicAdd(reinterpret_cast<float2*>(gb) + e, sb);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float w = corner_w(f, c);
+      run_atomic2(ga, gb, (size_t)l * A.T + idx[c], heads, w * da.x, w * da.y, w * db.x, w * db.y);
+    }
   }
   const float N = (float)A.res[l];
   dy[0] = g[0] * N;
