@@ -403,6 +403,13 @@ typedef struct {
    * n_contrib skips computing it. Entries outside [0, tiles) set
    * HYRF_ERR_BOUNDS and are skipped. */
   const int32_t* tile_order;
+  /* Optional [N][12] float, 16-byte aligned: the per-Gaussian records the
+   * compositing reads (mean2d, conic, opacity, colour and the exponent
+   * bound of the opacity test). NULL: each call packs them into its
+   * workspace. Given, the forward packs them here and the reverse given
+   * the same pointer reads them instead of packing again: between the two
+   * calls mean2d, conic, alpha and color must not change. */
+  float* records;
 } hyrf_rasterize_args;
 
 size_t hyrf_rasterize_workspace_size(const hyrf_rasterize_args* a);

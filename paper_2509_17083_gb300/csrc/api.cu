@@ -359,6 +359,7 @@ static hyrf_status raster_check(const hyrf_rasterize_args* a) {
   if (!a->n_vis || !a->ranges || !a->C_fg || !a->T_final || !a->n_contrib) return HYRF_ERR_INVALID_ARG;
   if (a->n > 0 && (!a->vals || !a->mean2d || !a->conic || !a->alpha || !a->color))
     return HYRF_ERR_INVALID_ARG;
+  if (a->records && (reinterpret_cast<uintptr_t>(a->records) & 15u)) return HYRF_ERR_INVALID_ARG;
   return HYRF_OK;
 }
 

@@ -116,17 +116,36 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Records of 256 Gaussians per CTA and pass: the inputs are read
+// coalesced into shared memory, the 48-byte records written coalesced as
+// consecutive float4.
 __global__ void __launch_bounds__(256) k_pack(const int32_t* __restrict__ n_vis, int n,
                                               const float* __restrict__ mean2d,
                                               const float* __restrict__ conic,
                                               const float* __restrict__ alpha,
                                               const float* __restrict__ color,
                                               float4* __restrict__ rec) {
+  __shared__ float sm2[2 * 256], sc3[3 * 256], sa[256], scl[3 * 256];
   const int nv = min(*n_vis, n);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
-    rec[3 * i] = make_float4(mean2d[2 * i], mean2d[2 * i + 1], conic[3 * i], conic[3 * i + 1]);
-    rec[3 * i + 1] = make_float4(conic[3 * i + 2], alpha[i], color[3 * i], color[3 * i + 1]);
-    rec[3 * i + 2] = make_float4(color[3 * i + 2], splat_pmin(alpha[i]), 0.0f, 0.0f);
+  const int t = threadIdx.x;
+  for (int i0 = blockIdx.x * 256; i0 < nv; i0 += gridDim.x * 256) {
+    const int m = min(256, nv - i0);
+    for (int k = t; k < 2 * m; k += 256) sm2[k] = mean2d[2 * (size_t)i0 + k];
+    for (int k = t; k < 3 * m; k += 256) {
+      sc3[k] = conic[3 * (size_t)i0 + k];
+      scl[k] = color[3 * (size_t)i0 + k];
+    }
+    if (t < m) sa[t] = alpha[i0 + t];
+    __syncthreads();
+    for (int k = t; k < 3 * m; k += 256) {
+      const int i = k / 3, part = k % 3;
+      float4 v;
+      if (part == 0) v = make_float4(sm2[2 * i], sm2[2 * i + 1], sc3[3 * i], sc3[3 * i + 1]);
+      else if (part == 1) v = make_float4(sc3[3 * i + 2], sa[i], scl[3 * i], scl[3 * i + 1]);
+      else v = make_float4(scl[3 * i + 2], splat_pmin(sa[i]), 0.0f, 0.0f);
+      rec[3 * (size_t)i0 + k] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -622,6 +641,7 @@ hyrf_status launch_raster_fwd(const hyrf_rasterize_args& a, void* ws, cudaStream
   const int TX = (a.width + kTile - 1) / kTile, TY = (a.height + kTile - 1) / kTile;
   Carver c(ws);
   float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
+  if (a.records) rec = reinterpret_cast<float4*>(a.records);  // kept for the reverse
   hyrf_status st = pack(a, rec, s);
   if (st != HYRF_OK) return st;
   HYRF_LAUNCH("k_raster_fwd", s,
@@ -638,8 +658,12 @@ hyrf_status launch_raster_bwd(const hyrf_rasterize_backward_args& b, void* ws, c
   float4* rec = c.take<float4>((size_t)3 * (a.n > 0 ? a.n : 1));
   int32_t* key = c.take<int32_t>((size_t)TX * TY);
   int32_t* order = c.take<int32_t>((size_t)TX * TY);
-  hyrf_status st = pack(a, rec, s);
-  if (st != HYRF_OK) return st;
+  if (a.records) {  // the forward's records
+    rec = reinterpret_cast<float4*>(a.records);
+  } else {
+    hyrf_status st = pack(a, rec, s);
+    if (st != HYRF_OK) return st;
+  }
   if (a.tile_order) {
     order = const_cast<int32_t*>(a.tile_order);
   } else {

@@ -106,7 +106,7 @@ class hyrf_rasterize_args(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_vis", _vp), ("ranges", _vp), ("vals", _vp), ("mean2d", _vp),
                 ("conic", _vp), ("alpha", _vp), ("color", _vp), ("width", C.c_int32),
                 ("height", C.c_int32), ("tile", C.c_int32), ("C_fg", _vp), ("T_final", _vp),
-                ("n_contrib", _vp), ("status", _vp), ("tile_order", _vp)]
+                ("n_contrib", _vp), ("status", _vp), ("tile_order", _vp), ("records", _vp)]
 
 
 class hyrf_tile_order_args(C.Structure):

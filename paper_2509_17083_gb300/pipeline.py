@@ -197,6 +197,8 @@ class ViewRenderer:
         self.vis_ids, self.n_vis = z(max(n, 1), dt=i32), z(1, dt=i32)
         self.alpha, self.scale, self.quat, self.color = z(n), z(n, 3), z(n, 4), z(n, 3)
         self.mean2d, self.conic, self.depth = z(n, 2), z(n, 3), z(n)
+        # the compositing records the forward packs and the reverse reuses
+        self.records = z(max(n, 1), 12)
         self.rect, self.ntiles = z(n, 4, dt=i32), z(n, dt=i32)
         # opacity-aware footprint of each projected Gaussian (hyrf_project):
         # the binning keeps only the tiles it can show in
@@ -263,7 +265,7 @@ class ViewRenderer:
                         mean2d=self.mean2d, conic=self.conic, alpha=self.alpha, color=self.color,
                         width=self.W, height=self.H, tile=H.TILE, C_fg=self.C_fg,
                         T_final=self.T_final, n_contrib=self.n_contrib, status=self.status,
-                        tile_order=self.tile_order))
+                        tile_order=self.tile_order, records=self.records))
         return a
 
     def rasterize(self):
