@@ -360,6 +360,40 @@ def test_rasterize_backward_matches_oracle(lib, W, H_, n):
         assert e < TOL_GRAD_F32, (key, e)
 
 
+def test_rasterize_records_shared_by_forward_and_reverse(lib):
+    """The optional records buffer: the forward packs the records into it
+    and the reverse reads them instead of packing again; every output equals
+    that of the calls without it, bit for bit."""
+    rng = np.random.default_rng(77)
+    W, H_, n = 181, 133, 3000
+    cam, m, c, op, col, vals, ranges = _raster_scene(rng, W, H_, n)
+    dev = "cuda"
+    a0, args0 = _gpu_raster(n, W, H_, m, c, op, col, vals, ranges)
+    rec = torch.full((n, 12), float("nan"), device=dev)  # must be overwritten by the forward
+    args1 = dict(args0, C_fg=torch.zeros(H_, W, 3, device=dev), T_final=torch.zeros(H_, W, device=dev),
+                 n_contrib=torch.zeros(H_, W, dtype=torch.int32, device=dev), records=rec)
+    a1 = H._fill(H.hyrf_rasterize_args(), args1)
+    H.call("hyrf_rasterize", a1)
+    dC = rng.standard_normal((H_, W, 3)).astype(np.float32)
+    dT = rng.standard_normal((H_, W)).astype(np.float32)
+    outs = []
+    for a in (a0, a1):
+        g = dict(d_mean2d=torch.zeros(n, 2, device=dev), d_conic=torch.zeros(n, 3, device=dev),
+                 d_alpha=torch.zeros(n, device=dev), d_color=torch.zeros(n, 3, device=dev))
+        H.hyrf_rasterize_backward(a, d_C_fg=cuda_f32(dC), d_T_final=cuda_f32(dT), **g)
+        outs.append(g)
+    torch.cuda.synchronize()
+    for k in ("C_fg", "T_final", "n_contrib"):
+        assert np.array_equal(np_(args0[k]), np_(args1[k])), k
+    for k in outs[0]:
+        assert np.array_equal(np_(outs[0][k]).view(np.uint32), np_(outs[1][k]).view(np.uint32)), k
+    assert not np.isnan(np_(rec)).any()
+    # a misaligned records pointer is refused
+    bad = dict(args1, records=torch.zeros(n * 12 + 1, device=dev)[1:])
+    with pytest.raises(H.HyrfError):
+        H.call("hyrf_rasterize", H._fill(H.hyrf_rasterize_args(), bad))
+
+
 # ------------------------------------------------------------------ background and loss
 
 @pytest.mark.parametrize("mode", [0, 1])
