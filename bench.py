@@ -252,6 +252,13 @@ def kernel_work(nv, K, P, tiles, bf16, pairs=0, macs=(0, 0), active=None):
         "k_decoder_bwd_tc<BgPixel>": P * mc * 3 * 2,
     }
     alu = {k: pairs * f for k, f in FP32_FLOPS_PER_PAIR.items()}
+    if not bf16:
+        # the FP32 path's register-tiled decoders: 2 FP32 FLOPs per
+        # multiply-accumulate, the reverse 3x (recomputed forward, dX, dW)
+        alu.update({"k_query_dec_f32<geo>": nv * mg * 2, "k_query_dec_f32<col>": nv * mc * 2,
+                    "k_bg_dec_f32": P * mc * 2, "k_bg_dec_bwd_f32": P * mc * 3 * 2,
+                    "k_query_dec_bwd_f32<geo>": active * mg * 3 * 2,
+                    "k_query_dec_bwd_f32<col>": active * mc * 3 * 2})
     out = {k: ("hbm", v) for k, v in hbm.items()}
     if bf16:
         out.update({k: ("tensor", v) for k, v in tensor.items()})

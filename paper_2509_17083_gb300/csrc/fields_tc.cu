@@ -8,8 +8,10 @@
 // accumulators live in tensor memory and come back with tcgen05.ld for the
 // bias + ReLU epilogue, which writes the next layer's bf16 A operand. The
 // field query runs three CTAs per SM (inputs share the hidden activations'
-// buffers, 128 tensor-memory columns each) and fetches the next tile's rows
-// into registers while the current tile's MMA chain runs.
+// buffers, 128 tensor-memory columns each), its geometry and colour
+// decoders as two independent 128-thread groups (own MMA issuer, mbarrier
+// and named barrier), and fetches the next tile's rows into registers
+// while the current tile's MMA chain runs.
 //
 // Shared-memory operands use the no-swizzle K-major core-matrix layout: an
 // 8-row x 16-byte core matrix is 128 contiguous bytes; core matrices

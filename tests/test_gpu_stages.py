@@ -362,8 +362,9 @@ def test_rasterize_backward_matches_oracle(lib, W, H_, n):
 
 def test_rasterize_records_shared_by_forward_and_reverse(lib):
     """The optional records buffer: the forward packs the records into it
-    and the reverse reads them instead of packing again; every output equals
-    that of the calls without it, bit for bit."""
+    and the reverse reads them instead of packing again; the image, T_final
+    and n_contrib equal those of the calls without it bit for bit, the
+    gradients up to the order of their atomic sums."""
     rng = np.random.default_rng(77)
     W, H_, n = 181, 133, 3000
     cam, m, c, op, col, vals, ranges = _raster_scene(rng, W, H_, n)
@@ -385,8 +386,10 @@ def test_rasterize_records_shared_by_forward_and_reverse(lib):
     torch.cuda.synchronize()
     for k in ("C_fg", "T_final", "n_contrib"):
         assert np.array_equal(np_(args0[k]), np_(args1[k])), k
+    # the gradients are sums of float atomics, whose order varies from run to
+    # run: equal up to that rounding
     for k in outs[0]:
-        assert np.array_equal(np_(outs[0][k]).view(np.uint32), np_(outs[1][k]).view(np.uint32)), k
+        assert rel_l2(np_(outs[1][k]), np_(outs[0][k])) < 1e-6, k
     assert not np.isnan(np_(rec)).any()
     # a misaligned records pointer is refused
     bad = dict(args1, records=torch.zeros(n * 12 + 1, device=dev)[1:])
