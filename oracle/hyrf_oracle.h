@@ -26,6 +26,11 @@
  *   projection       on-axis closed form; scipy rotation + FD Jacobian
  *                    reference; FD backward; FP32 rect vs FP64 definition
  *   binning          brute-force tile coverage; tiled == untiled compositing
+ *   footprint        threshold against numpy's logarithm; brute force over
+ *                    every pixel centre (no tile that Eq. 1 can show the
+ *                    Gaussian in is dropped); packed row spans decode to the
+ *                    instance lists; footprint lists composite exactly like
+ *                    the rectangles
  *   compositing      single-Gaussian closed form; weights sum to 1 - T_final;
  *                    FD backward
  *   background       |o + t d| = r with t > 0; constant field; FD backward.
