@@ -125,6 +125,16 @@ __device__ __forceinline__ unsigned cell_heads(uint64_t cell) {
   return __ballot_sync(0xffffffffu, lane == 0 || prev != cell);
 }
 
+// Length of the longest run of the heads (warp-uniform): a segmented scan
+// over runs no longer than this needs only its offsets below it; the later
+// steps would add nothing to any lane.
+__device__ __forceinline__ int longest_run(unsigned heads) {
+  const int lane = threadIdx.x & 31;
+  const unsigned above = heads & ~(0xffffffffu >> (31 - lane));  // heads after this lane
+  const int len = ((heads >> lane) & 1u) ? (above ? __ffs(above) - 1 : 32) - lane : 0;
+  return (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+}
+
 // Sums over the 32 lanes of eight float2 values by recursive halving (a
 // lane keeps half of its partial sums and adds its partner's copy of that
 // half): the lanes with (lane & 3) == 0 return the sum of value
@@ -160,11 +170,13 @@ __device__ __forceinline__ uint32_t lane_corner_index(const uint32_t idx[8]) {
   return ic;
 }
 
-// One float2 atomic per run (heads from cell_heads) of lanes that target
-// the same table entry e: each run's contributions are summed by a
-// segmented shuffle scan and its last lane issues the atomic. Warp-uniform
-// fast paths: no run longer than one lane, or one run over the whole warp.
-__device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, unsigned heads, float g0, float g1) {
+// One float2 atomic per run (heads from cell_heads, span = longest_run) of
+// lanes that target the same table entry e: each run's contributions are
+// summed by a segmented shuffle scan and its last lane issues the atomic.
+// Warp-uniform fast paths: no run longer than one lane, or one run over the
+// whole warp.
+__device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, unsigned heads, int span, float g0,
+                                           float g1) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   if (heads == full) {
@@ -184,6 +196,7 @@ __device__ __forceinline__ void run_atomic(float* __restrict__ gtab, size_t e, u
   const int start = 31 - __clz(heads & (full >> (31 - lane)));  // first lane of this run
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= span) break;  // warp-uniform
     const float a0 = __shfl_up_sync(full, g0, o), a1 = __shfl_up_sync(full, g1, o);
     if (lane - o >= start) {
       g0 += a0;
@@ -212,6 +225,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
   level_cell(G, l, y, idx, f, &cell);
   const unsigned heads = COHERENT ? cell_heads(cell) : 0u;
   const bool one_run = COHERENT && heads == 1u;  // the whole warp in one cell (warp-uniform)
+  const int span = COHERENT ? longest_run(heads) : 1;
   if (one_run) {  // the eight corners' sums at once, one atomic per corner
     float2 v[8];
 #pragma unroll
@@ -230,7 +244,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
     const float w = corner_w(f, c);
     const float g0 = w * d0, g1 = w * d1;
     if (COHERENT) {
-      if (!one_run) run_atomic(gtab, e, heads, g0, g1);
+      if (!one_run) run_atomic(gtab, e, heads, span, g0, g1);
     } else if (g0 != 0.0f || g1 != 0.0f) {
       atomicAdd(reinterpret_cast<float2*>(gtab) + e, make_float2(g0, g1));
     }
@@ -256,7 +270,7 @@ __device__ __forceinline__ void level_scatter(const GridDev& G, int l, const flo
 // run_atomic for the same entry e of two tables (ga, gb) at once: the four
 // sums scanned together.
 __device__ __forceinline__ void run_atomic2(float* __restrict__ ga, float* __restrict__ gb, size_t e, unsigned heads,
-                                            float a0, float a1, float b0, float b1) {
+                                            int span, float a0, float a1, float b0, float b1) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   bool issue = true;
@@ -273,6 +287,7 @@ __device__ __forceinline__ void run_atomic2(float* __restrict__ ga, float* __res
     const int start = 31 - __clz(heads & (full >> (31 - lane)));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+      if (o >= span) break;  // warp-uniform
       const float x0 = __shfl_up_sync(full, a0, o), x1 = __shfl_up_sync(full, a1, o);
       const float z0 = __shfl_up_sync(full, b0, o), z1 = __shfl_up_sync(full, b1, o);
       if (lane - o >= start) {
@@ -305,6 +320,7 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
   level_cell(A, l, y, idx, f, &cell);
   const unsigned heads = cell_heads(cell);
   const bool one_run = heads == 1u;  // the whole warp in one cell (warp-uniform)
+  const int span = longest_run(heads);
   float g[3] = {0.0f, 0.0f, 0.0f};
   // dL/dy first: the corner values of both tables are loaded together (one
   // round trip), not each behind the previous corner's atomics
@@ -344,7 +360,7 @@ __device__ __forceinline__ void level_scatter2(const GridDev& A, const GridDev& 
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const float w = corner_w(f, c);
-      run_atomic2(ga, gb, (size_t)l * A.T + idx[c], heads, w * da.x, w * da.y, w * db.x, w * db.y);
+      run_atomic2(ga, gb, (size_t)l * A.T + idx[c], heads, span, w * da.x, w * da.y, w * db.x, w * db.y);
     }
   }
   const float N = (float)A.res[l];
