@@ -15,6 +15,14 @@ constexpr int kRT = 256;         // radix threads per CTA
 constexpr int kSub = 2048;       // elements per scatter sub-tile (8 warps x 8 rounds x 32)
 constexpr int kRounds = kSub / 256;
 constexpr int kMaxRadixCTAs = 2048;
+// Elements per radix CTA (the CTA count is the capacity over this, at most
+// kMaxRadixCTAs) and the scatter's resident CTAs per SM (its register cap).
+#ifndef HYRF_RADIX_PER_CTA
+#define HYRF_RADIX_PER_CTA 2048
+#endif
+#ifndef HYRF_RADIX_SCATTER_CTAS
+#define HYRF_RADIX_SCATTER_CTAS 5
+#endif
 
 __device__ __forceinline__ int dev_chunk(int n, int G) {
   int c = (n + G - 1) / G;
@@ -80,7 +88,7 @@ __global__ void __launch_bounds__(kRT) k_radix_colscan(uint32_t* __restrict__ hi
   if (threadIdx.x == 0) totals[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(kRT, HYRF_RADIX_SCATTER_CTAS) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                        const int32_t* __restrict__ vals_in,
                                                        uint32_t* __restrict__ keys_out,
                                                        int32_t* __restrict__ vals_out,
@@ -119,24 +127,25 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
   const int64_t start = (int64_t)b * chunk;
   const int64_t end = (start + chunk < (int64_t)n) ? start + chunk : (int64_t)n;
   for (int64_t sub = start; sub < end; sub += kSub) {
+    // (a round's validity and digits are recomputed where needed: fewer
+    // registers, more CTAs per SM)
     uint32_t key[kRounds], rank[kRounds];
     int32_t val[kRounds];
-    uint32_t dig[kRounds];
-    bool valid[kRounds];
+    const int64_t idx0 = sub + w * (32 * kRounds) + lane;  // round r: idx0 + 32 r
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-      const int64_t idx = sub + w * (32 * kRounds) + r * 32 + lane;
-      valid[r] = idx < end;
-      key[r] = valid[r] ? keys_in[idx] : 0u;
-      val[r] = valid[r] ? vals_in[idx] : 0;
-      dig[r] = (key[r] >> shift) & mask;
-      const uint32_t m_valid = __ballot_sync(0xffffffffu, valid[r]);
-      const uint32_t peers = __match_any_sync(0xffffffffu, valid[r] ? dig[r] : 0x10000u + lane) & m_valid;
+      const int64_t idx = idx0 + r * 32;
+      const bool valid = idx < end;
+      key[r] = valid ? keys_in[idx] : 0u;
+      val[r] = valid ? vals_in[idx] : 0;
+      const uint32_t dig = (key[r] >> shift) & mask;
+      const uint32_t m_valid = __ballot_sync(0xffffffffu, valid);
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dig : 0x10000u + lane) & m_valid;
       uint32_t prev = 0;
-      if (valid[r]) prev = whist[w][dig[r]];
+      if (valid) prev = whist[w][dig];
       __syncwarp();
       rank[r] = prev + __popc(peers & ((1u << lane) - 1u));
-      if (valid[r] && lane == __ffs(peers) - 1) whist[w][dig[r]] = prev + __popc(peers);
+      if (valid && lane == __ffs(peers) - 1) whist[w][dig] = prev + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
@@ -172,8 +181,9 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(const uint32_t* __restric
     // consecutive global positions (coalesced)
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-      if (!valid[r]) continue;
-      const uint32_t lp = lstart[dig[r]] + whist[w][dig[r]] + rank[r];
+      if (idx0 + r * 32 >= end) continue;
+      const uint32_t dig = (key[r] >> shift) & mask;
+      const uint32_t lp = lstart[dig] + whist[w][dig] + rank[r];
       sk[lp] = key[r];
       sv[lp] = val[r];
     }
@@ -707,7 +717,7 @@ __global__ void __launch_bounds__(256) k_depth_keys(const float* __restrict__ de
 // ---------------------------------------------------------------- host side
 
 static int radix_ctas(int64_t cap) {
-  int64_t g = (cap + 4095) / 4096;
+  int64_t g = (cap + HYRF_RADIX_PER_CTA - 1) / HYRF_RADIX_PER_CTA;
   return (int)(g < 1 ? 1 : (g > kMaxRadixCTAs ? kMaxRadixCTAs : g));
 }
 
