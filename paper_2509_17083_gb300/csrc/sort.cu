@@ -48,11 +48,13 @@ __global__ void __launch_bounds__(kRT) k_radix_hist(const uint32_t* __restrict__
   const int64_t end = (start + chunk < (int64_t)n) ? start + chunk : (int64_t)n;
   for (int64_t i = start + threadIdx.x; i < end; i += kRT) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
   __syncthreads();
-  hist[threadIdx.x * G + b] = h[threadIdx.x];
+  if (threadIdx.x <= mask) hist[threadIdx.x * G + b] = h[threadIdx.x];  // the pass's digits only
 }
 
-// One CTA per digit: exclusive scan of the digit's column over the G CTAs;
-// digit totals to totals[d].
+// One CTA per digit of the pass (mask + 1 of them): exclusive scan of the
+// digit's column over the G CTAs; digit totals to totals[d]. Entries of
+// hist and totals past the pass's digits are left as they are: the
+// scatter's digit bases below mask + 1 do not depend on them.
 __global__ void __launch_bounds__(kRT) k_radix_colscan(uint32_t* __restrict__ hist, int G,
                                                        uint32_t* __restrict__ totals) {
   __shared__ uint32_t wsum[kRT / 32];
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kRT, HYRF_RADIX_SCATTER_CTAS) k_radix_scatter(
   const int lane = t & 31, w = t >> 5;
   // digit base = exclusive scan of the digit totals + this CTA's column prefix
   {
-    const uint32_t tot = totals[t];
+    const uint32_t tot = t <= (int)mask ? totals[t] : 0u;  // (only the pass's digits were written)
     uint32_t x = tot;
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kRT, HYRF_RADIX_SCATTER_CTAS) k_radix_scatter(
     __syncthreads();
     uint32_t before = 0;
     for (int j = 0; j < w; ++j) before += wsum[j];
-    base[t] = before + x - tot + hist[t * G + b];
+    base[t] = before + x - tot + (t <= (int)mask ? hist[t * G + b] : 0u);
 #pragma unroll
     for (int j = 0; j < 8; ++j) whist[j][t] = 0;
   }
@@ -783,7 +785,7 @@ static hyrf_status radix_sort(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* 
     HYRF_LAUNCH("k_radix_hist", s,
                 k_radix_hist<<<G, kRT, 0, s>>>(src_k, n_ptr, cap, shift, mask, hist));
     HYRF_LAUNCH("k_radix_colscan", s,
-                k_radix_colscan<<<256, kRT, 0, s>>>(hist, G, totals));
+                k_radix_colscan<<<(int)mask + 1, kRT, 0, s>>>(hist, G, totals));
     HYRF_LAUNCH(name, s,
                 k_radix_scatter<<<G, kRT, 0, s>>>(src_k, src_v, dst_k, dst_v, n_ptr, cap, shift, mask, hist,
                                       totals));
