@@ -36,8 +36,10 @@
  *   background       |o + t d| = r with t > 0; constant field; FD backward.
  *                    The equirect "background map" layout is a reading of
  *                    the paper's one-line mention: parity unpinned against
- *                    the paper for map mode (pinned only by FD and the
- *                    constant-field case).
+ *                    the paper for map mode (pinned by FD, the
+ *                    constant-field case and, from the centre of a cubic
+ *                    box, O(h^2) convergence of the map colour to the exact
+ *                    mode's colour of each ray).
  *   loss             scipy-correlate SSIM reference, SSIM(x,x) = 1, L1 closed
  *                    form, FD gradient
  *   whole path       reduction to isotropic 3DGS (Tab. 5 "w/o Neural"); FD of

@@ -314,6 +314,35 @@ def test_background_constant_field(orc, mode):
     np.testing.assert_allclose(C, Cfg + T[..., None] * sig(bb), rtol=1e-12)
 
 
+def test_background_map_converges_to_exact_mode(orc):
+    """Map-mode geometry (texel centres, the longitude and latitude axes,
+    bilinear weights) against the exact mode: seen from the centre of a cubic
+    box, a pixel's sphere hit lies along its own ray, so the map colour is the
+    bilinear interpolation, over the texel directions, of the colour the exact
+    mode gives that ray. For a smooth colour field the error falls as O(h^2),
+    about 4x per halving of the texel size. A half-texel offset gives O(h)
+    (ratios near 0.5), and a swapped or mirrored axis does not converge."""
+    rng = np.random.default_rng(21)
+    fl = synth.make_fields(rng, [-2, -2, -2], [2, 2, 2], 4, 8, 16, 2, 0.5, pe_freq=2, pe_pad=16)
+    fl.rad.table = np.zeros_like(fl.rad.table)  # the colour depends on the direction only
+    m = fl.col_mlp
+    # positive pre-activations in every hidden unit: a smooth colour field
+    m.W = [rng.uniform(-0.05, 0.05, w.shape).astype(np.float32) for w in m.W[:-1]] + \
+        [rng.uniform(-1, 1, m.W[-1].shape).astype(np.float32)]
+    m.b = [np.full_like(b, 4.0) for b in m.b[:-1]] + [np.zeros_like(m.b[-1])]
+    cam = synth.look_at([0, 0, 0], [0.1, 0.05, 1], 24, 16, 60.0)  # the box centre
+    Cfg, T = np.zeros((16, 24, 3)), np.ones((16, 24))
+    _, ce = orc.background(cam, fl, synth.Background(0, 0, 0, 100.0), Cfg, T)
+    assert np.ptp(ce) > 0.5  # the colour varies over the view
+    errs = []
+    for mh in (16, 32, 64, 128):
+        _, cm = orc.background(cam, fl, synth.Background(1, mh, 2 * mh, 100.0), Cfg, T)
+        errs.append(np.abs(cm - ce).max())
+    ratios = np.array(errs[1:]) / np.array(errs[:-1])
+    assert np.all((ratios > 0.15) & (ratios < 0.35)), (errs, ratios)
+    assert errs[-1] < 1e-5
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_background_backward_matches_finite_differences(orc, mode):
     rng = np.random.default_rng(9)
