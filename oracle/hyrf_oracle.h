@@ -33,7 +33,9 @@
  *                    the rectangles
  *   compositing      single-Gaussian closed form; weights sum to 1 - T_final;
  *                    FD backward
- *   background       |o + t d| = r with t > 0; constant field; FD backward.
+ *   background       |o + t d| = r with t > 0; constant field; FD backward;
+ *                    a camera rolled by 180 degrees sees the same colour
+ *                    along the same world ray (pixel (W-1-i, H-1-j)).
  *                    The equirect "background map" layout is a reading of
  *                    the paper's one-line mention: parity unpinned against
  *                    the paper for map mode (pinned by FD, the

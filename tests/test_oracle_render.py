@@ -314,6 +314,27 @@ def test_background_constant_field(orc, mode):
     np.testing.assert_allclose(C, Cfg + T[..., None] * sig(bb), rtol=1e-12)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_background_depends_on_the_world_ray_only(orc, mode):
+    """Eq. 10 queries the field along the pixel's world-space ray. A camera
+    rolled by 180 degrees about its optical axis (camera x and y negated;
+    principal point at the image centre) sees at pixel (W-1-i, H-1-j) the
+    ray of pixel (i, j): same centre, same world direction, so the same
+    background colour. A positional encoding of the camera-space direction,
+    or a ray origin taken from t alone, would break it."""
+    rng = np.random.default_rng(12)
+    fl = _bg_fields(rng)
+    cam = synth.look_at([0.2, 0.1, -2], [0, 0, 3], 24, 16, 70.0)
+    flip = np.diag([-1.0, -1.0, 1.0]).astype(np.float32)
+    rolled = synth.pinhole(24, 16, fx=cam.fx, R=flip @ cam.R, t=flip @ cam.t)
+    bg = synth.Background(mode, 8, 16)
+    Cfg, T = np.zeros((16, 24, 3)), np.ones((16, 24))
+    _, ca = orc.background(cam, fl, bg, Cfg, T)
+    _, cb = orc.background(rolled, fl, bg, Cfg, T)
+    np.testing.assert_allclose(cb, ca[::-1, ::-1], rtol=1e-12, atol=1e-14)
+    assert np.abs(ca - ca[::-1, ::-1]).max() > 1e-3  # the view itself is not symmetric
+
+
 def test_background_map_converges_to_exact_mode(orc):
     """Map-mode geometry (texel centres, the longitude and latitude axes,
     bilinear weights) against the exact mode: seen from the centre of a cubic
