@@ -21,7 +21,10 @@
  *   hash encoding    linear functions reproduced on a dense level, partition
  *                    of unity, level resolutions, Instant-NGP hash definition
  *   MLP / PE         numpy matmul reference; closed-form sin/cos values
- *   query + bwd      reduction to the biases; central finite differences
+ *   query + bwd      reduction to the biases; central finite differences;
+ *                    outputs unchanged under a camera roll about its centre
+ *                    (world-space view direction), geometry independent of
+ *                    the camera
  *   pre-cull         hand cases; FP64 agreement away from the thresholds
  *   projection       on-axis closed form; scipy rotation + FD Jacobian
  *                    reference; FD backward; FP32 rect vs FP64 definition

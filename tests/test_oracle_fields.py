@@ -166,6 +166,31 @@ def test_query_reduces_to_bias_when_weights_vanish(orc):
     np.testing.assert_allclose(c, sig(fl.col_mlp.b[-1].astype(np.float64)[None] + ce), rtol=1e-14)
 
 
+def test_query_depends_on_the_camera_centre_only(orc):
+    """The colour decoder's view direction (Eq. 6) runs from the camera centre
+    to the Gaussian in world space, and the geometry decoder sees no camera:
+    a camera rolled by 180 degrees about its optical axis (same centre) gives
+    the same outputs for every Gaussian, while moving the centre changes the
+    colours. The camera-space direction would fail the first check."""
+    rng = np.random.default_rng(14)
+    fl = _small_fields(rng)
+    n = 16
+    pos = rng.uniform(-1, 3, (n, 3))
+    ae, se, ce = rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal((n, 3))
+    cam = synth.look_at([0.5, -0.3, -4], [1, 1, 1], 64, 48, 60.0)
+    flip = np.diag([-1.0, -1.0, 1.0]).astype(np.float32)
+    rolled = synth.pinhole(64, 48, fx=cam.fx, R=flip @ cam.R, t=flip @ cam.t)
+    out_a = orc.query_fields(pos, ae, se, ce, cam, fl)
+    out_b = orc.query_fields(pos, ae, se, ce, rolled, fl)
+    for x, y in zip(out_a, out_b):
+        np.testing.assert_allclose(y, x, rtol=1e-12, atol=1e-15)
+    moved = synth.look_at([2.5, -0.3, -4], [1, 1, 1], 64, 48, 60.0)
+    out_c = orc.query_fields(pos, ae, se, ce, moved, fl)
+    for x, y in zip(out_a[:3], out_c[:3]):
+        np.testing.assert_allclose(y, x, rtol=1e-12, atol=1e-15)  # geometry: no camera
+    assert np.abs(out_c[3] - out_a[3]).max() > 1e-4  # colour: the direction changed
+
+
 def test_query_backward_matches_finite_differences(orc):
     rng = np.random.default_rng(9)
     fl = _small_fields(rng)
