@@ -34,8 +34,9 @@
  *                    Gaussian in is dropped); packed row spans decode to the
  *                    instance lists; footprint lists composite exactly like
  *                    the rectangles
- *   compositing      single-Gaussian closed form; weights sum to 1 - T_final;
- *                    FD backward
+ *   compositing      single-Gaussian closed form; two overlapping Gaussians
+ *                    in either depth order (front-to-back closed form);
+ *                    weights sum to 1 - T_final; FD backward
  *   background       |o + t d| = r with t > 0; constant field; FD backward;
  *                    a camera rolled by 180 degrees sees the same colour
  *                    along the same world ray (pixel (W-1-i, H-1-j)).

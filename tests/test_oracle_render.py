@@ -230,6 +230,35 @@ def test_single_gaussian_closed_form(orc):
     np.testing.assert_allclose(C, a[..., None] * col[0], atol=1e-15)
 
 
+def test_two_gaussians_composite_front_to_back(orc):
+    """Eq. 1 for two overlapping Gaussians binned and depth-sorted together:
+    C = c_n a_n + c_f a_f (1 - a_n) and T = (1 - a_n)(1 - a_f) at every pixel,
+    with n the nearer one whatever the input order; swapping the depths swaps
+    the roles."""
+    W, H = 40, 32
+    TX, TY = orc.tiles_of(W, H)
+    m = np.array([[15.2, 13.7], [21.9, 17.4]])
+    con = np.array([[0.02, 0.004, 0.03], [0.03, -0.006, 0.025]])
+    op = np.array([0.7, 0.8])
+    col = np.array([[0.9, 0.2, 0.1], [0.1, 0.3, 0.95]])
+    rect = np.array([[0, 0, TX, TY]] * 2, np.int32)
+    ys, xs = np.mgrid[0:H, 0:W]
+
+    def alpha(g):
+        dx, dy = m[g, 0] - (xs + 0.5), m[g, 1] - (ys + 0.5)
+        a = np.minimum(0.99, op[g] * np.exp(-0.5 * (con[g, 0] * dx ** 2 + con[g, 2] * dy ** 2)
+                                            - con[g, 1] * dx * dy))
+        return np.where(a < 1 / 255, 0.0, a)
+    for depths, near, far in (([5.0, 2.0], 1, 0), ([2.0, 5.0], 0, 1)):
+        _, vals, ranges = orc.bin_sort(rect, np.array(depths, np.float32), TX, TY)
+        C, T, _, _ = orc.rasterize(W, H, ranges, vals, m, con, op, col)
+        an, af = alpha(near), alpha(far)
+        np.testing.assert_allclose(T, (1 - an) * (1 - af), atol=1e-15)
+        np.testing.assert_allclose(C, an[..., None] * col[near] + (af * (1 - an))[..., None] * col[far],
+                                   atol=1e-14)
+        assert (an * af > 0.1).sum() > 20  # the two overlap
+
+
 def test_weights_sum_to_one_minus_T(orc):
     rng = np.random.default_rng(6)
     W, H = 64, 48
